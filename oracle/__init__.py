@@ -1,0 +1,194 @@
+"""CPU oracle for the ATM linked-cell method (arXiv 2510.21230).
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  It wraps the plain C
+oracle in ``atm_oracle.c`` through ctypes and shares nothing with the CUDA
+library.
+
+Every array argument is a NumPy array; 3-vectors are SoA ``[3, n]`` (x row,
+y row, z row) in float64.
+"""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "atm_oracle.c")
+_LIB = os.path.join(_HERE, "libatm_oracle.so")
+
+TRAV = {"3c01": 0, "3c18": 1, "3c08": 2}
+TRUNC = {"pair": 0, "product": 1}
+PREC = {"fp64": 0, "fp32": 1}
+
+GCC_FLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+             "-fno-fast-math", "-Wall"]
+
+
+def build(force=False):
+    """Compile the oracle with gcc (no contraction of multiply-adds)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    tmp = _LIB + ".%d.tmp" % os.getpid()
+    subprocess.check_call(["gcc", *GCC_FLAGS, "-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        d, i64, i32, ci = ctypes.c_double, ctypes.c_int64, ctypes.c_int32, ctypes.c_int
+        P = ctypes.c_void_p
+        L.orc_atm_u.restype = d
+        L.orc_atm_u.argtypes = [d, d, d, d]
+        L.orc_atm_du_dsq.restype = None
+        L.orc_atm_du_dsq.argtypes = [d, d, d, d, P]
+        L.orc_atm_dudr_paper.restype = d
+        L.orc_atm_dudr_paper.argtypes = [d, d, d, d]
+        L.orc_cell_grid.restype = ci
+        L.orc_cell_grid.argtypes = [P, P, P]
+        L.orc_build_cells.restype = ci
+        L.orc_build_cells.argtypes = [P, i64, P, P, P, P, P, P, P]
+        L.orc_atm_brute.restype = ci
+        L.orc_atm_brute.argtypes = [P, i64, P, ci, ci, P, P, P]
+        L.orc_atm_cells.restype = ci
+        L.orc_atm_cells.argtypes = [P, i64, P, ci, ci, ci, i64, i64, P, P, P]
+        L.orc_lj_brute.restype = ci
+        L.orc_lj_brute.argtypes = [P, i64, P, P, P, P]
+        L.orc_lj_cells.restype = ci
+        L.orc_lj_cells.argtypes = [P, i64, P, ci, P, P, P]
+        L.orc_md_run.restype = ci
+        L.orc_md_run.argtypes = [P, i64, P, P, ci, d, ci, ci, ci, P, P]
+        L.orc_num_threads.restype = ci
+        L.orc_num_threads.argtypes = []
+        _lib = L
+    return _lib
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(st):
+    if st != 0:
+        raise OracleError({1: "invalid argument", 2: "box smaller than 3 cells"}.get(st, str(st)))
+
+
+def params(box, rc, nu, lj_eps=1.0, lj_sigma=1.0, lj_shift=False):
+    b = np.broadcast_to(np.asarray(box, dtype=np.float64), (3,))
+    return np.array([b[0], b[1], b[2], rc, nu, lj_eps, lj_sigma, 1.0 if lj_shift else 0.0],
+                    dtype=np.float64)
+
+
+def _soa(x):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    assert x.ndim == 2 and x.shape[0] == 3
+    return x
+
+
+def atm_u(a, b, c, nu):
+    return lib().orc_atm_u(a, b, c, nu)
+
+
+def atm_du_dsq(a, b, c, nu):
+    out = np.zeros(3)
+    lib().orc_atm_du_dsq(a, b, c, nu, _p(out))
+    return out
+
+
+def atm_dudr_paper(rij, rik, rjk, nu):
+    return lib().orc_atm_dudr_paper(rij, rik, rjk, nu)
+
+
+def cell_grid(prm):
+    nc = np.zeros(3, dtype=np.int32)
+    w = np.zeros(3)
+    _check(lib().orc_cell_grid(_p(prm), _p(nc), _p(w)))
+    return nc, w
+
+
+def build_cells(prm, x):
+    x = _soa(x)
+    n = x.shape[1]
+    nc, _ = cell_grid(prm)
+    ncell = int(np.prod(nc.astype(np.int64)))
+    xw = np.zeros((3, n))
+    cell_of = np.zeros(n, dtype=np.int32)
+    start = np.zeros(ncell + 1, dtype=np.int32)
+    perm = np.zeros(n, dtype=np.int32)
+    xl = np.zeros((3, n))
+    xl32 = np.zeros((3, n), dtype=np.float32)
+    _check(lib().orc_build_cells(_p(prm), n, _p(x), _p(xw), _p(cell_of), _p(start), _p(perm),
+                                 _p(xl), _p(xl32)))
+    return dict(xw=xw, cell_of=cell_of, cell_start=start, perm=perm, xl=xl, xl32=xl32,
+                ncell=nc)
+
+
+def atm_brute(prm, x, trunc="pair", member=None):
+    x = _soa(x)
+    n = x.shape[1]
+    f = np.zeros((3, n))
+    ew = np.zeros(2)
+    cnt = np.zeros(1, dtype=np.uint64)
+    m = -1 if member is None else TRAV[member]
+    _check(lib().orc_atm_brute(_p(prm), n, _p(x), TRUNC[trunc], m, _p(f), _p(ew), _p(cnt)))
+    return dict(f=f, e3=ew[0], w3=ew[1], n_int3=int(cnt[0]))
+
+
+def atm_cells(prm, x, trav="3c18", trunc="pair", prec="fp64", unit_lo=-1, unit_hi=-1):
+    x = _soa(x)
+    n = x.shape[1]
+    f = np.zeros((3, n))
+    ew = np.zeros(2)
+    cnt = np.zeros(2, dtype=np.uint64)
+    _check(lib().orc_atm_cells(_p(prm), n, _p(x), TRAV[trav], TRUNC[trunc], PREC[prec],
+                               unit_lo, unit_hi, _p(f), _p(ew), _p(cnt)))
+    return dict(f=f, e3=ew[0], w3=ew[1], n_cand3=int(cnt[0]), n_int3=int(cnt[1]))
+
+
+def lj_brute(prm, x):
+    x = _soa(x)
+    n = x.shape[1]
+    f = np.zeros((3, n))
+    ew = np.zeros(2)
+    cnt = np.zeros(1, dtype=np.uint64)
+    _check(lib().orc_lj_brute(_p(prm), n, _p(x), _p(f), _p(ew), _p(cnt)))
+    return dict(f=f, e2=ew[0], w2=ew[1], n_int2=int(cnt[0]))
+
+
+def lj_cells(prm, x, prec="fp64"):
+    x = _soa(x)
+    n = x.shape[1]
+    f = np.zeros((3, n))
+    ew = np.zeros(2)
+    cnt = np.zeros(2, dtype=np.uint64)
+    _check(lib().orc_lj_cells(_p(prm), n, _p(x), PREC[prec], _p(f), _p(ew), _p(cnt)))
+    return dict(f=f, e2=ew[0], w2=ew[1], n_cand2=int(cnt[0]), n_int2=int(cnt[1]))
+
+
+def md_run(prm, x, v, nsteps, dt, trav="3c18", trunc="pair", prec="fp64"):
+    """Velocity-Verlet NVE; returns final x, v, f and per-step energies
+    ``[nsteps+1, 4]`` = (E2, E3, Ekin, W2+W3)."""
+    x = _soa(x).copy()
+    v = _soa(v).copy()
+    n = x.shape[1]
+    f = np.zeros((3, n))
+    en = np.zeros((nsteps + 1, 4))
+    _check(lib().orc_md_run(_p(prm), n, _p(x), _p(v), nsteps, dt, TRAV[trav], TRUNC[trunc],
+                            PREC[prec], _p(f), _p(en)))
+    return dict(x=x, v=v, f=f, energies=en)
+
+
+def num_threads():
+    return lib().orc_num_threads()

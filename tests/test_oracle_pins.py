@@ -1,0 +1,414 @@
+"""Pins of the CPU oracle against facts the paper and mathematics fix.
+
+Each test checks the oracle against something other than itself: closed-form
+energies of Eq. atm, the paper's separately printed gradient (Eq. ATMGradient),
+finite differences, the Euler identity of a degree -9 homogeneous potential,
+Newton's third law (Eq. newton3rdlaw), the counting identities of section 3,
+invariances, and brute force against linked cells.
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2510_21230_gb300 import synth
+
+NU = 0.073
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            rows.append([float(t) for t in line.split()])
+    return np.array(rows)
+
+
+# ---------------------------------------------------------------- potential
+
+def test_equilateral_and_collinear_closed_forms():
+    """Eq. atm: equilateral side r gives 11 nu / (8 r^9); collinear r, r, 2r gives -nu / (4 r^9)."""
+    g = _read_golden("atm_closed_forms.txt")
+    for nu, r, e_eq, e_col in g:
+        u_eq = oracle.atm_u(r * r, r * r, r * r, nu)
+        u_col = oracle.atm_u(r * r, 4 * r * r, r * r, nu)  # i--j = r, i--k = 2r, j--k = r
+        assert u_eq == pytest.approx(e_eq, rel=4e-16 * 8)
+        assert u_col == pytest.approx(e_col, rel=4e-16 * 64)
+        assert u_eq == pytest.approx(11 * nu / (8 * r ** 9), rel=1e-14)
+        assert u_col == pytest.approx(-nu / (4 * r ** 9), rel=1e-13)
+
+
+def test_energy_symmetric_in_sides():
+    rng = np.random.default_rng(1)
+    for _ in range(200):
+        p = rng.normal(size=(3, 3))
+        a = np.sum((p[0] - p[1]) ** 2)
+        b = np.sum((p[0] - p[2]) ** 2)
+        c = np.sum((p[1] - p[2]) ** 2)
+        vals = [oracle.atm_u(*perm, NU) for perm in itertools.permutations((a, b, c))]
+        assert np.allclose(vals, vals[0], rtol=1e-13, atol=0)
+
+
+def test_gradient_matches_paper_eleven_term_form():
+    """2 r_ij du/da equals du/dr_ij of Eq. ATMGradient; the other sides by cycling i, j, k."""
+    rng = np.random.default_rng(2)
+    for _ in range(300):
+        p = rng.uniform(0, 2.5, size=(3, 3))
+        rij = np.linalg.norm(p[0] - p[1])
+        rik = np.linalg.norm(p[0] - p[2])
+        rjk = np.linalg.norm(p[1] - p[2])
+        if min(rij, rik, rjk) < 0.7:
+            continue
+        du = oracle.atm_du_dsq(rij * rij, rik * rik, rjk * rjk, NU)
+        assert 2 * rij * du[0] == pytest.approx(oracle.atm_dudr_paper(rij, rik, rjk, NU), rel=1e-11)
+        # du/dr_ik: r_ik plays the role of r_ij, with (r_ij, r_jk) as the other two
+        assert 2 * rik * du[1] == pytest.approx(oracle.atm_dudr_paper(rik, rij, rjk, NU), rel=1e-11)
+        assert 2 * rjk * du[2] == pytest.approx(oracle.atm_dudr_paper(rjk, rij, rik, NU), rel=1e-11)
+
+
+def test_gradient_by_finite_differences_of_side_squares():
+    a, b, c = 1.21, 1.69, 2.89
+    du = oracle.atm_du_dsq(a, b, c, NU)
+    h = 1e-6
+    fd = [(oracle.atm_u(a + h, b, c, NU) - oracle.atm_u(a - h, b, c, NU)) / (2 * h),
+          (oracle.atm_u(a, b + h, c, NU) - oracle.atm_u(a, b - h, c, NU)) / (2 * h),
+          (oracle.atm_u(a, b, c + h, NU) - oracle.atm_u(a, b, c - h, NU)) / (2 * h)]
+    assert np.allclose(du, fd, rtol=1e-7)
+
+
+# ---------------------------------------------------------------- small systems
+
+def _small_fluid(n=60, rho=0.5, seed=7, rc=2.5):
+    rng = np.random.default_rng(seed)
+    box = (n / rho) ** (1 / 3)
+    box = max(box, 3 * rc + 0.1)
+    x = synth.random_sequential(n, [0, 0, 0], [box] * 3, 0.9, rng, box=np.array([box] * 3))
+    return np.ascontiguousarray(x.T), box
+
+
+def _prm(box, rc=2.5, nu=NU, shift=False):
+    return oracle.params(box, rc, nu, lj_shift=shift)
+
+
+@pytest.mark.parametrize("trunc", ["pair", "product"])
+def test_forces_are_minus_energy_gradient(trunc):
+    """Central finite differences of the brute-force E3 reproduce its forces (F = -grad u)."""
+    x, box = _small_fluid(n=40, rho=0.3, seed=11)
+    prm = _prm(box)
+    ref = oracle.atm_brute(prm, x, trunc)
+    assert ref["n_int3"] > 20
+    h = 1e-6
+    rng = np.random.default_rng(3)
+    for _ in range(12):
+        d, i = rng.integers(3), rng.integers(x.shape[1])
+        xp = x.copy(); xp[d, i] += h
+        xm = x.copy(); xm[d, i] -= h
+        ep = oracle.atm_brute(prm, xp, trunc)["e3"]
+        em = oracle.atm_brute(prm, xm, trunc)["e3"]
+        fd = -(ep - em) / (2 * h)
+        scale = np.abs(ref["f"]).max()
+        assert abs(fd - ref["f"][d, i]) < 1e-6 * scale + 1e-7 * abs(fd)
+
+
+def test_lj_forces_are_minus_energy_gradient():
+    x, box = _small_fluid(n=40, rho=0.3, seed=12)
+    prm = _prm(box)
+    ref = oracle.lj_brute(prm, x)
+    h = 1e-6
+    for d, i in [(0, 3), (1, 17), (2, 29)]:
+        xp = x.copy(); xp[d, i] += h
+        xm = x.copy(); xm[d, i] -= h
+        fd = -(oracle.lj_brute(prm, xp)["e2"] - oracle.lj_brute(prm, xm)["e2"]) / (2 * h)
+        assert fd == pytest.approx(ref["f"][d, i], rel=1e-6, abs=1e-7)
+
+
+def test_lj_closed_form_minimum():
+    """At r = 2^(1/6) sigma the LJ pair energy is -eps and the force vanishes."""
+    r = 2 ** (1 / 6)
+    box = 10.0
+    x = np.array([[1.0, 1.0 + r], [2.0, 2.0], [3.0, 3.0]])
+    out = oracle.lj_brute(_prm(box), x)
+    assert out["e2"] == pytest.approx(-1.0, rel=1e-14)
+    assert np.abs(out["f"]).max() < 1e-13
+    x1 = np.array([[1.0, 2.0], [2.0, 2.0], [3.0, 3.0]])
+    assert oracle.lj_brute(_prm(box), x1)["e2"] == pytest.approx(0.0, abs=1e-14)
+
+
+@pytest.mark.parametrize("trunc", ["pair", "product"])
+def test_virial_is_nine_times_energy(trunc):
+    """u is homogeneous of degree -9 in lengths, so r . grad u = -9 u and W3 = 9 E3."""
+    x, box = _small_fluid(n=80, rho=0.5, seed=13)
+    prm = _prm(box)
+    for trav in ["3c01", "3c18", "3c08"]:
+        out = oracle.atm_cells(prm, x, trav, trunc)
+        assert out["w3"] == pytest.approx(9 * out["e3"], rel=1e-12)
+    bf = oracle.atm_brute(prm, x, trunc)
+    assert bf["w3"] == pytest.approx(9 * bf["e3"], rel=1e-12)
+
+
+@pytest.mark.parametrize("trav", ["3c18", "3c08"])
+@pytest.mark.parametrize("trunc", ["pair", "product"])
+def test_net_force_vanishes_with_newton3(trav, trunc):
+    x, box = _small_fluid(n=80, rho=0.5, seed=14)
+    out = oracle.atm_cells(_prm(box), x, trav, trunc)
+    scale = np.abs(out["f"]).max()
+    assert np.abs(out["f"].sum(axis=1)).max() < 1e-12 * scale * x.shape[1]
+
+
+def test_permutation_invariance():
+    x, box = _small_fluid(n=70, rho=0.5, seed=15)
+    prm = _prm(box)
+    rng = np.random.default_rng(4)
+    p = rng.permutation(x.shape[1])
+    for trav in ["3c01", "3c18", "3c08"]:
+        a = oracle.atm_cells(prm, x, trav, "pair")
+        b = oracle.atm_cells(prm, x[:, p], trav, "pair")
+        assert a["n_int3"] == b["n_int3"] and a["n_cand3"] == b["n_cand3"]
+        assert b["e3"] == pytest.approx(a["e3"], rel=1e-12)
+        assert np.allclose(b["f"], a["f"][:, p], rtol=1e-10, atol=1e-13)
+
+
+def test_translation_invariance_pair_rule():
+    x, box = _small_fluid(n=70, rho=0.5, seed=16)
+    prm = _prm(box)
+    shift = np.array([[0.37], [-1.91], [4.4]])
+    for trav in ["3c01", "3c18", "3c08"]:
+        a = oracle.atm_cells(prm, x, trav, "pair")
+        b = oracle.atm_cells(prm, x + shift, trav, "pair")
+        assert a["n_int3"] == b["n_int3"]
+        assert b["e3"] == pytest.approx(a["e3"], rel=1e-10)
+        assert np.allclose(b["f"], a["f"], rtol=1e-8, atol=1e-11)
+
+
+def test_periodic_image_shift_changes_nothing():
+    x, box = _small_fluid(n=70, rho=0.5, seed=17)
+    prm = _prm(box)
+    img = x.copy()
+    img[:, ::3] += box * np.array([[1.0], [-2.0], [3.0]])
+    a = oracle.atm_brute(prm, x, "pair")
+    b = oracle.atm_brute(prm, img, "pair")
+    assert a["n_int3"] == b["n_int3"]
+    assert b["e3"] == pytest.approx(a["e3"], rel=1e-12)
+
+
+# ---------------------------------------------------------------- brute force vs cells
+
+@pytest.mark.parametrize("ncell_target", [3, 4, 5])
+@pytest.mark.parametrize("seed", [21, 22])
+def test_brute_force_equals_every_traversal_pair_rule(ncell_target, seed):
+    """Pair rule: every traversal finds exactly the interacting triplets of the
+    O(N^3) minimum-image brute force (cell edge >= r_c, >= 3 cells per axis)."""
+    rc = 2.5
+    box = ncell_target * rc + 0.3
+    rng = np.random.default_rng(seed)
+    n = int(0.35 * box ** 3)
+    x = synth.random_sequential(n, [0, 0, 0], [box] * 3, 0.85, rng, box=np.array([box] * 3)).T
+    x = np.ascontiguousarray(x)
+    prm = _prm(box, rc)
+    bf = oracle.atm_brute(prm, x, "pair")
+    assert bf["n_int3"] > 100
+    for trav in ["3c18", "3c08"]:
+        lc = oracle.atm_cells(prm, x, trav, "pair")
+        assert lc["n_int3"] == bf["n_int3"], trav
+        assert lc["e3"] == pytest.approx(bf["e3"], rel=1e-11)
+        assert np.allclose(lc["f"], bf["f"], rtol=1e-9, atol=1e-12)
+    # 3c01 visits each triplet once per owner and adds u/3 per visit
+    lc = oracle.atm_cells(prm, x, "3c01", "pair")
+    assert lc["n_int3"] == 3 * bf["n_int3"]
+    assert lc["e3"] == pytest.approx(bf["e3"], rel=1e-11)
+    assert np.allclose(lc["f"], bf["f"], rtol=1e-9, atol=1e-12)
+
+
+@pytest.mark.parametrize("trav", ["3c01", "3c18", "3c08"])
+def test_brute_force_with_membership_equals_cells_product_rule(trav):
+    """Product rule: the brute force restricted to the cell triples a traversal
+    visits equals the linked-cell traversal (box of 6 cells per axis, so the
+    base-frame displacement of every visited pair is its minimum image)."""
+    rc = 1.0
+    box = 6.4
+    rng = np.random.default_rng(31)
+    x = np.ascontiguousarray(
+        synth.random_sequential(240, [0, 0, 0], [box] * 3, 0.45, rng, box=np.array([box] * 3)).T)
+    prm = _prm(box, rc)
+    bf = oracle.atm_brute(prm, x, "product", member=trav)
+    lc = oracle.atm_cells(prm, x, trav, "product")
+    assert lc["n_int3"] == bf["n_int3"]
+    assert lc["e3"] == pytest.approx(bf["e3"], rel=1e-11)
+    assert np.allclose(lc["f"], bf["f"], rtol=1e-9, atol=1e-12)
+
+
+def test_pair_cutoff_is_subset_of_product_and_traversal_order():
+    """Pair-rule triplets are product-rule triplets; product triplets found:
+    3c01 >= 3c18 >= 3c08 (section 4)."""
+    x, box = _small_fluid(n=300, rho=0.6, seed=18, rc=2.5)
+    prm = _prm(box)
+    full = oracle.atm_brute(prm, x, "product")
+    got = {}
+    for trav in ["3c01", "3c18", "3c08"]:
+        pr = oracle.atm_cells(prm, x, trav, "pair")
+        pd = oracle.atm_cells(prm, x, trav, "product")
+        assert pr["n_int3"] <= pd["n_int3"]
+        got[trav] = pd["n_int3"]
+    assert got["3c18"] >= got["3c08"]
+    assert got["3c01"] >= got["3c18"]
+    assert full["n_int3"] >= got["3c18"]
+
+
+# ---------------------------------------------------------------- counting identities
+
+def _counts_per_cell(cells):
+    st = cells["cell_start"]
+    return np.diff(st).astype(np.int64)
+
+
+def _comb2(n):
+    return n * (n - 1) // 2
+
+
+def _comb3(n):
+    return n * (n - 1) * (n - 2) // 6
+
+
+def test_candidate_counts_follow_cell_identities():
+    """Candidate triplets of each traversal equal the sums of Eq. celltriplet,
+    Eq. twoonetriplets and Eq. carttriplets over the tasks it visits."""
+    x, box = _small_fluid(n=200, rho=0.5, seed=19)
+    prm = _prm(box)
+    cells = oracle.build_cells(prm, x)
+    nc = cells["ncell"]
+    cnt = _counts_per_cell(cells).reshape(nc[2], nc[1], nc[0])
+
+    def N(z, y, xx):
+        return int(cnt[z % nc[2], y % nc[1], xx % nc[0]])
+
+    fwd = [(dx, dy, dz) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)
+           if (dz, dy, dx) > (0, 0, 0)]
+    t18 = t08 = t01 = 0
+    for z in range(nc[2]):
+        for y in range(nc[1]):
+            for xx in range(nc[0]):
+                nb = N(z, y, xx)
+                t18 += _comb3(nb)
+                for (dx, dy, dz) in fwd:
+                    nn = N(z + dz, y + dy, xx + dx)
+                    t18 += nn * _comb2(nb) + nb * _comb2(nn)
+                for p, q in itertools.combinations(fwd, 2):
+                    t18 += nb * N(z + p[2], y + p[1], xx + p[0]) * N(z + q[2], y + q[1], xx + q[0])
+                # 3c08 block
+                sl = [N(z + (s >> 2 & 1), y + (s >> 1 & 1), xx + (s & 1)) for s in range(8)]
+                t08 += _comb3(sl[0])
+                for s, t in itertools.combinations(range(8), 2):
+                    if s & t == 0:
+                        t08 += sl[t] * _comb2(sl[s]) + sl[s] * _comb2(sl[t])
+                for s, t, u in itertools.combinations(range(8), 3):
+                    if s & t & u == 0:
+                        t08 += sl[s] * sl[t] * sl[u]
+                # 3c01: each molecule of the base cell against all pairs of the other
+                # molecules in its 27-cell neighbourhood
+                m = sum(N(z + dz, y + dy, xx + dx) for dz in (-1, 0, 1) for dy in (-1, 0, 1)
+                        for dx in (-1, 0, 1))
+                t01 += nb * _comb2(m - 1)
+    assert oracle.atm_cells(prm, x, "3c18", "pair")["n_cand3"] == t18
+    assert oracle.atm_cells(prm, x, "3c08", "product")["n_cand3"] == t08
+    assert oracle.atm_cells(prm, x, "3c01", "pair")["n_cand3"] == t01
+
+
+@pytest.mark.parametrize("trav", ["3c18", "3c08"])
+def test_three_cell_toy_visits_every_triple_once(trav):
+    """Eq. totalInteractions: molecules in three mutually adjacent cells are
+    split into one-, two- and three-cell triplets adding up to C(N,3)."""
+    rc = 2.5
+    box = 3 * rc + 0.03
+    w = box / 3
+    rng = np.random.default_rng(5)
+    pts = []
+    for cx, cy, cz, m in [(0, 0, 0, 5), (1, 0, 0, 4), (0, 1, 1, 6)]:
+        for _ in range(m):
+            pts.append([(cx + 0.1 + 0.8 * rng.random()) * w, (cy + 0.1 + 0.8 * rng.random()) * w,
+                        (cz + 0.1 + 0.8 * rng.random()) * w])
+    x = np.ascontiguousarray(np.array(pts).T)
+    n = x.shape[1]
+    out = oracle.atm_cells(_prm(box, rc), x, trav, "pair")
+    assert out["n_cand3"] == _comb3(n)
+
+
+# ---------------------------------------------------------------- cells
+
+def test_cells_bin_and_stable_sort():
+    x, box = _small_fluid(n=150, rho=0.5, seed=20)
+    x = x + np.array([[box], [-box], [2.5 * box]])  # outside the box: must wrap
+    prm = _prm(box)
+    c = oracle.build_cells(prm, x)
+    nc, w = oracle.cell_grid(prm)
+    n = x.shape[1]
+    assert c["cell_start"][0] == 0 and c["cell_start"][-1] == n
+    assert np.all(np.diff(c["cell_start"]) >= 0)
+    assert sorted(c["perm"]) == list(range(n))
+    for cid in range(len(c["cell_start"]) - 1):
+        seg = c["perm"][c["cell_start"][cid]:c["cell_start"][cid + 1]]
+        assert np.all(np.diff(seg) > 0)  # stable: original order inside a cell
+        assert np.all(c["cell_of"][seg] == cid)
+    xw = c["xw"]
+    assert np.all(xw >= 0) and np.all(xw < box)
+    cz, rem = np.divmod(c["cell_of"], nc[0] * nc[1])
+    cy, cx = np.divmod(rem, nc[0])
+    for d, cd in enumerate([cx, cy, cz]):
+        assert np.all(xw[d] >= cd * w[d] - 1e-12) and np.all(xw[d] <= (cd + 1) * w[d] + 1e-12)
+        xl = c["xl"][d]
+        assert np.all(xl >= 0) and np.all(xl <= w[d])
+        assert np.allclose(xl, xw[d][c["perm"]] - cd[c["perm"]] * w[d], atol=1e-12)
+    assert np.array_equal(c["xl32"], c["xl"].astype(np.float32))
+
+
+def test_cell_grid_rule():
+    """n_d is the largest k with L/k >= r_c; fewer than three cells is an error."""
+    nc, w = oracle.cell_grid(oracle.params([37.5, 10.0, 7.6], 2.5, NU))
+    assert list(nc) == [15, 4, 3]
+    assert w[0] == 2.5
+    with pytest.raises(oracle.OracleError):
+        oracle.cell_grid(oracle.params([7.4, 10.0, 10.0], 2.5, NU))
+
+
+# ---------------------------------------------------------------- FP32 decisions, LJ, MD
+
+def test_fp32_decisions_close_to_fp64():
+    x, box = _small_fluid(n=300, rho=0.6, seed=23)
+    prm = _prm(box)
+    for trunc in ["pair", "product"]:
+        a = oracle.atm_cells(prm, x, "3c18", trunc, "fp64")
+        b = oracle.atm_cells(prm, x, "3c18", trunc, "fp32")
+        assert a["n_cand3"] == b["n_cand3"]
+        assert abs(a["n_int3"] - b["n_int3"]) <= max(2, 1e-4 * a["n_int3"])
+
+
+def test_lj_cells_equal_brute_force():
+    x, box = _small_fluid(n=200, rho=0.5, seed=24)
+    prm = _prm(box)
+    a = oracle.lj_brute(prm, x)
+    b = oracle.lj_cells(prm, x)
+    assert a["n_int2"] == b["n_int2"]
+    assert b["e2"] == pytest.approx(a["e2"], rel=1e-12)
+    assert b["w2"] == pytest.approx(a["w2"], rel=1e-12)
+    assert np.allclose(a["f"], b["f"], rtol=1e-10, atol=1e-12)
+
+
+def test_velocity_verlet_is_time_reversible_and_conserves_energy():
+    cfg = synth.homogeneous(256, 0.8, 1.0, seed=99)
+    prm = oracle.params(cfg["box"], 2.5, NU, lj_shift=True)
+    # the fcc box for 256 at rho 0.8 is 6.84 < 3 r_c: shrink the cutoff
+    prm[3] = 2.2
+    out = oracle.md_run(prm, cfg["x"], cfg["v"], 40, 0.002, "3c18", "pair")
+    en = out["energies"]
+    etot = en[:, 0] + en[:, 1] + en[:, 2]
+    assert np.max(np.abs(etot - etot[0])) < 2e-3 * abs(etot[0]) + 0.05
+    back = oracle.md_run(prm, out["x"], -out["v"], 40, 0.002, "3c18", "pair")
+    d = back["x"] - np.mod(cfg["x"], cfg["box"][:, None])
+    d -= np.rint(d / cfg["box"][:, None]) * cfg["box"][:, None]
+    assert np.abs(d).max() < 1e-8
