@@ -1,0 +1,401 @@
+"""Benchmark: LJ + ATM molecular-dynamics steps on a homogeneous liquid.
+
+One step = one velocity-Verlet step of the whole hot path through the C ABI:
+half kick + drift, wrap + bin + stable sort into linked cells, LJ pair forces,
+ATM three-body forces (traversal x truncation x precision), reductions of
+energy / virial / counts, second half kick.  The default workload is the
+N = 256,000 liquid at rho* = 0.8, T* = 1.0 (fcc start with +-0.05 jitter,
+r_c = 2.5, nu = 0.073), 3c08 traversal, pair truncation, FP32C arithmetic.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
+the host cores on a bounded sample of the same workload instead.
+
+Multi-GPU (torchrun): every rank advances its own independent replica (seeded
+by rank); there is no data-path collective ("replicas only", weak scaling).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2510_21230_gb300 import synth  # noqa: E402
+
+METRIC = "3-body molecule updates/s at N=256k, FP64 exact vs FP32 vs surrogate at stated error"
+UNIT = "molecule updates/s"
+NU, RC = 0.073, 2.5
+L2_FLUSH_BYTES = 256 << 20
+
+# FP32 / FP64 issue widths per SM per clock on GB300 (152 SMs): 128 FP32 lanes,
+# FP64 derived from the nominal 1.25 TFLOP/s at 2070 MHz (about 2 DFMA per clock per SM)
+SMS = 152
+FP32_FLOPS_PER_CLK_SM = 256.0
+FP64_FLOPS_PER_CLK_SM = 1.25e12 / (SMS * 2.07e9)
+
+# Useful flops per interacting triplet, counted from the kernel's evaluate()
+# (FMA = 2, the reciprocal square root = 1): 3 displacements 42, ATM terms 49,
+# gradient scalars, energy and virial 9, force vectors 27 (3c01: 9).
+F3 = {"3c01": 109.0, "3c18": 127.0, "3c08": 127.0}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="liquid_n256k", choices=sorted(synth.CONFIGS))
+    p.add_argument("--trav", default="3c08", choices=["3c01", "3c18", "3c08"])
+    p.add_argument("--trunc", default="pair", choices=["pair", "product"])
+    p.add_argument("--prec", default="fp32c", choices=["fp64", "fp32c"])
+    p.add_argument("--no-variants", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(name, rank):
+    c = synth.CONFIGS[name]
+    cfg = synth.homogeneous(c["n"], c["rho"], c["T"], c["seed"] + rank)
+    cfg["name"] = name
+    return cfg
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [t.strip() for t in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                                      "sw_power_cap"], parts[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2510_21230_gb300 import atm3, build
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or ws > 1:
+        build.build()
+    if ws > 1:
+        dist.barrier()
+    atm3.load()
+    cfg = workload(args.workload, rank)
+    n = cfg["n"]
+    stream = torch.cuda.current_stream()
+    sysm = atm3.AtmSystem(cfg["box"], n, rc=RC, nu=NU, dt=0.002, device=local,
+                          stream=stream.cuda_stream)
+    sysm.set_state(cfg["x"], cfg["v"])
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def timed(trav, trunc, prec, steps, warmup, clocks=None):
+        sysm.step(warmup, trav, trunc, prec)
+        torch.cuda.synchronize()
+        sysm.set_profiling(True)
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+            time.sleep(0.3)
+        evs = []
+        t_host = time.perf_counter()
+        for _ in range(steps):
+            flush.fill_(1.0)  # evict L2 between timed steps (not timed)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sysm.step(1, trav, trunc, prec, sync=False)
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        t_host = time.perf_counter() - t_host
+        clk = clocks.stop() if clocks else None
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        prof = sysm.get_profile()
+        res = sysm.step(0, trav, trunc, prec)
+        if ws > 1:
+            t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return dict(ms=ms, host_s=t_host, prof=prof, res=res, clocks=clk)
+
+    clocks = ClockSampler(local) if rank == 0 else None
+    main = timed(args.trav, args.trunc, args.prec, args.steps, args.warmup, clocks)
+    ms_step = main["ms"] / args.steps
+    value = n * ws * args.steps / (main["ms"] * 1e-3)
+
+    # roofline of the dominant kernel (ATM triplets): useful flops per launch / launch time
+    prof = main["prof"]
+    atm_ms = prof["ms_atm"] / max(1, prof["n_atm_launches"])
+    flops = F3[args.trav] * main["res"]["n_int3"]
+    pk = peaks()
+    sm_max = pk.get("sm_max_mhz", 2070.0)
+    per_clk = FP32_FLOPS_PER_CLK_SM if args.prec == "fp32c" else FP64_FLOPS_PER_CLK_SM
+    peak = SMS * per_clk * sm_max * 1e6 / 1e12
+    achieved = flops / (atm_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "atm_unit_kernel<%s,%s,%s>" % (args.trav, args.trunc, args.prec),
+                "peak_source": "derived: %d SMs x %.2f flops/clk x %.0f MHz (%s pipe)"
+                               % (SMS, per_clk, sm_max, "FP32" if args.prec == "fp32c" else "FP64"),
+                "flops_per_interacting_triplet": F3[args.trav],
+                "ms_per_launch": atm_ms}
+
+    # paper-style 3-body MUPS: N / (ATM force time)
+    mups_3body = n / (atm_ms * 1e-3)
+
+    # force error of FP32C against the FP64 GPU path on the same state
+    force_err = None
+    if args.prec == "fp32c":
+        sysm.build_cells()
+        sysm.compute_forces(args.trav, args.trunc, "fp64")
+        f64 = sysm.get_forces("atm")
+        sysm.compute_forces(args.trav, args.trunc, "fp32c")
+        f32 = sysm.get_forces("atm")
+        scale = float(np.sqrt(np.mean(f64 ** 2)))
+        d = np.abs(f32 - f64)
+        force_err = {"vs": "fp64 GPU path, same state", "max_abs_over_rms": float(d.max() / scale),
+                     "rms_rel": float(np.sqrt(np.mean(d ** 2)) / scale)}
+
+    # variants (same state, fewer steps)
+    variants = []
+    if not args.no_variants and rank == 0:
+        for tv, tr, pr in [("3c08", "pair", "fp64"), ("3c18", "pair", "fp32c"),
+                           ("3c08", "product", "fp32c"), ("3c18", "pair", "fp64")]:
+            if (tv, tr, pr) == (args.trav, args.trunc, args.prec):
+                continue
+            k = max(2, min(5, args.steps))
+            r = timed(tv, tr, pr, k, 2)
+            am = r["prof"]["ms_atm"] / max(1, r["prof"]["n_atm_launches"])
+            variants.append({"traversal": tv, "truncation": tr, "precision": pr,
+                             "value": n * k / (r["ms"] * 1e-3), "ms_per_step": r["ms"] / k,
+                             "atm_ms_per_launch": am, "mups_3body": n / (am * 1e-3),
+                             "n_int3": r["res"]["n_int3"]})
+
+    # end to end through the public API with host buffers: per step H2D of
+    # (x, v) from pinned memory, one step, D2H of (x, v)
+    e2e = None
+    if rank == 0:
+        xh = torch.empty((3, n), dtype=torch.float64).pin_memory()
+        vh = torch.empty((3, n), dtype=torch.float64).pin_memory()
+        xh.numpy()[:] = cfg["x"]
+        vh.numpy()[:] = cfg["v"]
+        k = max(3, min(args.steps, 10))
+        for it in range(k + 2):
+            if it == 2:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+            sysm.set_state(xh.numpy(), vh.numpy())
+            sysm.step(1, args.trav, args.trunc, args.prec)
+            x2, v2 = sysm.get_state()
+            xh.numpy()[:] = x2
+            vh.numpy()[:] = v2
+        dt = time.perf_counter() - t0
+        e2e = {"value": n * k / dt, "unit": UNIT, "h2d_bytes_per_step": 2 * 3 * n * 8,
+               "d2h_bytes_per_step": 2 * 3 * n * 8 + 72,
+               "note": "host state in, one velocity-Verlet step (re-evaluates F at the "
+                       "input state, then the step), host state out"}
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu:
+            cpu = cpu_baseline(cfg, args.trav, args.trunc, args.cpu_seconds)
+        launches_per_step = prof["n_launches"] / max(1, args.steps + 1)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.prec == "fp32c" else "f64", "data": "synthetic",
+            "config": {"workload": "liquid N=%d rho=0.8 T=1.0 fcc+-0.05 (%s)" % (n, cfg["name"]),
+                       "n": n, "box": float(cfg["box"][0]), "rc": RC, "nu": NU,
+                       "traversal": args.trav, "truncation": args.trunc,
+                       "precision": args.prec, "dt": 0.002, "integrator": "velocity Verlet NVE",
+                       "parallelism": "replicas" if ws > 1 else "single GPU",
+                       "l2": "flushed between timed steps (256 MiB write, untimed)"},
+            "mups_3body": mups_3body,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(prof["n_launches"]),
+            "gpu_launches_per_step": launches_per_step,
+            "clocks": main["clocks"],
+            "force_error": force_err,
+            "profile_ms": {k: prof[k] for k in ("ms_cells", "ms_lj", "ms_atm", "ms_md")},
+            "counts": {k: int(main["res"][k]) for k in ("n_cand3", "n_int3", "n_cand2", "n_int2")},
+            "variants": variants,
+        }
+        print(json.dumps(line))
+    sysm.close()
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return line
+
+
+# ------------------------------------------------------------------ CPU oracle
+
+def cpu_baseline(cfg, trav, trunc, seconds):
+    """The oracle (linked-cell, FP64, OpenMP over units) on a bounded sample of
+    units of the same workload; molecule updates/s = molecules of the sampled
+    base cells / time."""
+    import oracle
+    prm = oracle.params(cfg["box"], RC, NU)
+    cells = oracle.build_cells(prm, cfg["x"])
+    occ = np.diff(cells["cell_start"])
+    ncell = len(occ)
+    u = 16
+    t0 = time.perf_counter()
+    oracle.atm_cells(prm, cfg["x"], trav, trunc, "fp64", 0, u)
+    t = time.perf_counter() - t0
+    while t < 0.5 and u < ncell:
+        u = min(ncell, u * 4)
+        t0 = time.perf_counter()
+        oracle.atm_cells(prm, cfg["x"], trav, trunc, "fp64", 0, u)
+        t = time.perf_counter() - t0
+    per_unit = t / u
+    units = int(min(ncell, max(u, seconds / max(per_unit, 1e-9))))
+    t0 = time.perf_counter()
+    oracle.atm_cells(prm, cfg["x"], trav, trunc, "fp64", 0, units)
+    t = time.perf_counter() - t0
+    mol = int(occ[:units].sum())
+    return {"value": mol / t, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "ATM forces (%s, %s, FP64 linked-cell oracle) of the first %d of %d units "
+                      "(%d molecules) of the N=%d liquid, %.1f s; LJ and integration excluded"
+                      % (trav, trunc, units, ncell, mol, cfg["n"], t)}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return None
+    import oracle
+    cfg = workload(args.workload, 0)
+    prm = oracle.params(cfg["box"], RC, NU)
+    cells = oracle.build_cells(prm, cfg["x"])
+    occ = np.diff(cells["cell_start"])
+    ncell = len(occ)
+    # size one step's sample to about 4 s of CPU work
+    u = 16
+    t0 = time.perf_counter()
+    oracle.atm_cells(prm, cfg["x"], args.trav, args.trunc, "fp64", 0, u)
+    t = time.perf_counter() - t0
+    units = int(min(ncell, max(u, 4.0 / max(t / u, 1e-9))))
+    for _ in range(args.warmup if args.warmup < 2 else 1):
+        oracle.atm_cells(prm, cfg["x"], args.trav, args.trunc, "fp64", 0, min(units, 16))
+    total, mol = 0.0, 0
+    for s in range(args.steps):
+        lo = (s * units) % ncell
+        hi = min(ncell, lo + units)
+        t0 = time.perf_counter()
+        oracle.atm_cells(prm, cfg["x"], args.trav, args.trunc, "fp64", lo, hi)
+        total += time.perf_counter() - t0
+        mol += int(occ[lo:hi].sum())
+    value = mol / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "liquid N=%d rho=0.8 T=1.0 fcc+-0.05 (%s)"
+                                   % (cfg["n"], cfg["name"]),
+                       "n": cfg["n"], "traversal": args.trav, "truncation": args.trunc,
+                       "precision": "fp64"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle",
+                             "sample": "per step the ATM forces of %d consecutive units of %d "
+                                       "(FP64 linked-cell oracle, OpenMP)" % (units, ncell)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return line
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

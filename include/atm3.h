@@ -1,0 +1,177 @@
+/*
+ * atm3.h -- C ABI of the GB300 (sm_103a) library for Axilrod-Teller-Muto
+ * three-body forces over linked-cell triplets, next to Lennard-Jones pair
+ * forces, after "Linked Cell Traversal Algorithms for Three-Body Interactions
+ * in Molecular Dynamics" (arXiv 2510.21230).
+ *
+ * Problem statement (paper section 2 and section 3 opening): N molecules in a
+ * periodic orthorhombic box [0,Lx)x[0,Ly)x[0,Lz), reduced LJ units
+ * (eps = sigma = m = 1 by default), one cutoff radius r_c for pairs and
+ * triplets, ATM strength nu.  Linked cells have edge w_d = L_d / n_d with n_d
+ * the largest integer such that L_d / n_d >= r_c; n_d >= 3 is required.
+ *
+ * Conventions shared by every entry point
+ *  - Every call returns an atm_status; nothing exits, aborts or throws across
+ *    the ABI.  atm_last_error() gives a one-line reason for the last failure.
+ *  - Arrays of 3-vectors are SoA: x[0..n), y[0..n), z[0..n) back to back
+ *    (3n doubles), in the caller's ("original") molecule order.
+ *  - Host pointers are caller-owned and only read or written during the call.
+ *    `_dev` variants take device pointers on the context's device; the data
+ *    is copied on the context's stream and the caller keeps ownership.
+ *  - Work is enqueued on params.cuda_stream (NULL = the legacy default
+ *    stream).  Calls that return host data (atm_get_*, or any call given a
+ *    non-NULL atm_result*) synchronise that stream before returning.
+ *  - The context owns all its device memory (allocated in atm_create, freed in
+ *    atm_destroy).  A context is not thread-safe: one host thread at a time.
+ */
+#ifndef ATM3_H
+#define ATM3_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ATM3_ABI_VERSION 1
+
+typedef enum {
+    ATM_OK = 0,
+    ATM_E_INVALID = 1,       /* bad argument (NULL pointer, n < 0, unknown enum, rc <= 0 ...) */
+    ATM_E_BOX_TOO_SMALL = 2, /* fewer than 3 cells along some axis */
+    ATM_E_CUDA = 3,          /* a CUDA runtime call or kernel launch failed */
+    ATM_E_TIMEOUT = 4,       /* a bounded device-side wait gave up */
+    ATM_E_NONFINITE = 5,     /* a position or velocity is NaN or infinite */
+    ATM_E_STATE = 6,         /* call out of order (e.g. forces before a state was set) */
+    ATM_E_CAPACITY = 7       /* a cell holds more molecules than the kernels stage (see atm_create) */
+} atm_status;
+
+/* Cell-triplet traversals (paper section 4).
+ *  3C01: no Newton-3; for every molecule i of a base cell, every pair {j,k} of
+ *        other molecules in its 27-cell neighbourhood; only F_i is written and
+ *        u/3 is added per visit.
+ *  3C18: Newton-3; base cell, its 13 forward neighbours ((dz,dy,dx)
+ *        lexicographically > 0) and every pair of those neighbours
+ *        (1 + 13 + 78 cell tasks per base cell, Algorithm 1).
+ *  3C08: Newton-3; 2x2x2 block anchored at the base cell; every cell multiset
+ *        of the block whose bounding box starts at the anchor
+ *        (1 + 13 + 44 cell tasks per block). */
+typedef enum { ATM_3C01 = 0, ATM_3C18 = 1, ATM_3C08 = 2 } atm_traversal;
+
+/* Truncation conditions (paper section 2).  A triplet interacts iff
+ *  PAIR:    r_ij < r_c and r_ik < r_c and r_jk < r_c;
+ *  PRODUCT: r_ij r_ik r_jk < r_c^3, decided as (p*q)*s < r_c^6 on the three
+ *           squared sides sorted ascending (p <= q <= s). */
+typedef enum { ATM_TRUNC_PAIR = 0, ATM_TRUNC_PRODUCT = 1 } atm_truncation;
+
+/* Arithmetic of the force evaluation.
+ *  FP64:  every decision and every force, energy and virial term in FP64.
+ *  FP32C: decisions and per-triplet arithmetic in FP32 on FP32 cell-local
+ *         coordinates; per-molecule force sums compensated (two-sum) in FP32 and
+ *         combined in FP64; energy/virial reduced in FP64. */
+typedef enum { ATM_FP64 = 0, ATM_FP32C = 1 } atm_precision;
+
+typedef struct {
+    double box[3];      /* L_x, L_y, L_z > 0 */
+    double rc;          /* cutoff radius for pairs and triplets, > 0 */
+    double nu;          /* ATM strength (0.073 argon-like reduced units) */
+    double lj_eps;      /* LJ epsilon (1) */
+    double lj_sigma;    /* LJ sigma (1) */
+    double dt;          /* velocity-Verlet time step used by atm_step */
+    int lj_shift;       /* 1: LJ energy shifted to 0 at r_c; 0: plain truncation */
+    int device;         /* CUDA device ordinal */
+    void* cuda_stream;  /* cudaStream_t to enqueue on; NULL = default stream */
+} atm_params;
+
+/* Scalars of one force evaluation (section 5 estimators).
+ * e2, e3: LJ and ATM potential energy; w2, w3: pair and three-body virial
+ * W = sum r_ab . F_ab (Eq. P_3); the caller assembles the virial pressure as
+ * P = rho T + (w2 + w3) / (3 V).  ekin = 1/2 sum v^2 (unit mass).
+ * n_cand3 / n_int3: candidate / interacting triplets of the traversal
+ * (3C01 counts owner visits); n_cand2 / n_int2: candidate / interacting
+ * pairs of the half-shell pair traversal (each pair once). */
+typedef struct {
+    double e2, e3, w2, w3, ekin;
+    uint64_t n_cand3, n_int3, n_cand2, n_int2;
+} atm_result;
+
+typedef struct atm_ctx atm_ctx;
+
+/* Create a context for n molecules (n >= 0).  Allocates every device buffer.
+ * Errors: INVALID, BOX_TOO_SMALL, CUDA.  *out is NULL on failure. */
+atm_status atm_create(const atm_params* params, int64_t n, atm_ctx** out);
+
+/* Destroy a context and free its device memory; NULL is allowed. */
+atm_status atm_destroy(atm_ctx* ctx);
+
+/* One-line description of the last error on ctx (never NULL). */
+const char* atm_last_error(const atm_ctx* ctx);
+
+/* ABI version number (ATM3_ABI_VERSION). */
+int atm_abi_version(void);
+
+/* Set positions x[3n] (any real values; wrapped into the box by
+ * atm_build_cells) and velocities v[3n] (NULL = zero) from host memory.
+ * Errors: INVALID, NONFINITE, CUDA. */
+atm_status atm_set_state(atm_ctx* ctx, const double* x, const double* v);
+/* Same from device memory (x_dev required, v_dev may be NULL).  The values
+ * are checked for finiteness on the device; a failure surfaces as NONFINITE
+ * from the next synchronising call. */
+atm_status atm_set_state_dev(atm_ctx* ctx, const double* x_dev, const double* v_dev);
+
+/* Linked cells (section 3): wrap positions into the box, bin them with the
+ * cell-edge rule above, and sort molecules by (cell id, original index) with
+ * cell id = (c_z n_y + c_y) n_x + c_x.  Also reads the largest cell occupancy
+ * back to size the force kernels (synchronises the stream).
+ * Errors: STATE (no positions), CUDA. */
+atm_status atm_build_cells(atm_ctx* ctx);
+
+/* Copy the cell arrays to caller-owned host memory (any pointer may be NULL):
+ * cell_of[n] (original order), cell_start[ncell+1], perm[n] (sorted slot ->
+ * original index).  ncell3[3] (may be NULL) receives n_x, n_y, n_z. */
+atm_status atm_get_cells(atm_ctx* ctx, int32_t* cell_of, int32_t* cell_start, int32_t* perm,
+                         int32_t* ncell3);
+
+/* LJ pair forces plus ATM three-body forces with the given traversal,
+ * truncation and precision (cells must be built).  If out is non-NULL the
+ * stream is synchronised and the scalars are written to *out.
+ * Errors: INVALID, STATE, CUDA, CAPACITY (the staged neighbourhood of the
+ * fullest cell does not fit in shared memory: more than about 60 molecules per
+ * cell for 3C01 in FP64, far more for 3C18/3C08). */
+atm_status atm_compute_forces(atm_ctx* ctx, atm_traversal trav, atm_truncation trunc,
+                              atm_precision prec, atm_result* out);
+
+/* Forces of the last evaluation in original order: which = 0 total,
+ * 1 LJ only, 2 ATM only.  f[3n] host (synchronises) or device. */
+atm_status atm_get_forces(atm_ctx* ctx, double* f, int which);
+atm_status atm_get_forces_dev(atm_ctx* ctx, double* f_dev, int which);
+
+/* Current (wrapped) positions and velocities, host, either may be NULL. */
+atm_status atm_get_state(atm_ctx* ctx, double* x, double* v);
+
+/* nsteps velocity-Verlet NVE steps of size params.dt (unit mass):
+ * v += dt/2 F; x += dt v; rebuild cells; F = LJ + ATM; v += dt/2 F.
+ * The first step computes F at the start if no evaluation is current.
+ * If last is non-NULL the scalars after the final step are written there
+ * (synchronises).  Errors: as atm_compute_forces. */
+atm_status atm_step(atm_ctx* ctx, int nsteps, atm_traversal trav, atm_truncation trunc,
+                    atm_precision prec, atm_result* last);
+
+/* Device-time profile of the library's own kernels (CUDA events recorded on
+ * the context's stream around each group of launches while profiling is on).
+ * ms_*: summed device time since profiling was (re)enabled; n_launches: kernels
+ * this library launched since then (profiling on or off: counted always since
+ * the last atm_set_profiling call); n_atm_launches: ATM triplet kernels among them. */
+typedef struct {
+    double ms_cells, ms_lj, ms_atm, ms_md;
+    int64_t n_launches, n_atm_launches;
+} atm_profile;
+
+/* on != 0: start recording (and reset the sums and counters); 0: stop. */
+atm_status atm_set_profiling(atm_ctx* ctx, int on);
+/* Synchronises the stream and returns the sums. */
+atm_status atm_get_profile(atm_ctx* ctx, atm_profile* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -60,6 +60,8 @@ def lib():
         L.orc_atm_brute.argtypes = [P, i64, P, ci, ci, P, P, P]
         L.orc_atm_cells.restype = ci
         L.orc_atm_cells.argtypes = [P, i64, P, ci, ci, ci, i64, i64, P, P, P]
+        L.orc_atm_cells_units.restype = ci
+        L.orc_atm_cells_units.argtypes = [P, i64, P, ci, ci, ci, P, i64, P, P, P]
         L.orc_lj_brute.restype = ci
         L.orc_lj_brute.argtypes = [P, i64, P, P, P, P]
         L.orc_lj_cells.restype = ci
@@ -154,6 +156,19 @@ def atm_cells(prm, x, trav="3c18", trunc="pair", prec="fp64", unit_lo=-1, unit_h
     cnt = np.zeros(2, dtype=np.uint64)
     _check(lib().orc_atm_cells(_p(prm), n, _p(x), TRAV[trav], TRUNC[trunc], PREC[prec],
                                unit_lo, unit_hi, _p(f), _p(ew), _p(cnt)))
+    return dict(f=f, e3=ew[0], w3=ew[1], n_cand3=int(cnt[0]), n_int3=int(cnt[1]))
+
+
+def atm_cells_units(prm, x, units, trav="3c18", trunc="pair", prec="fp64"):
+    """Linked-cell ATM restricted to the listed units (base cells / block anchors)."""
+    x = _soa(x)
+    n = x.shape[1]
+    u = np.ascontiguousarray(units, dtype=np.int64)
+    f = np.zeros((3, n))
+    ew = np.zeros(2)
+    cnt = np.zeros(2, dtype=np.uint64)
+    _check(lib().orc_atm_cells_units(_p(prm), n, _p(x), TRAV[trav], TRUNC[trunc], PREC[prec],
+                                     _p(u), u.size, _p(f), _p(ew), _p(cnt)))
     return dict(f=f, e3=ew[0], w3=ew[1], n_cand3=int(cnt[0]), n_int3=int(cnt[1]))
 
 

@@ -554,9 +554,9 @@ static void unit_3c08(ev_t* ev, int64_t b)
             }
 }
 
-int orc_atm_cells(const double* prm, int64_t n, const double* x, int trav, int trunc,
-                  int prec, int64_t unit_lo, int64_t unit_hi,
-                  double* f, double* ew, uint64_t* cnt)
+static int atm_cells_impl(const double* prm, int64_t n, const double* x, int trav, int trunc,
+                          int prec, int64_t unit_lo, int64_t unit_hi, const int64_t* units,
+                          int64_t nunits, double* f, double* ew, uint64_t* cnt)
 {
     if (trav < 0 || trav > 2 || trunc < 0 || trunc > 1 || prec < 0 || prec > 1) return 1;
     cells_t c;
@@ -564,6 +564,15 @@ int orc_atm_cells(const double* prm, int64_t n, const double* x, int trav, int t
     if (st) return st;
     int64_t lo = unit_lo < 0 ? 0 : unit_lo;
     int64_t hi = (unit_hi < 0 || unit_hi > c.g.ncell) ? c.g.ncell : unit_hi;
+    if (units) {
+        for (int64_t q = 0; q < nunits; q++)
+            if (units[q] < 0 || units[q] >= c.g.ncell) {
+                cells_free(&c);
+                return 1;
+            }
+        lo = 0;
+        hi = nunits;
+    }
     double* fs = calloc((size_t)(3 * (n > 0 ? n : 1)), sizeof(double));
     double e = 0.0, w = 0.0;
     uint64_t ncand = 0, nint = 0;
@@ -573,7 +582,8 @@ int orc_atm_cells(const double* prm, int64_t n, const double* x, int trav, int t
         ev_t ev;
         ev_init(&ev, &c, trunc, prec, fl);
 #pragma omp for schedule(dynamic, 4)
-        for (int64_t u = lo; u < hi; u++) {
+        for (int64_t q = lo; q < hi; q++) {
+            int64_t u = units ? units[q] : q;
             if (trav == ORC_3C01) unit_3c01(&ev, u);
             else if (trav == ORC_3C18) unit_3c18(&ev, u);
             else unit_3c08(&ev, u);
@@ -603,6 +613,21 @@ int orc_atm_cells(const double* prm, int64_t n, const double* x, int trav, int t
     free(fs);
     cells_free(&c);
     return 0;
+}
+
+int orc_atm_cells(const double* prm, int64_t n, const double* x, int trav, int trunc,
+                  int prec, int64_t unit_lo, int64_t unit_hi,
+                  double* f, double* ew, uint64_t* cnt)
+{
+    return atm_cells_impl(prm, n, x, trav, trunc, prec, unit_lo, unit_hi, NULL, 0, f, ew, cnt);
+}
+
+int orc_atm_cells_units(const double* prm, int64_t n, const double* x, int trav, int trunc,
+                        int prec, const int64_t* units, int64_t nunits,
+                        double* f, double* ew, uint64_t* cnt)
+{
+    if (!units && nunits > 0) return 1;
+    return atm_cells_impl(prm, n, x, trav, trunc, prec, 0, 0, units, nunits, f, ew, cnt);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -82,6 +82,11 @@ int orc_atm_cells(const double* prm, int64_t n, const double* x, int trav, int t
                   int prec, int64_t unit_lo, int64_t unit_hi,
                   double* f, double* ew, uint64_t* cnt);
 
+/* The same over an explicit list of units (each unit id in [0, ncell)). */
+int orc_atm_cells_units(const double* prm, int64_t n, const double* x, int trav, int trunc,
+                        int prec, const int64_t* units, int64_t nunits,
+                        double* f, double* ew, uint64_t* cnt);
+
 /* Brute-force LJ over all pairs (minimum image). ew = {E2, W2}, cnt[1] = pairs within r_c. */
 int orc_lj_brute(const double* prm, int64_t n, const double* x, double* f, double* ew,
                  uint64_t* cnt);

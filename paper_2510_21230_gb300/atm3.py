@@ -1,0 +1,235 @@
+"""Thin ctypes binding of the C ABI in ``include/atm3.h`` (libatm3.so).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels behind the C ABI.  Host arrays are NumPy float64 SoA ``[3, n]``;
+device arrays may be given as CUDA tensors (any object with ``data_ptr()``),
+in which case the ``_dev`` entry points are used.  If the shared library is
+missing, loading raises: there is no CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libatm3.so")
+
+TRAVERSALS = {"3c01": 0, "3c18": 1, "3c08": 2}
+TRUNCATIONS = {"pair": 0, "product": 1}
+PRECISIONS = {"fp64": 0, "fp32c": 1}
+FORCES = {"total": 0, "lj": 1, "atm": 2}
+
+STATUS = {0: "ok", 1: "invalid argument", 2: "box smaller than three cells", 3: "CUDA error",
+          4: "device wait timed out", 5: "non-finite input", 6: "call out of order",
+          7: "capacity exceeded"}
+
+EXPORTED = ["atm_abi_version", "atm_create", "atm_destroy", "atm_last_error", "atm_set_state",
+            "atm_set_state_dev", "atm_build_cells", "atm_get_cells", "atm_compute_forces",
+            "atm_get_forces", "atm_get_forces_dev", "atm_get_state", "atm_step",
+            "atm_set_profiling", "atm_get_profile"]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("box", ctypes.c_double * 3), ("rc", ctypes.c_double), ("nu", ctypes.c_double),
+                ("lj_eps", ctypes.c_double), ("lj_sigma", ctypes.c_double),
+                ("dt", ctypes.c_double), ("lj_shift", ctypes.c_int), ("device", ctypes.c_int),
+                ("cuda_stream", ctypes.c_void_p)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("e2", ctypes.c_double), ("e3", ctypes.c_double), ("w2", ctypes.c_double),
+                ("w3", ctypes.c_double), ("ekin", ctypes.c_double),
+                ("n_cand3", ctypes.c_uint64), ("n_int3", ctypes.c_uint64),
+                ("n_cand2", ctypes.c_uint64), ("n_int2", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("ms_cells", ctypes.c_double), ("ms_lj", ctypes.c_double),
+                ("ms_atm", ctypes.c_double), ("ms_md", ctypes.c_double),
+                ("n_launches", ctypes.c_int64), ("n_atm_launches", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class AtmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s (%d): %s" % (STATUS.get(status, "?"), status, msg))
+        self.status = status
+
+
+_lib = None
+
+
+def load():
+    """Load libatm3.so (must have been built; see ``build.py``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libatm3.so is not built (%s); run paper_2510_21230_gb300.build.build()"
+                           % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    P, i32, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+    L.atm_abi_version.restype = i32
+    L.atm_abi_version.argtypes = []
+    L.atm_create.restype = i32
+    L.atm_create.argtypes = [ctypes.POINTER(Params), i64, ctypes.POINTER(P)]
+    L.atm_destroy.restype = i32
+    L.atm_destroy.argtypes = [P]
+    L.atm_last_error.restype = ctypes.c_char_p
+    L.atm_last_error.argtypes = [P]
+    L.atm_set_state.restype = i32
+    L.atm_set_state.argtypes = [P, P, P]
+    L.atm_set_state_dev.restype = i32
+    L.atm_set_state_dev.argtypes = [P, P, P]
+    L.atm_build_cells.restype = i32
+    L.atm_build_cells.argtypes = [P]
+    L.atm_get_cells.restype = i32
+    L.atm_get_cells.argtypes = [P, P, P, P, P]
+    L.atm_compute_forces.restype = i32
+    L.atm_compute_forces.argtypes = [P, i32, i32, i32, ctypes.POINTER(Result)]
+    L.atm_get_forces.restype = i32
+    L.atm_get_forces.argtypes = [P, P, i32]
+    L.atm_get_forces_dev.restype = i32
+    L.atm_get_forces_dev.argtypes = [P, P, i32]
+    L.atm_get_state.restype = i32
+    L.atm_get_state.argtypes = [P, P, P]
+    L.atm_step.restype = i32
+    L.atm_step.argtypes = [P, i32, i32, i32, i32, ctypes.POINTER(Result)]
+    L.atm_set_profiling.restype = i32
+    L.atm_set_profiling.argtypes = [P, i32]
+    L.atm_get_profile.restype = i32
+    L.atm_get_profile.argtypes = [P, ctypes.POINTER(Profile)]
+    _lib = L
+    return L
+
+
+def _host_ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _is_device(a):
+    return hasattr(a, "data_ptr") and getattr(a, "is_cuda", False)
+
+
+class AtmSystem:
+    """One periodic LJ+ATM system on one GPU (wraps an ``atm_ctx``)."""
+
+    def __init__(self, box, n, rc=2.5, nu=0.073, lj_eps=1.0, lj_sigma=1.0, dt=0.002,
+                 lj_shift=False, device=0, stream=None):
+        self._lib = load()
+        box = np.broadcast_to(np.asarray(box, dtype=np.float64), (3,))
+        self.n = int(n)
+        self.box = box.copy()
+        p = Params()
+        for d in range(3):
+            p.box[d] = float(box[d])
+        p.rc, p.nu, p.lj_eps, p.lj_sigma, p.dt = rc, nu, lj_eps, lj_sigma, dt
+        p.lj_shift = 1 if lj_shift else 0
+        p.device = int(device)
+        p.cuda_stream = stream
+        self.params = p
+        ctx = ctypes.c_void_p()
+        st = self._lib.atm_create(ctypes.byref(p), self.n, ctypes.byref(ctx))
+        if st != 0:
+            raise AtmError(st, "atm_create failed")
+        self._ctx = ctx
+
+    # -- helpers
+    def _check(self, st):
+        if st != 0:
+            raise AtmError(st, self._lib.atm_last_error(self._ctx).decode())
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self._lib.atm_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- state
+    def set_state(self, x, v=None):
+        if _is_device(x):
+            assert tuple(x.shape) == (3, self.n) and x.is_contiguous()
+            vp = None
+            if v is not None:
+                assert tuple(v.shape) == (3, self.n) and v.is_contiguous()
+                vp = v.data_ptr()
+            self._check(self._lib.atm_set_state_dev(self._ctx, x.data_ptr(), vp))
+            return
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        assert x.shape == (3, self.n)
+        vp = None
+        if v is not None:
+            v = np.ascontiguousarray(v, dtype=np.float64)
+            assert v.shape == (3, self.n)
+            vp = _host_ptr(v)
+        self._check(self._lib.atm_set_state(self._ctx, _host_ptr(x), vp))
+
+    def get_state(self):
+        x = np.zeros((3, self.n))
+        v = np.zeros((3, self.n))
+        self._check(self._lib.atm_get_state(self._ctx, _host_ptr(x), _host_ptr(v)))
+        return x, v
+
+    # -- cells
+    def build_cells(self):
+        self._check(self._lib.atm_build_cells(self._ctx))
+
+    def get_cells(self):
+        nc = np.zeros(3, dtype=np.int32)
+        self._check(self._lib.atm_get_cells(self._ctx, None, None, None, _host_ptr(nc)))
+        ncell = int(np.prod(nc.astype(np.int64)))
+        cell_of = np.zeros(self.n, dtype=np.int32)
+        start = np.zeros(ncell + 1, dtype=np.int32)
+        perm = np.zeros(self.n, dtype=np.int32)
+        self._check(self._lib.atm_get_cells(self._ctx, _host_ptr(cell_of), _host_ptr(start),
+                                            _host_ptr(perm), _host_ptr(nc)))
+        return dict(cell_of=cell_of, cell_start=start, perm=perm, ncell=nc)
+
+    # -- forces
+    def compute_forces(self, trav="3c18", trunc="pair", prec="fp64", sync=True):
+        r = Result()
+        self._check(self._lib.atm_compute_forces(
+            self._ctx, TRAVERSALS[trav], TRUNCATIONS[trunc], PRECISIONS[prec],
+            ctypes.byref(r) if sync else None))
+        return r.as_dict() if sync else None
+
+    def get_forces(self, which="total", out=None):
+        if out is not None and _is_device(out):
+            assert tuple(out.shape) == (3, self.n) and out.is_contiguous()
+            self._check(self._lib.atm_get_forces_dev(self._ctx, out.data_ptr(), FORCES[which]))
+            return out
+        f = np.zeros((3, self.n)) if out is None else out
+        self._check(self._lib.atm_get_forces(self._ctx, _host_ptr(f), FORCES[which]))
+        return f
+
+    def step(self, nsteps=1, trav="3c18", trunc="pair", prec="fp64", sync=True):
+        r = Result()
+        self._check(self._lib.atm_step(self._ctx, int(nsteps), TRAVERSALS[trav],
+                                       TRUNCATIONS[trunc], PRECISIONS[prec],
+                                       ctypes.byref(r) if sync else None))
+        return r.as_dict() if sync else None
+
+    # -- profiling (device time of the library's kernels, launch counts)
+    def set_profiling(self, on=True):
+        self._check(self._lib.atm_set_profiling(self._ctx, 1 if on else 0))
+
+    def get_profile(self):
+        p = Profile()
+        self._check(self._lib.atm_get_profile(self._ctx, ctypes.byref(p)))
+        return p.as_dict()

@@ -1,0 +1,49 @@
+"""The C ABI library builds for sm_103a, loads, and exports every entry point
+that include/atm3.h declares (no GPU needed: nothing is computed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2510_21230_gb300 import atm3, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    with open(os.path.join(ROOT, "include", "atm3.h")) as fh:
+        text = fh.read()
+    for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(atm_[a-z0-9_]+)\s*\(",
+                         text, re.M):
+        names.add(m.group(1))
+    return names
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    declared = _declared()
+    assert "atm_compute_forces" in declared and "atm_step" in declared
+    for name in sorted(declared):
+        assert hasattr(lib, name), name
+    assert set(atm3.EXPORTED) <= declared
+    assert atm3.load().atm_abi_version() == 1
+
+
+def test_invalid_arguments_are_rejected_without_a_gpu():
+    lib = atm3.load()
+    p = atm3.Params()
+    for d in range(3):
+        p.box[d] = 10.0
+    p.rc, p.nu, p.lj_eps, p.lj_sigma, p.dt = 2.5, 0.073, 1.0, 1.0, 0.002
+    ctx = ctypes.c_void_p()
+    assert lib.atm_create(ctypes.byref(p), -1, ctypes.byref(ctx)) == 1
+    p.box[0] = 7.0  # two cells of 3.5 along x
+    assert lib.atm_create(ctypes.byref(p), 10, ctypes.byref(ctx)) == 2
+    p.box[0] = 10.0
+    p.rc = -1.0
+    assert lib.atm_create(ctypes.byref(p), 10, ctypes.byref(ctx)) == 1
+    assert lib.atm_destroy(None) == 0
+    assert lib.atm_compute_forces(None, 0, 0, 0, None) == 1
