@@ -83,53 +83,88 @@ struct Trav<2> {
     static constexpr int S = 8;
 };
 
-// Arguments of the ATM unit kernel.
+// Arguments of the ATM unit kernels.
 template <typename R>
 struct AtmArgs {
     Grid g;
     long long n;
-    const R* xl;              // sorted cell-local coordinates, SoA [3n]
+    const R* xl;              // sorted cell-local coordinates, SoA [3n], working precision
+    const float* xl32;        // the same in FP32 (prefilter of the FP64 path)
     const int* cell_start;    // [ncell + 1]
     double* fs;               // sorted-order ATM force accumulator, SoA [3n]
     double* unit_ew;          // [2 * ncell]: E3, W3 per unit
     unsigned long long* unit_cnt;  // [2 * ncell]: candidates, interacting
     int* status;
     R w[3];                   // cell edges in the working precision
+    float wf[3];              // cell edges in FP32
     R rc2, rc6, nu;
+    float p_lo, p_hi;         // FP64 prefilter band of a squared distance (pair rule)
+    float q_lo, q_hi, dmin;   // FP64 prefilter band of a sorted product (product rule)
     int mcap;                 // staged-molecule capacity of one unit
+    int gcap;                 // edge-accumulator capacity (block kernel)
+    int use_d;                // block kernel, product rule: dense FP32 distance table in smem
 };
 
-// Shared-memory plan of the ATM unit kernel.
-struct AtmSmem {
-    int mcap, nwarps, qcap;
-    size_t off_pos, off_idx, off_slot, off_acc, off_pl_q, off_pl_a, off_queue, total;
+// Shared-memory plan of the 3c01 (owner) kernel: staged positions, per-warp
+// partner lists (index, displacement, squared distance) and pair queues.
+struct OwnerSmem {
+    size_t off_pos, off_pos32, off_slot, off_pq, off_pd, off_pa32, off_queue, total;
 };
 
 template <typename R>
-__host__ __device__ inline AtmSmem atm_smem_plan(int mcap, int nwarps)
+__host__ __device__ inline OwnerSmem owner_smem_plan(int mcap, int nwarps)
 {
-    AtmSmem p;
-    p.mcap = mcap;
-    p.nwarps = nwarps;
-    p.qcap = 64;
+    OwnerSmem p;
     size_t o = 0;
     auto al = [](size_t v) { return (v + 15) & ~(size_t)15; };
-    p.off_pos = o;   o = al(o + sizeof(R) * 3 * mcap);
-    p.off_idx = o;   o = al(o + sizeof(int) * mcap);
-    p.off_slot = o;  o = al(o + sizeof(unsigned char) * mcap);
-    // force accumulators: FP64 path one double per component, FP32 path a
-    // (hi, lo) float pair per component -- 8 bytes per component either way
-    p.off_acc = o;   o = al(o + 8 * 3 * (size_t)mcap);
-    p.off_pl_q = o;  o = al(o + sizeof(unsigned short) * (size_t)mcap * nwarps);
-    p.off_pl_a = o;  o = al(o + sizeof(R) * (size_t)mcap * nwarps);
-    p.off_queue = o; o = al(o + sizeof(unsigned long long) * (size_t)p.qcap * nwarps);
+    const bool f64 = sizeof(R) == 8;
+    p.off_pos = o;   o = al(o + sizeof(R) * 3 * (size_t)mcap);
+    p.off_pos32 = o; o = al(o + (f64 ? sizeof(float) * 3 * (size_t)mcap : 0));
+    p.off_slot = o;  o = al(o + (size_t)mcap);
+    p.off_pq = o;    o = al(o + sizeof(unsigned short) * (size_t)mcap * nwarps);
+    p.off_pd = o;    o = al(o + sizeof(R) * 4 * (size_t)mcap * nwarps);
+    p.off_pa32 = o;  o = al(o + (f64 ? sizeof(float) * (size_t)mcap * nwarps : 0));
+    p.off_queue = o; o = al(o + sizeof(unsigned) * 64 * (size_t)nwarps);
+    p.total = o;
+    return p;
+}
+
+// Shared-memory plan of the Newton-3 block kernel (3c18 / 3c08).
+struct BlockSmem {
+    int W;
+    size_t off_pos, off_pos32, off_idx, off_slot, off_adj, off_adjT, off_rowoff, off_memb, off_G,
+        off_D, off_plq, off_queue, total;
+};
+
+template <typename R>
+__host__ __device__ inline BlockSmem block_smem_plan(int trunc, int mcap, int nwarps, int gcap,
+                                                     int use_d)
+{
+    BlockSmem p;
+    size_t o = 0;
+    auto al = [](size_t v) { return (v + 15) & ~(size_t)15; };
+    const bool f64 = sizeof(R) == 8, pair = trunc == 0;
+    const size_t M = (size_t)mcap, npair = M * (M - 1) / 2;
+    p.W = (mcap + 31) >> 5;
+    p.off_pos = o;    o = al(o + sizeof(R) * 3 * M);
+    p.off_pos32 = o;  o = al(o + (f64 ? sizeof(float) * 3 * M : 0));
+    p.off_idx = o;    o = al(o + sizeof(int) * M);
+    p.off_slot = o;   o = al(o + M);
+    p.off_adj = o;    o = al(o + (pair ? sizeof(unsigned) * M * p.W : 0));
+    p.off_adjT = o;   o = al(o + (pair ? sizeof(unsigned) * M * p.W : 0));
+    p.off_rowoff = o; o = al(o + (pair ? sizeof(int) * (M + 1) : 0));
+    p.off_memb = o;   o = al(o + (pair ? sizeof(unsigned) * 8 * p.W : 0));
+    p.off_G = o;      o = al(o + sizeof(R) * (pair ? (size_t)gcap : npair));
+    p.off_D = o;      o = al(o + (!pair && use_d ? sizeof(float) * npair : 0));
+    p.off_plq = o;    o = al(o + (pair ? sizeof(unsigned short) * M * nwarps : 0));
+    p.off_queue = o;  o = al(o + sizeof(unsigned long long) * 64 * (size_t)nwarps);
     p.total = o;
     return p;
 }
 
 }  // namespace atm3
 
-// kernel launchers (defined in the .cu files)
+// kernel launchers (defined in atm_fp64.cu / atm_fp32.cu)
 namespace atm3 {
 cudaError_t launch_atm_fp64(int trav, int trunc, const AtmArgs<double>& a, int nwarps,
                             size_t smem, cudaStream_t s);

@@ -1,0 +1,233 @@
+// atm_common.cuh -- arithmetic shared by the ATM triplet kernels.
+//
+// Distances follow one canonical formula for every traversal (base-frame
+// cell shifts, section 4): for staged molecules p, q with cell offsets o_p, o_q
+// relative to the unit's base cell,
+//     d = (xl_q - xl_p) + (o_q - o_p) w,     |d|^2 = (dx*dx + dy*dy) + dz*dz,
+// rounded operation by operation (no contraction), so truncation decisions
+// are reproducible bit for bit.
+//
+// FP64 decisions through an FP32 prefilter.  A squared distance computed in
+// FP32 on FP32-rounded cell-local coordinates differs from the FP64 one by at
+// most  2 delta (|dx|+|dy|+|dz|) + 3 delta^2 + 4 u D  with u = 2^-24 and
+// delta = 8 u w_max (two input roundings, the rounded shift, the subtraction
+// and the addition).  Near the cutoff (D ~ r_c^2, w <= 4/3 r_c) that is below
+// 2.5e-6 D, so an FP32 value outside [r_c^2 (1 - 2^-12), r_c^2 (1 + 2^-12)]
+// already decides the FP64 comparison; only values inside the band are
+// recomputed in FP64.  For the product rule each factor D >= (0.02 w_max)^2
+// has relative error below 8.3e-5, the product below 2.5e-4 < 2^-10, so an
+// FP32 product outside r_c^6 (1 -+ 2^-10) decides; smaller sides or values in
+// the band are recomputed in FP64.
+#pragma once
+#include "atm3_internal.cuh"
+
+namespace atm3 {
+
+template <typename R>
+struct Ar;
+template <>
+struct Ar<double> {
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double rsq(double a) { return ::rsqrt(a); }
+};
+template <>
+struct Ar<float> {
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float rsq(float a) { return rsqrtf(a); }
+};
+
+// canonical displacement p -> q (offset difference m in cells) and its square
+template <typename R>
+__device__ __forceinline__ R canon_disp(R xp, R yp, R zp, R xq, R yq, R zq, int mx, int my, int mz,
+                                        R w0, R w1, R w2, R& dx, R& dy, R& dz)
+{
+    typedef Ar<R> Q;
+    dx = Q::add(Q::sub(xq, xp), Q::mul((R)mx, w0));
+    dy = Q::add(Q::sub(yq, yp), Q::mul((R)my, w1));
+    dz = Q::add(Q::sub(zq, zp), Q::mul((R)mz, w2));
+    return Q::add(Q::add(Q::mul(dx, dx), Q::mul(dy, dy)), Q::mul(dz, dz));
+}
+
+// sorted product (lo * mid) * hi of three squared sides
+template <typename R>
+__device__ __forceinline__ R sorted_product(R a, R b, R c)
+{
+    R lo = fmin(a, b), hi = fmax(a, b);
+    R mid;
+    if (c < lo) {
+        mid = lo;
+        lo = c;
+    } else if (c < hi) {
+        mid = c;
+    } else {
+        mid = hi;
+        hi = c;
+    }
+    return Ar<R>::mul(Ar<R>::mul(lo, mid), hi);
+}
+
+// truncation test (section 2): pair = every side < r_c; product = the sorted
+// squared sides satisfy (p*q)*s < r_c^6
+template <int TRUNC, typename R>
+__device__ __forceinline__ bool keep_triplet(R a, R b, R c, R rc2, R rc6)
+{
+    if (TRUNC == 0) return a < rc2 && b < rc2 && c < rc2;
+    return sorted_product<R>(a, b, c) < rc6;
+}
+
+// ATM energy and its derivatives with respect to the squared sides, from
+// Eq. atm in r^2 form: with s = abc, q = s^(-1/2), A = -a+b+c, B = a-b+c,
+// C = a+b-c, P = ABC:
+//   u     = nu q^3 (1 + 3/8 P q^2)
+//   du/da = nu q^5 (3/8 (2aA - BC) - bc (3/2 + 15/16 P q^2))   (and cyclic)
+// One reciprocal square root, no division.
+template <typename R>
+__device__ __forceinline__ void atm_terms(R a, R b, R c, R nu, R& u, R& ua, R& ub, R& uc)
+{
+    R s = a * b * c;
+    R q = Ar<R>::rsq(s);
+    R q2 = q * q;
+    R q3 = q2 * q;
+    R q5 = q3 * q2;
+    R A = (b + c) - a;
+    R B = (a + c) - b;
+    R C = (a + b) - c;
+    R P = A * B * C;
+    R Pq2 = P * q2;
+    u = nu * q3 * (R(1) + R(0.375) * Pq2);
+    R K = R(1.5) + R(0.9375) * Pq2;
+    R nq5 = nu * q5;
+    ua = nq5 * (R(0.375) * (R(2) * a * A - B * C) - K * (b * c));
+    ub = nq5 * (R(0.375) * (R(2) * b * B - A * C) - K * (a * c));
+    uc = nq5 * (R(0.375) * (R(2) * c * C - A * B) - K * (a * b));
+}
+
+// running sum: plain for FP64, Neumaier-compensated for FP32
+template <typename R>
+struct Sum;
+template <>
+struct Sum<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double v) { s += v; }
+    __device__ __forceinline__ double get() const { return s; }
+};
+template <>
+struct Sum<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v)
+    {
+        float t = __fadd_rn(s, v);
+        if (fabsf(s) >= fabsf(v))
+            c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, t), v));
+        else
+            c = __fadd_rn(c, __fadd_rn(__fsub_rn(v, t), s));
+        s = t;
+    }
+    __device__ __forceinline__ double get() const { return (double)s + (double)c; }
+};
+
+// Candidate triplets of one unit's cell tasks (Eqs. celltriplet,
+// twoonetriplets, carttriplets) from the staged slot occupancies N[0..S).
+template <int TRAV, int S>
+__device__ inline unsigned long long unit_candidates(const int* beg)
+{
+    unsigned long long N[S];
+    for (int s = 0; s < S; s++) N[s] = (unsigned long long)(beg[s + 1] - beg[s]);
+    auto C2 = [](unsigned long long m) { return m < 2 ? 0ull : m * (m - 1) / 2; };
+    auto C3 = [](unsigned long long m) { return m < 3 ? 0ull : m * (m - 1) * (m - 2) / 6; };
+    unsigned long long cand = 0;
+    if (TRAV == 0) {
+        unsigned long long M = (unsigned long long)beg[S];
+        cand = M > 0 ? N[0] * C2(M - 1) : 0ull;
+    } else if (TRAV == 1) {
+        unsigned long long sum1 = 0, sum2 = 0;
+        cand = C3(N[0]);
+        for (int s = 1; s < S; s++) {
+            cand += N[s] * C2(N[0]) + N[0] * C2(N[s]);
+            sum2 += N[s] * sum1;
+            sum1 += N[s];
+        }
+        cand += N[0] * sum2;
+    } else {
+        cand = C3(N[0]);
+        for (int s = 0; s < S; s++)
+            for (int t = s + 1; t < S; t++) {
+                if ((s & t) == 0) cand += N[t] * C2(N[s]) + N[s] * C2(N[t]);
+                for (int v = t + 1; v < S; v++)
+                    if ((s & t & v) == 0) cand += N[s] * N[t] * N[v];
+            }
+    }
+    return cand;
+}
+
+// unit geometry: per-slot cell start, occupancy prefix and offsets (warp 0)
+template <int TRAV, int S>
+__device__ __forceinline__ void unit_slots(const Grid& g, const int* cell_start, long long u,
+                                          int* s_beg, int* s_cell0, signed char (*s_off)[3])
+{
+    const unsigned FULL = 0xffffffffu;
+    int lane = threadIdx.x & 31;
+    int cx, cy, cz;
+    cell_coords(g, u, cx, cy, cz);
+    int cnt = 0;
+    if (lane < S) {
+        int dx, dy, dz;
+        slot_offset<TRAV>(lane, dx, dy, dz);
+        long long c = cell_at(g, cx, cy, cz, dx, dy, dz);
+        int c0 = cell_start[c];
+        cnt = cell_start[c + 1] - c0;
+        s_cell0[lane] = c0;
+        s_off[lane][0] = (signed char)dx;
+        s_off[lane][1] = (signed char)dy;
+        s_off[lane][2] = (signed char)dz;
+    }
+    int incl = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+        int v = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane < S) s_beg[lane + 1] = incl;
+    if (lane == 0) s_beg[0] = 0;
+}
+
+// block-wide reduction of the unit partials and their store (thread 0 writes)
+template <int NWMAX>
+__device__ __forceinline__ void unit_reduce_store(double e, double w, unsigned long long ni,
+                                                  double scale, unsigned long long cand,
+                                                  double* unit_ew, unsigned long long* unit_cnt,
+                                                  long long u, double (*s_red)[NWMAX],
+                                                  unsigned long long* s_redn)
+{
+    const unsigned FULL = 0xffffffffu;
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        e += __shfl_down_sync(FULL, e, o);
+        w += __shfl_down_sync(FULL, w, o);
+        ni += __shfl_down_sync(FULL, ni, o);
+    }
+    if (lane == 0) {
+        s_red[0][warp] = e;
+        s_red[1][warp] = w;
+        s_redn[warp] = ni;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double et = 0.0, wt = 0.0;
+        unsigned long long nt = 0;
+        for (int q = 0; q < nw; q++) {
+            et += s_red[0][q];
+            wt += s_red[1][q];
+            nt += s_redn[q];
+        }
+        unit_ew[2 * u] = et * scale;
+        unit_ew[2 * u + 1] = wt * scale;
+        unit_cnt[2 * u] = cand;
+        unit_cnt[2 * u + 1] = nt;
+    }
+}
+
+}  // namespace atm3

@@ -1,14 +1,35 @@
-// FP32 (compensated) instantiations of the ATM unit kernel.
-#include "atm_kernels.cuh"
+// FP32 instantiations of the ATM triplet kernels (3c01 owner kernel,
+// 3c18 / 3c08 block kernel).
+#include "atm_block.cuh"
+#include "atm_owner.cuh"
 
 namespace atm3 {
+
 cudaError_t launch_atm_fp32(int trav, int trunc, const AtmArgs<float>& a, int nwarps,
                             size_t smem, cudaStream_t s)
 {
-    return launch_atm_t<float>(trav, trunc, a, nwarps, smem, s);
+    dim3 grid((unsigned)a.g.ncell), block(32 * nwarps);
+    if (a.g.ncell == 0) return cudaSuccess;
+    if (trav == 0 && trunc == 0) atm_owner_kernel<0, float><<<grid, block, smem, s>>>(a);
+    else if (trav == 0 && trunc == 1) atm_owner_kernel<1, float><<<grid, block, smem, s>>>(a);
+    else if (trav == 1 && trunc == 0) atm_block_kernel<1, 0, float><<<grid, block, smem, s>>>(a);
+    else if (trav == 1 && trunc == 1) atm_block_kernel<1, 1, float><<<grid, block, smem, s>>>(a);
+    else if (trav == 2 && trunc == 0) atm_block_kernel<2, 0, float><<<grid, block, smem, s>>>(a);
+    else if (trav == 2 && trunc == 1) atm_block_kernel<2, 1, float><<<grid, block, smem, s>>>(a);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
 }
+
 cudaError_t atm_attr_fp32(int trav, int trunc, size_t smem)
 {
-    return atm_attr_t<float>(trav, trunc, smem);
+    const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    if (trav == 0 && trunc == 0) return cudaFuncSetAttribute(atm_owner_kernel<0, float>, A, (int)smem);
+    if (trav == 0 && trunc == 1) return cudaFuncSetAttribute(atm_owner_kernel<1, float>, A, (int)smem);
+    if (trav == 1 && trunc == 0) return cudaFuncSetAttribute(atm_block_kernel<1, 0, float>, A, (int)smem);
+    if (trav == 1 && trunc == 1) return cudaFuncSetAttribute(atm_block_kernel<1, 1, float>, A, (int)smem);
+    if (trav == 2 && trunc == 0) return cudaFuncSetAttribute(atm_block_kernel<2, 0, float>, A, (int)smem);
+    if (trav == 2 && trunc == 1) return cudaFuncSetAttribute(atm_block_kernel<2, 1, float>, A, (int)smem);
+    return cudaErrorInvalidValue;
 }
+
 }  // namespace atm3

@@ -1,0 +1,250 @@
+// atm_owner.cuh -- 3c01 traversal (section 4): no Newton-3, owner computes.
+//
+// One CTA per base cell.  The 27-cell neighbourhood is staged in shared
+// memory; warps take the base cell's molecules i in turn.  For each i the
+// warp builds i's partner list (pair rule: partners within r_c; product rule:
+// every other staged molecule) holding the displacement d(i -> q) and its
+// square, then tests every pair {j, k} of the list and queues interacting
+// pairs.  A full queue (32 pairs) is evaluated by the whole warp; only F_i is
+// needed, so each lane keeps its share of F_i in registers (compensated in
+// FP32) and the warp reduces it once per i: no atomics, deterministic.
+// Energy and virial get u/3 and W/3 per visit (each triangle is found by up
+// to three owners).
+#pragma once
+#include "atm_common.cuh"
+
+namespace atm3 {
+
+template <int TRUNC, typename R>
+__global__ void __launch_bounds__(128) atm_owner_kernel(const AtmArgs<R> A)
+{
+    constexpr int TRAV = 0, S = 27;
+    constexpr bool F64 = sizeof(R) == 8;
+    constexpr unsigned FULL = 0xffffffffu;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_beg[S + 1];
+    __shared__ int s_cell0[S];
+    __shared__ signed char s_off[S][3];
+    __shared__ int s_next;
+    __shared__ double s_red[2][8];
+    __shared__ unsigned long long s_redn[8];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const long long u = blockIdx.x;
+    const int mcap = A.mcap;
+    const OwnerSmem plan = owner_smem_plan<R>(mcap, nwarps);
+    R* px = reinterpret_cast<R*>(smem + plan.off_pos);
+    R* py = px + mcap;
+    R* pz = py + mcap;
+    float* fx32 = F64 ? reinterpret_cast<float*>(smem + plan.off_pos32) : reinterpret_cast<float*>(px);
+    float* fy32 = fx32 + mcap;
+    float* fz32 = fy32 + mcap;
+    unsigned char* sslot = smem + plan.off_slot;
+    unsigned short* pq = reinterpret_cast<unsigned short*>(smem + plan.off_pq) + warp * mcap;
+    R* pdx = reinterpret_cast<R*>(smem + plan.off_pd) + (size_t)warp * 4 * mcap;
+    R* pdy = pdx + mcap;
+    R* pdz = pdy + mcap;
+    R* pa = pdz + mcap;
+    float* pa32 = F64 ? reinterpret_cast<float*>(smem + plan.off_pa32) + warp * mcap : nullptr;
+    unsigned* queue = reinterpret_cast<unsigned*>(smem + plan.off_queue) + warp * 64;
+
+    if (warp == 0) unit_slots<TRAV, S>(A.g, A.cell_start, u, s_beg, s_cell0, s_off);
+    if (tid == 0) s_next = 0;
+    __syncthreads();
+    const int M = s_beg[S];
+    const int Mfirst = s_beg[1];
+    if (M > mcap) {
+        if (tid == 0) {
+            atomicOr(A.status, ST_CAPACITY);
+            A.unit_ew[2 * u] = 0.0;
+            A.unit_ew[2 * u + 1] = 0.0;
+            A.unit_cnt[2 * u] = 0ull;
+            A.unit_cnt[2 * u + 1] = 0ull;
+        }
+        return;
+    }
+    const long long n = A.n;
+    for (int t = tid; t < M; t += blockDim.x) {
+        int s = 0;
+        while (s_beg[s + 1] <= t) s++;
+        int g = s_cell0[s] + (t - s_beg[s]);
+        px[t] = A.xl[g];
+        py[t] = A.xl[n + g];
+        pz[t] = A.xl[2 * n + g];
+        if (F64) {
+            fx32[t] = A.xl32[g];
+            fy32[t] = A.xl32[n + g];
+            fz32[t] = A.xl32[2 * n + g];
+        }
+        sslot[t] = (unsigned char)s;
+    }
+    __syncthreads();
+
+    const R w0 = A.w[0], w1 = A.w[1], w2 = A.w[2];
+    const float wf0 = A.wf[0], wf1 = A.wf[1], wf2 = A.wf[2];
+    const R rc2 = A.rc2, rc6 = A.rc6, nu = A.nu;
+    const unsigned lt_mask = (1u << lane) - 1u;
+
+    auto offs = [&](int p, int q, int& mx, int& my, int& mz) {
+        int sp = sslot[p], sq = sslot[q];
+        mx = s_off[sq][0] - s_off[sp][0];
+        my = s_off[sq][1] - s_off[sp][1];
+        mz = s_off[sq][2] - s_off[sp][2];
+    };
+    // squared distance decision p -> q under the pair rule (FP64 via the FP32 prefilter)
+    auto close_pair = [&](int p, int q) -> bool {
+        int mx, my, mz;
+        offs(p, q, mx, my, mz);
+        R dx, dy, dz;
+        if (!F64) {
+            R d2 = canon_disp<R>(px[p], py[p], pz[p], px[q], py[q], pz[q], mx, my, mz, w0, w1, w2,
+                                 dx, dy, dz);
+            return d2 < rc2;
+        }
+        float ex, ey, ez;
+        float f2 = canon_disp<float>(fx32[p], fy32[p], fz32[p], fx32[q], fy32[q], fz32[q], mx, my,
+                                     mz, wf0, wf1, wf2, ex, ey, ez);
+        if (f2 < A.p_lo) return true;
+        if (f2 > A.p_hi) return false;
+        R d2 = canon_disp<R>(px[p], py[p], pz[p], px[q], py[q], pz[q], mx, my, mz, w0, w1, w2, dx,
+                             dy, dz);
+        return d2 < rc2;
+    };
+
+    Sum<R> esum, wsum;
+    unsigned int nint = 0;
+
+    for (;;) {
+        int i = 0;
+        if (lane == 0) i = atomicAdd(&s_next, 1);
+        i = __shfl_sync(FULL, i, 0);
+        if (i >= Mfirst) break;
+
+        // partner list of i: every other staged molecule (product) or those within r_c (pair)
+        int np = 0;
+        for (int q0 = 0; q0 < M; q0 += 32) {
+            int q = q0 + lane;
+            bool keep = false;
+            if (q < M && q != i) keep = (TRUNC == 0) ? close_pair(i, q) : true;
+            unsigned m = __ballot_sync(FULL, keep);
+            if (keep) {
+                int pos = np + __popc(m & lt_mask);
+                int mx, my, mz;
+                offs(i, q, mx, my, mz);
+                R dx, dy, dz;
+                R d2 = canon_disp<R>(px[i], py[i], pz[i], px[q], py[q], pz[q], mx, my, mz, w0, w1,
+                                     w2, dx, dy, dz);
+                pq[pos] = (unsigned short)q;
+                pdx[pos] = dx;
+                pdy[pos] = dy;
+                pdz[pos] = dz;
+                pa[pos] = d2;
+                if (F64) {
+                    float ex, ey, ez;
+                    pa32[pos] = canon_disp<float>(fx32[i], fy32[i], fz32[i], fx32[q], fy32[q],
+                                                  fz32[q], mx, my, mz, wf0, wf1, wf2, ex, ey, ez);
+                }
+            }
+            np += __popc(m);
+        }
+        __syncwarp();
+
+        Sum<R> fxs, fys, fzs;
+        int qn = 0;
+        auto evaluate = [&](unsigned e) {
+            int jj = (int)(e & 0xffffu), kk = (int)(e >> 16);
+            R dijx = pdx[jj], dijy = pdy[jj], dijz = pdz[jj], a = pa[jj];
+            R dikx = pdx[kk], diky = pdy[kk], dikz = pdz[kk], b = pa[kk];
+            R djkx = dikx - dijx, djky = diky - dijy, djkz = dikz - dijz;
+            R c = djkx * djkx + djky * djky + djkz * djkz;
+            R uu, ua, ub, uc;
+            atm_terms<R>(a, b, c, nu, uu, ua, ub, uc);
+            R gij = R(2) * ua, gik = R(2) * ub, gjk = R(2) * uc;
+            esum.add(uu);
+            wsum.add(-(gij * a + gik * b + gjk * c));
+            fxs.add(gij * dijx + gik * dikx);
+            fys.add(gij * dijy + gik * diky);
+            fzs.add(gij * dijz + gik * dikz);
+        };
+
+        // pairs (jj < kk) of the partner list, t = kk (kk - 1) / 2 + jj
+        const int T = np * (np - 1) / 2;
+        for (int t0 = 0; t0 < T; t0 += 32) {
+            int t = t0 + lane;
+            bool keep = false;
+            int jj = 0, kk = 0;
+            if (t < T) {
+                kk = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)t)) * 0.5f);
+                while (kk * (kk - 1) / 2 > t) kk--;
+                while ((kk + 1) * kk / 2 <= t) kk++;
+                jj = t - kk * (kk - 1) / 2;
+                int j = pq[jj], k = pq[kk];
+                if (TRUNC == 0) {
+                    keep = close_pair(j, k);
+                } else {
+                    int mx, my, mz;
+                    offs(j, k, mx, my, mz);
+                    if (!F64) {
+                        R dx, dy, dz;
+                        R c = canon_disp<R>(px[j], py[j], pz[j], px[k], py[k], pz[k], mx, my, mz,
+                                            w0, w1, w2, dx, dy, dz);
+                        keep = sorted_product<R>(pa[jj], pa[kk], c) < rc6;
+                    } else {
+                        float ex, ey, ez;
+                        float a32 = pa32[jj], b32 = pa32[kk];
+                        float c32 = canon_disp<float>(fx32[j], fy32[j], fz32[j], fx32[k], fy32[k],
+                                                      fz32[k], mx, my, mz, wf0, wf1, wf2, ex, ey,
+                                                      ez);
+                        float pr = sorted_product<float>(a32, b32, c32);
+                        float lo = fminf(a32, fminf(b32, c32));
+                        if (lo >= A.dmin && pr < A.q_lo) {
+                            keep = true;
+                        } else if (lo >= A.dmin && pr > A.q_hi) {
+                            keep = false;
+                        } else {
+                            R dx, dy, dz;
+                            R c = canon_disp<R>(px[j], py[j], pz[j], px[k], py[k], pz[k], mx, my,
+                                                mz, w0, w1, w2, dx, dy, dz);
+                            keep = sorted_product<R>(pa[jj], pa[kk], c) < rc6;
+                        }
+                    }
+                }
+            }
+            unsigned m = __ballot_sync(FULL, keep);
+            if (keep) queue[qn + __popc(m & lt_mask)] = (unsigned)jj | ((unsigned)kk << 16);
+            qn += __popc(m);
+            nint += keep ? 1u : 0u;
+            __syncwarp();
+            if (qn >= 32) {
+                evaluate(queue[lane]);
+                __syncwarp();
+                if (lane < qn - 32) queue[lane] = queue[32 + lane];
+                qn -= 32;
+                __syncwarp();
+            }
+        }
+        if (lane < qn) evaluate(queue[lane]);
+        // F_i: lane shares combined in FP64
+        double f0 = fxs.get(), f1 = fys.get(), f2 = fzs.get();
+        for (int o = 16; o > 0; o >>= 1) {
+            f0 += __shfl_down_sync(FULL, f0, o);
+            f1 += __shfl_down_sync(FULL, f1, o);
+            f2 += __shfl_down_sync(FULL, f2, o);
+        }
+        if (lane == 0) {
+            int g = s_cell0[0] + i;  // base slot comes first: staged index = offset in the base cell
+            A.fs[g] = f0;
+            A.fs[n + g] = f1;
+            A.fs[2 * n + g] = f2;
+        }
+        __syncwarp();
+    }
+
+    unsigned long long cand = 0;
+    if (tid == 0) cand = unit_candidates<TRAV, S>(s_beg);
+    unit_reduce_store<8>(esum.get(), wsum.get(), (unsigned long long)nint, 1.0 / 3.0, cand,
+                         A.unit_ew, A.unit_cnt, u, s_red, s_redn);
+}
+
+}  // namespace atm3

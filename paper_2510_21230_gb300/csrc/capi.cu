@@ -1,4 +1,5 @@
 // capi.cu -- the C ABI declared in include/atm3.h: context, buffers, call order.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -13,8 +14,9 @@
 using namespace atm3;
 
 namespace {
-constexpr int ATM_NWARPS = 4;     // warps per ATM unit CTA
-constexpr int ATM_MCAP_MAX = 2048; // staged molecules per unit (queue packs 21-bit indices)
+constexpr int OWNER_NWARPS = 4;    // warps per 3c01 unit CTA
+constexpr int BLOCK_NWARPS = 8;    // warps per 3c18 / 3c08 unit CTA
+constexpr int ATM_MCAP_MAX = 2047; // staged molecules per unit (queue entries pack 11-bit indices)
 }  // namespace
 
 struct atm_ctx {
@@ -49,6 +51,7 @@ struct atm_ctx {
     int* d_maxocc = nullptr;
     int* h_maxocc = nullptr;
     int maxocc = 0;
+    int unit_max[3] = {0, 0, 0};  // largest unit (staged molecules) of 3c01, 3c18, 3c08
     bool have_x = false, cells_built = false, forces_valid = false;
     int f_trav = -1, f_trunc = -1, f_prec = -1;
     size_t smem_set[2][3][2] = {};
@@ -247,10 +250,10 @@ extern "C" atm_status atm_create(const atm_params* params, int64_t n, atm_ctx** 
     ok = ok && alloc((void**)&c->ke_part, (size_t)c->n_ke_blocks * sizeof(double));
     ok = ok && alloc((void**)&c->d_res, sizeof(ResultDev));
     ok = ok && alloc((void**)&c->d_status, sizeof(int));
-    ok = ok && alloc((void**)&c->d_maxocc, sizeof(int));
+    ok = ok && alloc((void**)&c->d_maxocc, 4 * sizeof(int));
     ok = ok && cudaMallocHost((void**)&c->h_res, sizeof(ResultDev)) == cudaSuccess;
     ok = ok && cudaMallocHost((void**)&c->h_status, sizeof(int)) == cudaSuccess;
-    ok = ok && cudaMallocHost((void**)&c->h_maxocc, sizeof(int)) == cudaSuccess;
+    ok = ok && cudaMallocHost((void**)&c->h_maxocc, 4 * sizeof(int)) == cudaSuccess;
     ok = ok && cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin,
                                       params->device) == cudaSuccess;
     ok = ok && cudaMemsetAsync(c->d_status, 0, sizeof(int), c->st) == cudaSuccess;
@@ -328,10 +331,11 @@ static atm_status enqueue_cells(atm_ctx* c)
                           c->xl, c->xl32, c->cell_sorted, c->d_maxocc, c->d_status, c->st));
     prof_end(c, PK_CELLS, ev);
     c->n_launch += c->n > 0 ? 5 : 1;
-    CU(cudaMemcpyAsync(c->h_maxocc, c->d_maxocc, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    CU(cudaMemcpyAsync(c->h_maxocc, c->d_maxocc, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->st));
     atm_status s = sync_and_check(c);
     if (s != ATM_OK) return s;
-    c->maxocc = *c->h_maxocc;
+    c->maxocc = c->h_maxocc[0];
+    for (int t = 0; t < 3; t++) c->unit_max[t] = c->h_maxocc[1 + t];
     c->cells_built = true;
     c->forces_valid = false;
     return ATM_OK;
@@ -396,45 +400,77 @@ static atm_status enqueue_forces(atm_ctx* c, int trav, int trunc, int prec)
     prof_end(c, PK_LJ, ev);
     c->n_launch += 1;
 
-    // ATM triplets
-    const int S = trav == ATM_3C01 ? 27 : (trav == ATM_3C18 ? 14 : 8);
-    int mcap = S * (c->maxocc > 0 ? c->maxocc : 1);
+    // ATM triplets: staged-molecule capacity = the largest unit of this traversal
+    int mcap = c->unit_max[trav] > 0 ? c->unit_max[trav] : 1;
     if (mcap > ATM_MCAP_MAX)
-        return fail(c, ATM_E_CAPACITY, "unit of %d cells x %d molecules exceeds %d staged", S,
-                    c->maxocc, ATM_MCAP_MAX);
-    size_t smem = prec == ATM_FP64 ? atm_smem_plan<double>(mcap, ATM_NWARPS).total
-                                   : atm_smem_plan<float>(mcap, ATM_NWARPS).total;
+        return fail(c, ATM_E_CAPACITY, "a traversal unit holds %d molecules (max %d staged)",
+                    mcap, ATM_MCAP_MAX);
+    const int nwarps = trav == ATM_3C01 ? OWNER_NWARPS : BLOCK_NWARPS;
+    // pair rule: room for 32 edges per staged molecule (more than 3x a liquid's count)
+    const int gcap = (int)std::min<long long>((long long)mcap * (mcap - 1) / 2, 32ll * mcap);
+    int use_d = 1;
+    auto plan_bytes = [&](int ud) -> size_t {
+        if (trav == ATM_3C01)
+            return prec == ATM_FP64 ? owner_smem_plan<double>(mcap, nwarps).total
+                                    : owner_smem_plan<float>(mcap, nwarps).total;
+        return prec == ATM_FP64 ? block_smem_plan<double>(trunc, mcap, nwarps, gcap, ud).total
+                                : block_smem_plan<float>(trunc, mcap, nwarps, gcap, ud).total;
+    };
+    size_t smem = plan_bytes(use_d);
+    if (smem > (size_t)c->smem_optin && trav != ATM_3C01 && trunc == ATM_TRUNC_PRODUCT) {
+        use_d = 0;  // distances on the fly instead of the dense table
+        smem = plan_bytes(use_d);
+    }
     if (smem > (size_t)c->smem_optin)
-        return fail(c, ATM_E_CAPACITY, "unit staging needs %zu bytes of shared memory (max %d)",
-                    smem, c->smem_optin);
+        return fail(c, ATM_E_CAPACITY,
+                    "a unit of %d molecules needs %zu bytes of shared memory (max %d)", mcap, smem,
+                    c->smem_optin);
     if (smem > c->smem_set[prec][trav][trunc]) {
         CU(prec == ATM_FP64 ? atm_attr_fp64(trav, trunc, smem) : atm_attr_fp32(trav, trunc, smem));
         c->smem_set[prec][trav][trunc] = smem;
     }
     if (trav != ATM_3C01)
         CU(cudaMemsetAsync(c->f_atm, 0, 3 * (size_t)c->n * sizeof(double), c->st));
+    // FP32 prefilter bands of the FP64 decisions (derivation in atm_common.cuh)
+    const double rc2d = rc * rc, rc6d = rc2d * rc2d * rc2d;
+    const double wmax = std::max(c->g.w[0], std::max(c->g.w[1], c->g.w[2]));
     ev = prof_begin(c);
     if (prec == ATM_FP64) {
         AtmArgs<double> a{};
-        a.g = c->g; a.n = c->n; a.xl = c->xl; a.cell_start = c->start; a.fs = c->f_atm;
-        a.unit_ew = c->unit_ew; a.unit_cnt = c->unit_cnt; a.status = c->d_status;
-        for (int d = 0; d < 3; d++) a.w[d] = c->g.w[d];
-        a.rc2 = rc * rc;
-        a.rc6 = a.rc2 * a.rc2 * a.rc2;
+        a.g = c->g; a.n = c->n; a.xl = c->xl; a.xl32 = c->xl32; a.cell_start = c->start;
+        a.fs = c->f_atm; a.unit_ew = c->unit_ew; a.unit_cnt = c->unit_cnt; a.status = c->d_status;
+        for (int d = 0; d < 3; d++) {
+            a.w[d] = c->g.w[d];
+            a.wf[d] = (float)c->g.w[d];
+        }
+        a.rc2 = rc2d;
+        a.rc6 = rc6d;
         a.nu = c->p.nu;
+        a.p_lo = (float)(rc2d * (1.0 - 1.0 / 4096.0));
+        a.p_hi = (float)(rc2d * (1.0 + 1.0 / 4096.0));
+        a.q_lo = (float)(rc6d * (1.0 - 1.0 / 1024.0));
+        a.q_hi = (float)(rc6d * (1.0 + 1.0 / 1024.0));
+        a.dmin = (float)((0.02 * wmax) * (0.02 * wmax));
         a.mcap = mcap;
-        CU(launch_atm_fp64(trav, trunc, a, ATM_NWARPS, smem, c->st));
+        a.gcap = gcap;
+        a.use_d = use_d;
+        CU(launch_atm_fp64(trav, trunc, a, nwarps, smem, c->st));
     } else {
         AtmArgs<float> a{};
         float rcf = (float)rc;
-        a.g = c->g; a.n = c->n; a.xl = c->xl32; a.cell_start = c->start; a.fs = c->f_atm;
-        a.unit_ew = c->unit_ew; a.unit_cnt = c->unit_cnt; a.status = c->d_status;
-        for (int d = 0; d < 3; d++) a.w[d] = (float)c->g.w[d];
+        a.g = c->g; a.n = c->n; a.xl = c->xl32; a.xl32 = c->xl32; a.cell_start = c->start;
+        a.fs = c->f_atm; a.unit_ew = c->unit_ew; a.unit_cnt = c->unit_cnt; a.status = c->d_status;
+        for (int d = 0; d < 3; d++) {
+            a.w[d] = (float)c->g.w[d];
+            a.wf[d] = (float)c->g.w[d];
+        }
         a.rc2 = rcf * rcf;
         a.rc6 = a.rc2 * a.rc2 * a.rc2;
         a.nu = (float)c->p.nu;
         a.mcap = mcap;
-        CU(launch_atm_fp32(trav, trunc, a, ATM_NWARPS, smem, c->st));
+        a.gcap = gcap;
+        a.use_d = use_d;
+        CU(launch_atm_fp32(trav, trunc, a, nwarps, smem, c->st));
     }
     prof_end(c, PK_ATM, ev);
     c->n_launch += 1;

@@ -94,6 +94,37 @@ __global__ void __launch_bounds__(1024) k_scan(long long ncell, const int* __res
     }
 }
 
+// largest staged-molecule count of a traversal unit, per traversal:
+// out[0] 3c01 (27 cells), out[1] 3c18 (base + 13 forward), out[2] 3c08 (2x2x2 block)
+__global__ void k_unit_max(Grid g, const int* __restrict__ start, int* __restrict__ out)
+{
+    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    int m01 = 0, m18 = 0, m08 = 0;
+    if (c < g.ncell) {
+        int cx, cy, cz;
+        cell_coords(g, c, cx, cy, cz);
+        for (int t = 0; t < 27; t++) {
+            int dx, dy, dz;
+            offset27(t, dx, dy, dz);
+            long long nc = cell_at(g, cx, cy, cz, dx, dy, dz);
+            int k = start[nc + 1] - start[nc];
+            m01 += k;
+            if (t >= 13) m18 += k;
+            if (dx >= 0 && dy >= 0 && dz >= 0) m08 += k;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        m01 = max(m01, __shfl_down_sync(0xffffffffu, m01, o));
+        m18 = max(m18, __shfl_down_sync(0xffffffffu, m18, o));
+        m08 = max(m08, __shfl_down_sync(0xffffffffu, m08, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(out, m01);
+        atomicMax(out + 1, m18);
+        atomicMax(out + 2, m08);
+    }
+}
+
 // K3a: scatter by arrival rank
 __global__ void k_scatter(long long n, const int* __restrict__ cell_of, const int* __restrict__ rank,
                           const int* __restrict__ start, int* __restrict__ perm)
@@ -379,6 +410,9 @@ cudaError_t launch_build_cells(const Grid& g, long long n, double* x, int* cell_
     if (e != cudaSuccess) return e;
     if (n > 0) k_wrap_bin<<<nblk(n, MD_BLOCK), MD_BLOCK, 0, st>>>(g, n, x, cell_of, rank, count, status);
     k_scan<<<1, 1024, 0, st>>>(g.ncell, count, start, maxocc);
+    e = cudaMemsetAsync(maxocc + 1, 0, 3 * sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    k_unit_max<<<nblk(g.ncell, MD_BLOCK), MD_BLOCK, 0, st>>>(g, start, maxocc + 1);
     if (n > 0) {
         k_scatter<<<nblk(n, MD_BLOCK), MD_BLOCK, 0, st>>>(n, cell_of, rank, start, perm);
         k_cell_sort<<<nblk(g.ncell, MD_BLOCK), MD_BLOCK, 0, st>>>(g.ncell, start, perm);
