@@ -156,6 +156,39 @@ atm_status atm_get_state(atm_ctx* ctx, double* x, double* v);
 atm_status atm_step(atm_ctx* ctx, int nsteps, atm_traversal trav, atm_truncation trunc,
                     atm_precision prec, atm_result* last);
 
+/* Allocation-free force evaluation.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc -- code that runs inside
+ * a host application which owns and budgets all device memory up front, a
+ * plug-in that is handed only raw device pointers, or a process whose
+ * allocator must not be touched after start-up.  It does what atm_create +
+ * atm_set_state_dev + atm_build_cells + atm_compute_forces + atm_get_forces_dev
+ * (which = 0) do for one set of positions, but allocates nothing: every
+ * intermediate array lives in one fixed __device__ array of about 5.3 MB that
+ * this library reserves on every GPU it is loaded on, until the process exits.
+ *
+ *   params  box, rc, nu, LJ parameters, device, cuda_stream (dt is unused)
+ *   n       molecules, 0 <= n <= ATM_NOALLOC_MAX_N
+ *   x_dev   [3n] device positions (SoA, any real values; only read)
+ *   f_dev   [3n] device output: total LJ + ATM force in the caller's order
+ *   out     host scalars of the evaluation (ekin = 0), may be NULL
+ *
+ * Errors: INVALID (NULL pointer, bad enum, device index >= 64), BOX_TOO_SMALL,
+ * CAPACITY (n > ATM_NOALLOC_MAX_N, more than ATM_NOALLOC_MAX_CELLS cells, or a
+ * unit that does not fit shared memory), NONFINITE, CUDA.  There is no context,
+ * so no message: the status code is the error.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  The call synchronises params.cuda_stream.  All
+ * calls share the one array and leave their data in it (what must start at
+ * zero is cleared on every call); calls whose GPU work overlaps -- on two
+ * streams, or from two host threads -- race on it and must be serialised by
+ * the caller. */
+#define ATM_NOALLOC_MAX_N 32768
+#define ATM_NOALLOC_MAX_CELLS 32768
+atm_status atm_compute_forces_noalloc(const atm_params* params, int64_t n, const double* x_dev,
+                                      atm_traversal trav, atm_truncation trunc,
+                                      atm_precision prec, double* f_dev, atm_result* out);
+
 /* Device-time profile of the library's own kernels (CUDA events recorded on
  * the context's stream around each group of launches while profiling is on).
  * ms_*: summed device time since profiling was (re)enabled; n_launches: kernels

@@ -26,7 +26,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "box smaller than three cells", 3: 
 EXPORTED = ["atm_abi_version", "atm_create", "atm_destroy", "atm_last_error", "atm_set_state",
             "atm_set_state_dev", "atm_build_cells", "atm_get_cells", "atm_compute_forces",
             "atm_get_forces", "atm_get_forces_dev", "atm_get_state", "atm_step",
-            "atm_set_profiling", "atm_get_profile"]
+            "atm_set_profiling", "atm_get_profile", "atm_compute_forces_noalloc"]
 
 
 class Params(ctypes.Structure):
@@ -100,6 +100,9 @@ def load():
     L.atm_get_state.argtypes = [P, P, P]
     L.atm_step.restype = i32
     L.atm_step.argtypes = [P, i32, i32, i32, i32, ctypes.POINTER(Result)]
+    L.atm_compute_forces_noalloc.restype = i32
+    L.atm_compute_forces_noalloc.argtypes = [ctypes.POINTER(Params), i64, P, i32, i32, i32, P,
+                                             ctypes.POINTER(Result)]
     L.atm_set_profiling.restype = i32
     L.atm_set_profiling.argtypes = [P, i32]
     L.atm_get_profile.restype = i32
@@ -233,3 +236,31 @@ class AtmSystem:
         p = Profile()
         self._check(self._lib.atm_get_profile(self._ctx, ctypes.byref(p)))
         return p.as_dict()
+
+
+def compute_forces_noalloc(box, x_dev, f_dev, trav="3c18", trunc="pair", prec="fp64", rc=2.5,
+                           nu=0.073, lj_eps=1.0, lj_sigma=1.0, lj_shift=False, device=0,
+                           stream=None):
+    """One force evaluation through ``atm_compute_forces_noalloc``: no device
+    memory is allocated by the library (for callers that cannot allocate);
+    ``x_dev`` and ``f_dev`` are caller-owned [3, n] float64 CUDA tensors.
+    Returns the scalars of the evaluation."""
+    L = load()
+    box = np.broadcast_to(np.asarray(box, dtype=np.float64), (3,))
+    n = int(x_dev.shape[1])
+    assert tuple(x_dev.shape) == (3, n) and tuple(f_dev.shape) == (3, n)
+    assert x_dev.is_contiguous() and f_dev.is_contiguous()
+    p = Params()
+    for d in range(3):
+        p.box[d] = float(box[d])
+    p.rc, p.nu, p.lj_eps, p.lj_sigma, p.dt = rc, nu, lj_eps, lj_sigma, 0.0
+    p.lj_shift = 1 if lj_shift else 0
+    p.device = int(device)
+    p.cuda_stream = stream
+    r = Result()
+    st = L.atm_compute_forces_noalloc(ctypes.byref(p), n, x_dev.data_ptr(), TRAVERSALS[trav],
+                                      TRUNCATIONS[trunc], PRECISIONS[prec], f_dev.data_ptr(),
+                                      ctypes.byref(r))
+    if st != 0:
+        raise AtmError(st, "atm_compute_forces_noalloc failed")
+    return r.as_dict()

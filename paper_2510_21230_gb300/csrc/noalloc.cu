@@ -1,0 +1,287 @@
+// noalloc.cu -- one force evaluation without any device allocation.
+//
+// For callers that cannot call cudaMalloc: code running where the device
+// memory is already budgeted and owned by someone else (a host application
+// that forbids allocation after start-up, a plug-in handed only raw device
+// pointers, a process whose allocator is locked).  The caller passes the
+// positions and the output buffers; every intermediate array (the linked
+// cells, the sorted coordinates, the per-unit partial sums) lives in one
+// file-scope __device__ array of fixed size below.
+//
+// The array belongs to every GPU that loads this library and stays reserved
+// until the process exits.  In host code its name is only a host-side stand-in
+// for the symbol, so the device address is fetched once per device with
+// cudaGetSymbolAddress (with that device current) and passed to the kernels.
+// Every call uses the same array and leaves its contents behind; everything
+// that must start at zero is cleared on each call.  Two calls whose GPU work
+// overlaps (different streams, or different host threads) race on the array.
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+
+#include "atm3.h"
+#include "atm3_internal.cuh"
+#include "md_kernels.cuh"
+
+using namespace atm3;
+
+namespace {
+
+constexpr size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+struct NaLayout {
+    size_t x, cell_of, rank, count, start, perm, cell_sorted, xl, xl32, f_lj, f_atm, unit_ew,
+        unit_cnt, lj_ew, lj_cnt, ke_part, res, status, maxocc, total;
+};
+
+constexpr long long NA_N = ATM_NOALLOC_MAX_N;
+constexpr long long NA_C = ATM_NOALLOC_MAX_CELLS;
+constexpr long long NA_LJB = (NA_N + LJ_BLOCK - 1) / LJ_BLOCK;
+constexpr long long NA_KEB = (NA_N + MD_BLOCK - 1) / MD_BLOCK;
+
+constexpr NaLayout na_layout()
+{
+    NaLayout L{};
+    size_t o = 0;
+    L.x = o;           o = al256(o + 3 * NA_N * sizeof(double));
+    L.cell_of = o;     o = al256(o + NA_N * sizeof(int));
+    L.rank = o;        o = al256(o + NA_N * sizeof(int));
+    L.count = o;       o = al256(o + NA_C * sizeof(int));
+    L.start = o;       o = al256(o + (NA_C + 1) * sizeof(int));
+    L.perm = o;        o = al256(o + NA_N * sizeof(int));
+    L.cell_sorted = o; o = al256(o + NA_N * sizeof(int));
+    L.xl = o;          o = al256(o + 3 * NA_N * sizeof(double));
+    L.xl32 = o;        o = al256(o + 3 * NA_N * sizeof(float));
+    L.f_lj = o;        o = al256(o + 3 * NA_N * sizeof(double));
+    L.f_atm = o;       o = al256(o + 3 * NA_N * sizeof(double));
+    L.unit_ew = o;     o = al256(o + 2 * NA_C * sizeof(double));
+    L.unit_cnt = o;    o = al256(o + 2 * NA_C * sizeof(unsigned long long));
+    L.lj_ew = o;       o = al256(o + 2 * NA_LJB * sizeof(double));
+    L.lj_cnt = o;      o = al256(o + 2 * NA_LJB * sizeof(unsigned long long));
+    L.ke_part = o;     o = al256(o + NA_KEB * sizeof(double));
+    L.res = o;         o = al256(o + sizeof(ResultDev));
+    L.status = o;      o = al256(o + sizeof(int));
+    L.maxocc = o;      o = al256(o + 4 * sizeof(int));
+    L.total = o;
+    return L;
+}
+constexpr NaLayout NA = na_layout();
+
+// the scratch array (about 5.3 MB at the limits above)
+__device__ __align__(256) unsigned char g_na_scratch[NA.total];
+
+constexpr int NA_MAX_DEVICES = 64;
+unsigned char* g_na_addr[NA_MAX_DEVICES] = {};
+std::mutex g_na_mutex;
+
+// device address of g_na_scratch on the current device (set-up on first use)
+cudaError_t na_scratch(int device, unsigned char** out)
+{
+    std::lock_guard<std::mutex> lk(g_na_mutex);
+    if (!g_na_addr[device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_na_scratch);
+        if (e != cudaSuccess) return e;
+        g_na_addr[device] = static_cast<unsigned char*>(p);
+    }
+    *out = g_na_addr[device];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+#define NA_CU(call)                                      \
+    do {                                                 \
+        if ((call) != cudaSuccess) return ATM_E_CUDA;    \
+    } while (0)
+
+extern "C" atm_status atm_compute_forces_noalloc(const atm_params* p, int64_t n,
+                                                 const double* x_dev, atm_traversal trav,
+                                                 atm_truncation trunc, atm_precision prec,
+                                                 double* f_dev, atm_result* out)
+{
+    if (!p || n < 0 || (n > 0 && (!x_dev || !f_dev))) return ATM_E_INVALID;
+    if (trav < 0 || trav > 2 || trunc < 0 || trunc > 1 || prec < 0 || prec > 1)
+        return ATM_E_INVALID;
+    if (p->device < 0 || p->device >= NA_MAX_DEVICES) return ATM_E_INVALID;
+    if (n > NA_N) return ATM_E_CAPACITY;
+    // linked-cell grid: n_d = largest k with L/k >= r_c, at least 3
+    Grid g;
+    long long ncell = 1;
+    for (int d = 0; d < 3; d++) {
+        double L = p->box[d], rc = p->rc;
+        if (!(L > 0.0) || !(rc > 0.0) || !std::isfinite(L) || !std::isfinite(rc))
+            return ATM_E_INVALID;
+        double k = std::floor(L / rc);
+        if (k < 1.0) k = 1.0;
+        while (L / (k + 1.0) >= rc) k += 1.0;
+        while (k > 0.0 && L / k < rc) k -= 1.0;
+        if (k < 3.0) return ATM_E_BOX_TOO_SMALL;
+        if (k > (double)NA_C) return ATM_E_CAPACITY;
+        g.nc[d] = (int)k;
+        g.L[d] = L;
+        g.w[d] = L / k;
+        ncell *= (long long)k;
+    }
+    if (ncell > NA_C) return ATM_E_CAPACITY;
+    g.ncell = ncell;
+
+    NA_CU(cudaSetDevice(p->device));
+    unsigned char* base = nullptr;
+    NA_CU(na_scratch(p->device, &base));
+    cudaStream_t st = (cudaStream_t)p->cuda_stream;
+    double* x = reinterpret_cast<double*>(base + NA.x);
+    int* cell_of = reinterpret_cast<int*>(base + NA.cell_of);
+    int* rank = reinterpret_cast<int*>(base + NA.rank);
+    int* count = reinterpret_cast<int*>(base + NA.count);
+    int* start = reinterpret_cast<int*>(base + NA.start);
+    int* perm = reinterpret_cast<int*>(base + NA.perm);
+    int* cell_sorted = reinterpret_cast<int*>(base + NA.cell_sorted);
+    double* xl = reinterpret_cast<double*>(base + NA.xl);
+    float* xl32 = reinterpret_cast<float*>(base + NA.xl32);
+    double* f_lj = reinterpret_cast<double*>(base + NA.f_lj);
+    double* f_atm = reinterpret_cast<double*>(base + NA.f_atm);
+    double* unit_ew = reinterpret_cast<double*>(base + NA.unit_ew);
+    unsigned long long* unit_cnt = reinterpret_cast<unsigned long long*>(base + NA.unit_cnt);
+    double* lj_ew = reinterpret_cast<double*>(base + NA.lj_ew);
+    unsigned long long* lj_cnt = reinterpret_cast<unsigned long long*>(base + NA.lj_cnt);
+    double* ke_part = reinterpret_cast<double*>(base + NA.ke_part);
+    ResultDev* res = reinterpret_cast<ResultDev*>(base + NA.res);
+    int* status = reinterpret_cast<int*>(base + NA.status);
+    int* maxocc = reinterpret_cast<int*>(base + NA.maxocc);
+
+    // positions are copied in (the cell build wraps them in place); the
+    // status word and the kinetic-energy partials start at zero
+    const size_t bytes3 = 3 * (size_t)n * sizeof(double);
+    if (bytes3) NA_CU(cudaMemcpyAsync(x, x_dev, bytes3, cudaMemcpyDeviceToDevice, st));
+    NA_CU(cudaMemsetAsync(status, 0, sizeof(int), st));
+    const long long n_lj = (n + LJ_BLOCK - 1) / LJ_BLOCK > 0 ? (n + LJ_BLOCK - 1) / LJ_BLOCK : 1;
+    const long long n_ke = (n + MD_BLOCK - 1) / MD_BLOCK > 0 ? (n + MD_BLOCK - 1) / MD_BLOCK : 1;
+    NA_CU(cudaMemsetAsync(ke_part, 0, (size_t)n_ke * sizeof(double), st));
+    if (n > 0) NA_CU(launch_check_finite(3 * n, x, status, st));
+    NA_CU(launch_build_cells(g, n, x, cell_of, rank, count, start, perm, xl, xl32, cell_sorted,
+                             maxocc, status, st));
+    int hocc[4] = {0, 0, 0, 0}, hstat = 0;
+    NA_CU(cudaMemcpyAsync(hocc, maxocc, sizeof(hocc), cudaMemcpyDeviceToHost, st));
+    NA_CU(cudaMemcpyAsync(&hstat, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    NA_CU(cudaStreamSynchronize(st));
+    if (hstat & ST_NONFINITE) return ATM_E_NONFINITE;
+
+    // LJ pairs
+    const double rc = p->rc, sig2 = p->lj_sigma * p->lj_sigma;
+    const double sc = sig2 / (rc * rc), sc3 = sc * sc * sc;
+    const double ushift = p->lj_shift ? 4.0 * p->lj_eps * (sc3 * sc3 - sc3) : 0.0;
+    LjArgs<double> l64{};
+    LjArgs<float> l32{};
+    if (prec == ATM_FP64) {
+        l64.g = g; l64.n = n; l64.xl = xl; l64.cell_start = start; l64.cell_sorted = cell_sorted;
+        l64.fs = f_lj; l64.part_ew = lj_ew; l64.part_cnt = lj_cnt;
+        for (int d = 0; d < 3; d++) l64.w[d] = g.w[d];
+        l64.rc2 = rc * rc; l64.sig2 = sig2; l64.eps4 = 4.0 * p->lj_eps;
+        l64.eps24 = 24.0 * p->lj_eps; l64.eps48 = 48.0 * p->lj_eps; l64.ushift = ushift;
+    } else {
+        float rcf = (float)rc;
+        l32.g = g; l32.n = n; l32.xl = xl32; l32.cell_start = start; l32.cell_sorted = cell_sorted;
+        l32.fs = f_lj; l32.part_ew = lj_ew; l32.part_cnt = lj_cnt;
+        for (int d = 0; d < 3; d++) l32.w[d] = (float)g.w[d];
+        l32.rc2 = rcf * rcf; l32.sig2 = (float)sig2; l32.eps4 = (float)(4.0 * p->lj_eps);
+        l32.eps24 = (float)(24.0 * p->lj_eps); l32.eps48 = (float)(48.0 * p->lj_eps);
+        l32.ushift = (float)ushift;
+    }
+    NA_CU(launch_lj(prec, l64, l32, st));
+
+    // ATM triplets, staged-molecule capacity = the largest unit of the traversal
+    const int mcap = hocc[1 + trav] > 0 ? hocc[1 + trav] : 1;
+    if (mcap > 2047) return ATM_E_CAPACITY;
+    const int nwarps = trav == ATM_3C01 ? 4 : 8;
+    const int gcap = (int)std::min<long long>((long long)mcap * (mcap - 1) / 2, 32ll * mcap);
+    int optin = 0;
+    NA_CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
+    int use_d = 1;
+    auto plan_bytes = [&](int ud) -> size_t {
+        if (trav == ATM_3C01)
+            return prec == ATM_FP64 ? owner_smem_plan<double>(mcap, nwarps).total
+                                    : owner_smem_plan<float>(mcap, nwarps).total;
+        return prec == ATM_FP64 ? block_smem_plan<double>(trunc, mcap, nwarps, gcap, ud).total
+                                : block_smem_plan<float>(trunc, mcap, nwarps, gcap, ud).total;
+    };
+    size_t smem = plan_bytes(use_d);
+    if (smem > (size_t)optin && trav != ATM_3C01 && trunc == ATM_TRUNC_PRODUCT) {
+        use_d = 0;
+        smem = plan_bytes(use_d);
+    }
+    if (smem > (size_t)optin) return ATM_E_CAPACITY;
+    NA_CU(prec == ATM_FP64 ? atm_attr_fp64(trav, trunc, smem) : atm_attr_fp32(trav, trunc, smem));
+    if (trav != ATM_3C01 && bytes3) NA_CU(cudaMemsetAsync(f_atm, 0, bytes3, st));
+    const double rc2d = rc * rc, rc6d = rc2d * rc2d * rc2d;
+    const double wmax = std::max(g.w[0], std::max(g.w[1], g.w[2]));
+    if (prec == ATM_FP64) {
+        AtmArgs<double> a{};
+        a.g = g; a.n = n; a.xl = xl; a.xl32 = xl32; a.cell_start = start; a.fs = f_atm;
+        a.unit_ew = unit_ew; a.unit_cnt = unit_cnt; a.status = status;
+        for (int d = 0; d < 3; d++) {
+            a.w[d] = g.w[d];
+            a.wf[d] = (float)g.w[d];
+        }
+        a.rc2 = rc2d;
+        a.rc6 = rc6d;
+        a.nu = p->nu;
+        a.p_lo = (float)(rc2d * (1.0 - 1.0 / 4096.0));
+        a.p_hi = (float)(rc2d * (1.0 + 1.0 / 4096.0));
+        a.q_lo = (float)(rc6d * (1.0 - 1.0 / 1024.0));
+        a.q_hi = (float)(rc6d * (1.0 + 1.0 / 1024.0));
+        a.dmin = (float)((0.02 * wmax) * (0.02 * wmax));
+        a.mcap = mcap;
+        a.gcap = gcap;
+        a.use_d = use_d;
+        NA_CU(launch_atm_fp64(trav, trunc, a, nwarps, smem, st));
+    } else {
+        AtmArgs<float> a{};
+        float rcf = (float)rc;
+        a.g = g; a.n = n; a.xl = xl32; a.xl32 = xl32; a.cell_start = start; a.fs = f_atm;
+        a.unit_ew = unit_ew; a.unit_cnt = unit_cnt; a.status = status;
+        for (int d = 0; d < 3; d++) {
+            a.w[d] = (float)g.w[d];
+            a.wf[d] = (float)g.w[d];
+        }
+        a.rc2 = rcf * rcf;
+        a.rc6 = a.rc2 * a.rc2 * a.rc2;
+        a.nu = (float)p->nu;
+        a.mcap = mcap;
+        a.gcap = gcap;
+        a.use_d = use_d;
+        NA_CU(launch_atm_fp32(trav, trunc, a, nwarps, smem, st));
+    }
+
+    // scalars, then the total force in the caller's order
+    ReduceArgs r;
+    r.unit_ew = unit_ew;
+    r.unit_cnt = unit_cnt;
+    r.n_units = g.ncell;
+    r.lj_ew = lj_ew;
+    r.lj_cnt = lj_cnt;
+    r.n_lj = n_lj;
+    r.ke_part = ke_part;
+    r.n_ke = n_ke;
+    r.out = res;
+    NA_CU(launch_final_reduce(r, st));
+    if (n > 0) NA_CU(launch_gather_forces(n, perm, f_lj, f_atm, 0, f_dev, st));
+    ResultDev hres{};
+    NA_CU(cudaMemcpyAsync(&hres, res, sizeof(ResultDev), cudaMemcpyDeviceToHost, st));
+    NA_CU(cudaMemcpyAsync(&hstat, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    NA_CU(cudaStreamSynchronize(st));
+    if (hstat & ST_NONFINITE) return ATM_E_NONFINITE;
+    if (hstat & ST_CAPACITY) return ATM_E_CAPACITY;
+    if (out) {
+        out->e2 = hres.e2;
+        out->e3 = hres.e3;
+        out->w2 = hres.w2;
+        out->w3 = hres.w3;
+        out->ekin = 0.0;
+        out->n_cand3 = hres.n_cand3;
+        out->n_int3 = hres.n_int3;
+        out->n_cand2 = hres.n_cand2;
+        out->n_int2 = hres.n_int2;
+    }
+    return ATM_OK;
+}
