@@ -214,7 +214,7 @@ def run_ours(args):
     achieved = flops / (atm_ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None,
-                "kernel": "atm_unit_kernel<%s,%s,%s>" % (args.trav, args.trunc, args.prec),
+                "kernel": ("atm_owner_kernel<%s,%s,%s>" if args.trav == "3c01" else "atm_block_kernel<%s,%s,%s>") % (args.trav, args.trunc, args.prec),
                 "peak_source": "derived: %d SMs x %.2f flops/clk x %.0f MHz (%s pipe)"
                                % (SMS, per_clk, sm_max, "FP32" if args.prec == "fp32c" else "FP64"),
                 "flops_per_interacting_triplet": F3[args.trav],

@@ -103,6 +103,7 @@ struct AtmArgs {
     int mcap;                 // staged-molecule capacity of one unit
     int gcap;                 // edge-accumulator capacity (block kernel)
     int use_d;                // block kernel, product rule: dense FP32 distance table in smem
+    int acc_mode;             // block kernel, product rule: 0 dense pair scalars, 1 per-molecule atomics
 };
 
 // Shared-memory plan of the 3c01 (owner) kernel: staged positions, per-warp
@@ -130,36 +131,106 @@ __host__ __device__ inline OwnerSmem owner_smem_plan(int mcap, int nwarps)
 }
 
 // Shared-memory plan of the Newton-3 block kernel (3c18 / 3c08).
+//  pos / sh      staged cell-local positions and exact base-frame shifts o*w
+//  pos32 / sh32  their FP32 copies (FP64 path: prefilter)
+//  pair rule:    adjacency bitmask rows and transpose, per-word prefix
+//                popcounts, row offsets (edge numbering), third-member slot
+//                masks, edge vectors (dx, dy, dz, r^2), edge scalars G; the
+//                per-molecule fallback accumulators alias the edge vectors
+//  product rule: dense FP32 squared distances D (optional), dense G
+//                (acc_mode 0) or per-molecule accumulators (acc_mode 1)
 struct BlockSmem {
     int W;
-    size_t off_pos, off_pos32, off_idx, off_slot, off_adj, off_adjT, off_rowoff, off_memb, off_G,
-        off_D, off_plq, off_queue, total;
+    size_t off_pos, off_sh, off_pos32, off_sh32, off_idx, off_slot, off_adj, off_adjT, off_rowpre,
+        off_rowoff, off_memb, off_ed, off_G, off_D, off_acc, off_plq, off_queue, total;
 };
 
 template <typename R>
 __host__ __device__ inline BlockSmem block_smem_plan(int trunc, int mcap, int nwarps, int gcap,
-                                                     int use_d)
+                                                     int use_d, int acc_mode)
 {
     BlockSmem p;
     size_t o = 0;
     auto al = [](size_t v) { return (v + 15) & ~(size_t)15; };
     const bool f64 = sizeof(R) == 8, pair = trunc == 0;
-    const size_t M = (size_t)mcap, npair = M * (M - 1) / 2;
+    const size_t M = (size_t)mcap, npair = M * (M - 1) / 2, accb = 24 * M;
     p.W = (mcap + 31) >> 5;
     p.off_pos = o;    o = al(o + sizeof(R) * 3 * M);
+    p.off_sh = o;     o = al(o + sizeof(R) * 3 * M);
     p.off_pos32 = o;  o = al(o + (f64 ? sizeof(float) * 3 * M : 0));
+    p.off_sh32 = o;   o = al(o + (f64 ? sizeof(float) * 3 * M : 0));
     p.off_idx = o;    o = al(o + sizeof(int) * M);
     p.off_slot = o;   o = al(o + M);
     p.off_adj = o;    o = al(o + (pair ? sizeof(unsigned) * M * p.W : 0));
     p.off_adjT = o;   o = al(o + (pair ? sizeof(unsigned) * M * p.W : 0));
+    p.off_rowpre = o; o = al(o + (pair ? sizeof(unsigned short) * M * p.W : 0));
     p.off_rowoff = o; o = al(o + (pair ? sizeof(int) * (M + 1) : 0));
     p.off_memb = o;   o = al(o + (pair ? sizeof(unsigned) * 8 * p.W : 0));
-    p.off_G = o;      o = al(o + sizeof(R) * (pair ? (size_t)gcap : npair));
+    // pair rule: edge vectors (dx, dy, dz, r^2) -- FP64: one table for the unit's
+    // edges (FP64 arithmetic is the scarce resource); FP32: per-warp partner
+    // vectors of the current first molecule only (shared memory is)
+    p.off_ed = o;
+    o = al(o + (pair ? sizeof(R) * 4 * (f64 ? (size_t)gcap : M * nwarps) : 0));
+    const size_t gb = sizeof(R) * (pair ? (size_t)gcap : (acc_mode == 0 ? npair : 0));
+    p.off_G = o;      o = al(o + (pair ? (gb > accb ? gb : accb) : gb));
     p.off_D = o;      o = al(o + (!pair && use_d ? sizeof(float) * npair : 0));
+    p.off_acc = pair ? p.off_G : o;  // pair rule: the fallback accumulators alias G
+    o = al(o + (!pair && acc_mode == 1 ? accb : 0));
     p.off_plq = o;    o = al(o + (pair ? sizeof(unsigned short) * M * nwarps : 0));
-    p.off_queue = o;  o = al(o + sizeof(unsigned long long) * 64 * (size_t)nwarps);
+    p.off_queue = o;  o = al(o + (pair ? 0 : sizeof(unsigned long long) * 64 * (size_t)nwarps));
     p.total = o;
     return p;
+}
+
+// Launch configuration of the ATM kernels for units of at most mcap molecules.
+// 3c01: 4 warps.  3c18/3c08 pair rule: 4 warps (FP32) or 8 (FP64) and pair
+// scalars for 20 edges per molecule (a liquid has about 15), halved until
+// they fit (a unit with more edges falls back to per-molecule accumulators);
+// product rule: 8 warps,
+// dense distances + dense pair scalars, else dense pair scalars only, else
+// per-molecule accumulators.  Returns false if nothing fits.
+struct AtmPlan {
+    int nwarps, gcap, use_d, acc_mode;
+    size_t smem;
+};
+
+inline bool atm_choose_plan(int trav, int trunc, int prec, int mcap, int optin, AtmPlan& P)
+{
+    P.nwarps = (trav == 0 || (trunc == 0 && prec == 1)) ? 4 : 8;
+    P.gcap = 0;
+    P.use_d = 0;
+    P.acc_mode = 0;
+    auto bytes = [&]() -> size_t {
+        if (trav == 0)
+            return prec == 0 ? owner_smem_plan<double>(mcap, P.nwarps).total
+                             : owner_smem_plan<float>(mcap, P.nwarps).total;
+        return prec == 0
+                   ? block_smem_plan<double>(trunc, mcap, P.nwarps, P.gcap, P.use_d, P.acc_mode).total
+                   : block_smem_plan<float>(trunc, mcap, P.nwarps, P.gcap, P.use_d, P.acc_mode).total;
+    };
+    if (trav == 0) {
+        P.smem = bytes();
+        return P.smem <= (size_t)optin;
+    }
+    const long long npair = (long long)mcap * (mcap - 1) / 2;
+    if (trunc == 0) {
+        long long g = npair < 20ll * mcap ? npair : 20ll * mcap;
+        for (;;) {
+            P.gcap = (int)g;
+            P.smem = bytes();
+            if (P.smem <= (size_t)optin || g == 0) break;
+            g /= 2;
+        }
+        return P.smem <= (size_t)optin;
+    }
+    const int modes[3][2] = {{1, 0}, {0, 0}, {0, 1}};
+    for (const auto& m : modes) {
+        P.use_d = m[0];
+        P.acc_mode = m[1];
+        P.smem = bytes();
+        if (P.smem <= (size_t)optin) return true;
+    }
+    return false;
 }
 
 }  // namespace atm3

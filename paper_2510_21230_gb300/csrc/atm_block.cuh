@@ -2,31 +2,103 @@
 //
 // One CTA per unit: the base cell with its 13 forward neighbours (3c18) or
 // the 2x2x2 block anchored at the base cell (3c08).  The unit's M molecules
-// are staged in shared memory in slot order, so a triplet i < j < k of staged
-// indices always lists its cells in the order the traversal's tasks do.
+// are staged in shared memory in slot order, so a triplet p < q < r of staged
+// indices lists its cells in the order the traversal's tasks do.  Each staged
+// molecule carries its exact base-frame shift o*w, so the canonical
+// displacement (xl_q - xl_p) + (o_q - o_p) w needs no slot lookups.
 //
-//  1. Pair decisions.  Pair rule: an upper-triangular bitmask adjacency
-//     adj[p] = {q > p : |d(p,q)| < r_c} (one ballot per 32 pairs) and its
-//     transpose; edges are numbered row by row.  Product rule: a dense table
-//     of FP32 squared distances (or on-the-fly distances when it does not fit).
-//  2. Triangles.  Pair rule: for every first molecule p and edge (p,q), the
-//     third molecules are the set bits of adj[p] & adj[q] & (allowed slots),
-//     i.e. the triplet's three pair tests are shared by every triplet that
-//     contains the pair.  Product rule: every candidate p < q < r of the
-//     unit's tasks is tested on the sorted product of its squared sides.
-//     Interacting triplets go to a warp queue and are evaluated 32 at a time.
-//  3. Edge scalars.  By Eq. forcepairs each triplet's forces are three pair
-//     terms g_e d_e along its sides (g = 2 du/d(r^2)), so a triplet adds three
-//     scalars to per-pair accumulators G_e instead of nine force components.
-//  4. Gather.  Every molecule m sums F_m = sum_e G_e d(m -> other end) over
-//     its pairs in one thread (compensated in FP32), and adds the unit's share
-//     to the global FP64 force once.
+// Pair rule
+//  1. Upper-triangular bitmask adjacency adj[p] = {q > p : |d(p,q)| < r_c}
+//     (one ballot per 32 pairs) and its transpose.
+//  2. Edges are numbered row by row (row offsets and per-word prefix
+//     popcounts).
+//  3. A warp takes a first molecule p and stores its partner vectors d(p, q).
+//     The triangles of its edges (p, q) are the set bits of
+//     adj[p] & adj[q] & (slots allowed as third member): counted per edge,
+//     prefix-summed over the warp and expanded 32 at a time, so every pair test
+//     is shared by all the triplets that contain the pair and every lane of an
+//     expansion round evaluates one triangle.
+// Product rule
+//  1. Dense FP32 squared distances (or on-the-fly when they do not fit).
+//  3. Every candidate p < q < r of the unit's tasks, enumerated r-major, is
+//     tested on the sorted product of its squared sides; interacting triplets
+//     are queued per warp and evaluated 32 at a time.
+// Both rules
+//  4. Evaluation: one reciprocal square root, no division.  By Eq. forcepairs
+//     a triplet's forces are three pair terms g_e d_e along its sides, so it
+//     adds three scalars to per-pair accumulators G_e (product rule: runs of
+//     equal pairs in a batch are first summed with a segmented warp reduction).
+//  5. Every molecule sums F_m = sum_e G_e d(m -> other end) over its pairs in
+//     one thread (Kahan-compensated in FP32) and adds the unit's share to the
+//     global FP64 force with one atomic per component.
+// When a unit has more edges than the edge table holds, or the dense pair
+// table does not fit, the unit falls back to per-molecule shared-memory force
+// accumulators (compensated atomics in FP32).
 #pragma once
 #include "atm_common.cuh"
 
 namespace atm3 {
 
 __device__ __forceinline__ int tri_index(int x, int y) { return y * (y - 1) / 2 + x; }  // x < y
+
+// per-molecule force accumulators in shared memory (fallback mode)
+template <typename R>
+struct Acc;
+template <>
+struct Acc<double> {
+    static __device__ __forceinline__ void add(unsigned char* base, int mcap, int idx, double v)
+    {
+        atomicAdd(reinterpret_cast<double*>(base) + idx, v);
+    }
+    static __device__ __forceinline__ double get(const unsigned char* base, int mcap, int idx)
+    {
+        return reinterpret_cast<const double*>(base)[idx];
+    }
+    static __device__ __forceinline__ void zero(unsigned char* base, int mcap, int idx)
+    {
+        reinterpret_cast<double*>(base)[idx] = 0.0;
+    }
+};
+// FP32: hi holds the rounded sum, lo the exact rounding error of every atomic
+// addition (two-sum of the value the atomic returned and the addend)
+template <>
+struct Acc<float> {
+    static __device__ __forceinline__ void add(unsigned char* base, int mcap, int idx, float v)
+    {
+        float* hi = reinterpret_cast<float*>(base);
+        float old = atomicAdd(hi + idx, v);
+        float s = __fadd_rn(old, v);
+        float bp = __fsub_rn(s, old);
+        float ap = __fsub_rn(s, bp);
+        float e = __fadd_rn(__fsub_rn(old, ap), __fsub_rn(v, bp));
+        if (e != 0.f) atomicAdd(hi + 3 * mcap + idx, e);
+    }
+    static __device__ __forceinline__ double get(const unsigned char* base, int mcap, int idx)
+    {
+        const float* hi = reinterpret_cast<const float*>(base);
+        return (double)hi[idx] + (double)hi[3 * mcap + idx];
+    }
+    static __device__ __forceinline__ void zero(unsigned char* base, int mcap, int idx)
+    {
+        float* hi = reinterpret_cast<float*>(base);
+        hi[idx] = 0.f;
+        hi[3 * mcap + idx] = 0.f;
+    }
+};
+
+// sum of v over the contiguous run of lanes that share key, delivered to the
+// run's first lane (the return value is meaningful there only)
+template <typename R>
+__device__ __forceinline__ R seg_sum(R v, int key, int lane)
+{
+    const unsigned FULL = 0xffffffffu;
+    for (int o = 1; o < 32; o <<= 1) {
+        R t = __shfl_down_sync(FULL, v, o);
+        int tk = __shfl_down_sync(FULL, key, o);
+        if (lane + o < 32 && tk == key) v += t;
+    }
+    return v;
+}
 
 template <int TRAV, int TRUNC, typename R>
 __global__ void __launch_bounds__(256) atm_block_kernel(const AtmArgs<R> A)
@@ -47,22 +119,32 @@ __global__ void __launch_bounds__(256) atm_block_kernel(const AtmArgs<R> A)
     const int nwarps = blockDim.x >> 5;
     const long long u = blockIdx.x;
     const int mcap = A.mcap;
-    const BlockSmem plan = block_smem_plan<R>(TRUNC, mcap, nwarps, A.gcap, A.use_d);
+    const BlockSmem plan = block_smem_plan<R>(TRUNC, mcap, nwarps, A.gcap, A.use_d, A.acc_mode);
     const int W = plan.W;
     R* px = reinterpret_cast<R*>(smem + plan.off_pos);
     R* py = px + mcap;
     R* pz = py + mcap;
+    R* shx = reinterpret_cast<R*>(smem + plan.off_sh);
+    R* shy = shx + mcap;
+    R* shz = shy + mcap;
     float* fx32 = F64 ? reinterpret_cast<float*>(smem + plan.off_pos32) : reinterpret_cast<float*>(px);
     float* fy32 = fx32 + mcap;
     float* fz32 = fy32 + mcap;
+    float* sx32 = F64 ? reinterpret_cast<float*>(smem + plan.off_sh32) : reinterpret_cast<float*>(shx);
+    float* sy32 = sx32 + mcap;
+    float* sz32 = sy32 + mcap;
     int* sidx = reinterpret_cast<int*>(smem + plan.off_idx);
     unsigned char* sslot = smem + plan.off_slot;
     unsigned* adj = reinterpret_cast<unsigned*>(smem + plan.off_adj);
     unsigned* adjT = reinterpret_cast<unsigned*>(smem + plan.off_adjT);
+    unsigned short* rowpre = reinterpret_cast<unsigned short*>(smem + plan.off_rowpre);
     int* rowoff = reinterpret_cast<int*>(smem + plan.off_rowoff);
     unsigned* memb = reinterpret_cast<unsigned*>(smem + plan.off_memb);
+    // FP64: the unit's edge-vector table; FP32: this warp's partner vectors
+    R* ED = reinterpret_cast<R*>(smem + plan.off_ed) + (F64 ? (size_t)0 : (size_t)warp * 4 * mcap);
     R* G = reinterpret_cast<R*>(smem + plan.off_G);
     float* D = reinterpret_cast<float*>(smem + plan.off_D);
+    unsigned char* acc = smem + plan.off_acc;
     unsigned short* plq = reinterpret_cast<unsigned short*>(smem + plan.off_plq) + warp * mcap;
     unsigned long long* queue =
         reinterpret_cast<unsigned long long*>(smem + plan.off_queue) + warp * 64;
@@ -72,7 +154,6 @@ __global__ void __launch_bounds__(256) atm_block_kernel(const AtmArgs<R> A)
     __syncthreads();
     const int M = s_beg[S];
     const int Mfirst = (TRAV == 2) ? M : s_beg[1];
-    const int npair = M * (M - 1) / 2;
     if (M > mcap) {
         if (tid == 0) {
             atomicOr(A.status, ST_CAPACITY);
@@ -85,8 +166,12 @@ __global__ void __launch_bounds__(256) atm_block_kernel(const AtmArgs<R> A)
     }
     const int Wm = (M + 31) >> 5;
     const long long n = A.n;
+    const R w0 = A.w[0], w1 = A.w[1], w2 = A.w[2];
+    const float wf0 = A.wf[0], wf1 = A.wf[1], wf2 = A.wf[2];
+    const R rc2 = A.rc2, rc6 = A.rc6, nu = A.nu;
+    const unsigned lt_mask = (1u << lane) - 1u;
 
-    // ---- stage the unit
+    // ---- stage the unit: positions and exact shifts o * w
     for (int t = tid; t < M; t += blockDim.x) {
         int s = 0;
         while (s_beg[s + 1] <= t) s++;
@@ -94,82 +179,90 @@ __global__ void __launch_bounds__(256) atm_block_kernel(const AtmArgs<R> A)
         px[t] = A.xl[g];
         py[t] = A.xl[n + g];
         pz[t] = A.xl[2 * n + g];
+        shx[t] = (R)s_off[s][0] * w0;
+        shy[t] = (R)s_off[s][1] * w1;
+        shz[t] = (R)s_off[s][2] * w2;
         if (F64) {
             fx32[t] = A.xl32[g];
             fy32[t] = A.xl32[n + g];
             fz32[t] = A.xl32[2 * n + g];
+            sx32[t] = (float)s_off[s][0] * wf0;
+            sy32[t] = (float)s_off[s][1] * wf1;
+            sz32[t] = (float)s_off[s][2] * wf2;
         }
         sidx[t] = g;
         sslot[t] = (unsigned char)s;
     }
-    const int gsize = PAIR ? A.gcap : npair;
-    for (int t = tid; t < gsize; t += blockDim.x) G[t] = R(0);
+    const bool dense_g = !PAIR && A.acc_mode == 0;
+    if (dense_g)
+        for (int t = tid; t < M * (M - 1) / 2; t += blockDim.x) G[t] = R(0);
+    if (!PAIR && A.acc_mode == 1)
+        for (int t = tid; t < M; t += blockDim.x) {
+            Acc<R>::zero(acc, mcap, t);
+            Acc<R>::zero(acc, mcap, mcap + t);
+            Acc<R>::zero(acc, mcap, 2 * mcap + t);
+        }
     if (PAIR)
         for (int t = tid; t < M * W; t += blockDim.x) adjT[t] = 0u;
     __syncthreads();
 
-    const R w0 = A.w[0], w1 = A.w[1], w2 = A.w[2];
-    const float wf0 = A.wf[0], wf1 = A.wf[1], wf2 = A.wf[2];
-    const R rc2 = A.rc2, rc6 = A.rc6, nu = A.nu;
-    const unsigned lt_mask = (1u << lane) - 1u;
-
-    auto offs = [&](int p, int q, int& mx, int& my, int& mz) {
-        int sp = sslot[p], sq = sslot[q];
-        mx = s_off[sq][0] - s_off[sp][0];
-        my = s_off[sq][1] - s_off[sp][1];
-        mz = s_off[sq][2] - s_off[sp][2];
-    };
+    // canonical displacement p -> q, working precision and FP32
     auto disp = [&](int p, int q, R& dx, R& dy, R& dz) -> R {
-        int mx, my, mz;
-        offs(p, q, mx, my, mz);
-        return canon_disp<R>(px[p], py[p], pz[p], px[q], py[q], pz[q], mx, my, mz, w0, w1, w2, dx,
-                             dy, dz);
+        typedef Ar<R> Q;
+        dx = Q::add(Q::sub(px[q], px[p]), Q::sub(shx[q], shx[p]));
+        dy = Q::add(Q::sub(py[q], py[p]), Q::sub(shy[q], shy[p]));
+        dz = Q::add(Q::sub(pz[q], pz[p]), Q::sub(shz[q], shz[p]));
+        return Q::add(Q::add(Q::mul(dx, dx), Q::mul(dy, dy)), Q::mul(dz, dz));
     };
     auto disp32 = [&](int p, int q) -> float {
-        int mx, my, mz;
-        offs(p, q, mx, my, mz);
-        float dx, dy, dz;
-        return canon_disp<float>(fx32[p], fy32[p], fz32[p], fx32[q], fy32[q], fz32[q], mx, my, mz,
-                                 wf0, wf1, wf2, dx, dy, dz);
+        typedef Ar<float> Q;
+        float dx = Q::add(Q::sub(fx32[q], fx32[p]), Q::sub(sx32[q], sx32[p]));
+        float dy = Q::add(Q::sub(fy32[q], fy32[p]), Q::sub(sy32[q], sy32[p]));
+        float dz = Q::add(Q::sub(fz32[q], fz32[p]), Q::sub(sz32[q], sz32[p]));
+        return Q::add(Q::add(Q::mul(dx, dx), Q::mul(dy, dy)), Q::mul(dz, dz));
+    };
+    // pair-rule decision |d(p,q)| < r_c (FP64 through the FP32 prefilter)
+    auto close = [&](int p, int q) -> bool {
+        R dx, dy, dz;
+        if (!F64) return disp(p, q, dx, dy, dz) < rc2;
+        float f2 = disp32(p, q);
+        if (f2 < A.p_lo) return true;
+        if (f2 > A.p_hi) return false;
+        return disp(p, q, dx, dy, dz) < rc2;
+    };
+    // rank of y among the set bits of row x = edge number of (x, y) within row x
+    auto rank = [&](int x, int y) -> int {
+        int wy = y >> 5;
+        return rowpre[x * W + wy] + __popc(adj[x * W + wy] & ((1u << (y & 31)) - 1u));
     };
 
     // ---- 1. pair decisions
     if (PAIR) {
         for (int p = warp; p < M; p += nwarps) {
-            for (int w = 0; w < (p >> 5); w++)
-                if (lane == 0) adj[p * W + w] = 0u;
-            for (int w = p >> 5; w < Wm; w++) {
-                int q = (w << 5) + lane;
-                bool keep = false;
-                if (q > p && q < M) {
-                    if (!F64) {
-                        R dx, dy, dz;
-                        keep = disp(p, q, dx, dy, dz) < rc2;
-                    } else {
-                        float f2 = disp32(p, q);
-                        if (f2 < A.p_lo) {
-                            keep = true;
-                        } else if (f2 <= A.p_hi) {
-                            R dx, dy, dz;
-                            keep = disp(p, q, dx, dy, dz) < rc2;
-                        }
-                    }
+            for (int w = 0; w < Wm; w++) {
+                if (w < (p >> 5)) {
+                    if (lane == 0) adj[p * W + w] = 0u;
+                    continue;
                 }
+                int q = (w << 5) + lane;
+                bool keep = q > p && q < M && close(p, q);
                 unsigned word = __ballot_sync(FULL, keep);
                 if (lane == 0) adj[p * W + w] = word;
                 if (keep) atomicOr(&adjT[q * W + (p >> 5)], 1u << (p & 31));
             }
         }
     } else if (A.use_d) {
-        for (int t = tid; t < npair; t += blockDim.x) {
+        for (int t = tid; t < M * (M - 1) / 2; t += blockDim.x) {
             int y = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)t)) * 0.5f);
             while (y * (y - 1) / 2 > t) y--;
             while ((y + 1) * y / 2 <= t) y++;
-            int x = t - y * (y - 1) / 2;
-            D[t] = disp32(x, y);
+            D[t] = disp32(t - y * (y - 1) / 2, y);
         }
     }
     __syncthreads();
+
+    // ---- 2. edge numbering, third-member slot masks, edge vectors
+    bool edge_mode = false;
     if (PAIR) {
         if (warp == 0) {
             int run = 0;
@@ -177,7 +270,10 @@ __global__ void __launch_bounds__(256) atm_block_kernel(const AtmArgs<R> A)
                 int p = p0 + lane;
                 int c = 0;
                 if (p < M)
-                    for (int w = 0; w < Wm; w++) c += __popc(adj[p * W + w]);
+                    for (int w = 0; w < Wm; w++) {
+                        rowpre[p * W + w] = (unsigned short)c;
+                        c += __popc(adj[p * W + w]);
+                    }
                 int incl = c;
                 for (int o = 1; o < 32; o <<= 1) {
                     int v = __shfl_up_sync(FULL, incl, o);
@@ -192,67 +288,144 @@ __global__ void __launch_bounds__(256) atm_block_kernel(const AtmArgs<R> A)
             }
         }
         if (TRAV == 2) {
-            // molecules r allowed as third member given v = slot(p) & slot(q): (v & slot(r)) == 0
-            for (int t = tid; t < 8 * Wm; t += blockDim.x) {
-                int v = t / Wm, w = t - v * Wm;
-                unsigned word = 0u;
-                for (int b = 0; b < 32; b++) {
-                    int r = (w << 5) + b;
-                    if (r < M && (v & sslot[r]) == 0) word |= 1u << b;
-                }
-                memb[v * W + w] = word;
+            // allowed third members r given v = slot(p) & slot(q): (v & slot(r)) == 0
+            const int w0w = nwarps > 1 ? 1 : 0, nw = nwarps > 1 ? nwarps - 1 : 1;
+            for (int idx = warp - w0w; idx >= 0 && idx < 8 * Wm; idx += nw) {
+                int v = idx / Wm, w = idx - v * Wm;
+                int r = (w << 5) + lane;
+                unsigned word = __ballot_sync(FULL, r < M && (v & sslot[r]) == 0);
+                if (lane == 0) memb[v * W + w] = word;
             }
         }
         __syncthreads();
-        if (s_edges > A.gcap) {
-            if (tid == 0) {
-                atomicOr(A.status, ST_CAPACITY);
-                A.unit_ew[2 * u] = 0.0;
-                A.unit_ew[2 * u + 1] = 0.0;
-                A.unit_cnt[2 * u] = 0ull;
-                A.unit_cnt[2 * u + 1] = 0ull;
+        edge_mode = s_edges <= A.gcap;
+        if (edge_mode) {
+            for (int t = tid; t < s_edges; t += blockDim.x) G[t] = R(0);
+            if (F64) {
+                // edge-vector table: d(p -> q) and |d|^2 of every edge, once per unit
+                for (int p = warp; p < M; p += nwarps) {
+                    for (int w = p >> 5; w < Wm; w++) {
+                        unsigned word = adj[p * W + w];
+                        if ((word >> lane) & 1u) {
+                            int q = (w << 5) + lane;
+                            int e = rowoff[p] + rowpre[p * W + w] + __popc(word & lt_mask);
+                            R dx, dy, dz;
+                            R a = disp(p, q, dx, dy, dz);
+                            ED[4 * e] = dx;
+                            ED[4 * e + 1] = dy;
+                            ED[4 * e + 2] = dz;
+                            ED[4 * e + 3] = a;
+                        }
+                    }
+                }
             }
-            return;
+        } else {
+            for (int t = tid; t < M; t += blockDim.x) {
+                Acc<R>::zero(acc, mcap, t);
+                Acc<R>::zero(acc, mcap, mcap + t);
+                Acc<R>::zero(acc, mcap, 2 * mcap + t);
+            }
         }
+        __syncthreads();
     }
+    const bool use_acc = PAIR ? !edge_mode : (A.acc_mode == 1);
 
-    // rank of y among the set bits of row x (edges of x are numbered in bit order)
-    auto rank = [&](int x, int y) -> int {
-        int wy = y >> 5, c = 0;
-        for (int w = 0; w < wy; w++) c += __popc(adj[x * W + w]);
-        return c + __popc(adj[x * W + wy] & ((1u << (y & 31)) - 1u));
-    };
-
-    // ---- 2 + 3. triangles, evaluation, edge scalars
+    // ---- 3 + 4. triangles, evaluation, pair scalars
     Sum<R> esum, wsum;
     unsigned int nint = 0;
     int qn = 0;
 
-    auto evaluate = [&](unsigned long long e) {
-        int p = (int)(e & 0x7ff), q = (int)((e >> 11) & 0x7ff), r = (int)((e >> 22) & 0x7ff);
-        int jj = (int)((e >> 33) & 0x7ff);
-        R dpqx, dpqy, dpqz, dprx, dpry, dprz, dqrx, dqry, dqrz;
-        R a = disp(p, q, dpqx, dpqy, dpqz);
-        R b = disp(p, r, dprx, dpry, dprz);
-        R c = disp(q, r, dqrx, dqry, dqrz);
+    // pair rule: evaluate triangle (p, q, r), q and r the jj-th and kk-th partners of p
+    // (all lanes call; invalid lanes only take part in nothing but the arithmetic)
+    auto eval_pair = [&](int p, int q, int r, int jj, int kk, bool valid) {
+        R dpqx, dpqy, dpqz, dprx, dpry, dprz, dqrx, dqry, dqrz, a, b, c;
+        if (F64 && use_acc) {
+            a = disp(p, q, dpqx, dpqy, dpqz);
+            b = disp(p, r, dprx, dpry, dprz);
+            c = disp(q, r, dqrx, dqry, dqrz);
+        } else {
+            const R* E = F64 ? ED + 4 * rowoff[p] : ED;  // p's partners, in bit order
+            dpqx = E[4 * jj]; dpqy = E[4 * jj + 1]; dpqz = E[4 * jj + 2]; a = E[4 * jj + 3];
+            dprx = E[4 * kk]; dpry = E[4 * kk + 1]; dprz = E[4 * kk + 2]; b = E[4 * kk + 3];
+            if (F64) {
+                const int e = rowoff[q] + rank(q, r);
+                dqrx = ED[4 * e]; dqry = ED[4 * e + 1]; dqrz = ED[4 * e + 2]; c = ED[4 * e + 3];
+            } else {
+                c = disp(q, r, dqrx, dqry, dqrz);
+            }
+        }
         R uu, ua, ub, uc;
         atm_terms<R>(a, b, c, nu, uu, ua, ub, uc);
         R gpq = R(2) * ua, gpr = R(2) * ub, gqr = R(2) * uc;
+        if (!valid) return;
         esum.add(uu);
         wsum.add(-(gpq * a + gpr * b + gqr * c));
-        int epq, epr, eqr;
-        if (PAIR) {
-            epq = rowoff[p] + jj;
-            epr = rowoff[p] + rank(p, r);
-            eqr = rowoff[q] + rank(q, r);
+        if (!use_acc) {
+            atomicAdd(G + rowoff[p] + jj, gpq);
+            atomicAdd(G + rowoff[p] + kk, gpr);
+            atomicAdd(G + rowoff[q] + rank(q, r), gqr);
         } else {
-            epq = tri_index(p, q);
-            epr = tri_index(p, r);
-            eqr = tri_index(q, r);
+            Acc<R>::add(acc, mcap, p, gpq * dpqx + gpr * dprx);
+            Acc<R>::add(acc, mcap, mcap + p, gpq * dpqy + gpr * dpry);
+            Acc<R>::add(acc, mcap, 2 * mcap + p, gpq * dpqz + gpr * dprz);
+            Acc<R>::add(acc, mcap, q, gqr * dqrx - gpq * dpqx);
+            Acc<R>::add(acc, mcap, mcap + q, gqr * dqry - gpq * dpqy);
+            Acc<R>::add(acc, mcap, 2 * mcap + q, gqr * dqrz - gpq * dpqz);
+            Acc<R>::add(acc, mcap, r, -(gpr * dprx + gqr * dqrx));
+            Acc<R>::add(acc, mcap, mcap + r, -(gpr * dpry + gqr * dqry));
+            Acc<R>::add(acc, mcap, 2 * mcap + r, -(gpr * dprz + gqr * dqrz));
         }
-        atomicAdd(G + epq, gpq);
-        atomicAdd(G + epr, gpr);
-        atomicAdd(G + eqr, gqr);
+    };
+
+    // product rule: evaluate one queued triplet per lane (all lanes call;
+    // invalid lanes take part in the warp reduction only)
+    auto evaluate = [&](unsigned long long ent, bool valid) {
+        int p = (int)(ent & 0x7ff), q = (int)((ent >> 11) & 0x7ff), r = (int)((ent >> 22) & 0x7ff);
+        R dpqx, dpqy, dpqz, dprx, dpry, dprz, dqrx, dqry, dqrz, a, b, c;
+        int epq = 0, epr = 0, eqr = 0;
+        {
+            a = disp(p, q, dpqx, dpqy, dpqz);
+            b = disp(p, r, dprx, dpry, dprz);
+            c = disp(q, r, dqrx, dqry, dqrz);
+            if (!PAIR) {
+                epq = tri_index(p, q);
+                epr = tri_index(p, r);
+                eqr = tri_index(q, r);
+            }
+        }
+        R uu, ua, ub, uc;
+        atm_terms<R>(a, b, c, nu, uu, ua, ub, uc);
+        R gpq = R(2) * ua, gpr = R(2) * ub, gqr = R(2) * uc;
+        if (!valid) {
+            uu = R(0);
+            gpq = gpr = gqr = R(0);
+        }
+        esum.add(uu);
+        wsum.add(-(gpq * a + gpr * b + gqr * c));
+        if (!use_acc) {
+            // runs of equal keys are contiguous in a batch: e(p,q) for the pair
+            // rule (edge-major order), e(p,r) for the product rule (r-major order)
+            int key = PAIR ? epq : epr;
+            if (!valid) key = -1 - lane;
+            R run = seg_sum<R>(PAIR ? gpq : gpr, key, lane);
+            int prev = __shfl_up_sync(FULL, key, 1);
+            bool head = lane == 0 || prev != key;
+            if (valid) {
+                if (head) atomicAdd(G + key, run);
+                atomicAdd(G + (PAIR ? epr : epq), PAIR ? gpr : gpq);
+                atomicAdd(G + eqr, gqr);
+            }
+        } else if (valid) {
+            Acc<R>::add(acc, mcap, p, gpq * dpqx + gpr * dprx);
+            Acc<R>::add(acc, mcap, mcap + p, gpq * dpqy + gpr * dpry);
+            Acc<R>::add(acc, mcap, 2 * mcap + p, gpq * dpqz + gpr * dprz);
+            Acc<R>::add(acc, mcap, q, gqr * dqrx - gpq * dpqx);
+            Acc<R>::add(acc, mcap, mcap + q, gqr * dqry - gpq * dpqy);
+            Acc<R>::add(acc, mcap, 2 * mcap + q, gqr * dqrz - gpq * dpqz);
+            Acc<R>::add(acc, mcap, r, -(gpr * dprx + gqr * dqrx));
+            Acc<R>::add(acc, mcap, mcap + r, -(gpr * dpry + gqr * dqry));
+            Acc<R>::add(acc, mcap, 2 * mcap + r, -(gpr * dprz + gqr * dqrz));
+        }
     };
     auto push = [&](bool keep, unsigned long long entry) {
         unsigned m = __ballot_sync(FULL, keep);
@@ -261,7 +434,7 @@ __global__ void __launch_bounds__(256) atm_block_kernel(const AtmArgs<R> A)
         nint += keep ? 1u : 0u;
         __syncwarp();
         if (qn >= 32) {
-            evaluate(queue[lane]);
+            evaluate(queue[lane], true);
             __syncwarp();
             if (lane < qn - 32) queue[lane] = queue[32 + lane];
             qn -= 32;
@@ -272,6 +445,9 @@ __global__ void __launch_bounds__(256) atm_block_kernel(const AtmArgs<R> A)
         return (unsigned long long)p | ((unsigned long long)q << 11) |
                ((unsigned long long)r << 22) | ((unsigned long long)jj << 33);
     };
+    auto kword = [&](int p, int q, int v, int w) -> unsigned {
+        return adj[p * W + w] & adj[q * W + w] & (TRAV == 2 ? memb[v * W + w] : FULL);
+    };
 
     for (;;) {
         int p = 0;
@@ -281,12 +457,23 @@ __global__ void __launch_bounds__(256) atm_block_kernel(const AtmArgs<R> A)
         const int sp = sslot[p];
         if (TRAV == 2 && sp == 7) continue;  // no later slot completes an anchored set
         if (PAIR) {
-            // edges (p, q), q > p, in bit order
-            int np = 0;
+            const int np = rowoff[p + 1] - rowoff[p];
+            // p's partners q in bit order with the vectors d(p -> q) and |d|^2
             for (int w = p >> 5; w < Wm; w++) {
                 unsigned word = adj[p * W + w];
-                if ((word >> lane) & 1u) plq[np + __popc(word & lt_mask)] = (unsigned short)((w << 5) + lane);
-                np += __popc(word);
+                if ((word >> lane) & 1u) {
+                    const int jj = rowpre[p * W + w] + __popc(word & lt_mask);
+                    const int q = (w << 5) + lane;
+                    plq[jj] = (unsigned short)q;
+                    if (!F64) {
+                        R dx, dy, dz;
+                        R a = disp(p, q, dx, dy, dz);
+                        ED[4 * jj] = dx;
+                        ED[4 * jj + 1] = dy;
+                        ED[4 * jj + 2] = dz;
+                        ED[4 * jj + 3] = a;
+                    }
+                }
             }
             __syncwarp();
             for (int c0 = 0; c0 < np; c0 += 32) {
@@ -294,44 +481,65 @@ __global__ void __launch_bounds__(256) atm_block_kernel(const AtmArgs<R> A)
                 const bool act = jj < np;
                 const int q = act ? plq[jj] : 0;
                 const int v = act ? (sp & sslot[q]) : 0;
-                int w = q >> 5;
-                unsigned cur = 0u;
+                int cnt = 0;
                 if (act)
-                    cur = adj[p * W + w] & adj[q * W + w] & (TRAV == 2 ? memb[v * W + w] : FULL);
-                for (;;) {
-                    if (act)
-                        while (cur == 0u && w + 1 < Wm) {
-                            w++;
-                            cur = adj[p * W + w] & adj[q * W + w] &
-                                  (TRAV == 2 ? memb[v * W + w] : FULL);
-                        }
-                    const bool has = act && cur != 0u;
-                    if (!__any_sync(FULL, has)) break;
-                    int r = 0;
-                    if (has) {
-                        r = (w << 5) + __ffs(cur) - 1;
-                        cur &= cur - 1u;
+                    for (int w = q >> 5; w < Wm; w++) cnt += __popc(kword(p, q, v, w));
+                int incl = cnt;
+                for (int o = 1; o < 32; o <<= 1) {
+                    int t = __shfl_up_sync(FULL, incl, o);
+                    if (lane >= o) incl += t;
+                }
+                const int total = __shfl_sync(FULL, incl, 31);
+                const int excl = incl - cnt;
+                for (int t0 = 0; t0 < total; t0 += 32) {
+                    const int t = t0 + lane;
+                    const bool valid = t < total;
+                    // lane owning triangle t: the last lane whose exclusive prefix is <= t
+                    int l = 0;
+                    for (int s = 16; s >= 1; s >>= 1) {
+                        int ec = __shfl_sync(FULL, excl, l + s);
+                        if (ec <= t) l += s;
                     }
-                    push(has, pack(p, q, r, jj));
+                    const int ql = __shfl_sync(FULL, q, l);
+                    const int vl = __shfl_sync(FULL, v, l);
+                    int nth = t - __shfl_sync(FULL, excl, l);
+                    int r = 0;
+                    if (valid) {
+                        for (int w = ql >> 5; w < Wm; w++) {
+                            unsigned K = kword(p, ql, vl, w);
+                            int c = __popc(K);
+                            if (nth < c) {
+                                for (int k = 0; k < nth; k++) K &= K - 1u;
+                                r = (w << 5) + __ffs(K) - 1;
+                                break;
+                            }
+                            nth -= c;
+                        }
+                    }
+                    nint += valid ? 1u : 0u;
+                    // invalid lanes evaluate a harmless stand-in (partners 0 and 0)
+                    eval_pair(p, valid ? ql : p, valid ? r : p, valid ? c0 + l : 0,
+                              valid ? rank(p, r) : 0, valid);
                 }
             }
+            __syncwarp();
         } else {
-            // every candidate p < q < r of the unit's tasks
+            // every candidate p < q < r, r-major: t = kk (kk - 1) / 2 + jj, q = p+1+jj, r = p+1+kk
             const int base = p + 1, L = M - base;
             const int T = L * (L - 1) / 2;
             for (int t0 = 0; t0 < T; t0 += 32) {
-                int t = t0 + lane;
+                int kk0 = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)t0)) * 0.5f);
+                while (kk0 * (kk0 - 1) / 2 > t0) kk0--;
+                while ((kk0 + 1) * kk0 / 2 <= t0) kk0++;
+                const int t = t0 + lane;
                 bool keep = false;
                 int q = 0, r = 0;
                 if (t < T) {
-                    int kk = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)t)) * 0.5f);
-                    while (kk * (kk - 1) / 2 > t) kk--;
+                    int kk = kk0;
                     while ((kk + 1) * kk / 2 <= t) kk++;
-                    int jj = t - kk * (kk - 1) / 2;
-                    q = base + jj;
+                    q = base + (t - kk * (kk - 1) / 2);
                     r = base + kk;
-                    bool member = (TRAV != 2) || ((sp & sslot[q] & sslot[r]) == 0);
-                    if (member) {
+                    if (TRAV != 2 || (sp & sslot[q] & sslot[r]) == 0) {
                         float a32, b32, c32;
                         if (A.use_d) {
                             a32 = D[tri_index(p, q)];
@@ -364,45 +572,75 @@ __global__ void __launch_bounds__(256) atm_block_kernel(const AtmArgs<R> A)
                 push(keep, pack(p, q, r, 0));
             }
         }
-        __syncwarp();
     }
-    if (lane < qn) evaluate(queue[lane]);
+    if (!PAIR && qn > 0) evaluate(queue[lane < qn ? lane : 0], lane < qn);
     __syncthreads();
 
-    // ---- 4. gather: F_m = sum over m's pairs of G_e d(m -> other end)
+    // ---- 5. gather: F_m = sum over m's pairs of G_e d(m -> other end)
     for (int m = tid; m < M; m += blockDim.x) {
         Sum<R> fxs, fys, fzs;
-        auto add_pair = [&](int y, R g) {
-            if (g == R(0)) return;
-            R dx, dy, dz;
-            disp(m, y, dx, dy, dz);
-            fxs.add(g * dx);
-            fys.add(g * dy);
-            fzs.add(g * dz);
-        };
-        if (PAIR) {
+        if (use_acc) {
+            fxs.add((R)Acc<R>::get(acc, mcap, m));
+            fys.add((R)Acc<R>::get(acc, mcap, mcap + m));
+            fzs.add((R)Acc<R>::get(acc, mcap, 2 * mcap + m));
+        } else if (PAIR) {
+            // edge vectors: FP64 from the table (d(lo -> hi), so the sign flips for
+            // edges where m is the upper end), FP32 recomputed
             int e = rowoff[m];
             for (int w = 0; w < Wm; w++) {
                 unsigned up = adj[m * W + w];
                 while (up) {
                     int y = (w << 5) + __ffs(up) - 1;
                     up &= up - 1u;
-                    add_pair(y, G[e++]);
+                    const int ee = e++;
+                    R g = G[ee];
+                    if (g != R(0)) {
+                        R dx, dy, dz;
+                        if (F64) {
+                            dx = ED[4 * ee]; dy = ED[4 * ee + 1]; dz = ED[4 * ee + 2];
+                        } else {
+                            disp(m, y, dx, dy, dz);
+                        }
+                        fxs.add(g * dx);
+                        fys.add(g * dy);
+                        fzs.add(g * dz);
+                    }
                 }
                 unsigned dn = adjT[m * W + w];
                 while (dn) {
                     int x = (w << 5) + __ffs(dn) - 1;
                     dn &= dn - 1u;
-                    add_pair(x, G[rowoff[x] + rank(x, m)]);
+                    const int ee = rowoff[x] + rank(x, m);
+                    R g = G[ee];
+                    if (g != R(0)) {
+                        R dx, dy, dz;
+                        if (F64) {
+                            dx = -ED[4 * ee]; dy = -ED[4 * ee + 1]; dz = -ED[4 * ee + 2];
+                        } else {
+                            disp(m, x, dx, dy, dz);
+                        }
+                        fxs.add(g * dx);
+                        fys.add(g * dy);
+                        fzs.add(g * dz);
+                    }
                 }
             }
         } else {
             for (int y = 0; y < M; y++) {
                 if (y == m) continue;
-                add_pair(y, G[y > m ? tri_index(m, y) : tri_index(y, m)]);
+                R g = G[y > m ? tri_index(m, y) : tri_index(y, m)];
+                if (g != R(0)) {
+                    R dx, dy, dz;
+                    disp(m, y, dx, dy, dz);
+                    fxs.add(g * dx);
+                    fys.add(g * dy);
+                    fzs.add(g * dz);
+                }
             }
         }
-        double f0 = fxs.get(), f1 = fys.get(), f2 = fzs.get();
+        double f0 = use_acc ? Acc<R>::get(acc, mcap, m) : fxs.get();
+        double f1 = use_acc ? Acc<R>::get(acc, mcap, mcap + m) : fys.get();
+        double f2 = use_acc ? Acc<R>::get(acc, mcap, 2 * mcap + m) : fzs.get();
         int g = sidx[m];
         if (f0 != 0.0) atomicAdd(A.fs + g, f0);
         if (f1 != 0.0) atomicAdd(A.fs + n + g, f1);

@@ -106,7 +106,7 @@ __device__ __forceinline__ void atm_terms(R a, R b, R c, R nu, R& u, R& ua, R& u
     uc = nq5 * (R(0.375) * (R(2) * c * C - A * B) - K * (a * b));
 }
 
-// running sum: plain for FP64, Neumaier-compensated for FP32
+// running sum: plain for FP64, Kahan-compensated for FP32
 template <typename R>
 struct Sum;
 template <>
@@ -117,17 +117,16 @@ struct Sum<double> {
 };
 template <>
 struct Sum<float> {
+    // Kahan: c carries the rounding error of the last addition, the sum is s - c
     float s = 0.f, c = 0.f;
     __device__ __forceinline__ void add(float v)
     {
-        float t = __fadd_rn(s, v);
-        if (fabsf(s) >= fabsf(v))
-            c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, t), v));
-        else
-            c = __fadd_rn(c, __fadd_rn(__fsub_rn(v, t), s));
+        float y = __fsub_rn(v, c);
+        float t = __fadd_rn(s, y);
+        c = __fsub_rn(__fsub_rn(t, s), y);
         s = t;
     }
-    __device__ __forceinline__ double get() const { return (double)s + (double)c; }
+    __device__ __forceinline__ double get() const { return (double)s - (double)c; }
 };
 
 // Candidate triplets of one unit's cell tasks (Eqs. celltriplet,

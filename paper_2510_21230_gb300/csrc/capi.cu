@@ -9,14 +9,12 @@
 
 #include "atm3.h"
 #include "atm3_internal.cuh"
+#include "forces.cuh"
 #include "md_kernels.cuh"
 
 using namespace atm3;
 
 namespace {
-constexpr int OWNER_NWARPS = 4;    // warps per 3c01 unit CTA
-constexpr int BLOCK_NWARPS = 8;    // warps per 3c18 / 3c08 unit CTA
-constexpr int ATM_MCAP_MAX = 2047; // staged molecules per unit (queue entries pack 11-bit indices)
 }  // namespace
 
 struct atm_ctx {
@@ -371,107 +369,45 @@ extern "C" atm_status atm_get_cells(atm_ctx* c, int32_t* cell_of, int32_t* cell_
 // LJ + ATM force kernels for the current cells
 static atm_status enqueue_forces(atm_ctx* c, int trav, int trunc, int prec)
 {
-    const double rc = c->p.rc;
-    // LJ pairs
-    LjArgs<double> l64{};
-    LjArgs<float> l32{};
-    double sig2 = c->p.lj_sigma * c->p.lj_sigma;
-    double sc = sig2 / (rc * rc), sc3 = sc * sc * sc;
-    double ushift = c->p.lj_shift ? 4.0 * c->p.lj_eps * (sc3 * sc3 - sc3) : 0.0;
-    if (prec == ATM_FP64) {
-        l64.g = c->g; l64.n = c->n; l64.xl = c->xl; l64.cell_start = c->start;
-        l64.cell_sorted = c->cell_sorted; l64.fs = c->f_lj; l64.part_ew = c->lj_ew;
-        l64.part_cnt = c->lj_cnt;
-        for (int d = 0; d < 3; d++) l64.w[d] = c->g.w[d];
-        l64.rc2 = rc * rc; l64.sig2 = sig2; l64.eps4 = 4.0 * c->p.lj_eps;
-        l64.eps24 = 24.0 * c->p.lj_eps; l64.eps48 = 48.0 * c->p.lj_eps; l64.ushift = ushift;
-    } else {
-        float rcf = (float)rc;
-        l32.g = c->g; l32.n = c->n; l32.xl = c->xl32; l32.cell_start = c->start;
-        l32.cell_sorted = c->cell_sorted; l32.fs = c->f_lj; l32.part_ew = c->lj_ew;
-        l32.part_cnt = c->lj_cnt;
-        for (int d = 0; d < 3; d++) l32.w[d] = (float)c->g.w[d];
-        l32.rc2 = rcf * rcf; l32.sig2 = (float)sig2; l32.eps4 = (float)(4.0 * c->p.lj_eps);
-        l32.eps24 = (float)(24.0 * c->p.lj_eps); l32.eps48 = (float)(48.0 * c->p.lj_eps);
-        l32.ushift = (float)ushift;
-    }
+    ForceJob j;
+    j.g = c->g;
+    j.n = c->n;
+    j.xl = c->xl;
+    j.xl32 = c->xl32;
+    j.start = c->start;
+    j.cell_sorted = c->cell_sorted;
+    j.f_lj = c->f_lj;
+    j.f_atm = c->f_atm;
+    j.lj_ew = c->lj_ew;
+    j.lj_cnt = c->lj_cnt;
+    j.unit_ew = c->unit_ew;
+    j.unit_cnt = c->unit_cnt;
+    j.status = c->d_status;
+    j.rc = c->p.rc;
+    j.nu = c->p.nu;
+    j.lj_eps = c->p.lj_eps;
+    j.lj_sigma = c->p.lj_sigma;
+    j.lj_shift = c->p.lj_shift;
+    j.trav = trav;
+    j.trunc = trunc;
+    j.prec = prec;
+    j.mcap = c->unit_max[trav] > 0 ? c->unit_max[trav] : 1;
+    j.optin = c->smem_optin;
+    j.st = c->st;
+
     cudaEvent_t ev = prof_begin(c);
-    CU(launch_lj(prec, l64, l32, c->st));
+    CU(enqueue_lj(j));
     prof_end(c, PK_LJ, ev);
     c->n_launch += 1;
 
-    // ATM triplets: staged-molecule capacity = the largest unit of this traversal
-    int mcap = c->unit_max[trav] > 0 ? c->unit_max[trav] : 1;
-    if (mcap > ATM_MCAP_MAX)
-        return fail(c, ATM_E_CAPACITY, "a traversal unit holds %d molecules (max %d staged)",
-                    mcap, ATM_MCAP_MAX);
-    const int nwarps = trav == ATM_3C01 ? OWNER_NWARPS : BLOCK_NWARPS;
-    // pair rule: room for 32 edges per staged molecule (more than 3x a liquid's count)
-    const int gcap = (int)std::min<long long>((long long)mcap * (mcap - 1) / 2, 32ll * mcap);
-    int use_d = 1;
-    auto plan_bytes = [&](int ud) -> size_t {
-        if (trav == ATM_3C01)
-            return prec == ATM_FP64 ? owner_smem_plan<double>(mcap, nwarps).total
-                                    : owner_smem_plan<float>(mcap, nwarps).total;
-        return prec == ATM_FP64 ? block_smem_plan<double>(trunc, mcap, nwarps, gcap, ud).total
-                                : block_smem_plan<float>(trunc, mcap, nwarps, gcap, ud).total;
-    };
-    size_t smem = plan_bytes(use_d);
-    if (smem > (size_t)c->smem_optin && trav != ATM_3C01 && trunc == ATM_TRUNC_PRODUCT) {
-        use_d = 0;  // distances on the fly instead of the dense table
-        smem = plan_bytes(use_d);
-    }
-    if (smem > (size_t)c->smem_optin)
-        return fail(c, ATM_E_CAPACITY,
-                    "a unit of %d molecules needs %zu bytes of shared memory (max %d)", mcap, smem,
-                    c->smem_optin);
-    if (smem > c->smem_set[prec][trav][trunc]) {
-        CU(prec == ATM_FP64 ? atm_attr_fp64(trav, trunc, smem) : atm_attr_fp32(trav, trunc, smem));
-        c->smem_set[prec][trav][trunc] = smem;
-    }
-    if (trav != ATM_3C01)
-        CU(cudaMemsetAsync(c->f_atm, 0, 3 * (size_t)c->n * sizeof(double), c->st));
-    // FP32 prefilter bands of the FP64 decisions (derivation in atm_common.cuh)
-    const double rc2d = rc * rc, rc6d = rc2d * rc2d * rc2d;
-    const double wmax = std::max(c->g.w[0], std::max(c->g.w[1], c->g.w[2]));
     ev = prof_begin(c);
-    if (prec == ATM_FP64) {
-        AtmArgs<double> a{};
-        a.g = c->g; a.n = c->n; a.xl = c->xl; a.xl32 = c->xl32; a.cell_start = c->start;
-        a.fs = c->f_atm; a.unit_ew = c->unit_ew; a.unit_cnt = c->unit_cnt; a.status = c->d_status;
-        for (int d = 0; d < 3; d++) {
-            a.w[d] = c->g.w[d];
-            a.wf[d] = (float)c->g.w[d];
-        }
-        a.rc2 = rc2d;
-        a.rc6 = rc6d;
-        a.nu = c->p.nu;
-        a.p_lo = (float)(rc2d * (1.0 - 1.0 / 4096.0));
-        a.p_hi = (float)(rc2d * (1.0 + 1.0 / 4096.0));
-        a.q_lo = (float)(rc6d * (1.0 - 1.0 / 1024.0));
-        a.q_hi = (float)(rc6d * (1.0 + 1.0 / 1024.0));
-        a.dmin = (float)((0.02 * wmax) * (0.02 * wmax));
-        a.mcap = mcap;
-        a.gcap = gcap;
-        a.use_d = use_d;
-        CU(launch_atm_fp64(trav, trunc, a, nwarps, smem, c->st));
-    } else {
-        AtmArgs<float> a{};
-        float rcf = (float)rc;
-        a.g = c->g; a.n = c->n; a.xl = c->xl32; a.xl32 = c->xl32; a.cell_start = c->start;
-        a.fs = c->f_atm; a.unit_ew = c->unit_ew; a.unit_cnt = c->unit_cnt; a.status = c->d_status;
-        for (int d = 0; d < 3; d++) {
-            a.w[d] = (float)c->g.w[d];
-            a.wf[d] = (float)c->g.w[d];
-        }
-        a.rc2 = rcf * rcf;
-        a.rc6 = a.rc2 * a.rc2 * a.rc2;
-        a.nu = (float)c->p.nu;
-        a.mcap = mcap;
-        a.gcap = gcap;
-        a.use_d = use_d;
-        CU(launch_atm_fp32(trav, trunc, a, nwarps, smem, c->st));
-    }
+    bool capacity = false;
+    cudaError_t e = enqueue_atm(j, &c->smem_set[prec][trav][trunc], &capacity);
+    if (capacity)
+        return fail(c, ATM_E_CAPACITY,
+                    "a traversal unit of %d molecules does not fit the kernels' shared memory",
+                    j.mcap);
+    CU(e);
     prof_end(c, PK_ATM, ev);
     c->n_launch += 1;
     c->n_atm += 1;

@@ -217,6 +217,16 @@ __global__ void __launch_bounds__(128) k_lj_owner(const LjArgs<R> A)
             R sx = Q::mul((R)dx, A.w[0]), sy = Q::mul((R)dy, A.w[1]), sz = Q::mul((R)dz, A.w[2]);
             for (int q = q0; q < q1; q++) {
                 if (q == s) continue;
+                if (sizeof(R) == 8) {
+                    // FP32 prefilter: values outside the band decide the FP64 test
+                    typedef LjArith<float> F;
+                    float ex = F::add(F::sub(A.xl32[q], A.xl32[s]), F::mul((float)dx, A.wf[0]));
+                    float ey = F::add(F::sub(A.xl32[n + q], A.xl32[n + s]), F::mul((float)dy, A.wf[1]));
+                    float ez = F::add(F::sub(A.xl32[2 * n + q], A.xl32[2 * n + s]),
+                                      F::mul((float)dz, A.wf[2]));
+                    float f2 = F::add(F::add(F::mul(ex, ex), F::mul(ey, ey)), F::mul(ez, ez));
+                    if (f2 > A.p_hi) continue;
+                }
                 R ddx = Q::add(Q::sub(A.xl[q], xs), sx);
                 R ddy = Q::add(Q::sub(A.xl[n + q], ys), sy);
                 R ddz = Q::add(Q::sub(A.xl[2 * n + q], zs), sz);

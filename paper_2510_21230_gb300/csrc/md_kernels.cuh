@@ -16,6 +16,11 @@ struct LjArgs {
     unsigned long long* part_cnt;  // [2 * blocks]: candidates, visits
     R w[3];
     R rc2, sig2, eps4, eps24, eps48, ushift;
+    // FP64 path: FP32 prefilter of the cutoff test (FP32 coordinates, cell
+    // edges, and the band outside which the FP32 value decides; see atm_common.cuh)
+    const float* xl32;
+    float wf[3];
+    float p_lo, p_hi;
 };
 
 // device-side copy of atm_result (same layout)

@@ -21,6 +21,7 @@
 
 #include "atm3.h"
 #include "atm3_internal.cuh"
+#include "forces.cuh"
 #include "md_kernels.cuh"
 
 using namespace atm3;
@@ -167,91 +168,37 @@ extern "C" atm_status atm_compute_forces_noalloc(const atm_params* p, int64_t n,
     NA_CU(cudaStreamSynchronize(st));
     if (hstat & ST_NONFINITE) return ATM_E_NONFINITE;
 
-    // LJ pairs
-    const double rc = p->rc, sig2 = p->lj_sigma * p->lj_sigma;
-    const double sc = sig2 / (rc * rc), sc3 = sc * sc * sc;
-    const double ushift = p->lj_shift ? 4.0 * p->lj_eps * (sc3 * sc3 - sc3) : 0.0;
-    LjArgs<double> l64{};
-    LjArgs<float> l32{};
-    if (prec == ATM_FP64) {
-        l64.g = g; l64.n = n; l64.xl = xl; l64.cell_start = start; l64.cell_sorted = cell_sorted;
-        l64.fs = f_lj; l64.part_ew = lj_ew; l64.part_cnt = lj_cnt;
-        for (int d = 0; d < 3; d++) l64.w[d] = g.w[d];
-        l64.rc2 = rc * rc; l64.sig2 = sig2; l64.eps4 = 4.0 * p->lj_eps;
-        l64.eps24 = 24.0 * p->lj_eps; l64.eps48 = 48.0 * p->lj_eps; l64.ushift = ushift;
-    } else {
-        float rcf = (float)rc;
-        l32.g = g; l32.n = n; l32.xl = xl32; l32.cell_start = start; l32.cell_sorted = cell_sorted;
-        l32.fs = f_lj; l32.part_ew = lj_ew; l32.part_cnt = lj_cnt;
-        for (int d = 0; d < 3; d++) l32.w[d] = (float)g.w[d];
-        l32.rc2 = rcf * rcf; l32.sig2 = (float)sig2; l32.eps4 = (float)(4.0 * p->lj_eps);
-        l32.eps24 = (float)(24.0 * p->lj_eps); l32.eps48 = (float)(48.0 * p->lj_eps);
-        l32.ushift = (float)ushift;
-    }
-    NA_CU(launch_lj(prec, l64, l32, st));
-
-    // ATM triplets, staged-molecule capacity = the largest unit of the traversal
-    const int mcap = hocc[1 + trav] > 0 ? hocc[1 + trav] : 1;
-    if (mcap > 2047) return ATM_E_CAPACITY;
-    const int nwarps = trav == ATM_3C01 ? 4 : 8;
-    const int gcap = (int)std::min<long long>((long long)mcap * (mcap - 1) / 2, 32ll * mcap);
-    int optin = 0;
-    NA_CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
-    int use_d = 1;
-    auto plan_bytes = [&](int ud) -> size_t {
-        if (trav == ATM_3C01)
-            return prec == ATM_FP64 ? owner_smem_plan<double>(mcap, nwarps).total
-                                    : owner_smem_plan<float>(mcap, nwarps).total;
-        return prec == ATM_FP64 ? block_smem_plan<double>(trunc, mcap, nwarps, gcap, ud).total
-                                : block_smem_plan<float>(trunc, mcap, nwarps, gcap, ud).total;
-    };
-    size_t smem = plan_bytes(use_d);
-    if (smem > (size_t)optin && trav != ATM_3C01 && trunc == ATM_TRUNC_PRODUCT) {
-        use_d = 0;
-        smem = plan_bytes(use_d);
-    }
-    if (smem > (size_t)optin) return ATM_E_CAPACITY;
-    NA_CU(prec == ATM_FP64 ? atm_attr_fp64(trav, trunc, smem) : atm_attr_fp32(trav, trunc, smem));
-    if (trav != ATM_3C01 && bytes3) NA_CU(cudaMemsetAsync(f_atm, 0, bytes3, st));
-    const double rc2d = rc * rc, rc6d = rc2d * rc2d * rc2d;
-    const double wmax = std::max(g.w[0], std::max(g.w[1], g.w[2]));
-    if (prec == ATM_FP64) {
-        AtmArgs<double> a{};
-        a.g = g; a.n = n; a.xl = xl; a.xl32 = xl32; a.cell_start = start; a.fs = f_atm;
-        a.unit_ew = unit_ew; a.unit_cnt = unit_cnt; a.status = status;
-        for (int d = 0; d < 3; d++) {
-            a.w[d] = g.w[d];
-            a.wf[d] = (float)g.w[d];
-        }
-        a.rc2 = rc2d;
-        a.rc6 = rc6d;
-        a.nu = p->nu;
-        a.p_lo = (float)(rc2d * (1.0 - 1.0 / 4096.0));
-        a.p_hi = (float)(rc2d * (1.0 + 1.0 / 4096.0));
-        a.q_lo = (float)(rc6d * (1.0 - 1.0 / 1024.0));
-        a.q_hi = (float)(rc6d * (1.0 + 1.0 / 1024.0));
-        a.dmin = (float)((0.02 * wmax) * (0.02 * wmax));
-        a.mcap = mcap;
-        a.gcap = gcap;
-        a.use_d = use_d;
-        NA_CU(launch_atm_fp64(trav, trunc, a, nwarps, smem, st));
-    } else {
-        AtmArgs<float> a{};
-        float rcf = (float)rc;
-        a.g = g; a.n = n; a.xl = xl32; a.xl32 = xl32; a.cell_start = start; a.fs = f_atm;
-        a.unit_ew = unit_ew; a.unit_cnt = unit_cnt; a.status = status;
-        for (int d = 0; d < 3; d++) {
-            a.w[d] = (float)g.w[d];
-            a.wf[d] = (float)g.w[d];
-        }
-        a.rc2 = rcf * rcf;
-        a.rc6 = a.rc2 * a.rc2 * a.rc2;
-        a.nu = (float)p->nu;
-        a.mcap = mcap;
-        a.gcap = gcap;
-        a.use_d = use_d;
-        NA_CU(launch_atm_fp32(trav, trunc, a, nwarps, smem, st));
-    }
+    // LJ pairs and ATM triplets (staged-molecule capacity = largest unit of the traversal)
+    ForceJob j;
+    j.g = g;
+    j.n = n;
+    j.xl = xl;
+    j.xl32 = xl32;
+    j.start = start;
+    j.cell_sorted = cell_sorted;
+    j.f_lj = f_lj;
+    j.f_atm = f_atm;
+    j.lj_ew = lj_ew;
+    j.lj_cnt = lj_cnt;
+    j.unit_ew = unit_ew;
+    j.unit_cnt = unit_cnt;
+    j.status = status;
+    j.rc = p->rc;
+    j.nu = p->nu;
+    j.lj_eps = p->lj_eps;
+    j.lj_sigma = p->lj_sigma;
+    j.lj_shift = p->lj_shift;
+    j.trav = trav;
+    j.trunc = trunc;
+    j.prec = prec;
+    j.mcap = hocc[1 + trav] > 0 ? hocc[1 + trav] : 1;
+    NA_CU(cudaDeviceGetAttribute(&j.optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
+    j.st = st;
+    NA_CU(enqueue_lj(j));
+    bool capacity = false;
+    cudaError_t e = enqueue_atm(j, nullptr, &capacity);
+    if (capacity) return ATM_E_CAPACITY;
+    NA_CU(e);
 
     // scalars, then the total force in the caller's order
     ReduceArgs r;

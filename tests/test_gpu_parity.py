@@ -237,3 +237,33 @@ def test_full_size_256k_sampled(atm3, trav, prec):
     net = np.abs(f.sum(axis=1)).max()
     assert net < (1e-9 if prec == "fp64" else 1e-3) * np.abs(f).max() * 10
     assert r["n_int3"] > 0.5e7
+
+
+# ------------------------------------------------------------------ capacity fallbacks
+
+@pytest.mark.parametrize("trav", ["3c18", "3c08"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_large_units_product_rule(atm3, trav, prec):
+    """Units too large for the dense pair tables (N = 1500 in a 4-cell box,
+    ~23 molecules per cell) take the per-molecule accumulator path."""
+    cfg = synth.homogeneous(1500, 0.8, 1.0, seed=1001)
+    prm = oracle.params(cfg["box"], 2.5, NU)
+    ref = oracle.atm_cells(prm, cfg["x"], trav, "product", ORC_PREC[prec])
+    r, f, _, _ = run_gpu(atm3, cfg, trav, "product", prec)
+    assert r["n_cand3"] == ref["n_cand3"] and r["n_int3"] == ref["n_int3"]
+    assert r["e3"] == pytest.approx(ref["e3"], rel=RTOL[prec])
+    assert_forces_close(f, ref["f"], RTOL[prec], "large units " + trav + prec)
+
+
+@pytest.mark.parametrize("trav", ["3c18", "3c08"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_dense_liquid_edge_table_overflow(atm3, trav, prec):
+    """At rho* = 1.4 units have more pair-rule edges than the per-unit edge table
+    holds and fall back to per-molecule accumulators; results are unchanged."""
+    cfg = synth.homogeneous(2000, 1.4, 1.0, seed=77, jitter=0.02)
+    prm = oracle.params(cfg["box"], 2.5, NU)
+    ref = oracle.atm_cells(prm, cfg["x"], trav, "pair", ORC_PREC[prec])
+    r, f, _, _ = run_gpu(atm3, cfg, trav, "pair", prec)
+    assert r["n_cand3"] == ref["n_cand3"] and r["n_int3"] == ref["n_int3"]
+    assert r["e3"] == pytest.approx(ref["e3"], rel=RTOL[prec])
+    assert_forces_close(f, ref["f"], RTOL[prec], "dense " + trav + prec)
