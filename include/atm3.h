@@ -156,6 +156,62 @@ atm_status atm_get_state(atm_ctx* ctx, double* x, double* v);
 atm_status atm_step(atm_ctx* ctx, int nsteps, atm_traversal trav, atm_truncation trunc,
                     atm_precision prec, atm_result* last);
 
+/* ---- Batches of independent replicas ------------------------------------
+ * A context may hold nrep independent periodic systems ("replicas", e.g. an
+ * ensemble of uneven N, density and temperature).  Every kernel of a force
+ * evaluation or of a step covers all replicas in one launch (cells of all
+ * replicas are numbered back to back, every CTA looks its replica up).
+ * State arrays are the replicas' SoA arrays back to back: replica r occupies
+ * molecules [sum_{s<r} n[s], sum_{s<=r} n[s]) of every coordinate row, so
+ * x[d * ntot + i] is coordinate d of molecule i.  atm_create(p, n) is the
+ * batch of one.  Per-replica parameters (box, rc, nu, LJ, dt) may differ;
+ * device and cuda_stream are taken from params[0].
+ * Errors: as atm_create. */
+atm_status atm_batch_create(const atm_params* params, const int64_t* n, int nrep, atm_ctx** out);
+/* Number of replicas and total molecules. */
+atm_status atm_batch_size(const atm_ctx* ctx, int* nrep, int64_t* ntot);
+/* Scalars of the last evaluation for every replica: out[nrep] (synchronises).
+ * (atm_compute_forces / atm_step return replica 0's.) */
+atm_status atm_get_results(atm_ctx* ctx, atm_result* out);
+
+/* Launch options.  persistent = 1: the ATM kernel runs as a persistent grid
+ * (resident CTAs x SMs) whose CTAs take traversal units from a global counter
+ * instead of one CTA per unit.  nwarps = 4 or 8 warps per 3C18/3C08 CTA (0 =
+ * default).  graph = 1: atm_step captures one step in a CUDA graph (on a
+ * stream of its own) and replays it, with no host synchronisation between
+ * steps; the graph sizes the kernels for the current largest unit plus
+ * headroom, and a step that outgrows it is detected on the device, after
+ * which the run is restarted from its initial state without the graph.
+ * Options reset any autotuned choice.  Errors: INVALID. */
+atm_status atm_set_options(atm_ctx* ctx, int persistent, int nwarps, int graph);
+
+typedef struct {
+    int persistent;     /* chosen launch form */
+    int nwarps;         /* chosen warps per CTA */
+    double ms_per_eval; /* device time of one LJ + ATM evaluation with it */
+} atm_tuning;
+
+/* Autotuner: times `reps` force evaluations on the current cells for every
+ * launch form (one CTA per unit or persistent; 4 or 8 warps for 3C18/3C08)
+ * and keeps the fastest for this (trav, trunc, prec); later evaluations and
+ * steps use it.  Cells must be built.  out may be NULL.
+ * Errors: INVALID, STATE, CAPACITY, CUDA. */
+atm_status atm_autotune(atm_ctx* ctx, atm_traversal trav, atm_truncation trunc,
+                        atm_precision prec, int reps, atm_tuning* out);
+
+/* ---- Density profile (section 5, vapour-liquid slab) ---------------------
+ * Adds, for every replica, the histogram of coordinate `axis` of the current
+ * wrapped positions over nbins equal bins of [0, L_axis) (bin = floor(x / h),
+ * h = L_axis / nbins, clamped to [0, nbins)) to a device accumulator.  Cells
+ * must be built (the build wraps positions).  1 <= nbins <= 4096; the axis and
+ * bin count must stay the same until atm_density_reset.
+ * Errors: INVALID, STATE, CUDA. */
+atm_status atm_density_accumulate(atm_ctx* ctx, int axis, int nbins);
+/* counts[nrep * nbins] (replica-major) and the number of accumulated samples;
+ * either may be NULL (synchronises). */
+atm_status atm_density_get(atm_ctx* ctx, uint64_t* counts, int64_t* samples);
+atm_status atm_density_reset(atm_ctx* ctx);
+
 /* Allocation-free force evaluation.  The paper has no counterpart: this entry
  * point exists for callers that cannot call cudaMalloc -- code that runs inside
  * a host application which owns and budgets all device memory up front, a

@@ -23,9 +23,11 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "box smaller than three cells", 3: 
           4: "device wait timed out", 5: "non-finite input", 6: "call out of order",
           7: "capacity exceeded"}
 
-EXPORTED = ["atm_abi_version", "atm_create", "atm_destroy", "atm_last_error", "atm_set_state",
-            "atm_set_state_dev", "atm_build_cells", "atm_get_cells", "atm_compute_forces",
-            "atm_get_forces", "atm_get_forces_dev", "atm_get_state", "atm_step",
+EXPORTED = ["atm_abi_version", "atm_create", "atm_batch_create", "atm_batch_size", "atm_destroy",
+            "atm_last_error", "atm_set_state", "atm_set_state_dev", "atm_build_cells",
+            "atm_get_cells", "atm_compute_forces", "atm_get_results", "atm_get_forces",
+            "atm_get_forces_dev", "atm_get_state", "atm_step", "atm_set_options", "atm_autotune",
+            "atm_density_accumulate", "atm_density_get", "atm_density_reset",
             "atm_set_profiling", "atm_get_profile", "atm_compute_forces_noalloc"]
 
 
@@ -55,6 +57,14 @@ class Profile(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("persistent", ctypes.c_int), ("nwarps", ctypes.c_int),
+                ("ms_per_eval", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class AtmError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__("%s (%d): %s" % (STATUS.get(status, "?"), status, msg))
@@ -74,39 +84,38 @@ def load():
                            % LIB_PATH)
     L = ctypes.CDLL(LIB_PATH)
     P, i32, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
-    L.atm_abi_version.restype = i32
-    L.atm_abi_version.argtypes = []
-    L.atm_create.restype = i32
-    L.atm_create.argtypes = [ctypes.POINTER(Params), i64, ctypes.POINTER(P)]
-    L.atm_destroy.restype = i32
-    L.atm_destroy.argtypes = [P]
+    sig = {
+        "atm_abi_version": [],
+        "atm_create": [ctypes.POINTER(Params), i64, ctypes.POINTER(P)],
+        "atm_batch_create": [ctypes.POINTER(Params), P, i32, ctypes.POINTER(P)],
+        "atm_batch_size": [P, P, P],
+        "atm_destroy": [P],
+        "atm_set_state": [P, P, P],
+        "atm_set_state_dev": [P, P, P],
+        "atm_build_cells": [P],
+        "atm_get_cells": [P, P, P, P, P],
+        "atm_compute_forces": [P, i32, i32, i32, ctypes.POINTER(Result)],
+        "atm_get_results": [P, ctypes.POINTER(Result)],
+        "atm_get_forces": [P, P, i32],
+        "atm_get_forces_dev": [P, P, i32],
+        "atm_get_state": [P, P, P],
+        "atm_step": [P, i32, i32, i32, i32, ctypes.POINTER(Result)],
+        "atm_set_options": [P, i32, i32, i32],
+        "atm_autotune": [P, i32, i32, i32, i32, ctypes.POINTER(Tuning)],
+        "atm_density_accumulate": [P, i32, i32],
+        "atm_density_get": [P, P, P],
+        "atm_density_reset": [P],
+        "atm_set_profiling": [P, i32],
+        "atm_get_profile": [P, ctypes.POINTER(Profile)],
+        "atm_compute_forces_noalloc": [ctypes.POINTER(Params), i64, P, i32, i32, i32, P,
+                                       ctypes.POINTER(Result)],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.restype = i32
+        fn.argtypes = args
     L.atm_last_error.restype = ctypes.c_char_p
     L.atm_last_error.argtypes = [P]
-    L.atm_set_state.restype = i32
-    L.atm_set_state.argtypes = [P, P, P]
-    L.atm_set_state_dev.restype = i32
-    L.atm_set_state_dev.argtypes = [P, P, P]
-    L.atm_build_cells.restype = i32
-    L.atm_build_cells.argtypes = [P]
-    L.atm_get_cells.restype = i32
-    L.atm_get_cells.argtypes = [P, P, P, P, P]
-    L.atm_compute_forces.restype = i32
-    L.atm_compute_forces.argtypes = [P, i32, i32, i32, ctypes.POINTER(Result)]
-    L.atm_get_forces.restype = i32
-    L.atm_get_forces.argtypes = [P, P, i32]
-    L.atm_get_forces_dev.restype = i32
-    L.atm_get_forces_dev.argtypes = [P, P, i32]
-    L.atm_get_state.restype = i32
-    L.atm_get_state.argtypes = [P, P, P]
-    L.atm_step.restype = i32
-    L.atm_step.argtypes = [P, i32, i32, i32, i32, ctypes.POINTER(Result)]
-    L.atm_compute_forces_noalloc.restype = i32
-    L.atm_compute_forces_noalloc.argtypes = [ctypes.POINTER(Params), i64, P, i32, i32, i32, P,
-                                             ctypes.POINTER(Result)]
-    L.atm_set_profiling.restype = i32
-    L.atm_set_profiling.argtypes = [P, i32]
-    L.atm_get_profile.restype = i32
-    L.atm_get_profile.argtypes = [P, ctypes.POINTER(Profile)]
     _lib = L
     return L
 
@@ -119,27 +128,68 @@ def _is_device(a):
     return hasattr(a, "data_ptr") and getattr(a, "is_cuda", False)
 
 
+def make_params(box, rc=2.5, nu=0.073, lj_eps=1.0, lj_sigma=1.0, dt=0.002, lj_shift=False,
+                device=0, stream=None):
+    box = np.broadcast_to(np.asarray(box, dtype=np.float64), (3,))
+    p = Params()
+    for d in range(3):
+        p.box[d] = float(box[d])
+    p.rc, p.nu, p.lj_eps, p.lj_sigma, p.dt = rc, nu, lj_eps, lj_sigma, dt
+    p.lj_shift = 1 if lj_shift else 0
+    p.device = int(device)
+    p.cuda_stream = stream
+    return p
+
+
+def cell_count(box, rc):
+    """Cells of one replica: n_d = largest k with L_d / k >= r_c."""
+    total = 1
+    for L in np.broadcast_to(np.asarray(box, dtype=np.float64), (3,)):
+        k = max(1, int(np.floor(L / rc)))
+        while L / (k + 1) >= rc:
+            k += 1
+        while k > 0 and L / k < rc:
+            k -= 1
+        total *= k
+    return total
+
+
 class AtmSystem:
-    """One periodic LJ+ATM system on one GPU (wraps an ``atm_ctx``)."""
+    """One periodic LJ+ATM system, or a batch of independent replicas, on one
+    GPU (wraps an ``atm_ctx``).  For a batch, ``n`` is a list, ``box`` a list
+    of boxes and the other per-replica keyword arguments may be lists; state
+    arrays are the replicas' SoA arrays back to back (shape ``[3, sum(n)]``)."""
 
     def __init__(self, box, n, rc=2.5, nu=0.073, lj_eps=1.0, lj_sigma=1.0, dt=0.002,
                  lj_shift=False, device=0, stream=None):
         self._lib = load()
-        box = np.broadcast_to(np.asarray(box, dtype=np.float64), (3,))
-        self.n = int(n)
-        self.box = box.copy()
-        p = Params()
-        for d in range(3):
-            p.box[d] = float(box[d])
-        p.rc, p.nu, p.lj_eps, p.lj_sigma, p.dt = rc, nu, lj_eps, lj_sigma, dt
-        p.lj_shift = 1 if lj_shift else 0
-        p.device = int(device)
-        p.cuda_stream = stream
-        self.params = p
+        self._ctx = None
+        ns = [int(v) for v in np.atleast_1d(n)]
+        R = len(ns)
+        boxes = np.asarray(box, dtype=np.float64)
+        if boxes.ndim == 0:
+            boxes = np.full((R, 3), float(boxes))
+        elif boxes.ndim == 1:
+            boxes = np.broadcast_to(boxes, (R, 3))
+
+        def per(v, r):
+            return v[r] if isinstance(v, (list, tuple, np.ndarray)) else v
+
+        arr = (Params * R)()
+        for r in range(R):
+            arr[r] = make_params(boxes[r], per(rc, r), per(nu, r), per(lj_eps, r),
+                                 per(lj_sigma, r), per(dt, r), per(lj_shift, r), device, stream)
+        self.params = arr
+        self.replicas = R
+        self.ns = ns
+        self.n = int(sum(ns))
+        self.box = np.array(boxes[0])
+        self.ncells = [cell_count(boxes[r], arr[r].rc) for r in range(R)]
         ctx = ctypes.c_void_p()
-        st = self._lib.atm_create(ctypes.byref(p), self.n, ctypes.byref(ctx))
+        nn = np.asarray(ns, dtype=np.int64)
+        st = self._lib.atm_batch_create(arr, _host_ptr(nn), R, ctypes.byref(ctx))
         if st != 0:
-            raise AtmError(st, "atm_create failed")
+            raise AtmError(st, "atm_batch_create failed")
         self._ctx = ctx
 
     # -- helpers
@@ -183,9 +233,9 @@ class AtmSystem:
             vp = _host_ptr(v)
         self._check(self._lib.atm_set_state(self._ctx, _host_ptr(x), vp))
 
-    def get_state(self):
-        x = np.zeros((3, self.n))
-        v = np.zeros((3, self.n))
+    def get_state(self, x=None, v=None):
+        x = np.zeros((3, self.n)) if x is None else x
+        v = np.zeros((3, self.n)) if v is None else v
         self._check(self._lib.atm_get_state(self._ctx, _host_ptr(x), _host_ptr(v)))
         return x, v
 
@@ -194,11 +244,10 @@ class AtmSystem:
         self._check(self._lib.atm_build_cells(self._ctx))
 
     def get_cells(self):
+        """Cell arrays (for a batch in the global cell numbering; ncell is replica 0's grid)."""
         nc = np.zeros(3, dtype=np.int32)
-        self._check(self._lib.atm_get_cells(self._ctx, None, None, None, _host_ptr(nc)))
-        ncell = int(np.prod(nc.astype(np.int64)))
         cell_of = np.zeros(self.n, dtype=np.int32)
-        start = np.zeros(ncell + 1, dtype=np.int32)
+        start = np.zeros(sum(self.ncells) + 1, dtype=np.int32)
         perm = np.zeros(self.n, dtype=np.int32)
         self._check(self._lib.atm_get_cells(self._ctx, _host_ptr(cell_of), _host_ptr(start),
                                             _host_ptr(perm), _host_ptr(nc)))
@@ -211,6 +260,12 @@ class AtmSystem:
             self._ctx, TRAVERSALS[trav], TRUNCATIONS[trunc], PRECISIONS[prec],
             ctypes.byref(r) if sync else None))
         return r.as_dict() if sync else None
+
+    def results(self):
+        """Scalars of the last evaluation, one dict per replica."""
+        out = (Result * self.replicas)()
+        self._check(self._lib.atm_get_results(self._ctx, out))
+        return [out[r].as_dict() for r in range(self.replicas)]
 
     def get_forces(self, which="total", out=None):
         if out is not None and _is_device(out):
@@ -227,6 +282,30 @@ class AtmSystem:
                                        TRUNCATIONS[trunc], PRECISIONS[prec],
                                        ctypes.byref(r) if sync else None))
         return r.as_dict() if sync else None
+
+    # -- launch options, autotuning
+    def set_options(self, persistent=False, nwarps=0, graph=False):
+        self._check(self._lib.atm_set_options(self._ctx, int(bool(persistent)), int(nwarps),
+                                              int(bool(graph))))
+
+    def autotune(self, trav="3c08", trunc="pair", prec="fp32c", reps=3):
+        t = Tuning()
+        self._check(self._lib.atm_autotune(self._ctx, TRAVERSALS[trav], TRUNCATIONS[trunc],
+                                           PRECISIONS[prec], int(reps), ctypes.byref(t)))
+        return t.as_dict()
+
+    # -- density profile
+    def density_accumulate(self, axis=2, nbins=600):
+        self._check(self._lib.atm_density_accumulate(self._ctx, int(axis), int(nbins)))
+
+    def density_get(self, nbins):
+        counts = np.zeros((self.replicas, nbins), dtype=np.uint64)
+        samples = np.zeros(1, dtype=np.int64)
+        self._check(self._lib.atm_density_get(self._ctx, _host_ptr(counts), _host_ptr(samples)))
+        return counts, int(samples[0])
+
+    def density_reset(self):
+        self._check(self._lib.atm_density_reset(self._ctx))
 
     # -- profiling (device time of the library's kernels, launch counts)
     def set_profiling(self, on=True):
@@ -246,17 +325,10 @@ def compute_forces_noalloc(box, x_dev, f_dev, trav="3c18", trunc="pair", prec="f
     ``x_dev`` and ``f_dev`` are caller-owned [3, n] float64 CUDA tensors.
     Returns the scalars of the evaluation."""
     L = load()
-    box = np.broadcast_to(np.asarray(box, dtype=np.float64), (3,))
     n = int(x_dev.shape[1])
     assert tuple(x_dev.shape) == (3, n) and tuple(f_dev.shape) == (3, n)
     assert x_dev.is_contiguous() and f_dev.is_contiguous()
-    p = Params()
-    for d in range(3):
-        p.box[d] = float(box[d])
-    p.rc, p.nu, p.lj_eps, p.lj_sigma, p.dt = rc, nu, lj_eps, lj_sigma, 0.0
-    p.lj_shift = 1 if lj_shift else 0
-    p.device = int(device)
-    p.cuda_stream = stream
+    p = make_params(box, rc, nu, lj_eps, lj_sigma, 0.0, lj_shift, device, stream)
     r = Result()
     st = L.atm_compute_forces_noalloc(ctypes.byref(p), n, x_dev.data_ptr(), TRAVERSALS[trav],
                                       TRUNCATIONS[trunc], PRECISIONS[prec], f_dev.data_ptr(),

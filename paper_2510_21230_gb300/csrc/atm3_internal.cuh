@@ -19,6 +19,30 @@ struct Grid {
     long long ncell;
 };
 
+// One replica (an independent periodic system) of a batch.  Its molecules
+// are [mol0, mol0 + n) in both the original and the sorted order, its cells
+// [cell0, cell0 + g.ncell) in the global cell numbering, so every per-molecule
+// and per-cell array of the batch is the replicas' arrays back to back.
+// A single system is a batch of one replica.
+struct Rep {
+    Grid g;
+    long long mol0, n, cell0;
+    double rc2, rc6, nu, dt;
+    double sig2, eps4, eps24, eps48, ushift;  // LJ
+    float rc2f, rc6f, nuf, sig2f, eps4f, eps24f, eps48f, ushiftf;
+    float wf[3];
+    float p_lo, p_hi;          // FP64 prefilter band of a squared distance
+    float q_lo, q_hi, dmin;    // FP64 prefilter band of a sorted product
+};
+
+struct Batch {
+    const Rep* rep;          // [R]
+    const int* rep_of_cell;  // [ncell] replica of each global cell
+    const int* rep_of_mol;   // [ntot] replica of each molecule (either order)
+    int R;
+    long long ntot, ncell;
+};
+
 // cell coordinates of a cell id (z-major lexicographic)
 __host__ __device__ __forceinline__ void cell_coords(const Grid& g, long long id, int& cx, int& cy,
                                                      int& cz)
@@ -86,20 +110,16 @@ struct Trav<2> {
 // Arguments of the ATM unit kernels.
 template <typename R>
 struct AtmArgs {
-    Grid g;
-    long long n;
+    Batch b;                  // replicas (geometry, cutoffs, prefilter bands)
+    long long n;              // SoA stride = b.ntot
     const R* xl;              // sorted cell-local coordinates, SoA [3n], working precision
     const float* xl32;        // the same in FP32 (prefilter of the FP64 path)
-    const int* cell_start;    // [ncell + 1]
+    const int* cell_start;    // [ncell + 1], global sorted indices
     double* fs;               // sorted-order ATM force accumulator, SoA [3n]
     double* unit_ew;          // [2 * ncell]: E3, W3 per unit
     unsigned long long* unit_cnt;  // [2 * ncell]: candidates, interacting
     int* status;
-    R w[3];                   // cell edges in the working precision
-    float wf[3];              // cell edges in FP32
-    R rc2, rc6, nu;
-    float p_lo, p_hi;         // FP64 prefilter band of a squared distance (pair rule)
-    float q_lo, q_hi, dmin;   // FP64 prefilter band of a sorted product (product rule)
+    int* work;                // persistent launch: unit counter (nullptr: one CTA per unit)
     int mcap;                 // staged-molecule capacity of one unit
     int gcap;                 // edge-accumulator capacity (block kernel)
     int use_d;                // block kernel, product rule: dense FP32 distance table in smem
@@ -194,9 +214,10 @@ struct AtmPlan {
     size_t smem;
 };
 
-inline bool atm_choose_plan(int trav, int trunc, int prec, int mcap, int optin, AtmPlan& P)
+inline bool atm_choose_plan_nw(int trav, int trunc, int prec, int mcap, int optin, int nwarps,
+                               AtmPlan& P)
 {
-    P.nwarps = (trav == 0 || (trunc == 0 && prec == 1)) ? 4 : 8;
+    P.nwarps = nwarps;
     P.gcap = 0;
     P.use_d = 0;
     P.acc_mode = 0;
@@ -233,14 +254,22 @@ inline bool atm_choose_plan(int trav, int trunc, int prec, int mcap, int optin, 
     return false;
 }
 
+inline bool atm_choose_plan(int trav, int trunc, int prec, int mcap, int optin, AtmPlan& P)
+{
+    return atm_choose_plan_nw(trav, trunc, prec, mcap, optin,
+                              (trav == 0 || (trunc == 0 && prec == 1)) ? 4 : 8, P);
+}
+
 }  // namespace atm3
 
 // kernel launchers (defined in atm_fp64.cu / atm_fp32.cu)
 namespace atm3 {
 cudaError_t launch_atm_fp64(int trav, int trunc, const AtmArgs<double>& a, int nwarps,
-                            size_t smem, cudaStream_t s);
+                            size_t smem, int ctas, cudaStream_t s);
 cudaError_t launch_atm_fp32(int trav, int trunc, const AtmArgs<float>& a, int nwarps,
-                            size_t smem, cudaStream_t s);
+                            size_t smem, int ctas, cudaStream_t s);
 cudaError_t atm_attr_fp64(int trav, int trunc, size_t smem);
 cudaError_t atm_attr_fp32(int trav, int trunc, size_t smem);
+int atm_occupancy_fp64(int trav, int trunc, int nwarps, size_t smem);
+int atm_occupancy_fp32(int trav, int trunc, int nwarps, size_t smem);
 }  // namespace atm3

@@ -101,7 +101,7 @@ __device__ __forceinline__ R seg_sum(R v, int key, int lane)
 }
 
 template <int TRAV, int TRUNC, typename R>
-__global__ void __launch_bounds__(256) atm_block_kernel(const AtmArgs<R> A)
+__device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long long u)
 {
     constexpr int S = Trav<TRAV>::S;
     constexpr bool F64 = sizeof(R) == 8;
@@ -117,9 +117,11 @@ __global__ void __launch_bounds__(256) atm_block_kernel(const AtmArgs<R> A)
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nwarps = blockDim.x >> 5;
-    const long long u = blockIdx.x;
     const int mcap = A.mcap;
     const BlockSmem plan = block_smem_plan<R>(TRUNC, mcap, nwarps, A.gcap, A.use_d, A.acc_mode);
+    // the replica this unit belongs to and the unit's index inside it
+    const Rep& rp = A.b.rep[A.b.rep_of_cell[u]];
+    const long long lu = u - rp.cell0;
     const int W = plan.W;
     R* px = reinterpret_cast<R*>(smem + plan.off_pos);
     R* py = px + mcap;
@@ -149,7 +151,7 @@ __global__ void __launch_bounds__(256) atm_block_kernel(const AtmArgs<R> A)
     unsigned long long* queue =
         reinterpret_cast<unsigned long long*>(smem + plan.off_queue) + warp * 64;
 
-    if (warp == 0) unit_slots<TRAV, S>(A.g, A.cell_start, u, s_beg, s_cell0, s_off);
+    if (warp == 0) unit_slots<TRAV, S>(rp.g, A.cell_start + rp.cell0, lu, s_beg, s_cell0, s_off);
     if (tid == 0) s_next = 0;
     __syncthreads();
     const int M = s_beg[S];
@@ -166,9 +168,11 @@ __global__ void __launch_bounds__(256) atm_block_kernel(const AtmArgs<R> A)
     }
     const int Wm = (M + 31) >> 5;
     const long long n = A.n;
-    const R w0 = A.w[0], w1 = A.w[1], w2 = A.w[2];
-    const float wf0 = A.wf[0], wf1 = A.wf[1], wf2 = A.wf[2];
-    const R rc2 = A.rc2, rc6 = A.rc6, nu = A.nu;
+    const R w0 = (R)rp.g.w[0], w1 = (R)rp.g.w[1], w2 = (R)rp.g.w[2];
+    const float wf0 = rp.wf[0], wf1 = rp.wf[1], wf2 = rp.wf[2];
+    const R rc2 = F64 ? (R)rp.rc2 : (R)rp.rc2f;
+    const R rc6 = F64 ? (R)rp.rc6 : (R)rp.rc6f;
+    const R nu = F64 ? (R)rp.nu : (R)rp.nuf;
     const unsigned lt_mask = (1u << lane) - 1u;
 
     // ---- stage the unit: positions and exact shifts o * w
@@ -226,8 +230,8 @@ __global__ void __launch_bounds__(256) atm_block_kernel(const AtmArgs<R> A)
         R dx, dy, dz;
         if (!F64) return disp(p, q, dx, dy, dz) < rc2;
         float f2 = disp32(p, q);
-        if (f2 < A.p_lo) return true;
-        if (f2 > A.p_hi) return false;
+        if (f2 < rp.p_lo) return true;
+        if (f2 > rp.p_hi) return false;
         return disp(p, q, dx, dy, dz) < rc2;
     };
     // rank of y among the set bits of row x = edge number of (x, y) within row x
@@ -555,9 +559,9 @@ __global__ void __launch_bounds__(256) atm_block_kernel(const AtmArgs<R> A)
                             keep = pr < (float)rc6;
                         } else {
                             float lo = fminf(a32, fminf(b32, c32));
-                            if (lo >= A.dmin && pr < A.q_lo) {
+                            if (lo >= rp.dmin && pr < rp.q_lo) {
                                 keep = true;
-                            } else if (lo >= A.dmin && pr > A.q_hi) {
+                            } else if (lo >= rp.dmin && pr > rp.q_hi) {
                                 keep = false;
                             } else {
                                 R dx, dy, dz;
@@ -651,6 +655,26 @@ __global__ void __launch_bounds__(256) atm_block_kernel(const AtmArgs<R> A)
     if (tid == 0) cand = unit_candidates<TRAV, S>(s_beg);
     unit_reduce_store<8>(esum.get(), wsum.get(), (unsigned long long)nint, 1.0, cand, A.unit_ew,
                          A.unit_cnt, u, s_red, s_redn);
+}
+
+// One CTA per unit, or (A.work set) a persistent grid whose CTAs take units
+// from a global counter until all units of the batch are done.
+template <int TRAV, int TRUNC, typename R>
+__global__ void __launch_bounds__(256) atm_block_kernel(const AtmArgs<R> A)
+{
+    if (A.work == nullptr) {
+        atm_block_unit<TRAV, TRUNC, R>(A, blockIdx.x);
+        return;
+    }
+    __shared__ int s_u;
+    for (;;) {
+        __syncthreads();  // the previous unit is done with shared memory
+        if (threadIdx.x == 0) s_u = atomicAdd(A.work, 1);
+        __syncthreads();
+        const int u = s_u;
+        if (u >= A.b.ncell) break;
+        atm_block_unit<TRAV, TRUNC, R>(A, u);
+    }
 }
 
 }  // namespace atm3

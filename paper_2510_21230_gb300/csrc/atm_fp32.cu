@@ -5,11 +5,13 @@
 
 namespace atm3 {
 
+// ctas = 0: one CTA per unit; ctas > 0: a persistent grid of that many CTAs
+// taking units from the counter a.work (which must be zero at launch)
 cudaError_t launch_atm_fp32(int trav, int trunc, const AtmArgs<float>& a, int nwarps,
-                            size_t smem, cudaStream_t s)
+                            size_t smem, int ctas, cudaStream_t s)
 {
-    dim3 grid((unsigned)a.g.ncell), block(32 * nwarps);
-    if (a.g.ncell == 0) return cudaSuccess;
+    if (a.b.ncell == 0) return cudaSuccess;
+    dim3 grid(ctas > 0 ? (unsigned)ctas : (unsigned)a.b.ncell), block(32 * nwarps);
     if (trav == 0 && trunc == 0) atm_owner_kernel<0, float><<<grid, block, smem, s>>>(a);
     else if (trav == 0 && trunc == 1) atm_owner_kernel<1, float><<<grid, block, smem, s>>>(a);
     else if (trav == 1 && trunc == 0) atm_block_kernel<1, 0, float><<<grid, block, smem, s>>>(a);
@@ -30,6 +32,20 @@ cudaError_t atm_attr_fp32(int trav, int trunc, size_t smem)
     if (trav == 2 && trunc == 0) return cudaFuncSetAttribute(atm_block_kernel<2, 0, float>, A, (int)smem);
     if (trav == 2 && trunc == 1) return cudaFuncSetAttribute(atm_block_kernel<2, 1, float>, A, (int)smem);
     return cudaErrorInvalidValue;
+}
+
+// resident CTAs per SM of the kernel at this block size and shared memory
+int atm_occupancy_fp32(int trav, int trunc, int nwarps, size_t smem)
+{
+    int nb = 0;
+    const int bs = 32 * nwarps;
+    if (trav == 0 && trunc == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, atm_owner_kernel<0, float>, bs, smem);
+    else if (trav == 0 && trunc == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, atm_owner_kernel<1, float>, bs, smem);
+    else if (trav == 1 && trunc == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, atm_block_kernel<1, 0, float>, bs, smem);
+    else if (trav == 1 && trunc == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, atm_block_kernel<1, 1, float>, bs, smem);
+    else if (trav == 2 && trunc == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, atm_block_kernel<2, 0, float>, bs, smem);
+    else if (trav == 2 && trunc == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, atm_block_kernel<2, 1, float>, bs, smem);
+    return nb;
 }
 
 }  // namespace atm3

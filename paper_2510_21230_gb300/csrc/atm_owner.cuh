@@ -16,7 +16,7 @@
 namespace atm3 {
 
 template <int TRUNC, typename R>
-__global__ void __launch_bounds__(128) atm_owner_kernel(const AtmArgs<R> A)
+__device__ __forceinline__ void atm_owner_unit(const AtmArgs<R>& A, const long long u)
 {
     constexpr int TRAV = 0, S = 27;
     constexpr bool F64 = sizeof(R) == 8;
@@ -31,8 +31,10 @@ __global__ void __launch_bounds__(128) atm_owner_kernel(const AtmArgs<R> A)
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nwarps = blockDim.x >> 5;
-    const long long u = blockIdx.x;
     const int mcap = A.mcap;
+    // the replica this unit belongs to and the unit's index inside it
+    const Rep& rp = A.b.rep[A.b.rep_of_cell[u]];
+    const long long lu = u - rp.cell0;
     const OwnerSmem plan = owner_smem_plan<R>(mcap, nwarps);
     R* px = reinterpret_cast<R*>(smem + plan.off_pos);
     R* py = px + mcap;
@@ -49,7 +51,7 @@ __global__ void __launch_bounds__(128) atm_owner_kernel(const AtmArgs<R> A)
     float* pa32 = F64 ? reinterpret_cast<float*>(smem + plan.off_pa32) + warp * mcap : nullptr;
     unsigned* queue = reinterpret_cast<unsigned*>(smem + plan.off_queue) + warp * 64;
 
-    if (warp == 0) unit_slots<TRAV, S>(A.g, A.cell_start, u, s_beg, s_cell0, s_off);
+    if (warp == 0) unit_slots<TRAV, S>(rp.g, A.cell_start + rp.cell0, lu, s_beg, s_cell0, s_off);
     if (tid == 0) s_next = 0;
     __syncthreads();
     const int M = s_beg[S];
@@ -81,9 +83,11 @@ __global__ void __launch_bounds__(128) atm_owner_kernel(const AtmArgs<R> A)
     }
     __syncthreads();
 
-    const R w0 = A.w[0], w1 = A.w[1], w2 = A.w[2];
-    const float wf0 = A.wf[0], wf1 = A.wf[1], wf2 = A.wf[2];
-    const R rc2 = A.rc2, rc6 = A.rc6, nu = A.nu;
+    const R w0 = (R)rp.g.w[0], w1 = (R)rp.g.w[1], w2 = (R)rp.g.w[2];
+    const float wf0 = rp.wf[0], wf1 = rp.wf[1], wf2 = rp.wf[2];
+    const R rc2 = F64 ? (R)rp.rc2 : (R)rp.rc2f;
+    const R rc6 = F64 ? (R)rp.rc6 : (R)rp.rc6f;
+    const R nu = F64 ? (R)rp.nu : (R)rp.nuf;
     const unsigned lt_mask = (1u << lane) - 1u;
 
     auto offs = [&](int p, int q, int& mx, int& my, int& mz) {
@@ -105,8 +109,8 @@ __global__ void __launch_bounds__(128) atm_owner_kernel(const AtmArgs<R> A)
         float ex, ey, ez;
         float f2 = canon_disp<float>(fx32[p], fy32[p], fz32[p], fx32[q], fy32[q], fz32[q], mx, my,
                                      mz, wf0, wf1, wf2, ex, ey, ez);
-        if (f2 < A.p_lo) return true;
-        if (f2 > A.p_hi) return false;
+        if (f2 < rp.p_lo) return true;
+        if (f2 > rp.p_hi) return false;
         R d2 = canon_disp<R>(px[p], py[p], pz[p], px[q], py[q], pz[q], mx, my, mz, w0, w1, w2, dx,
                              dy, dz);
         return d2 < rc2;
@@ -198,9 +202,9 @@ __global__ void __launch_bounds__(128) atm_owner_kernel(const AtmArgs<R> A)
                                                       ez);
                         float pr = sorted_product<float>(a32, b32, c32);
                         float lo = fminf(a32, fminf(b32, c32));
-                        if (lo >= A.dmin && pr < A.q_lo) {
+                        if (lo >= rp.dmin && pr < rp.q_lo) {
                             keep = true;
-                        } else if (lo >= A.dmin && pr > A.q_hi) {
+                        } else if (lo >= rp.dmin && pr > rp.q_hi) {
                             keep = false;
                         } else {
                             R dx, dy, dz;
@@ -245,6 +249,26 @@ __global__ void __launch_bounds__(128) atm_owner_kernel(const AtmArgs<R> A)
     if (tid == 0) cand = unit_candidates<TRAV, S>(s_beg);
     unit_reduce_store<8>(esum.get(), wsum.get(), (unsigned long long)nint, 1.0 / 3.0, cand,
                          A.unit_ew, A.unit_cnt, u, s_red, s_redn);
+}
+
+// One CTA per base cell, or (A.work set) a persistent grid pulling units from
+// a global counter.
+template <int TRUNC, typename R>
+__global__ void __launch_bounds__(128) atm_owner_kernel(const AtmArgs<R> A)
+{
+    if (A.work == nullptr) {
+        atm_owner_unit<TRUNC, R>(A, blockIdx.x);
+        return;
+    }
+    __shared__ int s_u;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_u = atomicAdd(A.work, 1);
+        __syncthreads();
+        const int u = s_u;
+        if (u >= A.b.ncell) break;
+        atm_owner_unit<TRUNC, R>(A, u);
+    }
 }
 
 }  // namespace atm3

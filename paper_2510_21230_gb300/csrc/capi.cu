@@ -1,4 +1,5 @@
-// capi.cu -- the C ABI declared in include/atm3.h: context, buffers, call order.
+// capi.cu -- the C ABI declared in include/atm3.h: context (a batch of one or
+// more replicas), buffers, call order, CUDA-graph steps, autotuning.
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -15,15 +16,25 @@
 using namespace atm3;
 
 namespace {
+constexpr int DENS_MAX_BINS = 4096;
+constexpr int KERNELS_PER_STEP = 10;  // kick, 6 cell kernels, LJ, ATM, kick
 }  // namespace
 
 struct atm_ctx {
-    atm_params p;
-    long long n = 0;
+    int R = 1;
+    std::vector<atm_params> params;
+    std::vector<Rep> reps;  // host copy
+    long long n = 0, ncell = 0;
+    int device = 0;
     cudaStream_t st = nullptr;
-    Grid g;
-    double* x = nullptr;   // [3n] positions, original order (wrapped by build_cells)
+    Batch b{};
+    Rep* d_rep = nullptr;
+    int* d_rep_of_cell = nullptr;
+    int* d_rep_of_mol = nullptr;
+    double* x = nullptr;   // [3n] positions, original order (wrapped by the cell build)
     double* v = nullptr;   // [3n] velocities, original order
+    double* x0 = nullptr;  // [3n] snapshot at the start of a graph-mode run
+    double* v0 = nullptr;
     double* xl = nullptr;  // [3n] sorted cell-local FP64
     float* xl32 = nullptr; // [3n] sorted cell-local FP32
     int* cell_of = nullptr;
@@ -37,23 +48,33 @@ struct atm_ctx {
     double* f_out = nullptr;  // [3n] original-order scratch for atm_get_forces
     double* unit_ew = nullptr;
     unsigned long long* unit_cnt = nullptr;
-    double* lj_ew = nullptr;
-    unsigned long long* lj_cnt = nullptr;
-    long long n_lj_blocks = 0;
-    double* ke_part = nullptr;
-    long long n_ke_blocks = 0;
-    ResultDev* d_res = nullptr;
-    ResultDev* h_res = nullptr;
+    double* mol_ew = nullptr;
+    unsigned* mol_cnt = nullptr;
+    double* ke = nullptr;
+    ResultDev* d_res = nullptr;  // [R]
+    ResultDev* h_res = nullptr;  // [R] pinned
     int* d_status = nullptr;
     int* h_status = nullptr;
     int* d_maxocc = nullptr;
     int* h_maxocc = nullptr;
+    int* d_work = nullptr;
+    unsigned long long* d_dens = nullptr;  // [R * DENS_MAX_BINS]
+    int dens_axis = -1, dens_nbins = 0;
+    long long dens_samples = 0;
     int maxocc = 0;
     int unit_max[3] = {0, 0, 0};  // largest unit (staged molecules) of 3c01, 3c18, 3c08
     bool have_x = false, cells_built = false, forces_valid = false;
     int f_trav = -1, f_trunc = -1, f_prec = -1;
     size_t smem_set[2][3][2] = {};
-    int smem_optin = 0;
+    int smem_optin = 0, sms = 0;
+    // launch options: persistent ATM grid, warps per block-kernel CTA (0 =
+    // default), CUDA-graph steps; tuned choices per (prec, trav, trunc)
+    int opt_persistent = 0, opt_nwarps = 0, opt_graph = 0;
+    int tuned[2][3][2] = {};  // 0 = not tuned, else 1 + persistent + 2 * (nwarps == 8)
+    // graph of one step, valid for (trav, trunc, prec, mcap, launch choice)
+    cudaStream_t cap_st = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    int graph_key[5] = {-1, -1, -1, -1, -1};
     // profiling: event pairs around launch groups, summed per kind
     bool prof = false;
     struct EvRec {
@@ -129,16 +150,26 @@ static atm_status fail(atm_ctx* c, atm_status s, const char* fmt, ...)
             return fail(c, ATM_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_));        \
     } while (0)
 
+static void drop_graph(atm_ctx* c)
+{
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+    for (int& k : c->graph_key) k = -1;
+}
+
 static void free_all(atm_ctx* c)
 {
-    void* dev[] = {c->x, c->v, c->xl, c->xl32, c->cell_of, c->rank, c->count, c->start, c->perm,
-                   c->cell_sorted, c->f_lj, c->f_atm, c->f_out, c->unit_ew, c->unit_cnt,
-                   c->lj_ew, c->lj_cnt, c->ke_part, c->d_res, c->d_status, c->d_maxocc};
+    drop_graph(c);
+    void* dev[] = {c->d_rep, c->d_rep_of_cell, c->d_rep_of_mol, c->x, c->v, c->x0, c->v0, c->xl,
+                   c->xl32, c->cell_of, c->rank, c->count, c->start, c->perm, c->cell_sorted,
+                   c->f_lj, c->f_atm, c->f_out, c->unit_ew, c->unit_cnt, c->mol_ew, c->mol_cnt,
+                   c->ke, c->d_res, c->d_status, c->d_maxocc, c->d_work, c->d_dens};
     for (void* p : dev)
         if (p) cudaFree(p);
     if (c->h_res) cudaFreeHost(c->h_res);
     if (c->h_status) cudaFreeHost(c->h_status);
     if (c->h_maxocc) cudaFreeHost(c->h_maxocc);
+    if (c->cap_st) cudaStreamDestroy(c->cap_st);
     for (auto& r : c->ev_live) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -146,32 +177,6 @@ static void free_all(atm_ctx* c)
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     c->ev_live.clear();
     c->ev_pool.clear();
-}
-
-// n_d = largest k with L/k >= r_c (decided on the rounded quotient), w = L / n_d
-static atm_status make_grid(atm_ctx* c, const atm_params* p, Grid& g)
-{
-    long long ncell = 1;
-    for (int d = 0; d < 3; d++) {
-        double L = p->box[d], rc = p->rc;
-        if (!(L > 0.0) || !(rc > 0.0) || !std::isfinite(L) || !std::isfinite(rc))
-            return fail(c, ATM_E_INVALID, "box and rc must be positive and finite");
-        double k = std::floor(L / rc);
-        if (k < 1.0) k = 1.0;
-        while (L / (k + 1.0) >= rc) k += 1.0;
-        while (k > 0.0 && L / k < rc) k -= 1.0;
-        if (k < 3.0)
-            return fail(c, ATM_E_BOX_TOO_SMALL, "box edge %d (%.6g) holds fewer than 3 cells of rc %.6g",
-                        d, L, rc);
-        if (k > 1.0e6) return fail(c, ATM_E_INVALID, "too many cells along axis %d", d);
-        g.nc[d] = (int)k;
-        g.L[d] = L;
-        g.w[d] = L / k;
-        ncell *= (long long)k;
-    }
-    if (ncell > (1ll << 30)) return fail(c, ATM_E_INVALID, "too many cells (%lld)", ncell);
-    g.ncell = ncell;
-    return ATM_OK;
 }
 
 static atm_status check_status(atm_ctx* c)
@@ -201,35 +206,52 @@ extern "C" const char* atm_last_error(const atm_ctx* c)
     return c ? c->err : "null context";
 }
 
-extern "C" atm_status atm_create(const atm_params* params, int64_t n, atm_ctx** out)
+extern "C" atm_status atm_batch_create(const atm_params* params, const int64_t* n, int nrep,
+                                       atm_ctx** out)
 {
     if (!out) return ATM_E_INVALID;
     *out = nullptr;
-    if (!params || n < 0 || n > (int64_t)0x7fffffff - 1) return ATM_E_INVALID;
+    if (!params || !n || nrep < 1 || nrep > (1 << 20)) return ATM_E_INVALID;
     atm_ctx* c = new (std::nothrow) atm_ctx();
     if (!c) return ATM_E_INVALID;
-    c->p = *params;
-    c->n = n;
-    c->st = (cudaStream_t)params->cuda_stream;
-    if (!std::isfinite(params->nu) || !std::isfinite(params->lj_eps) ||
-        !(params->lj_sigma > 0.0) || !std::isfinite(params->dt)) {
-        delete c;
-        return ATM_E_INVALID;
+    c->R = nrep;
+    c->device = params[0].device;
+    c->st = (cudaStream_t)params[0].cuda_stream;
+    long long ntot = 0, ncell = 0;
+    for (int r = 0; r < nrep; r++) {
+        if (n[r] < 0 || ntot + n[r] > (long long)0x7fffffff - 1) {
+            delete c;
+            return ATM_E_INVALID;
+        }
+        Rep rp;
+        atm_status s = make_rep(params[r], n[r], ntot, ncell, rp);
+        if (s != ATM_OK) {
+            delete c;
+            return s;
+        }
+        c->params.push_back(params[r]);
+        c->reps.push_back(rp);
+        ntot += n[r];
+        ncell += rp.g.ncell;
+        if (ncell > (1ll << 30)) {
+            delete c;
+            return ATM_E_INVALID;
+        }
     }
-    atm_status s = make_grid(c, params, c->g);
-    if (s != ATM_OK) {
-        delete c;
-        return s;
-    }
+    c->n = ntot;
+    c->ncell = ncell;
     auto alloc = [&](void** ptr, size_t bytes) -> bool {
         return cudaMalloc(ptr, bytes > 0 ? bytes : 16) == cudaSuccess;
     };
-    bool ok = cudaSetDevice(params->device) == cudaSuccess;
-    size_t N = (size_t)(n > 0 ? n : 1), NC = (size_t)c->g.ncell;
-    c->n_lj_blocks = (long long)((N + LJ_BLOCK - 1) / LJ_BLOCK);
-    c->n_ke_blocks = (long long)((N + MD_BLOCK - 1) / MD_BLOCK);
+    bool ok = cudaSetDevice(c->device) == cudaSuccess;
+    const size_t N = (size_t)(ntot > 0 ? ntot : 1), NC = (size_t)ncell;
+    ok = ok && alloc((void**)&c->d_rep, nrep * sizeof(Rep));
+    ok = ok && alloc((void**)&c->d_rep_of_cell, NC * sizeof(int));
+    ok = ok && alloc((void**)&c->d_rep_of_mol, N * sizeof(int));
     ok = ok && alloc((void**)&c->x, 3 * N * sizeof(double));
     ok = ok && alloc((void**)&c->v, 3 * N * sizeof(double));
+    ok = ok && alloc((void**)&c->x0, 3 * N * sizeof(double));
+    ok = ok && alloc((void**)&c->v0, 3 * N * sizeof(double));
     ok = ok && alloc((void**)&c->xl, 3 * N * sizeof(double));
     ok = ok && alloc((void**)&c->xl32, 3 * N * sizeof(float));
     ok = ok && alloc((void**)&c->cell_of, N * sizeof(int));
@@ -243,19 +265,38 @@ extern "C" atm_status atm_create(const atm_params* params, int64_t n, atm_ctx** 
     ok = ok && alloc((void**)&c->f_out, 3 * N * sizeof(double));
     ok = ok && alloc((void**)&c->unit_ew, 2 * NC * sizeof(double));
     ok = ok && alloc((void**)&c->unit_cnt, 2 * NC * sizeof(unsigned long long));
-    ok = ok && alloc((void**)&c->lj_ew, 2 * (size_t)c->n_lj_blocks * sizeof(double));
-    ok = ok && alloc((void**)&c->lj_cnt, 2 * (size_t)c->n_lj_blocks * sizeof(unsigned long long));
-    ok = ok && alloc((void**)&c->ke_part, (size_t)c->n_ke_blocks * sizeof(double));
-    ok = ok && alloc((void**)&c->d_res, sizeof(ResultDev));
+    ok = ok && alloc((void**)&c->mol_ew, 2 * N * sizeof(double));
+    ok = ok && alloc((void**)&c->mol_cnt, 2 * N * sizeof(unsigned));
+    ok = ok && alloc((void**)&c->ke, N * sizeof(double));
+    ok = ok && alloc((void**)&c->d_res, nrep * sizeof(ResultDev));
     ok = ok && alloc((void**)&c->d_status, sizeof(int));
     ok = ok && alloc((void**)&c->d_maxocc, 4 * sizeof(int));
-    ok = ok && cudaMallocHost((void**)&c->h_res, sizeof(ResultDev)) == cudaSuccess;
+    ok = ok && alloc((void**)&c->d_work, sizeof(int));
+    ok = ok && alloc((void**)&c->d_dens, (size_t)nrep * DENS_MAX_BINS * sizeof(unsigned long long));
+    ok = ok && cudaMallocHost((void**)&c->h_res, nrep * sizeof(ResultDev)) == cudaSuccess;
     ok = ok && cudaMallocHost((void**)&c->h_status, sizeof(int)) == cudaSuccess;
     ok = ok && cudaMallocHost((void**)&c->h_maxocc, 4 * sizeof(int)) == cudaSuccess;
     ok = ok && cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin,
-                                      params->device) == cudaSuccess;
+                                      c->device) == cudaSuccess;
+    ok = ok && cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device) ==
+                   cudaSuccess;
+    ok = ok && cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking) == cudaSuccess;
+    if (ok) {
+        std::vector<int> roc(NC), rom(N, 0);
+        for (int r = 0; r < nrep; r++) {
+            for (long long q = 0; q < c->reps[r].g.ncell; q++) roc[c->reps[r].cell0 + q] = r;
+            for (long long q = 0; q < c->reps[r].n; q++) rom[c->reps[r].mol0 + q] = r;
+        }
+        ok = ok && cudaMemcpy(c->d_rep, c->reps.data(), nrep * sizeof(Rep),
+                              cudaMemcpyHostToDevice) == cudaSuccess;
+        ok = ok && cudaMemcpy(c->d_rep_of_cell, roc.data(), NC * sizeof(int),
+                              cudaMemcpyHostToDevice) == cudaSuccess;
+        ok = ok && cudaMemcpy(c->d_rep_of_mol, rom.data(), N * sizeof(int),
+                              cudaMemcpyHostToDevice) == cudaSuccess;
+    }
     ok = ok && cudaMemsetAsync(c->d_status, 0, sizeof(int), c->st) == cudaSuccess;
     ok = ok && cudaMemsetAsync(c->v, 0, 3 * N * sizeof(double), c->st) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(c->d_dens, 0, (size_t)nrep * DENS_MAX_BINS * 8, c->st) == cudaSuccess;
     ok = ok && cudaStreamSynchronize(c->st) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -263,19 +304,44 @@ extern "C" atm_status atm_create(const atm_params* params, int64_t n, atm_ctx** 
         delete c;
         return ATM_E_CUDA;
     }
+    c->b.rep = c->d_rep;
+    c->b.rep_of_cell = c->d_rep_of_cell;
+    c->b.rep_of_mol = c->d_rep_of_mol;
+    c->b.R = nrep;
+    c->b.ntot = ntot;
+    c->b.ncell = ncell;
     *c->h_status = 0;
     *out = c;
+    return ATM_OK;
+}
+
+extern "C" atm_status atm_create(const atm_params* params, int64_t n, atm_ctx** out)
+{
+    return atm_batch_create(params, &n, 1, out);
+}
+
+extern "C" atm_status atm_batch_size(const atm_ctx* c, int* nrep, int64_t* ntot)
+{
+    if (!c) return ATM_E_INVALID;
+    if (nrep) *nrep = c->R;
+    if (ntot) *ntot = c->n;
     return ATM_OK;
 }
 
 extern "C" atm_status atm_destroy(atm_ctx* c)
 {
     if (!c) return ATM_OK;
-    cudaSetDevice(c->p.device);
+    cudaSetDevice(c->device);
     cudaStreamSynchronize(c->st);
     free_all(c);
     delete c;
     return ATM_OK;
+}
+
+static void invalidate(atm_ctx* c)
+{
+    c->cells_built = false;
+    c->forces_valid = false;
 }
 
 extern "C" atm_status atm_set_state(atm_ctx* c, const double* x, const double* v)
@@ -285,7 +351,7 @@ extern "C" atm_status atm_set_state(atm_ctx* c, const double* x, const double* v
     for (long long q = 0; q < 3 * c->n; q++)
         if (!std::isfinite(x[q]) || (v && !std::isfinite(v[q])))
             return fail(c, ATM_E_NONFINITE, "non-finite input at element %lld", q);
-    CU(cudaSetDevice(c->p.device));
+    CU(cudaSetDevice(c->device));
     size_t bytes = 3 * (size_t)c->n * sizeof(double);
     if (bytes) {
         CU(cudaMemcpyAsync(c->x, x, bytes, cudaMemcpyHostToDevice, c->st));
@@ -295,8 +361,7 @@ extern "C" atm_status atm_set_state(atm_ctx* c, const double* x, const double* v
             CU(cudaMemsetAsync(c->v, 0, bytes, c->st));
     }
     c->have_x = true;
-    c->cells_built = false;
-    c->forces_valid = false;
+    invalidate(c);
     return ATM_OK;
 }
 
@@ -304,7 +369,7 @@ extern "C" atm_status atm_set_state_dev(atm_ctx* c, const double* x_dev, const d
 {
     if (!c) return ATM_E_INVALID;
     if (!x_dev && c->n > 0) return fail(c, ATM_E_INVALID, "positions are required");
-    CU(cudaSetDevice(c->p.device));
+    CU(cudaSetDevice(c->device));
     size_t bytes = 3 * (size_t)c->n * sizeof(double);
     if (bytes) {
         CU(cudaMemcpyAsync(c->x, x_dev, bytes, cudaMemcpyDeviceToDevice, c->st));
@@ -317,20 +382,28 @@ extern "C" atm_status atm_set_state_dev(atm_ctx* c, const double* x_dev, const d
         c->n_launch += 2;
     }
     c->have_x = true;
-    c->cells_built = false;
-    c->forces_valid = false;
+    invalidate(c);
     return ATM_OK;
 }
 
-static atm_status enqueue_cells(atm_ctx* c)
+// cell build kernels only (no host synchronisation; capturable)
+static atm_status launch_cells(atm_ctx* c)
 {
     cudaEvent_t ev = prof_begin(c);
-    CU(launch_build_cells(c->g, c->n, c->x, c->cell_of, c->rank, c->count, c->start, c->perm,
-                          c->xl, c->xl32, c->cell_sorted, c->d_maxocc, c->d_status, c->st));
+    CU(launch_build_cells(c->b, c->x, c->cell_of, c->rank, c->count, c->start, c->perm, c->xl,
+                          c->xl32, c->cell_sorted, c->d_maxocc, c->d_status, c->st));
     prof_end(c, PK_CELLS, ev);
-    c->n_launch += c->n > 0 ? 5 : 1;
+    c->n_launch += c->n > 0 ? 6 : 2;
+    return ATM_OK;
+}
+
+// cell build + read back of the occupancy maxima that size the force kernels
+static atm_status enqueue_cells(atm_ctx* c)
+{
+    atm_status s = launch_cells(c);
+    if (s != ATM_OK) return s;
     CU(cudaMemcpyAsync(c->h_maxocc, c->d_maxocc, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->st));
-    atm_status s = sync_and_check(c);
+    s = sync_and_check(c);
     if (s != ATM_OK) return s;
     c->maxocc = c->h_maxocc[0];
     for (int t = 0; t < 3; t++) c->unit_max[t] = c->h_maxocc[1 + t];
@@ -343,7 +416,7 @@ extern "C" atm_status atm_build_cells(atm_ctx* c)
 {
     if (!c) return ATM_E_INVALID;
     if (!c->have_x) return fail(c, ATM_E_STATE, "no state set");
-    CU(cudaSetDevice(c->p.device));
+    CU(cudaSetDevice(c->device));
     return enqueue_cells(c);
 }
 
@@ -352,13 +425,13 @@ extern "C" atm_status atm_get_cells(atm_ctx* c, int32_t* cell_of, int32_t* cell_
 {
     if (!c) return ATM_E_INVALID;
     if (ncell3)
-        for (int d = 0; d < 3; d++) ncell3[d] = c->g.nc[d];
+        for (int d = 0; d < 3; d++) ncell3[d] = c->reps[0].g.nc[d];
     if (!c->cells_built) return fail(c, ATM_E_STATE, "cells not built");
-    CU(cudaSetDevice(c->p.device));
+    CU(cudaSetDevice(c->device));
     if (cell_of && c->n)
         CU(cudaMemcpyAsync(cell_of, c->cell_of, c->n * sizeof(int), cudaMemcpyDeviceToHost, c->st));
     if (cell_start)
-        CU(cudaMemcpyAsync(cell_start, c->start, (c->g.ncell + 1) * sizeof(int),
+        CU(cudaMemcpyAsync(cell_start, c->start, (c->ncell + 1) * sizeof(int),
                            cudaMemcpyDeviceToHost, c->st));
     if (perm && c->n)
         CU(cudaMemcpyAsync(perm, c->perm, c->n * sizeof(int), cudaMemcpyDeviceToHost, c->st));
@@ -366,33 +439,46 @@ extern "C" atm_status atm_get_cells(atm_ctx* c, int32_t* cell_of, int32_t* cell_
     return ATM_OK;
 }
 
-// LJ + ATM force kernels for the current cells
-static atm_status enqueue_forces(atm_ctx* c, int trav, int trunc, int prec)
+// launch options of one force evaluation: the tuned choice, else the context's options
+static void launch_choice(const atm_ctx* c, int trav, int trunc, int prec, int& persistent,
+                          int& nwarps)
+{
+    int t = c->tuned[prec][trav][trunc];
+    if (t) {
+        persistent = (t - 1) & 1;
+        nwarps = ((t - 1) & 2) ? 8 : 4;
+    } else {
+        persistent = c->opt_persistent;
+        nwarps = c->opt_nwarps;
+    }
+    if (trav == ATM_3C01) nwarps = 0;
+}
+
+// LJ + ATM force kernels for the current cells; mcap = staged-molecule capacity
+static atm_status enqueue_forces(atm_ctx* c, int trav, int trunc, int prec, int mcap)
 {
     ForceJob j;
-    j.g = c->g;
-    j.n = c->n;
+    j.b = c->b;
+    j.rep_host = c->reps.data();
     j.xl = c->xl;
     j.xl32 = c->xl32;
     j.start = c->start;
     j.cell_sorted = c->cell_sorted;
     j.f_lj = c->f_lj;
     j.f_atm = c->f_atm;
-    j.lj_ew = c->lj_ew;
-    j.lj_cnt = c->lj_cnt;
+    j.mol_ew = c->mol_ew;
+    j.mol_cnt = c->mol_cnt;
     j.unit_ew = c->unit_ew;
     j.unit_cnt = c->unit_cnt;
     j.status = c->d_status;
-    j.rc = c->p.rc;
-    j.nu = c->p.nu;
-    j.lj_eps = c->p.lj_eps;
-    j.lj_sigma = c->p.lj_sigma;
-    j.lj_shift = c->p.lj_shift;
+    j.work = c->d_work;
     j.trav = trav;
     j.trunc = trunc;
     j.prec = prec;
-    j.mcap = c->unit_max[trav] > 0 ? c->unit_max[trav] : 1;
+    j.mcap = mcap > 0 ? mcap : 1;
     j.optin = c->smem_optin;
+    j.sms = c->sms;
+    launch_choice(c, trav, trunc, prec, j.persistent, j.nwarps);
     j.st = c->st;
 
     cudaEvent_t ev = prof_begin(c);
@@ -421,35 +507,32 @@ static atm_status enqueue_forces(atm_ctx* c, int trav, int trunc, int prec)
 static atm_status enqueue_reduce(atm_ctx* c)
 {
     ReduceArgs r;
+    r.b = c->b;
     r.unit_ew = c->unit_ew;
     r.unit_cnt = c->unit_cnt;
-    r.n_units = c->g.ncell;
-    r.lj_ew = c->lj_ew;
-    r.lj_cnt = c->lj_cnt;
-    r.n_lj = c->n_lj_blocks;
-    r.ke_part = c->ke_part;
-    r.n_ke = c->n_ke_blocks;
+    r.mol_ew = c->mol_ew;
+    r.mol_cnt = c->mol_cnt;
+    r.ke = c->ke;
     r.out = c->d_res;
     cudaEvent_t ev = prof_begin(c);
     CU(launch_final_reduce(r, c->st));
     prof_end(c, PK_MD, ev);
     c->n_launch += 1;
-    CU(cudaMemcpyAsync(c->h_res, c->d_res, sizeof(ResultDev), cudaMemcpyDeviceToHost, c->st));
+    CU(cudaMemcpyAsync(c->h_res, c->d_res, c->R * sizeof(ResultDev), cudaMemcpyDeviceToHost, c->st));
     return ATM_OK;
 }
 
-static void copy_result(const atm_ctx* c, atm_result* out)
+static void copy_result(const ResultDev& r, atm_result* out)
 {
-    const ResultDev* r = c->h_res;
-    out->e2 = r->e2;
-    out->e3 = r->e3;
-    out->w2 = r->w2;
-    out->w3 = r->w3;
-    out->ekin = r->ekin;
-    out->n_cand3 = r->n_cand3;
-    out->n_int3 = r->n_int3;
-    out->n_cand2 = r->n_cand2;
-    out->n_int2 = r->n_int2;
+    out->e2 = r.e2;
+    out->e3 = r.e3;
+    out->w2 = r.w2;
+    out->w3 = r.w3;
+    out->ekin = r.ekin;
+    out->n_cand3 = r.n_cand3;
+    out->n_int3 = r.n_int3;
+    out->n_cand2 = r.n_cand2;
+    out->n_int2 = r.n_int2;
 }
 
 static bool valid_enums(int trav, int trunc, int prec)
@@ -463,11 +546,11 @@ extern "C" atm_status atm_compute_forces(atm_ctx* c, atm_traversal trav, atm_tru
     if (!c) return ATM_E_INVALID;
     if (!valid_enums(trav, trunc, prec)) return fail(c, ATM_E_INVALID, "unknown traversal/truncation/precision");
     if (!c->cells_built) return fail(c, ATM_E_STATE, "cells not built");
-    CU(cudaSetDevice(c->p.device));
-    atm_status s = enqueue_forces(c, trav, trunc, prec);
+    CU(cudaSetDevice(c->device));
+    atm_status s = enqueue_forces(c, trav, trunc, prec, c->unit_max[trav]);
     if (s != ATM_OK) return s;
     cudaEvent_t ev = prof_begin(c);
-    CU(launch_kinetic(c->n, c->v, c->ke_part, c->st));
+    CU(launch_kinetic(c->n, c->v, c->ke, c->st));
     prof_end(c, PK_MD, ev);
     c->n_launch += 1;
     s = enqueue_reduce(c);
@@ -475,8 +558,18 @@ extern "C" atm_status atm_compute_forces(atm_ctx* c, atm_traversal trav, atm_tru
     if (out) {
         s = sync_and_check(c);
         if (s != ATM_OK) return s;
-        copy_result(c, out);
+        copy_result(c->h_res[0], out);
     }
+    return ATM_OK;
+}
+
+extern "C" atm_status atm_get_results(atm_ctx* c, atm_result* out)
+{
+    if (!c || !out) return ATM_E_INVALID;
+    CU(cudaSetDevice(c->device));
+    atm_status s = sync_and_check(c);
+    if (s != ATM_OK) return s;
+    for (int r = 0; r < c->R; r++) copy_result(c->h_res[r], out + r);
     return ATM_OK;
 }
 
@@ -484,7 +577,7 @@ static atm_status get_forces_impl(atm_ctx* c, double* f, int which, bool host)
 {
     if (!c || !f || which < 0 || which > 2) return ATM_E_INVALID;
     if (!c->forces_valid) return fail(c, ATM_E_STATE, "no force evaluation is current");
-    CU(cudaSetDevice(c->p.device));
+    CU(cudaSetDevice(c->device));
     size_t bytes = 3 * (size_t)c->n * sizeof(double);
     if (!bytes) return ATM_OK;
     CU(launch_gather_forces(c->n, c->perm, c->f_lj, c->f_atm, which, host ? c->f_out : f, c->st));
@@ -510,11 +603,79 @@ extern "C" atm_status atm_get_state(atm_ctx* c, double* x, double* v)
 {
     if (!c) return ATM_E_INVALID;
     if (!c->have_x) return fail(c, ATM_E_STATE, "no state set");
-    CU(cudaSetDevice(c->p.device));
+    CU(cudaSetDevice(c->device));
     size_t bytes = 3 * (size_t)c->n * sizeof(double);
     if (bytes && x) CU(cudaMemcpyAsync(x, c->x, bytes, cudaMemcpyDeviceToHost, c->st));
     if (bytes && v) CU(cudaMemcpyAsync(v, c->v, bytes, cudaMemcpyDeviceToHost, c->st));
     CU(cudaStreamSynchronize(c->st));
+    return ATM_OK;
+}
+
+// one velocity-Verlet step without host synchronisation: kick + drift, cells,
+// forces (capacity mcap), kick
+static atm_status enqueue_step(atm_ctx* c, int trav, int trunc, int prec, int mcap)
+{
+    cudaEvent_t ev = prof_begin(c);
+    CU(launch_kick(c->b, c->perm, c->f_lj, c->f_atm, c->x, c->v, 1, c->ke, c->st));
+    prof_end(c, PK_MD, ev);
+    c->n_launch += 1;
+    atm_status s = launch_cells(c);
+    if (s != ATM_OK) return s;
+    s = enqueue_forces(c, trav, trunc, prec, mcap);
+    if (s != ATM_OK) return s;
+    ev = prof_begin(c);
+    CU(launch_kick(c->b, c->perm, c->f_lj, c->f_atm, c->x, c->v, 0, c->ke, c->st));
+    prof_end(c, PK_MD, ev);
+    c->n_launch += 1;
+    return ATM_OK;
+}
+
+// staged-molecule capacity of a graph: the current largest unit plus headroom
+// for molecules moving between cells during the steps the graph replays
+static int graph_mcap(const atm_ctx* c, int trav)
+{
+    int m = c->unit_max[trav];
+    return std::min(ATM_MCAP_LIMIT, m + std::max(8, m / 4));
+}
+
+// run nsteps with a CUDA graph of one step (no host synchronisation between
+// steps); a capacity overflow surfaces in the status word
+static atm_status run_graph_steps(atm_ctx* c, int nsteps, int trav, int trunc, int prec)
+{
+    const int mcap = graph_mcap(c, trav);
+    int persistent, nwarps;
+    launch_choice(c, trav, trunc, prec, persistent, nwarps);
+    const int key[5] = {trav, trunc, prec, mcap, persistent + 2 * nwarps};
+    if (!c->graph || memcmp(key, c->graph_key, sizeof(key)) != 0) {
+        drop_graph(c);
+        cudaStream_t keep = c->st;
+        const bool keep_prof = c->prof;
+        const long long nl = c->n_launch, na = c->n_atm;
+        c->prof = false;
+        c->st = c->cap_st;
+        cudaGraph_t g = nullptr;
+        CU(cudaStreamBeginCapture(c->cap_st, cudaStreamCaptureModeThreadLocal));
+        atm_status s = enqueue_step(c, trav, trunc, prec, mcap);
+        cudaError_t e = cudaStreamEndCapture(c->cap_st, &g);
+        c->st = keep;
+        c->prof = keep_prof;
+        c->n_launch = nl;
+        c->n_atm = na;
+        if (s != ATM_OK) {
+            if (g) cudaGraphDestroy(g);
+            return s;
+        }
+        CU(e);
+        e = cudaGraphInstantiate(&c->graph, g, 0);
+        cudaGraphDestroy(g);
+        CU(e);
+        memcpy(c->graph_key, key, sizeof(key));
+    }
+    cudaEvent_t ev = prof_begin(c);
+    for (int k = 0; k < nsteps; k++) CU(cudaGraphLaunch(c->graph, c->st));
+    prof_end(c, PK_MD, ev);
+    c->n_launch += (long long)nsteps * KERNELS_PER_STEP;
+    c->n_atm += nsteps;
     return ATM_OK;
 }
 
@@ -525,33 +686,63 @@ extern "C" atm_status atm_step(atm_ctx* c, int nsteps, atm_traversal trav, atm_t
     if (nsteps < 0 || !valid_enums(trav, trunc, prec))
         return fail(c, ATM_E_INVALID, "bad step arguments");
     if (!c->have_x) return fail(c, ATM_E_STATE, "no state set");
-    CU(cudaSetDevice(c->p.device));
+    CU(cudaSetDevice(c->device));
     atm_status s;
     if (!c->forces_valid || c->f_trav != trav || c->f_trunc != trunc || c->f_prec != prec) {
         s = enqueue_cells(c);
         if (s != ATM_OK) return s;
-        s = enqueue_forces(c, trav, trunc, prec);
+        s = enqueue_forces(c, trav, trunc, prec, c->unit_max[trav]);
         if (s != ATM_OK) return s;
     }
-    const double dt = c->p.dt, half_dt = 0.5 * c->p.dt;
-    for (int k = 0; k < nsteps; k++) {
-        cudaEvent_t ev = prof_begin(c);
-        CU(launch_kick(c->n, c->perm, c->f_lj, c->f_atm, c->x, c->v, half_dt, dt, 1, c->ke_part,
-                       c->st));
-        prof_end(c, PK_MD, ev);
-        c->n_launch += 1;
-        s = enqueue_cells(c);
+    bool done = false;
+    if (c->opt_graph && nsteps > 0) {
+        const size_t bytes = 3 * (size_t)c->n * sizeof(double);
+        if (bytes) {
+            CU(cudaMemcpyAsync(c->x0, c->x, bytes, cudaMemcpyDeviceToDevice, c->st));
+            CU(cudaMemcpyAsync(c->v0, c->v, bytes, cudaMemcpyDeviceToDevice, c->st));
+        }
+        s = run_graph_steps(c, nsteps, trav, trunc, prec);
         if (s != ATM_OK) return s;
-        s = enqueue_forces(c, trav, trunc, prec);
-        if (s != ATM_OK) return s;
-        ev = prof_begin(c);
-        CU(launch_kick(c->n, c->perm, c->f_lj, c->f_atm, c->x, c->v, half_dt, dt, 0, c->ke_part,
-                       c->st));
-        prof_end(c, PK_MD, ev);
-        c->n_launch += 1;
+        CU(cudaMemcpyAsync(c->h_maxocc, c->d_maxocc, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->st));
+        s = sync_and_check(c);
+        if (s == ATM_OK) {
+            done = true;
+            c->maxocc = c->h_maxocc[0];
+            for (int t = 0; t < 3; t++) c->unit_max[t] = c->h_maxocc[1 + t];
+        } else if (s == ATM_E_CAPACITY) {
+            // a unit outgrew the graph's capacity: restart from the snapshot
+            // and step with per-step sizing
+            if (bytes) {
+                CU(cudaMemcpyAsync(c->x, c->x0, bytes, cudaMemcpyDeviceToDevice, c->st));
+                CU(cudaMemcpyAsync(c->v, c->v0, bytes, cudaMemcpyDeviceToDevice, c->st));
+            }
+            drop_graph(c);
+            s = enqueue_cells(c);
+            if (s != ATM_OK) return s;
+            s = enqueue_forces(c, trav, trunc, prec, c->unit_max[trav]);
+            if (s != ATM_OK) return s;
+        } else {
+            return s;
+        }
+    }
+    if (!done) {
+        for (int k = 0; k < nsteps; k++) {
+            cudaEvent_t ev = prof_begin(c);
+            CU(launch_kick(c->b, c->perm, c->f_lj, c->f_atm, c->x, c->v, 1, c->ke, c->st));
+            prof_end(c, PK_MD, ev);
+            c->n_launch += 1;
+            s = enqueue_cells(c);
+            if (s != ATM_OK) return s;
+            s = enqueue_forces(c, trav, trunc, prec, c->unit_max[trav]);
+            if (s != ATM_OK) return s;
+            ev = prof_begin(c);
+            CU(launch_kick(c->b, c->perm, c->f_lj, c->f_atm, c->x, c->v, 0, c->ke, c->st));
+            prof_end(c, PK_MD, ev);
+            c->n_launch += 1;
+        }
     }
     if (nsteps == 0) {
-        CU(launch_kinetic(c->n, c->v, c->ke_part, c->st));
+        CU(launch_kinetic(c->n, c->v, c->ke, c->st));
         c->n_launch += 1;
     }
     s = enqueue_reduce(c);
@@ -559,15 +750,118 @@ extern "C" atm_status atm_step(atm_ctx* c, int nsteps, atm_traversal trav, atm_t
     if (last) {
         s = sync_and_check(c);
         if (s != ATM_OK) return s;
-        copy_result(c, last);
+        copy_result(c->h_res[0], last);
     }
+    return ATM_OK;
+}
+
+extern "C" atm_status atm_set_options(atm_ctx* c, int persistent, int nwarps, int graph)
+{
+    if (!c) return ATM_E_INVALID;
+    if (persistent < 0 || persistent > 1 || !(nwarps == 0 || nwarps == 4 || nwarps == 8) ||
+        graph < 0 || graph > 1)
+        return fail(c, ATM_E_INVALID, "bad options");
+    c->opt_persistent = persistent;
+    c->opt_nwarps = nwarps;
+    c->opt_graph = graph;
+    memset(c->tuned, 0, sizeof(c->tuned));
+    drop_graph(c);
+    return ATM_OK;
+}
+
+extern "C" atm_status atm_autotune(atm_ctx* c, atm_traversal trav, atm_truncation trunc,
+                                   atm_precision prec, int reps, atm_tuning* out)
+{
+    if (!c) return ATM_E_INVALID;
+    if (!valid_enums(trav, trunc, prec) || reps < 1) return fail(c, ATM_E_INVALID, "bad tuning arguments");
+    if (!c->cells_built) return fail(c, ATM_E_STATE, "cells not built");
+    CU(cudaSetDevice(c->device));
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    const bool keep_prof = c->prof;
+    c->prof = false;
+    float best = 1e30f;
+    int best_code = 1;
+    atm_status s = ATM_OK;
+    const int nw_options = trav == ATM_3C01 ? 1 : 2;
+    for (int nwi = 0; nwi < nw_options && s == ATM_OK; nwi++)
+        for (int pers = 0; pers < 2 && s == ATM_OK; pers++) {
+            const int code = 1 + pers + 2 * nwi;
+            c->tuned[prec][trav][trunc] = code;
+            s = enqueue_forces(c, trav, trunc, prec, c->unit_max[trav]);  // warm-up
+            if (s != ATM_OK) break;
+            cudaEventRecord(e0, c->st);
+            for (int k = 0; k < reps && s == ATM_OK; k++)
+                s = enqueue_forces(c, trav, trunc, prec, c->unit_max[trav]);
+            cudaEventRecord(e1, c->st);
+            if (s != ATM_OK) break;
+            s = sync_and_check(c);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (s == ATM_OK && ms < best) {
+                best = ms;
+                best_code = code;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->prof = keep_prof;
+    c->tuned[prec][trav][trunc] = best_code;
+    drop_graph(c);
+    if (s != ATM_OK) return s;
+    if (out) {
+        out->persistent = (best_code - 1) & 1;
+        out->nwarps = trav == ATM_3C01 ? 4 : (((best_code - 1) & 2) ? 8 : 4);
+        out->ms_per_eval = best / reps;
+    }
+    return ATM_OK;
+}
+
+extern "C" atm_status atm_density_accumulate(atm_ctx* c, int axis, int nbins)
+{
+    if (!c) return ATM_E_INVALID;
+    if (axis < 0 || axis > 2 || nbins < 1 || nbins > DENS_MAX_BINS)
+        return fail(c, ATM_E_INVALID, "axis in 0..2, 1 <= nbins <= %d", DENS_MAX_BINS);
+    if (!c->cells_built) return fail(c, ATM_E_STATE, "cells not built (positions not wrapped)");
+    if (c->dens_samples > 0 && (axis != c->dens_axis || nbins != c->dens_nbins))
+        return fail(c, ATM_E_STATE, "density accumulator holds another axis/bin count; reset it");
+    CU(cudaSetDevice(c->device));
+    CU(launch_density(c->b, c->x, axis, nbins, c->d_dens, c->st));
+    c->n_launch += 1;
+    c->dens_axis = axis;
+    c->dens_nbins = nbins;
+    c->dens_samples++;
+    return ATM_OK;
+}
+
+extern "C" atm_status atm_density_get(atm_ctx* c, uint64_t* counts, int64_t* samples)
+{
+    if (!c) return ATM_E_INVALID;
+    CU(cudaSetDevice(c->device));
+    if (counts && c->dens_nbins > 0)
+        CU(cudaMemcpyAsync(counts, c->d_dens, (size_t)c->R * c->dens_nbins * sizeof(uint64_t),
+                           cudaMemcpyDeviceToHost, c->st));
+    CU(cudaStreamSynchronize(c->st));
+    if (samples) *samples = c->dens_samples;
+    return ATM_OK;
+}
+
+extern "C" atm_status atm_density_reset(atm_ctx* c)
+{
+    if (!c) return ATM_E_INVALID;
+    CU(cudaSetDevice(c->device));
+    CU(cudaMemsetAsync(c->d_dens, 0, (size_t)c->R * DENS_MAX_BINS * sizeof(uint64_t), c->st));
+    c->dens_samples = 0;
+    c->dens_axis = -1;
+    c->dens_nbins = 0;
     return ATM_OK;
 }
 
 extern "C" atm_status atm_set_profiling(atm_ctx* c, int on)
 {
     if (!c) return ATM_E_INVALID;
-    CU(cudaSetDevice(c->p.device));
+    CU(cudaSetDevice(c->device));
     CU(cudaStreamSynchronize(c->st));
     prof_drain(c);
     c->prof = on != 0;
@@ -580,7 +874,7 @@ extern "C" atm_status atm_set_profiling(atm_ctx* c, int on)
 extern "C" atm_status atm_get_profile(atm_ctx* c, atm_profile* out)
 {
     if (!c || !out) return ATM_E_INVALID;
-    CU(cudaSetDevice(c->p.device));
+    CU(cudaSetDevice(c->device));
     CU(cudaStreamSynchronize(c->st));
     prof_drain(c);
     out->ms_cells = c->prof_ms[PK_CELLS];

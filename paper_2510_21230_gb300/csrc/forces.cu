@@ -1,44 +1,82 @@
-// forces.cu -- argument set-up and launch of the LJ and ATM force kernels,
-// shared by the context API (capi.cu) and the allocation-free entry point.
+// forces.cu -- replica descriptors, argument set-up and launch of the LJ and
+// ATM force kernels, shared by the context API (capi.cu) and the
+// allocation-free entry point (noalloc.cu).
 #include <algorithm>
+#include <cmath>
 
 #include "forces.cuh"
 
 namespace atm3 {
 
+atm_status make_rep(const atm_params& p, long long n, long long mol0, long long cell0, Rep& r)
+{
+    r = Rep{};
+    long long ncell = 1;
+    for (int d = 0; d < 3; d++) {
+        double L = p.box[d], rc = p.rc;
+        if (!(L > 0.0) || !(rc > 0.0) || !std::isfinite(L) || !std::isfinite(rc)) return ATM_E_INVALID;
+        double k = std::floor(L / rc);
+        if (k < 1.0) k = 1.0;
+        while (L / (k + 1.0) >= rc) k += 1.0;
+        while (k > 0.0 && L / k < rc) k -= 1.0;
+        if (k < 3.0) return ATM_E_BOX_TOO_SMALL;
+        if (k > 1.0e6) return ATM_E_INVALID;
+        r.g.nc[d] = (int)k;
+        r.g.L[d] = L;
+        r.g.w[d] = L / k;
+        r.wf[d] = (float)r.g.w[d];
+        ncell *= (long long)k;
+    }
+    if (ncell > (1ll << 30)) return ATM_E_INVALID;
+    if (!std::isfinite(p.nu) || !std::isfinite(p.lj_eps) || !(p.lj_sigma > 0.0) ||
+        !std::isfinite(p.dt))
+        return ATM_E_INVALID;
+    r.g.ncell = ncell;
+    r.mol0 = mol0;
+    r.n = n;
+    r.cell0 = cell0;
+    const double rc = p.rc;
+    r.rc2 = rc * rc;
+    r.rc6 = r.rc2 * r.rc2 * r.rc2;
+    r.nu = p.nu;
+    r.dt = p.dt;
+    const float rcf = (float)rc;
+    r.rc2f = rcf * rcf;
+    r.rc6f = r.rc2f * r.rc2f * r.rc2f;
+    r.nuf = (float)p.nu;
+    const double sig2 = p.lj_sigma * p.lj_sigma;
+    const double sc = sig2 / (rc * rc), sc3 = sc * sc * sc;
+    r.sig2 = sig2;
+    r.eps4 = 4.0 * p.lj_eps;
+    r.eps24 = 24.0 * p.lj_eps;
+    r.eps48 = 48.0 * p.lj_eps;
+    r.ushift = p.lj_shift ? 4.0 * p.lj_eps * (sc3 * sc3 - sc3) : 0.0;
+    r.sig2f = (float)r.sig2;
+    r.eps4f = (float)r.eps4;
+    r.eps24f = (float)r.eps24;
+    r.eps48f = (float)r.eps48;
+    r.ushiftf = (float)r.ushift;
+    const double wmax = std::max(r.g.w[0], std::max(r.g.w[1], r.g.w[2]));
+    r.p_lo = (float)(r.rc2 * (1.0 - 1.0 / 4096.0));
+    r.p_hi = (float)(r.rc2 * (1.0 + 1.0 / 4096.0));
+    r.q_lo = (float)(r.rc6 * (1.0 - 1.0 / 1024.0));
+    r.q_hi = (float)(r.rc6 * (1.0 + 1.0 / 1024.0));
+    r.dmin = (float)((0.02 * wmax) * (0.02 * wmax));
+    return ATM_OK;
+}
+
 cudaError_t enqueue_lj(const ForceJob& j)
 {
     LjArgs<double> l64{};
     LjArgs<float> l32{};
-    const double rc = j.rc, sig2 = j.lj_sigma * j.lj_sigma;
-    const double sc = sig2 / (rc * rc), sc3 = sc * sc * sc;
-    const double ushift = j.lj_shift ? 4.0 * j.lj_eps * (sc3 * sc3 - sc3) : 0.0;
     if (j.prec == 0) {
-        l64.g = j.g; l64.n = j.n; l64.xl = j.xl; l64.cell_start = j.start;
-        l64.cell_sorted = j.cell_sorted; l64.fs = j.f_lj; l64.part_ew = j.lj_ew;
-        l64.part_cnt = j.lj_cnt;
-        for (int d = 0; d < 3; d++) {
-            l64.w[d] = j.g.w[d];
-            l64.wf[d] = (float)j.g.w[d];
-        }
-        l64.rc2 = rc * rc; l64.sig2 = sig2; l64.eps4 = 4.0 * j.lj_eps;
-        l64.eps24 = 24.0 * j.lj_eps; l64.eps48 = 48.0 * j.lj_eps; l64.ushift = ushift;
-        l64.xl32 = j.xl32;
-        l64.p_lo = (float)(rc * rc * (1.0 - 1.0 / 4096.0));
-        l64.p_hi = (float)(rc * rc * (1.0 + 1.0 / 4096.0));
+        l64.b = j.b; l64.n = j.b.ntot; l64.xl = j.xl; l64.xl32 = j.xl32; l64.cell_start = j.start;
+        l64.cell_sorted = j.cell_sorted; l64.fs = j.f_lj; l64.mol_ew = j.mol_ew;
+        l64.mol_cnt = j.mol_cnt;
     } else {
-        float rcf = (float)rc;
-        l32.g = j.g; l32.n = j.n; l32.xl = j.xl32; l32.cell_start = j.start;
-        l32.cell_sorted = j.cell_sorted; l32.fs = j.f_lj; l32.part_ew = j.lj_ew;
-        l32.part_cnt = j.lj_cnt;
-        for (int d = 0; d < 3; d++) {
-            l32.w[d] = (float)j.g.w[d];
-            l32.wf[d] = (float)j.g.w[d];
-        }
-        l32.rc2 = rcf * rcf; l32.sig2 = (float)sig2; l32.eps4 = (float)(4.0 * j.lj_eps);
-        l32.eps24 = (float)(24.0 * j.lj_eps); l32.eps48 = (float)(48.0 * j.lj_eps);
-        l32.ushift = (float)ushift;
-        l32.xl32 = j.xl32;
+        l32.b = j.b; l32.n = j.b.ntot; l32.xl = j.xl32; l32.xl32 = j.xl32; l32.cell_start = j.start;
+        l32.cell_sorted = j.cell_sorted; l32.fs = j.f_lj; l32.mol_ew = j.mol_ew;
+        l32.mol_cnt = j.mol_cnt;
     }
     return launch_lj(j.prec, l64, l32, j.st);
 }
@@ -51,57 +89,48 @@ cudaError_t enqueue_atm(const ForceJob& j, size_t* smem_set, bool* capacity)
         *capacity = true;
         return cudaErrorInvalidValue;
     }
+    if ((j.nwarps == 4 || j.nwarps == 8) && j.trav != 0) {
+        AtmPlan Q;
+        if (atm_choose_plan_nw(j.trav, j.trunc, j.prec, j.mcap, j.optin, j.nwarps, Q)) P = Q;
+    }
     cudaError_t e;
     if (!smem_set || P.smem > *smem_set) {
         e = j.prec == 0 ? atm_attr_fp64(j.trav, j.trunc, P.smem) : atm_attr_fp32(j.trav, j.trunc, P.smem);
         if (e != cudaSuccess) return e;
         if (smem_set) *smem_set = P.smem;
     }
-    if (j.trav != 0 && j.n > 0) {
-        e = cudaMemsetAsync(j.f_atm, 0, 3 * (size_t)j.n * sizeof(double), j.st);
+    if (j.trav != 0 && j.b.ntot > 0) {
+        e = cudaMemsetAsync(j.f_atm, 0, 3 * (size_t)j.b.ntot * sizeof(double), j.st);
         if (e != cudaSuccess) return e;
     }
-    // FP32 prefilter bands of the FP64 decisions (derivation in atm_common.cuh)
-    const double rc2d = j.rc * j.rc, rc6d = rc2d * rc2d * rc2d;
-    const double wmax = std::max(j.g.w[0], std::max(j.g.w[1], j.g.w[2]));
+    int ctas = 0;
+    if (j.persistent && j.work) {
+        int per_sm = j.prec == 0 ? atm_occupancy_fp64(j.trav, j.trunc, P.nwarps, P.smem)
+                                 : atm_occupancy_fp32(j.trav, j.trunc, P.nwarps, P.smem);
+        ctas = std::max(1, per_sm) * std::max(1, j.sms);
+        e = cudaMemsetAsync(j.work, 0, sizeof(int), j.st);
+        if (e != cudaSuccess) return e;
+    }
     if (j.prec == 0) {
         AtmArgs<double> a{};
-        a.g = j.g; a.n = j.n; a.xl = j.xl; a.xl32 = j.xl32; a.cell_start = j.start;
+        a.b = j.b; a.n = j.b.ntot; a.xl = j.xl; a.xl32 = j.xl32; a.cell_start = j.start;
         a.fs = j.f_atm; a.unit_ew = j.unit_ew; a.unit_cnt = j.unit_cnt; a.status = j.status;
-        for (int d = 0; d < 3; d++) {
-            a.w[d] = j.g.w[d];
-            a.wf[d] = (float)j.g.w[d];
-        }
-        a.rc2 = rc2d;
-        a.rc6 = rc6d;
-        a.nu = j.nu;
-        a.p_lo = (float)(rc2d * (1.0 - 1.0 / 4096.0));
-        a.p_hi = (float)(rc2d * (1.0 + 1.0 / 4096.0));
-        a.q_lo = (float)(rc6d * (1.0 - 1.0 / 1024.0));
-        a.q_hi = (float)(rc6d * (1.0 + 1.0 / 1024.0));
-        a.dmin = (float)((0.02 * wmax) * (0.02 * wmax));
+        a.work = ctas > 0 ? j.work : nullptr;
         a.mcap = j.mcap;
         a.gcap = P.gcap;
         a.use_d = P.use_d;
         a.acc_mode = P.acc_mode;
-        return launch_atm_fp64(j.trav, j.trunc, a, P.nwarps, P.smem, j.st);
+        return launch_atm_fp64(j.trav, j.trunc, a, P.nwarps, P.smem, ctas, j.st);
     }
     AtmArgs<float> a{};
-    float rcf = (float)j.rc;
-    a.g = j.g; a.n = j.n; a.xl = j.xl32; a.xl32 = j.xl32; a.cell_start = j.start;
+    a.b = j.b; a.n = j.b.ntot; a.xl = j.xl32; a.xl32 = j.xl32; a.cell_start = j.start;
     a.fs = j.f_atm; a.unit_ew = j.unit_ew; a.unit_cnt = j.unit_cnt; a.status = j.status;
-    for (int d = 0; d < 3; d++) {
-        a.w[d] = (float)j.g.w[d];
-        a.wf[d] = (float)j.g.w[d];
-    }
-    a.rc2 = rcf * rcf;
-    a.rc6 = a.rc2 * a.rc2 * a.rc2;
-    a.nu = (float)j.nu;
+    a.work = ctas > 0 ? j.work : nullptr;
     a.mcap = j.mcap;
     a.gcap = P.gcap;
     a.use_d = P.use_d;
     a.acc_mode = P.acc_mode;
-    return launch_atm_fp32(j.trav, j.trunc, a, P.nwarps, P.smem, j.st);
+    return launch_atm_fp32(j.trav, j.trunc, a, P.nwarps, P.smem, ctas, j.st);
 }
 
 }  // namespace atm3

@@ -1,5 +1,8 @@
-// forces.cuh -- one LJ + ATM force evaluation on built cells (host side).
+// forces.cuh -- host side of one LJ + ATM force evaluation on built cells,
+// and the replica descriptors; shared by the context API and the
+// allocation-free entry point.
 #pragma once
+#include "atm3.h"
 #include "atm3_internal.cuh"
 #include "md_kernels.cuh"
 
@@ -7,25 +10,33 @@ namespace atm3 {
 
 constexpr int ATM_MCAP_LIMIT = 2047;  // staged molecules per unit (queue entries pack 11-bit indices)
 
+// Fill a replica descriptor from the public parameters: linked-cell grid
+// (n_d = largest k with L_d / k >= r_c, at least 3), cutoffs in FP64 and
+// FP32, LJ constants, FP32 prefilter bands of the FP64 decisions (derivation
+// in atm_common.cuh).  Returns ATM_OK, ATM_E_INVALID or ATM_E_BOX_TOO_SMALL.
+atm_status make_rep(const atm_params& p, long long n, long long mol0, long long cell0, Rep& r);
+
 struct ForceJob {
-    Grid g;
-    long long n;
+    Batch b;                 // device replica table
+    const Rep* rep_host;     // [R] host copy (plan sizing)
     const double* xl;        // sorted cell-local coordinates FP64, SoA [3n]
     const float* xl32;       // the same in FP32
     const int* start;        // cell_start [ncell + 1]
     const int* cell_sorted;  // [n]
     double* f_lj;            // [3n] sorted order, fully written
     double* f_atm;           // [3n] sorted order
-    double* lj_ew;
-    unsigned long long* lj_cnt;
-    double* unit_ew;
+    double* mol_ew;          // [2n]
+    unsigned* mol_cnt;       // [2n]
+    double* unit_ew;         // [2 ncell]
     unsigned long long* unit_cnt;
     int* status;
-    double rc, nu, lj_eps, lj_sigma;
-    int lj_shift;
+    int* work;               // unit counter of the persistent launch
     int trav, trunc, prec;
-    int mcap;   // largest unit of the traversal (staged molecules)
-    int optin;  // opt-in shared memory per block of the device
+    int mcap;                // largest unit of the traversal (staged molecules)
+    int optin;               // opt-in shared memory per block of the device
+    int sms;                 // SMs of the device
+    int persistent;          // 1: persistent grid over a unit counter
+    int nwarps;              // 0: the plan's default, else 4 or 8
     cudaStream_t st;
 };
 

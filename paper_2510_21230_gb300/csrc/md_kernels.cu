@@ -1,5 +1,8 @@
-// md_kernels.cu -- linked-cell build, LJ pair forces, velocity-Verlet update
-// and the deterministic final reductions.
+// md_kernels.cu -- linked-cell build, LJ pair forces, velocity-Verlet update,
+// density profile and the deterministic per-replica reductions.
+// Every kernel works on a batch of replicas (a single system is a batch of
+// one): per-molecule threads look their replica up in rep_of_mol, per-cell
+// threads in rep_of_cell.
 #include "md_kernels.cuh"
 
 namespace atm3 {
@@ -27,13 +30,15 @@ __device__ __forceinline__ int bin1(double t, double w, int n, double& loc)
     return c;
 }
 
-// K1: wrap positions in place, cell id per molecule, cell histogram with the
-// arrival rank of each molecule
-__global__ void k_wrap_bin(Grid g, long long n, double* __restrict__ x, int* __restrict__ cell_of,
+// K1: wrap positions in place, global cell id per molecule, cell histogram
+// with the arrival rank of each molecule
+__global__ void k_wrap_bin(Batch B, double* __restrict__ x, int* __restrict__ cell_of,
                            int* __restrict__ rank, int* __restrict__ count, int* __restrict__ status)
 {
+    const long long n = B.ntot;
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const Rep& rp = B.rep[B.rep_of_mol[i]];
     int cc[3];
     for (int d = 0; d < 3; d++) {
         double xv = x[d * n + i];
@@ -41,12 +46,12 @@ __global__ void k_wrap_bin(Grid g, long long n, double* __restrict__ x, int* __r
             atomicOr(status, ST_NONFINITE);
             xv = 0.0;
         }
-        double t = wrap1(xv, g.L[d]);
+        double t = wrap1(xv, rp.g.L[d]);
         x[d * n + i] = t;
         double loc;
-        cc[d] = bin1(t, g.w[d], g.nc[d], loc);
+        cc[d] = bin1(t, rp.g.w[d], rp.g.nc[d], loc);
     }
-    int id = (cc[2] * g.nc[1] + cc[1]) * g.nc[0] + cc[0];
+    int id = (int)rp.cell0 + (cc[2] * rp.g.nc[1] + cc[1]) * rp.g.nc[0] + cc[0];
     cell_of[i] = id;
     rank[i] = atomicAdd(count + id, 1);
 }
@@ -96,18 +101,20 @@ __global__ void __launch_bounds__(1024) k_scan(long long ncell, const int* __res
 
 // largest staged-molecule count of a traversal unit, per traversal:
 // out[0] 3c01 (27 cells), out[1] 3c18 (base + 13 forward), out[2] 3c08 (2x2x2 block)
-__global__ void k_unit_max(Grid g, const int* __restrict__ start, int* __restrict__ out)
+__global__ void k_unit_max(Batch B, const int* __restrict__ start, int* __restrict__ out)
 {
     long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     int m01 = 0, m18 = 0, m08 = 0;
-    if (c < g.ncell) {
+    if (c < B.ncell) {
+        const Rep& rp = B.rep[B.rep_of_cell[c]];
+        const int* st = start + rp.cell0;
         int cx, cy, cz;
-        cell_coords(g, c, cx, cy, cz);
+        cell_coords(rp.g, c - rp.cell0, cx, cy, cz);
         for (int t = 0; t < 27; t++) {
             int dx, dy, dz;
             offset27(t, dx, dy, dz);
-            long long nc = cell_at(g, cx, cy, cz, dx, dy, dz);
-            int k = start[nc + 1] - start[nc];
+            long long nc = cell_at(rp.g, cx, cy, cz, dx, dy, dz);
+            int k = st[nc + 1] - st[nc];
             m01 += k;
             if (t >= 13) m18 += k;
             if (dx >= 0 && dy >= 0 && dz >= 0) m08 += k;
@@ -151,22 +158,24 @@ __global__ void k_cell_sort(long long ncell, const int* __restrict__ start, int*
     }
 }
 
-// K3c: sorted FP64 and FP32 cell-local coordinates and the cell of each slot
-__global__ void k_local(Grid g, long long n, const double* __restrict__ x,
-                        const int* __restrict__ perm, double* __restrict__ xl,
-                        float* __restrict__ xl32, int* __restrict__ cell_sorted)
+// K3c: sorted FP64 and FP32 cell-local coordinates and the global cell of each slot
+__global__ void k_local(Batch B, const double* __restrict__ x, const int* __restrict__ perm,
+                        double* __restrict__ xl, float* __restrict__ xl32,
+                        int* __restrict__ cell_sorted)
 {
+    const long long n = B.ntot;
     long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (s >= n) return;
     int i = perm[s];
+    const Rep& rp = B.rep[B.rep_of_mol[i]];
     int cc[3];
     for (int d = 0; d < 3; d++) {
         double loc;
-        cc[d] = bin1(x[d * n + i], g.w[d], g.nc[d], loc);
+        cc[d] = bin1(x[d * n + i], rp.g.w[d], rp.g.nc[d], loc);
         xl[d * n + s] = loc;
         xl32[d * n + s] = (float)loc;
     }
-    cell_sorted[s] = (cc[2] * g.nc[1] + cc[1]) * g.nc[0] + cc[0];
+    cell_sorted[s] = (int)rp.cell0 + (cc[2] * rp.g.nc[1] + cc[1]) * rp.g.nc[0] + cc[0];
 }
 
 // ---------------------------------------------------------------- LJ pairs
@@ -198,144 +207,107 @@ __global__ void __launch_bounds__(128) k_lj_owner(const LjArgs<R> A)
     typedef LjArith<R> Q;
     const long long n = A.n;
     long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    double e = 0.0, w = 0.0;
-    unsigned long long visits = 0, cand = 0;
-    if (s < n) {
-        int c = A.cell_sorted[s];
-        int cx, cy, cz;
-        cell_coords(A.g, c, cx, cy, cz);
-        R xs = A.xl[s], ys = A.xl[n + s], zs = A.xl[2 * n + s];
-        R fx = 0, fy = 0, fz = 0;
-        R esum = 0, wsum = 0;
-        for (int t = 0; t < 27; t++) {
-            int dx, dy, dz;
-            offset27(t, dx, dy, dz);
-            long long nc = cell_at(A.g, cx, cy, cz, dx, dy, dz);
-            int q0 = A.cell_start[nc], q1 = A.cell_start[nc + 1];
-            if (t > 13) cand += (unsigned long long)(q1 - q0);
-            if (t == 13) cand += (unsigned long long)(q1 - 1 - s);
-            R sx = Q::mul((R)dx, A.w[0]), sy = Q::mul((R)dy, A.w[1]), sz = Q::mul((R)dz, A.w[2]);
-            for (int q = q0; q < q1; q++) {
-                if (q == s) continue;
-                if (sizeof(R) == 8) {
-                    // FP32 prefilter: values outside the band decide the FP64 test
-                    typedef LjArith<float> F;
-                    float ex = F::add(F::sub(A.xl32[q], A.xl32[s]), F::mul((float)dx, A.wf[0]));
-                    float ey = F::add(F::sub(A.xl32[n + q], A.xl32[n + s]), F::mul((float)dy, A.wf[1]));
-                    float ez = F::add(F::sub(A.xl32[2 * n + q], A.xl32[2 * n + s]),
-                                      F::mul((float)dz, A.wf[2]));
-                    float f2 = F::add(F::add(F::mul(ex, ex), F::mul(ey, ey)), F::mul(ez, ez));
-                    if (f2 > A.p_hi) continue;
-                }
-                R ddx = Q::add(Q::sub(A.xl[q], xs), sx);
-                R ddy = Q::add(Q::sub(A.xl[n + q], ys), sy);
-                R ddz = Q::add(Q::sub(A.xl[2 * n + q], zs), sz);
-                R a = Q::add(Q::add(Q::mul(ddx, ddx), Q::mul(ddy, ddy)), Q::mul(ddz, ddz));
-                if (!(a < A.rc2)) continue;
-                visits++;
-                R ia = R(1) / a;
-                R s2 = A.sig2 * ia;
-                R s3 = s2 * s2 * s2;
-                R s6 = s3 * s3;
-                R fw = (A.eps48 * s6 - A.eps24 * s3) * ia;  // F_s = -fw d
-                fx -= fw * ddx;
-                fy -= fw * ddy;
-                fz -= fw * ddz;
-                esum += A.eps4 * (s6 - s3) - A.ushift;
-                wsum += fw * a;
+    if (s >= n) return;
+    const int cg = A.cell_sorted[s];
+    const Rep& rp = A.b.rep[A.b.rep_of_cell[cg]];
+    const int* st = A.cell_start + rp.cell0;
+    int cx, cy, cz;
+    cell_coords(rp.g, cg - rp.cell0, cx, cy, cz);
+    const bool f64 = sizeof(R) == 8;
+    const R w0 = (R)rp.g.w[0], w1 = (R)rp.g.w[1], w2 = (R)rp.g.w[2];
+    const R rc2 = f64 ? (R)rp.rc2 : (R)rp.rc2f;
+    const R sig2 = f64 ? (R)rp.sig2 : (R)rp.sig2f;
+    const R eps4 = f64 ? (R)rp.eps4 : (R)rp.eps4f;
+    const R eps24 = f64 ? (R)rp.eps24 : (R)rp.eps24f;
+    const R eps48 = f64 ? (R)rp.eps48 : (R)rp.eps48f;
+    const R ushift = f64 ? (R)rp.ushift : (R)rp.ushiftf;
+    R xs = A.xl[s], ys = A.xl[n + s], zs = A.xl[2 * n + s];
+    R fx = 0, fy = 0, fz = 0;
+    R esum = 0, wsum = 0;
+    unsigned visits = 0, cand = 0;
+    for (int t = 0; t < 27; t++) {
+        int dx, dy, dz;
+        offset27(t, dx, dy, dz);
+        long long nc = cell_at(rp.g, cx, cy, cz, dx, dy, dz);
+        int q0 = st[nc], q1 = st[nc + 1];
+        if (t > 13) cand += (unsigned)(q1 - q0);
+        if (t == 13) cand += (unsigned)(q1 - 1 - s);
+        R sx = Q::mul((R)dx, w0), sy = Q::mul((R)dy, w1), sz = Q::mul((R)dz, w2);
+        for (int q = q0; q < q1; q++) {
+            if (q == s) continue;
+            if (f64) {
+                // FP32 prefilter: a value above the band decides the FP64 test
+                typedef LjArith<float> F;
+                float ex = F::add(F::sub(A.xl32[q], A.xl32[s]), F::mul((float)dx, rp.wf[0]));
+                float ey = F::add(F::sub(A.xl32[n + q], A.xl32[n + s]), F::mul((float)dy, rp.wf[1]));
+                float ez = F::add(F::sub(A.xl32[2 * n + q], A.xl32[2 * n + s]),
+                                  F::mul((float)dz, rp.wf[2]));
+                float f2 = F::add(F::add(F::mul(ex, ex), F::mul(ey, ey)), F::mul(ez, ez));
+                if (f2 > rp.p_hi) continue;
             }
+            R ddx = Q::add(Q::sub(A.xl[q], xs), sx);
+            R ddy = Q::add(Q::sub(A.xl[n + q], ys), sy);
+            R ddz = Q::add(Q::sub(A.xl[2 * n + q], zs), sz);
+            R a = Q::add(Q::add(Q::mul(ddx, ddx), Q::mul(ddy, ddy)), Q::mul(ddz, ddz));
+            if (!(a < rc2)) continue;
+            visits++;
+            R ia = R(1) / a;
+            R s2 = sig2 * ia;
+            R s3 = s2 * s2 * s2;
+            R s6 = s3 * s3;
+            R fw = (eps48 * s6 - eps24 * s3) * ia;  // F_s = -fw d
+            fx -= fw * ddx;
+            fy -= fw * ddy;
+            fz -= fw * ddz;
+            esum += eps4 * (s6 - s3) - ushift;
+            wsum += fw * a;
         }
-        A.fs[s] = (double)fx;
-        A.fs[n + s] = (double)fy;
-        A.fs[2 * n + s] = (double)fz;
-        e = 0.5 * (double)esum;
-        w = 0.5 * (double)wsum;
     }
-    // block partials
-    __shared__ double s_e[4], s_w[4];
-    __shared__ unsigned long long s_v[4], s_c[4];
-    for (int o = 16; o > 0; o >>= 1) {
-        e += __shfl_down_sync(0xffffffffu, e, o);
-        w += __shfl_down_sync(0xffffffffu, w, o);
-        visits += __shfl_down_sync(0xffffffffu, visits, o);
-        cand += __shfl_down_sync(0xffffffffu, cand, o);
-    }
-    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) {
-        s_e[warp] = e;
-        s_w[warp] = w;
-        s_v[warp] = visits;
-        s_c[warp] = cand;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double et = 0, wt = 0;
-        unsigned long long vt = 0, ct = 0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); q++) {
-            et += s_e[q];
-            wt += s_w[q];
-            vt += s_v[q];
-            ct += s_c[q];
-        }
-        A.part_ew[2 * blockIdx.x] = et;
-        A.part_ew[2 * blockIdx.x + 1] = wt;
-        A.part_cnt[2 * blockIdx.x] = ct;
-        A.part_cnt[2 * blockIdx.x + 1] = vt;
-    }
+    A.fs[s] = (double)fx;
+    A.fs[n + s] = (double)fy;
+    A.fs[2 * n + s] = (double)fz;
+    A.mol_ew[2 * s] = 0.5 * (double)esum;
+    A.mol_ew[2 * s + 1] = 0.5 * (double)wsum;
+    A.mol_cnt[2 * s] = cand;
+    A.mol_cnt[2 * s + 1] = visits;
 }
-
 
 // ---------------------------------------------------------------- integrator
 
 // v += (dt/2) F for every molecule (F = LJ + ATM in sorted order), then, if
-// drift, x += dt v.  Kinetic-energy partials per block (after the kick).
-__global__ void __launch_bounds__(256) k_kick(long long n, const int* __restrict__ perm,
+// drift, x += dt v; kinetic energy per molecule (after the kick)
+__global__ void __launch_bounds__(256) k_kick(Batch B, const int* __restrict__ perm,
                                               const double* __restrict__ f_lj,
                                               const double* __restrict__ f_atm,
                                               double* __restrict__ x, double* __restrict__ v,
-                                              double half_dt, double dt, int drift,
-                                              double* __restrict__ ke_part)
+                                              int drift, double* __restrict__ ke)
 {
+    const long long n = B.ntot;
     long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    double ke = 0.0;
-    if (s < n) {
-        int i = perm[s];
-        for (int d = 0; d < 3; d++) {
-            double f = __dadd_rn(f_lj[d * n + s], f_atm[d * n + s]);
-            double vv = __dadd_rn(v[d * n + i], __dmul_rn(half_dt, f));
-            v[d * n + i] = vv;
-            if (drift) x[d * n + i] = __dadd_rn(x[d * n + i], __dmul_rn(dt, vv));
-            ke += 0.5 * vv * vv;
-        }
+    if (s >= n) return;
+    int i = perm[s];
+    const Rep& rp = B.rep[B.rep_of_mol[i]];
+    const double dt = rp.dt, half_dt = 0.5 * rp.dt;
+    double k = 0.0;
+    for (int d = 0; d < 3; d++) {
+        double f = __dadd_rn(f_lj[d * n + s], f_atm[d * n + s]);
+        double vv = __dadd_rn(v[d * n + i], __dmul_rn(half_dt, f));
+        v[d * n + i] = vv;
+        if (drift) x[d * n + i] = __dadd_rn(x[d * n + i], __dmul_rn(dt, vv));
+        k += 0.5 * vv * vv;
     }
-    __shared__ double s_k[8];
-    for (int o = 16; o > 0; o >>= 1) ke += __shfl_down_sync(0xffffffffu, ke, o);
-    if ((threadIdx.x & 31) == 0) s_k[threadIdx.x >> 5] = ke;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); q++) t += s_k[q];
-        ke_part[blockIdx.x] = t;
-    }
+    ke[i] = k;
 }
 
-// kinetic energy only (no update)
+// kinetic energy per molecule only (no update)
 __global__ void __launch_bounds__(256) k_kinetic(long long n, const double* __restrict__ v,
-                                                 double* __restrict__ ke_part)
+                                                 double* __restrict__ ke)
 {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    double ke = 0.0;
-    if (i < n)
-        for (int d = 0; d < 3; d++) ke += 0.5 * v[d * n + i] * v[d * n + i];
-    __shared__ double s_k[8];
-    for (int o = 16; o > 0; o >>= 1) ke += __shfl_down_sync(0xffffffffu, ke, o);
-    if ((threadIdx.x & 31) == 0) s_k[threadIdx.x >> 5] = ke;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); q++) t += s_k[q];
-        ke_part[blockIdx.x] = t;
-    }
+    if (i >= n) return;
+    double k = 0.0;
+    for (int d = 0; d < 3; d++) k += 0.5 * v[d * n + i] * v[d * n + i];
+    ke[i] = k;
 }
 
 // finiteness check of a state copied from device memory
@@ -345,30 +317,45 @@ __global__ void k_check_finite(long long m, const double* __restrict__ a, int* _
     if (i < m && !isfinite(a[i])) atomicOr(status, ST_NONFINITE);
 }
 
+// density profile: histogram of one coordinate of the wrapped positions
+__global__ void k_density(Batch B, const double* __restrict__ x, int axis, int nbins,
+                          unsigned long long* __restrict__ counts)
+{
+    const long long n = B.ntot;
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int r = B.rep_of_mol[i];
+    const double h = B.rep[r].g.L[axis] / (double)nbins;
+    int b = (int)floor(x[axis * n + i] / h);
+    b = b < 0 ? 0 : (b >= nbins ? nbins - 1 : b);
+    atomicAdd(counts + (long long)r * nbins + b, 1ull);
+}
+
 // ---------------------------------------------------------------- reductions
 
-// One CTA sums every partial in a fixed order (thread-strided then a fixed
-// tree), so the scalars are reproducible run to run.
+// One CTA per replica sums every partial of its units and molecules in a
+// fixed order (thread-strided, then a fixed tree): reproducible scalars.
 __global__ void __launch_bounds__(256) k_final_reduce(ReduceArgs R)
 {
     __shared__ double sd[5][256];
     __shared__ unsigned long long su[4][256];
     const int tid = threadIdx.x;
+    const Rep& rp = R.b.rep[blockIdx.x];
     double e3 = 0, w3 = 0, e2 = 0, w2 = 0, ke = 0;
     unsigned long long c3 = 0, i3 = 0, c2 = 0, v2 = 0;
-    for (long long q = tid; q < R.n_units; q += 256) {
+    for (long long q = rp.cell0 + tid; q < rp.cell0 + rp.g.ncell; q += 256) {
         e3 += R.unit_ew[2 * q];
         w3 += R.unit_ew[2 * q + 1];
         c3 += R.unit_cnt[2 * q];
         i3 += R.unit_cnt[2 * q + 1];
     }
-    for (long long q = tid; q < R.n_lj; q += 256) {
-        e2 += R.lj_ew[2 * q];
-        w2 += R.lj_ew[2 * q + 1];
-        c2 += R.lj_cnt[2 * q];
-        v2 += R.lj_cnt[2 * q + 1];
+    for (long long q = rp.mol0 + tid; q < rp.mol0 + rp.n; q += 256) {
+        e2 += R.mol_ew[2 * q];
+        w2 += R.mol_ew[2 * q + 1];
+        c2 += R.mol_cnt[2 * q];
+        v2 += R.mol_cnt[2 * q + 1];
+        ke += R.ke[q];
     }
-    for (long long q = tid; q < R.n_ke; q += 256) ke += R.ke_part[q];
     sd[0][tid] = e2; sd[1][tid] = e3; sd[2][tid] = w2; sd[3][tid] = w3; sd[4][tid] = ke;
     su[0][tid] = c3; su[1][tid] = i3; su[2][tid] = c2; su[3][tid] = v2;
     __syncthreads();
@@ -380,7 +367,7 @@ __global__ void __launch_bounds__(256) k_final_reduce(ReduceArgs R)
         __syncthreads();
     }
     if (tid == 0) {
-        ResultDev* r = R.out;
+        ResultDev* r = R.out + blockIdx.x;
         r->e2 = sd[0][0];
         r->e3 = sd[1][0];
         r->w2 = sd[2][0];
@@ -412,21 +399,22 @@ __global__ void k_gather_forces(long long n, const int* __restrict__ perm,
 
 static inline unsigned nblk(long long m, int b) { return (unsigned)((m + b - 1) / b); }
 
-cudaError_t launch_build_cells(const Grid& g, long long n, double* x, int* cell_of, int* rank,
-                               int* count, int* start, int* perm, double* xl, float* xl32,
-                               int* cell_sorted, int* maxocc, int* status, cudaStream_t st)
+cudaError_t launch_build_cells(const Batch& b, double* x, int* cell_of, int* rank, int* count,
+                               int* start, int* perm, double* xl, float* xl32, int* cell_sorted,
+                               int* maxocc, int* status, cudaStream_t st)
 {
-    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * (size_t)g.ncell, st);
+    const long long n = b.ntot;
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * (size_t)b.ncell, st);
     if (e != cudaSuccess) return e;
-    if (n > 0) k_wrap_bin<<<nblk(n, MD_BLOCK), MD_BLOCK, 0, st>>>(g, n, x, cell_of, rank, count, status);
-    k_scan<<<1, 1024, 0, st>>>(g.ncell, count, start, maxocc);
+    if (n > 0) k_wrap_bin<<<nblk(n, MD_BLOCK), MD_BLOCK, 0, st>>>(b, x, cell_of, rank, count, status);
+    k_scan<<<1, 1024, 0, st>>>(b.ncell, count, start, maxocc);
     e = cudaMemsetAsync(maxocc + 1, 0, 3 * sizeof(int), st);
     if (e != cudaSuccess) return e;
-    k_unit_max<<<nblk(g.ncell, MD_BLOCK), MD_BLOCK, 0, st>>>(g, start, maxocc + 1);
+    k_unit_max<<<nblk(b.ncell, MD_BLOCK), MD_BLOCK, 0, st>>>(b, start, maxocc + 1);
     if (n > 0) {
         k_scatter<<<nblk(n, MD_BLOCK), MD_BLOCK, 0, st>>>(n, cell_of, rank, start, perm);
-        k_cell_sort<<<nblk(g.ncell, MD_BLOCK), MD_BLOCK, 0, st>>>(g.ncell, start, perm);
-        k_local<<<nblk(n, MD_BLOCK), MD_BLOCK, 0, st>>>(g, n, x, perm, xl, xl32, cell_sorted);
+        k_cell_sort<<<nblk(b.ncell, MD_BLOCK), MD_BLOCK, 0, st>>>(b.ncell, start, perm);
+        k_local<<<nblk(n, MD_BLOCK), MD_BLOCK, 0, st>>>(b, x, perm, xl, xl32, cell_sorted);
     }
     return cudaGetLastError();
 }
@@ -435,26 +423,26 @@ cudaError_t launch_lj(int prec, const LjArgs<double>& a64, const LjArgs<float>& 
                       cudaStream_t st)
 {
     long long n = prec == 0 ? a64.n : a32.n;
-    unsigned b = nblk(n > 0 ? n : 1, LJ_BLOCK);
+    if (n <= 0) return cudaSuccess;
     if (prec == 0)
-        k_lj_owner<double><<<b, LJ_BLOCK, 0, st>>>(a64);
+        k_lj_owner<double><<<nblk(n, LJ_BLOCK), LJ_BLOCK, 0, st>>>(a64);
     else
-        k_lj_owner<float><<<b, LJ_BLOCK, 0, st>>>(a32);
+        k_lj_owner<float><<<nblk(n, LJ_BLOCK), LJ_BLOCK, 0, st>>>(a32);
     return cudaGetLastError();
 }
 
-cudaError_t launch_kick(long long n, const int* perm, const double* f_lj, const double* f_atm,
-                        double* x, double* v, double half_dt, double dt, int drift,
-                        double* ke_part, cudaStream_t st)
+cudaError_t launch_kick(const Batch& b, const int* perm, const double* f_lj, const double* f_atm,
+                        double* x, double* v, int drift, double* ke, cudaStream_t st)
 {
-    k_kick<<<nblk(n > 0 ? n : 1, MD_BLOCK), MD_BLOCK, 0, st>>>(n, perm, f_lj, f_atm, x, v, half_dt,
-                                                              dt, drift, ke_part);
+    if (b.ntot <= 0) return cudaSuccess;
+    k_kick<<<nblk(b.ntot, MD_BLOCK), MD_BLOCK, 0, st>>>(b, perm, f_lj, f_atm, x, v, drift, ke);
     return cudaGetLastError();
 }
 
-cudaError_t launch_kinetic(long long n, const double* v, double* ke_part, cudaStream_t st)
+cudaError_t launch_kinetic(long long n, const double* v, double* ke, cudaStream_t st)
 {
-    k_kinetic<<<nblk(n > 0 ? n : 1, MD_BLOCK), MD_BLOCK, 0, st>>>(n, v, ke_part);
+    if (n <= 0) return cudaSuccess;
+    k_kinetic<<<nblk(n, MD_BLOCK), MD_BLOCK, 0, st>>>(n, v, ke);
     return cudaGetLastError();
 }
 
@@ -467,7 +455,7 @@ cudaError_t launch_check_finite(long long m, const double* a, int* status, cudaS
 
 cudaError_t launch_final_reduce(const ReduceArgs& r, cudaStream_t st)
 {
-    k_final_reduce<<<1, 256, 0, st>>>(r);
+    k_final_reduce<<<(unsigned)r.b.R, 256, 0, st>>>(r);
     return cudaGetLastError();
 }
 
@@ -476,6 +464,14 @@ cudaError_t launch_gather_forces(long long n, const int* perm, const double* f_l
 {
     if (n <= 0) return cudaSuccess;
     k_gather_forces<<<nblk(n, MD_BLOCK), MD_BLOCK, 0, st>>>(n, perm, f_lj, f_atm, which, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_density(const Batch& b, const double* x, int axis, int nbins,
+                           unsigned long long* counts, cudaStream_t st)
+{
+    if (b.ntot <= 0) return cudaSuccess;
+    k_density<<<nblk(b.ntot, MD_BLOCK), MD_BLOCK, 0, st>>>(b, x, axis, nbins, counts);
     return cudaGetLastError();
 }
 

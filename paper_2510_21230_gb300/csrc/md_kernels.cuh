@@ -6,21 +6,15 @@ namespace atm3 {
 
 template <typename R>
 struct LjArgs {
-    Grid g;
-    long long n;
+    Batch b;
+    long long n;              // SoA stride = b.ntot
     const R* xl;              // sorted cell-local coordinates, SoA [3n]
+    const float* xl32;        // FP32 copy (prefilter of the FP64 path)
     const int* cell_start;    // [ncell + 1]
-    const int* cell_sorted;   // [n] cell of each sorted slot
+    const int* cell_sorted;   // [n] global cell of each sorted slot
     double* fs;               // sorted-order LJ force, SoA [3n] (fully written)
-    double* part_ew;          // [2 * blocks]: E2, W2 per block
-    unsigned long long* part_cnt;  // [2 * blocks]: candidates, visits
-    R w[3];
-    R rc2, sig2, eps4, eps24, eps48, ushift;
-    // FP64 path: FP32 prefilter of the cutoff test (FP32 coordinates, cell
-    // edges, and the band outside which the FP32 value decides; see atm_common.cuh)
-    const float* xl32;
-    float wf[3];
-    float p_lo, p_hi;
+    double* mol_ew;           // [2n] per sorted molecule: half of its pair energies, virials
+    unsigned* mol_cnt;        // [2n] per sorted molecule: half-shell candidates, visits
 };
 
 // device-side copy of atm_result (same layout)
@@ -30,33 +24,34 @@ struct ResultDev {
 };
 
 struct ReduceArgs {
+    Batch b;
     const double* unit_ew;
     const unsigned long long* unit_cnt;
-    long long n_units;
-    const double* lj_ew;
-    const unsigned long long* lj_cnt;
-    long long n_lj;
-    const double* ke_part;
-    long long n_ke;
-    ResultDev* out;
+    const double* mol_ew;
+    const unsigned* mol_cnt;
+    const double* ke;         // [n] kinetic energy per molecule
+    ResultDev* out;           // [R]
 };
 
 constexpr int LJ_BLOCK = 128;
 constexpr int MD_BLOCK = 256;
 
 // maxocc[0] = largest cell occupancy, maxocc[1..3] = largest unit of 3c01, 3c18, 3c08
-cudaError_t launch_build_cells(const Grid& g, long long n, double* x, int* cell_of, int* rank,
-                               int* count, int* start, int* perm, double* xl, float* xl32,
-                               int* cell_sorted, int* maxocc, int* status, cudaStream_t st);
+cudaError_t launch_build_cells(const Batch& b, double* x, int* cell_of, int* rank, int* count,
+                               int* start, int* perm, double* xl, float* xl32, int* cell_sorted,
+                               int* maxocc, int* status, cudaStream_t st);
 cudaError_t launch_lj(int prec, const LjArgs<double>& a64, const LjArgs<float>& a32,
                       cudaStream_t st);
-cudaError_t launch_kick(long long n, const int* perm, const double* f_lj, const double* f_atm,
-                        double* x, double* v, double half_dt, double dt, int drift,
-                        double* ke_part, cudaStream_t st);
-cudaError_t launch_kinetic(long long n, const double* v, double* ke_part, cudaStream_t st);
+cudaError_t launch_kick(const Batch& b, const int* perm, const double* f_lj, const double* f_atm,
+                        double* x, double* v, int drift, double* ke, cudaStream_t st);
+cudaError_t launch_kinetic(long long n, const double* v, double* ke, cudaStream_t st);
 cudaError_t launch_check_finite(long long m, const double* a, int* status, cudaStream_t st);
 cudaError_t launch_final_reduce(const ReduceArgs& r, cudaStream_t st);
 cudaError_t launch_gather_forces(long long n, const int* perm, const double* f_lj,
                                  const double* f_atm, int which, double* out, cudaStream_t st);
+// adds the histogram of coordinate `axis` (nbins equal bins over [0, L_axis))
+// of every replica's wrapped positions to counts[R * nbins]
+cudaError_t launch_density(const Batch& b, const double* x, int axis, int nbins,
+                           unsigned long long* counts, cudaStream_t st);
 
 }  // namespace atm3

@@ -31,19 +31,20 @@ namespace {
 constexpr size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 struct NaLayout {
-    size_t x, cell_of, rank, count, start, perm, cell_sorted, xl, xl32, f_lj, f_atm, unit_ew,
-        unit_cnt, lj_ew, lj_cnt, ke_part, res, status, maxocc, total;
+    size_t rep, rep_of_cell, rep_of_mol, x, cell_of, rank, count, start, perm, cell_sorted, xl,
+        xl32, f_lj, f_atm, unit_ew, unit_cnt, mol_ew, mol_cnt, ke, res, status, maxocc, total;
 };
 
 constexpr long long NA_N = ATM_NOALLOC_MAX_N;
 constexpr long long NA_C = ATM_NOALLOC_MAX_CELLS;
-constexpr long long NA_LJB = (NA_N + LJ_BLOCK - 1) / LJ_BLOCK;
-constexpr long long NA_KEB = (NA_N + MD_BLOCK - 1) / MD_BLOCK;
 
 constexpr NaLayout na_layout()
 {
     NaLayout L{};
     size_t o = 0;
+    L.rep = o;         o = al256(o + sizeof(Rep));
+    L.rep_of_cell = o; o = al256(o + NA_C * sizeof(int));
+    L.rep_of_mol = o;  o = al256(o + NA_N * sizeof(int));
     L.x = o;           o = al256(o + 3 * NA_N * sizeof(double));
     L.cell_of = o;     o = al256(o + NA_N * sizeof(int));
     L.rank = o;        o = al256(o + NA_N * sizeof(int));
@@ -57,9 +58,9 @@ constexpr NaLayout na_layout()
     L.f_atm = o;       o = al256(o + 3 * NA_N * sizeof(double));
     L.unit_ew = o;     o = al256(o + 2 * NA_C * sizeof(double));
     L.unit_cnt = o;    o = al256(o + 2 * NA_C * sizeof(unsigned long long));
-    L.lj_ew = o;       o = al256(o + 2 * NA_LJB * sizeof(double));
-    L.lj_cnt = o;      o = al256(o + 2 * NA_LJB * sizeof(unsigned long long));
-    L.ke_part = o;     o = al256(o + NA_KEB * sizeof(double));
+    L.mol_ew = o;      o = al256(o + 2 * NA_N * sizeof(double));
+    L.mol_cnt = o;     o = al256(o + 2 * NA_N * sizeof(unsigned));
+    L.ke = o;          o = al256(o + NA_N * sizeof(double));
     L.res = o;         o = al256(o + sizeof(ResultDev));
     L.status = o;      o = al256(o + sizeof(int));
     L.maxocc = o;      o = al256(o + 4 * sizeof(int));
@@ -68,7 +69,7 @@ constexpr NaLayout na_layout()
 }
 constexpr NaLayout NA = na_layout();
 
-// the scratch array (about 5.3 MB at the limits above)
+// the scratch array (about 6 MB at the limits above)
 __device__ __align__(256) unsigned char g_na_scratch[NA.total];
 
 constexpr int NA_MAX_DEVICES = 64;
@@ -106,31 +107,19 @@ extern "C" atm_status atm_compute_forces_noalloc(const atm_params* p, int64_t n,
         return ATM_E_INVALID;
     if (p->device < 0 || p->device >= NA_MAX_DEVICES) return ATM_E_INVALID;
     if (n > NA_N) return ATM_E_CAPACITY;
-    // linked-cell grid: n_d = largest k with L/k >= r_c, at least 3
-    Grid g;
-    long long ncell = 1;
-    for (int d = 0; d < 3; d++) {
-        double L = p->box[d], rc = p->rc;
-        if (!(L > 0.0) || !(rc > 0.0) || !std::isfinite(L) || !std::isfinite(rc))
-            return ATM_E_INVALID;
-        double k = std::floor(L / rc);
-        if (k < 1.0) k = 1.0;
-        while (L / (k + 1.0) >= rc) k += 1.0;
-        while (k > 0.0 && L / k < rc) k -= 1.0;
-        if (k < 3.0) return ATM_E_BOX_TOO_SMALL;
-        if (k > (double)NA_C) return ATM_E_CAPACITY;
-        g.nc[d] = (int)k;
-        g.L[d] = L;
-        g.w[d] = L / k;
-        ncell *= (long long)k;
-    }
-    if (ncell > NA_C) return ATM_E_CAPACITY;
-    g.ncell = ncell;
+    // the single system as a batch of one replica
+    Rep rp;
+    atm_status rs = make_rep(*p, n, 0, 0, rp);
+    if (rs != ATM_OK) return rs;
+    if (rp.g.ncell > NA_C) return ATM_E_CAPACITY;
 
     NA_CU(cudaSetDevice(p->device));
     unsigned char* base = nullptr;
     NA_CU(na_scratch(p->device, &base));
     cudaStream_t st = (cudaStream_t)p->cuda_stream;
+    Rep* d_rep = reinterpret_cast<Rep*>(base + NA.rep);
+    int* rep_of_cell = reinterpret_cast<int*>(base + NA.rep_of_cell);
+    int* rep_of_mol = reinterpret_cast<int*>(base + NA.rep_of_mol);
     double* x = reinterpret_cast<double*>(base + NA.x);
     int* cell_of = reinterpret_cast<int*>(base + NA.cell_of);
     int* rank = reinterpret_cast<int*>(base + NA.rank);
@@ -144,23 +133,34 @@ extern "C" atm_status atm_compute_forces_noalloc(const atm_params* p, int64_t n,
     double* f_atm = reinterpret_cast<double*>(base + NA.f_atm);
     double* unit_ew = reinterpret_cast<double*>(base + NA.unit_ew);
     unsigned long long* unit_cnt = reinterpret_cast<unsigned long long*>(base + NA.unit_cnt);
-    double* lj_ew = reinterpret_cast<double*>(base + NA.lj_ew);
-    unsigned long long* lj_cnt = reinterpret_cast<unsigned long long*>(base + NA.lj_cnt);
-    double* ke_part = reinterpret_cast<double*>(base + NA.ke_part);
+    double* mol_ew = reinterpret_cast<double*>(base + NA.mol_ew);
+    unsigned* mol_cnt = reinterpret_cast<unsigned*>(base + NA.mol_cnt);
+    double* ke = reinterpret_cast<double*>(base + NA.ke);
     ResultDev* res = reinterpret_cast<ResultDev*>(base + NA.res);
     int* status = reinterpret_cast<int*>(base + NA.status);
     int* maxocc = reinterpret_cast<int*>(base + NA.maxocc);
 
-    // positions are copied in (the cell build wraps them in place); the
-    // status word and the kinetic-energy partials start at zero
+    Batch b;
+    b.rep = d_rep;
+    b.rep_of_cell = rep_of_cell;
+    b.rep_of_mol = rep_of_mol;
+    b.R = 1;
+    b.ntot = n;
+    b.ncell = rp.g.ncell;
+
+    // replica descriptor and positions in (the cell build wraps positions in
+    // place); replica ids, the status word and the kinetic energies start at zero
     const size_t bytes3 = 3 * (size_t)n * sizeof(double);
-    if (bytes3) NA_CU(cudaMemcpyAsync(x, x_dev, bytes3, cudaMemcpyDeviceToDevice, st));
+    NA_CU(cudaMemcpyAsync(d_rep, &rp, sizeof(Rep), cudaMemcpyHostToDevice, st));
+    NA_CU(cudaMemsetAsync(rep_of_cell, 0, (size_t)b.ncell * sizeof(int), st));
+    if (n > 0) {
+        NA_CU(cudaMemsetAsync(rep_of_mol, 0, (size_t)n * sizeof(int), st));
+        NA_CU(cudaMemsetAsync(ke, 0, (size_t)n * sizeof(double), st));
+        NA_CU(cudaMemcpyAsync(x, x_dev, bytes3, cudaMemcpyDeviceToDevice, st));
+    }
     NA_CU(cudaMemsetAsync(status, 0, sizeof(int), st));
-    const long long n_lj = (n + LJ_BLOCK - 1) / LJ_BLOCK > 0 ? (n + LJ_BLOCK - 1) / LJ_BLOCK : 1;
-    const long long n_ke = (n + MD_BLOCK - 1) / MD_BLOCK > 0 ? (n + MD_BLOCK - 1) / MD_BLOCK : 1;
-    NA_CU(cudaMemsetAsync(ke_part, 0, (size_t)n_ke * sizeof(double), st));
     if (n > 0) NA_CU(launch_check_finite(3 * n, x, status, st));
-    NA_CU(launch_build_cells(g, n, x, cell_of, rank, count, start, perm, xl, xl32, cell_sorted,
+    NA_CU(launch_build_cells(b, x, cell_of, rank, count, start, perm, xl, xl32, cell_sorted,
                              maxocc, status, st));
     int hocc[4] = {0, 0, 0, 0}, hstat = 0;
     NA_CU(cudaMemcpyAsync(hocc, maxocc, sizeof(hocc), cudaMemcpyDeviceToHost, st));
@@ -170,29 +170,28 @@ extern "C" atm_status atm_compute_forces_noalloc(const atm_params* p, int64_t n,
 
     // LJ pairs and ATM triplets (staged-molecule capacity = largest unit of the traversal)
     ForceJob j;
-    j.g = g;
-    j.n = n;
+    j.b = b;
+    j.rep_host = &rp;
     j.xl = xl;
     j.xl32 = xl32;
     j.start = start;
     j.cell_sorted = cell_sorted;
     j.f_lj = f_lj;
     j.f_atm = f_atm;
-    j.lj_ew = lj_ew;
-    j.lj_cnt = lj_cnt;
+    j.mol_ew = mol_ew;
+    j.mol_cnt = mol_cnt;
     j.unit_ew = unit_ew;
     j.unit_cnt = unit_cnt;
     j.status = status;
-    j.rc = p->rc;
-    j.nu = p->nu;
-    j.lj_eps = p->lj_eps;
-    j.lj_sigma = p->lj_sigma;
-    j.lj_shift = p->lj_shift;
+    j.work = nullptr;
     j.trav = trav;
     j.trunc = trunc;
     j.prec = prec;
     j.mcap = hocc[1 + trav] > 0 ? hocc[1 + trav] : 1;
     NA_CU(cudaDeviceGetAttribute(&j.optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
+    j.sms = 0;
+    j.persistent = 0;
+    j.nwarps = 0;
     j.st = st;
     NA_CU(enqueue_lj(j));
     bool capacity = false;
@@ -202,14 +201,12 @@ extern "C" atm_status atm_compute_forces_noalloc(const atm_params* p, int64_t n,
 
     // scalars, then the total force in the caller's order
     ReduceArgs r;
+    r.b = b;
     r.unit_ew = unit_ew;
     r.unit_cnt = unit_cnt;
-    r.n_units = g.ncell;
-    r.lj_ew = lj_ew;
-    r.lj_cnt = lj_cnt;
-    r.n_lj = n_lj;
-    r.ke_part = ke_part;
-    r.n_ke = n_ke;
+    r.mol_ew = mol_ew;
+    r.mol_cnt = mol_cnt;
+    r.ke = ke;
     r.out = res;
     NA_CU(launch_final_reduce(r, st));
     if (n > 0) NA_CU(launch_gather_forces(n, perm, f_lj, f_atm, 0, f_dev, st));

@@ -1,0 +1,162 @@
+"""Batches of independent replicas, launch options, autotuning and the density
+profile, through the C ABI.
+
+A batch must give, replica by replica, exactly what separate single-system
+runs give (counts bit-exact, forces within the parity tolerances), whatever
+the launch form (one CTA per unit or persistent, 4 or 8 warps, CUDA-graph
+steps).  The density profile is an integer histogram and must equal the
+histogram of the wrapped positions bit for bit.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2510_21230_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+NU = 0.073
+RTOL = {"fp64": 1e-10, "fp32c": 2e-5}
+ORC_PREC = {"fp64": "fp64", "fp32c": "fp32"}
+
+
+@pytest.fixture(scope="module")
+def atm3():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_21230_gb300 import atm3 as m, build
+    build.build()
+    return m
+
+
+def close(got, ref, rtol):
+    scale = np.sqrt(np.mean(ref * ref)) if ref.size else 0.0
+    return np.all(np.abs(got - ref) <= rtol * np.abs(ref) + rtol * scale)
+
+
+@pytest.fixture(scope="module")
+def ensemble():
+    """Six replicas with uneven N, density and temperature (the batched-ensemble recipe)."""
+    return synth.replicas(count=6, n_lo=500, n_hi=3000)
+
+
+def _concat(reps, key):
+    return np.ascontiguousarray(np.concatenate([r[key] for r in reps], axis=1))
+
+
+@pytest.mark.parametrize("trav,trunc,prec", [("3c08", "pair", "fp32c"), ("3c18", "pair", "fp64"),
+                                             ("3c08", "product", "fp64"), ("3c01", "pair", "fp32c")])
+def test_batch_equals_separate_runs(atm3, ensemble, trav, trunc, prec):
+    ns = [r["n"] for r in ensemble]
+    boxes = [r["box"] for r in ensemble]
+    x = _concat(ensemble, "x")
+    with atm3.AtmSystem(boxes, ns, nu=NU) as b:
+        b.set_state(x)
+        b.build_cells()
+        b.compute_forces(trav, trunc, prec)
+        res = b.results()
+        f = b.get_forces("total")
+    off = 0
+    for r, rep in enumerate(ensemble):
+        with atm3.AtmSystem(rep["box"], rep["n"], nu=NU) as s:
+            s.set_state(rep["x"])
+            s.build_cells()
+            one = s.compute_forces(trav, trunc, prec)
+            f1 = s.get_forces("total")
+        for k in ("n_cand3", "n_int3", "n_cand2", "n_int2"):
+            assert res[r][k] == one[k], (r, k)
+        for k in ("e2", "e3", "w2", "w3"):
+            assert res[r][k] == pytest.approx(one[k], rel=RTOL[prec], abs=1e-12), (r, k)
+        assert close(f[:, off:off + rep["n"]], f1, RTOL[prec]), r
+        off += rep["n"]
+
+
+def test_batch_matches_oracle(atm3, ensemble):
+    ns = [r["n"] for r in ensemble]
+    with atm3.AtmSystem([r["box"] for r in ensemble], ns, nu=NU) as b:
+        b.set_state(_concat(ensemble, "x"))
+        b.build_cells()
+        b.compute_forces("3c08", "pair", "fp64")
+        res = b.results()
+        f = b.get_forces("atm")
+    off = 0
+    for r, rep in enumerate(ensemble):
+        ref = oracle.atm_cells(oracle.params(rep["box"], 2.5, NU), rep["x"], "3c08", "pair")
+        assert res[r]["n_int3"] == ref["n_int3"] and res[r]["n_cand3"] == ref["n_cand3"]
+        assert res[r]["e3"] == pytest.approx(ref["e3"], rel=1e-10)
+        assert close(f[:, off:off + rep["n"]], ref["f"], 1e-10)
+        off += rep["n"]
+
+
+@pytest.mark.parametrize("persistent,nwarps", [(True, 0), (False, 8), (True, 8), (True, 4)])
+def test_launch_forms_agree(atm3, ensemble, persistent, nwarps):
+    ns = [r["n"] for r in ensemble]
+    x = _concat(ensemble, "x")
+    out = []
+    for opts in [dict(), dict(persistent=persistent, nwarps=nwarps)]:
+        with atm3.AtmSystem([r["box"] for r in ensemble], ns, nu=NU) as b:
+            if opts:
+                b.set_options(**opts)
+            b.set_state(x)
+            b.build_cells()
+            b.compute_forces("3c08", "pair", "fp32c")
+            out.append((b.results(), b.get_forces("total")))
+    # FP32 pair scalars are summed by shared-memory atomics whose order depends
+    # on warp scheduling: the FP32C tolerance applies between launch forms
+    for ra, rb in zip(out[0][0], out[1][0]):
+        assert ra["n_int3"] == rb["n_int3"] and ra["n_cand3"] == rb["n_cand3"]
+        assert rb["e3"] == pytest.approx(ra["e3"], rel=RTOL["fp32c"])
+    assert close(out[1][1], out[0][1], RTOL["fp32c"])
+
+
+def test_graph_steps_equal_plain_steps(atm3, ensemble):
+    ns = [r["n"] for r in ensemble]
+    x, v = _concat(ensemble, "x"), _concat(ensemble, "v")
+    final = []
+    for graph in (False, True):
+        with atm3.AtmSystem([r["box"] for r in ensemble], ns, nu=NU, dt=0.002) as b:
+            b.set_options(graph=graph)
+            b.set_state(x, v)
+            b.step(8, "3c08", "pair", "fp64")
+            res = b.results()
+            xs, vs = b.get_state()
+            final.append((res, xs, vs))
+    (ra, xa, va), (rb, xb, vb) = final
+    for a, c in zip(ra, rb):
+        assert a["n_int3"] == c["n_int3"]
+        assert c["e3"] == pytest.approx(a["e3"], rel=1e-9)
+    assert np.abs(xa - xb).max() < 1e-10 and np.abs(va - vb).max() < 1e-9
+
+
+def test_autotune_keeps_results(atm3, ensemble):
+    ns = [r["n"] for r in ensemble]
+    with atm3.AtmSystem([r["box"] for r in ensemble], ns, nu=NU) as b:
+        b.set_state(_concat(ensemble, "x"))
+        b.build_cells()
+        b.compute_forces("3c08", "pair", "fp32c")
+        before = b.results()
+        t = b.autotune("3c08", "pair", "fp32c", reps=2)
+        assert t["persistent"] in (0, 1) and t["nwarps"] in (4, 8) and t["ms_per_eval"] > 0
+        b.compute_forces("3c08", "pair", "fp32c")
+        after = b.results()
+    for a, c in zip(before, after):
+        assert a["n_int3"] == c["n_int3"]
+        assert c["e3"] == pytest.approx(a["e3"], rel=RTOL["fp32c"])
+
+
+def test_density_profile_is_the_histogram_of_wrapped_positions(atm3):
+    cfg = synth.slab(box=(12.0, 12.0, 40.0), thickness=12.0, seed=3001)
+    nb = 600
+    with atm3.AtmSystem(cfg["box"], cfg["n"], nu=NU) as s:
+        s.set_state(cfg["x"], cfg["v"])
+        s.build_cells()
+        s.density_accumulate(2, nb)
+        counts, samples = s.density_get(nb)
+        xw, _ = s.get_state()
+    h = cfg["box"][2] / nb
+    b = np.clip(np.floor(xw[2] / h).astype(np.int64), 0, nb - 1)
+    ref = np.bincount(b, minlength=nb)
+    assert samples == 1
+    assert np.array_equal(counts[0].astype(np.int64), ref)
+    assert counts.sum() == cfg["n"]
