@@ -219,7 +219,7 @@ atm_status atm_density_reset(atm_ctx* ctx);
  * allocator must not be touched after start-up.  It does what atm_create +
  * atm_set_state_dev + atm_build_cells + atm_compute_forces + atm_get_forces_dev
  * (which = 0) do for one set of positions, but allocates nothing: every
- * intermediate array lives in one fixed __device__ array of about 5.3 MB that
+ * intermediate array lives in one fixed __device__ array of about 6.7 MB that
  * this library reserves on every GPU it is loaded on, until the process exits.
  *
  *   params  box, rc, nu, LJ parameters, device, cuda_stream (dt is unused)

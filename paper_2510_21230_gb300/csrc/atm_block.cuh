@@ -660,7 +660,7 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
 // One CTA per unit, or (A.work set) a persistent grid whose CTAs take units
 // from a global counter until all units of the batch are done.
 template <int TRAV, int TRUNC, typename R>
-__global__ void __launch_bounds__(256) atm_block_kernel(const AtmArgs<R> A)
+__global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : 4) atm_block_kernel(const AtmArgs<R> A)
 {
     if (A.work == nullptr) {
         atm_block_unit<TRAV, TRUNC, R>(A, blockIdx.x);

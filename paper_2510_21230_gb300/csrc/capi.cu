@@ -52,6 +52,7 @@ struct atm_ctx {
     unsigned* mol_cnt = nullptr;
     double* ke = nullptr;
     ResultDev* d_res = nullptr;  // [R]
+    ResultDev* d_part = nullptr; // [R * REDUCE_PARTS] partial sums
     ResultDev* h_res = nullptr;  // [R] pinned
     int* d_status = nullptr;
     int* h_status = nullptr;
@@ -163,7 +164,7 @@ static void free_all(atm_ctx* c)
     void* dev[] = {c->d_rep, c->d_rep_of_cell, c->d_rep_of_mol, c->x, c->v, c->x0, c->v0, c->xl,
                    c->xl32, c->cell_of, c->rank, c->count, c->start, c->perm, c->cell_sorted,
                    c->f_lj, c->f_atm, c->f_out, c->unit_ew, c->unit_cnt, c->mol_ew, c->mol_cnt,
-                   c->ke, c->d_res, c->d_status, c->d_maxocc, c->d_work, c->d_dens};
+                   c->ke, c->d_res, c->d_part, c->d_status, c->d_maxocc, c->d_work, c->d_dens};
     for (void* p : dev)
         if (p) cudaFree(p);
     if (c->h_res) cudaFreeHost(c->h_res);
@@ -269,6 +270,7 @@ extern "C" atm_status atm_batch_create(const atm_params* params, const int64_t* 
     ok = ok && alloc((void**)&c->mol_cnt, 2 * N * sizeof(unsigned));
     ok = ok && alloc((void**)&c->ke, N * sizeof(double));
     ok = ok && alloc((void**)&c->d_res, nrep * sizeof(ResultDev));
+    ok = ok && alloc((void**)&c->d_part, (size_t)nrep * REDUCE_PARTS * sizeof(ResultDev));
     ok = ok && alloc((void**)&c->d_status, sizeof(int));
     ok = ok && alloc((void**)&c->d_maxocc, 4 * sizeof(int));
     ok = ok && alloc((void**)&c->d_work, sizeof(int));
@@ -513,11 +515,12 @@ static atm_status enqueue_reduce(atm_ctx* c)
     r.mol_ew = c->mol_ew;
     r.mol_cnt = c->mol_cnt;
     r.ke = c->ke;
+    r.part = c->d_part;
     r.out = c->d_res;
     cudaEvent_t ev = prof_begin(c);
     CU(launch_final_reduce(r, c->st));
     prof_end(c, PK_MD, ev);
-    c->n_launch += 1;
+    c->n_launch += 2;
     CU(cudaMemcpyAsync(c->h_res, c->d_res, c->R * sizeof(ResultDev), cudaMemcpyDeviceToHost, c->st));
     return ATM_OK;
 }

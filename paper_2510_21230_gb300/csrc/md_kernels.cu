@@ -333,23 +333,30 @@ __global__ void k_density(Batch B, const double* __restrict__ x, int axis, int n
 
 // ---------------------------------------------------------------- reductions
 
-// One CTA per replica sums every partial of its units and molecules in a
-// fixed order (thread-strided, then a fixed tree): reproducible scalars.
-__global__ void __launch_bounds__(256) k_final_reduce(ReduceArgs R)
+// Two-level reduction in a fixed order (reproducible scalars).  Level 1: CTA
+// (r, k) sums the k-th of REDUCE_PARTS equal slices of replica r's units and
+// molecules (thread-strided, then a fixed tree).  Level 2: one thread per
+// replica adds the REDUCE_PARTS partial sums in order.
+__global__ void __launch_bounds__(256) k_partial_reduce(ReduceArgs R)
 {
     __shared__ double sd[5][256];
     __shared__ unsigned long long su[4][256];
     const int tid = threadIdx.x;
-    const Rep& rp = R.b.rep[blockIdx.x];
+    const int r = blockIdx.x / REDUCE_PARTS, k = blockIdx.x % REDUCE_PARTS;
+    const Rep& rp = R.b.rep[r];
+    const long long cu = (rp.g.ncell + REDUCE_PARTS - 1) / REDUCE_PARTS;
+    const long long cm = (rp.n + REDUCE_PARTS - 1) / REDUCE_PARTS;
+    const long long u0 = rp.cell0 + k * cu, u1 = min(rp.cell0 + rp.g.ncell, u0 + cu);
+    const long long m0 = rp.mol0 + k * cm, m1 = min(rp.mol0 + rp.n, m0 + cm);
     double e3 = 0, w3 = 0, e2 = 0, w2 = 0, ke = 0;
     unsigned long long c3 = 0, i3 = 0, c2 = 0, v2 = 0;
-    for (long long q = rp.cell0 + tid; q < rp.cell0 + rp.g.ncell; q += 256) {
+    for (long long q = u0 + tid; q < u1; q += 256) {
         e3 += R.unit_ew[2 * q];
         w3 += R.unit_ew[2 * q + 1];
         c3 += R.unit_cnt[2 * q];
         i3 += R.unit_cnt[2 * q + 1];
     }
-    for (long long q = rp.mol0 + tid; q < rp.mol0 + rp.n; q += 256) {
+    for (long long q = m0 + tid; q < m1; q += 256) {
         e2 += R.mol_ew[2 * q];
         w2 += R.mol_ew[2 * q + 1];
         c2 += R.mol_cnt[2 * q];
@@ -367,17 +374,38 @@ __global__ void __launch_bounds__(256) k_final_reduce(ReduceArgs R)
         __syncthreads();
     }
     if (tid == 0) {
-        ResultDev* r = R.out + blockIdx.x;
-        r->e2 = sd[0][0];
-        r->e3 = sd[1][0];
-        r->w2 = sd[2][0];
-        r->w3 = sd[3][0];
-        r->ekin = sd[4][0];
-        r->n_cand3 = su[0][0];
-        r->n_int3 = su[1][0];
-        r->n_cand2 = su[2][0];
-        r->n_int2 = su[3][0] / 2;
+        ResultDev* p = R.part + blockIdx.x;
+        p->e2 = sd[0][0];
+        p->e3 = sd[1][0];
+        p->w2 = sd[2][0];
+        p->w3 = sd[3][0];
+        p->ekin = sd[4][0];
+        p->n_cand3 = su[0][0];
+        p->n_int3 = su[1][0];
+        p->n_cand2 = su[2][0];
+        p->n_int2 = su[3][0];
     }
+}
+
+__global__ void k_final_reduce(ReduceArgs R)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R.b.R) return;
+    ResultDev t{};
+    for (int k = 0; k < REDUCE_PARTS; k++) {
+        const ResultDev& p = R.part[r * REDUCE_PARTS + k];
+        t.e2 += p.e2;
+        t.e3 += p.e3;
+        t.w2 += p.w2;
+        t.w3 += p.w3;
+        t.ekin += p.ekin;
+        t.n_cand3 += p.n_cand3;
+        t.n_int3 += p.n_int3;
+        t.n_cand2 += p.n_cand2;
+        t.n_int2 += p.n_int2;
+    }
+    t.n_int2 /= 2;  // each pair was visited from both ends
+    R.out[r] = t;
 }
 
 // gather sorted-order forces to the original order: which 0 total, 1 LJ, 2 ATM
@@ -455,7 +483,8 @@ cudaError_t launch_check_finite(long long m, const double* a, int* status, cudaS
 
 cudaError_t launch_final_reduce(const ReduceArgs& r, cudaStream_t st)
 {
-    k_final_reduce<<<(unsigned)r.b.R, 256, 0, st>>>(r);
+    k_partial_reduce<<<(unsigned)(r.b.R * REDUCE_PARTS), 256, 0, st>>>(r);
+    k_final_reduce<<<nblk(r.b.R, 128), 128, 0, st>>>(r);
     return cudaGetLastError();
 }
 

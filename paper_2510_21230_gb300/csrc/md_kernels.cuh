@@ -30,8 +30,11 @@ struct ReduceArgs {
     const double* mol_ew;
     const unsigned* mol_cnt;
     const double* ke;         // [n] kinetic energy per molecule
+    ResultDev* part;          // [R * REDUCE_PARTS] partial sums
     ResultDev* out;           // [R]
 };
+
+constexpr int REDUCE_PARTS = 64;  // partial sums per replica of the two-level reduction
 
 constexpr int LJ_BLOCK = 128;
 constexpr int MD_BLOCK = 256;

@@ -61,7 +61,7 @@ constexpr NaLayout na_layout()
     L.mol_ew = o;      o = al256(o + 2 * NA_N * sizeof(double));
     L.mol_cnt = o;     o = al256(o + 2 * NA_N * sizeof(unsigned));
     L.ke = o;          o = al256(o + NA_N * sizeof(double));
-    L.res = o;         o = al256(o + sizeof(ResultDev));
+    L.res = o;         o = al256(o + (1 + REDUCE_PARTS) * sizeof(ResultDev));
     L.status = o;      o = al256(o + sizeof(int));
     L.maxocc = o;      o = al256(o + 4 * sizeof(int));
     L.total = o;
@@ -69,7 +69,7 @@ constexpr NaLayout na_layout()
 }
 constexpr NaLayout NA = na_layout();
 
-// the scratch array (about 6 MB at the limits above)
+// the scratch array (about 6.7 MB at the limits above)
 __device__ __align__(256) unsigned char g_na_scratch[NA.total];
 
 constexpr int NA_MAX_DEVICES = 64;
@@ -207,6 +207,7 @@ extern "C" atm_status atm_compute_forces_noalloc(const atm_params* p, int64_t n,
     r.mol_ew = mol_ew;
     r.mol_cnt = mol_cnt;
     r.ke = ke;
+    r.part = res + 1;
     r.out = res;
     NA_CU(launch_final_reduce(r, st));
     if (n > 0) NA_CU(launch_gather_forces(n, perm, f_lj, f_atm, 0, f_dev, st));
