@@ -47,6 +47,33 @@ FP64_FLOPS_PER_CLK_SM = 1.25e12 / (SMS * 2.07e9)
 # gradient scalars, energy and virial 9, force vectors 27 (3c01: 9).
 F3 = {"3c01": 109.0, "3c18": 127.0, "3c08": 127.0}
 
+# DRAM traffic per launch of the ATM kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum from one ncu capture), keyed by (traversal, truncation,
+# precision, workload), with the sha256 prefix of the kernel sources it was
+# taken from: a changed kernel reports null until it is captured again.
+# liquid_n256k is the N = 32,000 capture (2197 units) scaled to 19683 units.
+KERNEL_SOURCES = ["atm3_internal.cuh", "atm_common.cuh", "atm_block.cuh", "atm_owner.cuh",
+                  "atm_fp32.cu", "atm_fp64.cu"]
+TRAFFIC = {("3c08", "pair", "fp32c", "liquid_n256k"): (11.36e6, "c5b8b90152c4aeb0"),
+           ("3c08", "pair", "fp32c", "liquid_n32k"): (1.268e6, "c5b8b90152c4aeb0")}
+
+
+def kernel_hash():
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2510_21230_gb300", "csrc")
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(trav, trunc, prec, workload):
+    t = TRAFFIC.get((trav, trunc, prec, workload))
+    if t is None or t[1] != kernel_hash():
+        return None
+    return t[0]
+
 
 def parse():
     p = argparse.ArgumentParser()
@@ -61,6 +88,7 @@ def parse():
     p.add_argument("--no-variants", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--no-tune", action="store_true", help="skip the launch-form autotuner")
     return p.parse_args()
 
 
@@ -164,6 +192,12 @@ def run_ours(args):
     sysm = atm3.AtmSystem(cfg["box"], n, rc=RC, nu=NU, dt=0.002, device=local,
                           stream=stream.cuda_stream)
     sysm.set_state(cfg["x"], cfg["v"])
+    tuning = None
+    if not args.no_tune:
+        # the library's autotuner picks the launch form (one CTA per unit or
+        # persistent, warps per CTA) for the measured combination
+        sysm.build_cells()
+        tuning = sysm.autotune(args.trav, args.trunc, args.prec, reps=3)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def timed(trav, trunc, prec, steps, warmup, clocks=None):
@@ -213,7 +247,8 @@ def run_ours(args):
     peak = SMS * per_clk * sm_max * 1e6 / 1e12
     achieved = flops / (atm_ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak,
+                "traffic": traffic_for(args.trav, args.trunc, args.prec, args.workload),
                 "kernel": ("atm_owner_kernel<%s,%s,%s>" if args.trav == "3c01" else "atm_block_kernel<%s,%s,%s>") % (args.trav, args.trunc, args.prec),
                 "peak_source": "derived: %d SMs x %.2f flops/clk x %.0f MHz (%s pipe)"
                                % (SMS, per_clk, sm_max, "FP32" if args.prec == "fp32c" else "FP64"),
@@ -291,7 +326,8 @@ def run_ours(args):
                        "traversal": args.trav, "truncation": args.trunc,
                        "precision": args.prec, "dt": 0.002, "integrator": "velocity Verlet NVE",
                        "parallelism": "replicas" if ws > 1 else "single GPU",
-                       "l2": "flushed between timed steps (256 MiB write, untimed)"},
+                       "l2": "flushed between timed steps (256 MiB write, untimed)",
+                       "launch": tuning or "default (one CTA per unit)"},
             "mups_3body": mups_3body,
             "roofline": roofline,
             "cpu_baseline": cpu,
