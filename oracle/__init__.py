@@ -1,8 +1,9 @@
-"""CPU oracle for the ATM linked-cell method (arXiv 2510.21230).
+"""CPU oracle for the ATM linked-cell method (arXiv 2510.21230) and for the
+learned force surrogate that can stand in for its triplet sum.
 
 TEST INFRASTRUCTURE ONLY.  Only the tests, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py`` may import this package.  It wraps the plain C
-oracle in ``atm_oracle.c`` through ctypes and shares nothing with the CUDA
+oracles in ``atm_oracle.c`` and ``sur_oracle.c`` through ctypes and shares nothing with the CUDA
 library.
 
 Every array argument is a NumPy array; 3-vectors are SoA ``[3, n]`` (x row,
@@ -15,7 +16,8 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "atm_oracle.c")
+_SRCS = [os.path.join(_HERE, "atm_oracle.c"), os.path.join(_HERE, "sur_oracle.c")]
+_HDRS = [os.path.join(_HERE, "atm_oracle.h"), os.path.join(_HERE, "sur_oracle.h")]
 _LIB = os.path.join(_HERE, "libatm_oracle.so")
 
 TRAV = {"3c01": 0, "3c18": 1, "3c08": 2}
@@ -28,10 +30,11 @@ GCC_FLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=o
 
 def build(force=False):
     """Compile the oracle with gcc (no contraction of multiply-adds)."""
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(f) for f in _SRCS + _HDRS)
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= newest:
         return _LIB
     tmp = _LIB + ".%d.tmp" % os.getpid()
-    subprocess.check_call(["gcc", *GCC_FLAGS, "-o", tmp, _SRC, "-lm"])
+    subprocess.check_call(["gcc", *GCC_FLAGS, "-o", tmp, *_SRCS, "-lm"])
     os.replace(tmp, _LIB)
     return _LIB
 
@@ -70,6 +73,22 @@ def lib():
         L.orc_md_run.argtypes = [P, i64, P, P, ci, d, ci, ci, ci, P, P]
         L.orc_num_threads.restype = ci
         L.orc_num_threads.argtypes = []
+        L.orc_sur_basis.restype = None
+        L.orc_sur_basis.argtypes = [d, P, P, P, P]
+        L.orc_sur_fcut.restype = d
+        L.orc_sur_fcut.argtypes = [d, d]
+        L.orc_sur_descriptors.restype = ci
+        L.orc_sur_descriptors.argtypes = [P, P, i64, P, i64, P, P]
+        L.orc_bf16.restype = d
+        L.orc_bf16.argtypes = [d]
+        L.orc_sur_mlp.restype = None
+        L.orc_sur_mlp.argtypes = [P, P, P, i64, P, P, ci, P, P]
+        L.orc_sur_loss_grad.restype = None
+        L.orc_sur_loss_grad.argtypes = [P, P, P, i64, P, P, P, d, P, P]
+        L.orc_sur_adam.restype = None
+        L.orc_sur_adam.argtypes = [P, P, P, P, i64, i64, d, d, d, d]
+        L.orc_sur_stats.restype = None
+        L.orc_sur_stats.argtypes = [i64, P, P, P, P, P]
         _lib = L
     return _lib
 
@@ -207,3 +226,86 @@ def md_run(prm, x, v, nsteps, dt, trav="3c18", trunc="pair", prec="fp64"):
 
 def num_threads():
     return lib().orc_num_threads()
+
+
+# ---------------------------------------------------------------- surrogate
+
+SUR_ND, SUR_NH, SUR_NO, SUR_NV = 32, 64, 3, 9
+SUR_NP = SUR_ND * SUR_NH + SUR_NH + SUR_NH * SUR_NH + SUR_NH + SUR_NH * SUR_NO + SUR_NO
+
+
+def sur_basis(rc):
+    mu_g = np.zeros(16)
+    mu_v = np.zeros(4)
+    eg = np.zeros(1)
+    ev = np.zeros(1)
+    lib().orc_sur_basis(rc, _p(mu_g), _p(eg), _p(mu_v), _p(ev))
+    return mu_g, float(eg[0]), mu_v, float(ev[0])
+
+
+def sur_fcut(r, rc):
+    return lib().orc_sur_fcut(r, rc)
+
+
+def sur_descriptors(prm, x, rows=None):
+    """Descriptors ``[nrows, 32]`` and vectors ``[nrows, 9]`` (v_0, v_1, v_2) of
+    the molecules ``rows`` (default all), brute force over all molecules."""
+    x = _soa(x)
+    n = x.shape[1]
+    r = np.arange(n, dtype=np.int64) if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
+    D = np.zeros((r.size, SUR_ND))
+    V = np.zeros((r.size, SUR_NV))
+    st = lib().orc_sur_descriptors(_p(prm), _p(x), n, _p(r), r.size, _p(D), _p(V))
+    if st != 0:
+        raise OracleError("surrogate descriptors need rc > 0.8 and every box side >= 2 rc")
+    return D, V
+
+
+def bf16(x):
+    return lib().orc_bf16(float(x))
+
+
+def sur_mlp(P, mean, scale, D, V, bf16_=False):
+    """MLP weights ``w [n, 3]`` and forces ``F [n, 3]`` (row per molecule)."""
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    assert P.size == SUR_NP
+    mean = np.ascontiguousarray(mean, dtype=np.float64)
+    scale = np.ascontiguousarray(scale, dtype=np.float64)
+    D = np.ascontiguousarray(D, dtype=np.float64).reshape(-1, SUR_ND)
+    V = np.ascontiguousarray(V, dtype=np.float64).reshape(-1, SUR_NV)
+    n = D.shape[0]
+    w = np.zeros((n, SUR_NO))
+    F = np.zeros((n, 3))
+    lib().orc_sur_mlp(_p(P), _p(mean), _p(scale), n, _p(D), _p(V), 1 if bf16_ else 0, _p(w), _p(F))
+    return w, F
+
+
+def sur_loss_grad(P, mean, scale, D, V, Fref, sigma2):
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    mean = np.ascontiguousarray(mean, dtype=np.float64)
+    scale = np.ascontiguousarray(scale, dtype=np.float64)
+    D = np.ascontiguousarray(D, dtype=np.float64).reshape(-1, SUR_ND)
+    V = np.ascontiguousarray(V, dtype=np.float64).reshape(-1, SUR_NV)
+    Fref = np.ascontiguousarray(Fref, dtype=np.float64).reshape(-1, 3)
+    n = D.shape[0]
+    loss = np.zeros(1)
+    g = np.zeros(SUR_NP)
+    lib().orc_sur_loss_grad(_p(P), _p(mean), _p(scale), n, _p(D), _p(V), _p(Fref), sigma2,
+                            _p(loss), _p(g))
+    return float(loss[0]), g
+
+
+def sur_adam(P, m, v, g, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam step in place on float64 arrays P, m, v."""
+    lib().orc_sur_adam(_p(P), _p(m), _p(v), _p(np.ascontiguousarray(g, dtype=np.float64)),
+                       P.size, t, lr, beta1, beta2, eps)
+
+
+def sur_stats(D, F):
+    D = np.ascontiguousarray(D, dtype=np.float64).reshape(-1, SUR_ND)
+    F = np.ascontiguousarray(F, dtype=np.float64).reshape(-1, 3)
+    mean = np.zeros(SUR_ND)
+    scale = np.zeros(SUR_ND)
+    s2 = np.zeros(1)
+    lib().orc_sur_stats(D.shape[0], _p(D), _p(F), _p(mean), _p(scale), _p(s2))
+    return mean, scale, float(s2[0])
