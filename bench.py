@@ -89,6 +89,12 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-tune", action="store_true", help="skip the launch-form autotuner")
+    p.add_argument("--no-surrogate", action="store_true", help="skip the surrogate variant")
+    p.add_argument("--sur-frames", type=int, default=1000,
+                   help="training frames of each of the N=1000 and N=32,000 liquids")
+    p.add_argument("--sur-stride", type=int, default=10, help="MD steps between frames")
+    p.add_argument("--sur-steps", type=int, default=20000, help="Adam steps")
+    p.add_argument("--sur-batch", type=int, default=8192, help="rows per Adam step")
     return p.parse_args()
 
 
@@ -286,6 +292,42 @@ def run_ours(args):
                              "atm_ms_per_launch": am, "mups_3body": n / (am * 1e-3),
                              "n_int3": r["res"]["n_int3"]})
 
+    # learned surrogate: trained on exact forces of smaller liquids, then
+    # timed and checked on this workload's state
+    surrogate = None
+    if not args.no_surrogate and rank == 0:
+        P, mean, scale, info = train_surrogate(atm3, args, local, stream.cuda_stream)
+        sysm.surrogate_set_model(P, mean, scale)
+        sysm.build_cells()
+        sysm.compute_forces("3c08", "pair", "fp64")
+        f64 = sysm.get_forces("atm")
+        sysm.compute_forces("3c08", "pair", "surrogate")
+        fsur = sysm.get_forces("atm")
+        scale_f = float(np.sqrt(np.mean(f64 ** 2)))
+        d = fsur - f64
+        # surrogate kernel alone (no exact steps), then the amortised step with
+        # the exact FP32C traversal every 50 steps
+        sysm.surrogate_options(exact_every=0)
+        r0 = timed("3c08", "pair", "surrogate", 10, 3)
+        sm = r0["prof"]["ms_atm"] / max(1, r0["prof"]["n_atm_launches"])
+        sysm.surrogate_options(exact_every=50)
+        sysm.surrogate_error(reset=True)
+        r1 = timed("3c08", "pair", "surrogate", 50, 3)
+        ed, ee, ek = sysm.surrogate_error()
+        surrogate = {
+            "precision": "surrogate (bf16 tensor-core MLP, FP32 descriptors)",
+            "value": n * 50 / (r1["ms"] * 1e-3), "ms_per_step": r1["ms"] / 50,
+            "steps": "50 timed, exact FP32C 3c08 traversal every 50 (one in the timed run)",
+            "ms_per_step_surrogate_only": r0["ms"] / 10,
+            "sur_ms_per_launch": sm, "mups_3body": n / (sm * 1e-3),
+            "force_error": {"vs": "fp64 exact ATM force (3c08, pair), same state",
+                            "rms_rel": float(np.sqrt(np.mean(d ** 2)) / scale_f),
+                            "max_abs_over_rms": float(np.abs(d).max() / scale_f)},
+            "online_check": {"rms_diff_over_rms_exact": ed / ee if ee > 0 else None,
+                             "checks": ek},
+            "training": info,
+        }
+
     # end to end through the public API with host buffers: per step H2D of
     # (x, v) from pinned memory, one step, D2H of (x, v)
     e2e = None
@@ -339,6 +381,7 @@ def run_ours(args):
             "profile_ms": {k: prof[k] for k in ("ms_cells", "ms_lj", "ms_atm", "ms_md")},
             "counts": {k: int(main["res"][k]) for k in ("n_cand3", "n_int3", "n_cand2", "n_int2")},
             "variants": variants,
+            "surrogate": surrogate,
         }
         print(json.dumps(line))
     sysm.close()
@@ -346,6 +389,43 @@ def run_ours(args):
         dist.barrier()
         dist.destroy_process_group()
     return line
+
+
+# ------------------------------------------------------------------ surrogate
+
+def train_surrogate(atm3, args, device, stream):
+    """Training recipe of the surrogate: exact FP32C ATM forces (3c08, pair)
+    on `sur_frames` frames each of the N=1000 and N=32,000 liquids (rho 0.8,
+    T 1.0), run together as a batch of two replicas, frames `sur_stride`
+    velocity-Verlet steps apart; Adam on minibatches of `sur_batch` rows,
+    learning rate 2e-3 for the first half of the steps, 5e-4 after."""
+    c1 = synth.config("liquid_n1000")
+    c2 = synth.config("liquid_n32k")
+    t0 = time.perf_counter()
+    with atm3.AtmSystem([c1["box"], c2["box"]], [c1["n"], c2["n"]], rc=RC, nu=NU, dt=0.002,
+                        device=device, stream=stream) as tr:
+        tr.set_state(np.concatenate([c1["x"], c2["x"]], axis=1),
+                     np.concatenate([c1["v"], c2["v"]], axis=1))
+        tr.set_options(graph=True)
+        for _ in range(args.sur_frames):
+            tr.step(args.sur_stride, "3c08", "pair", "fp32c", sync=False)
+            tr.surrogate_add_frame("3c08", "pair", "fp32c")
+        rows, sigma2 = tr.surrogate_dataset()
+        t1 = time.perf_counter()
+        tr.surrogate_init(seed=1)
+        h = args.sur_steps // 2
+        l1 = tr.surrogate_train(h, batch=args.sur_batch, lr=2e-3, seed=2)
+        l2 = tr.surrogate_train(args.sur_steps - h, batch=args.sur_batch, lr=5e-4, seed=3)
+        t2 = time.perf_counter()
+        P, mean, scale = tr.surrogate_get_model()
+    loss = np.concatenate([l1, l2])
+    tail = loss[-min(200, len(loss)):]
+    info = {"frames": 2 * args.sur_frames, "rows": int(rows), "stride_steps": args.sur_stride,
+            "adam_steps": args.sur_steps, "batch": args.sur_batch,
+            "loss_first": float(loss[0]) if len(loss) else None,
+            "loss_last200_mean": float(tail.mean()) if len(loss) else None,
+            "collect_s": t1 - t0, "train_s": t2 - t1}
+    return P, mean, scale, info
 
 
 # ------------------------------------------------------------------ CPU oracle

@@ -67,8 +67,13 @@ typedef enum { ATM_TRUNC_PAIR = 0, ATM_TRUNC_PRODUCT = 1 } atm_truncation;
  *  FP64:  every decision and every force, energy and virial term in FP64.
  *  FP32C: decisions and per-triplet arithmetic in FP32 on FP32 cell-local
  *         coordinates; per-molecule force sums compensated (two-sum) in FP32 and
- *         combined in FP64; energy/virial reduced in FP64. */
-typedef enum { ATM_FP64 = 0, ATM_FP32C = 1 } atm_precision;
+ *         combined in FP64; energy/virial reduced in FP64.
+ *  SURROGATE: the ATM force comes from the learned per-molecule model below
+ *         (atm_surrogate_*), not from triplets; LJ runs in FP32.  The model
+ *         gives forces only: E3, W3 and the triplet counts are reported as 0.
+ *         Traversal and truncation select the exact evaluation that atm_step
+ *         interleaves every `exact_every` steps (atm_surrogate_options). */
+typedef enum { ATM_FP64 = 0, ATM_FP32C = 1, ATM_SURROGATE = 2 } atm_precision;
 
 typedef struct {
     double box[3];      /* L_x, L_y, L_z > 0 */
@@ -244,6 +249,98 @@ atm_status atm_density_reset(atm_ctx* ctx);
 atm_status atm_compute_forces_noalloc(const atm_params* params, int64_t n, const double* x_dev,
                                       atm_traversal trav, atm_truncation trunc,
                                       atm_precision prec, double* f_dev, atm_result* out);
+
+/* ------------------------------------------------------------------------
+ * Learned ATM force surrogate.  The paper has no counterpart: it evaluates
+ * the triplet sum of Eq. atm / Eq. forcepairs exactly.  The surrogate replaces
+ * that sum by a per-molecule model of the same force, for runs that trade a
+ * stated force error for speed:
+ *   neighbours j with r = |r_j - r_i| < r_c, rhat = (r_j - r_i) / r, cutoff
+ *   f_c = (cos(pi r / r_c) + 1) / 2;
+ *   D[0..15]  = sum_j exp(-eta_g (r - mu_k)^2) f_c, mu_k = 0.8 + k d_g,
+ *               d_g = (r_c - 0.8) / 15, eta_g = 1 / (2 d_g^2);
+ *   phi_a     = exp(-eta_v (r - nu_a)^2) f_c, nu_a = 0.8 + (a + 1/2) d_v,
+ *               d_v = (r_c - 0.8) / 4, eta_v = 1 / (2 d_v^2), a = 0..3;
+ *   p_a       = sum_j phi_a rhat, T_a = sum_j phi_a (rhat rhat^T - I/3);
+ *   D[16..25] = p_a . p_b for ab = 00 01 02 03 11 12 13 22 23 33;
+ *   D[26..31] = tr(T_a T_b) for ab = 00 01 02 11 12 22;
+ *   w = W3^T silu(W2^T silu(W1^T xn + b1) + b2) + b3, xn = (D - mean) / scale;
+ *   F_i = w_0 p_0 + w_1 p_1 + w_2 p_2.
+ * Parameters: ATM_SUR_NPARAM floats laid out W1[32][64], b1[64], W2[64][64],
+ * b2[64], W3[64][3], b3[3] (row-major, input index first), plus mean[32] and
+ * scale[32] (> 0).  Inference: inputs, weights and the two hidden layers in
+ * bfloat16 on the tensor cores, FP32 sums.  Training: FP32 master weights,
+ * FP32 gradients, Adam (beta1 0.9, beta2 0.999, eps 1e-8) on the loss
+ *   L = sum_i |F_i - F_i^ref|^2 / (3 B sigma2)
+ * over a minibatch of B rows, sigma2 = mean squared target force component of
+ * the data set (L = 1 for the zero model).
+ * Descriptor / vector rows are float [rows][32] and [rows][9] (p_0, p_1, p_2),
+ * targets float [rows][3]; all host arrays, caller-owned.
+ * ------------------------------------------------------------------------ */
+#define ATM_SUR_NDESC 32
+#define ATM_SUR_NVEC 9
+#define ATM_SUR_NPARAM 6467
+
+/* Set / get the model.  set_model copies (and validates: finite, scale > 0)
+ * the parameters and resets the Adam state.  get_model accepts NULL for any
+ * output.  STATE if no model was set or initialised. */
+atm_status atm_surrogate_set_model(atm_ctx* ctx, const float* params, const float* mean,
+                                   const float* scale);
+atm_status atm_surrogate_get_model(atm_ctx* ctx, float* params, float* mean, float* scale);
+
+/* Initialise a model for the current data set: mean / scale from its
+ * descriptor columns (population deviation, 1 where below 1e-12), weights
+ * uniform in +-sqrt(6 / (fan_in + fan_out)) from a splitmix64 stream of
+ * `seed` (output layer times 0.1), biases 0.  STATE if the data set is empty. */
+atm_status atm_surrogate_init(atm_ctx* ctx, uint64_t seed);
+
+/* Model file: 8-byte tag "ATMSUR01", int32 parameter count, int32 descriptor
+ * count, then params, mean, scale as little-endian float32.  IO errors return
+ * INVALID with the reason in atm_last_error(). */
+atm_status atm_surrogate_save(atm_ctx* ctx, const char* path);
+atm_status atm_surrogate_load(atm_ctx* ctx, const char* path);
+
+/* Descriptors and vectors of every molecule of the current cells (original
+ * order), computed by the same kernel as the inference.  STATE without cells. */
+atm_status atm_surrogate_descriptors(atm_ctx* ctx, float* desc, float* vec);
+
+/* Inference on given rows (no neighbour search): w[rows][3] and
+ * force[rows][3] = sum_m w_m vec_m.  STATE without a model. */
+atm_status atm_surrogate_mlp(atm_ctx* ctx, int64_t rows, const float* desc, const float* vec,
+                             float* w, float* force);
+
+/* FP32 loss and gradient of the current master parameters on given rows (the
+ * whole set is one batch).  loss may be NULL; grad has ATM_SUR_NPARAM floats. */
+atm_status atm_surrogate_loss_grad(atm_ctx* ctx, int64_t rows, const float* desc,
+                                   const float* vec, const float* target, double sigma2,
+                                   double* loss, float* grad);
+
+/* Data set.  add_frame evaluates the exact ATM force (traversal, truncation,
+ * precision FP64 or FP32C) on the current cells and appends one row per
+ * molecule (its descriptors, vectors and that force).  add_rows appends given
+ * rows.  The data set lives on the device and grows as needed. */
+atm_status atm_surrogate_add_frame(atm_ctx* ctx, atm_traversal trav, atm_truncation trunc,
+                                   atm_precision prec);
+atm_status atm_surrogate_add_rows(atm_ctx* ctx, int64_t rows, const float* desc,
+                                  const float* vec, const float* target);
+atm_status atm_surrogate_dataset(atm_ctx* ctx, int64_t* rows, double* sigma2);
+atm_status atm_surrogate_clear(atm_ctx* ctx);
+
+/* `steps` Adam steps of learning rate lr.  batch <= 0 or >= the data-set size:
+ * every step uses all rows in order; else each step draws `batch` rows with
+ * replacement, row = splitmix64(seed, step, b) mod size.  loss (may be NULL)
+ * receives the minibatch loss of each step.  STATE without model or data. */
+atm_status atm_surrogate_train(atm_ctx* ctx, int64_t steps, int64_t batch, double lr,
+                               uint64_t seed, double* loss);
+
+/* atm_step with ATM_SURROGATE: every `exact_every` steps (0 = never; default
+ * 50) the step uses the exact FP32C traversal instead and the surrogate is
+ * compared with it on that configuration.  atm_surrogate_error returns the
+ * accumulated comparison: RMS of the force difference and of the exact force
+ * (per component) and the number of comparisons; reset != 0 clears it. */
+atm_status atm_surrogate_options(atm_ctx* ctx, int exact_every);
+atm_status atm_surrogate_error(atm_ctx* ctx, double* rms_diff, double* rms_exact,
+                               int64_t* checks, int reset);
 
 /* Device-time profile of the library's own kernels (CUDA events recorded on
  * the context's stream around each group of launches while profiling is on).

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libatm3.so")
 
 TRAVERSALS = {"3c01": 0, "3c18": 1, "3c08": 2}
 TRUNCATIONS = {"pair": 0, "product": 1}
-PRECISIONS = {"fp64": 0, "fp32c": 1}
+PRECISIONS = {"fp64": 0, "fp32c": 1, "surrogate": 2}
 FORCES = {"total": 0, "lj": 1, "atm": 2}
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "box smaller than three cells", 3: "CUDA error",
@@ -28,7 +28,14 @@ EXPORTED = ["atm_abi_version", "atm_create", "atm_batch_create", "atm_batch_size
             "atm_get_cells", "atm_compute_forces", "atm_get_results", "atm_get_forces",
             "atm_get_forces_dev", "atm_get_state", "atm_step", "atm_set_options", "atm_autotune",
             "atm_density_accumulate", "atm_density_get", "atm_density_reset",
-            "atm_set_profiling", "atm_get_profile", "atm_compute_forces_noalloc"]
+            "atm_set_profiling", "atm_get_profile", "atm_compute_forces_noalloc",
+            "atm_surrogate_set_model", "atm_surrogate_get_model", "atm_surrogate_init",
+            "atm_surrogate_save", "atm_surrogate_load", "atm_surrogate_descriptors",
+            "atm_surrogate_mlp", "atm_surrogate_loss_grad", "atm_surrogate_add_frame",
+            "atm_surrogate_add_rows", "atm_surrogate_dataset", "atm_surrogate_clear",
+            "atm_surrogate_train", "atm_surrogate_options", "atm_surrogate_error"]
+
+SUR_NDESC, SUR_NVEC, SUR_NPARAM = 32, 9, 6467
 
 
 class Params(ctypes.Structure):
@@ -109,6 +116,21 @@ def load():
         "atm_get_profile": [P, ctypes.POINTER(Profile)],
         "atm_compute_forces_noalloc": [ctypes.POINTER(Params), i64, P, i32, i32, i32, P,
                                        ctypes.POINTER(Result)],
+        "atm_surrogate_set_model": [P, P, P, P],
+        "atm_surrogate_get_model": [P, P, P, P],
+        "atm_surrogate_init": [P, ctypes.c_uint64],
+        "atm_surrogate_save": [P, ctypes.c_char_p],
+        "atm_surrogate_load": [P, ctypes.c_char_p],
+        "atm_surrogate_descriptors": [P, P, P],
+        "atm_surrogate_mlp": [P, i64, P, P, P, P],
+        "atm_surrogate_loss_grad": [P, i64, P, P, P, ctypes.c_double, P, P],
+        "atm_surrogate_add_frame": [P, i32, i32, i32],
+        "atm_surrogate_add_rows": [P, i64, P, P, P],
+        "atm_surrogate_dataset": [P, P, P],
+        "atm_surrogate_clear": [P],
+        "atm_surrogate_train": [P, i64, i64, ctypes.c_double, ctypes.c_uint64, P],
+        "atm_surrogate_options": [P, i32],
+        "atm_surrogate_error": [P, P, P, P, i32],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -315,6 +337,103 @@ class AtmSystem:
         p = Profile()
         self._check(self._lib.atm_get_profile(self._ctx, ctypes.byref(p)))
         return p.as_dict()
+
+
+    # ------------------------------------------------------- surrogate
+
+    def surrogate_set_model(self, params, mean, scale):
+        params = np.ascontiguousarray(params, dtype=np.float32)
+        mean = np.ascontiguousarray(mean, dtype=np.float32)
+        scale = np.ascontiguousarray(scale, dtype=np.float32)
+        assert params.size == SUR_NPARAM and mean.size == SUR_NDESC and scale.size == SUR_NDESC
+        self._check(self._lib.atm_surrogate_set_model(self._ctx, _host_ptr(params), _host_ptr(mean),
+                                                    _host_ptr(scale)))
+
+    def surrogate_get_model(self):
+        params = np.zeros(SUR_NPARAM, dtype=np.float32)
+        mean = np.zeros(SUR_NDESC, dtype=np.float32)
+        scale = np.zeros(SUR_NDESC, dtype=np.float32)
+        self._check(self._lib.atm_surrogate_get_model(self._ctx, _host_ptr(params), _host_ptr(mean),
+                                                    _host_ptr(scale)))
+        return params, mean, scale
+
+    def surrogate_init(self, seed=0):
+        self._check(self._lib.atm_surrogate_init(self._ctx, int(seed)))
+
+    def surrogate_save(self, path):
+        self._check(self._lib.atm_surrogate_save(self._ctx, os.fsencode(path)))
+
+    def surrogate_load(self, path):
+        self._check(self._lib.atm_surrogate_load(self._ctx, os.fsencode(path)))
+
+    def surrogate_descriptors(self):
+        """Descriptors ``[n, 32]`` and vectors ``[n, 9]`` (float32, original order)."""
+        D = np.zeros((self.n, SUR_NDESC), dtype=np.float32)
+        V = np.zeros((self.n, SUR_NVEC), dtype=np.float32)
+        self._check(self._lib.atm_surrogate_descriptors(self._ctx, _host_ptr(D), _host_ptr(V)))
+        return D, V
+
+    def surrogate_mlp(self, D, V):
+        """Tensor-core inference on given rows: ``(w [rows, 3], F [rows, 3])``."""
+        D = np.ascontiguousarray(D, dtype=np.float32).reshape(-1, SUR_NDESC)
+        V = np.ascontiguousarray(V, dtype=np.float32).reshape(-1, SUR_NVEC)
+        n = D.shape[0]
+        w = np.zeros((n, 3), dtype=np.float32)
+        F = np.zeros((n, 3), dtype=np.float32)
+        self._check(self._lib.atm_surrogate_mlp(self._ctx, n, _host_ptr(D), _host_ptr(V),
+                                              _host_ptr(w), _host_ptr(F)))
+        return w, F
+
+    def surrogate_loss_grad(self, D, V, T, sigma2):
+        D = np.ascontiguousarray(D, dtype=np.float32).reshape(-1, SUR_NDESC)
+        V = np.ascontiguousarray(V, dtype=np.float32).reshape(-1, SUR_NVEC)
+        T = np.ascontiguousarray(T, dtype=np.float32).reshape(-1, 3)
+        loss = ctypes.c_double(0.0)
+        g = np.zeros(SUR_NPARAM, dtype=np.float32)
+        self._check(self._lib.atm_surrogate_loss_grad(self._ctx, D.shape[0], _host_ptr(D),
+                                                    _host_ptr(V), _host_ptr(T), float(sigma2),
+                                                    ctypes.byref(loss), _host_ptr(g)))
+        return loss.value, g
+
+    def surrogate_add_frame(self, trav="3c08", trunc="pair", prec="fp32c"):
+        self._check(self._lib.atm_surrogate_add_frame(self._ctx, TRAVERSALS[trav],
+                                                    TRUNCATIONS[trunc], PRECISIONS[prec]))
+
+    def surrogate_add_rows(self, D, V, T):
+        D = np.ascontiguousarray(D, dtype=np.float32).reshape(-1, SUR_NDESC)
+        V = np.ascontiguousarray(V, dtype=np.float32).reshape(-1, SUR_NVEC)
+        T = np.ascontiguousarray(T, dtype=np.float32).reshape(-1, 3)
+        self._check(self._lib.atm_surrogate_add_rows(self._ctx, D.shape[0], _host_ptr(D),
+                                                   _host_ptr(V), _host_ptr(T)))
+
+    def surrogate_dataset(self):
+        """``(rows, sigma2)`` of the device-side training set."""
+        rows = ctypes.c_int64(0)
+        s2 = ctypes.c_double(0.0)
+        self._check(self._lib.atm_surrogate_dataset(self._ctx, ctypes.byref(rows), ctypes.byref(s2)))
+        return rows.value, s2.value
+
+    def surrogate_clear(self):
+        self._check(self._lib.atm_surrogate_clear(self._ctx))
+
+    def surrogate_train(self, steps, batch=0, lr=1e-3, seed=0):
+        """Adam steps on the data set; returns the per-step minibatch losses."""
+        loss = np.zeros(max(0, int(steps)), dtype=np.float64)
+        self._check(self._lib.atm_surrogate_train(self._ctx, int(steps), int(batch), float(lr),
+                                                int(seed), _host_ptr(loss)))
+        return loss
+
+    def surrogate_options(self, exact_every=50):
+        self._check(self._lib.atm_surrogate_options(self._ctx, int(exact_every)))
+
+    def surrogate_error(self, reset=False):
+        """``(rms_diff, rms_exact, checks)`` of the interleaved exact steps."""
+        d = ctypes.c_double(0.0)
+        e = ctypes.c_double(0.0)
+        k = ctypes.c_int64(0)
+        self._check(self._lib.atm_surrogate_error(self._ctx, ctypes.byref(d), ctypes.byref(e),
+                                                ctypes.byref(k), 1 if reset else 0))
+        return d.value, e.value, k.value
 
 
 def compute_forces_noalloc(box, x_dev, f_dev, trav="3c18", trunc="pair", prec="fp64", rc=2.5,

@@ -27,9 +27,9 @@ struct Grid {
 struct Rep {
     Grid g;
     long long mol0, n, cell0;
-    double rc2, rc6, nu, dt;
+    double rc, rc2, rc6, nu, dt;
     double sig2, eps4, eps24, eps48, ushift;  // LJ
-    float rc2f, rc6f, nuf, sig2f, eps4f, eps24f, eps48f, ushiftf;
+    float rcf, rc2f, rc6f, nuf, sig2f, eps4f, eps24f, eps48f, ushiftf;
     float wf[3];
     float p_lo, p_hi;          // FP64 prefilter band of a squared distance
     float q_lo, q_hi, dmin;    // FP64 prefilter band of a sorted product

@@ -12,6 +12,7 @@
 #include "atm3_internal.cuh"
 #include "forces.cuh"
 #include "md_kernels.cuh"
+#include "ctx.cuh"
 
 using namespace atm3;
 
@@ -20,78 +21,10 @@ constexpr int DENS_MAX_BINS = 4096;
 constexpr int KERNELS_PER_STEP = 10;  // kick, 6 cell kernels, LJ, ATM, kick
 }  // namespace
 
-struct atm_ctx {
-    int R = 1;
-    std::vector<atm_params> params;
-    std::vector<Rep> reps;  // host copy
-    long long n = 0, ncell = 0;
-    int device = 0;
-    cudaStream_t st = nullptr;
-    Batch b{};
-    Rep* d_rep = nullptr;
-    int* d_rep_of_cell = nullptr;
-    int* d_rep_of_mol = nullptr;
-    double* x = nullptr;   // [3n] positions, original order (wrapped by the cell build)
-    double* v = nullptr;   // [3n] velocities, original order
-    double* x0 = nullptr;  // [3n] snapshot at the start of a graph-mode run
-    double* v0 = nullptr;
-    double* xl = nullptr;  // [3n] sorted cell-local FP64
-    float* xl32 = nullptr; // [3n] sorted cell-local FP32
-    int* cell_of = nullptr;
-    int* rank = nullptr;
-    int* count = nullptr;
-    int* start = nullptr;
-    int* perm = nullptr;
-    int* cell_sorted = nullptr;
-    double* f_lj = nullptr;   // [3n] sorted order
-    double* f_atm = nullptr;  // [3n] sorted order
-    double* f_out = nullptr;  // [3n] original-order scratch for atm_get_forces
-    double* unit_ew = nullptr;
-    unsigned long long* unit_cnt = nullptr;
-    double* mol_ew = nullptr;
-    unsigned* mol_cnt = nullptr;
-    double* ke = nullptr;
-    ResultDev* d_res = nullptr;  // [R]
-    ResultDev* d_part = nullptr; // [R * REDUCE_PARTS] partial sums
-    ResultDev* h_res = nullptr;  // [R] pinned
-    int* d_status = nullptr;
-    int* h_status = nullptr;
-    int* d_maxocc = nullptr;
-    int* h_maxocc = nullptr;
-    int* d_work = nullptr;
-    unsigned long long* d_dens = nullptr;  // [R * DENS_MAX_BINS]
-    int dens_axis = -1, dens_nbins = 0;
-    long long dens_samples = 0;
-    int maxocc = 0;
-    int unit_max[3] = {0, 0, 0};  // largest unit (staged molecules) of 3c01, 3c18, 3c08
-    bool have_x = false, cells_built = false, forces_valid = false;
-    int f_trav = -1, f_trunc = -1, f_prec = -1;
-    size_t smem_set[2][3][2] = {};
-    int smem_optin = 0, sms = 0;
-    // launch options: persistent ATM grid, warps per block-kernel CTA (0 =
-    // default), CUDA-graph steps; tuned choices per (prec, trav, trunc)
-    int opt_persistent = 0, opt_nwarps = 0, opt_graph = 0;
-    int tuned[2][3][2] = {};  // 0 = not tuned, else 1 + persistent + 2 * (nwarps == 8)
-    // graph of one step, valid for (trav, trunc, prec, mcap, launch choice)
-    cudaStream_t cap_st = nullptr;
-    cudaGraphExec_t graph = nullptr;
-    int graph_key[5] = {-1, -1, -1, -1, -1};
-    // profiling: event pairs around launch groups, summed per kind
-    bool prof = false;
-    struct EvRec {
-        cudaEvent_t a, b;
-        int kind;
-    };
-    std::vector<EvRec> ev_live;
-    std::vector<cudaEvent_t> ev_pool;
-    double prof_ms[4] = {0, 0, 0, 0};  // cells, lj, atm, md
-    long long n_launch = 0, n_atm = 0;
-    char err[256] = "no error";
-};
 
 enum { PK_CELLS = 0, PK_LJ = 1, PK_ATM = 2, PK_MD = 3 };
 
-static cudaEvent_t prof_begin(atm_ctx* c)
+cudaEvent_t atm3::ctx_prof_begin(atm_ctx* c)
 {
     if (!c->prof) return nullptr;
     cudaEvent_t e = nullptr;
@@ -105,7 +38,7 @@ static cudaEvent_t prof_begin(atm_ctx* c)
     return e;
 }
 
-static void prof_end(atm_ctx* c, int kind, cudaEvent_t a)
+void atm3::ctx_prof_end(atm_ctx* c, int kind, cudaEvent_t a)
 {
     if (!c->prof || !a) return;
     cudaEvent_t b = nullptr;
@@ -133,7 +66,7 @@ static void prof_drain(atm_ctx* c)
     cudaGetLastError();
 }
 
-static atm_status fail(atm_ctx* c, atm_status s, const char* fmt, ...)
+atm_status atm3::ctx_fail(atm_ctx* c, atm_status s, const char* fmt, ...)
 {
     if (c) {
         va_list ap;
@@ -144,12 +77,6 @@ static atm_status fail(atm_ctx* c, atm_status s, const char* fmt, ...)
     return s;
 }
 
-#define CU(call)                                                                        \
-    do {                                                                                \
-        cudaError_t e_ = (call);                                                        \
-        if (e_ != cudaSuccess)                                                          \
-            return fail(c, ATM_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_));        \
-    } while (0)
 
 static void drop_graph(atm_ctx* c)
 {
@@ -161,6 +88,7 @@ static void drop_graph(atm_ctx* c)
 static void free_all(atm_ctx* c)
 {
     drop_graph(c);
+    sur_free(c);
     void* dev[] = {c->d_rep, c->d_rep_of_cell, c->d_rep_of_mol, c->x, c->v, c->x0, c->v0, c->xl,
                    c->xl32, c->cell_of, c->rank, c->count, c->start, c->perm, c->cell_sorted,
                    c->f_lj, c->f_atm, c->f_out, c->unit_ew, c->unit_cnt, c->mol_ew, c->mol_cnt,
@@ -186,13 +114,13 @@ static atm_status check_status(atm_ctx* c)
     if (s == 0) return ATM_OK;
     *c->h_status = 0;
     cudaMemsetAsync(c->d_status, 0, sizeof(int), c->st);
-    if (s & ST_NONFINITE) return fail(c, ATM_E_NONFINITE, "non-finite position or velocity");
+    if (s & ST_NONFINITE) return ctx_fail(c, ATM_E_NONFINITE, "non-finite position or velocity");
     if (s & ST_CAPACITY)
-        return fail(c, ATM_E_CAPACITY, "a traversal unit holds more molecules than staged");
-    return fail(c, ATM_E_CUDA, "device status %d", s);
+        return ctx_fail(c, ATM_E_CAPACITY, "a traversal unit holds more molecules than staged");
+    return ctx_fail(c, ATM_E_CUDA, "device status %d", s);
 }
 
-static atm_status sync_and_check(atm_ctx* c)
+atm_status atm3::ctx_sync_and_check(atm_ctx* c)
 {
     CU(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->st));
     CU(cudaStreamSynchronize(c->st));
@@ -349,10 +277,10 @@ static void invalidate(atm_ctx* c)
 extern "C" atm_status atm_set_state(atm_ctx* c, const double* x, const double* v)
 {
     if (!c) return ATM_E_INVALID;
-    if (!x && c->n > 0) return fail(c, ATM_E_INVALID, "positions are required");
+    if (!x && c->n > 0) return ctx_fail(c, ATM_E_INVALID, "positions are required");
     for (long long q = 0; q < 3 * c->n; q++)
         if (!std::isfinite(x[q]) || (v && !std::isfinite(v[q])))
-            return fail(c, ATM_E_NONFINITE, "non-finite input at element %lld", q);
+            return ctx_fail(c, ATM_E_NONFINITE, "non-finite input at element %lld", q);
     CU(cudaSetDevice(c->device));
     size_t bytes = 3 * (size_t)c->n * sizeof(double);
     if (bytes) {
@@ -370,7 +298,7 @@ extern "C" atm_status atm_set_state(atm_ctx* c, const double* x, const double* v
 extern "C" atm_status atm_set_state_dev(atm_ctx* c, const double* x_dev, const double* v_dev)
 {
     if (!c) return ATM_E_INVALID;
-    if (!x_dev && c->n > 0) return fail(c, ATM_E_INVALID, "positions are required");
+    if (!x_dev && c->n > 0) return ctx_fail(c, ATM_E_INVALID, "positions are required");
     CU(cudaSetDevice(c->device));
     size_t bytes = 3 * (size_t)c->n * sizeof(double);
     if (bytes) {
@@ -391,10 +319,10 @@ extern "C" atm_status atm_set_state_dev(atm_ctx* c, const double* x_dev, const d
 // cell build kernels only (no host synchronisation; capturable)
 static atm_status launch_cells(atm_ctx* c)
 {
-    cudaEvent_t ev = prof_begin(c);
+    cudaEvent_t ev = ctx_prof_begin(c);
     CU(launch_build_cells(c->b, c->x, c->cell_of, c->rank, c->count, c->start, c->perm, c->xl,
                           c->xl32, c->cell_sorted, c->d_maxocc, c->d_status, c->st));
-    prof_end(c, PK_CELLS, ev);
+    ctx_prof_end(c, PK_CELLS, ev);
     c->n_launch += c->n > 0 ? 6 : 2;
     return ATM_OK;
 }
@@ -405,7 +333,7 @@ static atm_status enqueue_cells(atm_ctx* c)
     atm_status s = launch_cells(c);
     if (s != ATM_OK) return s;
     CU(cudaMemcpyAsync(c->h_maxocc, c->d_maxocc, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->st));
-    s = sync_and_check(c);
+    s = ctx_sync_and_check(c);
     if (s != ATM_OK) return s;
     c->maxocc = c->h_maxocc[0];
     for (int t = 0; t < 3; t++) c->unit_max[t] = c->h_maxocc[1 + t];
@@ -417,7 +345,7 @@ static atm_status enqueue_cells(atm_ctx* c)
 extern "C" atm_status atm_build_cells(atm_ctx* c)
 {
     if (!c) return ATM_E_INVALID;
-    if (!c->have_x) return fail(c, ATM_E_STATE, "no state set");
+    if (!c->have_x) return ctx_fail(c, ATM_E_STATE, "no state set");
     CU(cudaSetDevice(c->device));
     return enqueue_cells(c);
 }
@@ -428,7 +356,7 @@ extern "C" atm_status atm_get_cells(atm_ctx* c, int32_t* cell_of, int32_t* cell_
     if (!c) return ATM_E_INVALID;
     if (ncell3)
         for (int d = 0; d < 3; d++) ncell3[d] = c->reps[0].g.nc[d];
-    if (!c->cells_built) return fail(c, ATM_E_STATE, "cells not built");
+    if (!c->cells_built) return ctx_fail(c, ATM_E_STATE, "cells not built");
     CU(cudaSetDevice(c->device));
     if (cell_of && c->n)
         CU(cudaMemcpyAsync(cell_of, c->cell_of, c->n * sizeof(int), cudaMemcpyDeviceToHost, c->st));
@@ -457,7 +385,7 @@ static void launch_choice(const atm_ctx* c, int trav, int trunc, int prec, int& 
 }
 
 // LJ + ATM force kernels for the current cells; mcap = staged-molecule capacity
-static atm_status enqueue_forces(atm_ctx* c, int trav, int trunc, int prec, int mcap)
+atm_status atm3::ctx_enqueue_forces(atm_ctx* c, int trav, int trunc, int prec, int mcap)
 {
     ForceJob j;
     j.b = c->b;
@@ -476,27 +404,35 @@ static atm_status enqueue_forces(atm_ctx* c, int trav, int trunc, int prec, int 
     j.work = c->d_work;
     j.trav = trav;
     j.trunc = trunc;
-    j.prec = prec;
+    // the surrogate runs LJ in FP32
+    j.prec = prec == ATM_SURROGATE ? ATM_FP32C : prec;
     j.mcap = mcap > 0 ? mcap : 1;
     j.optin = c->smem_optin;
     j.sms = c->sms;
-    launch_choice(c, trav, trunc, prec, j.persistent, j.nwarps);
+    j.persistent = 0;
+    j.nwarps = 0;
+    if (prec != ATM_SURROGATE) launch_choice(c, trav, trunc, prec, j.persistent, j.nwarps);
     j.st = c->st;
 
-    cudaEvent_t ev = prof_begin(c);
+    cudaEvent_t ev = ctx_prof_begin(c);
     CU(enqueue_lj(j));
-    prof_end(c, PK_LJ, ev);
+    ctx_prof_end(c, PK_LJ, ev);
     c->n_launch += 1;
 
-    ev = prof_begin(c);
-    bool capacity = false;
-    cudaError_t e = enqueue_atm(j, &c->smem_set[prec][trav][trunc], &capacity);
-    if (capacity)
-        return fail(c, ATM_E_CAPACITY,
-                    "a traversal unit of %d molecules does not fit the kernels' shared memory",
-                    j.mcap);
-    CU(e);
-    prof_end(c, PK_ATM, ev);
+    ev = ctx_prof_begin(c);
+    if (prec == ATM_SURROGATE) {
+        atm_status s = sur_enqueue_atm(c);
+        if (s != ATM_OK) return s;
+    } else {
+        bool capacity = false;
+        cudaError_t e = enqueue_atm(j, &c->smem_set[prec][trav][trunc], &capacity);
+        if (capacity)
+            return ctx_fail(c, ATM_E_CAPACITY,
+                            "a traversal unit of %d molecules does not fit the kernels' shared memory",
+                            j.mcap);
+        CU(e);
+    }
+    ctx_prof_end(c, PK_ATM, ev);
     c->n_launch += 1;
     c->n_atm += 1;
     c->forces_valid = true;
@@ -517,9 +453,9 @@ static atm_status enqueue_reduce(atm_ctx* c)
     r.ke = c->ke;
     r.part = c->d_part;
     r.out = c->d_res;
-    cudaEvent_t ev = prof_begin(c);
+    cudaEvent_t ev = ctx_prof_begin(c);
     CU(launch_final_reduce(r, c->st));
-    prof_end(c, PK_MD, ev);
+    ctx_prof_end(c, PK_MD, ev);
     c->n_launch += 2;
     CU(cudaMemcpyAsync(c->h_res, c->d_res, c->R * sizeof(ResultDev), cudaMemcpyDeviceToHost, c->st));
     return ATM_OK;
@@ -540,26 +476,26 @@ static void copy_result(const ResultDev& r, atm_result* out)
 
 static bool valid_enums(int trav, int trunc, int prec)
 {
-    return trav >= 0 && trav <= 2 && trunc >= 0 && trunc <= 1 && prec >= 0 && prec <= 1;
+    return trav >= 0 && trav <= 2 && trunc >= 0 && trunc <= 1 && prec >= 0 && prec <= 2;
 }
 
 extern "C" atm_status atm_compute_forces(atm_ctx* c, atm_traversal trav, atm_truncation trunc,
                                          atm_precision prec, atm_result* out)
 {
     if (!c) return ATM_E_INVALID;
-    if (!valid_enums(trav, trunc, prec)) return fail(c, ATM_E_INVALID, "unknown traversal/truncation/precision");
-    if (!c->cells_built) return fail(c, ATM_E_STATE, "cells not built");
+    if (!valid_enums(trav, trunc, prec)) return ctx_fail(c, ATM_E_INVALID, "unknown traversal/truncation/precision");
+    if (!c->cells_built) return ctx_fail(c, ATM_E_STATE, "cells not built");
     CU(cudaSetDevice(c->device));
-    atm_status s = enqueue_forces(c, trav, trunc, prec, c->unit_max[trav]);
+    atm_status s = ctx_enqueue_forces(c, trav, trunc, prec, c->unit_max[trav]);
     if (s != ATM_OK) return s;
-    cudaEvent_t ev = prof_begin(c);
+    cudaEvent_t ev = ctx_prof_begin(c);
     CU(launch_kinetic(c->n, c->v, c->ke, c->st));
-    prof_end(c, PK_MD, ev);
+    ctx_prof_end(c, PK_MD, ev);
     c->n_launch += 1;
     s = enqueue_reduce(c);
     if (s != ATM_OK) return s;
     if (out) {
-        s = sync_and_check(c);
+        s = ctx_sync_and_check(c);
         if (s != ATM_OK) return s;
         copy_result(c->h_res[0], out);
     }
@@ -570,7 +506,7 @@ extern "C" atm_status atm_get_results(atm_ctx* c, atm_result* out)
 {
     if (!c || !out) return ATM_E_INVALID;
     CU(cudaSetDevice(c->device));
-    atm_status s = sync_and_check(c);
+    atm_status s = ctx_sync_and_check(c);
     if (s != ATM_OK) return s;
     for (int r = 0; r < c->R; r++) copy_result(c->h_res[r], out + r);
     return ATM_OK;
@@ -579,7 +515,7 @@ extern "C" atm_status atm_get_results(atm_ctx* c, atm_result* out)
 static atm_status get_forces_impl(atm_ctx* c, double* f, int which, bool host)
 {
     if (!c || !f || which < 0 || which > 2) return ATM_E_INVALID;
-    if (!c->forces_valid) return fail(c, ATM_E_STATE, "no force evaluation is current");
+    if (!c->forces_valid) return ctx_fail(c, ATM_E_STATE, "no force evaluation is current");
     CU(cudaSetDevice(c->device));
     size_t bytes = 3 * (size_t)c->n * sizeof(double);
     if (!bytes) return ATM_OK;
@@ -587,7 +523,7 @@ static atm_status get_forces_impl(atm_ctx* c, double* f, int which, bool host)
     c->n_launch += 1;
     if (host) {
         CU(cudaMemcpyAsync(f, c->f_out, bytes, cudaMemcpyDeviceToHost, c->st));
-        return sync_and_check(c);
+        return ctx_sync_and_check(c);
     }
     return ATM_OK;
 }
@@ -605,7 +541,7 @@ extern "C" atm_status atm_get_forces_dev(atm_ctx* c, double* f_dev, int which)
 extern "C" atm_status atm_get_state(atm_ctx* c, double* x, double* v)
 {
     if (!c) return ATM_E_INVALID;
-    if (!c->have_x) return fail(c, ATM_E_STATE, "no state set");
+    if (!c->have_x) return ctx_fail(c, ATM_E_STATE, "no state set");
     CU(cudaSetDevice(c->device));
     size_t bytes = 3 * (size_t)c->n * sizeof(double);
     if (bytes && x) CU(cudaMemcpyAsync(x, c->x, bytes, cudaMemcpyDeviceToHost, c->st));
@@ -618,17 +554,17 @@ extern "C" atm_status atm_get_state(atm_ctx* c, double* x, double* v)
 // forces (capacity mcap), kick
 static atm_status enqueue_step(atm_ctx* c, int trav, int trunc, int prec, int mcap)
 {
-    cudaEvent_t ev = prof_begin(c);
+    cudaEvent_t ev = ctx_prof_begin(c);
     CU(launch_kick(c->b, c->perm, c->f_lj, c->f_atm, c->x, c->v, 1, c->ke, c->st));
-    prof_end(c, PK_MD, ev);
+    ctx_prof_end(c, PK_MD, ev);
     c->n_launch += 1;
     atm_status s = launch_cells(c);
     if (s != ATM_OK) return s;
-    s = enqueue_forces(c, trav, trunc, prec, mcap);
+    s = ctx_enqueue_forces(c, trav, trunc, prec, mcap);
     if (s != ATM_OK) return s;
-    ev = prof_begin(c);
+    ev = ctx_prof_begin(c);
     CU(launch_kick(c->b, c->perm, c->f_lj, c->f_atm, c->x, c->v, 0, c->ke, c->st));
-    prof_end(c, PK_MD, ev);
+    ctx_prof_end(c, PK_MD, ev);
     c->n_launch += 1;
     return ATM_OK;
 }
@@ -646,8 +582,8 @@ static int graph_mcap(const atm_ctx* c, int trav)
 static atm_status run_graph_steps(atm_ctx* c, int nsteps, int trav, int trunc, int prec)
 {
     const int mcap = graph_mcap(c, trav);
-    int persistent, nwarps;
-    launch_choice(c, trav, trunc, prec, persistent, nwarps);
+    int persistent = 0, nwarps = 0;
+    if (prec != ATM_SURROGATE) launch_choice(c, trav, trunc, prec, persistent, nwarps);
     const int key[5] = {trav, trunc, prec, mcap, persistent + 2 * nwarps};
     if (!c->graph || memcmp(key, c->graph_key, sizeof(key)) != 0) {
         drop_graph(c);
@@ -674,9 +610,9 @@ static atm_status run_graph_steps(atm_ctx* c, int nsteps, int trav, int trunc, i
         CU(e);
         memcpy(c->graph_key, key, sizeof(key));
     }
-    cudaEvent_t ev = prof_begin(c);
+    cudaEvent_t ev = ctx_prof_begin(c);
     for (int k = 0; k < nsteps; k++) CU(cudaGraphLaunch(c->graph, c->st));
-    prof_end(c, PK_MD, ev);
+    ctx_prof_end(c, PK_MD, ev);
     c->n_launch += (long long)nsteps * KERNELS_PER_STEP;
     c->n_atm += nsteps;
     return ATM_OK;
@@ -687,18 +623,24 @@ extern "C" atm_status atm_step(atm_ctx* c, int nsteps, atm_traversal trav, atm_t
 {
     if (!c) return ATM_E_INVALID;
     if (nsteps < 0 || !valid_enums(trav, trunc, prec))
-        return fail(c, ATM_E_INVALID, "bad step arguments");
-    if (!c->have_x) return fail(c, ATM_E_STATE, "no state set");
+        return ctx_fail(c, ATM_E_INVALID, "bad step arguments");
+    if (!c->have_x) return ctx_fail(c, ATM_E_STATE, "no state set");
     CU(cudaSetDevice(c->device));
     atm_status s;
-    if (!c->forces_valid || c->f_trav != trav || c->f_trunc != trunc || c->f_prec != prec) {
+    // forces of the current state from this combination (for the surrogate, the
+    // exact FP32C forces of an interleaved step serve as well)
+    const bool fresh = c->forces_valid && c->f_trav == trav && c->f_trunc == trunc &&
+                       (c->f_prec == prec || (prec == ATM_SURROGATE && c->f_prec == ATM_FP32C));
+    if (!fresh) {
         s = enqueue_cells(c);
         if (s != ATM_OK) return s;
-        s = enqueue_forces(c, trav, trunc, prec, c->unit_max[trav]);
+        s = ctx_enqueue_forces(c, trav, trunc, prec, c->unit_max[trav]);
         if (s != ATM_OK) return s;
     }
     bool done = false;
-    if (c->opt_graph && nsteps > 0) {
+    // surrogate runs that interleave exact steps take the per-step path
+    const bool sur_mixed = prec == ATM_SURROGATE && sur_exact_every(c) > 0;
+    if (c->opt_graph && nsteps > 0 && !sur_mixed) {
         const size_t bytes = 3 * (size_t)c->n * sizeof(double);
         if (bytes) {
             CU(cudaMemcpyAsync(c->x0, c->x, bytes, cudaMemcpyDeviceToDevice, c->st));
@@ -707,7 +649,7 @@ extern "C" atm_status atm_step(atm_ctx* c, int nsteps, atm_traversal trav, atm_t
         s = run_graph_steps(c, nsteps, trav, trunc, prec);
         if (s != ATM_OK) return s;
         CU(cudaMemcpyAsync(c->h_maxocc, c->d_maxocc, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->st));
-        s = sync_and_check(c);
+        s = ctx_sync_and_check(c);
         if (s == ATM_OK) {
             done = true;
             c->maxocc = c->h_maxocc[0];
@@ -722,7 +664,7 @@ extern "C" atm_status atm_step(atm_ctx* c, int nsteps, atm_traversal trav, atm_t
             drop_graph(c);
             s = enqueue_cells(c);
             if (s != ATM_OK) return s;
-            s = enqueue_forces(c, trav, trunc, prec, c->unit_max[trav]);
+            s = ctx_enqueue_forces(c, trav, trunc, prec, c->unit_max[trav]);
             if (s != ATM_OK) return s;
         } else {
             return s;
@@ -730,17 +672,26 @@ extern "C" atm_status atm_step(atm_ctx* c, int nsteps, atm_traversal trav, atm_t
     }
     if (!done) {
         for (int k = 0; k < nsteps; k++) {
-            cudaEvent_t ev = prof_begin(c);
+            cudaEvent_t ev = ctx_prof_begin(c);
             CU(launch_kick(c->b, c->perm, c->f_lj, c->f_atm, c->x, c->v, 1, c->ke, c->st));
-            prof_end(c, PK_MD, ev);
+            ctx_prof_end(c, PK_MD, ev);
             c->n_launch += 1;
             s = enqueue_cells(c);
             if (s != ATM_OK) return s;
-            s = enqueue_forces(c, trav, trunc, prec, c->unit_max[trav]);
+            // every exact_every-th surrogate step uses the exact FP32C traversal
+            // and compares the surrogate with it
+            const bool exact = sur_mixed && sur_exact_due(c);
+            s = ctx_enqueue_forces(c, trav, trunc, exact ? (int)ATM_FP32C : (int)prec,
+                                   c->unit_max[trav]);
             if (s != ATM_OK) return s;
-            ev = prof_begin(c);
+            if (exact) {
+                s = sur_enqueue_monitor(c);
+                if (s != ATM_OK) return s;
+            }
+            if (prec == ATM_SURROGATE) sur_count_step(c);
+            ev = ctx_prof_begin(c);
             CU(launch_kick(c->b, c->perm, c->f_lj, c->f_atm, c->x, c->v, 0, c->ke, c->st));
-            prof_end(c, PK_MD, ev);
+            ctx_prof_end(c, PK_MD, ev);
             c->n_launch += 1;
         }
     }
@@ -751,7 +702,7 @@ extern "C" atm_status atm_step(atm_ctx* c, int nsteps, atm_traversal trav, atm_t
     s = enqueue_reduce(c);
     if (s != ATM_OK) return s;
     if (last) {
-        s = sync_and_check(c);
+        s = ctx_sync_and_check(c);
         if (s != ATM_OK) return s;
         copy_result(c->h_res[0], last);
     }
@@ -763,7 +714,7 @@ extern "C" atm_status atm_set_options(atm_ctx* c, int persistent, int nwarps, in
     if (!c) return ATM_E_INVALID;
     if (persistent < 0 || persistent > 1 || !(nwarps == 0 || nwarps == 4 || nwarps == 8) ||
         graph < 0 || graph > 1)
-        return fail(c, ATM_E_INVALID, "bad options");
+        return ctx_fail(c, ATM_E_INVALID, "bad options");
     c->opt_persistent = persistent;
     c->opt_nwarps = nwarps;
     c->opt_graph = graph;
@@ -776,8 +727,9 @@ extern "C" atm_status atm_autotune(atm_ctx* c, atm_traversal trav, atm_truncatio
                                    atm_precision prec, int reps, atm_tuning* out)
 {
     if (!c) return ATM_E_INVALID;
-    if (!valid_enums(trav, trunc, prec) || reps < 1) return fail(c, ATM_E_INVALID, "bad tuning arguments");
-    if (!c->cells_built) return fail(c, ATM_E_STATE, "cells not built");
+    if (!valid_enums(trav, trunc, prec) || prec == ATM_SURROGATE || reps < 1)
+        return ctx_fail(c, ATM_E_INVALID, "bad tuning arguments");
+    if (!c->cells_built) return ctx_fail(c, ATM_E_STATE, "cells not built");
     CU(cudaSetDevice(c->device));
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
@@ -792,14 +744,14 @@ extern "C" atm_status atm_autotune(atm_ctx* c, atm_traversal trav, atm_truncatio
         for (int pers = 0; pers < 2 && s == ATM_OK; pers++) {
             const int code = 1 + pers + 2 * nwi;
             c->tuned[prec][trav][trunc] = code;
-            s = enqueue_forces(c, trav, trunc, prec, c->unit_max[trav]);  // warm-up
+            s = ctx_enqueue_forces(c, trav, trunc, prec, c->unit_max[trav]);  // warm-up
             if (s != ATM_OK) break;
             cudaEventRecord(e0, c->st);
             for (int k = 0; k < reps && s == ATM_OK; k++)
-                s = enqueue_forces(c, trav, trunc, prec, c->unit_max[trav]);
+                s = ctx_enqueue_forces(c, trav, trunc, prec, c->unit_max[trav]);
             cudaEventRecord(e1, c->st);
             if (s != ATM_OK) break;
-            s = sync_and_check(c);
+            s = ctx_sync_and_check(c);
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
             if (s == ATM_OK && ms < best) {
@@ -825,10 +777,10 @@ extern "C" atm_status atm_density_accumulate(atm_ctx* c, int axis, int nbins)
 {
     if (!c) return ATM_E_INVALID;
     if (axis < 0 || axis > 2 || nbins < 1 || nbins > DENS_MAX_BINS)
-        return fail(c, ATM_E_INVALID, "axis in 0..2, 1 <= nbins <= %d", DENS_MAX_BINS);
-    if (!c->cells_built) return fail(c, ATM_E_STATE, "cells not built (positions not wrapped)");
+        return ctx_fail(c, ATM_E_INVALID, "axis in 0..2, 1 <= nbins <= %d", DENS_MAX_BINS);
+    if (!c->cells_built) return ctx_fail(c, ATM_E_STATE, "cells not built (positions not wrapped)");
     if (c->dens_samples > 0 && (axis != c->dens_axis || nbins != c->dens_nbins))
-        return fail(c, ATM_E_STATE, "density accumulator holds another axis/bin count; reset it");
+        return ctx_fail(c, ATM_E_STATE, "density accumulator holds another axis/bin count; reset it");
     CU(cudaSetDevice(c->device));
     CU(launch_density(c->b, c->x, axis, nbins, c->d_dens, c->st));
     c->n_launch += 1;

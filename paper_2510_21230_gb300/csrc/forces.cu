@@ -36,11 +36,13 @@ atm_status make_rep(const atm_params& p, long long n, long long mol0, long long 
     r.n = n;
     r.cell0 = cell0;
     const double rc = p.rc;
+    r.rc = rc;
     r.rc2 = rc * rc;
     r.rc6 = r.rc2 * r.rc2 * r.rc2;
     r.nu = p.nu;
     r.dt = p.dt;
     const float rcf = (float)rc;
+    r.rcf = rcf;
     r.rc2f = rcf * rcf;
     r.rc6f = r.rc2f * r.rc2f * r.rc2f;
     r.nuf = (float)p.nu;

@@ -1,0 +1,775 @@
+// sur_kernels.cu -- kernels of the learned ATM force surrogate (model in
+// surrogate.cuh): fused descriptors + bfloat16 tensor-core MLP + force
+// assembly, data-set collection, FP32 training gradient, Adam, statistics.
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "surrogate.cuh"
+
+namespace atm3 {
+
+namespace {
+
+constexpr int SUR_BLOCK = 128;  // molecules per CTA of the inference kernels (4 warps x 32 rows)
+constexpr float SUR_R0 = 0.8f;
+constexpr float SUR_PI = 3.14159265358979f;
+
+__device__ __forceinline__ float silu_fast(float z) { return z / (1.0f + __expf(-z)); }
+
+// ------------------------------------------------------------ descriptors
+
+// Descriptors D[32] and vectors V[9] (p_0, p_1, p_2) of sorted molecule s in
+// cell (cx, cy, cz) of replica rp: all molecules of the 27 neighbour cells
+// (cell edge >= r_c, so every neighbour within r_c is among them), FP32
+// displacements from cell-local coordinates plus the cell shift.
+__device__ __forceinline__ void sur_descriptor_row(const Rep& rp, const float* __restrict__ xl,
+                                                   long long n, const int* __restrict__ st,
+                                                   int cx, int cy, int cz, long long s,
+                                                   float D[SUR_ND], float V[SUR_NV])
+{
+    const float rc = rp.rcf, rc2 = rp.rc2f;
+    const float dg = (rc - SUR_R0) / 15.0f, dv = (rc - SUR_R0) / 4.0f;
+    const float eta_g = 1.0f / (2.0f * dg * dg), eta_v = 1.0f / (2.0f * dv * dv);
+    const float pi_rc = SUR_PI / rc;
+    const float third = 1.0f / 3.0f;
+    float G[16];
+    float p[4][3];
+    float T[3][6];
+#pragma unroll
+    for (int k = 0; k < 16; k++) G[k] = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 4; a++) p[a][0] = p[a][1] = p[a][2] = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int c = 0; c < 6; c++) T[a][c] = 0.0f;
+    const float xs = xl[s], ys = xl[n + s], zs = xl[2 * n + s];
+    for (int t = 0; t < 27; t++) {
+        int dx, dy, dz;
+        offset27(t, dx, dy, dz);
+        const long long nc = cell_at(rp.g, cx, cy, cz, dx, dy, dz);
+        const int q0 = st[nc], q1 = st[nc + 1];
+        const float sx = (float)dx * rp.wf[0], sy = (float)dy * rp.wf[1], sz = (float)dz * rp.wf[2];
+        for (int q = q0; q < q1; q++) {
+            if (q == s) continue;
+            const float ex = (xl[q] - xs) + sx;
+            const float ey = (xl[n + q] - ys) + sy;
+            const float ez = (xl[2 * n + q] - zs) + sz;
+            const float r2 = ex * ex + ey * ey + ez * ez;
+            if (!(r2 < rc2)) continue;
+            const float ir = rsqrtf(r2);
+            const float r = r2 * ir;
+            const float ux = ex * ir, uy = ey * ir, uz = ez * ir;
+            const float fc = 0.5f * (__cosf(pi_rc * r) + 1.0f);
+#pragma unroll
+            for (int k = 0; k < 16; k++) {
+                const float tt = r - (SUR_R0 + (float)k * dg);
+                G[k] += __expf(-eta_g * tt * tt) * fc;
+            }
+            const float qxx = ux * ux - third, qyy = uy * uy - third, qzz = uz * uz - third;
+            const float qxy = ux * uy, qxz = ux * uz, qyz = uy * uz;
+#pragma unroll
+            for (int a = 0; a < 4; a++) {
+                const float tt = r - (SUR_R0 + ((float)a + 0.5f) * dv);
+                const float ph = __expf(-eta_v * tt * tt) * fc;
+                p[a][0] += ph * ux;
+                p[a][1] += ph * uy;
+                p[a][2] += ph * uz;
+                if (a < 3) {
+                    T[a][0] += ph * qxx;
+                    T[a][1] += ph * qyy;
+                    T[a][2] += ph * qzz;
+                    T[a][3] += ph * qxy;
+                    T[a][4] += ph * qxz;
+                    T[a][5] += ph * qyz;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 16; k++) D[k] = G[k];
+    int e = 16;
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+        for (int b = a; b < 4; b++) D[e++] = p[a][0] * p[b][0] + p[a][1] * p[b][1] + p[a][2] * p[b][2];
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = a; b < 3; b++)
+            D[e++] = T[a][0] * T[b][0] + T[a][1] * T[b][1] + T[a][2] * T[b][2] +
+                     2.0f * (T[a][3] * T[b][3] + T[a][4] * T[b][4] + T[a][5] * T[b][5]);
+#pragma unroll
+    for (int m = 0; m < 3; m++) {
+        V[3 * m] = p[m][0];
+        V[3 * m + 1] = p[m][1];
+        V[3 * m + 2] = p[m][2];
+    }
+}
+
+// ---------------------------------------------------------- tensor-core MLP
+
+__device__ __forceinline__ uint32_t lds32(const __nv_bfloat16* p)
+{
+    return *reinterpret_cast<const uint32_t*>(p);
+}
+
+__device__ __forceinline__ void sts_bf2(__nv_bfloat16* p, float lo, float hi)
+{
+    *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(lo, hi);
+}
+
+// D += A B on one 16x8x16 tile: bfloat16 operands, FP32 accumulators
+__device__ __forceinline__ void mma_bf16_16816(float c[4], const uint32_t a[4], uint32_t b0,
+                                               uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+        "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// acc[2][NT][4] = A[32 rows of this warp][K] * Bt[NT*8][K]^T (A row stride AS,
+// Bt row stride BS, both bf16 in shared memory)
+template <int K, int NT, int AS, int BS>
+__device__ __forceinline__ void warp_gemm(float acc[2][NT][4], const __nv_bfloat16* A,
+                                          const __nv_bfloat16* Bt, int lane)
+{
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int mt = 0; mt < 2; mt++)
+#pragma unroll
+        for (int nt = 0; nt < NT; nt++) acc[mt][nt][0] = acc[mt][nt][1] = acc[mt][nt][2] = acc[mt][nt][3] = 0.0f;
+#pragma unroll
+    for (int kk = 0; kk < K / 16; kk++) {
+        uint32_t a[2][4];
+#pragma unroll
+        for (int mt = 0; mt < 2; mt++) {
+            const __nv_bfloat16* pa = A + (16 * mt + g) * AS + 16 * kk + 2 * t;
+            a[mt][0] = lds32(pa);
+            a[mt][1] = lds32(pa + 8 * AS);
+            a[mt][2] = lds32(pa + 8);
+            a[mt][3] = lds32(pa + 8 * AS + 8);
+        }
+#pragma unroll
+        for (int nt = 0; nt < NT; nt++) {
+            const __nv_bfloat16* pb = Bt + (8 * nt + g) * BS + 16 * kk + 2 * t;
+            const uint32_t b0 = lds32(pb), b1 = lds32(pb + 8);
+            mma_bf16_16816(acc[0][nt], a[0], b0, b1);
+            mma_bf16_16816(acc[1][nt], a[1], b0, b1);
+        }
+    }
+}
+
+// bias + SiLU of a 32x64 accumulator block, rounded to bfloat16 into H
+__device__ __forceinline__ void warp_silu_store(const float acc[2][8][4], const float* bias,
+                                                __nv_bfloat16* H, int lane)
+{
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int mt = 0; mt < 2; mt++)
+#pragma unroll
+        for (int nt = 0; nt < 8; nt++) {
+            const int col = 8 * nt + 2 * t;
+            const float b0 = bias[col], b1 = bias[col + 1];
+            __nv_bfloat16* h = H + (16 * mt + g) * SUR_HS + col;
+            sts_bf2(h, silu_fast(acc[mt][nt][0] + b0), silu_fast(acc[mt][nt][1] + b1));
+            sts_bf2(h + 8 * SUR_HS, silu_fast(acc[mt][nt][2] + b0), silu_fast(acc[mt][nt][3] + b1));
+        }
+}
+
+// The MLP on the 32 rows of one warp: X (bf16, stride SUR_XS) -> w (FP32,
+// Wo[row][4]).  H is the warp's 32-row hidden buffer (stride SUR_HS).  Only
+// the warp's own rows are touched, so warp barriers suffice.
+__device__ __forceinline__ void sur_mlp_warp(const SurPacked& M, const __nv_bfloat16* X,
+                                             __nv_bfloat16* H, float* Wo, int lane)
+{
+    float acc[2][8][4];
+    warp_gemm<SUR_ND, 8, SUR_XS, SUR_XS>(acc, X, M.w1t, lane);
+    warp_silu_store(acc, M.b1, H, lane);
+    __syncwarp();
+    warp_gemm<SUR_NH, 8, SUR_HS, SUR_HS>(acc, H, M.w2t, lane);
+    __syncwarp();  // every lane has read layer 1 before it is overwritten
+    warp_silu_store(acc, M.b2, H, lane);
+    __syncwarp();
+    float o[2][1][4];
+    warp_gemm<SUR_NH, 1, SUR_HS, SUR_HS>(o, H, M.w3t, lane);
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int mt = 0; mt < 2; mt++) {
+        const int row = 16 * mt + g, col = 2 * t;
+        if (col < SUR_NO) {
+            Wo[row * 4 + col] = o[mt][0][0] + M.b3[col];
+            Wo[(row + 8) * 4 + col] = o[mt][0][2] + M.b3[col];
+        }
+        if (col + 1 < SUR_NO) {
+            Wo[row * 4 + col + 1] = o[mt][0][1] + M.b3[col + 1];
+            Wo[(row + 8) * 4 + col + 1] = o[mt][0][3] + M.b3[col + 1];
+        }
+    }
+    __syncwarp();
+}
+
+struct SurSmem {
+    SurPacked M;
+    __nv_bfloat16 X[SUR_BLOCK * SUR_XS];
+    __nv_bfloat16 H[SUR_BLOCK * SUR_HS];
+    float Wo[SUR_BLOCK * 4];
+};
+
+__device__ __forceinline__ void stage_model(SurPacked& M, const SurPacked* src)
+{
+    const int4* s = reinterpret_cast<const int4*>(src);
+    int4* d = reinterpret_cast<int4*>(&M);
+    for (int k = threadIdx.x; k < (int)(sizeof(SurPacked) / 16); k += blockDim.x) d[k] = s[k];
+}
+
+// normalised input row of this thread into X (bf16)
+__device__ __forceinline__ void stage_input(const SurPacked& M, const float D[SUR_ND], bool active,
+                                            __nv_bfloat16* xrow)
+{
+#pragma unroll
+    for (int k = 0; k < SUR_ND; k += 2) {
+        const float a = active ? (D[k] - M.mean[k]) / M.scale[k] : 0.0f;
+        const float b = active ? (D[k + 1] - M.mean[k + 1]) / M.scale[k + 1] : 0.0f;
+        sts_bf2(xrow + k, a, b);
+    }
+}
+
+// ---------------------------------------------------------------- kernels
+
+// one thread per sorted molecule, 128 per CTA: descriptors in registers,
+// then (mode 0) the CTA's 128 x 32 input tile through the MLP on the tensor
+// cores (each warp its own 32 rows) and F = sum_m w_m v_m, or (mode 1) the
+// raw descriptors, vectors and current ATM force appended to the data set
+__global__ void __launch_bounds__(SUR_BLOCK, 4) k_sur_forces(const SurForceArgs A)
+{
+    __shared__ __align__(16) SurSmem S;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (A.mode == 0) stage_model(S.M, A.model);
+    const long long n = A.n;
+    const long long s = (long long)blockIdx.x * SUR_BLOCK + tid;
+    const bool active = s < n;
+    float D[SUR_ND], V[SUR_NV];
+    if (active) {
+        const int cg = A.cell_sorted[s];
+        const Rep& rp = A.b.rep[A.b.rep_of_cell[cg]];
+        int cx, cy, cz;
+        cell_coords(rp.g, cg - rp.cell0, cx, cy, cz);
+        sur_descriptor_row(rp, A.xl32, n, A.cell_start + rp.cell0, cx, cy, cz, s, D, V);
+    } else {
+#pragma unroll
+        for (int k = 0; k < SUR_ND; k++) D[k] = 0.0f;
+#pragma unroll
+        for (int k = 0; k < SUR_NV; k++) V[k] = 0.0f;
+    }
+    if (A.mode == 1) {
+        if (active) {
+            const long long row = A.row0 + s;
+            float* d = A.d_out + row * SUR_ND;
+#pragma unroll
+            for (int k = 0; k < SUR_ND; k++) d[k] = D[k];
+            float* v = A.v_out + row * SUR_NV;
+#pragma unroll
+            for (int k = 0; k < SUR_NV; k++) v[k] = V[k];
+            float* t = A.t_out + row * 3;
+            t[0] = (float)A.f_atm[s];
+            t[1] = (float)A.f_atm[n + s];
+            t[2] = (float)A.f_atm[2 * n + s];
+        }
+        return;
+    }
+    __syncthreads();  // model staged
+    stage_input(S.M, D, active, S.X + tid * SUR_XS);
+    __syncwarp();
+    sur_mlp_warp(S.M, S.X + warp * 32 * SUR_XS, S.H + warp * 32 * SUR_HS, S.Wo + warp * 32 * 4, lane);
+    if (active) {
+        const float w0 = S.Wo[tid * 4], w1 = S.Wo[tid * 4 + 1], w2 = S.Wo[tid * 4 + 2];
+#pragma unroll
+        for (int c = 0; c < 3; c++)
+            A.f_atm[c * n + s] = (double)(w0 * V[c] + w1 * V[3 + c] + w2 * V[6 + c]);
+    }
+}
+
+// the MLP on given rows D[n][32], V[n][9] -> w[n][3], f[n][3]
+__global__ void __launch_bounds__(SUR_BLOCK, 4) k_sur_mlp_rows(long long n, const float* __restrict__ Din,
+                                                            const float* __restrict__ Vin,
+                                                            const SurPacked* model, float* w,
+                                                            float* f)
+{
+    __shared__ __align__(16) SurSmem S;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    stage_model(S.M, model);
+    const long long s = (long long)blockIdx.x * SUR_BLOCK + tid;
+    const bool active = s < n;
+    float D[SUR_ND];
+#pragma unroll
+    for (int k = 0; k < SUR_ND; k++) D[k] = active ? Din[s * SUR_ND + k] : 0.0f;
+    __syncthreads();
+    stage_input(S.M, D, active, S.X + tid * SUR_XS);
+    __syncwarp();
+    sur_mlp_warp(S.M, S.X + warp * 32 * SUR_XS, S.H + warp * 32 * SUR_HS, S.Wo + warp * 32 * 4, lane);
+    if (active) {
+        const float w0 = S.Wo[tid * 4], w1 = S.Wo[tid * 4 + 1], w2 = S.Wo[tid * 4 + 2];
+        w[s * 3] = w0;
+        w[s * 3 + 1] = w1;
+        w[s * 3 + 2] = w2;
+        const float* v = Vin + s * SUR_NV;
+#pragma unroll
+        for (int c = 0; c < 3; c++) f[s * 3 + c] = w0 * v[c] + w1 * v[3 + c] + w2 * v[6 + c];
+    }
+}
+
+// ------------------------------------------------------------- training
+
+constexpr int GH = 65;                 // row stride of the 64-wide FP32 tiles
+constexpr int GX = 33;                 // row stride of the input tile
+constexpr int SUR_NP_PAD = 6468;
+
+struct GradSmem {
+    static constexpr int P = 0;
+    static constexpr int W2T = P + SUR_NP_PAD;          // W2 transposed [j][k]
+    static constexpr int X = W2T + SUR_NH * SUR_NH;
+    static constexpr int H1 = X + SUR_TILE * GX;
+    static constexpr int S1 = H1 + SUR_TILE * GH;       // silu'(z1), then dL/dz1
+    static constexpr int H2 = S1 + SUR_TILE * GH;
+    static constexpr int S2 = H2 + SUR_TILE * GH;       // silu'(z2), then dL/dz2
+    static constexpr int V = S2 + SUR_TILE * GH;
+    static constexpr int T = V + SUR_TILE * SUR_NV;
+    static constexpr int W = T + SUR_TILE * 3;          // outputs w, then dL/dw
+    static constexpr int END = W + SUR_TILE * 4;
+};
+constexpr size_t SUR_GRAD_SMEM = GradSmem::END * sizeof(float) + SUR_TILE * sizeof(double);
+
+__device__ __forceinline__ float sigm(float z) { return 1.0f / (1.0f + expf(-z)); }
+
+__global__ void __launch_bounds__(SUR_GRAD_THREADS) k_sur_grad(const SurGradArgs A)
+{
+    extern __shared__ __align__(16) float sm[];
+    float* P = sm + GradSmem::P;
+    float* W2T = sm + GradSmem::W2T;
+    float* X = sm + GradSmem::X;
+    float* H1 = sm + GradSmem::H1;
+    float* S1 = sm + GradSmem::S1;
+    float* H2 = sm + GradSmem::H2;
+    float* S2 = sm + GradSmem::S2;
+    float* Vs = sm + GradSmem::V;
+    float* Ts = sm + GradSmem::T;
+    float* Wt = sm + GradSmem::W;
+    double* Ls = reinterpret_cast<double*>(sm + GradSmem::END);
+    const int tid = threadIdx.x;
+    const long long base = (long long)blockIdx.x * SUR_TILE;
+
+    for (int k = tid; k < SUR_NP; k += SUR_GRAD_THREADS) P[k] = A.P[k];
+    for (int k = tid; k < SUR_NH * SUR_NH; k += SUR_GRAD_THREADS) {
+        const int kk = k / SUR_NH, j = k % SUR_NH;
+        W2T[j * SUR_NH + kk] = A.P[SUR_OFF_W2 + k];
+    }
+    for (int e = tid; e < SUR_TILE * SUR_ND; e += SUR_GRAD_THREADS) {
+        const int i = e / SUR_ND, q = e % SUR_ND;
+        const long long row = base + i;
+        float x = 0.0f;
+        if (row < A.batch) {
+            const long long smp = A.idx ? A.idx[row] : row;
+            x = (A.D[smp * SUR_ND + q] - A.mean[q]) / A.scale[q];
+        }
+        X[i * GX + q] = x;
+    }
+    for (int e = tid; e < SUR_TILE * SUR_NV; e += SUR_GRAD_THREADS) {
+        const int i = e / SUR_NV, q = e % SUR_NV;
+        const long long row = base + i;
+        Vs[e] = row < A.batch ? A.V[(A.idx ? A.idx[row] : row) * SUR_NV + q] : 0.0f;
+    }
+    for (int e = tid; e < SUR_TILE * 3; e += SUR_GRAD_THREADS) {
+        const int i = e / 3, q = e % 3;
+        const long long row = base + i;
+        Ts[e] = row < A.batch ? A.T[(A.idx ? A.idx[row] : row) * 3 + q] : 0.0f;
+    }
+    __syncthreads();
+
+    // thread tile of the 64 x 64 products: rows rg + 0..3, columns cg + 16 c
+    const int rg = (tid >> 4) * 4, cg = tid & 15;
+
+    // layer 1: z1 = X W1 + b1
+    {
+        float z[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; r++)
+#pragma unroll
+            for (int c = 0; c < 4; c++) z[r][c] = P[SUR_OFF_B1 + cg + 16 * c];
+        for (int q = 0; q < SUR_ND; q++) {
+            float xa[4], wb[4];
+#pragma unroll
+            for (int r = 0; r < 4; r++) xa[r] = X[(rg + r) * GX + q];
+#pragma unroll
+            for (int c = 0; c < 4; c++) wb[c] = P[SUR_OFF_W1 + q * SUR_NH + cg + 16 * c];
+#pragma unroll
+            for (int r = 0; r < 4; r++)
+#pragma unroll
+                for (int c = 0; c < 4; c++) z[r][c] = fmaf(xa[r], wb[c], z[r][c]);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; r++)
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                const float zz = z[r][c], sg = sigm(zz);
+                H1[(rg + r) * GH + cg + 16 * c] = zz * sg;
+                S1[(rg + r) * GH + cg + 16 * c] = sg * (1.0f + zz * (1.0f - sg));
+            }
+    }
+    __syncthreads();
+    // layer 2: z2 = H1 W2 + b2
+    {
+        float z[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; r++)
+#pragma unroll
+            for (int c = 0; c < 4; c++) z[r][c] = P[SUR_OFF_B2 + cg + 16 * c];
+        for (int k = 0; k < SUR_NH; k++) {
+            float ha[4], wb[4];
+#pragma unroll
+            for (int r = 0; r < 4; r++) ha[r] = H1[(rg + r) * GH + k];
+#pragma unroll
+            for (int c = 0; c < 4; c++) wb[c] = P[SUR_OFF_W2 + k * SUR_NH + cg + 16 * c];
+#pragma unroll
+            for (int r = 0; r < 4; r++)
+#pragma unroll
+                for (int c = 0; c < 4; c++) z[r][c] = fmaf(ha[r], wb[c], z[r][c]);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; r++)
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                const float zz = z[r][c], sg = sigm(zz);
+                H2[(rg + r) * GH + cg + 16 * c] = zz * sg;
+                S2[(rg + r) * GH + cg + 16 * c] = sg * (1.0f + zz * (1.0f - sg));
+            }
+    }
+    __syncthreads();
+    // outputs w = H2 W3 + b3
+    if (tid < SUR_TILE * SUR_NO) {
+        const int i = tid / SUR_NO, m = tid % SUR_NO;
+        float acc = P[SUR_OFF_B3 + m];
+        for (int k = 0; k < SUR_NH; k++) acc = fmaf(H2[i * GH + k], P[SUR_OFF_W3 + k * SUR_NO + m], acc);
+        Wt[i * 4 + m] = acc;
+    }
+    __syncthreads();
+    // residuals, loss and dL/dw (padding rows have V = T = 0: no contribution)
+    if (tid < SUR_TILE) {
+        const int i = tid;
+        const float* v = Vs + i * SUR_NV;
+        const float w0 = Wt[i * 4], w1 = Wt[i * 4 + 1], w2 = Wt[i * 4 + 2];
+        float r[3];
+        double l = 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            r[c] = (w0 * v[c] + w1 * v[3 + c] + w2 * v[6 + c]) - Ts[i * 3 + c];
+            l += (double)r[c] * (double)r[c];
+        }
+        Ls[i] = l * (double)A.norm;
+        const float two_norm = 2.0f * A.norm;
+#pragma unroll
+        for (int m = 0; m < 3; m++)
+            Wt[i * 4 + m] = two_norm * (r[0] * v[3 * m] + r[1] * v[3 * m + 1] + r[2] * v[3 * m + 2]);
+    }
+    __syncthreads();
+    float* G = A.part + (long long)blockIdx.x * SUR_NP;
+    if (tid == 0) {
+        double l = 0.0;
+        for (int i = 0; i < SUR_TILE; i++) l += Ls[i];
+        A.part_loss[blockIdx.x] = l;
+    }
+    // output layer gradient; dL/dz2 = silu'(z2) * (W3 dL/dw)
+    if (tid < SUR_NH * SUR_NO) {
+        const int k = tid / SUR_NO, m = tid % SUR_NO;
+        float acc = 0.0f;
+        for (int i = 0; i < SUR_TILE; i++) acc = fmaf(H2[i * GH + k], Wt[i * 4 + m], acc);
+        G[SUR_OFF_W3 + k * SUR_NO + m] = acc;
+    } else if (tid < SUR_NH * SUR_NO + SUR_NO) {
+        const int m = tid - SUR_NH * SUR_NO;
+        float acc = 0.0f;
+        for (int i = 0; i < SUR_TILE; i++) acc += Wt[i * 4 + m];
+        G[SUR_OFF_B3 + m] = acc;
+    }
+#pragma unroll
+    for (int r = 0; r < 4; r++)
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            const int i = rg + r, k = cg + 16 * c;
+            const float dh = P[SUR_OFF_W3 + k * 3] * Wt[i * 4] + P[SUR_OFF_W3 + k * 3 + 1] * Wt[i * 4 + 1] +
+                             P[SUR_OFF_W3 + k * 3 + 2] * Wt[i * 4 + 2];
+            S2[i * GH + k] *= dh;
+        }
+    __syncthreads();
+    // second layer gradient; dL/dz1 = silu'(z1) * (W2 dL/dz2)
+    {
+        float g[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; r++)
+#pragma unroll
+            for (int c = 0; c < 4; c++) g[r][c] = 0.0f;
+        for (int i = 0; i < SUR_TILE; i++) {
+            float ha[4], db[4];
+#pragma unroll
+            for (int r = 0; r < 4; r++) ha[r] = H1[i * GH + rg + r];
+#pragma unroll
+            for (int c = 0; c < 4; c++) db[c] = S2[i * GH + cg + 16 * c];
+#pragma unroll
+            for (int r = 0; r < 4; r++)
+#pragma unroll
+                for (int c = 0; c < 4; c++) g[r][c] = fmaf(ha[r], db[c], g[r][c]);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; r++)
+#pragma unroll
+            for (int c = 0; c < 4; c++) G[SUR_OFF_W2 + (rg + r) * SUR_NH + cg + 16 * c] = g[r][c];
+    }
+    if (tid < SUR_NH) {
+        float acc = 0.0f;
+        for (int i = 0; i < SUR_TILE; i++) acc += S2[i * GH + tid];
+        G[SUR_OFF_B2 + tid] = acc;
+    }
+    {
+        float d[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; r++)
+#pragma unroll
+            for (int c = 0; c < 4; c++) d[r][c] = 0.0f;
+        for (int j = 0; j < SUR_NH; j++) {
+            float da[4], wb[4];
+#pragma unroll
+            for (int r = 0; r < 4; r++) da[r] = S2[(rg + r) * GH + j];
+#pragma unroll
+            for (int c = 0; c < 4; c++) wb[c] = W2T[j * SUR_NH + cg + 16 * c];
+#pragma unroll
+            for (int r = 0; r < 4; r++)
+#pragma unroll
+                for (int c = 0; c < 4; c++) d[r][c] = fmaf(da[r], wb[c], d[r][c]);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; r++)
+#pragma unroll
+            for (int c = 0; c < 4; c++) S1[(rg + r) * GH + cg + 16 * c] *= d[r][c];
+    }
+    __syncthreads();
+    // first layer gradient: rows q = 2 (tid >> 4) + 0..1 of W1
+    {
+        const int qg = (tid >> 4) * 2;
+        float g[2][4];
+#pragma unroll
+        for (int r = 0; r < 2; r++)
+#pragma unroll
+            for (int c = 0; c < 4; c++) g[r][c] = 0.0f;
+        for (int i = 0; i < SUR_TILE; i++) {
+            float xa[2], db[4];
+#pragma unroll
+            for (int r = 0; r < 2; r++) xa[r] = X[i * GX + qg + r];
+#pragma unroll
+            for (int c = 0; c < 4; c++) db[c] = S1[i * GH + cg + 16 * c];
+#pragma unroll
+            for (int r = 0; r < 2; r++)
+#pragma unroll
+                for (int c = 0; c < 4; c++) g[r][c] = fmaf(xa[r], db[c], g[r][c]);
+        }
+#pragma unroll
+        for (int r = 0; r < 2; r++)
+#pragma unroll
+            for (int c = 0; c < 4; c++) G[SUR_OFF_W1 + (qg + r) * SUR_NH + cg + 16 * c] = g[r][c];
+    }
+    if (tid < SUR_NH) {
+        float acc = 0.0f;
+        for (int i = 0; i < SUR_TILE; i++) acc += S1[i * GH + tid];
+        G[SUR_OFF_B1 + tid] = acc;
+    }
+}
+
+// packed inference slot of master parameter k
+__device__ __forceinline__ void pack_param(SurPacked* Pk, int k, float val)
+{
+    if (k < SUR_OFF_B1) {
+        Pk->w1t[(k % SUR_NH) * SUR_XS + k / SUR_NH] = __float2bfloat16_rn(val);
+    } else if (k < SUR_OFF_W2) {
+        Pk->b1[k - SUR_OFF_B1] = val;
+    } else if (k < SUR_OFF_B2) {
+        const int e = k - SUR_OFF_W2;
+        Pk->w2t[(e % SUR_NH) * SUR_HS + e / SUR_NH] = __float2bfloat16_rn(val);
+    } else if (k < SUR_OFF_W3) {
+        Pk->b2[k - SUR_OFF_B2] = val;
+    } else if (k < SUR_OFF_B3) {
+        const int e = k - SUR_OFF_W3;
+        Pk->w3t[(e % SUR_NO) * SUR_HS + e / SUR_NO] = __float2bfloat16_rn(val);
+    } else {
+        Pk->b3[k - SUR_OFF_B3] = val;
+    }
+}
+
+// gradient = sum of the CTA parts in CTA order; Adam (Kingma & Ba, Algorithm 1)
+__global__ void __launch_bounds__(256) k_sur_adam(const SurAdamArgs A)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k == 0 && A.loss_out) {
+        double l = 0.0;
+        for (int c = 0; c < A.nct; c++) l += A.part_loss[c];
+        *A.loss_out = l;
+    }
+    if (k >= SUR_NP) return;
+    float g = 0.0f;
+    for (int c = 0; c < A.nct; c++) g += A.part[(long long)c * SUR_NP + k];
+    if (A.grad_out) A.grad_out[k] = g;
+    if (!A.update) return;
+    const float m = A.beta1 * A.m[k] + (1.0f - A.beta1) * g;
+    const float v = A.beta2 * A.v[k] + (1.0f - A.beta2) * g * g;
+    A.m[k] = m;
+    A.v[k] = v;
+    const float p = A.P[k] - A.lr * (m / A.c1) / (sqrtf(v / A.c2) + A.eps);
+    A.P[k] = p;
+    pack_param(A.packed, k, p);
+}
+
+__global__ void k_sur_pack(const float* P, const float* mean, const float* scale, SurPacked* Pk)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < SUR_NP) pack_param(Pk, k, P[k]);
+    if (k < SUR_ND) {
+        Pk->mean[k] = mean[k];
+        Pk->scale[k] = scale[k];
+    }
+}
+
+// splitmix64 output function (Steele, Lea & Flood 2014) of a (seed, step, b) counter
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_sur_sample(long long* idx, long long batch, long long S, unsigned long long seed,
+                             long long step)
+{
+    const long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (b >= batch) return;
+    unsigned long long z = mix64(seed + 0x9E3779B97F4A7C15ull * (unsigned long long)(step + 1));
+    z = mix64(z + 0x9E3779B97F4A7C15ull * (unsigned long long)(b + 1));
+    idx[b] = (long long)(z % (unsigned long long)S);
+}
+
+// column sums of a fixed chunk of rows per CTA (deterministic order)
+__global__ void __launch_bounds__(256) k_sur_stats(const float* __restrict__ D,
+                                                   const float* __restrict__ T, long long S,
+                                                   const double* center, int square,
+                                                   double* part)
+{
+    __shared__ double red[8][SUR_ND + 1];
+    const int tid = threadIdx.x, col = tid & 31, grp = tid >> 5;
+    const long long lo = S * blockIdx.x / SUR_STAT_PARTS, hi = S * (blockIdx.x + 1) / SUR_STAT_PARTS;
+    const double c = center ? center[col] : 0.0;
+    double acc = 0.0, acc_t = 0.0;
+    for (long long i = lo + grp; i < hi; i += 8) {
+        const double d = (double)D[i * SUR_ND + col] - c;
+        acc += square ? d * d : d;
+        if (col < 3) acc_t += (double)T[i * 3 + col] * (double)T[i * 3 + col];
+    }
+    red[grp][col] = acc;
+    // |T|^2 per group: lanes 0..2 add their component in lane order
+    const double t1 = __shfl_sync(0xffffffffu, acc_t, 1), t2 = __shfl_sync(0xffffffffu, acc_t, 2);
+    if (col == 0) red[grp][SUR_ND] = (acc_t + t1) + t2;
+    __syncthreads();
+    if (tid <= SUR_ND) {
+        double s = 0.0;
+        for (int g = 0; g < 8; g++) s += red[g][tid];
+        part[blockIdx.x * (SUR_ND + 1) + tid] = s;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_sur_diff(long long n, const double* __restrict__ a,
+                                                  const double* __restrict__ b, double* acc)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    double d2 = 0.0, b2 = 0.0;
+    if (i < n)
+        for (int c = 0; c < 3; c++) {
+            const double d = a[c * n + i] - b[c * n + i];
+            d2 += d * d;
+            b2 += b[c * n + i] * b[c * n + i];
+        }
+    for (int o = 16; o > 0; o >>= 1) {
+        d2 += __shfl_down_sync(0xffffffffu, d2, o);
+        b2 += __shfl_down_sync(0xffffffffu, b2, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(acc, d2);
+        atomicAdd(acc + 1, b2);
+    }
+}
+
+unsigned blocks_of(long long n, int b) { return (unsigned)((n + b - 1) / b); }
+
+}  // namespace
+
+cudaError_t launch_sur_forces(const SurForceArgs& a, cudaStream_t st)
+{
+    if (a.n <= 0) return cudaSuccess;
+    k_sur_forces<<<blocks_of(a.n, SUR_BLOCK), SUR_BLOCK, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sur_mlp_rows(long long n, const float* D, const float* V, const SurPacked* model,
+                                float* w, float* f, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    k_sur_mlp_rows<<<blocks_of(n, SUR_BLOCK), SUR_BLOCK, 0, st>>>(n, D, V, model, w, f);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sur_grad(const SurGradArgs& a, int nct, cudaStream_t st)
+{
+    if (nct <= 0) return cudaSuccess;
+    // per device; cheap enough to repeat on every launch
+    cudaError_t e = cudaFuncSetAttribute(k_sur_grad, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)SUR_GRAD_SMEM);
+    if (e != cudaSuccess) return e;
+    k_sur_grad<<<nct, SUR_GRAD_THREADS, SUR_GRAD_SMEM, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sur_adam(const SurAdamArgs& a, cudaStream_t st)
+{
+    k_sur_adam<<<blocks_of(SUR_NP, 256), 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sur_pack(const float* P, const float* mean, const float* scale, SurPacked* packed,
+                            cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(packed, 0, sizeof(SurPacked), st);
+    if (e != cudaSuccess) return e;
+    k_sur_pack<<<blocks_of(SUR_NP, 256), 256, 0, st>>>(P, mean, scale, packed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sur_sample(long long* idx, long long batch, long long S, unsigned long long seed,
+                              long long step, cudaStream_t st)
+{
+    if (batch <= 0 || S <= 0) return cudaSuccess;
+    k_sur_sample<<<blocks_of(batch, 256), 256, 0, st>>>(idx, batch, S, seed, step);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sur_stats(const float* D, const float* T, long long S, const double* center,
+                             int square, double* part, cudaStream_t st)
+{
+    k_sur_stats<<<SUR_STAT_PARTS, 256, 0, st>>>(D, T, S, center, square, part);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sur_diff(long long n, const double* a, const double* b, double* acc,
+                            cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    k_sur_diff<<<blocks_of(n, 256), 256, 0, st>>>(n, a, b, acc);
+    return cudaGetLastError();
+}
+
+}  // namespace atm3

@@ -1,0 +1,130 @@
+// surrogate.cuh -- learned per-molecule model of the ATM three-body force:
+// device types and host launchers of sur_kernels.cu.
+//
+// Model (the library's own; the paper evaluates the triplet sum exactly):
+//   neighbours j of i with r = |r_j - r_i| < r_c, rhat = (r_j - r_i) / r,
+//   cutoff f_c(r) = (cos(pi r / r_c) + 1) / 2;
+//   16 radial channels G_k = sum_j exp(-eta_g (r - mu_k)^2) f_c,
+//      mu_k = 0.8 + k d_g, d_g = (r_c - 0.8) / 15, eta_g = 1 / (2 d_g^2);
+//   4 vector channels phi_a = exp(-eta_v (r - nu_a)^2) f_c,
+//      nu_a = 0.8 + (a + 1/2) d_v, d_v = (r_c - 0.8) / 4, eta_v = 1 / (2 d_v^2),
+//      p_a = sum_j phi_a rhat, T_a = sum_j phi_a (rhat rhat^T - I/3) (a < 3);
+//   descriptors D = [G_0..15, p_a.p_b (ab = 00 01 02 03 11 12 13 22 23 33),
+//                    tr(T_a T_b) (ab = 00 01 02 11 12 22)];
+//   MLP xn = (D - mean) / scale -> silu(xn W1 + b1) -> silu(. W2 + b2) -> w = . W3 + b3;
+//   F_i = sum_{m<3} w_m p_m.
+// Inference runs in bfloat16 on the tensor cores with FP32 accumulation
+// (inputs, weights and the two hidden activations rounded to bfloat16);
+// training runs in FP32 on FP32 master weights.
+#pragma once
+#include <cuda_bf16.h>
+
+#include "atm3_internal.cuh"
+
+namespace atm3 {
+
+constexpr int SUR_ND = 32;   // descriptors
+constexpr int SUR_NH = 64;   // hidden width
+constexpr int SUR_NO = 3;    // outputs (weights of the three vectors)
+constexpr int SUR_NV = 9;    // three 3-vectors
+constexpr int SUR_OFF_W1 = 0;
+constexpr int SUR_OFF_B1 = SUR_OFF_W1 + SUR_ND * SUR_NH;
+constexpr int SUR_OFF_W2 = SUR_OFF_B1 + SUR_NH;
+constexpr int SUR_OFF_B2 = SUR_OFF_W2 + SUR_NH * SUR_NH;
+constexpr int SUR_OFF_W3 = SUR_OFF_B2 + SUR_NH;
+constexpr int SUR_OFF_B3 = SUR_OFF_W3 + SUR_NH * SUR_NO;
+constexpr int SUR_NP = SUR_OFF_B3 + SUR_NO;  // 6467
+
+// row strides (bf16 elements) of the tensor-core operands in shared memory;
+// 40 and 72 put the eight rows a fragment load touches in distinct banks
+constexpr int SUR_XS = 40;   // K = 32 operands
+constexpr int SUR_HS = 72;   // K = 64 operands
+
+// Inference weights as the tensor-core kernel stages them: B operands n-major
+// with k contiguous (row n holds the weights into output n), padded rows;
+// W3 padded to 8 outputs (rows 3..7 zero).  One flat block, copied to shared
+// memory with 16-byte loads.
+struct SurPacked {
+    __nv_bfloat16 w1t[SUR_NH * SUR_XS];
+    __nv_bfloat16 w2t[SUR_NH * SUR_HS];
+    __nv_bfloat16 w3t[8 * SUR_HS];
+    float b1[SUR_NH], b2[SUR_NH], b3[8];
+    float mean[SUR_ND], scale[SUR_ND];
+};
+static_assert(sizeof(SurPacked) % 16 == 0, "SurPacked is copied in 16-byte pieces");
+
+struct SurForceArgs {
+    Batch b;
+    long long n;              // SoA stride = b.ntot
+    const float* xl32;        // sorted cell-local FP32 coordinates, SoA [3n]
+    const int* cell_start;    // [ncell + 1]
+    const int* cell_sorted;   // [n]
+    const SurPacked* model;
+    double* f_atm;            // [3n] sorted order: surrogate force (mode 0)
+    // mode 1 (collect): raw descriptors, vectors and the current f_atm as the
+    // training target, rows [row0, row0 + n) of the data set (sorted order)
+    float* d_out;             // [.][32]
+    float* v_out;             // [.][9]
+    float* t_out;             // [.][3]
+    long long row0;
+    int mode;
+};
+
+// training: FP32 forward + backward of one minibatch; CTA c handles the
+// samples idx[64 c .. 64 c + 63] (< batch), writes its gradient part[c][SUR_NP]
+// and loss part_loss[c] (sum of squared residuals * norm)
+struct SurGradArgs {
+    const float* D;           // [S][32] raw descriptors
+    const float* V;           // [S][9]
+    const float* T;           // [S][3] target forces
+    const long long* idx;     // [batch] sample rows (nullptr: rows 0..batch-1)
+    long long batch;
+    const float* P;           // [SUR_NP] FP32 master parameters
+    const float* mean;        // [32]
+    const float* scale;       // [32]
+    float norm;               // 1 / (3 batch sigma2)
+    float* part;              // [nct][SUR_NP]
+    double* part_loss;        // [nct]
+};
+
+constexpr int SUR_TILE = 64;      // samples per CTA of the training kernel
+constexpr int SUR_GRAD_THREADS = 256;
+
+struct SurAdamArgs {
+    const float* part;        // [nct][SUR_NP]
+    const double* part_loss;  // [nct]
+    int nct;
+    float* P;                 // master parameters (updated when update != 0)
+    float* m;
+    float* v;
+    const float* mean;
+    const float* scale;
+    SurPacked* packed;        // inference copy (written when update != 0)
+    float* grad_out;          // optional [SUR_NP] summed gradient
+    double* loss_out;         // optional loss of this step
+    int update;
+    float lr, beta1, beta2, eps, c1, c2;  // c1 = 1 - beta1^t, c2 = 1 - beta2^t
+};
+
+cudaError_t launch_sur_forces(const SurForceArgs& a, cudaStream_t st);
+// MLP on given descriptor rows (no neighbour search): w[n][3], f[n][3]
+cudaError_t launch_sur_mlp_rows(long long n, const float* D, const float* V,
+                                const SurPacked* model, float* w, float* f, cudaStream_t st);
+cudaError_t launch_sur_grad(const SurGradArgs& a, int nct, cudaStream_t st);
+cudaError_t launch_sur_adam(const SurAdamArgs& a, cudaStream_t st);
+// pack FP32 master parameters + normalisation into the inference layout
+cudaError_t launch_sur_pack(const float* P, const float* mean, const float* scale,
+                            SurPacked* packed, cudaStream_t st);
+// minibatch rows: idx[b] = splitmix64(seed, step, b) mod S
+cudaError_t launch_sur_sample(long long* idx, long long batch, long long S, unsigned long long seed,
+                              long long step, cudaStream_t st);
+// partial sums over 256 fixed chunks of the data set: part[c][0..31] = sum of
+// (D - center) or (D - center)^2 (square != 0), part[c][32] = sum |T|^2
+cudaError_t launch_sur_stats(const float* D, const float* T, long long S, const double* center,
+                             int square, double* part, cudaStream_t st);
+constexpr int SUR_STAT_PARTS = 256;
+// sum of |a - b|^2 and |b|^2 over SoA [3n] FP64 arrays, added to acc[0..1]
+cudaError_t launch_sur_diff(long long n, const double* a, const double* b, double* acc,
+                            cudaStream_t st);
+
+}  // namespace atm3

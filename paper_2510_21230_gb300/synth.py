@@ -158,3 +158,26 @@ CONFIGS = {
 def config(name):
     c = CONFIGS[name]
     return homogeneous(c["n"], c["rho"], c["T"], c["seed"])
+
+
+# ------------------------------------------------- surrogate test inputs
+
+SUR_NDESC, SUR_NVEC, SUR_NPARAM = 32, 9, 6467
+
+
+def sur_params(seed, wscale=0.3):
+    """Random surrogate parameters (float32, the model's flat layout)."""
+    rng = np.random.default_rng(seed)
+    return rng.normal(0.0, wscale, SUR_NPARAM).astype(np.float32)
+
+
+def sur_rows(n, seed, mean=None, scale=None, tscale=0.1):
+    """Random descriptor rows around (mean, scale), vectors and targets
+    (float32), standing in for a data set in tests of the MLP alone."""
+    rng = np.random.default_rng(seed)
+    mean = np.zeros(SUR_NDESC) if mean is None else np.asarray(mean, dtype=np.float64)
+    scale = np.ones(SUR_NDESC) if scale is None else np.asarray(scale, dtype=np.float64)
+    D = (rng.normal(size=(n, SUR_NDESC)) * scale + mean).astype(np.float32)
+    V = rng.normal(size=(n, SUR_NVEC)).astype(np.float32)
+    T = (rng.normal(size=(n, 3)) * tscale).astype(np.float32)
+    return D, V, T
