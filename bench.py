@@ -105,6 +105,16 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(value, device):
+    """The largest value over all ranks of the process group (the job's time
+    is its slowest rank's)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def workload(name, rank):
     c = synth.CONFIGS[name]
     cfg = synth.homogeneous(c["n"], c["rho"], c["T"], c["seed"] + rank)
@@ -233,9 +243,7 @@ def run_ours(args):
         prof = sysm.get_profile()
         res = sysm.step(0, trav, trunc, prec)
         if ws > 1:
-            t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+            ms = max_over_ranks(ms, "cuda")
         return dict(ms=ms, host_s=t_host, prof=prof, res=res, clocks=clk)
 
     clocks = ClockSampler(local) if rank == 0 else None
