@@ -155,14 +155,14 @@ __host__ __device__ inline OwnerSmem owner_smem_plan(int mcap, int nwarps)
 //  pos32 / sh32  their FP32 copies (FP64 path: prefilter)
 //  pair rule:    adjacency bitmask rows and transpose, per-word prefix
 //                popcounts, row offsets (edge numbering), third-member slot
-//                masks, edge vectors (dx, dy, dz, r^2), edge scalars G; the
-//                per-molecule fallback accumulators alias the edge vectors
+//                masks, edge list, FP64 edge vectors (dx, dy, dz, r^2), edge
+//                scalars G; the per-molecule fallback accumulators alias G
 //  product rule: dense FP32 squared distances D (optional), dense G
 //                (acc_mode 0) or per-molecule accumulators (acc_mode 1)
 struct BlockSmem {
     int W;
     size_t off_pos, off_sh, off_pos32, off_sh32, off_idx, off_slot, off_adj, off_adjT, off_rowpre,
-        off_rowoff, off_memb, off_ed, off_G, off_D, off_acc, off_plq, off_queue, total;
+        off_rowoff, off_memb, off_ed, off_el, off_G, off_D, off_acc, off_queue, total;
 };
 
 template <typename R>
@@ -186,17 +186,17 @@ __host__ __device__ inline BlockSmem block_smem_plan(int trunc, int mcap, int nw
     p.off_rowpre = o; o = al(o + (pair ? sizeof(unsigned short) * M * p.W : 0));
     p.off_rowoff = o; o = al(o + (pair ? sizeof(int) * (M + 1) : 0));
     p.off_memb = o;   o = al(o + (pair ? sizeof(unsigned) * 8 * p.W : 0));
-    // pair rule: edge vectors (dx, dy, dz, r^2) -- FP64: one table for the unit's
-    // edges (FP64 arithmetic is the scarce resource); FP32: per-warp partner
-    // vectors of the current first molecule only (shared memory is)
+    // pair rule: FP64 keeps the edge vectors (dx, dy, dz, r^2) of the unit's
+    // edges (FP64 arithmetic is the scarce resource); FP32 recomputes them
+    // (shared memory is).  Both keep the edge list (p | q << 16).
     p.off_ed = o;
-    o = al(o + (pair ? sizeof(R) * 4 * (f64 ? (size_t)gcap : M * nwarps) : 0));
+    o = al(o + (pair && f64 ? sizeof(R) * 4 * (size_t)gcap : 0));
+    p.off_el = o;     o = al(o + (pair ? sizeof(unsigned) * (size_t)gcap : 0));
     const size_t gb = sizeof(R) * (pair ? (size_t)gcap : (acc_mode == 0 ? npair : 0));
     p.off_G = o;      o = al(o + (pair ? (gb > accb ? gb : accb) : gb));
     p.off_D = o;      o = al(o + (!pair && use_d ? sizeof(float) * npair : 0));
     p.off_acc = pair ? p.off_G : o;  // pair rule: the fallback accumulators alias G
     o = al(o + (!pair && acc_mode == 1 ? accb : 0));
-    p.off_plq = o;    o = al(o + (pair ? sizeof(unsigned short) * M * nwarps : 0));
     p.off_queue = o;  o = al(o + (pair ? 0 : sizeof(unsigned long long) * 64 * (size_t)nwarps));
     p.total = o;
     return p;

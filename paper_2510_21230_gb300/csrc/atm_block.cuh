@@ -11,13 +11,12 @@
 //  1. Upper-triangular bitmask adjacency adj[p] = {q > p : |d(p,q)| < r_c}
 //     (one ballot per 32 pairs) and its transpose.
 //  2. Edges are numbered row by row (row offsets and per-word prefix
-//     popcounts).
-//  3. A warp takes a first molecule p and stores its partner vectors d(p, q).
-//     The triangles of its edges (p, q) are the set bits of
-//     adj[p] & adj[q] & (slots allowed as third member): counted per edge,
-//     prefix-summed over the warp and expanded 32 at a time, so every pair test
-//     is shared by all the triplets that contain the pair and every lane of an
-//     expansion round evaluates one triangle.
+//     popcounts) and listed as (p, q); FP64 also tabulates their vectors.
+//  3. A warp takes 32 edges (p, q) at a time.  The triangles of an edge are
+//     the set bits r > q of adj[p] & adj[q] & (slots allowed as third member):
+//     counted per lane, prefix-summed over the warp and expanded 32 per round,
+//     so every pair test is shared by all the triplets that contain the pair
+//     and every lane of a round evaluates one triangle.
 // Product rule
 //  1. Dense FP32 squared distances (or on-the-fly when they do not fit).
 //  3. Every candidate p < q < r of the unit's tasks, enumerated r-major, is
@@ -40,6 +39,19 @@
 namespace atm3 {
 
 __device__ __forceinline__ int tri_index(int x, int y) { return y * (y - 1) / 2 + x; }  // x < y
+
+// position of the set bit of K with nth set bits below it (0 <= nth < popc(K)),
+// by halving the word: the same five steps for every lane
+__device__ __forceinline__ int nth_bit(unsigned K, int nth)
+{
+    int pos = 0, c;
+    c = __popc(K & 0xffffu); if (nth >= c) { nth -= c; K >>= 16; pos += 16; }
+    c = __popc(K & 0xffu);   if (nth >= c) { nth -= c; K >>= 8;  pos += 8; }
+    c = __popc(K & 0xfu);    if (nth >= c) { nth -= c; K >>= 4;  pos += 4; }
+    c = __popc(K & 0x3u);    if (nth >= c) { nth -= c; K >>= 2;  pos += 2; }
+    if (nth >= (int)(K & 1u)) pos += 1;
+    return pos;
+}
 
 // per-molecule force accumulators in shared memory (fallback mode)
 template <typename R>
@@ -142,12 +154,11 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
     unsigned short* rowpre = reinterpret_cast<unsigned short*>(smem + plan.off_rowpre);
     int* rowoff = reinterpret_cast<int*>(smem + plan.off_rowoff);
     unsigned* memb = reinterpret_cast<unsigned*>(smem + plan.off_memb);
-    // FP64: the unit's edge-vector table; FP32: this warp's partner vectors
-    R* ED = reinterpret_cast<R*>(smem + plan.off_ed) + (F64 ? (size_t)0 : (size_t)warp * 4 * mcap);
+    R* ED = reinterpret_cast<R*>(smem + plan.off_ed);                // FP64: edge vectors
+    unsigned* el = reinterpret_cast<unsigned*>(smem + plan.off_el);  // edge list p | q << 16
     R* G = reinterpret_cast<R*>(smem + plan.off_G);
     float* D = reinterpret_cast<float*>(smem + plan.off_D);
     unsigned char* acc = smem + plan.off_acc;
-    unsigned short* plq = reinterpret_cast<unsigned short*>(smem + plan.off_plq) + warp * mcap;
     unsigned long long* queue =
         reinterpret_cast<unsigned long long*>(smem + plan.off_queue) + warp * 64;
 
@@ -305,14 +316,15 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
         edge_mode = s_edges <= A.gcap;
         if (edge_mode) {
             for (int t = tid; t < s_edges; t += blockDim.x) G[t] = R(0);
-            if (F64) {
-                // edge-vector table: d(p -> q) and |d|^2 of every edge, once per unit
-                for (int p = warp; p < M; p += nwarps) {
-                    for (int w = p >> 5; w < Wm; w++) {
-                        unsigned word = adj[p * W + w];
-                        if ((word >> lane) & 1u) {
-                            int q = (w << 5) + lane;
-                            int e = rowoff[p] + rowpre[p * W + w] + __popc(word & lt_mask);
+            // edge list (p, q) in edge order; FP64: d(p -> q) and |d|^2 of every edge
+            for (int p = warp; p < M; p += nwarps) {
+                for (int w = p >> 5; w < Wm; w++) {
+                    unsigned word = adj[p * W + w];
+                    if ((word >> lane) & 1u) {
+                        int q = (w << 5) + lane;
+                        int e = rowoff[p] + rowpre[p * W + w] + __popc(word & lt_mask);
+                        el[e] = (unsigned)p | ((unsigned)q << 16);
+                        if (F64) {
                             R dx, dy, dz;
                             R a = disp(p, q, dx, dy, dz);
                             ED[4 * e] = dx;
@@ -339,24 +351,23 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
     unsigned int nint = 0;
     int qn = 0;
 
-    // pair rule: evaluate triangle (p, q, r), q and r the jj-th and kk-th partners of p
-    // (all lanes call; invalid lanes only take part in nothing but the arithmetic)
-    auto eval_pair = [&](int p, int q, int r, int jj, int kk, bool valid) {
+    // pair rule: evaluate triangle (p, q, r) whose edge (p, q) is edge epq (all
+    // lanes call; invalid lanes carry a valid stand-in and discard the result)
+    auto eval_tri = [&](int p, int q, int r, int epq, bool valid) {
         R dpqx, dpqy, dpqz, dprx, dpry, dprz, dqrx, dqry, dqrz, a, b, c;
-        if (F64 && use_acc) {
+        int epr = 0, eqr = 0;
+        if (!use_acc) {
+            epr = rowoff[p] + rank(p, r);
+            eqr = rowoff[q] + rank(q, r);
+        }
+        if (F64 && !use_acc) {
+            dpqx = ED[4 * epq]; dpqy = ED[4 * epq + 1]; dpqz = ED[4 * epq + 2]; a = ED[4 * epq + 3];
+            dprx = ED[4 * epr]; dpry = ED[4 * epr + 1]; dprz = ED[4 * epr + 2]; b = ED[4 * epr + 3];
+            dqrx = ED[4 * eqr]; dqry = ED[4 * eqr + 1]; dqrz = ED[4 * eqr + 2]; c = ED[4 * eqr + 3];
+        } else {
             a = disp(p, q, dpqx, dpqy, dpqz);
             b = disp(p, r, dprx, dpry, dprz);
             c = disp(q, r, dqrx, dqry, dqrz);
-        } else {
-            const R* E = F64 ? ED + 4 * rowoff[p] : ED;  // p's partners, in bit order
-            dpqx = E[4 * jj]; dpqy = E[4 * jj + 1]; dpqz = E[4 * jj + 2]; a = E[4 * jj + 3];
-            dprx = E[4 * kk]; dpry = E[4 * kk + 1]; dprz = E[4 * kk + 2]; b = E[4 * kk + 3];
-            if (F64) {
-                const int e = rowoff[q] + rank(q, r);
-                dqrx = ED[4 * e]; dqry = ED[4 * e + 1]; dqrz = ED[4 * e + 2]; c = ED[4 * e + 3];
-            } else {
-                c = disp(q, r, dqrx, dqry, dqrz);
-            }
         }
         R uu, ua, ub, uc;
         atm_terms<R>(a, b, c, nu, uu, ua, ub, uc);
@@ -365,9 +376,9 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
         esum.add(uu);
         wsum.add(-(gpq * a + gpr * b + gqr * c));
         if (!use_acc) {
-            atomicAdd(G + rowoff[p] + jj, gpq);
-            atomicAdd(G + rowoff[p] + kk, gpr);
-            atomicAdd(G + rowoff[q] + rank(q, r), gqr);
+            atomicAdd(G + epq, gpq);
+            atomicAdd(G + epr, gpr);
+            atomicAdd(G + eqr, gqr);
         } else {
             Acc<R>::add(acc, mcap, p, gpq * dpqx + gpr * dprx);
             Acc<R>::add(acc, mcap, mcap + p, gpq * dpqy + gpr * dpry);
@@ -453,81 +464,95 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
         return adj[p * W + w] & adj[q * W + w] & (TRAV == 2 ? memb[v * W + w] : FULL);
     };
 
-    for (;;) {
-        int p = 0;
-        if (lane == 0) p = atomicAdd(&s_next, 1);
-        p = __shfl_sync(FULL, p, 0);
-        if (p >= Mfirst) break;
-        const int sp = sslot[p];
-        if (TRAV == 2 && sp == 7) continue;  // no later slot completes an anchored set
-        if (PAIR) {
-            const int np = rowoff[p + 1] - rowoff[p];
-            // p's partners q in bit order with the vectors d(p -> q) and |d|^2
-            for (int w = p >> 5; w < Wm; w++) {
-                unsigned word = adj[p * W + w];
-                if ((word >> lane) & 1u) {
-                    const int jj = rowpre[p * W + w] + __popc(word & lt_mask);
-                    const int q = (w << 5) + lane;
-                    plq[jj] = (unsigned short)q;
-                    if (!F64) {
-                        R dx, dy, dz;
-                        R a = disp(p, q, dx, dy, dz);
-                        ED[4 * jj] = dx;
-                        ED[4 * jj + 1] = dy;
-                        ED[4 * jj + 2] = dz;
-                        ED[4 * jj + 3] = a;
-                    }
-                }
+    // ends (p, q) of edge e: from the edge list, or (no list) p = the last row
+    // with rowoff[p] <= e and q = the (e - rowoff[p])-th set bit of row p
+    auto edge_ends = [&](int e, int& p, int& q) {
+        if (edge_mode) {
+            const unsigned x = el[e];
+            p = (int)(x & 0xffffu);
+            q = (int)(x >> 16);
+            return;
+        }
+        int lo = 0, hi = M - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (rowoff[mid] <= e) lo = mid; else hi = mid - 1;
+        }
+        p = lo;
+        q = p;
+        int j = e - rowoff[p];
+        for (int w = p >> 5; w < Wm; w++) {
+            const unsigned word = adj[p * W + w];
+            const int c = __popc(word);
+            if (j < c) {
+                q = (w << 5) + nth_bit(word, j);
+                break;
             }
-            __syncwarp();
-            for (int c0 = 0; c0 < np; c0 += 32) {
-                const int jj = c0 + lane;
-                const bool act = jj < np;
-                const int q = act ? plq[jj] : 0;
-                const int v = act ? (sp & sslot[q]) : 0;
-                int cnt = 0;
-                if (act)
+            j -= c;
+        }
+    };
+
+    if (PAIR) {
+        // warps take 32 edges (p, q) at a time; the triangles of edge (p, q) are
+        // the set bits r > q of adj[p] & adj[q] (& the slots allowed as third
+        // member); they are counted per lane, prefix-summed and expanded 32 per
+        // round, so every lane of a round evaluates one triangle
+        const int Ework = rowoff[Mfirst];  // edges whose first molecule can open a triangle
+        for (;;) {
+            int e0 = 0;
+            if (lane == 0) e0 = atomicAdd(&s_next, 32);
+            e0 = __shfl_sync(FULL, e0, 0);
+            if (e0 >= Ework) break;
+            const int e = e0 + lane;
+            int p = 0, q = 0, v = 0, cnt = 0;
+            if (e < Ework) {
+                edge_ends(e, p, q);
+                v = sslot[p] & sslot[q];
+                if (!(TRAV == 2 && sslot[p] == 7))  // no later slot completes an anchored set
                     for (int w = q >> 5; w < Wm; w++) cnt += __popc(kword(p, q, v, w));
-                int incl = cnt;
-                for (int o = 1; o < 32; o <<= 1) {
-                    int t = __shfl_up_sync(FULL, incl, o);
-                    if (lane >= o) incl += t;
-                }
-                const int total = __shfl_sync(FULL, incl, 31);
-                const int excl = incl - cnt;
-                for (int t0 = 0; t0 < total; t0 += 32) {
-                    const int t = t0 + lane;
-                    const bool valid = t < total;
-                    // lane owning triangle t: the last lane whose exclusive prefix is <= t
-                    int l = 0;
-                    for (int s = 16; s >= 1; s >>= 1) {
-                        int ec = __shfl_sync(FULL, excl, l + s);
-                        if (ec <= t) l += s;
-                    }
-                    const int ql = __shfl_sync(FULL, q, l);
-                    const int vl = __shfl_sync(FULL, v, l);
-                    int nth = t - __shfl_sync(FULL, excl, l);
-                    int r = 0;
-                    if (valid) {
-                        for (int w = ql >> 5; w < Wm; w++) {
-                            unsigned K = kword(p, ql, vl, w);
-                            int c = __popc(K);
-                            if (nth < c) {
-                                for (int k = 0; k < nth; k++) K &= K - 1u;
-                                r = (w << 5) + __ffs(K) - 1;
-                                break;
-                            }
-                            nth -= c;
-                        }
-                    }
-                    nint += valid ? 1u : 0u;
-                    // invalid lanes evaluate a harmless stand-in (partners 0 and 0)
-                    eval_pair(p, valid ? ql : p, valid ? r : p, valid ? c0 + l : 0,
-                              valid ? rank(p, r) : 0, valid);
-                }
             }
-            __syncwarp();
-        } else {
+            int incl = cnt;
+            for (int o = 1; o < 32; o <<= 1) {
+                int t = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const int total = __shfl_sync(FULL, incl, 31);
+            const int excl = incl - cnt;
+            for (int t0 = 0; t0 < total; t0 += 32) {
+                const bool valid = t0 + lane < total;
+                const int t = valid ? t0 + lane : t0;  // invalid lanes repeat the round's first
+                // lane owning triangle t: the last lane whose exclusive prefix is <= t
+                int l = 0;
+                for (int s = 16; s >= 1; s >>= 1) {
+                    int ec = __shfl_sync(FULL, excl, l + s);
+                    if (ec <= t) l += s;
+                }
+                const int pl = __shfl_sync(FULL, p, l);
+                const int ql = __shfl_sync(FULL, q, l);
+                const int vl = __shfl_sync(FULL, v, l);
+                int nth = t - __shfl_sync(FULL, excl, l);
+                int r = ql;
+                for (int w = ql >> 5; w < Wm; w++) {
+                    const unsigned K = kword(pl, ql, vl, w);
+                    const int c = __popc(K);
+                    if (nth < c) {
+                        r = (w << 5) + nth_bit(K, nth);
+                        break;
+                    }
+                    nth -= c;
+                }
+                nint += valid ? 1u : 0u;
+                eval_tri(pl, ql, r, e0 + l, valid);
+            }
+        }
+    } else {
+        for (;;) {
+            int p = 0;
+            if (lane == 0) p = atomicAdd(&s_next, 1);
+            p = __shfl_sync(FULL, p, 0);
+            if (p >= Mfirst) break;
+            const int sp = sslot[p];
+            if (TRAV == 2 && sp == 7) continue;  // no later slot completes an anchored set
             // every candidate p < q < r, r-major: t = kk (kk - 1) / 2 + jj, q = p+1+jj, r = p+1+kk
             const int base = p + 1, L = M - base;
             const int T = L * (L - 1) / 2;

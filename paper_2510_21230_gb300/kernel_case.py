@@ -1,0 +1,58 @@
+"""Run one force evaluation configuration a few times on a synthetic workload
+and print its CUDA-event time per evaluation -- a small driver for profilers
+(it launches only the cell build, LJ and the chosen ATM or surrogate kernel).
+
+    python -m paper_2510_21230_gb300.kernel_case --workload liquid_n256k \\
+        --trav 3c08 --trunc pair --prec fp32c --reps 3
+
+With --prec surrogate the model is random (seeded) with the descriptor
+normalisation of the workload's own descriptors.
+"""
+import argparse
+import os
+import sys
+
+import numpy as np
+
+if __package__ in (None, ""):
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+from paper_2510_21230_gb300 import atm3, build, synth  # noqa: E402
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("--workload", default="liquid_n32k", choices=sorted(synth.CONFIGS))
+    p.add_argument("--trav", default="3c08", choices=sorted(atm3.TRAVERSALS))
+    p.add_argument("--trunc", default="pair", choices=sorted(atm3.TRUNCATIONS))
+    p.add_argument("--prec", default="fp32c", choices=sorted(atm3.PRECISIONS))
+    p.add_argument("--reps", type=int, default=3)
+    a = p.parse_args()
+    import torch
+    build.build()
+    cfg = synth.config(a.workload)
+    stream = torch.cuda.current_stream()
+    with atm3.AtmSystem(cfg["box"], cfg["n"], rc=2.5, nu=0.073, stream=stream.cuda_stream) as s:
+        s.set_state(cfg["x"], cfg["v"])
+        s.build_cells()
+        if a.prec == "surrogate":
+            D, _ = s.surrogate_descriptors()
+            sd = D.std(axis=0)
+            s.surrogate_set_model(synth.sur_params(7), D.mean(axis=0),
+                                  np.where(sd > 1e-12, sd, 1.0).astype(np.float32))
+        s.compute_forces(a.trav, a.trunc, a.prec)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(a.reps):
+            s.compute_forces(a.trav, a.trunc, a.prec, sync=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        r = s.results()[0]
+    print("%s %s %s %s: %.4f ms per evaluation (cells excluded), n_int3 %d"
+          % (a.workload, a.trav, a.trunc, a.prec, e0.elapsed_time(e1) / a.reps, r["n_int3"]))
+
+
+if __name__ == "__main__":
+    main()

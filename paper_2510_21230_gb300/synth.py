@@ -131,8 +131,8 @@ def slab(box=(30.0, 30.0, 120.0), thickness=30.0, rho_l=0.73, rho_v=0.02, temper
 def replicas(count=64, n_lo=500, n_hi=20000, rho_lo=0.1, rho_hi=0.85, t_lo=0.7, t_hi=1.3,
              config_index=4):
     """Batch of independent replicas: N log-uniform in [n_lo, n_hi], rho and T
-    uniform.  Dense replicas start on an fcc lattice, dilute ones uniformly
-    at random with a minimum spacing of 0.8."""
+    uniform; every replica starts on an fcc lattice scaled to its cubic box
+    (jitter +-0.05) with Maxwell-Boltzmann velocities."""
     out = []
     for r in range(count):
         rng = np.random.default_rng(config_index * 1000 + r)
