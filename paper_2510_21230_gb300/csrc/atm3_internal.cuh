@@ -175,8 +175,9 @@ __host__ __device__ inline BlockSmem block_smem_plan(int trunc, int mcap, int nw
     const bool f64 = sizeof(R) == 8, pair = trunc == 0;
     const size_t M = (size_t)mcap, npair = M * (M - 1) / 2, accb = 24 * M;
     p.W = (mcap + 31) >> 5;
-    p.off_pos = o;    o = al(o + sizeof(R) * 3 * M);
-    p.off_sh = o;     o = al(o + sizeof(R) * 3 * M);
+    // FP64: SoA x[M], y[M], z[M]; FP32: one float4 (x, y, z, 0) per molecule
+    p.off_pos = o;    o = al(o + (f64 ? sizeof(R) * 3 * M : 16 * M));
+    p.off_sh = o;     o = al(o + (f64 ? sizeof(R) * 3 * M : 16 * M));
     p.off_pos32 = o;  o = al(o + (f64 ? sizeof(float) * 3 * M : 0));
     p.off_sh32 = o;   o = al(o + (f64 ? sizeof(float) * 3 * M : 0));
     p.off_idx = o;    o = al(o + sizeof(int) * M);

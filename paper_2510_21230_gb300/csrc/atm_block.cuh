@@ -141,12 +141,15 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
     R* shx = reinterpret_cast<R*>(smem + plan.off_sh);
     R* shy = shx + mcap;
     R* shz = shy + mcap;
-    float* fx32 = F64 ? reinterpret_cast<float*>(smem + plan.off_pos32) : reinterpret_cast<float*>(px);
+    // FP64 path: FP32 copies for the prefilter (SoA); FP32 path: float4 rows
+    float* fx32 = reinterpret_cast<float*>(smem + plan.off_pos32);
     float* fy32 = fx32 + mcap;
     float* fz32 = fy32 + mcap;
-    float* sx32 = F64 ? reinterpret_cast<float*>(smem + plan.off_sh32) : reinterpret_cast<float*>(shx);
+    float* sx32 = reinterpret_cast<float*>(smem + plan.off_sh32);
     float* sy32 = sx32 + mcap;
     float* sz32 = sy32 + mcap;
+    float4* P4 = reinterpret_cast<float4*>(smem + plan.off_pos);
+    float4* S4 = reinterpret_cast<float4*>(smem + plan.off_sh);
     int* sidx = reinterpret_cast<int*>(smem + plan.off_idx);
     unsigned char* sslot = smem + plan.off_slot;
     unsigned* adj = reinterpret_cast<unsigned*>(smem + plan.off_adj);
@@ -191,13 +194,17 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
         int s = 0;
         while (s_beg[s + 1] <= t) s++;
         int g = s_cell0[s] + (t - s_beg[s]);
-        px[t] = A.xl[g];
-        py[t] = A.xl[n + g];
-        pz[t] = A.xl[2 * n + g];
-        shx[t] = (R)s_off[s][0] * w0;
-        shy[t] = (R)s_off[s][1] * w1;
-        shz[t] = (R)s_off[s][2] * w2;
-        if (F64) {
+        if (!F64) {
+            P4[t] = make_float4((float)A.xl[g], (float)A.xl[n + g], (float)A.xl[2 * n + g], 0.0f);
+            S4[t] = make_float4((float)s_off[s][0] * wf0, (float)s_off[s][1] * wf1,
+                                (float)s_off[s][2] * wf2, 0.0f);
+        } else {
+            px[t] = A.xl[g];
+            py[t] = A.xl[n + g];
+            pz[t] = A.xl[2 * n + g];
+            shx[t] = (R)s_off[s][0] * w0;
+            shy[t] = (R)s_off[s][1] * w1;
+            shz[t] = (R)s_off[s][2] * w2;
             fx32[t] = A.xl32[g];
             fy32[t] = A.xl32[n + g];
             fz32[t] = A.xl32[2 * n + g];
@@ -224,17 +231,29 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
     // canonical displacement p -> q, working precision and FP32
     auto disp = [&](int p, int q, R& dx, R& dy, R& dz) -> R {
         typedef Ar<R> Q;
-        dx = Q::add(Q::sub(px[q], px[p]), Q::sub(shx[q], shx[p]));
-        dy = Q::add(Q::sub(py[q], py[p]), Q::sub(shy[q], shy[p]));
-        dz = Q::add(Q::sub(pz[q], pz[p]), Q::sub(shz[q], shz[p]));
+        if constexpr (!F64) {
+            const float4 a = P4[q], b = P4[p], sa = S4[q], sb = S4[p];
+            dx = Q::add(Q::sub(a.x, b.x), Q::sub(sa.x, sb.x));
+            dy = Q::add(Q::sub(a.y, b.y), Q::sub(sa.y, sb.y));
+            dz = Q::add(Q::sub(a.z, b.z), Q::sub(sa.z, sb.z));
+        } else {
+            dx = Q::add(Q::sub(px[q], px[p]), Q::sub(shx[q], shx[p]));
+            dy = Q::add(Q::sub(py[q], py[p]), Q::sub(shy[q], shy[p]));
+            dz = Q::add(Q::sub(pz[q], pz[p]), Q::sub(shz[q], shz[p]));
+        }
         return Q::add(Q::add(Q::mul(dx, dx), Q::mul(dy, dy)), Q::mul(dz, dz));
     };
     auto disp32 = [&](int p, int q) -> float {
         typedef Ar<float> Q;
-        float dx = Q::add(Q::sub(fx32[q], fx32[p]), Q::sub(sx32[q], sx32[p]));
-        float dy = Q::add(Q::sub(fy32[q], fy32[p]), Q::sub(sy32[q], sy32[p]));
-        float dz = Q::add(Q::sub(fz32[q], fz32[p]), Q::sub(sz32[q], sz32[p]));
-        return Q::add(Q::add(Q::mul(dx, dx), Q::mul(dy, dy)), Q::mul(dz, dz));
+        if constexpr (!F64) {
+            R dx, dy, dz;
+            return disp(p, q, dx, dy, dz);
+        } else {
+            float dx = Q::add(Q::sub(fx32[q], fx32[p]), Q::sub(sx32[q], sx32[p]));
+            float dy = Q::add(Q::sub(fy32[q], fy32[p]), Q::sub(sy32[q], sy32[p]));
+            float dz = Q::add(Q::sub(fz32[q], fz32[p]), Q::sub(sz32[q], sz32[p]));
+            return Q::add(Q::add(Q::mul(dx, dx), Q::mul(dy, dy)), Q::mul(dz, dz));
+        }
     };
     // pair-rule decision |d(p,q)| < r_c (FP64 through the FP32 prefilter)
     auto close = [&](int p, int q) -> bool {
