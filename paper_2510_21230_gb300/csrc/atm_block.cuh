@@ -371,8 +371,10 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
     int qn = 0;
 
     // pair rule: evaluate triangle (p, q, r) whose edge (p, q) is edge epq (all
-    // lanes call; invalid lanes carry a valid stand-in and discard the result)
-    auto eval_tri = [&](int p, int q, int r, int epq, bool valid) {
+    // lanes call; invalid lanes carry a valid stand-in and discard the result).
+    // Adds the (p, r) and (q, r) pair scalars and returns the (p, q) one (0 for
+    // invalid lanes and in accumulator mode), which the edge's owner lane sums.
+    auto eval_tri = [&](int p, int q, int r, int epq, bool valid) -> R {
         R dpqx, dpqy, dpqz, dprx, dpry, dprz, dqrx, dqry, dqrz, a, b, c;
         int epr = 0, eqr = 0;
         if (!use_acc) {
@@ -391,13 +393,13 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
         R uu, ua, ub, uc;
         atm_terms<R>(a, b, c, nu, uu, ua, ub, uc);
         R gpq = R(2) * ua, gpr = R(2) * ub, gqr = R(2) * uc;
-        if (!valid) return;
+        if (!valid) return R(0);
         esum.add(uu);
         wsum.add(-(gpq * a + gpr * b + gqr * c));
         if (!use_acc) {
-            atomicAdd(G + epq, gpq);
             atomicAdd(G + epr, gpr);
             atomicAdd(G + eqr, gqr);
+            return gpq;
         } else {
             Acc<R>::add(acc, mcap, p, gpq * dpqx + gpr * dprx);
             Acc<R>::add(acc, mcap, mcap + p, gpq * dpqy + gpr * dpry);
@@ -409,6 +411,7 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
             Acc<R>::add(acc, mcap, mcap + r, -(gpr * dpry + gqr * dqry));
             Acc<R>::add(acc, mcap, 2 * mcap + r, -(gpr * dprz + gqr * dqrz));
         }
+        return R(0);
     };
 
     // product rule: evaluate one queued triplet per lane (all lanes call;
@@ -537,6 +540,7 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
             }
             const int total = __shfl_sync(FULL, incl, 31);
             const int excl = incl - cnt;
+            R gown = R(0);  // (p, q) scalar of this lane's edge, summed over its triangles
             for (int t0 = 0; t0 < total; t0 += 32) {
                 const bool valid = t0 + lane < total;
                 const int t = valid ? t0 + lane : t0;  // invalid lanes repeat the round's first
@@ -561,8 +565,18 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
                     nth -= c;
                 }
                 nint += valid ? 1u : 0u;
-                eval_tri(pl, ql, r, e0 + l, valid);
+                const R gpq = eval_tri(pl, ql, r, e0 + l, valid);
+                if (!use_acc) {
+                    // a round holds each edge's triangles as one run of lanes:
+                    // the run's sum goes to the edge's owner lane
+                    const R run = seg_sum<R>(gpq, valid ? l : -1 - lane, lane);
+                    const bool mine = cnt > 0 && excl < t0 + 32 && excl + cnt > t0;
+                    const int head = (excl > t0 ? excl : t0) - t0;
+                    const R got = __shfl_sync(FULL, run, mine ? head : 0);
+                    if (mine) gown += got;
+                }
             }
+            if (!use_acc && e < Ework && gown != R(0)) atomicAdd(G + e, gown);
         }
     } else {
         for (;;) {
