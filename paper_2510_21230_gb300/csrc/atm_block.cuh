@@ -272,18 +272,29 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
 
     // ---- 1. pair decisions
     if (PAIR) {
+        // row p of the adjacency, its per-word prefix popcounts and its edge
+        // count (kept in rowoff[p + 1] until the row offsets are formed)
         for (int p = warp; p < M; p += nwarps) {
+            int run = 0;
             for (int w = 0; w < Wm; w++) {
                 if (w < (p >> 5)) {
-                    if (lane == 0) adj[p * W + w] = 0u;
+                    if (lane == 0) {
+                        adj[p * W + w] = 0u;
+                        rowpre[p * W + w] = 0;
+                    }
                     continue;
                 }
                 int q = (w << 5) + lane;
                 bool keep = q > p && q < M && close(p, q);
                 unsigned word = __ballot_sync(FULL, keep);
-                if (lane == 0) adj[p * W + w] = word;
+                if (lane == 0) {
+                    adj[p * W + w] = word;
+                    rowpre[p * W + w] = (unsigned short)run;
+                }
+                run += __popc(word);
                 if (keep) atomicOr(&adjT[q * W + (p >> 5)], 1u << (p & 31));
             }
+            if (lane == 0) rowoff[p + 1] = run;
         }
     } else if (A.use_d) {
         for (int t = tid; t < M * (M - 1) / 2; t += blockDim.x) {
@@ -299,22 +310,20 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
     bool edge_mode = false;
     if (PAIR) {
         if (warp == 0) {
+            // row offsets: exclusive prefix sum of the row edge counts
             int run = 0;
             for (int p0 = 0; p0 < M; p0 += 32) {
                 int p = p0 + lane;
-                int c = 0;
-                if (p < M)
-                    for (int w = 0; w < Wm; w++) {
-                        rowpre[p * W + w] = (unsigned short)c;
-                        c += __popc(adj[p * W + w]);
-                    }
+                int c = p < M ? rowoff[p + 1] : 0;
                 int incl = c;
                 for (int o = 1; o < 32; o <<= 1) {
                     int v = __shfl_up_sync(FULL, incl, o);
                     if (lane >= o) incl += v;
                 }
+                __syncwarp();  // every count of this chunk is read before it is overwritten
                 if (p < M) rowoff[p] = run + incl - c;
                 run += __shfl_sync(FULL, incl, 31);
+                __syncwarp();
             }
             if (lane == 0) {
                 rowoff[M] = run;
