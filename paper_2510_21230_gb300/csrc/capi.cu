@@ -13,6 +13,7 @@
 #include "forces.cuh"
 #include "md_kernels.cuh"
 #include "ctx.cuh"
+#include "surrogate.cuh"
 
 using namespace atm3;
 
@@ -613,7 +614,7 @@ static atm_status run_graph_steps(atm_ctx* c, int nsteps, int trav, int trunc, i
     cudaEvent_t ev = ctx_prof_begin(c);
     for (int k = 0; k < nsteps; k++) CU(cudaGraphLaunch(c->graph, c->st));
     ctx_prof_end(c, PK_MD, ev);
-    c->n_launch += (long long)nsteps * KERNELS_PER_STEP;
+    c->n_launch += (long long)nsteps * (KERNELS_PER_STEP + (prec == ATM_SURROGATE ? SUR_LAUNCHES - 1 : 0));
     c->n_atm += nsteps;
     return ATM_OK;
 }

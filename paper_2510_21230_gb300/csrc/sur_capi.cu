@@ -54,6 +54,10 @@ struct SurState {
     int exact_every = 50;
     long long count = 0;
     double* f_scratch = nullptr;  // [3n] surrogate force at an exact step
+    // per-evaluation scratch of the kernels (n rows)
+    float4* xl4 = nullptr;
+    __nv_bfloat16* xb = nullptr;
+    float* vb = nullptr;
     double* d_mon = nullptr;      // [2] sum |diff|^2, sum |exact|^2
     long long checks = 0;
 };
@@ -170,6 +174,27 @@ uint64_t splitmix64(uint64_t& x)
     return z ^ (z >> 31);
 }
 
+// kernel arguments for the context's current cells (scratch allocated on first use)
+atm_status sur_args(atm_ctx* c, SurState* S, SurForceArgs& a)
+{
+    if (!S->xl4 && c->n > 0) {
+        CU(cudaMalloc(&S->xl4, (size_t)c->n * sizeof(float4)));
+        CU(cudaMalloc(&S->xb, (size_t)c->n * SUR_ND * sizeof(__nv_bfloat16)));
+        CU(cudaMalloc(&S->vb, (size_t)c->n * SUR_NV * sizeof(float)));
+    }
+    a = SurForceArgs{};
+    a.b = c->b;
+    a.n = c->n;
+    a.xl32 = c->xl32;
+    a.cell_start = c->start;
+    a.cell_sorted = c->cell_sorted;
+    a.model = S->packed;
+    a.xl4 = S->xl4;
+    a.xb = S->xb;
+    a.vb = S->vb;
+    return ATM_OK;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------- library hooks
@@ -182,16 +207,13 @@ atm_status atm3::sur_enqueue_atm(atm_ctx* c)
     // no triplets: the per-unit energy / virial / count sums are zero
     CU(cudaMemsetAsync(c->unit_ew, 0, 2 * (size_t)c->ncell * sizeof(double), c->st));
     CU(cudaMemsetAsync(c->unit_cnt, 0, 2 * (size_t)c->ncell * sizeof(unsigned long long), c->st));
-    SurForceArgs a{};
-    a.b = c->b;
-    a.n = c->n;
-    a.xl32 = c->xl32;
-    a.cell_start = c->start;
-    a.cell_sorted = c->cell_sorted;
-    a.model = S->packed;
+    SurForceArgs a;
+    atm_status s = sur_args(c, S, a);
+    if (s != ATM_OK) return s;
     a.f_atm = c->f_atm;
     a.mode = 0;
     CU(launch_sur_forces(a, c->st));
+    c->n_launch += SUR_LAUNCHES - 1;  // the caller counts one
     return ATM_OK;
 }
 
@@ -204,18 +226,14 @@ atm_status atm3::sur_enqueue_monitor(atm_ctx* c)
         CU(cudaMalloc(&S->d_mon, 2 * sizeof(double)));
         CU(cudaMemsetAsync(S->d_mon, 0, 2 * sizeof(double), c->st));
     }
-    SurForceArgs a{};
-    a.b = c->b;
-    a.n = c->n;
-    a.xl32 = c->xl32;
-    a.cell_start = c->start;
-    a.cell_sorted = c->cell_sorted;
-    a.model = S->packed;
+    SurForceArgs a;
+    atm_status s = sur_args(c, S, a);
+    if (s != ATM_OK) return s;
     a.f_atm = S->f_scratch;
     a.mode = 0;
     CU(launch_sur_forces(a, c->st));
     CU(launch_sur_diff(c->n, S->f_scratch, c->f_atm, S->d_mon, c->st));
-    c->n_launch += 2;
+    c->n_launch += SUR_LAUNCHES + 1;
     S->checks += 1;
     return ATM_OK;
 }
@@ -239,7 +257,7 @@ void atm3::sur_free(atm_ctx* c)
     if (!S) return;
     void* dev[] = {S->P, S->m, S->v, S->mean, S->scale, S->packed, S->D, S->V, S->T,
                    S->idx, S->part, S->part_loss, S->d_loss, S->stat_part, S->stat_center,
-                   S->grad, S->rows_buf, S->f_scratch, S->d_mon};
+                   S->grad, S->rows_buf, S->f_scratch, S->d_mon, S->xl4, S->xb, S->vb};
     for (void* p : dev)
         if (p) cudaFree(p);
     delete S;
@@ -348,12 +366,9 @@ extern "C" atm_status atm_surrogate_descriptors(atm_ctx* c, float* desc, float* 
     atm_status s = stage(c, S, bd + bv + bt, &buf);
     if (s != ATM_OK) return s;
     char* b = static_cast<char*>(buf);
-    SurForceArgs a{};
-    a.b = c->b;
-    a.n = c->n;
-    a.xl32 = c->xl32;
-    a.cell_start = c->start;
-    a.cell_sorted = c->cell_sorted;
+    SurForceArgs a;
+    s = sur_args(c, S, a);
+    if (s != ATM_OK) return s;
     a.f_atm = c->f_atm;  // read as the (unused) target rows
     a.d_out = reinterpret_cast<float*>(b);
     a.v_out = reinterpret_cast<float*>(b + bd);
@@ -361,7 +376,7 @@ extern "C" atm_status atm_surrogate_descriptors(atm_ctx* c, float* desc, float* 
     a.row0 = 0;
     a.mode = 1;
     CU(launch_sur_forces(a, c->st));
-    c->n_launch += 1;
+    c->n_launch += 2;  // packing + descriptors
     std::vector<float> ds(n * SUR_ND), vs(n * SUR_NV);
     std::vector<int32_t> perm(n);
     CU(cudaMemcpyAsync(ds.data(), a.d_out, n * SUR_ND * 4, cudaMemcpyDeviceToHost, c->st));
@@ -551,12 +566,9 @@ extern "C" atm_status atm_surrogate_add_frame(atm_ctx* c, atm_traversal trav, at
     if (s != ATM_OK) return s;
     s = ctx_enqueue_forces(c, trav, trunc, prec, c->unit_max[trav]);
     if (s != ATM_OK) return s;
-    SurForceArgs a{};
-    a.b = c->b;
-    a.n = c->n;
-    a.xl32 = c->xl32;
-    a.cell_start = c->start;
-    a.cell_sorted = c->cell_sorted;
+    SurForceArgs a;
+    s = sur_args(c, S, a);
+    if (s != ATM_OK) return s;
     a.f_atm = c->f_atm;
     a.d_out = S->D;
     a.v_out = S->V;
@@ -564,7 +576,7 @@ extern "C" atm_status atm_surrogate_add_frame(atm_ctx* c, atm_traversal trav, at
     a.row0 = S->rows;
     a.mode = 1;
     CU(launch_sur_forces(a, c->st));
-    c->n_launch += 1;
+    c->n_launch += 2;  // packing + descriptors
     s = ctx_sync_and_check(c);
     if (s != ATM_OK) return s;
     S->rows += c->n;

@@ -1,6 +1,6 @@
 // sur_kernels.cu -- kernels of the learned ATM force surrogate (model in
-// surrogate.cuh): fused descriptors + bfloat16 tensor-core MLP + force
-// assembly, data-set collection, FP32 training gradient, Adam, statistics.
+// surrogate.cuh): descriptors, bfloat16 tensor-core MLP + force assembly,
+// data-set collection, FP32 training gradient, Adam, statistics.
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -18,92 +18,100 @@ __device__ __forceinline__ float silu_fast(float z) { return z / (1.0f + __expf(
 
 // ------------------------------------------------------------ descriptors
 
-// Descriptors D[32] and vectors V[9] (p_0, p_1, p_2) of sorted molecule s in
-// cell (cx, cy, cz) of replica rp: all molecules of the 27 neighbour cells
-// (cell edge >= r_c, so every neighbour within r_c is among them), FP32
-// displacements from cell-local coordinates plus the cell shift.
-__device__ __forceinline__ void sur_descriptor_row(const Rep& rp, const float* __restrict__ xl,
-                                                   long long n, const int* __restrict__ st,
-                                                   int cx, int cy, int cz, long long s,
-                                                   float D[SUR_ND], float V[SUR_NV])
+// descriptor accumulators of one molecule (registers: every index is static)
+struct SurAcc {
+    float G[16];    // radial channels
+    float p[4][3];  // vector moments
+    float T[3][6];  // traceless quadrupole moments xx yy zz xy xz yz
+};
+
+struct SurConst {
+    float rc2, dg, dv, eta_g, eta_v, pi_rc;
+};
+
+__device__ __forceinline__ SurConst sur_consts(const Rep& rp)
 {
-    const float rc = rp.rcf, rc2 = rp.rc2f;
-    const float dg = (rc - SUR_R0) / 15.0f, dv = (rc - SUR_R0) / 4.0f;
-    const float eta_g = 1.0f / (2.0f * dg * dg), eta_v = 1.0f / (2.0f * dv * dv);
-    const float pi_rc = SUR_PI / rc;
+    SurConst k;
+    const float rc = rp.rcf;
+    k.rc2 = rp.rc2f;
+    k.dg = (rc - SUR_R0) / 15.0f;
+    k.dv = (rc - SUR_R0) / 4.0f;
+    k.eta_g = 1.0f / (2.0f * k.dg * k.dg);
+    k.eta_v = 1.0f / (2.0f * k.dv * k.dv);
+    k.pi_rc = SUR_PI / rc;
+    return k;
+}
+
+__device__ __forceinline__ void sur_zero(SurAcc& a)
+{
+#pragma unroll
+    for (int k = 0; k < 16; k++) a.G[k] = 0.0f;
+#pragma unroll
+    for (int m = 0; m < 4; m++) a.p[m][0] = a.p[m][1] = a.p[m][2] = 0.0f;
+#pragma unroll
+    for (int m = 0; m < 3; m++)
+#pragma unroll
+        for (int c = 0; c < 6; c++) a.T[m][c] = 0.0f;
+}
+
+// one neighbour at displacement (ex, ey, ez), r2 = |e|^2 < r_c^2
+__device__ __forceinline__ void sur_add(SurAcc& a, const SurConst& k, float ex, float ey, float ez,
+                                        float r2)
+{
+    const float ir = rsqrtf(r2);
+    const float r = r2 * ir;
+    const float ux = ex * ir, uy = ey * ir, uz = ez * ir;
+    const float fc = 0.5f * (__cosf(k.pi_rc * r) + 1.0f);
+    const float rr = r - SUR_R0;
+    // r - mu_j as one multiply-add with an immediate (no per-channel constants held)
+#pragma unroll
+    for (int j = 0; j < 16; j++) {
+        const float tt = fmaf(-(float)j, k.dg, rr);
+        a.G[j] += __expf(-k.eta_g * tt * tt) * fc;
+    }
     const float third = 1.0f / 3.0f;
-    float G[16];
-    float p[4][3];
-    float T[3][6];
+    const float qxx = ux * ux - third, qyy = uy * uy - third, qzz = uz * uz - third;
+    const float qxy = ux * uy, qxz = ux * uz, qyz = uy * uz;
 #pragma unroll
-    for (int k = 0; k < 16; k++) G[k] = 0.0f;
-#pragma unroll
-    for (int a = 0; a < 4; a++) p[a][0] = p[a][1] = p[a][2] = 0.0f;
-#pragma unroll
-    for (int a = 0; a < 3; a++)
-#pragma unroll
-        for (int c = 0; c < 6; c++) T[a][c] = 0.0f;
-    const float xs = xl[s], ys = xl[n + s], zs = xl[2 * n + s];
-    for (int t = 0; t < 27; t++) {
-        int dx, dy, dz;
-        offset27(t, dx, dy, dz);
-        const long long nc = cell_at(rp.g, cx, cy, cz, dx, dy, dz);
-        const int q0 = st[nc], q1 = st[nc + 1];
-        const float sx = (float)dx * rp.wf[0], sy = (float)dy * rp.wf[1], sz = (float)dz * rp.wf[2];
-        for (int q = q0; q < q1; q++) {
-            if (q == s) continue;
-            const float ex = (xl[q] - xs) + sx;
-            const float ey = (xl[n + q] - ys) + sy;
-            const float ez = (xl[2 * n + q] - zs) + sz;
-            const float r2 = ex * ex + ey * ey + ez * ez;
-            if (!(r2 < rc2)) continue;
-            const float ir = rsqrtf(r2);
-            const float r = r2 * ir;
-            const float ux = ex * ir, uy = ey * ir, uz = ez * ir;
-            const float fc = 0.5f * (__cosf(pi_rc * r) + 1.0f);
-#pragma unroll
-            for (int k = 0; k < 16; k++) {
-                const float tt = r - (SUR_R0 + (float)k * dg);
-                G[k] += __expf(-eta_g * tt * tt) * fc;
-            }
-            const float qxx = ux * ux - third, qyy = uy * uy - third, qzz = uz * uz - third;
-            const float qxy = ux * uy, qxz = ux * uz, qyz = uy * uz;
-#pragma unroll
-            for (int a = 0; a < 4; a++) {
-                const float tt = r - (SUR_R0 + ((float)a + 0.5f) * dv);
-                const float ph = __expf(-eta_v * tt * tt) * fc;
-                p[a][0] += ph * ux;
-                p[a][1] += ph * uy;
-                p[a][2] += ph * uz;
-                if (a < 3) {
-                    T[a][0] += ph * qxx;
-                    T[a][1] += ph * qyy;
-                    T[a][2] += ph * qzz;
-                    T[a][3] += ph * qxy;
-                    T[a][4] += ph * qxz;
-                    T[a][5] += ph * qyz;
-                }
-            }
+    for (int m = 0; m < 4; m++) {
+        const float tt = fmaf(-((float)m + 0.5f), k.dv, rr);
+        const float ph = __expf(-k.eta_v * tt * tt) * fc;
+        a.p[m][0] += ph * ux;
+        a.p[m][1] += ph * uy;
+        a.p[m][2] += ph * uz;
+        if (m < 3) {
+            a.T[m][0] += ph * qxx;
+            a.T[m][1] += ph * qyy;
+            a.T[m][2] += ph * qzz;
+            a.T[m][3] += ph * qxy;
+            a.T[m][4] += ph * qxz;
+            a.T[m][5] += ph * qyz;
         }
     }
+}
+
+// invariants D[32] and vectors V[9] (p_0, p_1, p_2) of the accumulated moments
+__device__ __forceinline__ void sur_finish(const SurAcc& a, float D[SUR_ND], float V[SUR_NV])
+{
 #pragma unroll
-    for (int k = 0; k < 16; k++) D[k] = G[k];
+    for (int k = 0; k < 16; k++) D[k] = a.G[k];
     int e = 16;
 #pragma unroll
-    for (int a = 0; a < 4; a++)
+    for (int m = 0; m < 4; m++)
 #pragma unroll
-        for (int b = a; b < 4; b++) D[e++] = p[a][0] * p[b][0] + p[a][1] * p[b][1] + p[a][2] * p[b][2];
+        for (int b = m; b < 4; b++)
+            D[e++] = a.p[m][0] * a.p[b][0] + a.p[m][1] * a.p[b][1] + a.p[m][2] * a.p[b][2];
 #pragma unroll
-    for (int a = 0; a < 3; a++)
+    for (int m = 0; m < 3; m++)
 #pragma unroll
-        for (int b = a; b < 3; b++)
-            D[e++] = T[a][0] * T[b][0] + T[a][1] * T[b][1] + T[a][2] * T[b][2] +
-                     2.0f * (T[a][3] * T[b][3] + T[a][4] * T[b][4] + T[a][5] * T[b][5]);
+        for (int b = m; b < 3; b++)
+            D[e++] = a.T[m][0] * a.T[b][0] + a.T[m][1] * a.T[b][1] + a.T[m][2] * a.T[b][2] +
+                     2.0f * (a.T[m][3] * a.T[b][3] + a.T[m][4] * a.T[b][4] + a.T[m][5] * a.T[b][5]);
 #pragma unroll
     for (int m = 0; m < 3; m++) {
-        V[3 * m] = p[m][0];
-        V[3 * m + 1] = p[m][1];
-        V[3 * m + 2] = p[m][2];
+        V[3 * m] = a.p[m][0];
+        V[3 * m + 1] = a.p[m][1];
+        V[3 * m + 2] = a.p[m][2];
     }
 }
 
@@ -187,6 +195,7 @@ __device__ __forceinline__ void sur_mlp_warp(const SurPacked& M, const __nv_bflo
 {
     float acc[2][8][4];
     warp_gemm<SUR_ND, 8, SUR_XS, SUR_XS>(acc, X, M.w1t, lane);
+    __syncwarp();  // the input rows are read before the hidden rows (which may overlay them) are written
     warp_silu_store(acc, M.b1, H, lane);
     __syncwarp();
     warp_gemm<SUR_NH, 8, SUR_HS, SUR_HS>(acc, H, M.w2t, lane);
@@ -218,6 +227,8 @@ struct SurSmem {
     float Wo[SUR_BLOCK * 4];
 };
 
+constexpr int SUR_MW = 32;  // candidate-mask words per molecule: 1024 candidates of its 27 cells
+
 __device__ __forceinline__ void stage_model(SurPacked& M, const SurPacked* src)
 {
     const int4* s = reinterpret_cast<const int4*>(src);
@@ -239,85 +250,218 @@ __device__ __forceinline__ void stage_input(const SurPacked& M, const float D[SU
 
 // ---------------------------------------------------------------- kernels
 
-// one thread per sorted molecule, 128 per CTA: descriptors in registers,
-// then (mode 0) the CTA's 128 x 32 input tile through the MLP on the tensor
-// cores (each warp its own 32 rows) and F = sum_m w_m v_m, or (mode 1) the
-// raw descriptors, vectors and current ATM force appended to the data set
-__global__ void __launch_bounds__(SUR_BLOCK, 4) k_sur_forces(const SurForceArgs A)
+__global__ void __launch_bounds__(256) k_sur_xyz4(long long n, const float* __restrict__ xl,
+                                                  float4* __restrict__ xl4)
 {
-    __shared__ __align__(16) SurSmem S;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    if (A.mode == 0) stage_model(S.M, A.model);
+    const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (s < n) xl4[s] = make_float4(xl[s], xl[n + s], xl[2 * n + s], 0.0f);
+}
+
+// One thread per sorted molecule.  Descriptors in two passes: (A) every
+// candidate of the molecule's 27 cells is tested against the cutoff and
+// recorded as one bit (cheap, so lanes in different cells diverge little);
+// (B) the thread walks its set bits and accumulates the descriptor terms, so
+// the expensive part keeps every lane busy.  More than 1024 candidates: one
+// direct pass.  Mode 0 writes the normalised bfloat16 input row and the
+// vectors for the MLP kernel; mode 1 appends the raw descriptors, vectors and
+// the current ATM force to the data set.  The masks are word-major (word w of
+// thread t at w * SUR_BLOCK + t), free of bank conflicts.
+__global__ void __launch_bounds__(SUR_BLOCK, 5) k_sur_desc(const SurForceArgs A)
+{
+    __shared__ unsigned mask[SUR_MW * SUR_BLOCK];
+    // per thread and neighbour cell t: end of t's candidates in the bit order
+    // and q - k for t's candidates ([t][thread], free of bank conflicts)
+    __shared__ int s_kend[27 * SUR_BLOCK];
+    __shared__ int s_qoff[27 * SUR_BLOCK];
+    const int tid = threadIdx.x;
     const long long n = A.n;
     const long long s = (long long)blockIdx.x * SUR_BLOCK + tid;
-    const bool active = s < n;
-    float D[SUR_ND], V[SUR_NV];
-    if (active) {
-        const int cg = A.cell_sorted[s];
-        const Rep& rp = A.b.rep[A.b.rep_of_cell[cg]];
-        int cx, cy, cz;
-        cell_coords(rp.g, cg - rp.cell0, cx, cy, cz);
-        sur_descriptor_row(rp, A.xl32, n, A.cell_start + rp.cell0, cx, cy, cz, s, D, V);
-    } else {
-#pragma unroll
-        for (int k = 0; k < SUR_ND; k++) D[k] = 0.0f;
-#pragma unroll
-        for (int k = 0; k < SUR_NV; k++) V[k] = 0.0f;
-    }
-    if (A.mode == 1) {
-        if (active) {
-            const long long row = A.row0 + s;
-            float* d = A.d_out + row * SUR_ND;
-#pragma unroll
-            for (int k = 0; k < SUR_ND; k++) d[k] = D[k];
-            float* v = A.v_out + row * SUR_NV;
-#pragma unroll
-            for (int k = 0; k < SUR_NV; k++) v[k] = V[k];
-            float* t = A.t_out + row * 3;
-            t[0] = (float)A.f_atm[s];
-            t[1] = (float)A.f_atm[n + s];
-            t[2] = (float)A.f_atm[2 * n + s];
+    if (s >= n) return;
+    const int cg = A.cell_sorted[s];
+    const Rep& rp = A.b.rep[A.b.rep_of_cell[cg]];
+    int cx, cy, cz;
+    cell_coords(rp.g, cg - rp.cell0, cx, cy, cz);
+    const int* st = A.cell_start + rp.cell0;
+    const SurConst kc = sur_consts(rp);
+    const float4* __restrict__ x4 = A.xl4;
+    const float4 xs = x4[s];
+    SurAcc acc;
+    sur_zero(acc);
+    // (A) candidate k of the concatenated 27 cells -> bit k (the molecule itself
+    // passes the test; its bit is cleared below)
+    int K = 0, kself = 0;
+    unsigned word = 0u;
+    for (int t = 0; t < 27; t++) {
+        int dx, dy, dz;
+        offset27(t, dx, dy, dz);
+        const long long nc = cell_at(rp.g, cx, cy, cz, dx, dy, dz);
+        const int q0 = st[nc], q1 = st[nc + 1];
+        if (t == 13) kself = K + (int)(s - q0);
+        s_kend[t * SUR_BLOCK + tid] = K + (q1 - q0);
+        s_qoff[t * SUR_BLOCK + tid] = q0 - K;
+        const float sx = (float)dx * rp.wf[0], sy = (float)dy * rp.wf[1], sz = (float)dz * rp.wf[2];
+        for (int q = q0; q < q1; q++) {
+            const float4 xq = x4[q];
+            const float ex = (xq.x - xs.x) + sx;
+            const float ey = (xq.y - xs.y) + sy;
+            const float ez = (xq.z - xs.z) + sz;
+            const float r2 = ex * ex + ey * ey + ez * ez;
+            word |= (r2 < kc.rc2 ? 1u : 0u) << (K & 31);
+            K++;
+            if ((K & 31) == 0) {
+                if (K <= 32 * SUR_MW) mask[((K >> 5) - 1) * SUR_BLOCK + tid] = word;
+                word = 0u;
+            }
         }
-        return;
     }
-    __syncthreads();  // model staged
-    stage_input(S.M, D, active, S.X + tid * SUR_XS);
-    __syncwarp();
-    sur_mlp_warp(S.M, S.X + warp * 32 * SUR_XS, S.H + warp * 32 * SUR_HS, S.Wo + warp * 32 * 4, lane);
-    if (active) {
-        const float w0 = S.Wo[tid * 4], w1 = S.Wo[tid * 4 + 1], w2 = S.Wo[tid * 4 + 2];
+    if ((K & 31) != 0 && K < 32 * SUR_MW) mask[(K >> 5) * SUR_BLOCK + tid] = word;
+    if (K <= 32 * SUR_MW) {
+        mask[(kself >> 5) * SUR_BLOCK + tid] &= ~(1u << (kself & 31));
+        // (B) one iteration per set bit (not per mask word), so every lane
+        // runs as many iterations as it has neighbours
+        const int nw = (K + 31) >> 5;
+        int t = 0, w = -1;
+        unsigned bits = 0u;
+        for (;;) {
+            while (bits == 0u && ++w < nw) bits = mask[w * SUR_BLOCK + tid];
+            if (bits == 0u) break;
+            const int k = (w << 5) + __ffs(bits) - 1;
+            bits &= bits - 1u;
+            while (k >= s_kend[t * SUR_BLOCK + tid]) t++;
+            int dx, dy, dz;
+            offset27(t, dx, dy, dz);
+            const float4 xq = x4[k + s_qoff[t * SUR_BLOCK + tid]];
+            const float ex = (xq.x - xs.x) + (float)dx * rp.wf[0];
+            const float ey = (xq.y - xs.y) + (float)dy * rp.wf[1];
+            const float ez = (xq.z - xs.z) + (float)dz * rp.wf[2];
+            sur_add(acc, kc, ex, ey, ez, ex * ex + ey * ey + ez * ez);
+        }
+    } else {
+        // crowded neighbourhood: test and accumulate in one pass
+        for (int t = 0; t < 27; t++) {
+            int dx, dy, dz;
+            offset27(t, dx, dy, dz);
+            const long long nc = cell_at(rp.g, cx, cy, cz, dx, dy, dz);
+            const int q0 = st[nc], q1 = st[nc + 1];
+            const float sx = (float)dx * rp.wf[0], sy = (float)dy * rp.wf[1], sz = (float)dz * rp.wf[2];
+            for (int q = q0; q < q1; q++) {
+                if (q == s) continue;
+                const float4 xq = x4[q];
+                const float ex = (xq.x - xs.x) + sx;
+                const float ey = (xq.y - xs.y) + sy;
+                const float ez = (xq.z - xs.z) + sz;
+                const float r2 = ex * ex + ey * ey + ez * ez;
+                if (r2 < kc.rc2) sur_add(acc, kc, ex, ey, ez, r2);
+            }
+        }
+    }
+    // the invariants, streamed out eight at a time: raw FP32 (mode 1) or
+    // normalised bfloat16 in 16-byte stores (mode 0)
+    const bool collect = A.mode == 1;
+    const long long row = A.row0 + s;
+    const float* mean = A.model ? A.model->mean : nullptr;
+    const float* scale = A.model ? A.model->scale : nullptr;
+    float buf[8];
+    auto put = [&](int k, float dk) {
+        buf[k & 7] = dk;
+        if ((k & 7) != 7) return;
+        const int k0 = k - 7;
+        if (collect) {
+            float4* d = reinterpret_cast<float4*>(A.d_out + row * SUR_ND + k0);
+            d[0] = make_float4(buf[0], buf[1], buf[2], buf[3]);
+            d[1] = make_float4(buf[4], buf[5], buf[6], buf[7]);
+        } else {
+            uint32_t h[4];
 #pragma unroll
-        for (int c = 0; c < 3; c++)
-            A.f_atm[c * n + s] = (double)(w0 * V[c] + w1 * V[3 + c] + w2 * V[6 + c]);
+            for (int j = 0; j < 4; j++) {
+                __nv_bfloat162 b2 = __floats2bfloat162_rn((buf[2 * j] - mean[k0 + 2 * j]) / scale[k0 + 2 * j],
+                                                          (buf[2 * j + 1] - mean[k0 + 2 * j + 1]) /
+                                                              scale[k0 + 2 * j + 1]);
+                h[j] = *reinterpret_cast<uint32_t*>(&b2);
+            }
+            reinterpret_cast<uint4*>(A.xb + s * SUR_ND)[k0 >> 3] = make_uint4(h[0], h[1], h[2], h[3]);
+        }
+    };
+#pragma unroll
+    for (int k = 0; k < 16; k++) put(k, acc.G[k]);
+    int e = 16;
+#pragma unroll
+    for (int m = 0; m < 4; m++)
+#pragma unroll
+        for (int b = m; b < 4; b++)
+            put(e++, acc.p[m][0] * acc.p[b][0] + acc.p[m][1] * acc.p[b][1] + acc.p[m][2] * acc.p[b][2]);
+#pragma unroll
+    for (int m = 0; m < 3; m++)
+#pragma unroll
+        for (int b = m; b < 3; b++)
+            put(e++, acc.T[m][0] * acc.T[b][0] + acc.T[m][1] * acc.T[b][1] + acc.T[m][2] * acc.T[b][2] +
+                         2.0f * (acc.T[m][3] * acc.T[b][3] + acc.T[m][4] * acc.T[b][4] +
+                                 acc.T[m][5] * acc.T[b][5]));
+    float* v = collect ? A.v_out + row * SUR_NV : A.vb + s * SUR_NV;
+#pragma unroll
+    for (int m = 0; m < 3; m++) {
+        v[3 * m] = acc.p[m][0];
+        v[3 * m + 1] = acc.p[m][1];
+        v[3 * m + 2] = acc.p[m][2];
+    }
+    if (collect) {
+        float* t = A.t_out + row * 3;
+        t[0] = (float)A.f_atm[s];
+        t[1] = (float)A.f_atm[n + s];
+        t[2] = (float)A.f_atm[2 * n + s];
     }
 }
 
-// the MLP on given rows D[n][32], V[n][9] -> w[n][3], f[n][3]
-__global__ void __launch_bounds__(SUR_BLOCK, 4) k_sur_mlp_rows(long long n, const float* __restrict__ Din,
+// The MLP on 128 rows per CTA (each warp its own 32 rows on the tensor cores):
+// input rows FP32 raw (normalised here) or bfloat16 normalised; outputs any
+// of w[n][3], F[n][3] (FP32 rows) and F as FP64 SoA [3][n].
+template <bool BF16_IN>
+__global__ void __launch_bounds__(SUR_BLOCK, 4) k_sur_mlp_tile(long long n, const float* __restrict__ Din,
+                                                            const __nv_bfloat16* __restrict__ Xin,
                                                             const float* __restrict__ Vin,
                                                             const SurPacked* model, float* w,
-                                                            float* f)
+                                                            float* f, double* f_soa)
 {
     __shared__ __align__(16) SurSmem S;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     stage_model(S.M, model);
     const long long s = (long long)blockIdx.x * SUR_BLOCK + tid;
     const bool active = s < n;
-    float D[SUR_ND];
-#pragma unroll
-    for (int k = 0; k < SUR_ND; k++) D[k] = active ? Din[s * SUR_ND + k] : 0.0f;
     __syncthreads();
-    stage_input(S.M, D, active, S.X + tid * SUR_XS);
+    __nv_bfloat16* xrow = S.X + tid * SUR_XS;
+    if (BF16_IN) {
+        const uint4* src = reinterpret_cast<const uint4*>(Xin + s * SUR_ND);
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            const uint4 u = active ? src[c] : make_uint4(0u, 0u, 0u, 0u);
+            uint32_t* d = reinterpret_cast<uint32_t*>(xrow + 8 * c);
+            d[0] = u.x;
+            d[1] = u.y;
+            d[2] = u.z;
+            d[3] = u.w;
+        }
+    } else {
+        float D[SUR_ND];
+#pragma unroll
+        for (int k = 0; k < SUR_ND; k++) D[k] = active ? Din[s * SUR_ND + k] : 0.0f;
+        stage_input(S.M, D, active, xrow);
+    }
     __syncwarp();
     sur_mlp_warp(S.M, S.X + warp * 32 * SUR_XS, S.H + warp * 32 * SUR_HS, S.Wo + warp * 32 * 4, lane);
     if (active) {
         const float w0 = S.Wo[tid * 4], w1 = S.Wo[tid * 4 + 1], w2 = S.Wo[tid * 4 + 2];
-        w[s * 3] = w0;
-        w[s * 3 + 1] = w1;
-        w[s * 3 + 2] = w2;
+        if (w) {
+            w[s * 3] = w0;
+            w[s * 3 + 1] = w1;
+            w[s * 3 + 2] = w2;
+        }
         const float* v = Vin + s * SUR_NV;
 #pragma unroll
-        for (int c = 0; c < 3; c++) f[s * 3 + c] = w0 * v[c] + w1 * v[3 + c] + w2 * v[6 + c];
+        for (int c = 0; c < 3; c++) {
+            const float fc = w0 * v[c] + w1 * v[3 + c] + w2 * v[6 + c];
+            if (f) f[s * 3 + c] = fc;
+            if (f_soa) f_soa[c * n + s] = (double)fc;
+        }
     }
 }
 
@@ -711,7 +855,11 @@ unsigned blocks_of(long long n, int b) { return (unsigned)((n + b - 1) / b); }
 cudaError_t launch_sur_forces(const SurForceArgs& a, cudaStream_t st)
 {
     if (a.n <= 0) return cudaSuccess;
-    k_sur_forces<<<blocks_of(a.n, SUR_BLOCK), SUR_BLOCK, 0, st>>>(a);
+    k_sur_xyz4<<<blocks_of(a.n, 256), 256, 0, st>>>(a.n, a.xl32, a.xl4);
+    k_sur_desc<<<blocks_of(a.n, SUR_BLOCK), SUR_BLOCK, 0, st>>>(a);
+    if (a.mode == 0)
+        k_sur_mlp_tile<true><<<blocks_of(a.n, SUR_BLOCK), SUR_BLOCK, 0, st>>>(
+            a.n, nullptr, a.xb, a.vb, a.model, nullptr, nullptr, a.f_atm);
     return cudaGetLastError();
 }
 
@@ -719,7 +867,8 @@ cudaError_t launch_sur_mlp_rows(long long n, const float* D, const float* V, con
                                 float* w, float* f, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
-    k_sur_mlp_rows<<<blocks_of(n, SUR_BLOCK), SUR_BLOCK, 0, st>>>(n, D, V, model, w, f);
+    k_sur_mlp_tile<false><<<blocks_of(n, SUR_BLOCK), SUR_BLOCK, 0, st>>>(n, D, nullptr, V, model, w,
+                                                                        f, nullptr);
     return cudaGetLastError();
 }
 

@@ -61,6 +61,11 @@ struct SurForceArgs {
     const int* cell_sorted;   // [n]
     const SurPacked* model;
     double* f_atm;            // [3n] sorted order: surrogate force (mode 0)
+    // scratch owned by the caller: packed coordinates [n] (both modes),
+    // normalised bfloat16 descriptor rows [n][32] and vectors [n][9] (mode 0)
+    float4* xl4;
+    __nv_bfloat16* xb;
+    float* vb;
     // mode 1 (collect): raw descriptors, vectors and the current f_atm as the
     // training target, rows [row0, row0 + n) of the data set (sorted order)
     float* d_out;             // [.][32]
@@ -106,7 +111,9 @@ struct SurAdamArgs {
     float lr, beta1, beta2, eps, c1, c2;  // c1 = 1 - beta1^t, c2 = 1 - beta2^t
 };
 
+// descriptors (and, mode 0, the MLP and the force): three launches
 cudaError_t launch_sur_forces(const SurForceArgs& a, cudaStream_t st);
+constexpr int SUR_LAUNCHES = 3;
 // MLP on given descriptor rows (no neighbour search): w[n][3], f[n][3]
 cudaError_t launch_sur_mlp_rows(long long n, const float* D, const float* V,
                                 const SurPacked* model, float* w, float* f, cudaStream_t st);
