@@ -25,8 +25,13 @@ struct SurAcc {
     float T[3][6];  // traceless quadrupole moments xx yy zz xy xz yz
 };
 
+// Every channel has eta d^2 = 1/2, so with u = (r - mu_0) / d the channel-j
+// Gaussian is exp(-(u - j)^2 / 2) = 2^(-((u - j) s)^2), s = sqrt(log2(e) / 2):
+// one subtraction of an immediate, one square and one base-2 exponential.
+constexpr float SUR_SQH = 0.8493218002880191f;  // sqrt(log2(e) / 2)
+
 struct SurConst {
-    float rc2, dg, dv, eta_g, eta_v, pi_rc;
+    float rc2, sg, sv, pi_rc;  // sg = s / d_g, sv = s / d_v
 };
 
 __device__ __forceinline__ SurConst sur_consts(const Rep& rp)
@@ -34,12 +39,19 @@ __device__ __forceinline__ SurConst sur_consts(const Rep& rp)
     SurConst k;
     const float rc = rp.rcf;
     k.rc2 = rp.rc2f;
-    k.dg = (rc - SUR_R0) / 15.0f;
-    k.dv = (rc - SUR_R0) / 4.0f;
-    k.eta_g = 1.0f / (2.0f * k.dg * k.dg);
-    k.eta_v = 1.0f / (2.0f * k.dv * k.dv);
+    k.sg = SUR_SQH / ((rc - SUR_R0) / 15.0f);
+    k.sv = SUR_SQH / ((rc - SUR_R0) / 4.0f);
     k.pi_rc = SUR_PI / rc;
     return k;
+}
+
+// 2^x (hardware approximation; x <= 0 here, results below the FP32 normal
+// range flush to zero)
+__device__ __forceinline__ float sur_exp2(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 
 __device__ __forceinline__ void sur_zero(SurAcc& a)
@@ -63,19 +75,20 @@ __device__ __forceinline__ void sur_add(SurAcc& a, const SurConst& k, float ex, 
     const float ux = ex * ir, uy = ey * ir, uz = ez * ir;
     const float fc = 0.5f * (__cosf(k.pi_rc * r) + 1.0f);
     const float rr = r - SUR_R0;
-    // r - mu_j as one multiply-add with an immediate (no per-channel constants held)
+    const float vg = rr * k.sg;  // (r - mu_0) s / d_g
 #pragma unroll
     for (int j = 0; j < 16; j++) {
-        const float tt = fmaf(-(float)j, k.dg, rr);
-        a.G[j] += __expf(-k.eta_g * tt * tt) * fc;
+        const float tt = vg - (float)j * SUR_SQH;
+        a.G[j] += sur_exp2(-(tt * tt)) * fc;
     }
+    const float vv = rr * k.sv - 0.5f * SUR_SQH;  // (r - nu_0) s / d_v
     const float third = 1.0f / 3.0f;
     const float qxx = ux * ux - third, qyy = uy * uy - third, qzz = uz * uz - third;
     const float qxy = ux * uy, qxz = ux * uz, qyz = uy * uz;
 #pragma unroll
     for (int m = 0; m < 4; m++) {
-        const float tt = fmaf(-((float)m + 0.5f), k.dv, rr);
-        const float ph = __expf(-k.eta_v * tt * tt) * fc;
+        const float tt = vv - (float)m * SUR_SQH;
+        const float ph = sur_exp2(-(tt * tt)) * fc;
         a.p[m][0] += ph * ux;
         a.p[m][1] += ph * uy;
         a.p[m][2] += ph * uz;
