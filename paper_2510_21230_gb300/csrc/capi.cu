@@ -415,15 +415,20 @@ atm_status atm3::ctx_enqueue_forces(atm_ctx* c, int trav, int trunc, int prec, i
     if (prec != ATM_SURROGATE) launch_choice(c, trav, trunc, prec, j.persistent, j.nwarps);
     j.st = c->st;
 
-    cudaEvent_t ev = ctx_prof_begin(c);
-    CU(enqueue_lj(j));
-    ctx_prof_end(c, PK_LJ, ev);
-    c->n_launch += 1;
+    cudaEvent_t ev;
+    if (prec != ATM_SURROGATE) {
+        // (the surrogate's descriptor pass computes LJ from the same neighbours)
+        ev = ctx_prof_begin(c);
+        CU(enqueue_lj(j));
+        ctx_prof_end(c, PK_LJ, ev);
+        c->n_launch += 1;
+    }
 
     ev = ctx_prof_begin(c);
     if (prec == ATM_SURROGATE) {
         atm_status s = sur_enqueue_atm(c);
         if (s != ATM_OK) return s;
+        c->n_launch -= 1;  // counted by the surrogate launcher
     } else {
         bool capacity = false;
         cudaError_t e = enqueue_atm(j, &c->smem_set[prec][trav][trunc], &capacity);
@@ -614,7 +619,7 @@ static atm_status run_graph_steps(atm_ctx* c, int nsteps, int trav, int trunc, i
     cudaEvent_t ev = ctx_prof_begin(c);
     for (int k = 0; k < nsteps; k++) CU(cudaGraphLaunch(c->graph, c->st));
     ctx_prof_end(c, PK_MD, ev);
-    c->n_launch += (long long)nsteps * (KERNELS_PER_STEP + (prec == ATM_SURROGATE ? SUR_LAUNCHES - 1 : 0));
+    c->n_launch += (long long)nsteps * (KERNELS_PER_STEP + (prec == ATM_SURROGATE ? SUR_LAUNCHES - 2 : 0));
     c->n_atm += nsteps;
     return ATM_OK;
 }

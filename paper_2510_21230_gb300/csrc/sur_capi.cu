@@ -211,9 +211,13 @@ atm_status atm3::sur_enqueue_atm(atm_ctx* c)
     atm_status s = sur_args(c, S, a);
     if (s != ATM_OK) return s;
     a.f_atm = c->f_atm;
+    // LJ from the descriptor kernel's neighbour pass
+    a.f_lj = c->f_lj;
+    a.mol_ew = c->mol_ew;
+    a.mol_cnt = c->mol_cnt;
     a.mode = 0;
     CU(launch_sur_forces(a, c->st));
-    c->n_launch += SUR_LAUNCHES - 1;  // the caller counts one
+    c->n_launch += SUR_LAUNCHES;
     return ATM_OK;
 }
 

@@ -275,10 +275,14 @@ __global__ void __launch_bounds__(256) k_sur_xyz4(long long n, const float* __re
 // recorded as one bit (cheap, so lanes in different cells diverge little);
 // (B) the thread walks its set bits and accumulates the descriptor terms, so
 // the expensive part keeps every lane busy.  More than 1024 candidates: one
-// direct pass.  Mode 0 writes the normalised bfloat16 input row and the
+// direct pass.  With LJ the same neighbours give the FP32 LJ pair force,
+// energy, virial and counts of the molecule (the decisions and arithmetic of
+// the FP32 LJ kernel, so no separate LJ pass is needed).  Mode 0 writes the
+// normalised bfloat16 input row and the
 // vectors for the MLP kernel; mode 1 appends the raw descriptors, vectors and
 // the current ATM force to the data set.  The masks are word-major (word w of
 // thread t at w * SUR_BLOCK + t), free of bank conflicts.
+template <bool LJ>
 __global__ void __launch_bounds__(SUR_BLOCK, 5) k_sur_desc(const SurForceArgs A)
 {
     __shared__ unsigned mask[SUR_MW * SUR_BLOCK];
@@ -302,6 +306,31 @@ __global__ void __launch_bounds__(SUR_BLOCK, 5) k_sur_desc(const SurForceArgs A)
     sur_zero(acc);
     // (A) candidate k of the concatenated 27 cells -> bit k (the molecule itself
     // passes the test; its bit is cleared below)
+    // displacement and squared distance rounded as written (no contraction):
+    // the cutoff decisions are those of the FP32 LJ kernel
+    auto dist2 = [&](const float4& xq, float sx, float sy, float sz, float& ex, float& ey,
+                     float& ez) -> float {
+        ex = __fadd_rn(__fsub_rn(xq.x, xs.x), sx);
+        ey = __fadd_rn(__fsub_rn(xq.y, xs.y), sy);
+        ez = __fadd_rn(__fsub_rn(xq.z, xs.z), sz);
+        return __fadd_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)), __fmul_rn(ez, ez));
+    };
+    // LJ of one neighbour (the FP32 LJ kernel's expressions)
+    float ljx = 0.f, ljy = 0.f, ljz = 0.f, lje = 0.f, ljw = 0.f;
+    unsigned lj_cand = 0u, lj_visits = 0u;
+    auto lj_add = [&](float ex, float ey, float ez, float a) {
+        const float ia = 1.0f / a;
+        const float s2 = rp.sig2f * ia;
+        const float s3 = s2 * s2 * s2;
+        const float s6 = s3 * s3;
+        const float fw = (rp.eps48f * s6 - rp.eps24f * s3) * ia;
+        ljx -= fw * ex;
+        ljy -= fw * ey;
+        ljz -= fw * ez;
+        lje += rp.eps4f * (s6 - s3) - rp.ushiftf;
+        ljw += fw * a;
+        lj_visits++;
+    };
     int K = 0, kself = 0;
     unsigned word = 0u;
     for (int t = 0; t < 27; t++) {
@@ -310,15 +339,16 @@ __global__ void __launch_bounds__(SUR_BLOCK, 5) k_sur_desc(const SurForceArgs A)
         const long long nc = cell_at(rp.g, cx, cy, cz, dx, dy, dz);
         const int q0 = st[nc], q1 = st[nc + 1];
         if (t == 13) kself = K + (int)(s - q0);
+        if (LJ) {
+            if (t > 13) lj_cand += (unsigned)(q1 - q0);
+            if (t == 13) lj_cand += (unsigned)(q1 - 1 - s);
+        }
         s_kend[t * SUR_BLOCK + tid] = K + (q1 - q0);
         s_qoff[t * SUR_BLOCK + tid] = q0 - K;
         const float sx = (float)dx * rp.wf[0], sy = (float)dy * rp.wf[1], sz = (float)dz * rp.wf[2];
         for (int q = q0; q < q1; q++) {
-            const float4 xq = x4[q];
-            const float ex = (xq.x - xs.x) + sx;
-            const float ey = (xq.y - xs.y) + sy;
-            const float ez = (xq.z - xs.z) + sz;
-            const float r2 = ex * ex + ey * ey + ez * ez;
+            float ex, ey, ez;
+            const float r2 = dist2(x4[q], sx, sy, sz, ex, ey, ez);
             word |= (r2 < kc.rc2 ? 1u : 0u) << (K & 31);
             K++;
             if ((K & 31) == 0) {
@@ -343,11 +373,11 @@ __global__ void __launch_bounds__(SUR_BLOCK, 5) k_sur_desc(const SurForceArgs A)
             while (k >= s_kend[t * SUR_BLOCK + tid]) t++;
             int dx, dy, dz;
             offset27(t, dx, dy, dz);
-            const float4 xq = x4[k + s_qoff[t * SUR_BLOCK + tid]];
-            const float ex = (xq.x - xs.x) + (float)dx * rp.wf[0];
-            const float ey = (xq.y - xs.y) + (float)dy * rp.wf[1];
-            const float ez = (xq.z - xs.z) + (float)dz * rp.wf[2];
-            sur_add(acc, kc, ex, ey, ez, ex * ex + ey * ey + ez * ez);
+            float ex, ey, ez;
+            const float r2 = dist2(x4[k + s_qoff[t * SUR_BLOCK + tid]], (float)dx * rp.wf[0],
+                                   (float)dy * rp.wf[1], (float)dz * rp.wf[2], ex, ey, ez);
+            sur_add(acc, kc, ex, ey, ez, r2);
+            if (LJ) lj_add(ex, ey, ez, r2);
         }
     } else {
         // crowded neighbourhood: test and accumulate in one pass
@@ -359,14 +389,23 @@ __global__ void __launch_bounds__(SUR_BLOCK, 5) k_sur_desc(const SurForceArgs A)
             const float sx = (float)dx * rp.wf[0], sy = (float)dy * rp.wf[1], sz = (float)dz * rp.wf[2];
             for (int q = q0; q < q1; q++) {
                 if (q == s) continue;
-                const float4 xq = x4[q];
-                const float ex = (xq.x - xs.x) + sx;
-                const float ey = (xq.y - xs.y) + sy;
-                const float ez = (xq.z - xs.z) + sz;
-                const float r2 = ex * ex + ey * ey + ez * ez;
-                if (r2 < kc.rc2) sur_add(acc, kc, ex, ey, ez, r2);
+                float ex, ey, ez;
+                const float r2 = dist2(x4[q], sx, sy, sz, ex, ey, ez);
+                if (r2 < kc.rc2) {
+                    sur_add(acc, kc, ex, ey, ez, r2);
+                    if (LJ) lj_add(ex, ey, ez, r2);
+                }
             }
         }
+    }
+    if (LJ) {
+        A.f_lj[s] = (double)ljx;
+        A.f_lj[n + s] = (double)ljy;
+        A.f_lj[2 * n + s] = (double)ljz;
+        A.mol_ew[2 * s] = 0.5 * (double)lje;
+        A.mol_ew[2 * s + 1] = 0.5 * (double)ljw;
+        A.mol_cnt[2 * s] = lj_cand;
+        A.mol_cnt[2 * s + 1] = lj_visits;
     }
     // the invariants, streamed out eight at a time: raw FP32 (mode 1) or
     // normalised bfloat16 in 16-byte stores (mode 0)
@@ -869,7 +908,10 @@ cudaError_t launch_sur_forces(const SurForceArgs& a, cudaStream_t st)
 {
     if (a.n <= 0) return cudaSuccess;
     k_sur_xyz4<<<blocks_of(a.n, 256), 256, 0, st>>>(a.n, a.xl32, a.xl4);
-    k_sur_desc<<<blocks_of(a.n, SUR_BLOCK), SUR_BLOCK, 0, st>>>(a);
+    if (a.f_lj)
+        k_sur_desc<true><<<blocks_of(a.n, SUR_BLOCK), SUR_BLOCK, 0, st>>>(a);
+    else
+        k_sur_desc<false><<<blocks_of(a.n, SUR_BLOCK), SUR_BLOCK, 0, st>>>(a);
     if (a.mode == 0)
         k_sur_mlp_tile<true><<<blocks_of(a.n, SUR_BLOCK), SUR_BLOCK, 0, st>>>(
             a.n, nullptr, a.xb, a.vb, a.model, nullptr, nullptr, a.f_atm);

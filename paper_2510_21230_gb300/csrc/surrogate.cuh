@@ -66,6 +66,11 @@ struct SurForceArgs {
     float4* xl4;
     __nv_bfloat16* xb;
     float* vb;
+    // LJ pair forces from the same neighbour pass (FP32, owner computes, the
+    // arithmetic of the FP32 LJ kernel); nullptr: not computed
+    double* f_lj;             // [3n] sorted order
+    double* mol_ew;           // [2n] half pair energies and virials per molecule
+    unsigned* mol_cnt;        // [2n] half-shell candidates, visits
     // mode 1 (collect): raw descriptors, vectors and the current f_atm as the
     // training target, rows [row0, row0 + n) of the data set (sorted order)
     float* d_out;             // [.][32]

@@ -304,3 +304,25 @@ def test_surrogate_graph_steps_equal_plain(atm3, liquid, liquid_desc):
             s.step(6, "3c08", "pair", "surrogate")
             out.append(s.get_state())
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_surrogate_lj_equals_fp32_lj_kernel(atm3, liquid, liquid_desc):
+    # the surrogate's neighbour pass computes LJ with the FP32 LJ kernel's
+    # decisions and arithmetic: same counts, same forces up to FMA contraction
+    Do, _ = liquid_desc
+    P, mean, scale = _model_for(Do)
+    with atm3.AtmSystem(liquid["box"], 1000, rc=RC, nu=NU) as s:
+        s.set_state(liquid["x"])
+        s.surrogate_set_model(P, mean, scale)
+        s.build_cells()
+        s.compute_forces("3c08", "pair", "fp32c")
+        r1 = s.results()[0]
+        f1 = s.get_forces("lj")
+        s.compute_forces("3c08", "pair", "surrogate")
+        r2 = s.results()[0]
+        f2 = s.get_forces("lj")
+    assert r2["n_int2"] == r1["n_int2"] and r2["n_cand2"] == r1["n_cand2"]
+    assert abs(r2["e2"] - r1["e2"]) <= 1e-6 * abs(r1["e2"])
+    assert abs(r2["w2"] - r1["w2"]) <= 1e-6 * abs(r1["w2"])
+    sc = np.sqrt(np.mean(f1 ** 2))
+    assert np.max(np.abs(f2 - f1)) <= 1e-6 * sc
