@@ -9,6 +9,7 @@ namespace atm3 {
 enum : int {
     ST_CAPACITY = 1,   // a unit stages more molecules than its shared memory holds
     ST_NONFINITE = 2,  // a non-finite position or velocity was seen
+    ST_TIMEOUT = 4,    // a bounded device-side wait gave up
 };
 
 // Linked-cell grid (section 3): n_d cells of edge w_d = L_d / n_d per axis.

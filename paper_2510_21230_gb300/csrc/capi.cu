@@ -118,6 +118,8 @@ static atm_status check_status(atm_ctx* c)
     if (s & ST_NONFINITE) return ctx_fail(c, ATM_E_NONFINITE, "non-finite position or velocity");
     if (s & ST_CAPACITY)
         return ctx_fail(c, ATM_E_CAPACITY, "a traversal unit holds more molecules than staged");
+    if (s & ST_TIMEOUT)
+        return ctx_fail(c, ATM_E_TIMEOUT, "a device-side wait for the tensor cores gave up");
     return ctx_fail(c, ATM_E_CUDA, "device status %d", s);
 }
 

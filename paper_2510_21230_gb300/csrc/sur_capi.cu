@@ -192,6 +192,8 @@ atm_status sur_args(atm_ctx* c, SurState* S, SurForceArgs& a)
     a.xl4 = S->xl4;
     a.xb = S->xb;
     a.vb = S->vb;
+    a.status = c->d_status;
+    a.sms = c->sms;
     return ATM_OK;
 }
 
@@ -418,7 +420,7 @@ extern "C" atm_status atm_surrogate_mlp(atm_ctx* c, int64_t rows, const float* d
     float* dF = reinterpret_cast<float*>(b + bd + bv + bw);
     CU(cudaMemcpyAsync(dD, desc, n * SUR_ND * 4, cudaMemcpyHostToDevice, c->st));
     CU(cudaMemcpyAsync(dV, vec, n * SUR_NV * 4, cudaMemcpyHostToDevice, c->st));
-    CU(launch_sur_mlp_rows(rows, dD, dV, S->packed, dW, dF, c->st));
+    CU(launch_sur_mlp_rows(rows, dD, dV, S->packed, dW, dF, c->d_status, c->sms, c->st));
     c->n_launch += 1;
     CU(cudaMemcpyAsync(w, dW, n * 3 * 4, cudaMemcpyDeviceToHost, c->st));
     CU(cudaMemcpyAsync(force, dF, n * 3 * 4, cudaMemcpyDeviceToHost, c->st));

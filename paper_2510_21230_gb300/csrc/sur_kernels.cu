@@ -10,11 +10,9 @@ namespace atm3 {
 
 namespace {
 
-constexpr int SUR_BLOCK = 128;  // molecules per CTA of the inference kernels (4 warps x 32 rows)
+constexpr int SUR_BLOCK = 128;  // molecules per CTA of the descriptor kernel
 constexpr float SUR_R0 = 0.8f;
 constexpr float SUR_PI = 3.14159265358979f;
-
-__device__ __forceinline__ float silu_fast(float z) { return z / (1.0f + __expf(-z)); }
 
 // ------------------------------------------------------------ descriptors
 
@@ -103,163 +101,7 @@ __device__ __forceinline__ void sur_add(SurAcc& a, const SurConst& k, float ex, 
     }
 }
 
-// invariants D[32] and vectors V[9] (p_0, p_1, p_2) of the accumulated moments
-__device__ __forceinline__ void sur_finish(const SurAcc& a, float D[SUR_ND], float V[SUR_NV])
-{
-#pragma unroll
-    for (int k = 0; k < 16; k++) D[k] = a.G[k];
-    int e = 16;
-#pragma unroll
-    for (int m = 0; m < 4; m++)
-#pragma unroll
-        for (int b = m; b < 4; b++)
-            D[e++] = a.p[m][0] * a.p[b][0] + a.p[m][1] * a.p[b][1] + a.p[m][2] * a.p[b][2];
-#pragma unroll
-    for (int m = 0; m < 3; m++)
-#pragma unroll
-        for (int b = m; b < 3; b++)
-            D[e++] = a.T[m][0] * a.T[b][0] + a.T[m][1] * a.T[b][1] + a.T[m][2] * a.T[b][2] +
-                     2.0f * (a.T[m][3] * a.T[b][3] + a.T[m][4] * a.T[b][4] + a.T[m][5] * a.T[b][5]);
-#pragma unroll
-    for (int m = 0; m < 3; m++) {
-        V[3 * m] = a.p[m][0];
-        V[3 * m + 1] = a.p[m][1];
-        V[3 * m + 2] = a.p[m][2];
-    }
-}
-
-// ---------------------------------------------------------- tensor-core MLP
-
-__device__ __forceinline__ uint32_t lds32(const __nv_bfloat16* p)
-{
-    return *reinterpret_cast<const uint32_t*>(p);
-}
-
-__device__ __forceinline__ void sts_bf2(__nv_bfloat16* p, float lo, float hi)
-{
-    *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(lo, hi);
-}
-
-// D += A B on one 16x8x16 tile: bfloat16 operands, FP32 accumulators
-__device__ __forceinline__ void mma_bf16_16816(float c[4], const uint32_t a[4], uint32_t b0,
-                                               uint32_t b1)
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-        "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// acc[2][NT][4] = A[32 rows of this warp][K] * Bt[NT*8][K]^T (A row stride AS,
-// Bt row stride BS, both bf16 in shared memory)
-template <int K, int NT, int AS, int BS>
-__device__ __forceinline__ void warp_gemm(float acc[2][NT][4], const __nv_bfloat16* A,
-                                          const __nv_bfloat16* Bt, int lane)
-{
-    const int g = lane >> 2, t = lane & 3;
-#pragma unroll
-    for (int mt = 0; mt < 2; mt++)
-#pragma unroll
-        for (int nt = 0; nt < NT; nt++) acc[mt][nt][0] = acc[mt][nt][1] = acc[mt][nt][2] = acc[mt][nt][3] = 0.0f;
-#pragma unroll
-    for (int kk = 0; kk < K / 16; kk++) {
-        uint32_t a[2][4];
-#pragma unroll
-        for (int mt = 0; mt < 2; mt++) {
-            const __nv_bfloat16* pa = A + (16 * mt + g) * AS + 16 * kk + 2 * t;
-            a[mt][0] = lds32(pa);
-            a[mt][1] = lds32(pa + 8 * AS);
-            a[mt][2] = lds32(pa + 8);
-            a[mt][3] = lds32(pa + 8 * AS + 8);
-        }
-#pragma unroll
-        for (int nt = 0; nt < NT; nt++) {
-            const __nv_bfloat16* pb = Bt + (8 * nt + g) * BS + 16 * kk + 2 * t;
-            const uint32_t b0 = lds32(pb), b1 = lds32(pb + 8);
-            mma_bf16_16816(acc[0][nt], a[0], b0, b1);
-            mma_bf16_16816(acc[1][nt], a[1], b0, b1);
-        }
-    }
-}
-
-// bias + SiLU of a 32x64 accumulator block, rounded to bfloat16 into H
-__device__ __forceinline__ void warp_silu_store(const float acc[2][8][4], const float* bias,
-                                                __nv_bfloat16* H, int lane)
-{
-    const int g = lane >> 2, t = lane & 3;
-#pragma unroll
-    for (int mt = 0; mt < 2; mt++)
-#pragma unroll
-        for (int nt = 0; nt < 8; nt++) {
-            const int col = 8 * nt + 2 * t;
-            const float b0 = bias[col], b1 = bias[col + 1];
-            __nv_bfloat16* h = H + (16 * mt + g) * SUR_HS + col;
-            sts_bf2(h, silu_fast(acc[mt][nt][0] + b0), silu_fast(acc[mt][nt][1] + b1));
-            sts_bf2(h + 8 * SUR_HS, silu_fast(acc[mt][nt][2] + b0), silu_fast(acc[mt][nt][3] + b1));
-        }
-}
-
-// The MLP on the 32 rows of one warp: X (bf16, stride SUR_XS) -> w (FP32,
-// Wo[row][4]).  H is the warp's 32-row hidden buffer (stride SUR_HS).  Only
-// the warp's own rows are touched, so warp barriers suffice.
-__device__ __forceinline__ void sur_mlp_warp(const SurPacked& M, const __nv_bfloat16* X,
-                                             __nv_bfloat16* H, float* Wo, int lane)
-{
-    float acc[2][8][4];
-    warp_gemm<SUR_ND, 8, SUR_XS, SUR_XS>(acc, X, M.w1t, lane);
-    __syncwarp();  // the input rows are read before the hidden rows (which may overlay them) are written
-    warp_silu_store(acc, M.b1, H, lane);
-    __syncwarp();
-    warp_gemm<SUR_NH, 8, SUR_HS, SUR_HS>(acc, H, M.w2t, lane);
-    __syncwarp();  // every lane has read layer 1 before it is overwritten
-    warp_silu_store(acc, M.b2, H, lane);
-    __syncwarp();
-    float o[2][1][4];
-    warp_gemm<SUR_NH, 1, SUR_HS, SUR_HS>(o, H, M.w3t, lane);
-    const int g = lane >> 2, t = lane & 3;
-#pragma unroll
-    for (int mt = 0; mt < 2; mt++) {
-        const int row = 16 * mt + g, col = 2 * t;
-        if (col < SUR_NO) {
-            Wo[row * 4 + col] = o[mt][0][0] + M.b3[col];
-            Wo[(row + 8) * 4 + col] = o[mt][0][2] + M.b3[col];
-        }
-        if (col + 1 < SUR_NO) {
-            Wo[row * 4 + col + 1] = o[mt][0][1] + M.b3[col + 1];
-            Wo[(row + 8) * 4 + col + 1] = o[mt][0][3] + M.b3[col + 1];
-        }
-    }
-    __syncwarp();
-}
-
-struct SurSmem {
-    SurPacked M;
-    __nv_bfloat16 X[SUR_BLOCK * SUR_XS];
-    __nv_bfloat16 H[SUR_BLOCK * SUR_HS];
-    float Wo[SUR_BLOCK * 4];
-};
-
 constexpr int SUR_MW = 32;  // candidate-mask words per molecule: 1024 candidates of its 27 cells
-
-__device__ __forceinline__ void stage_model(SurPacked& M, const SurPacked* src)
-{
-    const int4* s = reinterpret_cast<const int4*>(src);
-    int4* d = reinterpret_cast<int4*>(&M);
-    for (int k = threadIdx.x; k < (int)(sizeof(SurPacked) / 16); k += blockDim.x) d[k] = s[k];
-}
-
-// normalised input row of this thread into X (bf16)
-__device__ __forceinline__ void stage_input(const SurPacked& M, const float D[SUR_ND], bool active,
-                                            __nv_bfloat16* xrow)
-{
-#pragma unroll
-    for (int k = 0; k < SUR_ND; k += 2) {
-        const float a = active ? (D[k] - M.mean[k]) / M.scale[k] : 0.0f;
-        const float b = active ? (D[k + 1] - M.mean[k + 1]) / M.scale[k + 1] : 0.0f;
-        sts_bf2(xrow + k, a, b);
-    }
-}
 
 // ---------------------------------------------------------------- kernels
 
@@ -461,59 +303,6 @@ __global__ void __launch_bounds__(SUR_BLOCK, 5) k_sur_desc(const SurForceArgs A)
         t[0] = (float)A.f_atm[s];
         t[1] = (float)A.f_atm[n + s];
         t[2] = (float)A.f_atm[2 * n + s];
-    }
-}
-
-// The MLP on 128 rows per CTA (each warp its own 32 rows on the tensor cores):
-// input rows FP32 raw (normalised here) or bfloat16 normalised; outputs any
-// of w[n][3], F[n][3] (FP32 rows) and F as FP64 SoA [3][n].
-template <bool BF16_IN>
-__global__ void __launch_bounds__(SUR_BLOCK, 4) k_sur_mlp_tile(long long n, const float* __restrict__ Din,
-                                                            const __nv_bfloat16* __restrict__ Xin,
-                                                            const float* __restrict__ Vin,
-                                                            const SurPacked* model, float* w,
-                                                            float* f, double* f_soa)
-{
-    __shared__ __align__(16) SurSmem S;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    stage_model(S.M, model);
-    const long long s = (long long)blockIdx.x * SUR_BLOCK + tid;
-    const bool active = s < n;
-    __syncthreads();
-    __nv_bfloat16* xrow = S.X + tid * SUR_XS;
-    if (BF16_IN) {
-        const uint4* src = reinterpret_cast<const uint4*>(Xin + s * SUR_ND);
-#pragma unroll
-        for (int c = 0; c < 4; c++) {
-            const uint4 u = active ? src[c] : make_uint4(0u, 0u, 0u, 0u);
-            uint32_t* d = reinterpret_cast<uint32_t*>(xrow + 8 * c);
-            d[0] = u.x;
-            d[1] = u.y;
-            d[2] = u.z;
-            d[3] = u.w;
-        }
-    } else {
-        float D[SUR_ND];
-#pragma unroll
-        for (int k = 0; k < SUR_ND; k++) D[k] = active ? Din[s * SUR_ND + k] : 0.0f;
-        stage_input(S.M, D, active, xrow);
-    }
-    __syncwarp();
-    sur_mlp_warp(S.M, S.X + warp * 32 * SUR_XS, S.H + warp * 32 * SUR_HS, S.Wo + warp * 32 * 4, lane);
-    if (active) {
-        const float w0 = S.Wo[tid * 4], w1 = S.Wo[tid * 4 + 1], w2 = S.Wo[tid * 4 + 2];
-        if (w) {
-            w[s * 3] = w0;
-            w[s * 3 + 1] = w1;
-            w[s * 3 + 2] = w2;
-        }
-        const float* v = Vin + s * SUR_NV;
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-            const float fc = w0 * v[c] + w1 * v[3 + c] + w2 * v[6 + c];
-            if (f) f[s * 3 + c] = fc;
-            if (f_soa) f_soa[c * n + s] = (double)fc;
-        }
     }
 }
 
@@ -912,19 +701,16 @@ cudaError_t launch_sur_forces(const SurForceArgs& a, cudaStream_t st)
         k_sur_desc<true><<<blocks_of(a.n, SUR_BLOCK), SUR_BLOCK, 0, st>>>(a);
     else
         k_sur_desc<false><<<blocks_of(a.n, SUR_BLOCK), SUR_BLOCK, 0, st>>>(a);
-    if (a.mode == 0)
-        k_sur_mlp_tile<true><<<blocks_of(a.n, SUR_BLOCK), SUR_BLOCK, 0, st>>>(
-            a.n, nullptr, a.xb, a.vb, a.model, nullptr, nullptr, a.f_atm);
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || a.mode != 0) return e;
+    return launch_sur_mlp_tc(a.n, nullptr, a.xb, a.vb, a.model, nullptr, nullptr, a.f_atm, a.status,
+                             a.sms, st);
 }
 
 cudaError_t launch_sur_mlp_rows(long long n, const float* D, const float* V, const SurPacked* model,
-                                float* w, float* f, cudaStream_t st)
+                                float* w, float* f, int* status, int sms, cudaStream_t st)
 {
-    if (n <= 0) return cudaSuccess;
-    k_sur_mlp_tile<false><<<blocks_of(n, SUR_BLOCK), SUR_BLOCK, 0, st>>>(n, D, nullptr, V, model, w,
-                                                                        f, nullptr);
-    return cudaGetLastError();
+    return launch_sur_mlp_tc(n, D, nullptr, V, model, w, f, nullptr, status, sms, st);
 }
 
 cudaError_t launch_sur_grad(const SurGradArgs& a, int nct, cudaStream_t st)

@@ -1,0 +1,327 @@
+// sur_tc.cu -- the surrogate MLP (32 -> 64 -> 64 -> 3, SiLU) on the
+// fifth-generation tensor cores: tcgen05.mma with bfloat16 operands staged in
+// shared memory and FP32 accumulators in tensor memory (TMEM).
+//
+// A persistent CTA of 128 threads takes 128-row tiles.  Thread t owns row t:
+// it writes the row's operand into shared memory, and after each layer reads
+// the row's accumulators back from TMEM lane t (tcgen05.ld 32x32b), applies
+// bias + SiLU and writes the next layer's operand row -- no shuffles, no
+// shared-memory transposes.  One elected thread issues the MMAs (M = 128,
+// N = 64 / 64 / 16, K = 16 per instruction) and commits them to an mbarrier
+// that all threads wait on with a bounded number of tries.
+//
+// Operands use the canonical K-major layout without swizzle: 8-row x 16-byte
+// core matrices, core matrix (row group g, 8-element chunk j) at byte
+// g * SBO + j * LBO with LBO = 128 and SBO = (K / 8) * 128.  TMEM columns:
+// layer 1 in [0, 64), layer 2 in [64, 128), layer 3 in [0, 16) (layer 1 is
+// consumed by then); 128 columns per CTA.
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "surrogate.cuh"
+
+namespace atm3 {
+
+namespace {
+
+constexpr int TC_M = 128;           // rows per tile = TMEM lanes
+constexpr uint32_t TC_COLS = 128;   // TMEM columns per CTA
+constexpr uint32_t TC_LBO = 128;    // bytes between core matrices along K
+constexpr long TC_WAIT_TRIES = 1L << 20;
+
+__host__ __device__ constexpr uint32_t cm_off(int row, int chunk, int kchunks)
+{
+    return (uint32_t)((row >> 3) * (kchunks * 128) + chunk * (int)TC_LBO + (row & 7) * 16);
+}
+
+struct TcSmem {
+    alignas(128) unsigned char w1[64 * 32 * 2];   // W1^T  N 64 x K 32
+    alignas(128) unsigned char w2[64 * 64 * 2];   // W2^T  N 64 x K 64
+    alignas(128) unsigned char w3[16 * 64 * 2];   // W3^T  N 16 (rows 3..15 zero) x K 64
+    alignas(128) unsigned char x[TC_M * 32 * 2];  // input tile   M 128 x K 32
+    alignas(128) unsigned char h[TC_M * 64 * 2];  // hidden tile  M 128 x K 64
+    float b1[64], b2[64], b3[16];
+    alignas(8) unsigned long long mbar;
+    uint32_t tmem_base;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// shared-memory matrix descriptor: start, LBO, SBO (bytes), fixed version 1,
+// no swizzle
+__device__ __forceinline__ uint64_t sdesc(const void* p, uint32_t sbo)
+{
+    const uint32_t a = smem_u32(p);
+    uint64_t d = (uint64_t)((a & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((TC_LBO >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// instruction descriptor of kind::f16: D FP32, A and B bfloat16, both K-major
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                          uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void umma_commit(unsigned long long* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t phase)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0u;
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 16 consecutive FP32 columns of this thread's TMEM lane (load and wait in
+// one statement, so no use can be scheduled before the wait)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+        "%12, %13, %14, %15}, [%16];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float silu(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
+
+__device__ __forceinline__ uint32_t pack_bf2(float lo, float hi)
+{
+    __nv_bfloat162 b = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&b);
+}
+
+// stage one 8-element chunk (16 bytes) of a K-major operand row
+__device__ __forceinline__ void put_chunk(unsigned char* base, int row, int chunk, int kchunks,
+                                          uint4 v)
+{
+    *reinterpret_cast<uint4*>(base + cm_off(row, chunk, kchunks)) = v;
+}
+
+template <bool BF16_IN>
+__global__ void __launch_bounds__(TC_M) k_sur_mlp_tc(long long n, const float* __restrict__ Din,
+                                                     const __nv_bfloat16* __restrict__ Xin,
+                                                     const float* __restrict__ Vin,
+                                                     const SurPacked* __restrict__ model, float* w,
+                                                     float* f, double* f_soa, int* status)
+{
+    __shared__ TcSmem S;
+    const int tid = threadIdx.x, warp = tid >> 5;
+
+    // weights in the canonical layouts (16-byte chunks of the packed rows)
+    for (int e = tid; e < 64 * 4; e += TC_M) {
+        const int r = e >> 2, j = e & 3;
+        put_chunk(S.w1, r, j, 4, *reinterpret_cast<const uint4*>(model->w1t + r * SUR_XS + 8 * j));
+    }
+    for (int e = tid; e < 64 * 8; e += TC_M) {
+        const int r = e >> 3, j = e & 7;
+        put_chunk(S.w2, r, j, 8, *reinterpret_cast<const uint4*>(model->w2t + r * SUR_HS + 8 * j));
+    }
+    for (int e = tid; e < 16 * 8; e += TC_M) {
+        const int r = e >> 3, j = e & 7;
+        const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+        put_chunk(S.w3, r, j, 8, r < 8 ? *reinterpret_cast<const uint4*>(model->w3t + r * SUR_HS + 8 * j) : z);
+    }
+    if (tid < 64) {
+        S.b1[tid] = model->b1[tid];
+        S.b2[tid] = model->b2[tid];
+    }
+    if (tid < 16) S.b3[tid] = tid < 8 ? model->b3[tid] : 0.0f;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&S.tmem_base)),
+                     "r"(TC_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = S.tmem_base;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;  // this warp's TMEM lane quarter
+    const uint32_t id64 = idesc_bf16(TC_M, 64), id16 = idesc_bf16(TC_M, 16);
+
+    uint32_t phase = 0u;
+    bool ok = true;
+    // every thread waits for the committed MMAs; all agree on the outcome
+    auto wait_mma = [&]() {
+        bool done = false;
+        for (long it = 0; it < TC_WAIT_TRIES && !done; it++) done = mbar_try_wait(&S.mbar, phase);
+        phase ^= 1u;
+        ok = __syncthreads_and(done) != 0;
+        tc_fence_after();
+    };
+    // bias + SiLU of 64 accumulator columns at TMEM column c0, written as row
+    // `tid` of the hidden operand
+    auto hidden = [&](uint32_t c0, const float* bias) {
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            float v[16];
+            tmem_ld16(tmem + lane_base + c0 + 16 * q, v);
+            uint32_t p[8];
+#pragma unroll
+            for (int i = 0; i < 8; i++)
+                p[i] = pack_bf2(silu(v[2 * i] + bias[16 * q + 2 * i]), silu(v[2 * i + 1] + bias[16 * q + 2 * i + 1]));
+            put_chunk(S.h, tid, 2 * q, 8, make_uint4(p[0], p[1], p[2], p[3]));
+            put_chunk(S.h, tid, 2 * q + 1, 8, make_uint4(p[4], p[5], p[6], p[7]));
+        }
+        tc_fence_before();
+        fence_async_smem();
+        __syncthreads();
+    };
+
+    const long long ntiles = (n + TC_M - 1) / TC_M;
+    for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const long long s = tile * TC_M + tid;
+        const bool active = s < n;
+        // input row
+        if (BF16_IN) {
+            const uint4* src = reinterpret_cast<const uint4*>(Xin + s * SUR_ND);
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+                put_chunk(S.x, tid, j, 4, active ? src[j] : make_uint4(0u, 0u, 0u, 0u));
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                uint32_t p[4];
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    const int k = 8 * j + 2 * i;
+                    const float a = active ? (Din[s * SUR_ND + k] - model->mean[k]) / model->scale[k] : 0.0f;
+                    const float b = active ? (Din[s * SUR_ND + k + 1] - model->mean[k + 1]) / model->scale[k + 1] : 0.0f;
+                    p[i] = pack_bf2(a, b);
+                }
+                put_chunk(S.x, tid, j, 4, make_uint4(p[0], p[1], p[2], p[3]));
+            }
+        }
+        float v9[SUR_NV];
+#pragma unroll
+        for (int k = 0; k < SUR_NV; k++) v9[k] = active ? Vin[s * SUR_NV + k] : 0.0f;
+        fence_async_smem();
+        __syncthreads();
+
+        // layer 1: TMEM [0, 64) = X W1
+        if (tid == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int kk = 0; kk < 2; kk++)
+                umma_bf16(tmem, sdesc(S.x + kk * 2 * TC_LBO, 4 * 128), sdesc(S.w1 + kk * 2 * TC_LBO, 4 * 128),
+                          id64, kk > 0);
+            umma_commit(&S.mbar);
+        }
+        wait_mma();
+        if (!ok) break;
+        hidden(0u, S.b1);
+
+        // layer 2: TMEM [64, 128) = H1 W2
+        if (tid == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int kk = 0; kk < 4; kk++)
+                umma_bf16(tmem + 64u, sdesc(S.h + kk * 2 * TC_LBO, 8 * 128), sdesc(S.w2 + kk * 2 * TC_LBO, 8 * 128),
+                          id64, kk > 0);
+            umma_commit(&S.mbar);
+        }
+        wait_mma();
+        if (!ok) break;
+        hidden(64u, S.b2);
+
+        // layer 3: TMEM [0, 16) = H2 W3 (layer 1's columns are consumed)
+        if (tid == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int kk = 0; kk < 4; kk++)
+                umma_bf16(tmem, sdesc(S.h + kk * 2 * TC_LBO, 8 * 128), sdesc(S.w3 + kk * 2 * TC_LBO, 8 * 128),
+                          id16, kk > 0);
+            umma_commit(&S.mbar);
+        }
+        wait_mma();
+        if (!ok) break;
+        float o[16];
+        tmem_ld16(tmem + lane_base, o);
+        if (active) {
+            const float w0 = o[0] + S.b3[0], w1 = o[1] + S.b3[1], w2 = o[2] + S.b3[2];
+            if (w) {
+                w[s * 3] = w0;
+                w[s * 3 + 1] = w1;
+                w[s * 3 + 2] = w2;
+            }
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                const float fc = w0 * v9[c] + w1 * v9[3 + c] + w2 * v9[6 + c];
+                if (f) f[s * 3 + c] = fc;
+                if (f_soa) f_soa[c * n + s] = (double)fc;
+            }
+        }
+        tc_fence_before();
+        __syncthreads();  // TMEM read and operands consumed before the next tile overwrites them
+        tc_fence_after();
+    }
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_COLS)
+                     : "memory");
+    if (!ok && tid == 0) atomicOr(status, ST_TIMEOUT);
+}
+
+}  // namespace
+
+cudaError_t launch_sur_mlp_tc(long long n, const float* D, const __nv_bfloat16* X, const float* V,
+                              const SurPacked* model, float* w, float* f, double* f_soa, int* status,
+                              int sms, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const long long ntiles = (n + TC_M - 1) / TC_M;
+    // four CTAs per SM hold all 512 TMEM columns
+    const long long grid = ntiles < 4ll * sms ? ntiles : 4ll * sms;
+    if (X)
+        k_sur_mlp_tc<true><<<(unsigned)grid, TC_M, 0, st>>>(n, nullptr, X, V, model, w, f, f_soa, status);
+    else
+        k_sur_mlp_tc<false><<<(unsigned)grid, TC_M, 0, st>>>(n, D, nullptr, V, model, w, f, f_soa, status);
+    return cudaGetLastError();
+}
+
+}  // namespace atm3

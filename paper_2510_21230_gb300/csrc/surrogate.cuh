@@ -13,9 +13,10 @@
 //                    tr(T_a T_b) (ab = 00 01 02 11 12 22)];
 //   MLP xn = (D - mean) / scale -> silu(xn W1 + b1) -> silu(. W2 + b2) -> w = . W3 + b3;
 //   F_i = sum_{m<3} w_m p_m.
-// Inference runs in bfloat16 on the tensor cores with FP32 accumulation
-// (inputs, weights and the two hidden activations rounded to bfloat16);
-// training runs in FP32 on FP32 master weights.
+// Inference runs in bfloat16 on the tcgen05 tensor cores with FP32
+// accumulation in tensor memory (inputs, weights and the two hidden
+// activations rounded to bfloat16); training runs in FP32 on FP32 master
+// weights.
 #pragma once
 #include <cuda_bf16.h>
 
@@ -35,15 +36,14 @@ constexpr int SUR_OFF_W3 = SUR_OFF_B2 + SUR_NH;
 constexpr int SUR_OFF_B3 = SUR_OFF_W3 + SUR_NH * SUR_NO;
 constexpr int SUR_NP = SUR_OFF_B3 + SUR_NO;  // 6467
 
-// row strides (bf16 elements) of the tensor-core operands in shared memory;
-// 40 and 72 put the eight rows a fragment load touches in distinct banks
-constexpr int SUR_XS = 40;   // K = 32 operands
-constexpr int SUR_HS = 72;   // K = 64 operands
+// row strides (bf16 elements) of the packed weight rows: 16-byte multiples,
+// so the tensor-core kernel stages them in 16-byte chunks
+constexpr int SUR_XS = 40;   // K = 32 rows
+constexpr int SUR_HS = 72;   // K = 64 rows
 
-// Inference weights as the tensor-core kernel stages them: B operands n-major
-// with k contiguous (row n holds the weights into output n), padded rows;
-// W3 padded to 8 outputs (rows 3..7 zero).  One flat block, copied to shared
-// memory with 16-byte loads.
+// Inference weights in bfloat16, n-major with k contiguous (row n holds the
+// weights into output n), padded rows; W3 padded to 8 outputs (rows 3..7
+// zero); FP32 biases and the descriptor normalisation.
 struct SurPacked {
     __nv_bfloat16 w1t[SUR_NH * SUR_XS];
     __nv_bfloat16 w2t[SUR_NH * SUR_HS];
@@ -71,6 +71,8 @@ struct SurForceArgs {
     double* f_lj;             // [3n] sorted order
     double* mol_ew;           // [2n] half pair energies and virials per molecule
     unsigned* mol_cnt;        // [2n] half-shell candidates, visits
+    int* status;              // device status word (ST_TIMEOUT)
+    int sms;                  // SMs of the device (persistent MLP grid)
     // mode 1 (collect): raw descriptors, vectors and the current f_atm as the
     // training target, rows [row0, row0 + n) of the data set (sorted order)
     float* d_out;             // [.][32]
@@ -121,7 +123,14 @@ cudaError_t launch_sur_forces(const SurForceArgs& a, cudaStream_t st);
 constexpr int SUR_LAUNCHES = 3;
 // MLP on given descriptor rows (no neighbour search): w[n][3], f[n][3]
 cudaError_t launch_sur_mlp_rows(long long n, const float* D, const float* V,
-                                const SurPacked* model, float* w, float* f, cudaStream_t st);
+                                const SurPacked* model, float* w, float* f, int* status, int sms,
+                                cudaStream_t st);
+// the MLP on the tcgen05 tensor cores (sur_tc.cu): input raw FP32 rows D or
+// normalised bfloat16 rows X, vectors V; outputs any of w[n][3], f[n][3] and
+// f_soa [3][n] (FP64); a wait that gives up sets ST_TIMEOUT in *status
+cudaError_t launch_sur_mlp_tc(long long n, const float* D, const __nv_bfloat16* X, const float* V,
+                              const SurPacked* model, float* w, float* f, double* f_soa, int* status,
+                              int sms, cudaStream_t st);
 cudaError_t launch_sur_grad(const SurGradArgs& a, int nct, cudaStream_t st);
 cudaError_t launch_sur_adam(const SurAdamArgs& a, cudaStream_t st);
 // pack FP32 master parameters + normalisation into the inference layout
