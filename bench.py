@@ -329,7 +329,7 @@ def run_ours(args):
         r1 = timed("3c08", "pair", "surrogate", 50, 3)
         ed, ee, ek = sysm.surrogate_error()
         surrogate = {
-            "precision": "surrogate (bf16 tensor-core MLP, FP32 descriptors)",
+            "precision": "surrogate (FP32 descriptors + LJ in one neighbour pass, bf16 tcgen05 MLP)",
             "value": n * 50 / (r1["ms"] * 1e-3), "ms_per_step": r1["ms"] / 50,
             "steps": "50 timed, exact FP32C 3c08 traversal every 50 (one in the timed run)",
             "ms_per_step_surrogate_only": r0["ms"] / 10,

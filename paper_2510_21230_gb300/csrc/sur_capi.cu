@@ -178,9 +178,13 @@ uint64_t splitmix64(uint64_t& x)
 atm_status sur_args(atm_ctx* c, SurState* S, SurForceArgs& a)
 {
     if (!S->xl4 && c->n > 0) {
+        // the MLP's tiles are read whole: pad to a multiple of the tile rows
+        const size_t rows = (size_t)((c->n + SUR_TILE_M - 1) / SUR_TILE_M) * SUR_TILE_M;
         CU(cudaMalloc(&S->xl4, (size_t)c->n * sizeof(float4)));
-        CU(cudaMalloc(&S->xb, (size_t)c->n * SUR_ND * sizeof(__nv_bfloat16)));
-        CU(cudaMalloc(&S->vb, (size_t)c->n * SUR_NV * sizeof(float)));
+        CU(cudaMalloc(&S->xb, rows * SUR_ND * sizeof(__nv_bfloat16)));
+        CU(cudaMalloc(&S->vb, rows * SUR_NV * sizeof(float)));
+        CU(cudaMemsetAsync(S->xb, 0, rows * SUR_ND * sizeof(__nv_bfloat16), c->st));
+        CU(cudaMemsetAsync(S->vb, 0, rows * SUR_NV * sizeof(float), c->st));
     }
     a = SurForceArgs{};
     a.b = c->b;

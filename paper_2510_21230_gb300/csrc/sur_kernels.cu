@@ -273,7 +273,9 @@ __global__ void __launch_bounds__(SUR_BLOCK, 5) k_sur_desc(const SurForceArgs A)
                                                               scale[k0 + 2 * j + 1]);
                 h[j] = *reinterpret_cast<uint32_t*>(&b2);
             }
-            reinterpret_cast<uint4*>(A.xb + s * SUR_ND)[k0 >> 3] = make_uint4(h[0], h[1], h[2], h[3]);
+            unsigned char* tile = reinterpret_cast<unsigned char*>(A.xb + (s / SUR_TILE_M) * (SUR_TILE_M * SUR_ND));
+            *reinterpret_cast<uint4*>(tile + sur_tile_off((int)(s % SUR_TILE_M), k0 >> 3, SUR_ND / 8)) =
+                make_uint4(h[0], h[1], h[2], h[3]);
         }
     };
 #pragma unroll

@@ -2,11 +2,15 @@
 // fifth-generation tensor cores: tcgen05.mma with bfloat16 operands staged in
 // shared memory and FP32 accumulators in tensor memory (TMEM).
 //
-// A persistent CTA of 128 threads takes 128-row tiles.  Thread t owns row t:
-// it writes the row's operand into shared memory, and after each layer reads
+// A persistent CTA of 128 threads takes 128-row tiles.  The input tile (stored
+// by the descriptor kernel already in the operand layout) and its vectors
+// arrive by bulk asynchronous copies (cp.async.bulk on the TMA engine) issued
+// one tile ahead, completing on an mbarrier.  Thread t owns row t: after each
+// layer it reads
 // the row's accumulators back from TMEM lane t (tcgen05.ld 32x32b), applies
 // bias + SiLU and writes the next layer's operand row -- no shuffles, no
-// shared-memory transposes.  One elected thread issues the MMAs (M = 128,
+// shared-memory transposes.  (Raw FP32 input rows are normalised and staged by
+// the threads instead.)  One elected thread issues the MMAs (M = 128,
 // N = 64 / 64 / 16, K = 16 per instruction) and commits them to an mbarrier
 // that all threads wait on with a bounded number of tries.
 //
@@ -29,9 +33,11 @@ constexpr uint32_t TC_COLS = 128;   // TMEM columns per CTA
 constexpr uint32_t TC_LBO = 128;    // bytes between core matrices along K
 constexpr long TC_WAIT_TRIES = 1L << 20;
 
+static_assert(TC_M == SUR_TILE_M && TC_LBO == 128, "the tile layout is the operand layout");
+
 __host__ __device__ constexpr uint32_t cm_off(int row, int chunk, int kchunks)
 {
-    return (uint32_t)((row >> 3) * (kchunks * 128) + chunk * (int)TC_LBO + (row & 7) * 16);
+    return sur_tile_off(row, chunk, kchunks);
 }
 
 struct TcSmem {
@@ -40,14 +46,31 @@ struct TcSmem {
     alignas(128) unsigned char w3[16 * 64 * 2];   // W3^T  N 16 (rows 3..15 zero) x K 64
     alignas(128) unsigned char x[TC_M * 32 * 2];  // input tile   M 128 x K 32
     alignas(128) unsigned char h[TC_M * 64 * 2];  // hidden tile  M 128 x K 64
+    alignas(16) float v[TC_M * SUR_NV];           // vectors of the tile's rows
     float b1[64], b2[64], b3[16];
-    alignas(8) unsigned long long mbar;
+    alignas(8) unsigned long long mbar;           // MMA completion
+    alignas(8) unsigned long long xbar;           // bulk-copy completion
     uint32_t tmem_base;
 };
+
+constexpr uint32_t TC_X_BYTES = TC_M * 32 * 2;
+constexpr uint32_t TC_V_BYTES = TC_M * SUR_NV * 4;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
 {
     return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// bulk asynchronous copy global -> shared (the TMA engine, no tensor map),
+// completing on an mbarrier that expects the bytes
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         unsigned long long* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
 }
 
 // shared-memory matrix descriptor: start, LBO, SBO (bytes), fixed version 1,
@@ -167,6 +190,7 @@ __global__ void __launch_bounds__(TC_M) k_sur_mlp_tc(long long n, const float* _
     if (tid < 16) S.b3[tid] = tid < 8 ? model->b3[tid] : 0.0f;
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.mbar)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.xbar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -184,15 +208,29 @@ __global__ void __launch_bounds__(TC_M) k_sur_mlp_tc(long long n, const float* _
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;  // this warp's TMEM lane quarter
     const uint32_t id64 = idesc_bf16(TC_M, 64), id16 = idesc_bf16(TC_M, 16);
 
-    uint32_t phase = 0u;
+    uint32_t phase = 0u, xphase = 0u;
     bool ok = true;
-    // every thread waits for the committed MMAs; all agree on the outcome
-    auto wait_mma = [&]() {
+    // every thread waits on a barrier phase; all agree on the outcome
+    auto wait_bar = [&](unsigned long long* bar, uint32_t& ph) {
         bool done = false;
-        for (long it = 0; it < TC_WAIT_TRIES && !done; it++) done = mbar_try_wait(&S.mbar, phase);
-        phase ^= 1u;
+        for (long it = 0; it < TC_WAIT_TRIES && !done; it++) done = mbar_try_wait(bar, ph);
+        ph ^= 1u;
         ok = __syncthreads_and(done) != 0;
+    };
+    auto wait_mma = [&]() {
+        wait_bar(&S.mbar, phase);
         tc_fence_after();
+    };
+    // the next tile's inputs: one bulk copy each for the X tile and its vectors
+    auto prefetch = [&](long long tile) {
+        if (tid == 0) {
+            fence_async_smem();  // earlier generic reads of S.v before the async writes
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&S.xbar)),
+                         "r"(TC_X_BYTES + TC_V_BYTES)
+                         : "memory");
+            bulk_g2s(S.x, Xin + tile * (TC_M * SUR_ND), TC_X_BYTES, &S.xbar);
+            bulk_g2s(S.v, Vin + tile * (TC_M * SUR_NV), TC_V_BYTES, &S.xbar);
+        }
     };
     // bias + SiLU of 64 accumulator columns at TMEM column c0, written as row
     // `tid` of the hidden operand
@@ -214,15 +252,16 @@ __global__ void __launch_bounds__(TC_M) k_sur_mlp_tc(long long n, const float* _
     };
 
     const long long ntiles = (n + TC_M - 1) / TC_M;
+    if (BF16_IN && blockIdx.x < ntiles) prefetch(blockIdx.x);
     for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         const long long s = tile * TC_M + tid;
         const bool active = s < n;
-        // input row
+        float v9[SUR_NV];
         if (BF16_IN) {
-            const uint4* src = reinterpret_cast<const uint4*>(Xin + s * SUR_ND);
+            wait_bar(&S.xbar, xphase);
+            if (!ok) break;
 #pragma unroll
-            for (int j = 0; j < 4; j++)
-                put_chunk(S.x, tid, j, 4, active ? src[j] : make_uint4(0u, 0u, 0u, 0u));
+            for (int k = 0; k < SUR_NV; k++) v9[k] = S.v[tid * SUR_NV + k];
         } else {
 #pragma unroll
             for (int j = 0; j < 4; j++) {
@@ -236,12 +275,11 @@ __global__ void __launch_bounds__(TC_M) k_sur_mlp_tc(long long n, const float* _
                 }
                 put_chunk(S.x, tid, j, 4, make_uint4(p[0], p[1], p[2], p[3]));
             }
-        }
-        float v9[SUR_NV];
 #pragma unroll
-        for (int k = 0; k < SUR_NV; k++) v9[k] = active ? Vin[s * SUR_NV + k] : 0.0f;
-        fence_async_smem();
-        __syncthreads();
+            for (int k = 0; k < SUR_NV; k++) v9[k] = active ? Vin[s * SUR_NV + k] : 0.0f;
+            fence_async_smem();
+            __syncthreads();
+        }
 
         // layer 1: TMEM [0, 64) = X W1
         if (tid == 0) {
@@ -254,6 +292,8 @@ __global__ void __launch_bounds__(TC_M) k_sur_mlp_tc(long long n, const float* _
         }
         wait_mma();
         if (!ok) break;
+        // the X tile and the vectors are consumed: fetch the next tile's meanwhile
+        if (BF16_IN && tile + gridDim.x < ntiles) prefetch(tile + gridDim.x);
         hidden(0u, S.b1);
 
         // layer 2: TMEM [64, 128) = H1 W2
@@ -299,6 +339,11 @@ __global__ void __launch_bounds__(TC_M) k_sur_mlp_tc(long long n, const float* _
         tc_fence_before();
         __syncthreads();  // TMEM read and operands consumed before the next tile overwrites them
         tc_fence_after();
+    }
+    // a bulk copy still in flight (a wait gave up) lands before shared memory is released
+    if (BF16_IN && !ok) {
+        bool done = false;
+        for (long it = 0; it < TC_WAIT_TRIES && !done; it++) done = mbar_try_wait(&S.xbar, xphase);
     }
     __syncthreads();
     if (warp == 0)

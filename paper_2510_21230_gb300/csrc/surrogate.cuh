@@ -53,6 +53,17 @@ struct SurPacked {
 };
 static_assert(sizeof(SurPacked) % 16 == 0, "SurPacked is copied in 16-byte pieces");
 
+// Tiles of 128 rows for the tensor-core MLP.  The normalised bfloat16 input
+// rows are stored tile by tile in the tensor cores' canonical K-major layout
+// without swizzle (8-row x 16-byte core matrices; core matrix (row group g,
+// 8-element chunk j) at byte g * (K / 8) * 128 + j * 128, row r of it at
+// + 16 r), so one bulk copy moves a tile into shared memory as is.
+constexpr int SUR_TILE_M = 128;
+__host__ __device__ constexpr unsigned sur_tile_off(int row, int chunk, int kchunks)
+{
+    return (unsigned)((row >> 3) * (kchunks * 128) + chunk * 128 + (row & 7) * 16);
+}
+
 struct SurForceArgs {
     Batch b;
     long long n;              // SoA stride = b.ntot
@@ -62,7 +73,8 @@ struct SurForceArgs {
     const SurPacked* model;
     double* f_atm;            // [3n] sorted order: surrogate force (mode 0)
     // scratch owned by the caller: packed coordinates [n] (both modes),
-    // normalised bfloat16 descriptor rows [n][32] and vectors [n][9] (mode 0)
+    // normalised bfloat16 descriptor tiles [ceil(n/128)][128 x 32] (tile
+    // layout above) and vectors [ceil(n/128) * 128][9] (mode 0)
     float4* xl4;
     __nv_bfloat16* xb;
     float* vb;
@@ -126,8 +138,9 @@ cudaError_t launch_sur_mlp_rows(long long n, const float* D, const float* V,
                                 const SurPacked* model, float* w, float* f, int* status, int sms,
                                 cudaStream_t st);
 // the MLP on the tcgen05 tensor cores (sur_tc.cu): input raw FP32 rows D or
-// normalised bfloat16 rows X, vectors V; outputs any of w[n][3], f[n][3] and
-// f_soa [3][n] (FP64); a wait that gives up sets ST_TIMEOUT in *status
+// normalised bfloat16 tiles X (tile layout, padded to whole tiles like V),
+// vectors V; outputs any of w[n][3], f[n][3] and f_soa [3][n] (FP64); a wait
+// that gives up sets ST_TIMEOUT in *status
 cudaError_t launch_sur_mlp_tc(long long n, const float* D, const __nv_bfloat16* X, const float* V,
                               const SurPacked* model, float* w, float* f, double* f_soa, int* status,
                               int sms, cudaStream_t st);
