@@ -54,8 +54,8 @@ F3 = {"3c01": 109.0, "3c18": 127.0, "3c08": 127.0}
 # liquid_n256k is the N = 32,000 capture (2197 units) scaled to 19683 units.
 KERNEL_SOURCES = ["atm3_internal.cuh", "atm_common.cuh", "atm_block.cuh", "atm_owner.cuh",
                   "atm_fp32.cu", "atm_fp64.cu"]
-TRAFFIC = {("3c08", "pair", "fp32c", "liquid_n256k"): (11.36e6, "c5b8b90152c4aeb0"),
-           ("3c08", "pair", "fp32c", "liquid_n32k"): (1.268e6, "c5b8b90152c4aeb0")}
+TRAFFIC = {("3c08", "pair", "fp32c", "liquid_n256k"): (11.36e6, "3312bd986874ed88"),
+           ("3c08", "pair", "fp32c", "liquid_n32k"): (1.267e6, "3312bd986874ed88")}
 
 
 def kernel_hash():
