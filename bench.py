@@ -58,6 +58,13 @@ TRAFFIC = {("3c08", "pair", "fp32c", "liquid_n256k"): (11.36e6, "3312bd986874ed8
            ("3c08", "pair", "fp32c", "liquid_n32k"): (1.267e6, "3312bd986874ed88")}
 
 
+# Issued FP32 flops (fadd + fmul + 2 ffma thread instructions of the ATM
+# kernel, from the same ncu capture) per interacting triplet, with the source
+# hash they belong to: the useful count above plus what candidates and
+# bookkeeping cost in floating point.
+ISSUED = {("3c08", "pair", "fp32c"): (160.6, "3312bd986874ed88")}
+
+
 def kernel_hash():
     import hashlib
     h = hashlib.sha256()
@@ -267,7 +274,12 @@ def run_ours(args):
                 "peak_source": "derived: %d SMs x %.2f flops/clk x %.0f MHz (%s pipe)"
                                % (SMS, per_clk, sm_max, "FP32" if args.prec == "fp32c" else "FP64"),
                 "flops_per_interacting_triplet": F3[args.trav],
-                "ms_per_launch": atm_ms}
+                "ms_per_launch": atm_ms,
+                "measured_fma_peak_tflops": atm3.measure_fma_peak(local, args.prec == "fp64")}
+    iss = ISSUED.get((args.trav, args.trunc, args.prec))
+    if iss is not None and iss[1] == kernel_hash():
+        roofline["issued_flops_per_interacting_triplet"] = iss[0]
+        roofline["issued_frac"] = roofline["frac"] * iss[0] / F3[args.trav]
 
     # paper-style 3-body MUPS: N / (ATM force time)
     mups_3body = n / (atm_ms * 1e-3)

@@ -342,6 +342,12 @@ atm_status atm_surrogate_options(atm_ctx* ctx, int exact_every);
 atm_status atm_surrogate_error(atm_ctx* ctx, double* rms_diff, double* rms_exact,
                                int64_t* checks, int reset);
 
+/* Measured fused multiply-add throughput of the device (TFLOP/s, one FMA = 2
+ * flops): a kernel of independent FMA chains in FP32 (fp64 = 0) or FP64,
+ * best of three timed launches.  Roofline context for the ALU-bound kernels;
+ * the paper has no counterpart. */
+atm_status atm_measure_fma_peak(int device, int fp64, double* tflops);
+
 /* Device-time profile of the library's own kernels (CUDA events recorded on
  * the context's stream around each group of launches while profiling is on).
  * ms_*: summed device time since profiling was (re)enabled; n_launches: kernels

@@ -33,7 +33,8 @@ EXPORTED = ["atm_abi_version", "atm_create", "atm_batch_create", "atm_batch_size
             "atm_surrogate_save", "atm_surrogate_load", "atm_surrogate_descriptors",
             "atm_surrogate_mlp", "atm_surrogate_loss_grad", "atm_surrogate_add_frame",
             "atm_surrogate_add_rows", "atm_surrogate_dataset", "atm_surrogate_clear",
-            "atm_surrogate_train", "atm_surrogate_options", "atm_surrogate_error"]
+            "atm_surrogate_train", "atm_surrogate_options", "atm_surrogate_error",
+            "atm_measure_fma_peak"]
 
 SUR_NDESC, SUR_NVEC, SUR_NPARAM = 32, 9, 6467
 
@@ -131,6 +132,7 @@ def load():
         "atm_surrogate_train": [P, i64, i64, ctypes.c_double, ctypes.c_uint64, P],
         "atm_surrogate_options": [P, i32],
         "atm_surrogate_error": [P, P, P, P, i32],
+        "atm_measure_fma_peak": [i32, i32, P],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -434,6 +436,16 @@ class AtmSystem:
         self._check(self._lib.atm_surrogate_error(self._ctx, ctypes.byref(d), ctypes.byref(e),
                                                 ctypes.byref(k), 1 if reset else 0))
         return d.value, e.value, k.value
+
+
+def measure_fma_peak(device=0, fp64=False):
+    """Measured FMA throughput of the device in TFLOP/s (FP32 or FP64)."""
+    L = load()
+    t = ctypes.c_double(0.0)
+    st = L.atm_measure_fma_peak(int(device), 1 if fp64 else 0, ctypes.byref(t))
+    if st != 0:
+        raise AtmError(st, "atm_measure_fma_peak failed")
+    return t.value
 
 
 def compute_forces_noalloc(box, x_dev, f_dev, trav="3c18", trunc="pair", prec="fp64", rc=2.5,

@@ -1,0 +1,69 @@
+// peak.cu -- measured arithmetic peaks of the device, for roofline context:
+// a kernel of independent fused multiply-add chains (FP32 or FP64), timed
+// with CUDA events.
+#include <cuda_runtime.h>
+
+#include "atm3.h"
+
+namespace {
+
+constexpr int PK_CHAINS = 8;     // independent accumulators per thread
+constexpr int PK_ITERS = 4096;   // multiply-adds per chain
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_chains(T a, T b, T* out)
+{
+    T acc[PK_CHAINS];
+#pragma unroll
+    for (int c = 0; c < PK_CHAINS; c++) acc[c] = (T)(threadIdx.x + c);
+    for (int i = 0; i < PK_ITERS; i++) {
+#pragma unroll
+        for (int c = 0; c < PK_CHAINS; c++) acc[c] = fma(acc[c], a, b);
+    }
+    T s = 0;
+#pragma unroll
+    for (int c = 0; c < PK_CHAINS; c++) s += acc[c];
+    // practically never true; keeps the chains alive
+    if (s == (T)-1.2345) out[blockIdx.x] = s;
+}
+
+template <typename T>
+atm_status run(int device, double* tflops)
+{
+    if (cudaSetDevice(device) != cudaSuccess) return ATM_E_CUDA;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+        return ATM_E_CUDA;
+    T* out = nullptr;
+    const int blocks = sms * 8;
+    if (cudaMalloc(&out, blocks * sizeof(T)) != cudaSuccess) return ATM_E_CUDA;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; rep++) {
+        cudaEventRecord(e0);
+        k_fma_chains<T><<<blocks, 256>>>((T)0.999999, (T)1e-7, out);
+        cudaEventRecord(e1);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0 && ms < best) best = ms;  // the first launch warms up
+    }
+    const cudaError_t err = cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    if (err != cudaSuccess) return ATM_E_CUDA;
+    const double flops = 2.0 * PK_CHAINS * (double)PK_ITERS * 256.0 * blocks;
+    *tflops = flops / (best * 1e-3) / 1e12;
+    return ATM_OK;
+}
+
+}  // namespace
+
+extern "C" atm_status atm_measure_fma_peak(int device, int fp64, double* tflops)
+{
+    if (!tflops || device < 0) return ATM_E_INVALID;
+    return fp64 ? run<double>(device, tflops) : run<float>(device, tflops);
+}
