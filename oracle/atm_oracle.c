@@ -437,6 +437,91 @@ static void unit_3c01(ev_t* ev, int64_t b)
     }
 }
 
+/* ---- 3cw, the wide owner traversal (not in the paper; it measures what the
+ *      paper's traversals miss under the product rule): for i in C_b, every
+ *      pair {j, k} of molecules of the 5^3 neighbourhood within R_w = 2 min(w)
+ *      of i, kept if the third side is shorter than R_w too and the
+ *      truncation test holds; forces on i only, u/3 and W/3 per visit.  It
+ *      finds every triplet with all sides shorter than R_w, which under the
+ *      product rule is every interacting triplet once the closest pair is at
+ *      least r_min apart with (r_min + sqrt(r_min^2 + 4 r_c^3 / r_min)) / 2
+ *      <= R_w (the longest side L of a triplet with shortest side r_min obeys
+ *      r_min (L - r_min) L < r_c^3).  Needs at least 5 cells per axis.
+ *      Candidates: the partner pairs of every owner. */
+static void unit_3cw(ev_t* ev, int64_t b, int64_t* plist, int* poff)
+{
+    const cells_t* c = ev->c;
+    double wmin = c->g.w[0];
+    for (int d = 1; d < 3; d++) wmin = c->g.w[d] < wmin ? c->g.w[d] : wmin;
+    const double rw2 = (2.0 * wmin) * (2.0 * wmin);
+    const float rw2f = (float)rw2;
+    int off[125][3];
+    int64_t cid[125];
+    int m = 0;
+    for (int dz = -2; dz <= 2; dz++)
+        for (int dy = -2; dy <= 2; dy++)
+            for (int dx = -2; dx <= 2; dx++) {
+                off[m][0] = dx;
+                off[m][1] = dy;
+                off[m][2] = dz;
+                cid[m] = nb_cell(&c->g, b, off[m]);
+                m++;
+            }
+    for (int64_t i = c->start[b]; i < c->start[b + 1]; i++) {
+        /* partners of i: within R_w */
+        int64_t np = 0;
+        for (int s = 0; s < 125; s++)
+            for (int64_t j = c->start[cid[s]]; j < c->start[cid[s] + 1]; j++) {
+                if (j == i) continue;
+                int in;
+                if (ev->prec == ORC_FP32) {
+                    in = dsq32(ev, i, ZERO3, j, off[s]) < rw2f;
+                } else {
+                    double d[3];
+                    in = dsq64(ev, i, ZERO3, j, off[s], d) < rw2;
+                }
+                if (in) {
+                    plist[np] = j;
+                    poff[np] = s;
+                    np++;
+                }
+            }
+        for (int64_t kk = 1; kk < np; kk++)
+            for (int64_t jj = 0; jj < kk; jj++) {
+                const int64_t j = plist[jj], k = plist[kk];
+                const int* oj = off[poff[jj]];
+                const int* ok = off[poff[kk]];
+                ev->ncand++;
+                double dij[3], dik[3], djk[3];
+                if (ev->prec == ORC_FP32) {
+                    float a32 = dsq32(ev, i, ZERO3, j, oj);
+                    float b32 = dsq32(ev, i, ZERO3, k, ok);
+                    float c32 = dsq32(ev, j, oj, k, ok);
+                    if (!(c32 < rw2f) || !keep32(ev, a32, b32, c32)) continue;
+                }
+                double a = dsq64(ev, i, ZERO3, j, oj, dij);
+                double bb = dsq64(ev, i, ZERO3, k, ok, dik);
+                double cc = dsq64(ev, j, oj, k, ok, djk);
+                if (ev->prec == ORC_FP64 && (!(cc < rw2) || !keep64(ev, a, bb, cc))) continue;
+                ev->nint++;
+                double du[3];
+                orc_atm_du_dsq(a, bb, cc, c->g.nu, du);
+                double u = orc_atm_u(a, bb, cc, c->g.nu);
+                double W = 0.0;
+                const int64_t n = c->n;
+                for (int d = 0; d < 3; d++) {
+                    double gij = 2.0 * du[0] * dij[d];
+                    double gik = 2.0 * du[1] * dik[d];
+                    double gjk = 2.0 * du[2] * djk[d];
+                    ev->f[d * n + i] += gij + gik;
+                    W += -(dij[d] * gij + dik[d] * gik + djk[d] * gjk);
+                }
+                ev->e += u / 3.0;
+                ev->w += W / 3.0;
+            }
+    }
+}
+
 /* ---- 3c18: base cell, its 13 forward neighbours and every pair of them
  *      (Algorithm 1 with forward neighbours only, section 4) ------------ */
 static void unit_3c18(ev_t* ev, int64_t b)
@@ -558,10 +643,14 @@ static int atm_cells_impl(const double* prm, int64_t n, const double* x, int tra
                           int prec, int64_t unit_lo, int64_t unit_hi, const int64_t* units,
                           int64_t nunits, double* f, double* ew, uint64_t* cnt)
 {
-    if (trav < 0 || trav > 2 || trunc < 0 || trunc > 1 || prec < 0 || prec > 1) return 1;
+    if (trav < 0 || trav > 3 || trunc < 0 || trunc > 1 || prec < 0 || prec > 1) return 1;
     cells_t c;
     int st = cells_make(prm, n, x, &c);
     if (st) return st;
+    if (trav == ORC_3CW && (c.g.nc[0] < 5 || c.g.nc[1] < 5 || c.g.nc[2] < 5)) {
+        cells_free(&c);
+        return 2;
+    }
     int64_t lo = unit_lo < 0 ? 0 : unit_lo;
     int64_t hi = (unit_hi < 0 || unit_hi > c.g.ncell) ? c.g.ncell : unit_hi;
     if (units) {
@@ -579,6 +668,8 @@ static int atm_cells_impl(const double* prm, int64_t n, const double* x, int tra
 #pragma omp parallel
     {
         double* fl = calloc((size_t)(3 * (n > 0 ? n : 1)), sizeof(double));
+        int64_t* plist = trav == ORC_3CW ? malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1)) : NULL;
+        int* poff = trav == ORC_3CW ? malloc(sizeof(int) * (size_t)(n > 0 ? n : 1)) : NULL;
         ev_t ev;
         ev_init(&ev, &c, trunc, prec, fl);
 #pragma omp for schedule(dynamic, 4)
@@ -586,8 +677,11 @@ static int atm_cells_impl(const double* prm, int64_t n, const double* x, int tra
             int64_t u = units ? units[q] : q;
             if (trav == ORC_3C01) unit_3c01(&ev, u);
             else if (trav == ORC_3C18) unit_3c18(&ev, u);
-            else unit_3c08(&ev, u);
+            else if (trav == ORC_3C08) unit_3c08(&ev, u);
+            else unit_3cw(&ev, u, plist, poff);
         }
+        free(plist);
+        free(poff);
 #pragma omp critical
         {
             for (int64_t q = 0; q < 3 * n; q++) fs[q] += fl[q];
@@ -725,12 +819,15 @@ static int bf_keep(double rc2, double rc6, int trunc, double a, double b, double
 int orc_atm_brute(const double* prm, int64_t n, const double* x, int trunc, int member,
                   double* f, double* ew, uint64_t* cnt)
 {
-    if (trunc < 0 || trunc > 1 || member < -1 || member > 2) return 1;
+    if (trunc < 0 || trunc > 1 || member < -1 || member > 3) return 1;
     cells_t c;
     int st = cells_make(prm, n, x, &c);
     if (st) return st;
     const grid_t* g = &c.g;
     double rc2 = g->rc * g->rc, rc6 = rc2 * rc2 * rc2;
+    double wmin = g->w[0];
+    for (int d = 1; d < 3; d++) wmin = g->w[d] < wmin ? g->w[d] : wmin;
+    const double rw2 = (2.0 * wmin) * (2.0 * wmin);  /* 3cw: every side shorter than R_w */
     double e = 0.0, w = 0.0;
     uint64_t nint = 0;
     double* F = calloc((size_t)(3 * (n > 0 ? n : 1)), sizeof(double));
@@ -754,6 +851,7 @@ int orc_atm_brute(const double* prm, int64_t n, const double* x, int trunc, int 
                 double b = bf_dsq(c.xw, n, g->L, i, k, dik);
                 double cc = bf_dsq(c.xw, n, g->L, j, k, djk);
                 if (!bf_keep(rc2, rc6, trunc, a, b, cc)) continue;
+                if (member == ORC_3CW && !(a < rw2 && b < rw2 && cc < rw2)) continue;
                 nint++;
                 double du[3];
                 orc_atm_du_dsq(a, b, cc, g->nu, du);

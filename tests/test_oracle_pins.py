@@ -412,3 +412,75 @@ def test_velocity_verlet_is_time_reversible_and_conserves_energy():
     d = back["x"] - np.mod(cfg["x"], cfg["box"][:, None])
     d -= np.rint(d / cfg["box"][:, None]) * cfg["box"][:, None]
     assert np.abs(d).max() < 1e-8
+
+
+# ---------------------------------------------------- wide owner traversal
+
+def _wide_system(n=1000, rho=0.5, seed=77):
+    cfg = synth.homogeneous(n, rho, 1.0, seed)
+    return cfg, oracle.params(cfg["box"], 2.5, 0.073)
+
+
+def test_wide_traversal_equals_brute_force_with_member_filter():
+    cfg, prm = _wide_system()
+    nc, w = oracle.cell_grid(prm)
+    assert nc.min() >= 5
+    bf = oracle.atm_brute(prm, cfg["x"], "product", member="3cw")
+    lc = oracle.atm_cells(prm, cfg["x"], "3cw", "product", "fp64")
+    # owner traversal: each triplet visited by its three members
+    assert lc["n_int3"] == 3 * bf["n_int3"]
+    assert abs(lc["e3"] - bf["e3"]) <= 1e-10 * abs(bf["e3"])
+    assert abs(lc["w3"] - bf["w3"]) <= 1e-10 * abs(bf["w3"])
+    scale = np.sqrt(np.mean(bf["f"] ** 2))
+    assert np.max(np.abs(lc["f"] - bf["f"])) <= 1e-10 * scale
+
+
+def test_wide_traversal_is_complete_for_the_product_rule():
+    # closest pair r_min: every product-rule triplet has its longest side below
+    # (r_min + sqrt(r_min^2 + 4 rc^3 / r_min)) / 2, here below R_w = 2 min(w)
+    cfg, prm = _wide_system()
+    x = cfg["x"]
+    L = cfg["box"][0]
+    d = x[:, :, None] - x[:, None, :]
+    d -= L * np.rint(d / L)
+    r = np.sqrt((d ** 2).sum(0))
+    np.fill_diagonal(r, np.inf)
+    rmin = r.min()
+    lmax = (rmin + np.sqrt(rmin ** 2 + 4 * 2.5 ** 3 / rmin)) / 2
+    _, w = oracle.cell_grid(prm)
+    assert lmax < 2 * w.min()
+    full = oracle.atm_brute(prm, x, "product")
+    wide = oracle.atm_brute(prm, x, "product", member="3cw")
+    assert full["n_int3"] == wide["n_int3"]
+    assert abs(full["e3"] - wide["e3"]) <= 1e-12 * abs(full["e3"])
+    # and the paper's traversals find a subset
+    for trav in ("3c01", "3c18", "3c08"):
+        t = oracle.atm_cells(prm, x, trav, "product", "fp64")
+        n_unique = t["n_int3"] // 3 if trav == "3c01" else t["n_int3"]
+        assert n_unique <= full["n_int3"]
+
+
+def test_wide_traversal_pair_rule_and_candidates():
+    cfg, prm = _wide_system(n=600, rho=0.3, seed=78)
+    x = cfg["x"]
+    lc = oracle.atm_cells(prm, x, "3cw", "pair", "fp64")
+    bf = oracle.atm_brute(prm, x, "pair")
+    assert lc["n_int3"] == 3 * bf["n_int3"]
+    assert abs(lc["e3"] - bf["e3"]) <= 1e-10 * abs(bf["e3"])
+    # candidates: the partner pairs of every owner (partners within R_w)
+    _, w = oracle.cell_grid(prm)
+    rw2 = (2 * w.min()) ** 2
+    L = cfg["box"][0]
+    d = x[:, :, None] - x[:, None, :]
+    d -= L * np.rint(d / L)
+    d2 = (d ** 2).sum(0)
+    np.fill_diagonal(d2, np.inf)
+    npart = (d2 < rw2).sum(1)
+    assert lc["n_cand3"] == int((npart * (npart - 1) // 2).sum())
+
+
+def test_wide_traversal_needs_five_cells():
+    cfg = synth.config("liquid_n1000")  # 4 cells per axis
+    prm = oracle.params(cfg["box"], 2.5, 0.073)
+    with pytest.raises(oracle.OracleError):
+        oracle.atm_cells(prm, cfg["x"], "3cw", "product", "fp64")
