@@ -45,7 +45,7 @@ typedef enum {
     ATM_E_CAPACITY = 7       /* a cell holds more molecules than the kernels stage (see atm_create) */
 } atm_status;
 
-/* Cell-triplet traversals (paper section 4).
+/* Cell-triplet traversals (paper section 4, and one wide traversal).
  *  3C01: no Newton-3; for every molecule i of a base cell, every pair {j,k} of
  *        other molecules in its 27-cell neighbourhood; only F_i is written and
  *        u/3 is added per visit.
@@ -55,7 +55,16 @@ typedef enum {
  *  3C08: Newton-3; 2x2x2 block anchored at the base cell; every cell multiset
  *        of the block whose bounding box starts at the anchor
  *        (1 + 13 + 44 cell tasks per block). */
-typedef enum { ATM_3C01 = 0, ATM_3C18 = 1, ATM_3C08 = 2 } atm_traversal;
+/*  3CW:  not in the paper.  Like 3C01 (owner computes, u/3 per visit) over the
+ *        5x5x5 cells around the base cell: for i in the base cell, every pair
+ *        {j, k} of molecules within R_w = 2 min(w_d) of i (within r_c under the
+ *        pair rule) whose third side is below R_w too.  Under the product rule it finds every interacting
+ *        triplet with all sides below R_w -- every one, once the closest pair
+ *        is r_min apart with (r_min + sqrt(r_min^2 + 4 r_c^3 / r_min)) / 2 <=
+ *        R_w -- and so measures what the paper's traversals miss.  Needs 5
+ *        cells per axis (BOX_TOO_SMALL otherwise).  n_cand3 counts the
+ *        partner pairs of every owner, n_int3 the owner visits. */
+typedef enum { ATM_3C01 = 0, ATM_3C18 = 1, ATM_3C08 = 2, ATM_3CW = 3 } atm_traversal;
 
 /* Truncation conditions (paper section 2).  A triplet interacts iff
  *  PAIR:    r_ij < r_c and r_ik < r_c and r_jk < r_c;

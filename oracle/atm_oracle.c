@@ -440,7 +440,8 @@ static void unit_3c01(ev_t* ev, int64_t b)
 /* ---- 3cw, the wide owner traversal (not in the paper; it measures what the
  *      paper's traversals miss under the product rule): for i in C_b, every
  *      pair {j, k} of molecules of the 5^3 neighbourhood within R_w = 2 min(w)
- *      of i, kept if the third side is shorter than R_w too and the
+ *      of i (within r_c under the pair rule, where no longer side can
+ *      interact), kept if the third side is shorter than R_w too and the
  *      truncation test holds; forces on i only, u/3 and W/3 per visit.  It
  *      finds every triplet with all sides shorter than R_w, which under the
  *      product rule is every interacting triplet once the closest pair is at
@@ -455,6 +456,9 @@ static void unit_3cw(ev_t* ev, int64_t b, int64_t* plist, int* poff)
     for (int d = 1; d < 3; d++) wmin = c->g.w[d] < wmin ? c->g.w[d] : wmin;
     const double rw2 = (2.0 * wmin) * (2.0 * wmin);
     const float rw2f = (float)rw2;
+    /* partner radius: R_w, or r_c under the pair rule */
+    const double pr2 = ev->trunc == ORC_PAIR ? ev->rc2 : rw2;
+    const float pr2f = ev->trunc == ORC_PAIR ? ev->rc2f : rw2f;
     int off[125][3];
     int64_t cid[125];
     int m = 0;
@@ -475,10 +479,10 @@ static void unit_3cw(ev_t* ev, int64_t b, int64_t* plist, int* poff)
                 if (j == i) continue;
                 int in;
                 if (ev->prec == ORC_FP32) {
-                    in = dsq32(ev, i, ZERO3, j, off[s]) < rw2f;
+                    in = dsq32(ev, i, ZERO3, j, off[s]) < pr2f;
                 } else {
                     double d[3];
-                    in = dsq64(ev, i, ZERO3, j, off[s], d) < rw2;
+                    in = dsq64(ev, i, ZERO3, j, off[s], d) < pr2;
                 }
                 if (in) {
                     plist[np] = j;

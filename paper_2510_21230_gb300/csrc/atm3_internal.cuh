@@ -5,6 +5,8 @@
 
 namespace atm3 {
 
+constexpr int ATM_NTRAV = 4;  // 3c01, 3c18, 3c08, 3cw
+
 // device status word bits (set by kernels, read back by the host)
 enum : int {
     ST_CAPACITY = 1,   // a unit stages more molecules than its shared memory holds
@@ -34,6 +36,8 @@ struct Rep {
     float wf[3];
     float p_lo, p_hi;          // FP64 prefilter band of a squared distance
     float q_lo, q_hi, dmin;    // FP64 prefilter band of a sorted product
+    double rw2;                // wide traversal: (2 min w)^2, partners and third sides below it
+    float rw2f;
 };
 
 struct Batch {
@@ -76,6 +80,8 @@ __host__ __device__ __forceinline__ void offset27(int t, int& dx, int& dy, int& 
 
 // Cell slots staged by each traversal's unit, base cell first.
 //  3c01: slot 0 = base, then the other 26 neighbours in linear order.
+//  3cw:  slot 0 = base, then the other 124 cells of the 5^3 neighbourhood in
+//        linear order ((dz, dy, dx) in -2..2).
 //  3c18: slot 0 = base, slots 1..13 = forward neighbours in lexicographic order.
 //  3c08: slot s = offset (s & 1, s >> 1 & 1, s >> 2 & 1) inside the 2x2x2 block.
 template <int TRAV>
@@ -86,6 +92,11 @@ __host__ __device__ __forceinline__ void slot_offset(int s, int& dx, int& dy, in
         offset27(t, dx, dy, dz);
     } else if (TRAV == 1) {
         offset27(13 + s, dx, dy, dz);
+    } else if (TRAV == 3) {
+        int t = s == 0 ? 62 : (s <= 62 ? s - 1 : s);
+        dx = t % 5 - 2;
+        dy = (t / 5) % 5 - 2;
+        dz = t / 25 - 2;
     } else {
         dx = s & 1;
         dy = (s >> 1) & 1;
@@ -107,6 +118,10 @@ template <>
 struct Trav<2> {
     static constexpr int S = 8;
 };
+template <>
+struct Trav<3> {
+    static constexpr int S = 125;
+};
 
 // Arguments of the ATM unit kernels.
 template <typename R>
@@ -125,16 +140,18 @@ struct AtmArgs {
     int gcap;                 // edge-accumulator capacity (block kernel)
     int use_d;                // block kernel, product rule: dense FP32 distance table in smem
     int acc_mode;             // block kernel, product rule: 0 dense pair scalars, 1 per-molecule atomics
+    int pcap;                 // owner kernels: partner-list capacity per warp
 };
 
-// Shared-memory plan of the 3c01 (owner) kernel: staged positions, per-warp
-// partner lists (index, displacement, squared distance) and pair queues.
+// Shared-memory plan of the owner kernels (3c01, 3cw): staged positions,
+// per-warp partner lists of capacity pcap (index, displacement, squared
+// distance) and pair queues.
 struct OwnerSmem {
     size_t off_pos, off_pos32, off_slot, off_pq, off_pd, off_pa32, off_queue, total;
 };
 
 template <typename R>
-__host__ __device__ inline OwnerSmem owner_smem_plan(int mcap, int nwarps)
+__host__ __device__ inline OwnerSmem owner_smem_plan(int mcap, int nwarps, int pcap)
 {
     OwnerSmem p;
     size_t o = 0;
@@ -143,9 +160,9 @@ __host__ __device__ inline OwnerSmem owner_smem_plan(int mcap, int nwarps)
     p.off_pos = o;   o = al(o + sizeof(R) * 3 * (size_t)mcap);
     p.off_pos32 = o; o = al(o + (f64 ? sizeof(float) * 3 * (size_t)mcap : 0));
     p.off_slot = o;  o = al(o + (size_t)mcap);
-    p.off_pq = o;    o = al(o + sizeof(unsigned short) * (size_t)mcap * nwarps);
-    p.off_pd = o;    o = al(o + sizeof(R) * 4 * (size_t)mcap * nwarps);
-    p.off_pa32 = o;  o = al(o + (f64 ? sizeof(float) * (size_t)mcap * nwarps : 0));
+    p.off_pq = o;    o = al(o + sizeof(unsigned short) * (size_t)pcap * nwarps);
+    p.off_pd = o;    o = al(o + sizeof(R) * 4 * (size_t)pcap * nwarps);
+    p.off_pa32 = o;  o = al(o + (f64 ? sizeof(float) * (size_t)pcap * nwarps : 0));
     p.off_queue = o; o = al(o + sizeof(unsigned) * 64 * (size_t)nwarps);
     p.total = o;
     return p;
@@ -212,27 +229,44 @@ __host__ __device__ inline BlockSmem block_smem_plan(int trunc, int mcap, int nw
 // dense distances + dense pair scalars, else dense pair scalars only, else
 // per-molecule accumulators.  Returns false if nothing fits.
 struct AtmPlan {
-    int nwarps, gcap, use_d, acc_mode;
+    int nwarps, gcap, use_d, acc_mode, pcap;
     size_t smem;
 };
+
+// partner capacity of the wide traversal's warps (molecules within twice the
+// cell edge: about 380 in a liquid at rho* = 0.8)
+constexpr int ATM_WIDE_PCAP = 1024;
 
 inline bool atm_choose_plan_nw(int trav, int trunc, int prec, int mcap, int optin, int nwarps,
                                AtmPlan& P)
 {
+    // the kernels' static shared memory (slot tables, reductions; under 2 KB)
+    // counts against the same per-block limit as the dynamic part
+    optin -= 4096;
     P.nwarps = nwarps;
     P.gcap = 0;
     P.use_d = 0;
     P.acc_mode = 0;
+    P.pcap = trav == 3 ? (mcap < ATM_WIDE_PCAP ? mcap : ATM_WIDE_PCAP) : mcap;
     auto bytes = [&]() -> size_t {
-        if (trav == 0)
-            return prec == 0 ? owner_smem_plan<double>(mcap, P.nwarps).total
-                             : owner_smem_plan<float>(mcap, P.nwarps).total;
+        if (trav == 0 || trav == 3)
+            return prec == 0 ? owner_smem_plan<double>(mcap, P.nwarps, P.pcap).total
+                             : owner_smem_plan<float>(mcap, P.nwarps, P.pcap).total;
         return prec == 0
                    ? block_smem_plan<double>(trunc, mcap, P.nwarps, P.gcap, P.use_d, P.acc_mode).total
                    : block_smem_plan<float>(trunc, mcap, P.nwarps, P.gcap, P.use_d, P.acc_mode).total;
     };
-    if (trav == 0) {
+    if (trav == 0 || trav == 3) {
         P.smem = bytes();
+        // the wide traversal: fewer warps, then fewer partner slots, before giving up
+        while (trav == 3 && P.smem > (size_t)optin && P.nwarps > 1) {
+            P.nwarps /= 2;
+            P.smem = bytes();
+        }
+        while (trav == 3 && P.smem > (size_t)optin && P.pcap > 256) {
+            P.pcap /= 2;
+            P.smem = bytes();
+        }
         return P.smem <= (size_t)optin;
     }
     const long long npair = (long long)mcap * (mcap - 1) / 2;
@@ -259,7 +293,7 @@ inline bool atm_choose_plan_nw(int trav, int trunc, int prec, int mcap, int opti
 inline bool atm_choose_plan(int trav, int trunc, int prec, int mcap, int optin, AtmPlan& P)
 {
     return atm_choose_plan_nw(trav, trunc, prec, mcap, optin,
-                              (trav == 0 || (trunc == 0 && prec == 1)) ? 4 : 8, P);
+                              (trav == 0 || trav == 3 || (trunc == 0 && prec == 1)) ? 4 : 8, P);
 }
 
 }  // namespace atm3

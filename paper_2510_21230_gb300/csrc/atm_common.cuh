@@ -172,24 +172,29 @@ __device__ __forceinline__ void unit_slots(const Grid& g, const int* cell_start,
     int lane = threadIdx.x & 31;
     int cx, cy, cz;
     cell_coords(g, u, cx, cy, cz);
-    int cnt = 0;
-    if (lane < S) {
-        int dx, dy, dz;
-        slot_offset<TRAV>(lane, dx, dy, dz);
-        long long c = cell_at(g, cx, cy, cz, dx, dy, dz);
-        int c0 = cell_start[c];
-        cnt = cell_start[c + 1] - c0;
-        s_cell0[lane] = c0;
-        s_off[lane][0] = (signed char)dx;
-        s_off[lane][1] = (signed char)dy;
-        s_off[lane][2] = (signed char)dz;
+    int run = 0;  // staged molecules of the slots before this chunk of 32
+    for (int s0 = 0; s0 < S; s0 += 32) {
+        const int s = s0 + lane;
+        int cnt = 0;
+        if (s < S) {
+            int dx, dy, dz;
+            slot_offset<TRAV>(s, dx, dy, dz);
+            long long c = cell_at(g, cx, cy, cz, dx, dy, dz);
+            int c0 = cell_start[c];
+            cnt = cell_start[c + 1] - c0;
+            s_cell0[s] = c0;
+            s_off[s][0] = (signed char)dx;
+            s_off[s][1] = (signed char)dy;
+            s_off[s][2] = (signed char)dz;
+        }
+        int incl = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            int v = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (s < S) s_beg[s + 1] = run + incl;
+        run += __shfl_sync(FULL, incl, 31);
     }
-    int incl = cnt;
-    for (int o = 1; o < 32; o <<= 1) {
-        int v = __shfl_up_sync(FULL, incl, o);
-        if (lane >= o) incl += v;
-    }
-    if (lane < S) s_beg[lane + 1] = incl;
     if (lane == 0) s_beg[0] = 0;
 }
 

@@ -12,8 +12,10 @@ cudaError_t launch_atm_fp64(int trav, int trunc, const AtmArgs<double>& a, int n
 {
     if (a.b.ncell == 0) return cudaSuccess;
     dim3 grid(ctas > 0 ? (unsigned)ctas : (unsigned)a.b.ncell), block(32 * nwarps);
-    if (trav == 0 && trunc == 0) atm_owner_kernel<0, double><<<grid, block, smem, s>>>(a);
-    else if (trav == 0 && trunc == 1) atm_owner_kernel<1, double><<<grid, block, smem, s>>>(a);
+    if (trav == 0 && trunc == 0) atm_owner_kernel<0, 0, double><<<grid, block, smem, s>>>(a);
+    else if (trav == 3 && trunc == 0) atm_owner_kernel<3, 0, double><<<grid, block, smem, s>>>(a);
+    else if (trav == 3 && trunc == 1) atm_owner_kernel<3, 1, double><<<grid, block, smem, s>>>(a);
+    else if (trav == 0 && trunc == 1) atm_owner_kernel<0, 1, double><<<grid, block, smem, s>>>(a);
     else if (trav == 1 && trunc == 0) atm_block_kernel<1, 0, double><<<grid, block, smem, s>>>(a);
     else if (trav == 1 && trunc == 1) atm_block_kernel<1, 1, double><<<grid, block, smem, s>>>(a);
     else if (trav == 2 && trunc == 0) atm_block_kernel<2, 0, double><<<grid, block, smem, s>>>(a);
@@ -25,8 +27,10 @@ cudaError_t launch_atm_fp64(int trav, int trunc, const AtmArgs<double>& a, int n
 cudaError_t atm_attr_fp64(int trav, int trunc, size_t smem)
 {
     const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    if (trav == 0 && trunc == 0) return cudaFuncSetAttribute(atm_owner_kernel<0, double>, A, (int)smem);
-    if (trav == 0 && trunc == 1) return cudaFuncSetAttribute(atm_owner_kernel<1, double>, A, (int)smem);
+    if (trav == 0 && trunc == 0) return cudaFuncSetAttribute(atm_owner_kernel<0, 0, double>, A, (int)smem);
+    if (trav == 3 && trunc == 0) return cudaFuncSetAttribute(atm_owner_kernel<3, 0, double>, A, (int)smem);
+    if (trav == 3 && trunc == 1) return cudaFuncSetAttribute(atm_owner_kernel<3, 1, double>, A, (int)smem);
+    if (trav == 0 && trunc == 1) return cudaFuncSetAttribute(atm_owner_kernel<0, 1, double>, A, (int)smem);
     if (trav == 1 && trunc == 0) return cudaFuncSetAttribute(atm_block_kernel<1, 0, double>, A, (int)smem);
     if (trav == 1 && trunc == 1) return cudaFuncSetAttribute(atm_block_kernel<1, 1, double>, A, (int)smem);
     if (trav == 2 && trunc == 0) return cudaFuncSetAttribute(atm_block_kernel<2, 0, double>, A, (int)smem);
@@ -39,8 +43,10 @@ int atm_occupancy_fp64(int trav, int trunc, int nwarps, size_t smem)
 {
     int nb = 0;
     const int bs = 32 * nwarps;
-    if (trav == 0 && trunc == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, atm_owner_kernel<0, double>, bs, smem);
-    else if (trav == 0 && trunc == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, atm_owner_kernel<1, double>, bs, smem);
+    if (trav == 0 && trunc == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, atm_owner_kernel<0, 0, double>, bs, smem);
+    else if (trav == 3 && trunc == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, atm_owner_kernel<3, 0, double>, bs, smem);
+    else if (trav == 3 && trunc == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, atm_owner_kernel<3, 1, double>, bs, smem);
+    else if (trav == 0 && trunc == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, atm_owner_kernel<0, 1, double>, bs, smem);
     else if (trav == 1 && trunc == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, atm_block_kernel<1, 0, double>, bs, smem);
     else if (trav == 1 && trunc == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, atm_block_kernel<1, 1, double>, bs, smem);
     else if (trav == 2 && trunc == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, atm_block_kernel<2, 0, double>, bs, smem);

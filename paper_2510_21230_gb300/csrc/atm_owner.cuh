@@ -1,11 +1,14 @@
-// atm_owner.cuh -- 3c01 traversal (section 4): no Newton-3, owner computes.
+// atm_owner.cuh -- owner-computes traversals: 3c01 (section 4) and the wide
+// traversal 3cw (not in the paper: 5^3 cells, partners within R_w = 2 min w,
+// third side below R_w too, which under the product rule finds the triplets
+// the paper's traversals miss).
 //
-// One CTA per base cell.  The 27-cell neighbourhood is staged in shared
-// memory; warps take the base cell's molecules i in turn.  For each i the
-// warp builds i's partner list (pair rule: partners within r_c; product rule:
-// every other staged molecule) holding the displacement d(i -> q) and its
-// square, then tests every pair {j, k} of the list and queues interacting
-// pairs.  A full queue (32 pairs) is evaluated by the whole warp; only F_i is
+// One CTA per base cell.  The 27- (125-) cell neighbourhood is staged in
+// shared memory; warps take the base cell's molecules i in turn.  For each i
+// the warp builds i's partner list (pair rule: partners within r_c; product
+// rule: every other staged molecule, 3cw: those within R_w) holding the
+// displacement d(i -> q) and its square, then tests every pair {j, k} of the
+// list and queues interacting pairs.  A full queue (32 pairs) is evaluated by the whole warp; only F_i is
 // needed, so each lane keeps its share of F_i in registers (compensated in
 // FP32) and the warp reduces it once per i: no atomics, deterministic.
 // Energy and virial get u/3 and W/3 per visit (each triangle is found by up
@@ -15,10 +18,11 @@
 
 namespace atm3 {
 
-template <int TRUNC, typename R>
+template <int TRAV, int TRUNC, typename R>
 __device__ __forceinline__ void atm_owner_unit(const AtmArgs<R>& A, const long long u)
 {
-    constexpr int TRAV = 0, S = 27;
+    constexpr int S = Trav<TRAV>::S;
+    constexpr bool WIDE = TRAV == 3;
     constexpr bool F64 = sizeof(R) == 8;
     constexpr unsigned FULL = 0xffffffffu;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -26,6 +30,7 @@ __device__ __forceinline__ void atm_owner_unit(const AtmArgs<R>& A, const long l
     __shared__ int s_cell0[S];
     __shared__ signed char s_off[S][3];
     __shared__ int s_next;
+    __shared__ unsigned long long s_cand;
     __shared__ double s_red[2][8];
     __shared__ unsigned long long s_redn[8];
 
@@ -35,7 +40,8 @@ __device__ __forceinline__ void atm_owner_unit(const AtmArgs<R>& A, const long l
     // the replica this unit belongs to and the unit's index inside it
     const Rep& rp = A.b.rep[A.b.rep_of_cell[u]];
     const long long lu = u - rp.cell0;
-    const OwnerSmem plan = owner_smem_plan<R>(mcap, nwarps);
+    const int pcap = A.pcap;
+    const OwnerSmem plan = owner_smem_plan<R>(mcap, nwarps, pcap);
     R* px = reinterpret_cast<R*>(smem + plan.off_pos);
     R* py = px + mcap;
     R* pz = py + mcap;
@@ -43,16 +49,19 @@ __device__ __forceinline__ void atm_owner_unit(const AtmArgs<R>& A, const long l
     float* fy32 = fx32 + mcap;
     float* fz32 = fy32 + mcap;
     unsigned char* sslot = smem + plan.off_slot;
-    unsigned short* pq = reinterpret_cast<unsigned short*>(smem + plan.off_pq) + warp * mcap;
-    R* pdx = reinterpret_cast<R*>(smem + plan.off_pd) + (size_t)warp * 4 * mcap;
-    R* pdy = pdx + mcap;
-    R* pdz = pdy + mcap;
-    R* pa = pdz + mcap;
-    float* pa32 = F64 ? reinterpret_cast<float*>(smem + plan.off_pa32) + warp * mcap : nullptr;
+    unsigned short* pq = reinterpret_cast<unsigned short*>(smem + plan.off_pq) + warp * pcap;
+    R* pdx = reinterpret_cast<R*>(smem + plan.off_pd) + (size_t)warp * 4 * pcap;
+    R* pdy = pdx + pcap;
+    R* pdz = pdy + pcap;
+    R* pa = pdz + pcap;
+    float* pa32 = F64 ? reinterpret_cast<float*>(smem + plan.off_pa32) + warp * pcap : nullptr;
     unsigned* queue = reinterpret_cast<unsigned*>(smem + plan.off_queue) + warp * 64;
 
     if (warp == 0) unit_slots<TRAV, S>(rp.g, A.cell_start + rp.cell0, lu, s_beg, s_cell0, s_off);
-    if (tid == 0) s_next = 0;
+    if (tid == 0) {
+        s_next = 0;
+        s_cand = 0ull;
+    }
     __syncthreads();
     const int M = s_beg[S];
     const int Mfirst = s_beg[1];
@@ -68,8 +77,17 @@ __device__ __forceinline__ void atm_owner_unit(const AtmArgs<R>& A, const long l
     }
     const long long n = A.n;
     for (int t = tid; t < M; t += blockDim.x) {
+        // slot of staged molecule t: the last s with s_beg[s] <= t (a slot may be empty)
         int s = 0;
-        while (s_beg[s + 1] <= t) s++;
+        if (S <= 32) {
+            while (s_beg[s + 1] <= t) s++;
+        } else {
+            int hi = S - 1;
+            while (s < hi) {
+                const int mid = (s + hi + 1) >> 1;
+                if (s_beg[mid] <= t) s = mid; else hi = mid - 1;
+            }
+        }
         int g = s_cell0[s] + (t - s_beg[s]);
         px[t] = A.xl[g];
         py[t] = A.xl[n + g];
@@ -116,6 +134,16 @@ __device__ __forceinline__ void atm_owner_unit(const AtmArgs<R>& A, const long l
         return d2 < rc2;
     };
 
+    // wide traversal: within R_w (FP32 decisions in FP32, FP64 ones in FP64)
+    const R rw2 = F64 ? (R)rp.rw2 : (R)rp.rw2f;
+    auto within_rw = [&](int p, int q) -> bool {
+        int mx, my, mz;
+        offs(p, q, mx, my, mz);
+        R dx, dy, dz;
+        return canon_disp<R>(px[p], py[p], pz[p], px[q], py[q], pz[q], mx, my, mz, w0, w1, w2, dx,
+                             dy, dz) < rw2;
+    };
+
     Sum<R> esum, wsum;
     unsigned int nint = 0;
 
@@ -130,10 +158,15 @@ __device__ __forceinline__ void atm_owner_unit(const AtmArgs<R>& A, const long l
         for (int q0 = 0; q0 < M; q0 += 32) {
             int q = q0 + lane;
             bool keep = false;
-            if (q < M && q != i) keep = (TRUNC == 0) ? close_pair(i, q) : true;
+            if (q < M && q != i)
+                keep = (TRUNC == 0) ? close_pair(i, q) : (WIDE ? within_rw(i, q) : true);
             unsigned m = __ballot_sync(FULL, keep);
+            const int pos = np + __popc(m & lt_mask);
+            if (keep && pos >= pcap) {
+                atomicOr(A.status, ST_CAPACITY);  // more partners than the list holds
+                keep = false;
+            }
             if (keep) {
-                int pos = np + __popc(m & lt_mask);
                 int mx, my, mz;
                 offs(i, q, mx, my, mz);
                 R dx, dy, dz;
@@ -152,6 +185,8 @@ __device__ __forceinline__ void atm_owner_unit(const AtmArgs<R>& A, const long l
             }
             np += __popc(m);
         }
+        if (np > pcap) np = pcap;
+        if (WIDE && lane == 0) atomicAdd(&s_cand, (unsigned long long)np * (unsigned long long)(np - 1) / 2ull);
         __syncwarp();
 
         Sum<R> fxs, fys, fzs;
@@ -186,6 +221,14 @@ __device__ __forceinline__ void atm_owner_unit(const AtmArgs<R>& A, const long l
                 int j = pq[jj], k = pq[kk];
                 if (TRUNC == 0) {
                     keep = close_pair(j, k);
+                } else if (WIDE) {
+                    // third side below R_w, then the sorted product, in the working precision
+                    int mx, my, mz;
+                    offs(j, k, mx, my, mz);
+                    R dx, dy, dz;
+                    R c = canon_disp<R>(px[j], py[j], pz[j], px[k], py[k], pz[k], mx, my, mz, w0,
+                                        w1, w2, dx, dy, dz);
+                    keep = c < rw2 && sorted_product<R>(pa[jj], pa[kk], c) < rc6;
                 } else {
                     int mx, my, mz;
                     offs(j, k, mx, my, mz);
@@ -246,18 +289,22 @@ __device__ __forceinline__ void atm_owner_unit(const AtmArgs<R>& A, const long l
     }
 
     unsigned long long cand = 0;
-    if (tid == 0) cand = unit_candidates<TRAV, S>(s_beg);
+    if (WIDE) __syncthreads();  // every warp's partner-pair count is in
+    if (tid == 0) {
+        if constexpr (WIDE) cand = s_cand;
+        else cand = unit_candidates<TRAV, S>(s_beg);
+    }
     unit_reduce_store<8>(esum.get(), wsum.get(), (unsigned long long)nint, 1.0 / 3.0, cand,
                          A.unit_ew, A.unit_cnt, u, s_red, s_redn);
 }
 
 // One CTA per base cell, or (A.work set) a persistent grid pulling units from
 // a global counter.
-template <int TRUNC, typename R>
+template <int TRAV, int TRUNC, typename R>
 __global__ void __launch_bounds__(128) atm_owner_kernel(const AtmArgs<R> A)
 {
     if (A.work == nullptr) {
-        atm_owner_unit<TRUNC, R>(A, blockIdx.x);
+        atm_owner_unit<TRAV, TRUNC, R>(A, blockIdx.x);
         return;
     }
     __shared__ int s_u;
@@ -267,7 +314,7 @@ __global__ void __launch_bounds__(128) atm_owner_kernel(const AtmArgs<R> A)
         __syncthreads();
         const int u = s_u;
         if (u >= A.b.ncell) break;
-        atm_owner_unit<TRUNC, R>(A, u);
+        atm_owner_unit<TRAV, TRUNC, R>(A, u);
     }
 }
 

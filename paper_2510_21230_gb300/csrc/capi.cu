@@ -203,12 +203,12 @@ extern "C" atm_status atm_batch_create(const atm_params* params, const int64_t* 
     ok = ok && alloc((void**)&c->d_res, nrep * sizeof(ResultDev));
     ok = ok && alloc((void**)&c->d_part, (size_t)nrep * REDUCE_PARTS * sizeof(ResultDev));
     ok = ok && alloc((void**)&c->d_status, sizeof(int));
-    ok = ok && alloc((void**)&c->d_maxocc, 4 * sizeof(int));
+    ok = ok && alloc((void**)&c->d_maxocc, (1 + ATM_NTRAV) * sizeof(int));
     ok = ok && alloc((void**)&c->d_work, sizeof(int));
     ok = ok && alloc((void**)&c->d_dens, (size_t)nrep * DENS_MAX_BINS * sizeof(unsigned long long));
     ok = ok && cudaMallocHost((void**)&c->h_res, nrep * sizeof(ResultDev)) == cudaSuccess;
     ok = ok && cudaMallocHost((void**)&c->h_status, sizeof(int)) == cudaSuccess;
-    ok = ok && cudaMallocHost((void**)&c->h_maxocc, 4 * sizeof(int)) == cudaSuccess;
+    ok = ok && cudaMallocHost((void**)&c->h_maxocc, (1 + ATM_NTRAV) * sizeof(int)) == cudaSuccess;
     ok = ok && cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin,
                                       c->device) == cudaSuccess;
     ok = ok && cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device) ==
@@ -335,11 +335,11 @@ static atm_status enqueue_cells(atm_ctx* c)
 {
     atm_status s = launch_cells(c);
     if (s != ATM_OK) return s;
-    CU(cudaMemcpyAsync(c->h_maxocc, c->d_maxocc, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    CU(cudaMemcpyAsync(c->h_maxocc, c->d_maxocc, (1 + ATM_NTRAV) * sizeof(int), cudaMemcpyDeviceToHost, c->st));
     s = ctx_sync_and_check(c);
     if (s != ATM_OK) return s;
     c->maxocc = c->h_maxocc[0];
-    for (int t = 0; t < 3; t++) c->unit_max[t] = c->h_maxocc[1 + t];
+    for (int t = 0; t < ATM_NTRAV; t++) c->unit_max[t] = c->h_maxocc[1 + t];
     c->cells_built = true;
     c->forces_valid = false;
     return ATM_OK;
@@ -384,12 +384,16 @@ static void launch_choice(const atm_ctx* c, int trav, int trunc, int prec, int& 
         persistent = c->opt_persistent;
         nwarps = c->opt_nwarps;
     }
-    if (trav == ATM_3C01) nwarps = 0;
+    if (trav == ATM_3C01 || trav == ATM_3CW) nwarps = 0;
 }
 
 // LJ + ATM force kernels for the current cells; mcap = staged-molecule capacity
 atm_status atm3::ctx_enqueue_forces(atm_ctx* c, int trav, int trunc, int prec, int mcap)
 {
+    if (trav == ATM_3CW)
+        for (const Rep& r : c->reps)
+            if (r.g.nc[0] < 5 || r.g.nc[1] < 5 || r.g.nc[2] < 5)
+                return ctx_fail(c, ATM_E_BOX_TOO_SMALL, "the wide traversal needs 5 cells per axis");
     ForceJob j;
     j.b = c->b;
     j.rep_host = c->reps.data();
@@ -484,7 +488,7 @@ static void copy_result(const ResultDev& r, atm_result* out)
 
 static bool valid_enums(int trav, int trunc, int prec)
 {
-    return trav >= 0 && trav <= 2 && trunc >= 0 && trunc <= 1 && prec >= 0 && prec <= 2;
+    return trav >= 0 && trav <= 3 && trunc >= 0 && trunc <= 1 && prec >= 0 && prec <= 2;
 }
 
 extern "C" atm_status atm_compute_forces(atm_ctx* c, atm_traversal trav, atm_truncation trunc,
@@ -582,7 +586,8 @@ static atm_status enqueue_step(atm_ctx* c, int trav, int trunc, int prec, int mc
 static int graph_mcap(const atm_ctx* c, int trav)
 {
     int m = c->unit_max[trav];
-    return std::min(ATM_MCAP_LIMIT, m + std::max(8, m / 4));
+    const int limit = (trav == ATM_3C01 || trav == ATM_3CW) ? 65535 : ATM_MCAP_LIMIT;
+    return std::min(limit, m + std::max(8, m / 4));
 }
 
 // run nsteps with a CUDA graph of one step (no host synchronisation between
@@ -656,12 +661,12 @@ extern "C" atm_status atm_step(atm_ctx* c, int nsteps, atm_traversal trav, atm_t
         }
         s = run_graph_steps(c, nsteps, trav, trunc, prec);
         if (s != ATM_OK) return s;
-        CU(cudaMemcpyAsync(c->h_maxocc, c->d_maxocc, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->st));
+        CU(cudaMemcpyAsync(c->h_maxocc, c->d_maxocc, (1 + ATM_NTRAV) * sizeof(int), cudaMemcpyDeviceToHost, c->st));
         s = ctx_sync_and_check(c);
         if (s == ATM_OK) {
             done = true;
             c->maxocc = c->h_maxocc[0];
-            for (int t = 0; t < 3; t++) c->unit_max[t] = c->h_maxocc[1 + t];
+            for (int t = 0; t < ATM_NTRAV; t++) c->unit_max[t] = c->h_maxocc[1 + t];
         } else if (s == ATM_E_CAPACITY) {
             // a unit outgrew the graph's capacity: restart from the snapshot
             // and step with per-step sizing
@@ -747,7 +752,7 @@ extern "C" atm_status atm_autotune(atm_ctx* c, atm_traversal trav, atm_truncatio
     float best = 1e30f;
     int best_code = 1;
     atm_status s = ATM_OK;
-    const int nw_options = trav == ATM_3C01 ? 1 : 2;
+    const int nw_options = (trav == ATM_3C01 || trav == ATM_3CW) ? 1 : 2;
     for (int nwi = 0; nwi < nw_options && s == ATM_OK; nwi++)
         for (int pers = 0; pers < 2 && s == ATM_OK; pers++) {
             const int code = 1 + pers + 2 * nwi;

@@ -57,15 +57,15 @@ struct atm_ctx {
     int dens_axis = -1, dens_nbins = 0;
     long long dens_samples = 0;
     int maxocc = 0;
-    int unit_max[3] = {0, 0, 0};  // largest unit (staged molecules) of 3c01, 3c18, 3c08
+    int unit_max[atm3::ATM_NTRAV] = {};  // largest unit (staged molecules) of 3c01, 3c18, 3c08, 3cw
     bool have_x = false, cells_built = false, forces_valid = false;
     int f_trav = -1, f_trunc = -1, f_prec = -1;
-    size_t smem_set[2][3][2] = {};
+    size_t smem_set[2][atm3::ATM_NTRAV][2] = {};
     int smem_optin = 0, sms = 0;
     // launch options: persistent ATM grid, warps per block-kernel CTA (0 =
     // default), CUDA-graph steps; tuned choices per (prec, trav, trunc)
     int opt_persistent = 0, opt_nwarps = 0, opt_graph = 0;
-    int tuned[2][3][2] = {};  // 0 = not tuned, else 1 + persistent + 2 * (nwarps == 8)
+    int tuned[2][atm3::ATM_NTRAV][2] = {};  // 0 = not tuned, else 1 + persistent + 2 * (nwarps == 8)
     // graph of one step, valid for (trav, trunc, prec, mcap, launch choice)
     cudaStream_t cap_st = nullptr;
     cudaGraphExec_t graph = nullptr;

@@ -64,6 +64,9 @@ atm_status make_rep(const atm_params& p, long long n, long long mol0, long long 
     r.q_lo = (float)(r.rc6 * (1.0 - 1.0 / 1024.0));
     r.q_hi = (float)(r.rc6 * (1.0 + 1.0 / 1024.0));
     r.dmin = (float)((0.02 * wmax) * (0.02 * wmax));
+    const double wmin = std::min(r.g.w[0], std::min(r.g.w[1], r.g.w[2]));
+    r.rw2 = (2.0 * wmin) * (2.0 * wmin);
+    r.rw2f = (float)r.rw2;
     return ATM_OK;
 }
 
@@ -87,11 +90,13 @@ cudaError_t enqueue_atm(const ForceJob& j, size_t* smem_set, bool* capacity)
 {
     *capacity = false;
     AtmPlan P;
-    if (j.mcap > ATM_MCAP_LIMIT || !atm_choose_plan(j.trav, j.trunc, j.prec, j.mcap, j.optin, P)) {
+    // the block kernel packs staged indices in 11 bits, the owner kernels in 16
+    const int limit = (j.trav == 0 || j.trav == 3) ? 65535 : ATM_MCAP_LIMIT;
+    if (j.mcap > limit || !atm_choose_plan(j.trav, j.trunc, j.prec, j.mcap, j.optin, P)) {
         *capacity = true;
         return cudaErrorInvalidValue;
     }
-    if ((j.nwarps == 4 || j.nwarps == 8) && j.trav != 0) {
+    if ((j.nwarps == 4 || j.nwarps == 8) && j.trav != 0 && j.trav != 3) {
         AtmPlan Q;
         if (atm_choose_plan_nw(j.trav, j.trunc, j.prec, j.mcap, j.optin, j.nwarps, Q)) P = Q;
     }
@@ -101,7 +106,7 @@ cudaError_t enqueue_atm(const ForceJob& j, size_t* smem_set, bool* capacity)
         if (e != cudaSuccess) return e;
         if (smem_set) *smem_set = P.smem;
     }
-    if (j.trav != 0 && j.b.ntot > 0) {
+    if (j.trav != 0 && j.trav != 3 && j.b.ntot > 0) {  // owner traversals write every F_i
         e = cudaMemsetAsync(j.f_atm, 0, 3 * (size_t)j.b.ntot * sizeof(double), j.st);
         if (e != cudaSuccess) return e;
     }
@@ -122,6 +127,7 @@ cudaError_t enqueue_atm(const ForceJob& j, size_t* smem_set, bool* capacity)
         a.gcap = P.gcap;
         a.use_d = P.use_d;
         a.acc_mode = P.acc_mode;
+        a.pcap = P.pcap;
         return launch_atm_fp64(j.trav, j.trunc, a, P.nwarps, P.smem, ctas, j.st);
     }
     AtmArgs<float> a{};
@@ -132,6 +138,7 @@ cudaError_t enqueue_atm(const ForceJob& j, size_t* smem_set, bool* capacity)
     a.gcap = P.gcap;
     a.use_d = P.use_d;
     a.acc_mode = P.acc_mode;
+    a.pcap = P.pcap;
     return launch_atm_fp32(j.trav, j.trunc, a, P.nwarps, P.smem, ctas, j.st);
 }
 

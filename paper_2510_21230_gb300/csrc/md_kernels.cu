@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(1024) k_scan(long long ncell, const int* __res
 __global__ void k_unit_max(Batch B, const int* __restrict__ start, int* __restrict__ out)
 {
     long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    int m01 = 0, m18 = 0, m08 = 0;
+    int m01 = 0, m18 = 0, m08 = 0, mw = 0;
     if (c < B.ncell) {
         const Rep& rp = B.rep[B.rep_of_cell[c]];
         const int* st = start + rp.cell0;
@@ -119,16 +119,23 @@ __global__ void k_unit_max(Batch B, const int* __restrict__ start, int* __restri
             if (t >= 13) m18 += k;
             if (dx >= 0 && dy >= 0 && dz >= 0) m08 += k;
         }
+        // the wide traversal's 5^3 neighbourhood
+        for (int t = 0; t < 125; t++) {
+            long long nc = cell_at(rp.g, cx, cy, cz, t % 5 - 2, (t / 5) % 5 - 2, t / 25 - 2);
+            mw += st[nc + 1] - st[nc];
+        }
     }
     for (int o = 16; o > 0; o >>= 1) {
         m01 = max(m01, __shfl_down_sync(0xffffffffu, m01, o));
         m18 = max(m18, __shfl_down_sync(0xffffffffu, m18, o));
         m08 = max(m08, __shfl_down_sync(0xffffffffu, m08, o));
+        mw = max(mw, __shfl_down_sync(0xffffffffu, mw, o));
     }
     if ((threadIdx.x & 31) == 0) {
         atomicMax(out, m01);
         atomicMax(out + 1, m18);
         atomicMax(out + 2, m08);
+        atomicMax(out + 3, mw);
     }
 }
 
@@ -436,7 +443,7 @@ cudaError_t launch_build_cells(const Batch& b, double* x, int* cell_of, int* ran
     if (e != cudaSuccess) return e;
     if (n > 0) k_wrap_bin<<<nblk(n, MD_BLOCK), MD_BLOCK, 0, st>>>(b, x, cell_of, rank, count, status);
     k_scan<<<1, 1024, 0, st>>>(b.ncell, count, start, maxocc);
-    e = cudaMemsetAsync(maxocc + 1, 0, 3 * sizeof(int), st);
+    e = cudaMemsetAsync(maxocc + 1, 0, ATM_NTRAV * sizeof(int), st);
     if (e != cudaSuccess) return e;
     k_unit_max<<<nblk(b.ncell, MD_BLOCK), MD_BLOCK, 0, st>>>(b, start, maxocc + 1);
     if (n > 0) {

@@ -63,7 +63,7 @@ constexpr NaLayout na_layout()
     L.ke = o;          o = al256(o + NA_N * sizeof(double));
     L.res = o;         o = al256(o + (1 + REDUCE_PARTS) * sizeof(ResultDev));
     L.status = o;      o = al256(o + sizeof(int));
-    L.maxocc = o;      o = al256(o + 4 * sizeof(int));
+    L.maxocc = o;      o = al256(o + (1 + ATM_NTRAV) * sizeof(int));
     L.total = o;
     return L;
 }
@@ -162,7 +162,7 @@ extern "C" atm_status atm_compute_forces_noalloc(const atm_params* p, int64_t n,
     if (n > 0) NA_CU(launch_check_finite(3 * n, x, status, st));
     NA_CU(launch_build_cells(b, x, cell_of, rank, count, start, perm, xl, xl32, cell_sorted,
                              maxocc, status, st));
-    int hocc[4] = {0, 0, 0, 0}, hstat = 0;
+    int hocc[1 + ATM_NTRAV] = {}, hstat = 0;
     NA_CU(cudaMemcpyAsync(hocc, maxocc, sizeof(hocc), cudaMemcpyDeviceToHost, st));
     NA_CU(cudaMemcpyAsync(&hstat, status, sizeof(int), cudaMemcpyDeviceToHost, st));
     NA_CU(cudaStreamSynchronize(st));

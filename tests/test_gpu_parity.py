@@ -267,3 +267,64 @@ def test_dense_liquid_edge_table_overflow(atm3, trav, prec):
     assert r["n_cand3"] == ref["n_cand3"] and r["n_int3"] == ref["n_int3"]
     assert r["e3"] == pytest.approx(ref["e3"], rel=RTOL[prec])
     assert_forces_close(f, ref["f"], RTOL[prec], "dense " + trav + prec)
+
+
+# ------------------------------------------------------------------ wide traversal
+
+def _wide_liquid():
+    # rho 0.5, 12.6-sigma box: 5 cells per axis
+    return synth.homogeneous(1000, 0.5, 1.0, seed=77)
+
+
+@pytest.mark.parametrize("trunc", ["pair", "product"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_wide_traversal_matches_oracle(atm3, trunc, prec):
+    cfg = _wide_liquid()
+    prm = oracle.params(cfg["box"], 2.5, NU)
+    r, f, _, _ = run_gpu(atm3, cfg, "3cw", trunc, prec)
+    ref = oracle.atm_cells(prm, cfg["x"], "3cw", trunc, ORC_PREC[prec])
+    assert r["n_int3"] == ref["n_int3"] and r["n_cand3"] == ref["n_cand3"]
+    assert_forces_close(f, ref["f"], RTOL[prec], "3cw " + trunc)
+    assert abs(r["e3"] - ref["e3"]) <= RTOL[prec] * abs(ref["e3"]) * 10
+    assert abs(r["w3"] - ref["w3"]) <= RTOL[prec] * abs(ref["w3"]) * 10
+
+
+def test_wide_traversal_finds_what_the_paper_traversals_miss(atm3):
+    # product rule: the wide traversal equals the brute force over all triplets
+    # (its completeness bound holds here), the paper's traversals find fewer
+    cfg = _wide_liquid()
+    prm = oracle.params(cfg["box"], 2.5, NU)
+    bf = oracle.atm_brute(prm, cfg["x"], "product")
+    r, f, _, _ = run_gpu(atm3, cfg, "3cw", "product", "fp64")
+    assert r["n_int3"] == 3 * bf["n_int3"]
+    assert abs(r["e3"] - bf["e3"]) <= 1e-10 * abs(bf["e3"])
+    assert_forces_close(f, bf["f"], 1e-10, "3cw vs brute force")
+    for trav in ("3c18", "3c08"):
+        rt, _, _, _ = run_gpu(atm3, cfg, trav, "product", "fp64")
+        assert rt["n_int3"] < bf["n_int3"]
+
+
+def test_wide_traversal_needs_five_cells(atm3):
+    cfg = small_liquid()  # 4 cells per axis
+    with atm3.AtmSystem(cfg["box"], 1000, nu=NU) as s:
+        s.set_state(cfg["x"])
+        s.build_cells()
+        with pytest.raises(atm3.AtmError) as e:
+            s.compute_forces("3cw", "product", "fp64")
+        assert e.value.status == 2
+
+
+def test_wide_traversal_32k_sampled(atm3):
+    """N = 32,000 liquid (13 cells per axis): the owner forces of molecules in
+    sampled base cells against the oracle run on those units alone."""
+    cfg = synth.config("liquid_n32k")
+    prm = oracle.params(cfg["box"], 2.5, NU)
+    r, f, _, cells = run_gpu(atm3, cfg, "3cw", "product", "fp32c")
+    rng = np.random.default_rng(2)
+    ncell = len(cells["cell_start"]) - 1
+    sample = rng.choice(ncell, size=8, replace=False)
+    ref = oracle.atm_cells_units(prm, cfg["x"], sample, "3cw", "product", "fp32")
+    mol = np.concatenate([cells["perm"][cells["cell_start"][c]:cells["cell_start"][c + 1]]
+                          for c in sample])
+    assert_forces_close(f[:, mol], ref["f"][:, mol], RTOL["fp32c"], "sampled 3cw")
+    assert r["n_int3"] > 0 and r["w3"] == pytest.approx(9 * r["e3"], rel=1e-5)

@@ -467,9 +467,8 @@ def test_wide_traversal_pair_rule_and_candidates():
     bf = oracle.atm_brute(prm, x, "pair")
     assert lc["n_int3"] == 3 * bf["n_int3"]
     assert abs(lc["e3"] - bf["e3"]) <= 1e-10 * abs(bf["e3"])
-    # candidates: the partner pairs of every owner (partners within R_w)
-    _, w = oracle.cell_grid(prm)
-    rw2 = (2 * w.min()) ** 2
+    # candidates: the partner pairs of every owner (pair rule: partners within r_c)
+    rw2 = 2.5 ** 2
     L = cfg["box"][0]
     d = x[:, :, None] - x[:, None, :]
     d -= L * np.rint(d / L)
