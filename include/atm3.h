@@ -351,6 +351,33 @@ atm_status atm_surrogate_options(atm_ctx* ctx, int exact_every);
 atm_status atm_surrogate_error(atm_ctx* ctx, double* rms_diff, double* rms_exact,
                                int64_t* checks, int reset);
 
+/* Velocity-rescaling thermostat for the NVT runs of section 5.1 (the paper
+ * names no thermostat): the velocities of replica r are scaled by
+ * sqrt(T_r (3 N_r - 3) / (2 K_r)) so that its kinetic temperature
+ * 2 K / (3 N - 3) becomes t_target[r] (host array of R values >= 0,
+ * INVALID otherwise); a replica with K = 0 or N < 2 is left alone.  Called
+ * between atm_step calls (every k steps); synchronises; the results then
+ * report the new kinetic energy.  STATE without a state. */
+atm_status atm_thermostat(atm_ctx* ctx, const double* t_target);
+
+/* Radial distribution (paper section 5, Fig. rdfs): adds to a per-replica
+ * integer histogram every pair once with r < r_max, bin floor(r / (r_max /
+ * nbins)), r from the FP64 canonical displacement of the linked cells.
+ * r_max must not exceed the smallest cell edge (INVALID); needs built cells
+ * (STATE); range and bins are fixed until reset.  get copies counts
+ * [R][nbins] (uint64) and the number of accumulated configurations.
+ * g(r) = counts / (samples * N / 2 * rho * shell volume). */
+atm_status atm_rdf_accumulate(atm_ctx* ctx, double r_max, int nbins);
+atm_status atm_rdf_get(atm_ctx* ctx, uint64_t* counts, int64_t* samples);
+atm_status atm_rdf_reset(atm_ctx* ctx);
+
+/* Long-range corrections of the truncated (unshifted) LJ pair terms of a
+ * homogeneous system (section 5 applies them to E2 and P2; the standard
+ * tail integrals): e_tail = 8/3 pi N rho eps sigma^3 [(sigma/r_c)^9 / 3 -
+ * (sigma/r_c)^3], p_tail = 16/3 pi rho^2 eps sigma^3 [2/3 (sigma/r_c)^9 -
+ * (sigma/r_c)^3], rho = N / V.  Host arithmetic; either output may be NULL. */
+atm_status atm_lj_tail(const atm_params* params, int64_t n, double* e_tail, double* p_tail);
+
 /* Measured fused multiply-add throughput of the device (TFLOP/s, one FMA = 2
  * flops): a kernel of independent FMA chains in FP32 (fp64 = 0) or FP64,
  * best of three timed launches.  Roofline context for the ALU-bound kernels;

@@ -71,6 +71,12 @@ def lib():
         L.orc_lj_cells.argtypes = [P, i64, P, ci, P, P, P]
         L.orc_md_run.restype = ci
         L.orc_md_run.argtypes = [P, i64, P, P, ci, d, ci, ci, ci, P, P]
+        L.orc_rdf.restype = ci
+        L.orc_rdf.argtypes = [P, i64, P, d, ci, P]
+        L.orc_lj_tail.restype = ci
+        L.orc_lj_tail.argtypes = [P, i64, ci, P]
+        L.orc_rescale.restype = ci
+        L.orc_rescale.argtypes = [i64, P, d]
         L.orc_num_threads.restype = ci
         L.orc_num_threads.argtypes = []
         L.orc_sur_basis.restype = None
@@ -222,6 +228,38 @@ def md_run(prm, x, v, nsteps, dt, trav="3c18", trunc="pair", prec="fp64"):
     _check(lib().orc_md_run(_p(prm), n, _p(x), _p(v), nsteps, dt, TRAV[trav], TRUNC[trunc],
                             PREC[prec], _p(f), _p(en)))
     return dict(x=x, v=v, f=f, energies=en)
+
+
+def rdf_counts(prm, x, r_max, nbins):
+    """Pair-distance histogram (every pair once) over [0, r_max) in nbins bins."""
+    x = _soa(x)
+    counts = np.zeros(nbins, dtype=np.uint64)
+    _check(lib().orc_rdf(_p(prm), x.shape[1], _p(x), float(r_max), int(nbins), _p(counts)))
+    return counts
+
+
+def rdf_normalise(counts, samples, n, volume, r_max):
+    """g(r) at the bin centres from pair counts: counts / (samples N/2 rho dV)."""
+    counts = np.asarray(counts, dtype=np.float64)
+    nb = counts.shape[-1]
+    edges = np.linspace(0.0, r_max, nb + 1)
+    shell = 4.0 / 3.0 * np.pi * (edges[1:] ** 3 - edges[:-1] ** 3)
+    rho = n / volume
+    return 0.5 * (edges[1:] + edges[:-1]), counts / (samples * 0.5 * n * rho * shell)
+
+
+def lj_tail(prm, n, intervals=20000):
+    """(E_tail, P_tail) of truncated LJ by quadrature of the tail integrals."""
+    out = np.zeros(2)
+    _check(lib().orc_lj_tail(_p(prm), int(n), int(intervals), _p(out)))
+    return out[0], out[1]
+
+
+def rescale(v, temperature):
+    """Velocities scaled to kinetic temperature ``temperature`` (a copy)."""
+    v = _soa(v).copy()
+    _check(lib().orc_rescale(v.shape[1], _p(v), float(temperature)))
+    return v
 
 
 def num_threads():

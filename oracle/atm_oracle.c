@@ -993,6 +993,112 @@ int orc_lj_cells(const double* prm, int64_t n, const double* x, int prec,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Observables of the validation runs (section 5)                           */
+/* ------------------------------------------------------------------------ */
+
+/* pair-distance histogram behind the radial distribution functions of the
+ * single-phase runs (section 5.1, Fig. rdfs): every pair once (own cell and
+ * the 13 forward neighbour cells), r = sqrt of the FP64 canonical squared
+ * distance, bin floor(r / (r_max / nbins)) for r < r_max; r_max must not
+ * exceed the smallest cell edge, so the cell loop misses no pair            */
+int orc_rdf(const double* prm, int64_t n, const double* x, double rmax, int nbins,
+            uint64_t* counts)
+{
+    if (nbins < 1 || !(rmax > 0.0) || !isfinite(rmax) || !counts) return 1;
+    cells_t c;
+    int st = cells_make(prm, n, x, &c);
+    if (st) return st;
+    const grid_t* g = &c.g;
+    for (int d = 0; d < 3; d++)
+        if (rmax > g->w[d]) {
+            cells_free(&c);
+            return 1;
+        }
+    ev_t ev;
+    ev_init(&ev, &c, ORC_PAIR, ORC_FP64, NULL);
+    const double dr = rmax / (double)nbins, rmax2 = rmax * rmax;
+    int fw13[13][3];
+    forward13(fw13);
+    for (int b = 0; b < nbins; b++) counts[b] = 0;
+    for (int64_t b = 0; b < g->ncell; b++) {
+        int64_t b0 = c.start[b], b1 = c.start[b + 1];
+        for (int q = -1; q < 13; q++) {
+            const int* o = q < 0 ? ZERO3 : fw13[q];
+            int64_t nc = q < 0 ? b : nb_cell(g, b, o);
+            for (int64_t i = b0; i < b1; i++)
+                for (int64_t j = (q < 0 ? i + 1 : c.start[nc]); j < c.start[nc + 1]; j++) {
+                    double d[3];
+                    double a = dsq64(&ev, i, ZERO3, j, o, d);
+                    if (!(a < rmax2)) continue;
+                    int k = (int)(sqrt(a) / dr);
+                    if (k > nbins - 1) k = nbins - 1;
+                    counts[k]++;
+                }
+        }
+    }
+    cells_free(&c);
+    return 0;
+}
+
+/* velocity rescaling for the NVT runs of section 5.1 (no thermostat is
+ * named; reading: the kinetic temperature T = 2K / (3n - 3) is set to the
+ * target by scaling every velocity by one factor): v *= sqrt(T0 / T) */
+int orc_rescale(int64_t n, double* v, double t0)
+{
+    if (n < 0 || !v || !(t0 >= 0.0)) return 1;
+    if (n < 2) return 0;
+    double k = 0.0;
+    for (int64_t i = 0; i < n; i++)
+        for (int d = 0; d < 3; d++) k += 0.5 * v[d * n + i] * v[d * n + i];
+    if (!(k > 0.0)) return 0;
+    double t = 2.0 * k / (3.0 * (double)n - 3.0);
+    double lam = sqrt(t0 / t);
+    for (int64_t i = 0; i < 3 * n; i++) v[i] *= lam;
+    return 0;
+}
+
+/* LJ 12-6 pair energy and its derivative du/dr at distance r */
+static void lj_u_du(double r, double eps, double sig, double* u, double* du)
+{
+    double s6 = pow(sig / r, 6.0), s12 = s6 * s6;
+    *u = 4.0 * eps * (s12 - s6);
+    *du = 4.0 * eps * (-12.0 * s12 + 6.0 * s6) / r;
+}
+
+/* long-range corrections of the truncated LJ pair terms of a homogeneous
+ * fluid (section 5.1 applies them to E2 and P2; g(r) = 1 beyond r_c):
+ *   E_tail = 2 pi N rho  int_{r_c}^inf r^2 u(r) dr
+ *   P_tail = -2/3 pi rho^2 int_{r_c}^inf r^3 u'(r) dr,   rho = N / V,
+ * both integrals taken numerically (composite Simpson, `intervals` even) in
+ * s = r_c / r on (0, 1], where dr = r_c / s^2 ds and both integrands vanish
+ * at s = 0                                                                  */
+int orc_lj_tail(const double* prm, int64_t n, int intervals, double* out)
+{
+    if (n < 0 || intervals < 2 || (intervals & 1) || !out) return 1;
+    const double V = prm[0] * prm[1] * prm[2], rc = prm[3], eps = prm[5], sig = prm[6];
+    if (!(V > 0.0) || !(rc > 0.0) || !(sig > 0.0)) return 1;
+    const double pi = 3.14159265358979323846, rho = (double)n / V;
+    double ie = 0.0, ip = 0.0;
+    for (int k = 0; k <= intervals; k++) {
+        double s = (double)k / intervals, fe = 0.0, fp = 0.0;
+        if (k > 0) {
+            double r = rc / s, u, du, jac = rc / (s * s);
+            lj_u_du(r, eps, sig, &u, &du);
+            fe = r * r * u * jac;
+            fp = r * r * r * du * jac;
+        }
+        double wgt = (k == 0 || k == intervals) ? 1.0 : ((k & 1) ? 4.0 : 2.0);
+        ie += wgt * fe;
+        ip += wgt * fp;
+    }
+    ie *= 1.0 / (3.0 * intervals);
+    ip *= 1.0 / (3.0 * intervals);
+    out[0] = 2.0 * pi * (double)n * rho * ie;
+    out[1] = -2.0 / 3.0 * pi * rho * rho * ip;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Velocity-Verlet NVE (unit mass; the paper's integrator is not named)     */
 /* ------------------------------------------------------------------------ */
 

@@ -105,6 +105,19 @@ int orc_lj_cells(const double* prm, int64_t n, const double* x, int prec,
 int orc_md_run(const double* prm, int64_t n, double* x, double* v, int nsteps, double dt,
                int trav, int trunc, int prec, double* f, double* energies);
 
+/* Pair-distance histogram (every pair once, linked cells, FP64 canonical
+ * distance): counts[nbins], bin floor(r / (r_max / nbins)), r < r_max,
+ * r_max at most the smallest cell edge. */
+int orc_rdf(const double* prm, int64_t n, const double* x, double rmax, int nbins,
+            uint64_t* counts);
+
+/* Velocity rescaling to kinetic temperature t0 (T = 2K / (3n - 3)), in place. */
+int orc_rescale(int64_t n, double* v, double t0);
+
+/* LJ long-range corrections of a homogeneous fluid by numerical quadrature:
+ * out = {E_tail (total), P_tail}. */
+int orc_lj_tail(const double* prm, int64_t n, int intervals, double* out);
+
 /* number of OpenMP threads the oracle uses (1 without OpenMP) */
 int orc_num_threads(void);
 

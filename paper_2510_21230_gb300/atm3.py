@@ -34,7 +34,8 @@ EXPORTED = ["atm_abi_version", "atm_create", "atm_batch_create", "atm_batch_size
             "atm_surrogate_mlp", "atm_surrogate_loss_grad", "atm_surrogate_add_frame",
             "atm_surrogate_add_rows", "atm_surrogate_dataset", "atm_surrogate_clear",
             "atm_surrogate_train", "atm_surrogate_options", "atm_surrogate_error",
-            "atm_measure_fma_peak"]
+            "atm_measure_fma_peak", "atm_rdf_accumulate", "atm_rdf_get", "atm_rdf_reset",
+            "atm_lj_tail", "atm_thermostat"]
 
 SUR_NDESC, SUR_NVEC, SUR_NPARAM = 32, 9, 6467
 
@@ -133,6 +134,11 @@ def load():
         "atm_surrogate_options": [P, i32],
         "atm_surrogate_error": [P, P, P, P, i32],
         "atm_measure_fma_peak": [i32, i32, P],
+        "atm_rdf_accumulate": [P, ctypes.c_double, i32],
+        "atm_rdf_get": [P, P, P],
+        "atm_rdf_reset": [P],
+        "atm_lj_tail": [ctypes.POINTER(Params), i64, P, P],
+        "atm_thermostat": [P, P],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -328,6 +334,25 @@ class AtmSystem:
         self._check(self._lib.atm_density_get(self._ctx, _host_ptr(counts), _host_ptr(samples)))
         return counts, int(samples[0])
 
+    def thermostat(self, temperature):
+        """Rescale velocities so that each replica's kinetic temperature is
+        ``temperature`` (a number or one value per replica)."""
+        t = np.ascontiguousarray(np.broadcast_to(np.asarray(temperature, dtype=np.float64),
+                                                 (self.replicas,)))
+        self._check(self._lib.atm_thermostat(self._ctx, _host_ptr(t)))
+
+    def rdf_accumulate(self, r_max=2.5, nbins=250):
+        self._check(self._lib.atm_rdf_accumulate(self._ctx, float(r_max), int(nbins)))
+
+    def rdf_get(self, nbins):
+        counts = np.zeros((self.replicas, nbins), dtype=np.uint64)
+        samples = np.zeros(1, dtype=np.int64)
+        self._check(self._lib.atm_rdf_get(self._ctx, _host_ptr(counts), _host_ptr(samples)))
+        return counts, int(samples[0])
+
+    def rdf_reset(self):
+        self._check(self._lib.atm_rdf_reset(self._ctx))
+
     def density_reset(self):
         self._check(self._lib.atm_density_reset(self._ctx))
 
@@ -436,6 +461,18 @@ class AtmSystem:
         self._check(self._lib.atm_surrogate_error(self._ctx, ctypes.byref(d), ctypes.byref(e),
                                                 ctypes.byref(k), 1 if reset else 0))
         return d.value, e.value, k.value
+
+
+def lj_tail(box, n, rc=2.5, lj_eps=1.0, lj_sigma=1.0):
+    """Long-range corrections (total energy, pressure) of truncated LJ."""
+    L = load()
+    p = make_params(box, rc=rc, lj_eps=lj_eps, lj_sigma=lj_sigma)
+    e = ctypes.c_double(0.0)
+    pt = ctypes.c_double(0.0)
+    st = L.atm_lj_tail(ctypes.byref(p), int(n), ctypes.byref(e), ctypes.byref(pt))
+    if st != 0:
+        raise AtmError(st, "atm_lj_tail failed")
+    return e.value, pt.value
 
 
 def measure_fma_peak(device=0, fp64=False):

@@ -93,7 +93,8 @@ static void free_all(atm_ctx* c)
     void* dev[] = {c->d_rep, c->d_rep_of_cell, c->d_rep_of_mol, c->x, c->v, c->x0, c->v0, c->xl,
                    c->xl32, c->cell_of, c->rank, c->count, c->start, c->perm, c->cell_sorted,
                    c->f_lj, c->f_atm, c->f_out, c->unit_ew, c->unit_cnt, c->mol_ew, c->mol_cnt,
-                   c->ke, c->d_res, c->d_part, c->d_status, c->d_maxocc, c->d_work, c->d_dens};
+                   c->ke, c->d_res, c->d_part, c->d_status, c->d_maxocc, c->d_work, c->d_dens,
+                   c->d_rdf, c->d_ttarget};
     for (void* p : dev)
         if (p) cudaFree(p);
     if (c->h_res) cudaFreeHost(c->h_res);
@@ -206,6 +207,8 @@ extern "C" atm_status atm_batch_create(const atm_params* params, const int64_t* 
     ok = ok && alloc((void**)&c->d_maxocc, (1 + ATM_NTRAV) * sizeof(int));
     ok = ok && alloc((void**)&c->d_work, sizeof(int));
     ok = ok && alloc((void**)&c->d_dens, (size_t)nrep * DENS_MAX_BINS * sizeof(unsigned long long));
+    ok = ok && alloc((void**)&c->d_rdf, (size_t)nrep * DENS_MAX_BINS * sizeof(unsigned long long));
+    ok = ok && alloc((void**)&c->d_ttarget, nrep * sizeof(double));
     ok = ok && cudaMallocHost((void**)&c->h_res, nrep * sizeof(ResultDev)) == cudaSuccess;
     ok = ok && cudaMallocHost((void**)&c->h_status, sizeof(int)) == cudaSuccess;
     ok = ok && cudaMallocHost((void**)&c->h_maxocc, (1 + ATM_NTRAV) * sizeof(int)) == cudaSuccess;
@@ -229,7 +232,13 @@ extern "C" atm_status atm_batch_create(const atm_params* params, const int64_t* 
     }
     ok = ok && cudaMemsetAsync(c->d_status, 0, sizeof(int), c->st) == cudaSuccess;
     ok = ok && cudaMemsetAsync(c->v, 0, 3 * N * sizeof(double), c->st) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(c->mol_ew, 0, 2 * N * sizeof(double), c->st) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(c->mol_cnt, 0, 2 * N * sizeof(unsigned), c->st) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(c->unit_ew, 0, 2 * NC * sizeof(double), c->st) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(c->unit_cnt, 0, 2 * NC * sizeof(unsigned long long), c->st) ==
+                   cudaSuccess;
     ok = ok && cudaMemsetAsync(c->d_dens, 0, (size_t)nrep * DENS_MAX_BINS * 8, c->st) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(c->d_rdf, 0, (size_t)nrep * DENS_MAX_BINS * 8, c->st) == cudaSuccess;
     ok = ok && cudaStreamSynchronize(c->st) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -823,6 +832,83 @@ extern "C" atm_status atm_density_reset(atm_ctx* c)
     c->dens_samples = 0;
     c->dens_axis = -1;
     c->dens_nbins = 0;
+    return ATM_OK;
+}
+
+extern "C" atm_status atm_thermostat(atm_ctx* c, const double* t_target)
+{
+    if (!c || !t_target) return ATM_E_INVALID;
+    for (int r = 0; r < c->R; r++)
+        if (!(t_target[r] >= 0.0) || !std::isfinite(t_target[r]))
+            return ctx_fail(c, ATM_E_INVALID, "target temperature of replica %d", r);
+    if (!c->have_x) return ctx_fail(c, ATM_E_STATE, "no state set");
+    CU(cudaSetDevice(c->device));
+    CU(cudaMemcpyAsync(c->d_ttarget, t_target, c->R * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    CU(launch_kinetic(c->n, c->v, c->ke, c->st));
+    c->n_launch += 1;
+    atm_status s = enqueue_reduce(c);
+    if (s != ATM_OK) return s;
+    CU(launch_rescale(c->b, c->v, c->ke, c->d_res, c->d_ttarget, c->st));
+    c->n_launch += 1;
+    s = enqueue_reduce(c);
+    if (s != ATM_OK) return s;
+    return ctx_sync_and_check(c);
+}
+
+extern "C" atm_status atm_rdf_accumulate(atm_ctx* c, double r_max, int nbins)
+{
+    if (!c) return ATM_E_INVALID;
+    if (nbins < 1 || nbins > DENS_MAX_BINS || !(r_max > 0.0) || !std::isfinite(r_max))
+        return ctx_fail(c, ATM_E_INVALID, "r_max > 0, 1 <= nbins <= %d", DENS_MAX_BINS);
+    for (const Rep& r : c->reps)
+        for (int d = 0; d < 3; d++)
+            if (r_max > r.g.w[d])
+                return ctx_fail(c, ATM_E_INVALID, "r_max above a cell edge (%g)", r.g.w[d]);
+    if (!c->cells_built) return ctx_fail(c, ATM_E_STATE, "cells not built");
+    if (c->rdf_samples > 0 && (r_max != c->rdf_rmax || nbins != c->rdf_nbins))
+        return ctx_fail(c, ATM_E_STATE, "the RDF accumulator holds another range/bin count; reset it");
+    CU(cudaSetDevice(c->device));
+    CU(launch_rdf(c->b, c->xl, c->start, c->cell_sorted, r_max, nbins, c->d_rdf, c->st));
+    c->n_launch += 1;
+    c->rdf_rmax = r_max;
+    c->rdf_nbins = nbins;
+    c->rdf_samples++;
+    return ATM_OK;
+}
+
+extern "C" atm_status atm_rdf_get(atm_ctx* c, uint64_t* counts, int64_t* samples)
+{
+    if (!c) return ATM_E_INVALID;
+    CU(cudaSetDevice(c->device));
+    if (counts && c->rdf_nbins > 0)
+        CU(cudaMemcpyAsync(counts, c->d_rdf, (size_t)c->R * c->rdf_nbins * sizeof(uint64_t),
+                           cudaMemcpyDeviceToHost, c->st));
+    CU(cudaStreamSynchronize(c->st));
+    if (samples) *samples = c->rdf_samples;
+    return ATM_OK;
+}
+
+extern "C" atm_status atm_rdf_reset(atm_ctx* c)
+{
+    if (!c) return ATM_E_INVALID;
+    CU(cudaSetDevice(c->device));
+    CU(cudaMemsetAsync(c->d_rdf, 0, (size_t)c->R * DENS_MAX_BINS * sizeof(uint64_t), c->st));
+    c->rdf_samples = 0;
+    c->rdf_rmax = 0.0;
+    c->rdf_nbins = 0;
+    return ATM_OK;
+}
+
+extern "C" atm_status atm_lj_tail(const atm_params* p, int64_t n, double* e_tail, double* p_tail)
+{
+    if (!p || n < 0 || !(p->rc > 0.0) || !(p->lj_sigma > 0.0)) return ATM_E_INVALID;
+    const double V = p->box[0] * p->box[1] * p->box[2];
+    if (!(V > 0.0)) return ATM_E_INVALID;
+    const double rho = (double)n / V, pi = 3.14159265358979323846;
+    const double sr3 = std::pow(p->lj_sigma / p->rc, 3.0), sr9 = sr3 * sr3 * sr3;
+    const double s3 = p->lj_sigma * p->lj_sigma * p->lj_sigma;
+    if (e_tail) *e_tail = 8.0 / 3.0 * pi * (double)n * rho * p->lj_eps * s3 * (sr9 / 3.0 - sr3);
+    if (p_tail) *p_tail = 16.0 / 3.0 * pi * rho * rho * p->lj_eps * s3 * (2.0 / 3.0 * sr9 - sr3);
     return ATM_OK;
 }
 

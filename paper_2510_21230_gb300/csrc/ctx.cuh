@@ -54,6 +54,11 @@ struct atm_ctx {
     int* h_maxocc = nullptr;
     int* d_work = nullptr;
     unsigned long long* d_dens = nullptr;  // [R * DENS_MAX_BINS]
+    unsigned long long* d_rdf = nullptr;   // [R * DENS_MAX_BINS]
+    double* d_ttarget = nullptr;           // [R] thermostat temperatures
+    double rdf_rmax = 0.0;
+    int rdf_nbins = 0;
+    long long rdf_samples = 0;
     int dens_axis = -1, dens_nbins = 0;
     long long dens_samples = 0;
     int maxocc = 0;

@@ -317,6 +317,25 @@ __global__ void __launch_bounds__(256) k_kinetic(long long n, const double* __re
     ke[i] = k;
 }
 
+// velocity rescaling thermostat: every velocity of replica r times
+// lambda_r = sqrt(T_r (3 N_r - 3) / (2 K_r)) (K_r from the last reduction;
+// unchanged when K_r = 0 or N_r < 2), kinetic energies times lambda_r^2
+__global__ void __launch_bounds__(256) k_rescale(Batch B, double* __restrict__ v,
+                                                 double* __restrict__ ke,
+                                                 const ResultDev* __restrict__ res,
+                                                 const double* __restrict__ t_target)
+{
+    const long long n = B.ntot;
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int r = B.rep_of_mol[i];
+    const double k = res[r].ekin, dof = 3.0 * (double)B.rep[r].n - 3.0;
+    if (!(k > 0.0) || !(dof > 0.0)) return;
+    const double l2 = t_target[r] * dof / (2.0 * k), l = sqrt(l2);
+    for (int d = 0; d < 3; d++) v[d * n + i] *= l;
+    ke[i] *= l2;
+}
+
 // finiteness check of a state copied from device memory
 __global__ void k_check_finite(long long m, const double* __restrict__ a, int* __restrict__ status)
 {
@@ -336,6 +355,57 @@ __global__ void k_density(Batch B, const double* __restrict__ x, int axis, int n
     int b = (int)floor(x[axis * n + i] / h);
     b = b < 0 ? 0 : (b >= nbins ? nbins - 1 : b);
     atomicAdd(counts + (long long)r * nbins + b, 1ull);
+}
+
+// radial distribution: every pair once (forward half shell of the 27 cells,
+// later molecules of the own cell) with r < r_max, binned by floor(r / dr) in
+// FP64 on the canonical displacement; per-CTA shared histogram of the CTA's
+// first replica (molecules of a second replica go straight to global memory)
+__global__ void __launch_bounds__(128) k_rdf(Batch B, const double* __restrict__ xl,
+                                             const int* __restrict__ start,
+                                             const int* __restrict__ cell_sorted, double rmax,
+                                             int nbins, unsigned long long* __restrict__ counts)
+{
+    extern __shared__ unsigned hist[];
+    typedef LjArith<double> Q;
+    for (int k = threadIdx.x; k < nbins; k += blockDim.x) hist[k] = 0u;
+    __syncthreads();
+    const long long n = B.ntot;
+    const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int r0 = B.rep_of_cell[cell_sorted[blockIdx.x * (long long)blockDim.x]];
+    if (s < n) {
+        const int cg = cell_sorted[s];
+        const int rep = B.rep_of_cell[cg];
+        const Rep& rp = B.rep[rep];
+        const int* st = start + rp.cell0;
+        int cx, cy, cz;
+        cell_coords(rp.g, cg - rp.cell0, cx, cy, cz);
+        const double dr = rmax / (double)nbins, rmax2 = rmax * rmax;
+        const double xs = xl[s], ys = xl[n + s], zs = xl[2 * n + s];
+        for (int t = 13; t < 27; t++) {
+            int dx, dy, dz;
+            offset27(t, dx, dy, dz);
+            const long long nc = cell_at(rp.g, cx, cy, cz, dx, dy, dz);
+            const int q1 = st[nc + 1];
+            const int q0 = t == 13 ? (int)s + 1 : st[nc];
+            const double sx = Q::mul((double)dx, rp.g.w[0]), sy = Q::mul((double)dy, rp.g.w[1]),
+                         sz = Q::mul((double)dz, rp.g.w[2]);
+            for (int q = q0; q < q1; q++) {
+                const double ex = Q::add(Q::sub(xl[q], xs), sx);
+                const double ey = Q::add(Q::sub(xl[n + q], ys), sy);
+                const double ez = Q::add(Q::sub(xl[2 * n + q], zs), sz);
+                const double r2 = Q::add(Q::add(Q::mul(ex, ex), Q::mul(ey, ey)), Q::mul(ez, ez));
+                if (!(r2 < rmax2)) continue;
+                int b = (int)(sqrt(r2) / dr);
+                b = b >= nbins ? nbins - 1 : b;
+                if (rep == r0) atomicAdd(hist + b, 1u);
+                else atomicAdd(counts + (long long)rep * nbins + b, 1ull);
+            }
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < nbins; k += blockDim.x)
+        if (hist[k]) atomicAdd(counts + (long long)r0 * nbins + k, (unsigned long long)hist[k]);
 }
 
 // ---------------------------------------------------------------- reductions
@@ -474,6 +544,14 @@ cudaError_t launch_kick(const Batch& b, const int* perm, const double* f_lj, con
     return cudaGetLastError();
 }
 
+cudaError_t launch_rescale(const Batch& b, double* v, double* ke, const ResultDev* res,
+                           const double* t_target, cudaStream_t st)
+{
+    if (b.ntot <= 0) return cudaSuccess;
+    k_rescale<<<nblk(b.ntot, MD_BLOCK), MD_BLOCK, 0, st>>>(b, v, ke, res, t_target);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_kinetic(long long n, const double* v, double* ke, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
@@ -500,6 +578,15 @@ cudaError_t launch_gather_forces(long long n, const int* perm, const double* f_l
 {
     if (n <= 0) return cudaSuccess;
     k_gather_forces<<<nblk(n, MD_BLOCK), MD_BLOCK, 0, st>>>(n, perm, f_lj, f_atm, which, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rdf(const Batch& b, const double* xl, const int* start, const int* cell_sorted,
+                       double rmax, int nbins, unsigned long long* counts, cudaStream_t st)
+{
+    if (b.ntot <= 0) return cudaSuccess;
+    k_rdf<<<nblk(b.ntot, 128), 128, (size_t)nbins * sizeof(unsigned), st>>>(b, xl, start, cell_sorted,
+                                                                           rmax, nbins, counts);
     return cudaGetLastError();
 }
 

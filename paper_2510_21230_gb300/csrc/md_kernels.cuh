@@ -48,12 +48,20 @@ cudaError_t launch_lj(int prec, const LjArgs<double>& a64, const LjArgs<float>& 
 cudaError_t launch_kick(const Batch& b, const int* perm, const double* f_lj, const double* f_atm,
                         double* x, double* v, int drift, double* ke, cudaStream_t st);
 cudaError_t launch_kinetic(long long n, const double* v, double* ke, cudaStream_t st);
+// v *= sqrt(T_r (3 N_r - 3) / (2 K_r)) per replica (K_r = res[r].ekin)
+cudaError_t launch_rescale(const Batch& b, double* v, double* ke, const ResultDev* res,
+                           const double* t_target, cudaStream_t st);
 cudaError_t launch_check_finite(long long m, const double* a, int* status, cudaStream_t st);
 cudaError_t launch_final_reduce(const ReduceArgs& r, cudaStream_t st);
 cudaError_t launch_gather_forces(long long n, const int* perm, const double* f_lj,
                                  const double* f_atm, int which, double* out, cudaStream_t st);
 // adds the histogram of coordinate `axis` (nbins equal bins over [0, L_axis))
 // of every replica's wrapped positions to counts[R * nbins]
+// adds the pair-distance histogram (nbins equal bins over [0, rmax), every
+// pair once, rmax at most the smallest cell edge) of every replica to
+// counts[R * nbins]
+cudaError_t launch_rdf(const Batch& b, const double* xl, const int* start, const int* cell_sorted,
+                       double rmax, int nbins, unsigned long long* counts, cudaStream_t st);
 cudaError_t launch_density(const Batch& b, const double* x, int axis, int nbins,
                            unsigned long long* counts, cudaStream_t st);
 

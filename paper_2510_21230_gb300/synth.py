@@ -43,6 +43,21 @@ def fcc_positions(n, box, rng, jitter=0.05):
     return np.ascontiguousarray(pts.T)
 
 
+def simple_cubic_positions(n, box, rng):
+    """n molecules on a simple cubic lattice filling a cubic box of edge ``box``
+    (the single-phase start of section 5.1); if n is not m^3, a seeded random
+    subset of the smallest lattice with at least n sites is kept."""
+    m = 1
+    while m ** 3 < n:
+        m += 1
+    g = (np.arange(m, dtype=np.float64) + 0.5) * (box / m)
+    cx, cy, cz = np.meshgrid(g, g, g, indexing="ij")
+    pts = np.stack([cx.ravel(), cy.ravel(), cz.ravel()], axis=1)
+    if pts.shape[0] > n:
+        pts = pts[np.sort(rng.choice(pts.shape[0], size=n, replace=False))]
+    return np.ascontiguousarray(pts.T)
+
+
 def uniform_positions(n, box, rng):
     box = np.broadcast_to(np.asarray(box, dtype=np.float64), (3,))
     return np.ascontiguousarray((rng.random((n, 3)) * box).T)

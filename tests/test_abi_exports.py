@@ -47,3 +47,19 @@ def test_invalid_arguments_are_rejected_without_a_gpu():
     assert lib.atm_create(ctypes.byref(p), 10, ctypes.byref(ctx)) == 1
     assert lib.atm_destroy(None) == 0
     assert lib.atm_compute_forces(None, 0, 0, 0, None) == 1
+
+
+@pytest.mark.parametrize("rc,rho,eps,sig", [(2.5, 0.8, 1.0, 1.0), (3.0, 0.65, 1.0, 1.0),
+                                            (5.0, 0.1, 2.0, 1.7)])
+def test_lj_tail_matches_the_oracle_quadrature(rc, rho, eps, sig):
+    """atm_lj_tail is host arithmetic: checked here against the oracle's
+    numerical tail integrals."""
+    import oracle
+    n = 2000
+    box = (n / rho) ** (1.0 / 3.0)
+    e, p = atm3.lj_tail(box, n, rc=rc, lj_eps=eps, lj_sigma=sig)
+    eo, po = oracle.lj_tail(oracle.params(box, rc, 0.0, lj_eps=eps, lj_sigma=sig), n)
+    assert e == pytest.approx(eo, rel=1e-11)
+    assert p == pytest.approx(po, rel=1e-11)
+    with pytest.raises(atm3.AtmError):
+        atm3.lj_tail(box, n, rc=0.0)

@@ -483,3 +483,108 @@ def test_wide_traversal_needs_five_cells():
     prm = oracle.params(cfg["box"], 2.5, 0.073)
     with pytest.raises(oracle.OracleError):
         oracle.atm_cells(prm, cfg["x"], "3cw", "product", "fp64")
+
+
+# ---------------------------------------------------------------- observables
+
+def _minimum_image_histogram(box, x, r_max, nbins):
+    """All pairs, minimum image, numpy distances: an independent histogram."""
+    L = np.asarray(box, dtype=np.float64)[:, None, None]
+    d = x[:, None, :] - x[:, :, None]
+    d -= L * np.round(d / L)
+    r = np.sqrt((d * d).sum(axis=0))
+    iu = np.triu_indices(x.shape[1], 1)
+    r = r[iu]
+    r = r[r < r_max]
+    return np.bincount(np.minimum((r / (r_max / nbins)).astype(np.int64), nbins - 1),
+                       minlength=nbins)
+
+
+@pytest.mark.parametrize("box,n,seed", [((9.0, 10.0, 11.5), 700, 61), ((7.6, 7.6, 15.2), 450, 62)])
+def test_rdf_histogram_equals_all_pairs_minimum_image(box, n, seed):
+    """Section 5.1 RDFs: the linked-cell pair histogram holds every pair within
+    r_max exactly once (against an all-pairs minimum-image count)."""
+    rng = np.random.default_rng(seed)
+    x = synth.uniform_positions(n, box, rng)
+    prm = oracle.params(box, 2.5, NU)
+    _, w = oracle.cell_grid(prm)
+    r_max = float(min(w))
+    got = oracle.rdf_counts(prm, x, r_max, 40)
+    ref = _minimum_image_histogram(box, x, r_max, 40)
+    assert np.array_equal(got.astype(np.int64), ref)
+
+
+def test_rdf_of_a_simple_cubic_lattice_counts_its_coordination_shells():
+    """Simple cubic lattice of spacing 1: shells at 1, sqrt2, sqrt3, 2, sqrt5,
+    sqrt6 hold 6, 12, 8, 6, 24, 24 neighbours per site, each pair counted once."""
+    m = 8
+    g = np.arange(m, dtype=np.float64) + 0.25
+    cx, cy, cz = np.meshgrid(g, g, g, indexing="ij")
+    x = np.ascontiguousarray(np.stack([cx.ravel(), cy.ravel(), cz.ravel()]))
+    prm = oracle.params(float(m), 2.5, NU)
+    r_max, nbins = 2.55, 17
+    got = oracle.rdf_counts(prm, x, r_max, nbins).astype(np.int64)
+    ref = np.zeros(nbins, dtype=np.int64)
+    for r2, z in ((1, 6), (2, 12), (3, 8), (4, 6), (5, 24), (6, 24)):
+        ref[int(math.sqrt(r2) / (r_max / nbins))] += m ** 3 * z // 2
+    assert np.array_equal(got, ref)
+
+
+def test_rdf_of_an_ideal_gas_is_one():
+    """Uniform random positions: g(r) = 1 within counting noise."""
+    rng = np.random.default_rng(63)
+    box = 20.0
+    n = 4000
+    x = synth.uniform_positions(n, box, rng)
+    prm = oracle.params(box, 2.5, NU)
+    counts = oracle.rdf_counts(prm, x, 2.5, 10)
+    r, g = oracle.rdf_normalise(counts, 1, n, box ** 3, 2.5)
+    assert r[0] == pytest.approx(0.125)
+    sigma = 1.0 / np.sqrt(np.maximum(counts, 1))
+    assert np.all(np.abs(g[2:] - 1.0) < 5 * sigma[2:])
+
+
+def test_rdf_rejects_a_range_beyond_the_cell_edge():
+    prm = oracle.params(10.0, 2.5, NU)
+    x = synth.uniform_positions(50, 10.0, np.random.default_rng(64))
+    with pytest.raises(oracle.OracleError):
+        oracle.rdf_counts(prm, x, 3.4, 10)
+
+
+@pytest.mark.parametrize("rc,rho", [(2.5, 0.8), (3.0, 0.65), (2.0, 0.3)])
+def test_lj_tail_corrections_equal_the_closed_forms(rc, rho):
+    """Tail integrals of the LJ 12-6 pair potential (homogeneous fluid, g = 1
+    beyond r_c): E_tail / N = 8/3 pi rho [(1/3) rc^-9 - rc^-3] and
+    P_tail = 16/3 pi rho^2 [(2/3) rc^-9 - rc^-3] in reduced units."""
+    n = 1000
+    box = (n / rho) ** (1.0 / 3.0)
+    e, p = oracle.lj_tail(oracle.params(box, rc, NU), n)
+    assert e / n == pytest.approx(8 / 3 * math.pi * rho * (rc ** -9 / 3 - rc ** -3), rel=1e-11)
+    assert p == pytest.approx(16 / 3 * math.pi * rho ** 2 * (2 / 3 * rc ** -9 - rc ** -3), rel=1e-11)
+
+
+def test_lj_tail_scales_with_epsilon_and_sigma():
+    """u = 4 eps [(s/r)^12 - (s/r)^6]: E_tail is linear in eps and, at fixed
+    r_c / sigma and rho sigma^3, scales as eps (dimensionless form)."""
+    base = oracle.lj_tail(oracle.params(10.0, 2.5, NU), 800)
+    scaled = oracle.lj_tail(oracle.params(20.0, 5.0, NU, lj_eps=3.0, lj_sigma=2.0), 800)
+    assert scaled[0] == pytest.approx(3.0 * base[0], rel=1e-12)
+    assert scaled[1] == pytest.approx(3.0 / 8.0 * base[1], rel=1e-12)
+
+
+def test_velocity_rescaling_sets_the_kinetic_temperature():
+    """NVT by velocity rescaling: afterwards 2K / (3n - 3) equals the target,
+    every velocity keeps its direction, the total momentum stays zero, and a
+    resting system (K = 0) is left alone."""
+    rng = np.random.default_rng(65)
+    n = 500
+    v = synth.maxwell_boltzmann(n, 1.7, rng)
+    w = oracle.rescale(v, 0.746)
+    k = 0.5 * (w * w).sum()
+    assert 2.0 * k / (3 * n - 3) == pytest.approx(0.746, rel=1e-13)
+    ratio = w / v
+    assert np.allclose(ratio, ratio.flat[0], rtol=1e-14)
+    assert ratio.flat[0] == pytest.approx(math.sqrt(0.746 / 1.7), rel=1e-12)
+    assert np.abs(w.sum(axis=1)).max() < 1e-10
+    z = np.zeros((3, n))
+    assert np.array_equal(oracle.rescale(z, 1.0), z)
