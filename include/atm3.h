@@ -64,7 +64,15 @@ typedef enum {
  *        R_w -- and so measures what the paper's traversals miss.  Needs 5
  *        cells per axis (BOX_TOO_SMALL otherwise).  n_cand3 counts the
  *        partner pairs of every owner, n_int3 the owner visits. */
-typedef enum { ATM_3C01 = 0, ATM_3C18 = 1, ATM_3C08 = 2, ATM_3CW = 3 } atm_traversal;
+/*  3C08A: the 3c08 of the paper's text (section 4, Fig. c08traversal): the
+ *        procedure of 3C18 with the partners of the base cell restricted to
+ *        the other 7 cells of the 2x2x2 block in front of it, so every task
+ *        holds the block's corner cell (1 + 14 + 21 tasks per block).  A
+ *        triplet whose cells form a block triple without its corner cell
+ *        (e.g. the three face neighbours of a cell) is never visited: these
+ *        are interactions the paper says 3c08 omits.  Newton-3, same units
+ *        and launch plans as 3C08. */
+typedef enum { ATM_3C01 = 0, ATM_3C18 = 1, ATM_3C08 = 2, ATM_3CW = 3, ATM_3C08A = 4 } atm_traversal;
 
 /* Truncation conditions (paper section 2).  A triplet interacts iff
  *  PAIR:    r_ij < r_c and r_ik < r_c and r_jk < r_c;

@@ -20,7 +20,7 @@ _SRCS = [os.path.join(_HERE, "atm_oracle.c"), os.path.join(_HERE, "sur_oracle.c"
 _HDRS = [os.path.join(_HERE, "atm_oracle.h"), os.path.join(_HERE, "sur_oracle.h")]
 _LIB = os.path.join(_HERE, "libatm_oracle.so")
 
-TRAV = {"3c01": 0, "3c18": 1, "3c08": 2, "3cw": 3}
+TRAV = {"3c01": 0, "3c18": 1, "3c08": 2, "3cw": 3, "3c08a": 4}
 TRUNC = {"pair": 0, "product": 1}
 PREC = {"fp64": 0, "fp32": 1}
 

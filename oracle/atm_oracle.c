@@ -526,15 +526,13 @@ static void unit_3cw(ev_t* ev, int64_t b, int64_t* plist, int* poff)
     }
 }
 
-/* ---- 3c18: base cell, its 13 forward neighbours and every pair of them
- *      (Algorithm 1 with forward neighbours only, section 4) ------------ */
-static void unit_3c18(ev_t* ev, int64_t b)
+/* ---- every task holds the base cell: <C_b>, <C_b, C_n1> and
+ *      <C_b, C_n1, C_n2> with C_n1 before C_n2 in the partner list -------- */
+static void unit_based(ev_t* ev, int64_t b, const int (*po)[3], int np)
 {
     const cells_t* c = ev->c;
-    int fw[13][3];
-    forward13(fw);
     int64_t cid[13];
-    for (int q = 0; q < 13; q++) cid[q] = nb_cell(&c->g, b, fw[q]);
+    for (int q = 0; q < np; q++) cid[q] = nb_cell(&c->g, b, po[q]);
     int64_t b0 = c->start[b], b1 = c->start[b + 1];
     /* <C_b>: i < j < k inside the base cell */
     for (int64_t i = b0; i < b1; i++)
@@ -545,40 +543,67 @@ static void unit_3c18(ev_t* ev, int64_t b)
                 else ev->ncand++;
             }
         }
-    for (int q = 0; q < 13; q++) {
+    for (int q = 0; q < np; q++) {
         int64_t n0 = c->start[cid[q]], n1 = c->start[cid[q] + 1];
         /* <C_b, C_n1>: two in C_b and one in C_n1, then one in C_b and two in C_n1 */
         for (int64_t i = b0; i < b1; i++)
             for (int64_t j = i + 1; j < b1; j++) {
                 int pj = side_ok(ev, i, ZERO3, j, ZERO3);
                 for (int64_t k = n0; k < n1; k++) {
-                    if (pj) triplet(ev, i, ZERO3, j, ZERO3, k, fw[q], 0);
+                    if (pj) triplet(ev, i, ZERO3, j, ZERO3, k, po[q], 0);
                     else ev->ncand++;
                 }
             }
         for (int64_t i = b0; i < b1; i++)
             for (int64_t j = n0; j < n1; j++) {
-                int pj = side_ok(ev, i, ZERO3, j, fw[q]);
+                int pj = side_ok(ev, i, ZERO3, j, po[q]);
                 for (int64_t k = j + 1; k < n1; k++) {
-                    if (pj) triplet(ev, i, ZERO3, j, fw[q], k, fw[q], 0);
+                    if (pj) triplet(ev, i, ZERO3, j, po[q], k, po[q], 0);
                     else ev->ncand++;
                 }
             }
     }
-    /* <C_b, C_n1, C_n2>: C_n2 after C_n1 in the forward list */
-    for (int q1 = 0; q1 < 13; q1++)
-        for (int q2 = q1 + 1; q2 < 13; q2++) {
+    /* <C_b, C_n1, C_n2>: C_n2 after C_n1 in the partner list */
+    for (int q1 = 0; q1 < np; q1++)
+        for (int q2 = q1 + 1; q2 < np; q2++) {
             int64_t j0 = c->start[cid[q1]], j1 = c->start[cid[q1] + 1];
             int64_t k0 = c->start[cid[q2]], k1 = c->start[cid[q2] + 1];
             for (int64_t i = b0; i < b1; i++)
                 for (int64_t j = j0; j < j1; j++) {
-                    int pj = side_ok(ev, i, ZERO3, j, fw[q1]);
+                    int pj = side_ok(ev, i, ZERO3, j, po[q1]);
                     for (int64_t k = k0; k < k1; k++) {
-                        if (pj) triplet(ev, i, ZERO3, j, fw[q1], k, fw[q2], 0);
+                        if (pj) triplet(ev, i, ZERO3, j, po[q1], k, po[q2], 0);
                         else ev->ncand++;
                     }
                 }
         }
+}
+
+/* ---- 3c18: base cell, its 13 forward neighbours and every pair of them
+ *      (Algorithm 1 with forward neighbours only, section 4) ------------ */
+static void unit_3c18(ev_t* ev, int64_t b)
+{
+    int fw[13][3];
+    forward13(fw);
+    unit_based(ev, b, (const int (*)[3])fw, 13);
+}
+
+/* ---- 3c08 as the text describes it (section 4, Fig. c08traversal): the
+ *      procedure of 3c18 with the partners restricted to the 2x2x2 block in
+ *      front of the base cell (offsets in {0,1}^3 other than 0, in slot
+ *      order x + 2y + 4z), so every task holds the block's corner cell.  A
+ *      cell triple of the block that misses the corner (e.g. the three
+ *      face neighbours of the corner) belongs to no task: the omitted
+ *      interactions the paper mentions. ------------------------------------ */
+static void unit_3c08a(ev_t* ev, int64_t b)
+{
+    int blk[7][3];
+    for (int s = 1; s < 8; s++) {
+        blk[s - 1][0] = s & 1;
+        blk[s - 1][1] = (s >> 1) & 1;
+        blk[s - 1][2] = (s >> 2) & 1;
+    }
+    unit_based(ev, b, (const int (*)[3])blk, 7);
 }
 
 /* ---- 3c08: the 2x2x2 block anchored at the base cell; every cell multiset
@@ -647,7 +672,7 @@ static int atm_cells_impl(const double* prm, int64_t n, const double* x, int tra
                           int prec, int64_t unit_lo, int64_t unit_hi, const int64_t* units,
                           int64_t nunits, double* f, double* ew, uint64_t* cnt)
 {
-    if (trav < 0 || trav > 3 || trunc < 0 || trunc > 1 || prec < 0 || prec > 1) return 1;
+    if (trav < 0 || trav > 4 || trunc < 0 || trunc > 1 || prec < 0 || prec > 1) return 1;
     cells_t c;
     int st = cells_make(prm, n, x, &c);
     if (st) return st;
@@ -682,6 +707,7 @@ static int atm_cells_impl(const double* prm, int64_t n, const double* x, int tra
             if (trav == ORC_3C01) unit_3c01(&ev, u);
             else if (trav == ORC_3C18) unit_3c18(&ev, u);
             else if (trav == ORC_3C08) unit_3c08(&ev, u);
+            else if (trav == ORC_3C08A) unit_3c08a(&ev, u);
             else unit_3cw(&ev, u, plist, poff);
         }
         free(plist);
@@ -810,6 +836,31 @@ static int member_3c08(const grid_t* g, int32_t ci, int32_t cj, int32_t ck)
     return 1;
 }
 
+/* the corner-anchored 3c08 visits a cell multiset iff it fits in one 2x2x2
+ * block and that block's corner (the smallest coordinate along every axis,
+ * cyclically) is one of its cells */
+static int member_3c08a(const grid_t* g, int32_t ci, int32_t cj, int32_t ck)
+{
+    if (!member_3c08(g, ci, cj, ck)) return 0;
+    int32_t cs[3] = {ci, cj, ck};
+    int v[3][3], lo[3];
+    for (int m = 0; m < 3; m++) {
+        v[m][0] = cs[m] % g->nc[0];
+        v[m][1] = (cs[m] / g->nc[0]) % g->nc[1];
+        v[m][2] = cs[m] / (g->nc[0] * g->nc[1]);
+    }
+    for (int d = 0; d < 3; d++) {
+        /* two distinct values are cyclic neighbours: the lower one is the one
+         * whose successor is the other */
+        lo[d] = v[0][d];
+        for (int m = 1; m < 3; m++)
+            if (v[m][d] != lo[d] && (v[m][d] + 1) % g->nc[d] == lo[d]) lo[d] = v[m][d];
+    }
+    for (int m = 0; m < 3; m++)
+        if (v[m][0] == lo[0] && v[m][1] == lo[1] && v[m][2] == lo[2]) return 1;
+    return 0;
+}
+
 static int bf_keep(double rc2, double rc6, int trunc, double a, double b, double c)
 {
     if (trunc == ORC_PAIR) return a < rc2 && b < rc2 && c < rc2;
@@ -823,7 +874,7 @@ static int bf_keep(double rc2, double rc6, int trunc, double a, double b, double
 int orc_atm_brute(const double* prm, int64_t n, const double* x, int trunc, int member,
                   double* f, double* ew, uint64_t* cnt)
 {
-    if (trunc < 0 || trunc > 1 || member < -1 || member > 3) return 1;
+    if (trunc < 0 || trunc > 1 || member < -1 || member > 4) return 1;
     cells_t c;
     int st = cells_make(prm, n, x, &c);
     if (st) return st;
@@ -849,6 +900,8 @@ int orc_atm_brute(const double* prm, int64_t n, const double* x, int trunc, int 
                     if (!member_3c18(g, c.cell[i], c.cell[j], c.cell[k])) continue;
                 } else if (member == ORC_3C08) {
                     if (!member_3c08(g, c.cell[i], c.cell[j], c.cell[k])) continue;
+                } else if (member == ORC_3C08A) {
+                    if (!member_3c08a(g, c.cell[i], c.cell[j], c.cell[k])) continue;
                 }
                 double dij[3], dik[3], djk[3];
                 double a = bf_dsq(c.xw, n, g->L, i, j, dij);

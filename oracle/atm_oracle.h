@@ -30,7 +30,7 @@ extern "C" {
 #endif
 
 /* traversal, truncation and precision selectors */
-enum { ORC_3C01 = 0, ORC_3C18 = 1, ORC_3C08 = 2, ORC_3CW = 3 };
+enum { ORC_3C01 = 0, ORC_3C18 = 1, ORC_3C08 = 2, ORC_3CW = 3, ORC_3C08A = 4 };
 enum { ORC_PAIR = 0, ORC_PRODUCT = 1 };
 enum { ORC_FP64 = 0, ORC_FP32 = 1 };
 /* brute-force membership filters: all triples, or the triples a traversal visits */

@@ -14,7 +14,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libatm3.so")
 
-TRAVERSALS = {"3c01": 0, "3c18": 1, "3c08": 2, "3cw": 3}
+TRAVERSALS = {"3c01": 0, "3c18": 1, "3c08": 2, "3cw": 3, "3c08a": 4}
 TRUNCATIONS = {"pair": 0, "product": 1}
 PRECISIONS = {"fp64": 0, "fp32c": 1, "surrogate": 2}
 FORCES = {"total": 0, "lj": 1, "atm": 2}

@@ -5,7 +5,7 @@
 
 namespace atm3 {
 
-constexpr int ATM_NTRAV = 4;  // 3c01, 3c18, 3c08, 3cw
+constexpr int ATM_NTRAV = 5;  // 3c01, 3c18, 3c08, 3cw, corner-anchored 3c08
 
 // device status word bits (set by kernels, read back by the host)
 enum : int {
@@ -83,7 +83,8 @@ __host__ __device__ __forceinline__ void offset27(int t, int& dx, int& dy, int& 
 //  3cw:  slot 0 = base, then the other 124 cells of the 5^3 neighbourhood in
 //        linear order ((dz, dy, dx) in -2..2).
 //  3c18: slot 0 = base, slots 1..13 = forward neighbours in lexicographic order.
-//  3c08: slot s = offset (s & 1, s >> 1 & 1, s >> 2 & 1) inside the 2x2x2 block.
+//  3c08 and the corner-anchored 3c08: slot s = offset (s & 1, s >> 1 & 1,
+//        s >> 2 & 1) inside the 2x2x2 block.
 template <int TRAV>
 __host__ __device__ __forceinline__ void slot_offset(int s, int& dx, int& dy, int& dz)
 {
@@ -121,6 +122,10 @@ struct Trav<2> {
 template <>
 struct Trav<3> {
     static constexpr int S = 125;
+};
+template <>
+struct Trav<4> {
+    static constexpr int S = 8;
 };
 
 // Arguments of the ATM unit kernels.

@@ -1,7 +1,9 @@
 // atm_block.cuh -- Newton-3 traversals 3c18 and 3c08 (section 4).
 //
 // One CTA per unit: the base cell with its 13 forward neighbours (3c18) or
-// the 2x2x2 block anchored at the base cell (3c08).  The unit's M molecules
+// the 2x2x2 block anchored at the base cell (3c08, and TRAV 4, the
+// corner-anchored 3c08 whose tasks all hold the base cell: the 3c18 procedure
+// over the block's 7 other cells).  The unit's M molecules
 // are staged in shared memory in slot order, so a triplet p < q < r of staged
 // indices lists its cells in the order the traversal's tasks do.  Each staged
 // molecule carries its exact base-frame shift o*w, so the canonical

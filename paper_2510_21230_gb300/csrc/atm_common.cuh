@@ -142,7 +142,8 @@ __device__ inline unsigned long long unit_candidates(const int* beg)
     if (TRAV == 0) {
         unsigned long long M = (unsigned long long)beg[S];
         cand = M > 0 ? N[0] * C2(M - 1) : 0ull;
-    } else if (TRAV == 1) {
+    } else if (TRAV == 1 || TRAV == 4) {
+        // every task holds the base cell (slot 0): <b>, <b, s>, <b, s, t>
         unsigned long long sum1 = 0, sum2 = 0;
         cand = C3(N[0]);
         for (int s = 1; s < S; s++) {

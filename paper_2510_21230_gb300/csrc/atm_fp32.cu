@@ -1,5 +1,5 @@
 // FP32 instantiations of the ATM triplet kernels (3c01 and 3cw owner kernel,
-// 3c18 / 3c08 block kernel).
+// 3c18 / 3c08 / corner-anchored 3c08 block kernel).
 #include "atm_block.cuh"
 #include "atm_owner.cuh"
 
@@ -19,7 +19,9 @@ cudaError_t launch_atm_fp32(int trav, int trunc, const AtmArgs<float>& a, int nw
     else if (trav == 1 && trunc == 0) atm_block_kernel<1, 0, float><<<grid, block, smem, s>>>(a);
     else if (trav == 1 && trunc == 1) atm_block_kernel<1, 1, float><<<grid, block, smem, s>>>(a);
     else if (trav == 2 && trunc == 0) atm_block_kernel<2, 0, float><<<grid, block, smem, s>>>(a);
+    else if (trav == 4 && trunc == 0) atm_block_kernel<4, 0, float><<<grid, block, smem, s>>>(a);
     else if (trav == 2 && trunc == 1) atm_block_kernel<2, 1, float><<<grid, block, smem, s>>>(a);
+    else if (trav == 4 && trunc == 1) atm_block_kernel<4, 1, float><<<grid, block, smem, s>>>(a);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
@@ -34,7 +36,9 @@ cudaError_t atm_attr_fp32(int trav, int trunc, size_t smem)
     if (trav == 1 && trunc == 0) return cudaFuncSetAttribute(atm_block_kernel<1, 0, float>, A, (int)smem);
     if (trav == 1 && trunc == 1) return cudaFuncSetAttribute(atm_block_kernel<1, 1, float>, A, (int)smem);
     if (trav == 2 && trunc == 0) return cudaFuncSetAttribute(atm_block_kernel<2, 0, float>, A, (int)smem);
+    if (trav == 4 && trunc == 0) return cudaFuncSetAttribute(atm_block_kernel<4, 0, float>, A, (int)smem);
     if (trav == 2 && trunc == 1) return cudaFuncSetAttribute(atm_block_kernel<2, 1, float>, A, (int)smem);
+    if (trav == 4 && trunc == 1) return cudaFuncSetAttribute(atm_block_kernel<4, 1, float>, A, (int)smem);
     return cudaErrorInvalidValue;
 }
 
@@ -50,7 +54,9 @@ int atm_occupancy_fp32(int trav, int trunc, int nwarps, size_t smem)
     else if (trav == 1 && trunc == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, atm_block_kernel<1, 0, float>, bs, smem);
     else if (trav == 1 && trunc == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, atm_block_kernel<1, 1, float>, bs, smem);
     else if (trav == 2 && trunc == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, atm_block_kernel<2, 0, float>, bs, smem);
+    else if (trav == 4 && trunc == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, atm_block_kernel<4, 0, float>, bs, smem);
     else if (trav == 2 && trunc == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, atm_block_kernel<2, 1, float>, bs, smem);
+    else if (trav == 4 && trunc == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, atm_block_kernel<4, 1, float>, bs, smem);
     return nb;
 }
 

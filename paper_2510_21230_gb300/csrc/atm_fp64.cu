@@ -1,5 +1,5 @@
 // FP64 instantiations of the ATM triplet kernels (3c01 owner kernel,
-// 3c18 / 3c08 block kernel).
+// 3c18 / 3c08 / corner-anchored 3c08 block kernel).
 #include "atm_block.cuh"
 #include "atm_owner.cuh"
 
@@ -19,7 +19,9 @@ cudaError_t launch_atm_fp64(int trav, int trunc, const AtmArgs<double>& a, int n
     else if (trav == 1 && trunc == 0) atm_block_kernel<1, 0, double><<<grid, block, smem, s>>>(a);
     else if (trav == 1 && trunc == 1) atm_block_kernel<1, 1, double><<<grid, block, smem, s>>>(a);
     else if (trav == 2 && trunc == 0) atm_block_kernel<2, 0, double><<<grid, block, smem, s>>>(a);
+    else if (trav == 4 && trunc == 0) atm_block_kernel<4, 0, double><<<grid, block, smem, s>>>(a);
     else if (trav == 2 && trunc == 1) atm_block_kernel<2, 1, double><<<grid, block, smem, s>>>(a);
+    else if (trav == 4 && trunc == 1) atm_block_kernel<4, 1, double><<<grid, block, smem, s>>>(a);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
@@ -34,7 +36,9 @@ cudaError_t atm_attr_fp64(int trav, int trunc, size_t smem)
     if (trav == 1 && trunc == 0) return cudaFuncSetAttribute(atm_block_kernel<1, 0, double>, A, (int)smem);
     if (trav == 1 && trunc == 1) return cudaFuncSetAttribute(atm_block_kernel<1, 1, double>, A, (int)smem);
     if (trav == 2 && trunc == 0) return cudaFuncSetAttribute(atm_block_kernel<2, 0, double>, A, (int)smem);
+    if (trav == 4 && trunc == 0) return cudaFuncSetAttribute(atm_block_kernel<4, 0, double>, A, (int)smem);
     if (trav == 2 && trunc == 1) return cudaFuncSetAttribute(atm_block_kernel<2, 1, double>, A, (int)smem);
+    if (trav == 4 && trunc == 1) return cudaFuncSetAttribute(atm_block_kernel<4, 1, double>, A, (int)smem);
     return cudaErrorInvalidValue;
 }
 
@@ -50,7 +54,9 @@ int atm_occupancy_fp64(int trav, int trunc, int nwarps, size_t smem)
     else if (trav == 1 && trunc == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, atm_block_kernel<1, 0, double>, bs, smem);
     else if (trav == 1 && trunc == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, atm_block_kernel<1, 1, double>, bs, smem);
     else if (trav == 2 && trunc == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, atm_block_kernel<2, 0, double>, bs, smem);
+    else if (trav == 4 && trunc == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, atm_block_kernel<4, 0, double>, bs, smem);
     else if (trav == 2 && trunc == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, atm_block_kernel<2, 1, double>, bs, smem);
+    else if (trav == 4 && trunc == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, atm_block_kernel<4, 1, double>, bs, smem);
     return nb;
 }
 

@@ -497,7 +497,7 @@ static void copy_result(const ResultDev& r, atm_result* out)
 
 static bool valid_enums(int trav, int trunc, int prec)
 {
-    return trav >= 0 && trav <= 3 && trunc >= 0 && trunc <= 1 && prec >= 0 && prec <= 2;
+    return trav >= 0 && trav <= 4 && trunc >= 0 && trunc <= 1 && prec >= 0 && prec <= 2;
 }
 
 extern "C" atm_status atm_compute_forces(atm_ctx* c, atm_traversal trav, atm_truncation trunc,

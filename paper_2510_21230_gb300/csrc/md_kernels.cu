@@ -136,6 +136,7 @@ __global__ void k_unit_max(Batch B, const int* __restrict__ start, int* __restri
         atomicMax(out + 1, m18);
         atomicMax(out + 2, m08);
         atomicMax(out + 3, mw);
+        atomicMax(out + 4, m08);  // the corner-anchored 3c08 stages the same blocks
     }
 }
 

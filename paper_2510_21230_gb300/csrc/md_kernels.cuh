@@ -39,7 +39,8 @@ constexpr int REDUCE_PARTS = 64;  // partial sums per replica of the two-level r
 constexpr int LJ_BLOCK = 128;
 constexpr int MD_BLOCK = 256;
 
-// maxocc[0] = largest cell occupancy, maxocc[1..4] = largest unit of 3c01, 3c18, 3c08, 3cw
+// maxocc[0] = largest cell occupancy, maxocc[1..5] = largest unit of 3c01, 3c18, 3c08, 3cw,
+// corner-anchored 3c08
 cudaError_t launch_build_cells(const Batch& b, double* x, int* cell_of, int* rank, int* count,
                                int* start, int* perm, double* xl, float* xl32, int* cell_sorted,
                                int* maxocc, int* status, cudaStream_t st);

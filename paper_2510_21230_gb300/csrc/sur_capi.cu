@@ -566,7 +566,7 @@ extern "C" atm_status atm_surrogate_add_frame(atm_ctx* c, atm_traversal trav, at
                                               atm_precision prec)
 {
     if (!c) return ATM_E_INVALID;
-    if (trav < 0 || trav > 3 || trunc < 0 || trunc > 1 || prec < 0 || prec > 1)
+    if (trav < 0 || trav > 4 || trunc < 0 || trunc > 1 || prec < 0 || prec > 1)
         return ctx_fail(c, ATM_E_INVALID, "add_frame needs an exact traversal, truncation, precision");
     if (!c->cells_built) return ctx_fail(c, ATM_E_STATE, "cells not built");
     SurState* S = state(c);

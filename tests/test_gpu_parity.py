@@ -90,7 +90,7 @@ def test_cells_bit_exact(atm3, maker):
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32c"])
 @pytest.mark.parametrize("trunc", ["pair", "product"])
-@pytest.mark.parametrize("trav", ["3c01", "3c18", "3c08"])
+@pytest.mark.parametrize("trav", ["3c01", "3c18", "3c08", "3c08a"])
 def test_atm_parity_small_liquid(atm3, trav, trunc, prec):
     cfg = small_liquid()
     prm = oracle.params(cfg["box"], 2.5, NU)
@@ -142,14 +142,14 @@ def test_empty_and_tiny_systems(atm3):
         with atm3.AtmSystem(box, n) as s:
             s.set_state(x)
             s.build_cells()
-            for trav in ["3c01", "3c18", "3c08"]:
+            for trav in ["3c01", "3c18", "3c08", "3c08a"]:
                 r = s.compute_forces(trav, "product", "fp64")
                 ref = oracle.atm_cells(oracle.params(box, 2.5, NU), x, trav, "product")
                 assert r["n_int3"] == ref["n_int3"] and r["n_cand3"] == ref["n_cand3"]
                 assert r["e3"] == pytest.approx(ref["e3"], rel=1e-12, abs=1e-300)
 
 
-@pytest.mark.parametrize("trav", ["3c01", "3c18", "3c08"])
+@pytest.mark.parametrize("trav", ["3c01", "3c18", "3c08", "3c08a"])
 def test_crowded_cell_and_ragged_occupancy(atm3, trav):
     """One cell holds far more molecules than the rest (ragged staging tails)."""
     rng = np.random.default_rng(9)
@@ -186,7 +186,7 @@ def test_call_order_is_checked(atm3):
 # ------------------------------------------------------------------ medium size: many units, ragged tails
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32c"])
-@pytest.mark.parametrize("trav", ["3c18", "3c08"])
+@pytest.mark.parametrize("trav", ["3c18", "3c08", "3c08a"])
 def test_atm_parity_32k_pair(atm3, trav, prec):
     cfg = synth.homogeneous(32000, 0.8, 1.0, seed=2000)
     prm = oracle.params(cfg["box"], 2.5, NU)
@@ -241,7 +241,7 @@ def test_full_size_256k_sampled(atm3, trav, prec):
 
 # ------------------------------------------------------------------ capacity fallbacks
 
-@pytest.mark.parametrize("trav", ["3c18", "3c08"])
+@pytest.mark.parametrize("trav", ["3c18", "3c08", "3c08a"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32c"])
 def test_large_units_product_rule(atm3, trav, prec):
     """Units too large for the dense pair tables (N = 1500 in a 4-cell box,
@@ -255,7 +255,7 @@ def test_large_units_product_rule(atm3, trav, prec):
     assert_forces_close(f, ref["f"], RTOL[prec], "large units " + trav + prec)
 
 
-@pytest.mark.parametrize("trav", ["3c18", "3c08"])
+@pytest.mark.parametrize("trav", ["3c18", "3c08", "3c08a"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32c"])
 def test_dense_liquid_edge_table_overflow(atm3, trav, prec):
     """At rho* = 1.4 units have more pair-rule edges than the per-unit edge table
@@ -328,3 +328,26 @@ def test_wide_traversal_32k_sampled(atm3):
                           for c in sample])
     assert_forces_close(f[:, mol], ref["f"][:, mol], RTOL["fp32c"], "sampled 3cw")
     assert r["n_int3"] > 0 and r["w3"] == pytest.approx(9 * r["e3"], rel=1e-5)
+
+
+# ------------------------------------------------------------------ corner-anchored 3c08
+
+@pytest.mark.parametrize("trunc", ["pair", "product"])
+def test_corner_anchored_3c08_equals_the_filtered_brute_force(atm3, trunc):
+    """The corner-anchored 3c08 (every task holds the block's corner cell)
+    finds exactly the brute-force triplets whose cell triple contains its own
+    bounding-box corner (6 cells per axis, so the product rule's base-frame
+    displacements are minimum images), fewer than the complete 3c08."""
+    rng = np.random.default_rng(44)
+    box = np.array([15.3, 15.3, 15.3])
+    x = np.ascontiguousarray(
+        synth.random_sequential(1100, [0, 0, 0], box, 0.85, rng, box=box).T)
+    cfg = dict(x=x, box=box)
+    prm = oracle.params(box, 2.5, NU)
+    bf = oracle.atm_brute(prm, x, trunc, member="3c08a")
+    r, f, _, _ = run_gpu(atm3, cfg, "3c08a", trunc, "fp64")
+    assert r["n_int3"] == bf["n_int3"]
+    assert r["e3"] == pytest.approx(bf["e3"], rel=1e-10)
+    assert_forces_close(f, bf["f"], 1e-10, "3c08a/" + trunc)
+    full, _, _, _ = run_gpu(atm3, cfg, "3c08", trunc, "fp64")
+    assert r["n_int3"] < full["n_int3"]

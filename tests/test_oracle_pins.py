@@ -226,7 +226,7 @@ def test_brute_force_equals_every_traversal_pair_rule(ncell_target, seed):
     assert np.allclose(lc["f"], bf["f"], rtol=1e-9, atol=1e-12)
 
 
-@pytest.mark.parametrize("trav", ["3c01", "3c18", "3c08"])
+@pytest.mark.parametrize("trav", ["3c01", "3c18", "3c08", "3c08a"])
 def test_brute_force_with_membership_equals_cells_product_rule(trav):
     """Product rule: the brute force restricted to the cell triples a traversal
     visits equals the linked-cell traversal (box of 6 cells per axis, so the
@@ -290,7 +290,7 @@ def test_candidate_counts_follow_cell_identities():
 
     fwd = [(dx, dy, dz) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)
            if (dz, dy, dx) > (0, 0, 0)]
-    t18 = t08 = t01 = 0
+    t18 = t08 = t01 = t08a = 0
     for z in range(nc[2]):
         for y in range(nc[1]):
             for xx in range(nc[0]):
@@ -310,6 +310,12 @@ def test_candidate_counts_follow_cell_identities():
                 for s, t, u in itertools.combinations(range(8), 3):
                     if s & t & u == 0:
                         t08 += sl[s] * sl[t] * sl[u]
+                # corner-anchored 3c08: the tasks that hold the corner cell
+                t08a += _comb3(sl[0])
+                for t in range(1, 8):
+                    t08a += sl[t] * _comb2(sl[0]) + sl[0] * _comb2(sl[t])
+                for t, u in itertools.combinations(range(1, 8), 2):
+                    t08a += sl[0] * sl[t] * sl[u]
                 # 3c01: each molecule of the base cell against all pairs of the other
                 # molecules in its 27-cell neighbourhood
                 m = sum(N(z + dz, y + dy, xx + dx) for dz in (-1, 0, 1) for dy in (-1, 0, 1)
@@ -318,6 +324,7 @@ def test_candidate_counts_follow_cell_identities():
     assert oracle.atm_cells(prm, x, "3c18", "pair")["n_cand3"] == t18
     assert oracle.atm_cells(prm, x, "3c08", "product")["n_cand3"] == t08
     assert oracle.atm_cells(prm, x, "3c01", "pair")["n_cand3"] == t01
+    assert oracle.atm_cells(prm, x, "3c08a", "pair")["n_cand3"] == t08a
 
 
 @pytest.mark.parametrize("trav", ["3c18", "3c08"])
@@ -588,3 +595,52 @@ def test_velocity_rescaling_sets_the_kinetic_temperature():
     assert np.abs(w.sum(axis=1)).max() < 1e-10
     z = np.zeros((3, n))
     assert np.array_equal(oracle.rescale(z, 1.0), z)
+
+
+# ---------------------------------------------------------------- corner-anchored 3c08
+
+def test_corner_anchored_3c08_omits_exactly_the_cornerless_block_triples():
+    """The 3c08 of the text (every task holds the block's corner cell) finds
+    the pair-rule triplets whose cell triple contains its own bounding-box
+    corner, and misses the rest (section 4 says some are omitted): brute force
+    with that membership filter = the traversal; the complete 3c08 = all."""
+    rc = 2.5
+    box = 4 * rc + 0.3
+    rng = np.random.default_rng(41)
+    n = int(0.35 * box ** 3)
+    x = np.ascontiguousarray(
+        synth.random_sequential(n, [0, 0, 0], [box] * 3, 0.85, rng, box=np.array([box] * 3)).T)
+    prm = _prm(box, rc)
+    full = oracle.atm_brute(prm, x, "pair")
+    anch_bf = oracle.atm_brute(prm, x, "pair", member="3c08a")
+    anch = oracle.atm_cells(prm, x, "3c08a", "pair")
+    assert anch["n_int3"] == anch_bf["n_int3"]
+    assert anch["e3"] == pytest.approx(anch_bf["e3"], rel=1e-11)
+    assert np.allclose(anch["f"], anch_bf["f"], rtol=1e-9, atol=1e-12)
+    assert 0.5 * full["n_int3"] < anch["n_int3"] < full["n_int3"]
+    assert oracle.atm_cells(prm, x, "3c08", "pair")["n_int3"] == full["n_int3"]
+    # fewer candidates than the complete 3c08 and a higher hit rate
+    c08 = oracle.atm_cells(prm, x, "3c08", "pair")
+    assert anch["n_cand3"] < c08["n_cand3"]
+    assert anch["n_int3"] / anch["n_cand3"] > c08["n_int3"] / c08["n_cand3"]
+
+
+def test_corner_anchored_3c08_on_three_cells_skips_the_cornerless_triple():
+    """Three molecules, one in each face neighbour of a corner cell (cells
+    (1,0,0), (0,1,0), (0,0,1) of a 4^3 grid) and mutually within r_c: the
+    complete 3c08 finds the triplet, the corner-anchored one does not; moving
+    one molecule into the corner cell makes both find it."""
+    rc = 2.5
+    box = 4 * rc
+    w = rc
+    x = np.array([[w + 0.2, w - 0.4, w - 0.4],
+                  [w - 0.4, w + 0.2, w - 0.4],
+                  [w - 0.4, w - 0.4, w + 0.2]]).T.copy()
+    # cells (1,0,0), (0,1,0), (0,0,1) relative to the corner (0,0,0)
+    prm = _prm(box, rc)
+    assert oracle.atm_cells(prm, x, "3c08", "pair")["n_int3"] == 1
+    assert oracle.atm_cells(prm, x, "3c08a", "pair")["n_int3"] == 0
+    x2 = x.copy()
+    x2[0, 0] = w - 0.1
+    assert oracle.atm_cells(prm, x2, "3c08", "pair")["n_int3"] == 1
+    assert oracle.atm_cells(prm, x2, "3c08a", "pair")["n_int3"] == 1
