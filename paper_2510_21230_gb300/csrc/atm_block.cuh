@@ -227,7 +227,11 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
             Acc<R>::zero(acc, mcap, 2 * mcap + t);
         }
     if (PAIR)
-        for (int t = tid; t < M * W; t += blockDim.x) adjT[t] = 0u;
+        for (int t = tid; t < M * W; t += blockDim.x) {
+            adjT[t] = 0u;
+            adj[t] = 0u;
+            rowpre[t] = 0;
+        }
     __syncthreads();
 
     // canonical displacement p -> q, working precision and FP32
@@ -278,14 +282,7 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
         // count (kept in rowoff[p + 1] until the row offsets are formed)
         for (int p = warp; p < M; p += nwarps) {
             int run = 0;
-            for (int w = 0; w < Wm; w++) {
-                if (w < (p >> 5)) {
-                    if (lane == 0) {
-                        adj[p * W + w] = 0u;
-                        rowpre[p * W + w] = 0;
-                    }
-                    continue;
-                }
+            for (int w = p >> 5; w < Wm; w++) {  // words below the diagonal stay zero
                 int q = (w << 5) + lane;
                 bool keep = q > p && q < M && close(p, q);
                 unsigned word = __ballot_sync(FULL, keep);
@@ -565,16 +562,22 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
                 const int ql = __shfl_sync(FULL, q, l);
                 const int vl = __shfl_sync(FULL, v, l);
                 int nth = t - __shfl_sync(FULL, excl, l);
-                int r = ql;
+                // the word holding the nth third member, then its bit: the bit
+                // search runs once per lane, outside the (divergent) word loop
+                int wsel = ql >> 5;
+                unsigned Ksel = 0u;
                 for (int w = ql >> 5; w < Wm; w++) {
                     const unsigned K = kword(pl, ql, vl, w);
                     const int c = __popc(K);
                     if (nth < c) {
-                        r = (w << 5) + nth_bit(K, nth);
+                        wsel = w;
+                        Ksel = K;
                         break;
                     }
                     nth -= c;
                 }
+                // invalid lanes repeat a valid triangle, so Ksel has a set bit here
+                const int r = (wsel << 5) + nth_bit(Ksel, nth);
                 nint += valid ? 1u : 0u;
                 const R gpq = eval_tri(pl, ql, r, e0 + l, valid);
                 if (!use_acc) {
@@ -721,7 +724,7 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
     }
 
     unsigned long long cand = 0;
-    if (tid == 0) cand = unit_candidates<TRAV, S>(s_beg);
+    if (warp == 0) cand = unit_candidates_warp<TRAV, S>(s_beg);
     unit_reduce_store<8>(esum.get(), wsum.get(), (unsigned long long)nint, 1.0, cand, A.unit_ew,
                          A.unit_cnt, u, s_red, s_redn);
 }

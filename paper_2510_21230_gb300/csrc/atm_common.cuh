@@ -164,6 +164,45 @@ __device__ inline unsigned long long unit_candidates(const int* beg)
     return cand;
 }
 
+// The same count for the block traversals (3c18, 3c08, corner-anchored 3c08),
+// spread over the lanes of one warp (every lane calls; lane 0 gets the total).
+template <int TRAV, int S>
+__device__ inline unsigned long long unit_candidates_warp(const int* beg)
+{
+    static_assert(S <= 32, "one slot per lane");
+    const int lane = threadIdx.x & 31;
+    auto Nn = [&](int s) { return (unsigned long long)(beg[s + 1] - beg[s]); };
+    auto C2 = [](unsigned long long m) { return m < 2 ? 0ull : m * (m - 1) / 2; };
+    auto C3 = [](unsigned long long m) { return m < 3 ? 0ull : m * (m - 1) * (m - 2) / 6; };
+    unsigned long long cand = 0;
+    if (lane < S) {
+        const int s = lane;
+        const unsigned long long Ns = Nn(s);
+        if (TRAV == 2) {
+            // lane s: the tasks whose first slot is s
+            if (s == 0) cand += C3(Ns);
+            for (int t = s + 1; t < S; t++) {
+                const unsigned long long Nt = Nn(t);
+                if ((s & t) == 0) cand += Nt * C2(Ns) + Ns * C2(Nt);
+                for (int v = t + 1; v < S; v++)
+                    if ((s & t & v) == 0) cand += Ns * Nt * Nn(v);
+            }
+        } else {
+            // every task holds slot 0: lane s > 0 takes <0, s> and <0, s, t > s>
+            const unsigned long long N0 = Nn(0);
+            if (s == 0) {
+                cand = C3(N0);
+            } else {
+                unsigned long long later = 0;
+                for (int t = s + 1; t < S; t++) later += Nn(t);
+                cand = Ns * C2(N0) + N0 * C2(Ns) + N0 * Ns * later;
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) cand += __shfl_down_sync(0xffffffffu, cand, o);
+    return cand;
+}
+
 // unit geometry: per-slot cell start, occupancy prefix and offsets (warp 0)
 template <int TRAV, int S>
 __device__ __forceinline__ void unit_slots(const Grid& g, const int* cell_start, long long u,

@@ -195,12 +195,14 @@ struct LjArith<double> {
     static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
     static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
     static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double rcp(double a) { return __drcp_rn(a); }
 };
 template <>
 struct LjArith<float> {
     static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
     static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
     static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float rcp(float a) { return __frcp_rn(a); }
 };
 
 // LJ (section 5) with owner-computes over the 27-cell neighbourhood: every
@@ -259,7 +261,7 @@ __global__ void __launch_bounds__(128) k_lj_owner(const LjArgs<R> A)
             R a = Q::add(Q::add(Q::mul(ddx, ddx), Q::mul(ddy, ddy)), Q::mul(ddz, ddz));
             if (!(a < rc2)) continue;
             visits++;
-            R ia = R(1) / a;
+            R ia = Q::rcp(a);  // correctly rounded: the same value as 1 / a
             R s2 = sig2 * ia;
             R s3 = s2 * s2 * s2;
             R s6 = s3 * s3;

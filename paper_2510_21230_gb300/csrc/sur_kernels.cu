@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(SUR_BLOCK, 5) k_sur_desc(const SurForceArgs A)
     float ljx = 0.f, ljy = 0.f, ljz = 0.f, lje = 0.f, ljw = 0.f;
     unsigned lj_cand = 0u, lj_visits = 0u;
     auto lj_add = [&](float ex, float ey, float ez, float a) {
-        const float ia = 1.0f / a;
+        const float ia = __frcp_rn(a);  // correctly rounded: the same value as 1 / a
         const float s2 = rp.sig2f * ia;
         const float s3 = s2 * s2 * s2;
         const float s6 = s3 * s3;

@@ -6,7 +6,10 @@ and print its CUDA-event time per evaluation -- a small driver for profilers
         --trav 3c08 --trunc pair --prec fp32c --reps 3
 
 With --prec surrogate the model is random (seeded) with the descriptor
-normalisation of the workload's own descriptors.
+normalisation of the workload's own descriptors.  --n N replaces the workload
+by a liquid of N molecules at rho 0.8 (fcc start, seed 7000); N = 104052
+gives the cell edge of the 256,000-molecule liquid (20 instead of 27 cells per
+axis).  The ATM kernel's own time comes from the library's launch profiler.
 """
 import argparse
 import os
@@ -27,10 +30,13 @@ def main():
     p.add_argument("--trunc", default="pair", choices=sorted(atm3.TRUNCATIONS))
     p.add_argument("--prec", default="fp32c", choices=sorted(atm3.PRECISIONS))
     p.add_argument("--reps", type=int, default=3)
+    p.add_argument("--n", type=int, default=0)
+    p.add_argument("--nwarps", type=int, default=0)
     a = p.parse_args()
     import torch
     build.build()
-    cfg = synth.config(a.workload)
+    cfg = synth.homogeneous(a.n, 0.8, 1.0, seed=7000) if a.n > 0 else synth.config(a.workload)
+    name = "liquid_n%d" % a.n if a.n > 0 else a.workload
     stream = torch.cuda.current_stream()
     with atm3.AtmSystem(cfg["box"], cfg["n"], rc=2.5, nu=0.073, stream=stream.cuda_stream) as s:
         s.set_state(cfg["x"], cfg["v"])
@@ -40,8 +46,11 @@ def main():
             sd = D.std(axis=0)
             s.surrogate_set_model(synth.sur_params(7), D.mean(axis=0),
                                   np.where(sd > 1e-12, sd, 1.0).astype(np.float32))
+        if a.nwarps:
+            s.set_options(nwarps=a.nwarps)
         s.compute_forces(a.trav, a.trunc, a.prec)
         torch.cuda.synchronize()
+        s.set_profiling(True)
         times = []
         for _ in range(3):
             e0 = torch.cuda.Event(enable_timing=True)
@@ -53,8 +62,11 @@ def main():
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1) / a.reps)
         r = s.results()[0]
-    print("%s %s %s %s: %.4f ms per evaluation (median of 3 x %d; cells excluded), n_int3 %d"
-          % (a.workload, a.trav, a.trunc, a.prec, sorted(times)[1], a.reps, r["n_int3"]))
+        prof = s.get_profile()
+    atm = prof["ms_atm"] / max(1, prof["n_atm_launches"])
+    print("%s %s %s %s: %.4f ms per evaluation (median of 3 x %d; cells excluded), ATM kernel "
+          "%.4f ms, n_int3 %d" % (name, a.trav, a.trunc, a.prec, sorted(times)[1], a.reps, atm,
+                                  r["n_int3"]))
 
 
 if __name__ == "__main__":
