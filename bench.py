@@ -45,7 +45,13 @@ FP64_FLOPS_PER_CLK_SM = 1.25e12 / (SMS * 2.07e9)
 # Useful flops per interacting triplet, counted from the kernel's evaluate()
 # (FMA = 2, the reciprocal square root = 1): 3 displacements 42, ATM terms 49,
 # gradient scalars, energy and virial 9, force vectors 27 (3c01: 9).
-F3 = {"3c01": 109.0, "3c18": 127.0, "3c08": 127.0}
+F3 = {"3c01": 109.0, "3c18": 127.0, "3c08": 127.0, "3c08a": 127.0}
+
+# Useful flops per interacting LJ pair when a step evaluates LJ inside the
+# 3c08 units (3c08 / 3c08a, pair rule): displacement and square 14, the LJ
+# scalar 9, energy and virial 4 (the force vector is the ATM gather's).
+F2_FUSED = 27.0
+FUSED_TRAV = ("3c08", "3c08a")
 
 # DRAM traffic per launch of the ATM kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum from one ncu capture), keyed by (traversal, truncation,
@@ -59,10 +65,10 @@ TRAFFIC = {("3c08", "pair", "fp32c", "liquid_n256k"): (11.36e6, "c414422717eba6f
 
 
 # Issued FP32 flops (fadd + fmul + 2 ffma thread instructions of the ATM
-# kernel, from the same ncu capture) per interacting triplet, with the source
-# hash they belong to: the useful count above plus what candidates and
-# bookkeeping cost in floating point.
-ISSUED = {("3c08", "pair", "fp32c"): (160.6, "c414422717eba6fa")}
+# kernel, from the same ncu capture) over the useful flops of that launch,
+# with the source hash they belong to: what candidates and bookkeeping add
+# in floating point.
+ISSUED = {}
 
 
 def kernel_hash():
@@ -261,7 +267,10 @@ def run_ours(args):
     # roofline of the dominant kernel (ATM triplets): useful flops per launch / launch time
     prof = main["prof"]
     atm_ms = prof["ms_atm"] / max(1, prof["n_atm_launches"])
+    fused = args.trav in FUSED_TRAV and args.trunc == "pair"
     flops = F3[args.trav] * main["res"]["n_int3"]
+    if fused:
+        flops += F2_FUSED * main["res"]["n_int2"]
     pk = peaks()
     sm_max = pk.get("sm_max_mhz", 2070.0)
     per_clk = FP32_FLOPS_PER_CLK_SM if args.prec == "fp32c" else FP64_FLOPS_PER_CLK_SM
@@ -270,16 +279,18 @@ def run_ours(args):
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
                 "traffic": traffic_for(args.trav, args.trunc, args.prec, args.workload),
-                "kernel": ("atm_owner_kernel<%s,%s,%s>" if args.trav == "3c01" else "atm_block_kernel<%s,%s,%s>") % (args.trav, args.trunc, args.prec),
+                "kernel": ("atm_owner_kernel<%s,%s,%s>" if args.trav == "3c01" else "atm_block_kernel<%s,%s,%s>") % (args.trav, args.trunc, args.prec)
+                          + (" (LJ of the c08 pairs inside)" if fused else ""),
                 "peak_source": "derived: %d SMs x %.2f flops/clk x %.0f MHz (%s pipe)"
                                % (SMS, per_clk, sm_max, "FP32" if args.prec == "fp32c" else "FP64"),
                 "flops_per_interacting_triplet": F3[args.trav],
+                "flops_per_interacting_pair": F2_FUSED if fused else None,
                 "ms_per_launch": atm_ms,
                 "measured_fma_peak_tflops": atm3.measure_fma_peak(local, args.prec == "fp64")}
     iss = ISSUED.get((args.trav, args.trunc, args.prec))
     if iss is not None and iss[1] == kernel_hash():
-        roofline["issued_flops_per_interacting_triplet"] = iss[0]
-        roofline["issued_frac"] = roofline["frac"] * iss[0] / F3[args.trav]
+        roofline["issued_over_useful_flops"] = iss[0]
+        roofline["issued_frac"] = roofline["frac"] * iss[0]
 
     # paper-style 3-body MUPS: N / (ATM force time)
     mups_3body = n / (atm_ms * 1e-3)

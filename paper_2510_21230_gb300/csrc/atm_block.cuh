@@ -179,6 +179,12 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
             A.unit_ew[2 * u + 1] = 0.0;
             A.unit_cnt[2 * u] = 0ull;
             A.unit_cnt[2 * u + 1] = 0ull;
+            if (PAIR && (TRAV == 2 || TRAV == 4) && A.lj) {
+                A.unit_ew2[2 * u] = 0.0;
+                A.unit_ew2[2 * u + 1] = 0.0;
+                A.unit_cnt2[2 * u] = 0ull;
+                A.unit_cnt2[2 * u + 1] = 0ull;
+            }
         }
         return;
     }
@@ -190,6 +196,28 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
     const R rc6 = F64 ? (R)rp.rc6 : (R)rp.rc6f;
     const R nu = F64 ? (R)rp.nu : (R)rp.nuf;
     const unsigned lt_mask = (1u << lane) - 1u;
+    // LJ of the unit's c08 cell pairs (3c08 pair rule in a step): the LJ
+    // kernel's arithmetic on the same canonical displacement
+    const bool LJ = PAIR && (TRAV == 2 || TRAV == 4) && A.lj != 0;
+    const R sig2 = F64 ? (R)rp.sig2 : (R)rp.sig2f;
+    const R eps4 = F64 ? (R)rp.eps4 : (R)rp.eps4f;
+    const R eps24 = F64 ? (R)rp.eps24 : (R)rp.eps24f;
+    const R eps48 = F64 ? (R)rp.eps48 : (R)rp.eps48f;
+    const R ushift = F64 ? (R)rp.ushift : (R)rp.ushiftf;
+    Sum<R> e2sum, w2sum;
+    unsigned n2 = 0;
+    // LJ pair scalar of squared distance a (F_p = G d(p -> q)); adds E2, W2
+    auto lj_pair = [&](R a) -> R {
+        const R ia = Ar<R>::rcp(a);
+        const R s2 = sig2 * ia;
+        const R s3 = s2 * s2 * s2;
+        const R s6 = s3 * s3;
+        const R fw = (eps48 * s6 - eps24 * s3) * ia;
+        e2sum.add(eps4 * (s6 - s3) - ushift);
+        w2sum.add(fw * a);
+        n2++;
+        return -fw;
+    };
 
     // ---- stage the unit: positions and exact shifts o * w
     for (int t = tid; t < M; t += blockDim.x) {
@@ -342,7 +370,6 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
         __syncthreads();
         edge_mode = s_edges <= A.gcap;
         if (edge_mode) {
-            for (int t = tid; t < s_edges; t += blockDim.x) G[t] = R(0);
             // edge list (p, q) in edge order; FP64: d(p -> q) and |d|^2 of every edge
             for (int p = warp; p < M; p += nwarps) {
                 for (int w = p >> 5; w < Wm; w++) {
@@ -351,6 +378,7 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
                         int q = (w << 5) + lane;
                         int e = rowoff[p] + rowpre[p * W + w] + __popc(word & lt_mask);
                         el[e] = (unsigned)p | ((unsigned)q << 16);
+                        G[e] = R(0);
                         if (F64) {
                             R dx, dy, dz;
                             R a = disp(p, q, dx, dy, dz);
@@ -368,8 +396,52 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
                 Acc<R>::zero(acc, mcap, mcap + t);
                 Acc<R>::zero(acc, mcap, 2 * mcap + t);
             }
+            if (LJ) {
+                __syncthreads();
+                // LJ of the c08 pairs straight into the per-molecule accumulators
+                for (int p = warp; p < M; p += nwarps)
+                    for (int w = p >> 5; w < Wm; w++) {
+                        const int q = (w << 5) + lane;
+                        if (((adj[p * W + w] >> lane) & 1u) && (sslot[p] & sslot[q]) == 0) {
+                            R dx, dy, dz;
+                            const R g = lj_pair(disp(p, q, dx, dy, dz));
+                            Acc<R>::add(acc, mcap, p, g * dx);
+                            Acc<R>::add(acc, mcap, mcap + p, g * dy);
+                            Acc<R>::add(acc, mcap, 2 * mcap + p, g * dz);
+                            Acc<R>::add(acc, mcap, q, -(g * dx));
+                            Acc<R>::add(acc, mcap, mcap + q, -(g * dy));
+                            Acc<R>::add(acc, mcap, 2 * mcap + q, -(g * dz));
+                        }
+                    }
+            }
         }
         __syncthreads();
+    }
+    if (LJ && edge_mode) {
+        // pair scalars of the c08 pairs start at their LJ term (thread per edge)
+        for (int e = tid; e < s_edges; e += blockDim.x) {
+            const unsigned x = el[e];
+            const int p = (int)(x & 0xffffu), q = (int)(x >> 16);
+            if ((sslot[p] & sslot[q]) == 0) {
+                R a;
+                if (F64) {
+                    a = ED[4 * e + 3];
+                } else {
+                    R dx, dy, dz;
+                    a = disp(p, q, dx, dy, dz);
+                }
+                G[e] = lj_pair(a);
+            }
+        }
+    }
+    if (LJ) {
+        // the unit's LJ sums are complete: store them now (nothing stays live
+        // through the triplet phase; the reduction's barriers also order the
+        // pair-scalar writes above before the triplet phase)
+        unsigned long long cand2 = 0;
+        if (warp == 0) cand2 = unit_pair_candidates_warp<S>(s_beg);
+        unit_reduce_store2<8>(e2sum.get(), w2sum.get(), (unsigned long long)n2, cand2, A.unit_ew2,
+                              A.unit_cnt2, u, s_red, s_redn);
     }
     const bool use_acc = PAIR ? !edge_mode : (A.acc_mode == 1);
 

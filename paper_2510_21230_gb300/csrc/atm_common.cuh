@@ -31,6 +31,7 @@ struct Ar<double> {
     static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
     static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
     static __device__ __forceinline__ double rsq(double a) { return ::rsqrt(a); }
+    static __device__ __forceinline__ double rcp(double a) { return __drcp_rn(a); }
 };
 template <>
 struct Ar<float> {
@@ -38,6 +39,7 @@ struct Ar<float> {
     static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
     static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
     static __device__ __forceinline__ float rsq(float a) { return rsqrtf(a); }
+    static __device__ __forceinline__ float rcp(float a) { return __frcp_rn(a); }
 };
 
 // canonical displacement p -> q (offset difference m in cells) and its square
@@ -203,6 +205,25 @@ __device__ inline unsigned long long unit_candidates_warp(const int* beg)
     return cand;
 }
 
+// Candidate pairs of the c08 2-body traversal in one 2x2x2 block: the
+// anchor cell's own pairs and the pairs of every two slots whose bounding
+// box starts at the anchor (13 slot pairs); summed over all blocks this is
+// the half-shell count.  Lane 0 of the calling warp gets the total.
+template <int S>
+__device__ inline unsigned long long unit_pair_candidates_warp(const int* beg)
+{
+    const int lane = threadIdx.x & 31;
+    unsigned long long c = 0;
+    if (lane < S) {
+        const unsigned long long Ns = (unsigned long long)(beg[lane + 1] - beg[lane]);
+        if (lane == 0) c = Ns < 2 ? 0ull : Ns * (Ns - 1) / 2;
+        for (int t = lane + 1; t < S; t++)
+            if ((lane & t) == 0) c += Ns * (unsigned long long)(beg[t + 1] - beg[t]);
+    }
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    return c;
+}
+
 // unit geometry: per-slot cell start, occupancy prefix and offsets (warp 0)
 template <int TRAV, int S>
 __device__ __forceinline__ void unit_slots(const Grid& g, const int* cell_start, long long u,
@@ -239,6 +260,44 @@ __device__ __forceinline__ void unit_slots(const Grid& g, const int* cell_start,
 }
 
 // block-wide reduction of the unit partials and their store (thread 0 writes)
+// the fused LJ sums of a unit (E2, W2 doubles, pair count) to unit_ew2 /
+// unit_cnt2; every thread calls, thread 0 writes
+template <int NWMAX>
+__device__ __forceinline__ void unit_reduce_store2(double e, double w, unsigned long long np,
+                                                   unsigned long long cand, double* unit_ew2,
+                                                   unsigned long long* unit_cnt2, long long u,
+                                                   double (*s_red)[NWMAX],
+                                                   unsigned long long* s_redn)
+{
+    const unsigned FULL = 0xffffffffu;
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        e += __shfl_down_sync(FULL, e, o);
+        w += __shfl_down_sync(FULL, w, o);
+        np += __shfl_down_sync(FULL, np, o);
+    }
+    __syncthreads();  // the slots are free (a previous reduction may still read them)
+    if (lane == 0) {
+        s_red[0][warp] = e;
+        s_red[1][warp] = w;
+        s_redn[warp] = np;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double et = 0.0, wt = 0.0;
+        unsigned long long nt = 0;
+        for (int q = 0; q < nw; q++) {
+            et += s_red[0][q];
+            wt += s_red[1][q];
+            nt += s_redn[q];
+        }
+        unit_ew2[2 * u] = et;
+        unit_ew2[2 * u + 1] = wt;
+        unit_cnt2[2 * u] = cand;
+        unit_cnt2[2 * u + 1] = 2 * nt;  // the reduction halves the pair visits of the owner kernel
+    }
+}
+
 template <int NWMAX>
 __device__ __forceinline__ void unit_reduce_store(double e, double w, unsigned long long ni,
                                                   double scale, unsigned long long cand,

@@ -94,7 +94,7 @@ static void free_all(atm_ctx* c)
                    c->xl32, c->cell_of, c->rank, c->count, c->start, c->perm, c->cell_sorted,
                    c->f_lj, c->f_atm, c->f_out, c->unit_ew, c->unit_cnt, c->mol_ew, c->mol_cnt,
                    c->ke, c->d_res, c->d_part, c->d_status, c->d_maxocc, c->d_work, c->d_dens,
-                   c->d_rdf, c->d_ttarget};
+                   c->d_rdf, c->d_ttarget, c->unit_ew2, c->unit_cnt2};
     for (void* p : dev)
         if (p) cudaFree(p);
     if (c->h_res) cudaFreeHost(c->h_res);
@@ -198,6 +198,8 @@ extern "C" atm_status atm_batch_create(const atm_params* params, const int64_t* 
     ok = ok && alloc((void**)&c->f_out, 3 * N * sizeof(double));
     ok = ok && alloc((void**)&c->unit_ew, 2 * NC * sizeof(double));
     ok = ok && alloc((void**)&c->unit_cnt, 2 * NC * sizeof(unsigned long long));
+    ok = ok && alloc((void**)&c->unit_ew2, 2 * NC * sizeof(double));
+    ok = ok && alloc((void**)&c->unit_cnt2, 2 * NC * sizeof(unsigned long long));
     ok = ok && alloc((void**)&c->mol_ew, 2 * N * sizeof(double));
     ok = ok && alloc((void**)&c->mol_cnt, 2 * N * sizeof(unsigned));
     ok = ok && alloc((void**)&c->ke, N * sizeof(double));
@@ -397,8 +399,11 @@ static void launch_choice(const atm_ctx* c, int trav, int trunc, int prec, int& 
 }
 
 // LJ + ATM force kernels for the current cells; mcap = staged-molecule capacity
-atm_status atm3::ctx_enqueue_forces(atm_ctx* c, int trav, int trunc, int prec, int mcap)
+atm_status atm3::ctx_enqueue_forces(atm_ctx* c, int trav, int trunc, int prec, int mcap,
+                                    bool fuse_lj)
 {
+    const bool fused = fuse_lj && (trav == ATM_3C08 || trav == ATM_3C08A) && trunc == ATM_TRUNC_PAIR &&
+                       prec != ATM_SURROGATE;
     if (trav == ATM_3CW)
         for (const Rep& r : c->reps)
             if (r.g.nc[0] < 5 || r.g.nc[1] < 5 || r.g.nc[2] < 5)
@@ -416,6 +421,9 @@ atm_status atm3::ctx_enqueue_forces(atm_ctx* c, int trav, int trunc, int prec, i
     j.mol_cnt = c->mol_cnt;
     j.unit_ew = c->unit_ew;
     j.unit_cnt = c->unit_cnt;
+    j.lj = fused ? 1 : 0;
+    j.unit_ew2 = c->unit_ew2;
+    j.unit_cnt2 = c->unit_cnt2;
     j.status = c->d_status;
     j.work = c->d_work;
     j.trav = trav;
@@ -431,7 +439,7 @@ atm_status atm3::ctx_enqueue_forces(atm_ctx* c, int trav, int trunc, int prec, i
     j.st = c->st;
 
     cudaEvent_t ev;
-    if (prec != ATM_SURROGATE) {
+    if (prec != ATM_SURROGATE && !fused) {
         // (the surrogate's descriptor pass computes LJ from the same neighbours)
         ev = ctx_prof_begin(c);
         CU(enqueue_lj(j));
@@ -460,6 +468,7 @@ atm_status atm3::ctx_enqueue_forces(atm_ctx* c, int trav, int trunc, int prec, i
     c->f_trav = trav;
     c->f_trunc = trunc;
     c->f_prec = prec;
+    c->f_fused = fused;
     return ATM_OK;
 }
 
@@ -469,6 +478,8 @@ static atm_status enqueue_reduce(atm_ctx* c)
     r.b = c->b;
     r.unit_ew = c->unit_ew;
     r.unit_cnt = c->unit_cnt;
+    r.unit_ew2 = c->f_fused ? c->unit_ew2 : nullptr;
+    r.unit_cnt2 = c->f_fused ? c->unit_cnt2 : nullptr;
     r.mol_ew = c->mol_ew;
     r.mol_cnt = c->mol_cnt;
     r.ke = c->ke;
@@ -538,6 +549,13 @@ static atm_status get_forces_impl(atm_ctx* c, double* f, int which, bool host)
     if (!c || !f || which < 0 || which > 2) return ATM_E_INVALID;
     if (!c->forces_valid) return ctx_fail(c, ATM_E_STATE, "no force evaluation is current");
     CU(cudaSetDevice(c->device));
+    if (c->f_fused && which != 0) {
+        // a step kept only LJ + ATM together: evaluate the parts apart for the
+        // same state (the cells are those of the current positions)
+        atm_status s = ctx_enqueue_forces(c, c->f_trav, c->f_trunc, c->f_prec,
+                                          c->unit_max[c->f_trav], false);
+        if (s != ATM_OK) return s;
+    }
     size_t bytes = 3 * (size_t)c->n * sizeof(double);
     if (!bytes) return ATM_OK;
     CU(launch_gather_forces(c->n, c->perm, c->f_lj, c->f_atm, which, host ? c->f_out : f, c->st));
@@ -581,7 +599,7 @@ static atm_status enqueue_step(atm_ctx* c, int trav, int trunc, int prec, int mc
     c->n_launch += 1;
     atm_status s = launch_cells(c);
     if (s != ATM_OK) return s;
-    s = ctx_enqueue_forces(c, trav, trunc, prec, mcap);
+    s = ctx_enqueue_forces(c, trav, trunc, prec, mcap, true);
     if (s != ATM_OK) return s;
     ev = ctx_prof_begin(c);
     CU(launch_kick(c->b, c->perm, c->f_lj, c->f_atm, c->x, c->v, 0, c->ke, c->st));
@@ -656,7 +674,7 @@ extern "C" atm_status atm_step(atm_ctx* c, int nsteps, atm_traversal trav, atm_t
     if (!fresh) {
         s = enqueue_cells(c);
         if (s != ATM_OK) return s;
-        s = ctx_enqueue_forces(c, trav, trunc, prec, c->unit_max[trav]);
+        s = ctx_enqueue_forces(c, trav, trunc, prec, c->unit_max[trav], true);
         if (s != ATM_OK) return s;
     }
     bool done = false;
@@ -686,7 +704,7 @@ extern "C" atm_status atm_step(atm_ctx* c, int nsteps, atm_traversal trav, atm_t
             drop_graph(c);
             s = enqueue_cells(c);
             if (s != ATM_OK) return s;
-            s = ctx_enqueue_forces(c, trav, trunc, prec, c->unit_max[trav]);
+            s = ctx_enqueue_forces(c, trav, trunc, prec, c->unit_max[trav], true);
             if (s != ATM_OK) return s;
         } else {
             return s;
@@ -704,7 +722,7 @@ extern "C" atm_status atm_step(atm_ctx* c, int nsteps, atm_traversal trav, atm_t
             // and compares the surrogate with it
             const bool exact = sur_mixed && sur_exact_due(c);
             s = ctx_enqueue_forces(c, trav, trunc, exact ? (int)ATM_FP32C : (int)prec,
-                                   c->unit_max[trav]);
+                                   c->unit_max[trav], !exact);
             if (s != ATM_OK) return s;
             if (exact) {
                 s = sur_enqueue_monitor(c);

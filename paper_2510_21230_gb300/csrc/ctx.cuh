@@ -42,6 +42,8 @@ struct atm_ctx {
     double* f_out = nullptr;  // [3n] original-order scratch for atm_get_forces
     double* unit_ew = nullptr;
     unsigned long long* unit_cnt = nullptr;
+    double* unit_ew2 = nullptr;             // [2 ncell] LJ E2, W2 of the units (fused steps)
+    unsigned long long* unit_cnt2 = nullptr;
     double* mol_ew = nullptr;
     unsigned* mol_cnt = nullptr;
     double* ke = nullptr;
@@ -65,6 +67,7 @@ struct atm_ctx {
     int unit_max[atm3::ATM_NTRAV] = {};  // largest unit (staged molecules) of 3c01, 3c18, 3c08, 3cw
     bool have_x = false, cells_built = false, forces_valid = false;
     int f_trav = -1, f_trunc = -1, f_prec = -1;
+    bool f_fused = false;  // the current forces came from units that also did LJ
     size_t smem_set[2][atm3::ATM_NTRAV][2] = {};
     int smem_optin = 0, sms = 0;
     // launch options: persistent ATM grid, warps per block-kernel CTA (0 =
@@ -97,7 +100,10 @@ atm_status ctx_fail(atm_ctx* c, atm_status s, const char* fmt, ...);
 // wait for the stream, fold the device status word into a status
 atm_status ctx_sync_and_check(atm_ctx* c);
 // LJ + ATM (exact or surrogate) forces of the current cells
-atm_status ctx_enqueue_forces(atm_ctx* c, int trav, int trunc, int prec, int mcap);
+// fuse_lj: 3c08 / corner-anchored 3c08 under the pair rule evaluate LJ inside
+// the ATM units (only the total force is kept apart from the energies)
+atm_status ctx_enqueue_forces(atm_ctx* c, int trav, int trunc, int prec, int mcap,
+                              bool fuse_lj = false);
 // profiling of a launch group (kind: 0 cells, 1 LJ, 2 ATM, 3 MD)
 cudaEvent_t ctx_prof_begin(atm_ctx* c);
 void ctx_prof_end(atm_ctx* c, int kind, cudaEvent_t a);

@@ -110,6 +110,11 @@ cudaError_t enqueue_atm(const ForceJob& j, size_t* smem_set, bool* capacity)
         e = cudaMemsetAsync(j.f_atm, 0, 3 * (size_t)j.b.ntot * sizeof(double), j.st);
         if (e != cudaSuccess) return e;
     }
+    const int lj = j.lj && (j.trav == 2 || j.trav == 4) && j.trunc == 0;
+    if (lj && j.b.ntot > 0) {  // the units write LJ + ATM into f_atm
+        e = cudaMemsetAsync(j.f_lj, 0, 3 * (size_t)j.b.ntot * sizeof(double), j.st);
+        if (e != cudaSuccess) return e;
+    }
     int ctas = 0;
     if (j.persistent && j.work) {
         int per_sm = j.prec == 0 ? atm_occupancy_fp64(j.trav, j.trunc, P.nwarps, P.smem)
@@ -128,6 +133,9 @@ cudaError_t enqueue_atm(const ForceJob& j, size_t* smem_set, bool* capacity)
         a.use_d = P.use_d;
         a.acc_mode = P.acc_mode;
         a.pcap = P.pcap;
+        a.lj = lj;
+        a.unit_ew2 = j.unit_ew2;
+        a.unit_cnt2 = j.unit_cnt2;
         return launch_atm_fp64(j.trav, j.trunc, a, P.nwarps, P.smem, ctas, j.st);
     }
     AtmArgs<float> a{};
@@ -139,6 +147,9 @@ cudaError_t enqueue_atm(const ForceJob& j, size_t* smem_set, bool* capacity)
     a.use_d = P.use_d;
     a.acc_mode = P.acc_mode;
     a.pcap = P.pcap;
+    a.lj = lj;
+    a.unit_ew2 = j.unit_ew2;
+    a.unit_cnt2 = j.unit_cnt2;
     return launch_atm_fp32(j.trav, j.trunc, a, P.nwarps, P.smem, ctas, j.st);
 }
 

@@ -435,12 +435,20 @@ __global__ void __launch_bounds__(256) k_partial_reduce(ReduceArgs R)
         w3 += R.unit_ew[2 * q + 1];
         c3 += R.unit_cnt[2 * q];
         i3 += R.unit_cnt[2 * q + 1];
+        if (R.unit_ew2) {
+            e2 += R.unit_ew2[2 * q];
+            w2 += R.unit_ew2[2 * q + 1];
+            c2 += R.unit_cnt2[2 * q];
+            v2 += R.unit_cnt2[2 * q + 1];
+        }
     }
     for (long long q = m0 + tid; q < m1; q += 256) {
-        e2 += R.mol_ew[2 * q];
-        w2 += R.mol_ew[2 * q + 1];
-        c2 += R.mol_cnt[2 * q];
-        v2 += R.mol_cnt[2 * q + 1];
+        if (!R.unit_ew2) {
+            e2 += R.mol_ew[2 * q];
+            w2 += R.mol_ew[2 * q + 1];
+            c2 += R.mol_cnt[2 * q];
+            v2 += R.mol_cnt[2 * q + 1];
+        }
         ke += R.ke[q];
     }
     sd[0][tid] = e2; sd[1][tid] = e3; sd[2][tid] = w2; sd[3][tid] = w3; sd[4][tid] = ke;

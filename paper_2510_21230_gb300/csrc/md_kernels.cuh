@@ -30,6 +30,10 @@ struct ReduceArgs {
     const double* mol_ew;
     const unsigned* mol_cnt;
     const double* ke;         // [n] kinetic energy per molecule
+    // non-null when the ATM units evaluated LJ too: E2, W2 and the pair counts
+    // per unit ([2 ncell] each) replace mol_ew / mol_cnt
+    const double* unit_ew2 = nullptr;
+    const unsigned long long* unit_cnt2 = nullptr;
     ResultDev* part;          // [R * REDUCE_PARTS] partial sums
     ResultDev* out;           // [R]
 };

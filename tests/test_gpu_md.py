@@ -80,3 +80,50 @@ def test_nve_drift_32k_matches_oracle(atm3):
         # make the total energy jump at every cutoff crossing on both sides)
         assert abs(d - d_ref) / n < 1e-4, (trav, prec, d, d_ref)
         assert m <= 1.2 * m_ref + 1e-3 * n, (trav, prec, m, m_ref)
+
+
+@pytest.mark.parametrize("trav,prec", [("3c08", "fp32c"), ("3c08", "fp64"), ("3c08a", "fp32c")])
+def test_step_with_lj_inside_the_units_equals_separate_kernels(atm3, trav, prec):
+    """A step under the 3c08 pair rule evaluates LJ inside the ATM units (the
+    c08 cell pairs of each block): same counts, energies and total force as
+    the separate LJ and ATM kernels on the same state; asking for the LJ or
+    ATM part afterwards re-evaluates them apart."""
+    rtol = 1e-10 if prec == "fp64" else 2e-5
+    cfg = synth.homogeneous(4000, 0.8, 1.0, seed=1100)
+    with atm3.AtmSystem(cfg["box"], cfg["n"], nu=NU, dt=0.002) as s:
+        s.set_state(cfg["x"], cfg["v"])
+        s.step(3, trav, "pair", prec)
+        fused = s.step(0, trav, "pair", prec)   # forces of this state, fused
+        f_tot = s.get_forces("total")
+        f_lj = s.get_forces("lj")              # re-evaluated apart
+        f_atm = s.get_forces("atm")
+        sep = s.compute_forces(trav, "pair", prec)
+        f_tot2 = s.get_forces("total")
+        f_lj2 = s.get_forces("lj")
+    for k in ("n_cand2", "n_int2", "n_cand3", "n_int3"):
+        assert fused[k] == sep[k], k
+    for k in ("e2", "w2", "e3", "w3"):
+        assert fused[k] == pytest.approx(sep[k], rel=rtol), k
+    scale = np.sqrt(np.mean(f_tot2 ** 2))
+    assert np.abs(f_tot - f_tot2).max() <= rtol * 4 * scale
+    assert np.allclose(f_lj, f_lj2, rtol=0, atol=1e-12 * scale)
+    assert np.abs(f_lj + f_atm - f_tot2).max() <= 1e-12 * scale + rtol * scale
+
+
+def test_fused_batch_step_equals_oracle_energies(atm3):
+    """Uneven replicas stepped together with LJ inside the 3c08 units: per
+    replica the energies after two FP64 steps match the oracle's run."""
+    reps = synth.replicas(count=3, n_lo=800, n_hi=2500)
+    x = np.ascontiguousarray(np.concatenate([r["x"] for r in reps], axis=1))
+    v = np.ascontiguousarray(np.concatenate([r["v"] for r in reps], axis=1))
+    with atm3.AtmSystem([r["box"] for r in reps], [r["n"] for r in reps], nu=NU, dt=0.002) as s:
+        s.set_state(x, v)
+        s.step(2, "3c08", "pair", "fp64")
+        res = s.results()
+    for r, rep in enumerate(reps):
+        prm = oracle.params(rep["box"], 2.5, NU)
+        ref = oracle.md_run(prm, rep["x"], rep["v"], 2, 0.002, "3c08", "pair", "fp64")
+        e2, e3, ek = ref["energies"][-1][:3]
+        assert res[r]["e2"] == pytest.approx(e2, rel=1e-9), r
+        assert res[r]["e3"] == pytest.approx(e3, rel=1e-9), r
+        assert res[r]["ekin"] == pytest.approx(ek, rel=1e-9), r
