@@ -131,12 +131,22 @@ __global__ void k_unit_max(Batch B, const int* __restrict__ start, int* __restri
         m08 = max(m08, __shfl_down_sync(0xffffffffu, m08, o));
         mw = max(mw, __shfl_down_sync(0xffffffffu, mw, o));
     }
-    if ((threadIdx.x & 31) == 0) {
-        atomicMax(out, m01);
-        atomicMax(out + 1, m18);
-        atomicMax(out + 2, m08);
-        atomicMax(out + 3, mw);
-        atomicMax(out + 4, m08);  // the corner-anchored 3c08 stages the same blocks
+    // block maximum first: one global atomic per value and block
+    __shared__ int s_m[4][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) {
+        s_m[0][warp] = m01;
+        s_m[1][warp] = m18;
+        s_m[2][warp] = m08;
+        s_m[3][warp] = mw;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        int m = 0;
+        for (int w = 0; w < nw; w++) m = max(m, s_m[threadIdx.x][w]);
+        atomicMax(out + threadIdx.x, m);
+        // the corner-anchored 3c08 stages the same blocks as 3c08
+        if (threadIdx.x == 2) atomicMax(out + 4, m);
     }
 }
 
