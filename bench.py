@@ -299,14 +299,19 @@ def run_ours(args):
     force_err = None
     if args.prec == "fp32c":
         sysm.build_cells()
-        sysm.compute_forces(args.trav, args.trunc, "fp64")
+        r64 = sysm.compute_forces(args.trav, args.trunc, "fp64")
         f64 = sysm.get_forces("atm")
-        sysm.compute_forces(args.trav, args.trunc, "fp32c")
+        r32 = sysm.compute_forces(args.trav, args.trunc, "fp32c")
         f32 = sysm.get_forces("atm")
         scale = float(np.sqrt(np.mean(f64 ** 2)))
         d = np.abs(f32 - f64)
+        # a pair within FP32 rounding of r_c can be decided differently in
+        # the two precisions; every triplet on it then changes the force of
+        # its three molecules by a term of the size of a triplet at the cutoff
         force_err = {"vs": "fp64 GPU path, same state", "max_abs_over_rms": float(d.max() / scale),
-                     "rms_rel": float(np.sqrt(np.mean(d ** 2)) / scale)}
+                     "p99_99_abs_over_rms": float(np.quantile(d, 0.9999) / scale),
+                     "rms_rel": float(np.sqrt(np.mean(d ** 2)) / scale),
+                     "n_int3_fp32c": int(r32["n_int3"]), "n_int3_fp64": int(r64["n_int3"])}
 
     # variants (same state, fewer steps)
     variants = []
