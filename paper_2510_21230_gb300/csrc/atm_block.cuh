@@ -304,6 +304,32 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
         return rowpre[x * W + wy] + __popc(adj[x * W + wy] & ((1u << (y & 31)) - 1u));
     };
 
+    // ends (p, q) of edge e from the row offsets and the adjacency: p = the
+    // last row with rowoff[p] <= e, q = the (e - rowoff[p])-th set bit of row
+    // p (the word by a scan, then its bit once)
+    auto locate_edge = [&](int e, int& p, int& q) {
+        int lo = 0, hi = M - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (rowoff[mid] <= e) lo = mid; else hi = mid - 1;
+        }
+        p = lo;
+        int j = e - rowoff[p];
+        int wsel = p >> 5;
+        unsigned Ksel = 0u;
+        for (int w = p >> 5; w < Wm; w++) {
+            const unsigned word = adj[p * W + w];
+            const int c = __popc(word);
+            if (j < c) {
+                wsel = w;
+                Ksel = word;
+                break;
+            }
+            j -= c;
+        }
+        q = (wsel << 5) + nth_bit(Ksel, j);
+    };
+
     // ---- 1. pair decisions
     if (PAIR) {
         // row p of the adjacency, its per-word prefix popcounts and its edge
@@ -370,22 +396,31 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
         __syncthreads();
         edge_mode = s_edges <= A.gcap;
         if (edge_mode) {
-            // edge list (p, q) in edge order; FP64: d(p -> q) and |d|^2 of every edge
-            for (int p = warp; p < M; p += nwarps) {
-                for (int w = p >> 5; w < Wm; w++) {
-                    unsigned word = adj[p * W + w];
-                    if ((word >> lane) & 1u) {
-                        int q = (w << 5) + lane;
-                        int e = rowoff[p] + rowpre[p * W + w] + __popc(word & lt_mask);
-                        el[e] = (unsigned)p | ((unsigned)q << 16);
-                        G[e] = R(0);
-                        if (F64) {
-                            R dx, dy, dz;
-                            R a = disp(p, q, dx, dy, dz);
-                            ED[4 * e] = dx;
-                            ED[4 * e + 1] = dy;
-                            ED[4 * e + 2] = dz;
-                            ED[4 * e + 3] = a;
+            // edge list (p, q) in edge order.  FP64: one thread per edge, which
+            // also tabulates d(p -> q) and |d|^2 (every lane does FP64 work);
+            // FP32: lanes take the set bits of each row word
+            if (F64) {
+                for (int e = tid; e < s_edges; e += blockDim.x) {
+                    int p, q;
+                    locate_edge(e, p, q);
+                    el[e] = (unsigned)p | ((unsigned)q << 16);
+                    G[e] = R(0);
+                    R dx, dy, dz;
+                    R a = disp(p, q, dx, dy, dz);
+                    ED[4 * e] = dx;
+                    ED[4 * e + 1] = dy;
+                    ED[4 * e + 2] = dz;
+                    ED[4 * e + 3] = a;
+                }
+            } else {
+                for (int p = warp; p < M; p += nwarps) {
+                    for (int w = p >> 5; w < Wm; w++) {
+                        unsigned word = adj[p * W + w];
+                        if ((word >> lane) & 1u) {
+                            int q = (w << 5) + lane;
+                            int e = rowoff[p] + rowpre[p * W + w] + __popc(word & lt_mask);
+                            el[e] = (unsigned)p | ((unsigned)q << 16);
+                            G[e] = R(0);
                         }
                     }
                 }
@@ -575,23 +610,7 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
             q = (int)(x >> 16);
             return;
         }
-        int lo = 0, hi = M - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (rowoff[mid] <= e) lo = mid; else hi = mid - 1;
-        }
-        p = lo;
-        q = p;
-        int j = e - rowoff[p];
-        for (int w = p >> 5; w < Wm; w++) {
-            const unsigned word = adj[p * W + w];
-            const int c = __popc(word);
-            if (j < c) {
-                q = (w << 5) + nth_bit(word, j);
-                break;
-            }
-            j -= c;
-        }
+        locate_edge(e, p, q);
     };
 
     if (PAIR) {

@@ -288,21 +288,41 @@ static void invalidate(atm_ctx* c)
     c->forces_valid = false;
 }
 
+// true when no element is NaN or infinite (exponent field all ones); a
+// branch-free OR over the bit patterns, which the host compiler vectorises
+static bool all_finite(const double* a, long long m)
+{
+    uint64_t bad = 0;
+    for (long long i = 0; i < m; i++) {
+        uint64_t u;
+        memcpy(&u, a + i, sizeof(u));
+        bad |= (uint64_t)((~u & 0x7ff0000000000000ull) == 0);
+    }
+    return bad == 0;
+}
+
 extern "C" atm_status atm_set_state(atm_ctx* c, const double* x, const double* v)
 {
     if (!c) return ATM_E_INVALID;
     if (!x && c->n > 0) return ctx_fail(c, ATM_E_INVALID, "positions are required");
-    for (long long q = 0; q < 3 * c->n; q++)
-        if (!std::isfinite(x[q]) || (v && !std::isfinite(v[q])))
-            return ctx_fail(c, ATM_E_NONFINITE, "non-finite input at element %lld", q);
     CU(cudaSetDevice(c->device));
-    size_t bytes = 3 * (size_t)c->n * sizeof(double);
+    const long long m = 3 * c->n;
+    size_t bytes = (size_t)m * sizeof(double);
+    // start the copies first; the host checks the same buffers meanwhile
     if (bytes) {
         CU(cudaMemcpyAsync(c->x, x, bytes, cudaMemcpyHostToDevice, c->st));
         if (v)
             CU(cudaMemcpyAsync(c->v, v, bytes, cudaMemcpyHostToDevice, c->st));
         else
             CU(cudaMemsetAsync(c->v, 0, bytes, c->st));
+    }
+    if (!all_finite(x, m) || (v && !all_finite(v, m))) {
+        long long q = 0;
+        while (q < m && std::isfinite(x[q]) && (!v || std::isfinite(v[q]))) q++;
+        c->have_x = false;
+        invalidate(c);
+        CU(cudaStreamSynchronize(c->st));  // the caller may reuse its buffers at once
+        return ctx_fail(c, ATM_E_NONFINITE, "non-finite input at element %lld", q);
     }
     c->have_x = true;
     invalidate(c);
