@@ -286,7 +286,16 @@ def run_ours(args):
                 "flops_per_interacting_triplet": F3[args.trav],
                 "flops_per_interacting_pair": F2_FUSED if fused else None,
                 "ms_per_launch": atm_ms,
-                "measured_fma_peak_tflops": atm3.measure_fma_peak(local, args.prec == "fp64")}
+                "measured_fma_peak_tflops": atm3.measure_fma_peak(local, args.prec == "fp64"),
+                "measured_rsqrt_peak_gops": atm3.measure_rsqrt_peak(local),
+                "rsqrt_per_s_needed_gops": main["res"]["n_int3"] / (atm_ms * 1e-3) / 1e9}
+    tr = roofline["traffic"]
+    hbm = pk.get("hbm_gbs")
+    if tr is not None and hbm:
+        # the kernel's DRAM bytes per launch over its time, against measured HBM copy bandwidth
+        roofline["hbm_achieved_gbs"] = tr / (atm_ms * 1e-3) / 1e9
+        roofline["hbm_peak_gbs"] = hbm
+        roofline["hbm_frac"] = roofline["hbm_achieved_gbs"] / hbm
     iss = ISSUED.get((args.trav, args.trunc, args.prec))
     if iss is not None and iss[1] == kernel_hash():
         roofline["issued_over_useful_flops"] = iss[0]
@@ -524,10 +533,12 @@ def completeness_variant(atm3, device, stream, workload="liquid_n32k"):
 
 # ------------------------------------------------------------------ slab
 
-def slab_variant(atm3, device, stream, flush, steps=20, warmup=5, nbins=600):
+def slab_variant(atm3, device, stream, flush, steps=20, warmup=5, nbins=600, compare_steps=500):
     """Vapour-liquid slab: 30 x 30 x 120 box, a 30-sigma fcc liquid slab at
     rho 0.73 with vapour at rho 0.02 (random sequential insertion), T 0.85,
-    3c08 + pair + FP32C; every step also adds the 600-bin histogram of z."""
+    3c08 + pair + FP32C; every step also adds the 600-bin histogram of z.  Then
+    the same start is run 500 steps in FP32C and in FP64 and the two density
+    profiles are compared."""
     import torch
     cfg = synth.slab()
     n = cfg["n"]
@@ -559,12 +570,35 @@ def slab_variant(atm3, device, stream, flush, steps=20, warmup=5, nbins=600):
         fit = {side: {k: round(v, 4) for k, v in fit[side].items()} for side in ("left", "right")}
     except ImportError:
         fit = None
+    # the same start run 500 steps in FP32C and in FP64 with rho(z) sampled
+    # every step: the two profiles must agree to within sampling noise
+    profiles = {}
+    for prec in ("fp32c", "fp64"):
+        with atm3.AtmSystem(cfg["box"], n, rc=RC, nu=NU, dt=0.002, device=device,
+                            stream=stream.cuda_stream) as b:
+            b.set_state(cfg["x"], cfg["v"])
+            b.set_options(graph=True)
+            for _ in range(compare_steps):
+                b.step(1, "3c08", "pair", prec, sync=False)
+                b.density_accumulate(axis=2, nbins=nbins)
+            c, smp = b.density_get(nbins)
+            profiles[prec] = analysis.density_profile(c[0], smp, L)[1]
+    d = np.abs(profiles["fp32c"] - profiles["fp64"])
+    # counting noise of one bin: sqrt(mean count per sample / samples) / bin volume
+    bin_vol = L[0] * L[1] * L[2] / nbins
+    noise = np.sqrt(np.maximum(profiles["fp64"], 1e-12) / (bin_vol * compare_steps))
+    compare = {"steps": compare_steps, "max_abs_diff": float(d.max()),
+               "mean_abs_diff": float(d.mean()),
+               "rho_centre_fp32c": float(profiles["fp32c"][nbins // 2 - 50: nbins // 2 + 50].mean()),
+               "rho_centre_fp64": float(profiles["fp64"][nbins // 2 - 50: nbins // 2 + 50].mean()),
+               "max_diff_over_bin_noise": float((d / np.maximum(noise, 1e-12)).max())}
     return {"workload": "slab 30x30x120, liquid rho 0.73 (30 sigma) + vapour rho 0.02, N=%d, T 0.85"
                         % n,
             "traversal": "3c08", "truncation": "pair", "precision": "fp32c",
             "value": n * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
             "density_bins": nbins, "density_samples": samples,
-            "rho_centre": float(mid), "rho_edges": float(edge), "tanh_fit": fit}
+            "rho_centre": float(mid), "rho_edges": float(edge), "tanh_fit": fit,
+            "fp32c_vs_fp64_profile": compare}
 
 
 # ------------------------------------------------------------------ surrogate

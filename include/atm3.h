@@ -391,6 +391,10 @@ atm_status atm_lj_tail(const atm_params* params, int64_t n, double* e_tail, doub
  * best of three timed launches.  Roofline context for the ALU-bound kernels;
  * the paper has no counterpart. */
 atm_status atm_measure_fma_peak(int device, int fp64, double* tflops);
+/* Measured FP32 reciprocal-square-root throughput (rsqrtf, the special-function
+ * unit) in G operations/s, measured the same way; it bounds the one rsqrt per
+ * triplet.  Errors: INVALID (NULL output, negative device), CUDA. */
+atm_status atm_measure_rsqrt_peak(int device, double* gops);
 
 /* Device-time profile of the library's own kernels (CUDA events recorded on
  * the context's stream around each group of launches while profiling is on).

@@ -35,7 +35,7 @@ EXPORTED = ["atm_abi_version", "atm_create", "atm_batch_create", "atm_batch_size
             "atm_surrogate_add_rows", "atm_surrogate_dataset", "atm_surrogate_clear",
             "atm_surrogate_train", "atm_surrogate_options", "atm_surrogate_error",
             "atm_measure_fma_peak", "atm_rdf_accumulate", "atm_rdf_get", "atm_rdf_reset",
-            "atm_lj_tail", "atm_thermostat"]
+            "atm_lj_tail", "atm_thermostat", "atm_measure_rsqrt_peak"]
 
 SUR_NDESC, SUR_NVEC, SUR_NPARAM = 32, 9, 6467
 
@@ -139,6 +139,7 @@ def load():
         "atm_rdf_reset": [P],
         "atm_lj_tail": [ctypes.POINTER(Params), i64, P, P],
         "atm_thermostat": [P, P],
+        "atm_measure_rsqrt_peak": [i32, P],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -473,6 +474,16 @@ def lj_tail(box, n, rc=2.5, lj_eps=1.0, lj_sigma=1.0):
     if st != 0:
         raise AtmError(st, "atm_lj_tail failed")
     return e.value, pt.value
+
+
+def measure_rsqrt_peak(device=0):
+    """Measured FP32 rsqrt throughput of the device in G operations/s."""
+    L = load()
+    g = ctypes.c_double(0.0)
+    st = L.atm_measure_rsqrt_peak(int(device), ctypes.byref(g))
+    if st != 0:
+        raise AtmError(st, "atm_measure_rsqrt_peak failed")
+    return g.value
 
 
 def measure_fma_peak(device=0, fp64=False):

@@ -1,6 +1,6 @@
 // peak.cu -- measured arithmetic peaks of the device, for roofline context:
-// a kernel of independent fused multiply-add chains (FP32 or FP64), timed
-// with CUDA events.
+// kernels of independent fused multiply-add chains (FP32 or FP64) and of
+// independent FP32 reciprocal-square-root chains, timed with CUDA events.
 #include <cuda_runtime.h>
 
 #include "atm3.h"
@@ -25,6 +25,22 @@ __global__ void __launch_bounds__(256) k_fma_chains(T a, T b, T* out)
     for (int c = 0; c < PK_CHAINS; c++) s += acc[c];
     // practically never true; keeps the chains alive
     if (s == (T)-1.2345) out[blockIdx.x] = s;
+}
+
+// independent rsqrtf chains (the special-function unit's throughput)
+__global__ void __launch_bounds__(256) k_rsqrt_chains(float a, float* out)
+{
+    float acc[PK_CHAINS];
+#pragma unroll
+    for (int c = 0; c < PK_CHAINS; c++) acc[c] = a + (float)(threadIdx.x + c);
+    for (int i = 0; i < PK_ITERS / 4; i++) {
+#pragma unroll
+        for (int c = 0; c < PK_CHAINS; c++) acc[c] = rsqrtf(acc[c]);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < PK_CHAINS; c++) s += acc[c];
+    if (s == -1.2345f) out[blockIdx.x] = s;
 }
 
 template <typename T>
@@ -66,4 +82,37 @@ extern "C" atm_status atm_measure_fma_peak(int device, int fp64, double* tflops)
 {
     if (!tflops || device < 0) return ATM_E_INVALID;
     return fp64 ? run<double>(device, tflops) : run<float>(device, tflops);
+}
+
+extern "C" atm_status atm_measure_rsqrt_peak(int device, double* gops)
+{
+    if (!gops || device < 0) return ATM_E_INVALID;
+    if (cudaSetDevice(device) != cudaSuccess) return ATM_E_CUDA;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+        return ATM_E_CUDA;
+    float* out = nullptr;
+    const int blocks = sms * 8;
+    if (cudaMalloc(&out, blocks * sizeof(float)) != cudaSuccess) return ATM_E_CUDA;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; rep++) {
+        cudaEventRecord(e0);
+        k_rsqrt_chains<<<blocks, 256>>>(1.5f, out);
+        cudaEventRecord(e1);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0 && ms < best) best = ms;
+    }
+    const cudaError_t err = cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    if (err != cudaSuccess) return ATM_E_CUDA;
+    const double ops = (double)PK_CHAINS * (PK_ITERS / 4) * 256.0 * blocks;
+    *gops = ops / (best * 1e-3) / 1e9;
+    return ATM_OK;
 }
