@@ -333,21 +333,47 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
     // ---- 1. pair decisions
     if (PAIR) {
         // row p of the adjacency, its per-word prefix popcounts and its edge
-        // count (kept in rowoff[p + 1] until the row offsets are formed)
-        for (int p = warp; p < M; p += nwarps) {
-            int run = 0;
-            for (int w = p >> 5; w < Wm; w++) {  // words below the diagonal stay zero
-                int q = (w << 5) + lane;
-                bool keep = q > p && q < M && close(p, q);
-                unsigned word = __ballot_sync(FULL, keep);
-                if (lane == 0) {
+        // count (kept in rowoff[p + 1] until the row offsets are formed).
+        // FP32: one thread per row builds the row's words in a register while
+        // the warp walks the columns together (the column's staged row is a
+        // broadcast load).  FP64: one warp per row, one ballot per 32 pairs
+        // (the rare FP64 recomputations of the prefilter band stay spread
+        // over the lanes).
+        if (!F64) {
+            for (int p = tid; p < M; p += blockDim.x) {
+                int run = 0;
+                const unsigned pbit = 1u << (p & 31);
+                const int pw = p >> 5;
+                for (int w = p >> 5; w < Wm; w++) {  // words below the diagonal stay zero
+                    unsigned word = 0u;
+                    const int qa = max(p + 1, w << 5), qb = min(M, (w << 5) + 32);
+                    for (int q = qa; q < qb; q++)
+                        if (close(p, q)) {
+                            word |= 1u << (q & 31);
+                            atomicOr(&adjT[q * W + pw], pbit);
+                        }
                     adj[p * W + w] = word;
                     rowpre[p * W + w] = (unsigned short)run;
+                    run += __popc(word);
                 }
-                run += __popc(word);
-                if (keep) atomicOr(&adjT[q * W + (p >> 5)], 1u << (p & 31));
+                rowoff[p + 1] = run;
             }
-            if (lane == 0) rowoff[p + 1] = run;
+        } else {
+            for (int p = warp; p < M; p += nwarps) {
+                int run = 0;
+                for (int w = p >> 5; w < Wm; w++) {  // words below the diagonal stay zero
+                    int q = (w << 5) + lane;
+                    bool keep = q > p && q < M && close(p, q);
+                    unsigned word = __ballot_sync(FULL, keep);
+                    if (lane == 0) {
+                        adj[p * W + w] = word;
+                        rowpre[p * W + w] = (unsigned short)run;
+                    }
+                    run += __popc(word);
+                    if (keep) atomicOr(&adjT[q * W + (p >> 5)], 1u << (p & 31));
+                }
+                if (lane == 0) rowoff[p + 1] = run;
+            }
         }
     } else if (A.use_d) {
         for (int t = tid; t < M * (M - 1) / 2; t += blockDim.x) {

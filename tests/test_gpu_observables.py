@@ -170,3 +170,18 @@ def test_nvt_run_follows_the_oracle(atm3):
     d -= np.rint(d / cfg["box"][:, None]) * cfg["box"][:, None]
     assert np.abs(d).max() < 1e-9
     assert np.abs(vg - v).max() < 1e-7
+
+
+# ---------------------------------------------------------------- peak probes
+
+def test_measured_peaks_are_plausible(atm3):
+    """The roofline denominators measured by the library: FP32 / FP64 FMA
+    throughput and FP32 rsqrt throughput, positive and below the nominal
+    rates derived from unit counts (152 SMs at 2.07 GHz: FP32 80.5 TFLOP/s;
+    16 rsqrt per SM per clock, 5.0 T/s)."""
+    f32 = atm3.measure_fma_peak(0, fp64=False)
+    f64 = atm3.measure_fma_peak(0, fp64=True)
+    rs = atm3.measure_rsqrt_peak(0)
+    assert 10.0 < f32 < 90.0
+    assert 0.1 < f64 < f32
+    assert 100.0 < rs < 6000.0
