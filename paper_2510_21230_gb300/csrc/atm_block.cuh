@@ -424,7 +424,7 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
         if (edge_mode) {
             // edge list (p, q) in edge order.  FP64: one thread per edge, which
             // also tabulates d(p -> q) and |d|^2 (every lane does FP64 work);
-            // FP32: lanes take the set bits of each row word
+            // FP32: one thread per row
             if (F64) {
                 for (int e = tid; e < s_edges; e += blockDim.x) {
                     int p, q;
@@ -439,14 +439,17 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
                     ED[4 * e + 3] = a;
                 }
             } else {
-                for (int p = warp; p < M; p += nwarps) {
+                // one thread per row writes the row's edges in order
+                for (int p = tid; p < M; p += blockDim.x) {
+                    int e = rowoff[p];
                     for (int w = p >> 5; w < Wm; w++) {
                         unsigned word = adj[p * W + w];
-                        if ((word >> lane) & 1u) {
-                            int q = (w << 5) + lane;
-                            int e = rowoff[p] + rowpre[p * W + w] + __popc(word & lt_mask);
+                        while (word) {
+                            const int q = (w << 5) + __ffs(word) - 1;
+                            word &= word - 1u;
                             el[e] = (unsigned)p | ((unsigned)q << 16);
                             G[e] = R(0);
+                            e++;
                         }
                     }
                 }
