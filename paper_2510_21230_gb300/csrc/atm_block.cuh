@@ -422,36 +422,32 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
         __syncthreads();
         edge_mode = s_edges <= A.gcap;
         if (edge_mode) {
-            // edge list (p, q) in edge order.  FP64: one thread per edge, which
-            // also tabulates d(p -> q) and |d|^2 (every lane does FP64 work);
-            // FP32: one thread per row
+            // edge list (p, q) in edge order, one thread per row; FP64 then
+            // tabulates d(p -> q) and |d|^2 one thread per edge (every lane
+            // does FP64 work)
+            for (int p = tid; p < M; p += blockDim.x) {
+                int e = rowoff[p];
+                for (int w = p >> 5; w < Wm; w++) {
+                    unsigned word = adj[p * W + w];
+                    while (word) {
+                        const int q = (w << 5) + __ffs(word) - 1;
+                        word &= word - 1u;
+                        el[e] = (unsigned)p | ((unsigned)q << 16);
+                        G[e] = R(0);
+                        e++;
+                    }
+                }
+            }
             if (F64) {
+                __syncthreads();
                 for (int e = tid; e < s_edges; e += blockDim.x) {
-                    int p, q;
-                    locate_edge(e, p, q);
-                    el[e] = (unsigned)p | ((unsigned)q << 16);
-                    G[e] = R(0);
+                    const unsigned x = el[e];
                     R dx, dy, dz;
-                    R a = disp(p, q, dx, dy, dz);
+                    const R a = disp((int)(x & 0xffffu), (int)(x >> 16), dx, dy, dz);
                     ED[4 * e] = dx;
                     ED[4 * e + 1] = dy;
                     ED[4 * e + 2] = dz;
                     ED[4 * e + 3] = a;
-                }
-            } else {
-                // one thread per row writes the row's edges in order
-                for (int p = tid; p < M; p += blockDim.x) {
-                    int e = rowoff[p];
-                    for (int w = p >> 5; w < Wm; w++) {
-                        unsigned word = adj[p * W + w];
-                        while (word) {
-                            const int q = (w << 5) + __ffs(word) - 1;
-                            word &= word - 1u;
-                            el[e] = (unsigned)p | ((unsigned)q << 16);
-                            G[e] = R(0);
-                            e++;
-                        }
-                    }
                 }
             }
         } else {
