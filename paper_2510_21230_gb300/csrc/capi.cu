@@ -355,7 +355,8 @@ static atm_status launch_cells(atm_ctx* c)
 {
     cudaEvent_t ev = ctx_prof_begin(c);
     CU(launch_build_cells(c->b, c->x, c->cell_of, c->rank, c->count, c->start, c->perm, c->xl,
-                          c->xl32, c->cell_sorted, c->d_maxocc, c->d_status, c->st));
+                          c->xl32, c->cell_sorted, c->d_maxocc, c->d_status, c->wide_cells,
+                          c->st));
     ctx_prof_end(c, PK_CELLS, ev);
     c->n_launch += c->n > 0 ? 6 : 2;
     return ATM_OK;
@@ -374,6 +375,16 @@ static atm_status enqueue_cells(atm_ctx* c)
     c->cells_built = true;
     c->forces_valid = false;
     return ATM_OK;
+}
+
+// the wide traversal's units are sized by cell builds only once it is in use:
+// the first request rebuilds the (unchanged) cells with that size
+atm_status atm3::ctx_want_wide(atm_ctx* c, int trav)
+{
+    if (trav != ATM_3CW || c->wide_cells) return ATM_OK;
+    c->wide_cells = true;
+    drop_graph(c);
+    return c->cells_built ? enqueue_cells(c) : ATM_OK;
 }
 
 extern "C" atm_status atm_build_cells(atm_ctx* c)
@@ -538,6 +549,10 @@ extern "C" atm_status atm_compute_forces(atm_ctx* c, atm_traversal trav, atm_tru
     if (!valid_enums(trav, trunc, prec)) return ctx_fail(c, ATM_E_INVALID, "unknown traversal/truncation/precision");
     if (!c->cells_built) return ctx_fail(c, ATM_E_STATE, "cells not built");
     CU(cudaSetDevice(c->device));
+    {
+        atm_status w = ctx_want_wide(c, trav);
+        if (w != ATM_OK) return w;
+    }
     atm_status s = ctx_enqueue_forces(c, trav, trunc, prec, c->unit_max[trav]);
     if (s != ATM_OK) return s;
     cudaEvent_t ev = ctx_prof_begin(c);
@@ -686,7 +701,8 @@ extern "C" atm_status atm_step(atm_ctx* c, int nsteps, atm_traversal trav, atm_t
         return ctx_fail(c, ATM_E_INVALID, "bad step arguments");
     if (!c->have_x) return ctx_fail(c, ATM_E_STATE, "no state set");
     CU(cudaSetDevice(c->device));
-    atm_status s;
+    atm_status s = ctx_want_wide(c, trav);
+    if (s != ATM_OK) return s;
     // forces of the current state from this combination (for the surrogate, the
     // exact FP32C forces of an interleaved step serve as well)
     const bool fresh = c->forces_valid && c->f_trav == trav && c->f_trunc == trunc &&
@@ -791,6 +807,10 @@ extern "C" atm_status atm_autotune(atm_ctx* c, atm_traversal trav, atm_truncatio
         return ctx_fail(c, ATM_E_INVALID, "bad tuning arguments");
     if (!c->cells_built) return ctx_fail(c, ATM_E_STATE, "cells not built");
     CU(cudaSetDevice(c->device));
+    {
+        atm_status w = ctx_want_wide(c, trav);
+        if (w != ATM_OK) return w;
+    }
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));

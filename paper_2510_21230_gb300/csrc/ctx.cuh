@@ -68,6 +68,7 @@ struct atm_ctx {
     bool have_x = false, cells_built = false, forces_valid = false;
     int f_trav = -1, f_trunc = -1, f_prec = -1;
     bool f_fused = false;  // the current forces came from units that also did LJ
+    bool wide_cells = false;  // cell builds also size the wide traversal's 5^3 units
     size_t smem_set[2][atm3::ATM_NTRAV][2] = {};
     int smem_optin = 0, sms = 0;
     // launch options: persistent ATM grid, warps per block-kernel CTA (0 =
@@ -100,6 +101,9 @@ atm_status ctx_fail(atm_ctx* c, atm_status s, const char* fmt, ...);
 // wait for the stream, fold the device status word into a status
 atm_status ctx_sync_and_check(atm_ctx* c);
 // LJ + ATM (exact or surrogate) forces of the current cells
+// the wide traversal's units are sized by cell builds only once it is in use:
+// its first request rebuilds the (unchanged) cells with that size
+atm_status ctx_want_wide(atm_ctx* c, int trav);
 // fuse_lj: 3c08 / corner-anchored 3c08 under the pair rule evaluate LJ inside
 // the ATM units (only the total force is kept apart from the energies)
 atm_status ctx_enqueue_forces(atm_ctx* c, int trav, int trunc, int prec, int mcap,

@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(1024) k_scan(long long ncell, const int* __res
 
 // largest staged-molecule count of a traversal unit, per traversal:
 // out[0] 3c01 (27 cells), out[1] 3c18 (base + 13 forward), out[2] 3c08 (2x2x2 block)
-__global__ void k_unit_max(Batch B, const int* __restrict__ start, int* __restrict__ out)
+__global__ void k_unit_max(Batch B, const int* __restrict__ start, int wide, int* __restrict__ out)
 {
     long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     int m01 = 0, m18 = 0, m08 = 0, mw = 0;
@@ -119,8 +119,8 @@ __global__ void k_unit_max(Batch B, const int* __restrict__ start, int* __restri
             if (t >= 13) m18 += k;
             if (dx >= 0 && dy >= 0 && dz >= 0) m08 += k;
         }
-        // the wide traversal's 5^3 neighbourhood
-        for (int t = 0; t < 125; t++) {
+        // the wide traversal's 5^3 neighbourhood (only when that traversal is in use)
+        for (int t = 0; t < (wide ? 125 : 0); t++) {
             long long nc = cell_at(rp.g, cx, cy, cz, t % 5 - 2, (t / 5) % 5 - 2, t / 25 - 2);
             mw += st[nc + 1] - st[nc];
         }
@@ -527,7 +527,7 @@ static inline unsigned nblk(long long m, int b) { return (unsigned)((m + b - 1) 
 
 cudaError_t launch_build_cells(const Batch& b, double* x, int* cell_of, int* rank, int* count,
                                int* start, int* perm, double* xl, float* xl32, int* cell_sorted,
-                               int* maxocc, int* status, cudaStream_t st)
+                               int* maxocc, int* status, bool wide, cudaStream_t st)
 {
     const long long n = b.ntot;
     cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * (size_t)b.ncell, st);
@@ -536,7 +536,7 @@ cudaError_t launch_build_cells(const Batch& b, double* x, int* cell_of, int* ran
     k_scan<<<1, 1024, 0, st>>>(b.ncell, count, start, maxocc);
     e = cudaMemsetAsync(maxocc + 1, 0, ATM_NTRAV * sizeof(int), st);
     if (e != cudaSuccess) return e;
-    k_unit_max<<<nblk(b.ncell, MD_BLOCK), MD_BLOCK, 0, st>>>(b, start, maxocc + 1);
+    k_unit_max<<<nblk(b.ncell, MD_BLOCK), MD_BLOCK, 0, st>>>(b, start, wide ? 1 : 0, maxocc + 1);
     if (n > 0) {
         k_scatter<<<nblk(n, MD_BLOCK), MD_BLOCK, 0, st>>>(n, cell_of, rank, start, perm);
         k_cell_sort<<<nblk(b.ncell, MD_BLOCK), MD_BLOCK, 0, st>>>(b.ncell, start, perm);

@@ -44,10 +44,10 @@ constexpr int LJ_BLOCK = 128;
 constexpr int MD_BLOCK = 256;
 
 // maxocc[0] = largest cell occupancy, maxocc[1..5] = largest unit of 3c01, 3c18, 3c08, 3cw,
-// corner-anchored 3c08
+// corner-anchored 3c08 (3cw's only when wide; 0 otherwise)
 cudaError_t launch_build_cells(const Batch& b, double* x, int* cell_of, int* rank, int* count,
                                int* start, int* perm, double* xl, float* xl32, int* cell_sorted,
-                               int* maxocc, int* status, cudaStream_t st);
+                               int* maxocc, int* status, bool wide, cudaStream_t st);
 cudaError_t launch_lj(int prec, const LjArgs<double>& a64, const LjArgs<float>& a32,
                       cudaStream_t st);
 cudaError_t launch_kick(const Batch& b, const int* perm, const double* f_lj, const double* f_atm,

@@ -161,7 +161,7 @@ extern "C" atm_status atm_compute_forces_noalloc(const atm_params* p, int64_t n,
     NA_CU(cudaMemsetAsync(status, 0, sizeof(int), st));
     if (n > 0) NA_CU(launch_check_finite(3 * n, x, status, st));
     NA_CU(launch_build_cells(b, x, cell_of, rank, count, start, perm, xl, xl32, cell_sorted,
-                             maxocc, status, st));
+                             maxocc, status, false, st));
     int hocc[1 + ATM_NTRAV] = {}, hstat = 0;
     NA_CU(cudaMemcpyAsync(hocc, maxocc, sizeof(hocc), cudaMemcpyDeviceToHost, st));
     NA_CU(cudaMemcpyAsync(&hstat, status, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -572,7 +572,9 @@ extern "C" atm_status atm_surrogate_add_frame(atm_ctx* c, atm_traversal trav, at
     SurState* S = state(c);
     if (!S) return ctx_fail(c, ATM_E_CUDA, "out of host memory");
     CU(cudaSetDevice(c->device));
-    atm_status s = reserve_rows(c, S, S->rows + c->n);
+    atm_status s = ctx_want_wide(c, trav);
+    if (s != ATM_OK) return s;
+    s = reserve_rows(c, S, S->rows + c->n);
     if (s != ATM_OK) return s;
     s = ctx_enqueue_forces(c, trav, trunc, prec, c->unit_max[trav]);
     if (s != ATM_OK) return s;
