@@ -19,6 +19,7 @@ struct Grid {
     int nc[3];
     double L[3];
     double w[3];
+    double iw[3];  // 1 / w rounded to nearest (the binning's fast path)
     long long ncell;
 };
 

@@ -19,7 +19,20 @@ using namespace atm3;
 
 namespace {
 constexpr int DENS_MAX_BINS = 4096;
-constexpr int KERNELS_PER_STEP = 10;  // kick, 6 cell kernels, LJ, ATM, kick
+constexpr int CELL_KERNELS = 5;  // wrap/bin, scan, unit sizes, scatter, per-cell order
+
+// steps under the 3c08 (or corner-anchored 3c08) pair rule evaluate LJ inside the ATM units
+static bool lj_fused(int trav, int trunc, int prec)
+{
+    return (trav == ATM_3C08 || trav == ATM_3C08A) && trunc == ATM_TRUNC_PAIR && prec != ATM_SURROGATE;
+}
+
+// kernels of one step: two kicks, the cell build and the force kernels
+static int kernels_per_step(int trav, int trunc, int prec)
+{
+    const int forces = prec == ATM_SURROGATE ? SUR_LAUNCHES : (lj_fused(trav, trunc, prec) ? 1 : 2);
+    return 2 + CELL_KERNELS + forces;
+}
 }  // namespace
 
 
@@ -358,7 +371,7 @@ static atm_status launch_cells(atm_ctx* c)
                           c->xl32, c->cell_sorted, c->d_maxocc, c->d_status, c->wide_cells,
                           c->st));
     ctx_prof_end(c, PK_CELLS, ev);
-    c->n_launch += c->n > 0 ? 6 : 2;
+    c->n_launch += c->n > 0 ? CELL_KERNELS : 2;
     return ATM_OK;
 }
 
@@ -433,8 +446,7 @@ static void launch_choice(const atm_ctx* c, int trav, int trunc, int prec, int& 
 atm_status atm3::ctx_enqueue_forces(atm_ctx* c, int trav, int trunc, int prec, int mcap,
                                     bool fuse_lj)
 {
-    const bool fused = fuse_lj && (trav == ATM_3C08 || trav == ATM_3C08A) && trunc == ATM_TRUNC_PAIR &&
-                       prec != ATM_SURROGATE;
+    const bool fused = fuse_lj && lj_fused(trav, trunc, prec);
     if (trav == ATM_3CW)
         for (const Rep& r : c->reps)
             if (r.g.nc[0] < 5 || r.g.nc[1] < 5 || r.g.nc[2] < 5)
@@ -688,7 +700,7 @@ static atm_status run_graph_steps(atm_ctx* c, int nsteps, int trav, int trunc, i
     cudaEvent_t ev = ctx_prof_begin(c);
     for (int k = 0; k < nsteps; k++) CU(cudaGraphLaunch(c->graph, c->st));
     ctx_prof_end(c, PK_MD, ev);
-    c->n_launch += (long long)nsteps * (KERNELS_PER_STEP + (prec == ATM_SURROGATE ? SUR_LAUNCHES - 2 : 0));
+    c->n_launch += (long long)nsteps * kernels_per_step(trav, trunc, prec);
     c->n_atm += nsteps;
     return ATM_OK;
 }

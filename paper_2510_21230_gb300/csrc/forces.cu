@@ -24,6 +24,7 @@ atm_status make_rep(const atm_params& p, long long n, long long mol0, long long 
         r.g.nc[d] = (int)k;
         r.g.L[d] = L;
         r.g.w[d] = L / k;
+        r.g.iw[d] = 1.0 / r.g.w[d];
         r.wf[d] = (float)r.g.w[d];
         ncell *= (long long)k;
     }

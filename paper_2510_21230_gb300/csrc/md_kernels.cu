@@ -10,19 +10,32 @@ namespace atm3 {
 // ---------------------------------------------------------------- linked cells
 
 // periodic wrap into [0, L): t = x - floor(x/L) L, folded once more if the
-// rounding lands outside [0, L)
+// rounding lands outside [0, L).  A value already in [0, L) comes back
+// unchanged from those steps (x/L rounds to below 1, or to 1 and then
+// x - L and (x - L) + L are exact), so it skips the division.
 __device__ __forceinline__ double wrap1(double x, double L)
 {
+    if (x >= 0.0 && x < L) return x;
     double t = __dsub_rn(x, __dmul_rn(floor(__ddiv_rn(x, L)), L));
     if (t < 0.0) t = __dadd_rn(t, L);
     if (t >= L) t = 0.0;
     return t;
 }
 
-// cell coordinate and clamped cell-local coordinate in [0, w]
-__device__ __forceinline__ int bin1(double t, double w, int n, double& loc)
+// cell coordinate floor(t / w) (correctly rounded quotient) and clamped
+// cell-local coordinate in [0, w].  q = t * (1/w) is within 3 units of 2^-53
+// |t/w| of the rounded quotient, so when no integer lies within 5 units of q
+// both have the same floor and the division is skipped.
+__device__ __forceinline__ int bin1(double t, double w, double iw, int n, double& loc)
 {
-    int c = (int)floor(__ddiv_rn(t, w));
+    const double q = __dmul_rn(t, iw);
+    const double fq = floor(q);
+    const double tol = __dmul_rn(fabs(q), 5.551115123125783e-16);  // 5 * 2^-53
+    int c;
+    if (__dsub_rn(q, fq) > tol && __dsub_rn(__dadd_rn(fq, 1.0), q) > tol)
+        c = (int)fq;
+    else
+        c = (int)floor(__ddiv_rn(t, w));
     c = c > n - 1 ? n - 1 : (c < 0 ? 0 : c);
     double l = __dsub_rn(t, __dmul_rn((double)c, w));
     l = l < 0.0 ? 0.0 : (l > w ? w : l);
@@ -49,7 +62,7 @@ __global__ void k_wrap_bin(Batch B, double* __restrict__ x, int* __restrict__ ce
         double t = wrap1(xv, rp.g.L[d]);
         x[d * n + i] = t;
         double loc;
-        cc[d] = bin1(t, rp.g.w[d], rp.g.nc[d], loc);
+        cc[d] = bin1(t, rp.g.w[d], rp.g.iw[d], rp.g.nc[d], loc);
     }
     int id = (int)rp.cell0 + (cc[2] * rp.g.nc[1] + cc[1]) * rp.g.nc[0] + cc[0];
     cell_of[i] = id;
@@ -159,41 +172,56 @@ __global__ void k_scatter(long long n, const int* __restrict__ cell_of, const in
     perm[start[cell_of[i]] + rank[i]] = (int)i;
 }
 
-// K3b: make the order inside every cell the original index order (stable sort)
-__global__ void k_cell_sort(long long ncell, const int* __restrict__ start, int* __restrict__ perm)
+// K3b+c: one warp per cell restores the original index order inside the cell
+// (the rank of each entry among the cell's entries; lane 0 insertion-sorts a
+// cell of more than 32) and writes, for every sorted slot, the FP64 and FP32
+// cell-local coordinates (t - c w clamped to [0, w], the cell's own c: the
+// binning's arithmetic without its division) and the slot's global cell
+__global__ void __launch_bounds__(128) k_cell_order(Batch B, const double* __restrict__ x,
+                                                    const int* __restrict__ start,
+                                                    int* __restrict__ perm, double* __restrict__ xl,
+                                                    float* __restrict__ xl32,
+                                                    int* __restrict__ cell_sorted)
 {
-    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (c >= ncell) return;
-    int lo = start[c], hi = start[c + 1];
-    for (int a = lo + 1; a < hi; a++) {
-        int v = perm[a];
-        int b = a - 1;
-        while (b >= lo && perm[b] > v) {
-            perm[b + 1] = perm[b];
-            b--;
-        }
-        perm[b + 1] = v;
-    }
-}
-
-// K3c: sorted FP64 and FP32 cell-local coordinates and the global cell of each slot
-__global__ void k_local(Batch B, const double* __restrict__ x, const int* __restrict__ perm,
-                        double* __restrict__ xl, float* __restrict__ xl32,
-                        int* __restrict__ cell_sorted)
-{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const long long c = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (c >= B.ncell) return;  // whole warps leave together
     const long long n = B.ntot;
-    long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    int i = perm[s];
-    const Rep& rp = B.rep[B.rep_of_mol[i]];
-    int cc[3];
-    for (int d = 0; d < 3; d++) {
-        double loc;
-        cc[d] = bin1(x[d * n + i], rp.g.w[d], rp.g.nc[d], loc);
-        xl[d * n + s] = loc;
-        xl32[d * n + s] = (float)loc;
+    const int lo = start[c], hi = start[c + 1], cnt = hi - lo;
+    if (cnt <= 32) {
+        const int v = lane < cnt ? perm[lo + lane] : 0x7fffffff;
+        int r = 0;
+        for (int k = 0; k < cnt; k++) r += __shfl_sync(FULL, v, k) < v ? 1 : 0;
+        __syncwarp();  // every entry is read before any is overwritten
+        if (lane < cnt) perm[lo + r] = v;
+    } else {
+        if (lane == 0)
+            for (int a = lo + 1; a < hi; a++) {
+                const int v = perm[a];
+                int b = a - 1;
+                while (b >= lo && perm[b] > v) {
+                    perm[b + 1] = perm[b];
+                    b--;
+                }
+                perm[b + 1] = v;
+            }
     }
-    cell_sorted[s] = (int)rp.cell0 + (cc[2] * rp.g.nc[1] + cc[1]) * rp.g.nc[0] + cc[0];
+    __syncwarp();
+    const Rep& rp = B.rep[B.rep_of_cell[c]];
+    int cc[3];
+    cell_coords(rp.g, c - rp.cell0, cc[0], cc[1], cc[2]);
+    for (int s = lo + lane; s < hi; s += 32) {
+        const int i = perm[s];
+        for (int d = 0; d < 3; d++) {
+            const double w = rp.g.w[d];
+            double l = __dsub_rn(x[d * n + i], __dmul_rn((double)cc[d], w));
+            l = l < 0.0 ? 0.0 : (l > w ? w : l);
+            xl[d * n + s] = l;
+            xl32[d * n + s] = (float)l;
+        }
+        cell_sorted[s] = (int)c;
+    }
 }
 
 // ---------------------------------------------------------------- LJ pairs
@@ -539,8 +567,8 @@ cudaError_t launch_build_cells(const Batch& b, double* x, int* cell_of, int* ran
     k_unit_max<<<nblk(b.ncell, MD_BLOCK), MD_BLOCK, 0, st>>>(b, start, wide ? 1 : 0, maxocc + 1);
     if (n > 0) {
         k_scatter<<<nblk(n, MD_BLOCK), MD_BLOCK, 0, st>>>(n, cell_of, rank, start, perm);
-        k_cell_sort<<<nblk(b.ncell, MD_BLOCK), MD_BLOCK, 0, st>>>(b.ncell, start, perm);
-        k_local<<<nblk(n, MD_BLOCK), MD_BLOCK, 0, st>>>(b, x, perm, xl, xl32, cell_sorted);
+        k_cell_order<<<(unsigned)((b.ncell + 3) / 4), 128, 0, st>>>(b, x, start, perm, xl, xl32,
+                                                                  cell_sorted);
     }
     return cudaGetLastError();
 }
