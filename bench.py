@@ -491,12 +491,43 @@ def batch_variant(atm3, device, stream, flush, count=64, steps=10, warmup=5):
         ms = sum(a.elapsed_time(c) for a, c in evs)
         res = b.results()
     ntot = int(sum(ns))
+    # the same replicas as 64 separate contexts, each stepped with its own
+    # launches (graph steps too), one after another on the same stream
+    seps = []
+    try:
+        for r in reps:
+            s = atm3.AtmSystem(r["box"], r["n"], rc=RC, nu=NU, dt=0.002, device=device,
+                               stream=stream.cuda_stream)
+            seps.append(s)
+            s.set_state(r["x"], r["v"])
+            s.set_options(graph=True)
+            s.step(warmup, "3c08", "pair", "fp32c")
+        torch.cuda.synchronize()
+        evs = []
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for s in seps:
+                s.step(1, "3c08", "pair", "fp32c", sync=False)
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        ms_sep = sum(a.elapsed_time(c) for a, c in evs)
+    finally:
+        for s in seps:
+            s.close()
     return {"workload": "%d replicas, N log-uniform [500, 20000] (total %d), rho U(0.1, 0.85), "
                         "T U(0.7, 1.3), fcc starts" % (count, ntot),
             "traversal": "3c08", "truncation": "pair", "precision": "fp32c",
             "launch": tuning, "graph": True, "value": ntot * steps / (ms * 1e-3),
             "unit": UNIT, "ms_per_step": ms / steps,
-            "n_int3": int(sum(r["n_int3"] for r in res))}
+            "n_int3": int(sum(r["n_int3"] for r in res)),
+            "separate_contexts": {"ms_per_step": ms_sep / steps,
+                                  "value": ntot * steps / (ms_sep * 1e-3),
+                                  "note": "the same replicas in %d contexts stepped one after "
+                                          "another (graph steps each)" % count}}
 
 
 # ------------------------------------------------------------------ completeness

@@ -326,3 +326,55 @@ def test_surrogate_lj_equals_fp32_lj_kernel(atm3, liquid, liquid_desc):
     assert abs(r2["w2"] - r1["w2"]) <= 1e-6 * abs(r1["w2"])
     sc = np.sqrt(np.mean(f1 ** 2))
     assert np.max(np.abs(f2 - f1)) <= 1e-6 * sc
+
+
+def test_trained_surrogate_gains_over_the_method_without_it(atm3):
+    """What the learned part adds: trained on the GPU (forward and backward
+    kernels, Adam) on exact FP32C ATM forces of 60 frames of the N = 1000
+    liquid, the surrogate reproduces the exact FP64 ATM force of a state it
+    never saw far better than leaving the three-body force out (relative RMS
+    error 1) and than the untrained network, and the surrogate evaluation runs
+    faster than the exact FP64 traversal of the same state."""
+    import torch
+    cfg = synth.config("liquid_n1000")
+    stream = torch.cuda.current_stream()
+    with atm3.AtmSystem(cfg["box"], cfg["n"], rc=RC, nu=NU, dt=0.002,
+                        stream=stream.cuda_stream) as s:
+        s.set_state(cfg["x"], cfg["v"])
+        for _ in range(60):
+            s.step(10, "3c08", "pair", "fp32c")
+            s.surrogate_add_frame("3c08", "pair", "fp32c")
+        s.surrogate_init(seed=1)
+        s.step(100, "3c08", "pair", "fp32c")   # a state outside the training frames
+        s.build_cells()
+        s.compute_forces("3c08", "pair", "fp64")
+        f_exact = s.get_forces("atm")
+        s.compute_forces("3c08", "pair", "surrogate")
+        f_untrained = s.get_forces("atm")
+        s.surrogate_train(1500, batch=4096, lr=2e-3, seed=2)
+        s.surrogate_train(1500, batch=4096, lr=5e-4, seed=3)
+        s.compute_forces("3c08", "pair", "surrogate")
+        f_trained = s.get_forces("atm")
+
+        def ms_per_eval(prec, reps=5):
+            s.compute_forces("3c08", "pair", prec)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                s.compute_forces("3c08", "pair", prec, sync=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / reps
+
+        t_exact = ms_per_eval("fp64")
+        t_sur = ms_per_eval("surrogate")
+
+    def err(f):
+        return np.sqrt(np.mean((f - f_exact) ** 2)) / np.sqrt(np.mean(f_exact ** 2))
+
+    e_tr, e_un = err(f_trained), err(f_untrained)
+    assert e_tr < 0.6, e_tr                 # without the surrogate (no ATM force): error 1.0
+    assert e_tr < 0.7 * e_un, (e_tr, e_un)  # training is what brings it there
+    assert t_sur < t_exact, (t_sur, t_exact)
