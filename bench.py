@@ -143,6 +143,43 @@ def peaks():
         return {}
 
 
+# ------------------------------------------------------------------ per-phase rooflines
+
+# Algorithmic HBM bytes per molecule and step of the memory-bound phases (the
+# minimum each must move, counted from the kernels' loads and stores):
+#  cell build: wrap x in place (24 + 24), cell id and arrival rank (4 + 4),
+#    scatter (reads cell id and rank 8, writes the slot 4), per-cell order and
+#    local coordinates (perm 4 + 4, x 24, FP64 and FP32 local 24 + 12, slot cell 4)
+#  two half kicks: forces 24 (LJ part 24, zero when fused), v 24 + 24, x 24 + 24
+#    (drift, once), kinetic energy 8, perm 4
+CELL_BYTES_PER_MOL = 24 + 24 + 4 + 4 + 8 + 4 + 4 + 4 + 24 + 24 + 12 + 4
+CELL_BYTES_PER_CELL = 4 * 4
+KICK_BYTES_PER_MOL = 2 * (24 + 24 + 24 + 24 + 8 + 4) + (24 + 24)
+
+
+def ncell_of(cfg):
+    from paper_2510_21230_gb300 import atm3
+    return atm3.cell_count(cfg["box"], RC)
+
+
+def kernel_rooflines(prof, steps, n, ncell, atm_roof, pk):
+    """Achieved fraction of the bounding roofline for each phase of a step:
+    the ATM kernel against the FP32 pipe (from `roofline`), the cell build and
+    the kicks against the measured HBM bandwidth (algorithmic bytes)."""
+    hbm = pk.get("hbm_gbs")
+    out = {"atm_triplets": {"bound": "alu", "frac": atm_roof["frac"],
+                            "ms_per_step": prof["ms_atm"] / max(1, prof["n_atm_launches"])}}
+    per_step = max(1, steps)
+    for name, key, nbytes in (("cell_build", "ms_cells", CELL_BYTES_PER_MOL * n + CELL_BYTES_PER_CELL * ncell),
+                              ("kicks_and_reductions", "ms_md", KICK_BYTES_PER_MOL * n)):
+        ms = prof[key] / per_step
+        gbs = nbytes / (ms * 1e-3) / 1e9 if ms > 0 else None
+        out[name] = {"bound": "hbm", "ms_per_step": ms, "bytes_per_step": nbytes,
+                     "achieved_gbs": gbs, "peak_gbs": hbm,
+                     "frac": (gbs / hbm) if (gbs and hbm) else None}
+    return out
+
+
 # ------------------------------------------------------------------ clocks
 
 class ClockSampler:
@@ -444,6 +481,7 @@ def run_ours(args):
             "clocks": main["clocks"],
             "force_error": force_err,
             "profile_ms": {k: prof[k] for k in ("ms_cells", "ms_lj", "ms_atm", "ms_md")},
+            "kernels": kernel_rooflines(prof, args.steps, n, ncell_of(cfg), roofline, pk),
             "counts": {k: int(main["res"][k]) for k in ("n_cand3", "n_int3", "n_cand2", "n_int2")},
             "variants": variants,
             "surrogate": surrogate,

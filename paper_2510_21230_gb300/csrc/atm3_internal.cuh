@@ -6,6 +6,7 @@
 namespace atm3 {
 
 constexpr int ATM_NTRAV = 5;  // 3c01, 3c18, 3c08, 3cw, corner-anchored 3c08
+constexpr int ATM_MAX_DEVICES = 64;  // per-device kernel attribute bookkeeping
 
 // device status word bits (set by kernels, read back by the host)
 enum : int {

@@ -1,5 +1,7 @@
 // FP32 instantiations of the ATM triplet kernels (3c01 and 3cw owner kernel,
 // 3c18 / 3c08 / corner-anchored 3c08 block kernel).
+#include <mutex>
+
 #include "atm_block.cuh"
 #include "atm_owner.cuh"
 
@@ -26,7 +28,28 @@ cudaError_t launch_atm_fp32(int trav, int trunc, const AtmArgs<float>& a, int nw
     return cudaGetLastError();
 }
 
+// the shared-memory limit is an attribute of the kernel for the whole
+// process (per device), so contexts of different unit sizes share it: it is
+// only ever raised, never set below the largest plan any context launched
+static cudaError_t set_attr_fp32(int trav, int trunc, size_t smem);
+
 cudaError_t atm_attr_fp32(int trav, int trunc, size_t smem)
+{
+    static std::mutex mu;
+    static size_t done[ATM_MAX_DEVICES][ATM_NTRAV][2] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= ATM_MAX_DEVICES || trav < 0 || trav >= ATM_NTRAV || trunc < 0 || trunc > 1)
+        return cudaErrorInvalidValue;
+    std::lock_guard<std::mutex> lock(mu);
+    if (smem <= done[dev][trav][trunc]) return cudaSuccess;
+    e = set_attr_fp32(trav, trunc, smem);
+    if (e == cudaSuccess) done[dev][trav][trunc] = smem;
+    return e;
+}
+
+static cudaError_t set_attr_fp32(int trav, int trunc, size_t smem)
 {
     const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
     if (trav == 0 && trunc == 0) return cudaFuncSetAttribute(atm_owner_kernel<0, 0, float>, A, (int)smem);

@@ -453,8 +453,8 @@ __global__ void __launch_bounds__(128) k_rdf(Batch B, const double* __restrict__
 
 // Two-level reduction in a fixed order (reproducible scalars).  Level 1: CTA
 // (r, k) sums the k-th of REDUCE_PARTS equal slices of replica r's units and
-// molecules (thread-strided, then a fixed tree).  Level 2: one thread per
-// replica adds the REDUCE_PARTS partial sums in order.
+// molecules (thread-strided, then a fixed tree).  Level 2: one warp per
+// replica adds the REDUCE_PARTS partial sums in a fixed tree.
 __global__ void __launch_bounds__(256) k_partial_reduce(ReduceArgs R)
 {
     __shared__ double sd[5][256];
@@ -513,25 +513,45 @@ __global__ void __launch_bounds__(256) k_partial_reduce(ReduceArgs R)
     }
 }
 
-__global__ void k_final_reduce(ReduceArgs R)
+// one warp per replica: lane k holds partials k and k + 32 (added in that
+// order), then a fixed shuffle tree; the order is the same for every launch
+__global__ void __launch_bounds__(128) k_final_reduce(ReduceArgs R)
 {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= R.b.R) return;
-    ResultDev t{};
-    for (int k = 0; k < REDUCE_PARTS; k++) {
-        const ResultDev& p = R.part[r * REDUCE_PARTS + k];
-        t.e2 += p.e2;
-        t.e3 += p.e3;
-        t.w2 += p.w2;
-        t.w3 += p.w3;
-        t.ekin += p.ekin;
-        t.n_cand3 += p.n_cand3;
-        t.n_int3 += p.n_int3;
-        t.n_cand2 += p.n_cand2;
-        t.n_int2 += p.n_int2;
+    static_assert(REDUCE_PARTS == 64, "two partials per lane");
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (r >= R.b.R) return;  // whole warps leave together
+    const ResultDev& a = R.part[r * REDUCE_PARTS + lane];
+    const ResultDev& b = R.part[r * REDUCE_PARTS + 32 + lane];
+    double e2 = a.e2 + b.e2, e3 = a.e3 + b.e3, w2 = a.w2 + b.w2, w3 = a.w3 + b.w3;
+    double ek = a.ekin + b.ekin;
+    unsigned long long c3 = a.n_cand3 + b.n_cand3, i3 = a.n_int3 + b.n_int3;
+    unsigned long long c2 = a.n_cand2 + b.n_cand2, i2 = a.n_int2 + b.n_int2;
+    for (int o = 16; o > 0; o >>= 1) {
+        e2 += __shfl_down_sync(FULL, e2, o);
+        e3 += __shfl_down_sync(FULL, e3, o);
+        w2 += __shfl_down_sync(FULL, w2, o);
+        w3 += __shfl_down_sync(FULL, w3, o);
+        ek += __shfl_down_sync(FULL, ek, o);
+        c3 += __shfl_down_sync(FULL, c3, o);
+        i3 += __shfl_down_sync(FULL, i3, o);
+        c2 += __shfl_down_sync(FULL, c2, o);
+        i2 += __shfl_down_sync(FULL, i2, o);
     }
-    t.n_int2 /= 2;  // each pair was visited from both ends
-    R.out[r] = t;
+    if (lane == 0) {
+        ResultDev t;
+        t.e2 = e2;
+        t.e3 = e3;
+        t.w2 = w2;
+        t.w3 = w3;
+        t.ekin = ek;
+        t.n_cand3 = c3;
+        t.n_int3 = i3;
+        t.n_cand2 = c2;
+        t.n_int2 = i2 / 2;  // each pair was visited from both ends
+        R.out[r] = t;
+    }
 }
 
 // gather sorted-order forces to the original order: which 0 total, 1 LJ, 2 ATM
@@ -618,7 +638,7 @@ cudaError_t launch_check_finite(long long m, const double* a, int* status, cudaS
 cudaError_t launch_final_reduce(const ReduceArgs& r, cudaStream_t st)
 {
     k_partial_reduce<<<(unsigned)(r.b.R * REDUCE_PARTS), 256, 0, st>>>(r);
-    k_final_reduce<<<nblk(r.b.R, 128), 128, 0, st>>>(r);
+    k_final_reduce<<<(unsigned)((r.b.R + 3) / 4), 128, 0, st>>>(r);
     return cudaGetLastError();
 }
 

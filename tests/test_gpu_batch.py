@@ -160,3 +160,25 @@ def test_density_profile_is_the_histogram_of_wrapped_positions(atm3):
     assert samples == 1
     assert np.array_equal(counts[0].astype(np.int64), ref)
     assert counts.sum() == cfg["n"]
+
+
+def test_contexts_of_different_unit_sizes_interleave(atm3):
+    """Contexts in one process share the kernels' shared-memory limit: a
+    context with small units launched after one with large units must not
+    lower it under the large one's next launch (steps and graph steps)."""
+    big = synth.homogeneous(4000, 0.95, 1.0, seed=1200)
+    small = synth.homogeneous(600, 0.3, 1.0, seed=1201)
+    with atm3.AtmSystem(big["box"], big["n"], nu=NU) as a, \
+            atm3.AtmSystem(small["box"], small["n"], nu=NU) as b:
+        a.set_state(big["x"], big["v"])
+        b.set_state(small["x"], small["v"])
+        for prec in ("fp32c", "fp64"):
+            ra = a.step(2, "3c08", "pair", prec)
+            rb = b.step(2, "3c08", "pair", prec)
+            ra2 = a.step(2, "3c08", "pair", prec)
+            assert ra["n_int3"] > 0 and rb["n_int3"] > 0 and ra2["n_int3"] > 0
+        a.set_options(graph=True)
+        b.set_options(graph=True)
+        for _ in range(2):
+            a.step(3, "3c08", "pair", "fp32c")
+            b.step(3, "3c08", "pair", "fp32c")
