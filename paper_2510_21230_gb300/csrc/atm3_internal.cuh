@@ -238,8 +238,9 @@ __host__ __device__ inline BlockSmem block_smem_plan(int trunc, int mcap, int nw
 
 // Launch configuration of the ATM kernels for units of at most mcap molecules.
 // 3c01: 4 warps.  3c18/3c08 pair rule: 4 warps (FP32) or 8 (FP64) and pair
-// scalars for 20 edges per molecule (a liquid has about 15), halved until
-// they fit (a unit with more edges falls back to per-molecule accumulators);
+// scalars for 16 edges per staged molecule of the largest unit (the rho* =
+// 0.8 liquids have at most 14.4 (256k) and 15.9 (32k)), halved until they
+// fit (a unit with more edges falls back to per-molecule accumulators);
 // product rule: 8 warps,
 // dense distances + dense pair scalars, else dense pair scalars only, else
 // per-molecule accumulators.  Returns false if nothing fits.
@@ -286,7 +287,7 @@ inline bool atm_choose_plan_nw(int trav, int trunc, int prec, int mcap, int opti
     }
     const long long npair = (long long)mcap * (mcap - 1) / 2;
     if (trunc == 0) {
-        long long g = npair < 20ll * mcap ? npair : 20ll * mcap;
+        long long g = npair < 16ll * mcap ? npair : 16ll * mcap;
         for (;;) {
             P.gcap = (int)g;
             P.smem = bytes();

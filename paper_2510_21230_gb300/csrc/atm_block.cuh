@@ -856,8 +856,12 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
 
 // One CTA per unit, or (A.work set) a persistent grid whose CTAs take units
 // from a global counter until all units of the batch are done.
+// FP32: at most 56 registers, so that 9 CTAs of 4 warps fit an SM (with the
+// 16-edge-per-molecule pair-scalar table, 9 also fit its shared memory at the
+// rho* = 0.8 cell occupancy); FP64: 2 CTAs of 8 warps
 template <int TRAV, int TRUNC, typename R>
-__global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : 4) atm_block_kernel(const AtmArgs<R> A)
+__global__ void __launch_bounds__(256) __maxnreg__(sizeof(R) == 8 ? 128 : 56)
+    atm_block_kernel(const AtmArgs<R> A)
 {
     if (A.work == nullptr) {
         atm_block_unit<TRAV, TRUNC, R>(A, blockIdx.x);
