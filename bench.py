@@ -396,6 +396,12 @@ def run_ours(args):
     if not args.no_variants and rank == 0:
         completeness = completeness_variant(atm3, local, stream)
 
+    # the paper's own runtime workload (its node-level table): all six
+    # traversal / truncation combinations, three-body force time only
+    paper_table = None
+    if not args.no_variants and rank == 0:
+        paper_table = paper_table_variant(atm3, local, stream)
+
     # learned surrogate: trained on exact forces of smaller liquids, then
     # timed and checked on this workload's state
     surrogate = None
@@ -488,6 +494,7 @@ def run_ours(args):
             "batch": batch,
             "slab": slab,
             "product_completeness": completeness,
+            "paper_runtime_workload": paper_table,
         }
         print(json.dumps(line))
     sysm.close()
@@ -569,6 +576,53 @@ def batch_variant(atm3, device, stream, flush, count=64, steps=10, warmup=5):
 
 
 # ------------------------------------------------------------------ completeness
+
+# The paper's runtime table (section 5.3): 10 iterations of the three-body
+# force computation on 64 cores of an AMD EPYC 7763, per traversal and cutoff
+# (seconds), for the workload below; context only (another machine and a CPU).
+PAPER_RUNTIME_64C = {("3c01", "product"): 18.3553, ("3c01", "pair"): 12.7049,
+                     ("3c18", "product"): 3.8193, ("3c18", "pair"): 2.5725,
+                     ("3c08", "product"): 2.0499, ("3c08", "pair"): 1.3221}
+
+
+def paper_table_variant(atm3, device, stream, iters=10):
+    """The paper's runtime workload: N = 37,000 in a cubic box of edge 37.5
+    (rho* = 0.70, 15^3 cells), simple cubic start, T* = 1.2, r_c = 2.5; for
+    every traversal and cutoff, `iters` velocity-Verlet steps with the ATM
+    kernel's own time of a force evaluation at each visited state (the
+    paper's time counts the three-body forces only).  Three-body molecule
+    updates/s = N iters / time, FP64 and FP32C, beside the paper's 64-core
+    figure."""
+    n, box = 37000, 37.5
+    rng = np.random.default_rng(7100)
+    x = synth.simple_cubic_positions(n, box, rng)
+    v = synth.maxwell_boltzmann(n, 1.2, rng)
+    out = {"workload": "N=37000, box 37.5 (rho 0.70, 15^3 cells), simple cubic start, T 1.2, "
+                       "%d iterations" % iters, "unit": UNIT, "rows": []}
+    for trav in ("3c01", "3c18", "3c08"):
+        for trunc in ("product", "pair"):
+            row = {"traversal": trav, "truncation": trunc}
+            for prec in ("fp64", "fp32c"):
+                with atm3.AtmSystem(box, n, rc=RC, nu=NU, dt=0.002, device=device,
+                                    stream=stream.cuda_stream) as s:
+                    s.set_state(x, v)
+                    s.build_cells()
+                    s.compute_forces(trav, trunc, prec)  # warm-up
+                    ms = 0.0
+                    for _ in range(iters):
+                        s.step(1, trav, trunc, prec)
+                        s.set_profiling(True)
+                        s.compute_forces(trav, trunc, prec)
+                        prof = s.get_profile()
+                        s.set_profiling(False)
+                        ms += prof["ms_atm"]
+                row[prec] = {"ms_per_iteration": ms / iters,
+                             "value": n * iters / (ms * 1e-3)}
+            t64 = PAPER_RUNTIME_64C[(trav, trunc)]
+            row["paper_64_cores"] = {"s_per_10_iterations": t64, "value": n * 10 / t64}
+            out["rows"].append(row)
+    return out
+
 
 def completeness_variant(atm3, device, stream, workload="liquid_n32k"):
     """Product rule on the N = 32,000 liquid: interacting triplets found by the
