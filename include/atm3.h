@@ -359,6 +359,18 @@ atm_status atm_surrogate_options(atm_ctx* ctx, int exact_every);
 atm_status atm_surrogate_error(atm_ctx* ctx, double* rms_diff, double* rms_exact,
                                int64_t* checks, int reset);
 
+/* Give the total force of the state just set (host memory, f[3n], original
+ * order, as atm_get_forces(..., 0) returns it) as computed with (trav, trunc,
+ * prec): the next atm_step with that combination uses it for its first half
+ * kick instead of evaluating the forces of the state again -- velocity
+ * Verlet carries the force with the state, so a caller that keeps the state
+ * on the host between steps keeps it too.  Must follow atm_set_state (which
+ * forgets it); the library does not check that it belongs to the state.
+ * Errors: INVALID (surrogate or unknown combination, NULL), STATE (no state),
+ * NONFINITE, CUDA. */
+atm_status atm_set_forces(atm_ctx* ctx, const double* f, atm_traversal trav, atm_truncation trunc,
+                          atm_precision prec);
+
 /* Velocity-rescaling thermostat for the NVT runs of section 5.1 (the paper
  * names no thermostat): the velocities of replica r are scaled by
  * sqrt(T_r (3 N_r - 3) / (2 K_r)) so that its kinetic temperature

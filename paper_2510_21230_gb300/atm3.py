@@ -35,7 +35,7 @@ EXPORTED = ["atm_abi_version", "atm_create", "atm_batch_create", "atm_batch_size
             "atm_surrogate_add_rows", "atm_surrogate_dataset", "atm_surrogate_clear",
             "atm_surrogate_train", "atm_surrogate_options", "atm_surrogate_error",
             "atm_measure_fma_peak", "atm_rdf_accumulate", "atm_rdf_get", "atm_rdf_reset",
-            "atm_lj_tail", "atm_thermostat", "atm_measure_rsqrt_peak"]
+            "atm_lj_tail", "atm_thermostat", "atm_measure_rsqrt_peak", "atm_set_forces"]
 
 SUR_NDESC, SUR_NVEC, SUR_NPARAM = 32, 9, 6467
 
@@ -140,6 +140,7 @@ def load():
         "atm_lj_tail": [ctypes.POINTER(Params), i64, P, P],
         "atm_thermostat": [P, P],
         "atm_measure_rsqrt_peak": [i32, P],
+        "atm_set_forces": [P, P, i32, i32, i32],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -263,6 +264,14 @@ class AtmSystem:
             assert v.shape == (3, self.n)
             vp = _host_ptr(v)
         self._check(self._lib.atm_set_state(self._ctx, _host_ptr(x), vp))
+
+    def set_forces(self, f, trav="3c08", trunc="pair", prec="fp32c"):
+        """Total force of the state just set (original order), as computed with
+        (trav, trunc, prec): the next step with that combination starts from it."""
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        assert f.shape == (3, self.n)
+        self._check(self._lib.atm_set_forces(self._ctx, _host_ptr(f), TRAVERSALS[trav],
+                                             TRUNCATIONS[trunc], PRECISIONS[prec]))
 
     def get_state(self, x=None, v=None):
         x = np.zeros((3, self.n)) if x is None else x

@@ -107,7 +107,7 @@ static void free_all(atm_ctx* c)
                    c->xl32, c->cell_of, c->rank, c->count, c->start, c->perm, c->cell_sorted,
                    c->f_lj, c->f_atm, c->f_out, c->unit_ew, c->unit_cnt, c->mol_ew, c->mol_cnt,
                    c->ke, c->d_res, c->d_part, c->d_status, c->d_maxocc, c->d_work, c->d_dens,
-                   c->d_rdf, c->d_ttarget, c->unit_ew2, c->unit_cnt2};
+                   c->d_rdf, c->d_ttarget, c->unit_ew2, c->unit_cnt2, c->f_in};
     for (void* p : dev)
         if (p) cudaFree(p);
     if (c->h_res) cudaFreeHost(c->h_res);
@@ -209,6 +209,7 @@ extern "C" atm_status atm_batch_create(const atm_params* params, const int64_t* 
     ok = ok && alloc((void**)&c->f_lj, 3 * N * sizeof(double));
     ok = ok && alloc((void**)&c->f_atm, 3 * N * sizeof(double));
     ok = ok && alloc((void**)&c->f_out, 3 * N * sizeof(double));
+    ok = ok && alloc((void**)&c->f_in, 3 * N * sizeof(double));
     ok = ok && alloc((void**)&c->unit_ew, 2 * NC * sizeof(double));
     ok = ok && alloc((void**)&c->unit_cnt, 2 * NC * sizeof(unsigned long long));
     ok = ok && alloc((void**)&c->unit_ew2, 2 * NC * sizeof(double));
@@ -299,6 +300,7 @@ static void invalidate(atm_ctx* c)
 {
     c->cells_built = false;
     c->forces_valid = false;
+    c->f_in_valid = false;
 }
 
 // true when no element is NaN or infinite (exponent field all ones); a
@@ -717,8 +719,24 @@ extern "C" atm_status atm_step(atm_ctx* c, int nsteps, atm_traversal trav, atm_t
     if (s != ATM_OK) return s;
     // forces of the current state from this combination (for the surrogate, the
     // exact FP32C forces of an interleaved step serve as well)
-    const bool fresh = c->forces_valid && c->f_trav == trav && c->f_trunc == trunc &&
-                       (c->f_prec == prec || (prec == ATM_SURROGATE && c->f_prec == ATM_FP32C));
+    bool fresh = c->forces_valid && c->f_trav == trav && c->f_trunc == trunc &&
+                 (c->f_prec == prec || (prec == ATM_SURROGATE && c->f_prec == ATM_FP32C));
+    if (!fresh && nsteps > 0 && c->f_in_valid && c->f_in_key[0] == trav &&
+        c->f_in_key[1] == trunc && c->f_in_key[2] == prec) {
+        // the caller gave the forces of this state: the first step's half kick
+        // and drift use them, then the step continues as usual
+        CU(launch_kick_orig(c->b, c->f_in, c->x, c->v, c->ke, c->st));
+        c->n_launch += 1;
+        c->f_in_valid = false;
+        s = enqueue_cells(c);
+        if (s != ATM_OK) return s;
+        s = ctx_enqueue_forces(c, trav, trunc, prec, c->unit_max[trav], true);
+        if (s != ATM_OK) return s;
+        CU(launch_kick(c->b, c->perm, c->f_lj, c->f_atm, c->x, c->v, 0, c->ke, c->st));
+        c->n_launch += 1;
+        nsteps -= 1;
+        fresh = true;
+    }
     if (!fresh) {
         s = enqueue_cells(c);
         if (s != ATM_OK) return s;
@@ -902,6 +920,25 @@ extern "C" atm_status atm_density_reset(atm_ctx* c)
     c->dens_samples = 0;
     c->dens_axis = -1;
     c->dens_nbins = 0;
+    return ATM_OK;
+}
+
+extern "C" atm_status atm_set_forces(atm_ctx* c, const double* f, atm_traversal trav,
+                                     atm_truncation trunc, atm_precision prec)
+{
+    if (!c) return ATM_E_INVALID;
+    if (!valid_enums(trav, trunc, prec) || prec == ATM_SURROGATE)
+        return ctx_fail(c, ATM_E_INVALID, "set_forces needs an exact traversal, truncation, precision");
+    if (!f && c->n > 0) return ctx_fail(c, ATM_E_INVALID, "forces are required");
+    if (!c->have_x) return ctx_fail(c, ATM_E_STATE, "set the state before its forces");
+    const long long m = 3 * c->n;
+    if (!all_finite(f, m)) return ctx_fail(c, ATM_E_NONFINITE, "non-finite force");
+    CU(cudaSetDevice(c->device));
+    if (m > 0) CU(cudaMemcpyAsync(c->f_in, f, (size_t)m * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    c->f_in_valid = true;
+    c->f_in_key[0] = trav;
+    c->f_in_key[1] = trunc;
+    c->f_in_key[2] = prec;
     return ATM_OK;
 }
 

@@ -69,6 +69,11 @@ struct atm_ctx {
     int f_trav = -1, f_trunc = -1, f_prec = -1;
     bool f_fused = false;  // the current forces came from units that also did LJ
     bool wide_cells = false;  // cell builds also size the wide traversal's 5^3 units
+    // forces of the current state given by the caller (original order, total),
+    // for the combination f_in_key = (traversal, truncation, precision)
+    double* f_in = nullptr;
+    bool f_in_valid = false;
+    int f_in_key[3] = {-1, -1, -1};
     size_t smem_set[2][atm3::ATM_NTRAV][2] = {};
     int smem_optin = 0, sms = 0;
     // launch options: persistent ATM grid, warps per block-kernel CTA (0 =

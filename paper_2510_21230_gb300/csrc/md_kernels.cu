@@ -1,5 +1,5 @@
 // md_kernels.cu -- linked-cell build, LJ pair forces, velocity-Verlet update,
-// density profile and the deterministic per-replica reductions.
+// density profile and the per-replica reductions (in a fixed order).
 // Every kernel works on a batch of replicas (a single system is a batch of
 // one): per-molecule threads look their replica up in rep_of_mol, per-cell
 // threads in rep_of_cell.
@@ -347,6 +347,27 @@ __global__ void __launch_bounds__(256) k_kick(Batch B, const int* __restrict__ p
     ke[i] = k;
 }
 
+// the first half kick and the drift from a total force given in the
+// original molecule order (a state restored with its forces)
+__global__ void __launch_bounds__(256) k_kick_orig(Batch B, const double* __restrict__ f,
+                                                   double* __restrict__ x, double* __restrict__ v,
+                                                   double* __restrict__ ke)
+{
+    const long long n = B.ntot;
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const Rep& rp = B.rep[B.rep_of_mol[i]];
+    const double dt = rp.dt, half_dt = 0.5 * rp.dt;
+    double k = 0.0;
+    for (int d = 0; d < 3; d++) {
+        double vv = __dadd_rn(v[d * n + i], __dmul_rn(half_dt, f[d * n + i]));
+        v[d * n + i] = vv;
+        x[d * n + i] = __dadd_rn(x[d * n + i], __dmul_rn(dt, vv));
+        k += 0.5 * vv * vv;
+    }
+    ke[i] = k;
+}
+
 // kinetic energy per molecule only (no update)
 __global__ void __launch_bounds__(256) k_kinetic(long long n, const double* __restrict__ v,
                                                  double* __restrict__ ke)
@@ -451,7 +472,7 @@ __global__ void __launch_bounds__(128) k_rdf(Batch B, const double* __restrict__
 
 // ---------------------------------------------------------------- reductions
 
-// Two-level reduction in a fixed order (reproducible scalars).  Level 1: CTA
+// Two-level reduction in a fixed order (the same sums for the same partials).  Level 1: CTA
 // (r, k) sums the k-th of REDUCE_PARTS equal slices of replica r's units and
 // molecules (thread-strided, then a fixed tree).  Level 2: one warp per
 // replica adds the REDUCE_PARTS partial sums in a fixed tree.
@@ -610,6 +631,14 @@ cudaError_t launch_kick(const Batch& b, const int* perm, const double* f_lj, con
 {
     if (b.ntot <= 0) return cudaSuccess;
     k_kick<<<nblk(b.ntot, MD_BLOCK), MD_BLOCK, 0, st>>>(b, perm, f_lj, f_atm, x, v, drift, ke);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kick_orig(const Batch& b, const double* f, double* x, double* v, double* ke,
+                             cudaStream_t st)
+{
+    if (b.ntot <= 0) return cudaSuccess;
+    k_kick_orig<<<nblk(b.ntot, MD_BLOCK), MD_BLOCK, 0, st>>>(b, f, x, v, ke);
     return cudaGetLastError();
 }
 

@@ -53,6 +53,9 @@ cudaError_t launch_lj(int prec, const LjArgs<double>& a64, const LjArgs<float>& 
 cudaError_t launch_kick(const Batch& b, const int* perm, const double* f_lj, const double* f_atm,
                         double* x, double* v, int drift, double* ke, cudaStream_t st);
 cudaError_t launch_kinetic(long long n, const double* v, double* ke, cudaStream_t st);
+// first half kick + drift with a total force in the original order
+cudaError_t launch_kick_orig(const Batch& b, const double* f, double* x, double* v, double* ke,
+                             cudaStream_t st);
 // v *= sqrt(T_r (3 N_r - 3) / (2 K_r)) per replica (K_r = res[r].ekin)
 cudaError_t launch_rescale(const Batch& b, double* v, double* ke, const ResultDev* res,
                            const double* t_target, cudaStream_t st);

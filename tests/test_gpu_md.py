@@ -127,3 +127,57 @@ def test_fused_batch_step_equals_oracle_energies(atm3):
         assert res[r]["e2"] == pytest.approx(e2, rel=1e-9), r
         assert res[r]["e3"] == pytest.approx(e3, rel=1e-9), r
         assert res[r]["ekin"] == pytest.approx(ek, rel=1e-9), r
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_host_round_trips_with_forces_equal_continuous_steps(atm3, prec):
+    """A caller that keeps the state on the host between steps gives the
+    state's force back with it (atm_set_forces): each step then evaluates the
+    forces once, and the run follows the continuous device run (to the
+    rounding of the force sums, whose atomic accumulation order varies from
+    evaluation to evaluation)."""
+    cfg = synth.homogeneous(2000, 0.8, 1.0, seed=1300)
+    with atm3.AtmSystem(cfg["box"], cfg["n"], nu=NU, dt=0.002) as a:
+        a.set_state(cfg["x"], cfg["v"])
+        a.step(0, "3c08", "pair", prec)
+        ra = a.step(4, "3c08", "pair", prec)
+        xa, va = a.get_state()
+    with atm3.AtmSystem(cfg["box"], cfg["n"], nu=NU, dt=0.002) as b:
+        b.set_state(cfg["x"], cfg["v"])
+        b.step(0, "3c08", "pair", prec)
+        x, v = b.get_state()          # wrapped by the cell build, as on the device
+        f = b.get_forces("total")
+        for _ in range(4):
+            b.set_state(x, v)
+            b.set_forces(f, "3c08", "pair", prec)
+            rb = b.step(1, "3c08", "pair", prec)
+            x, v = b.get_state()
+            f = b.get_forces("total")
+        with pytest.raises(atm3.AtmError):
+            b.set_forces(f, "3c08", "pair", "surrogate")
+    tol = {"fp64": (1e-12, 1e-12, 1e-10), "fp32c": (1e-9, 1e-7, 1e-6)}[prec]
+    d = x - xa
+    d -= np.rint(d / cfg["box"][:, None]) * cfg["box"][:, None]
+    assert np.abs(d).max() <= tol[0]
+    assert np.abs(v - va).max() <= tol[1]
+    for k in ("n_int3", "n_int2"):
+        assert rb[k] == ra[k], k
+    for k in ("e2", "e3", "ekin"):
+        assert rb[k] == pytest.approx(ra[k], rel=tol[2]), k
+
+
+def test_forces_are_forgotten_with_a_new_state(atm3):
+    cfg = synth.homogeneous(1000, 0.8, 1.0, seed=1301)
+    with atm3.AtmSystem(cfg["box"], cfg["n"], nu=NU) as s:
+        with pytest.raises(atm3.AtmError):
+            s.set_forces(np.zeros((3, cfg["n"])))       # no state yet
+        s.set_state(cfg["x"], cfg["v"])
+        s.set_forces(np.zeros((3, cfg["n"])), "3c08", "pair", "fp32c")
+        s.set_state(cfg["x"], cfg["v"])                 # forgets the forces above
+        r1 = s.step(1, "3c08", "pair", "fp32c")
+    with atm3.AtmSystem(cfg["box"], cfg["n"], nu=NU) as t:
+        t.set_state(cfg["x"], cfg["v"])
+        r2 = t.step(1, "3c08", "pair", "fp32c")
+    # zero forces in the first half kick would change the kinetic energy by far more
+    assert r1["e3"] == pytest.approx(r2["e3"], rel=1e-6)
+    assert r1["ekin"] == pytest.approx(r2["ekin"], rel=1e-9)
