@@ -132,7 +132,9 @@ const char* atm_last_error(const atm_ctx* ctx);
 int atm_abi_version(void);
 
 /* Set positions x[3n] (any real values; wrapped into the box by
- * atm_build_cells) and velocities v[3n] (NULL = zero) from host memory.
+ * atm_build_cells) and velocities v[3n] (NULL = zero) from host memory.  The
+ * copies are checked for NaN / Inf on the device; the call synchronises the
+ * stream, so the caller may reuse its buffers on return.
  * Errors: INVALID, NONFINITE, CUDA. */
 atm_status atm_set_state(atm_ctx* ctx, const double* x, const double* v);
 /* Same from device memory (x_dev required, v_dev may be NULL).  The values

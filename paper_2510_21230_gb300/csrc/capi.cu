@@ -107,11 +107,12 @@ static void free_all(atm_ctx* c)
                    c->xl32, c->cell_of, c->rank, c->count, c->start, c->perm, c->cell_sorted,
                    c->f_lj, c->f_atm, c->f_out, c->unit_ew, c->unit_cnt, c->mol_ew, c->mol_cnt,
                    c->ke, c->d_res, c->d_part, c->d_status, c->d_maxocc, c->d_work, c->d_dens,
-                   c->d_rdf, c->d_ttarget, c->unit_ew2, c->unit_cnt2, c->f_in};
+                   c->d_rdf, c->d_ttarget, c->unit_ew2, c->unit_cnt2, c->f_in, c->d_chk};
     for (void* p : dev)
         if (p) cudaFree(p);
     if (c->h_res) cudaFreeHost(c->h_res);
     if (c->h_status) cudaFreeHost(c->h_status);
+    if (c->h_chk) cudaFreeHost(c->h_chk);
     if (c->h_maxocc) cudaFreeHost(c->h_maxocc);
     if (c->cap_st) cudaStreamDestroy(c->cap_st);
     for (auto& r : c->ev_live) {
@@ -210,6 +211,7 @@ extern "C" atm_status atm_batch_create(const atm_params* params, const int64_t* 
     ok = ok && alloc((void**)&c->f_atm, 3 * N * sizeof(double));
     ok = ok && alloc((void**)&c->f_out, 3 * N * sizeof(double));
     ok = ok && alloc((void**)&c->f_in, 3 * N * sizeof(double));
+    ok = ok && alloc((void**)&c->d_chk, sizeof(int));
     ok = ok && alloc((void**)&c->unit_ew, 2 * NC * sizeof(double));
     ok = ok && alloc((void**)&c->unit_cnt, 2 * NC * sizeof(unsigned long long));
     ok = ok && alloc((void**)&c->unit_ew2, 2 * NC * sizeof(double));
@@ -227,6 +229,7 @@ extern "C" atm_status atm_batch_create(const atm_params* params, const int64_t* 
     ok = ok && alloc((void**)&c->d_ttarget, nrep * sizeof(double));
     ok = ok && cudaMallocHost((void**)&c->h_res, nrep * sizeof(ResultDev)) == cudaSuccess;
     ok = ok && cudaMallocHost((void**)&c->h_status, sizeof(int)) == cudaSuccess;
+    ok = ok && cudaMallocHost((void**)&c->h_chk, sizeof(int)) == cudaSuccess;
     ok = ok && cudaMallocHost((void**)&c->h_maxocc, (1 + ATM_NTRAV) * sizeof(int)) == cudaSuccess;
     ok = ok && cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin,
                                       c->device) == cudaSuccess;
@@ -303,17 +306,21 @@ static void invalidate(atm_ctx* c)
     c->f_in_valid = false;
 }
 
-// true when no element is NaN or infinite (exponent field all ones); a
-// branch-free OR over the bit patterns, which the host compiler vectorises
-static bool all_finite(const double* a, long long m)
+// copies m doubles from host memory to dev and checks them for NaN / Inf on
+// the device (the copy's data, one pass); synchronises, so the caller may
+// reuse its buffer on return.  *bad: a non-finite element was found
+static atm_status copy_in_checked(atm_ctx* c, double* dev, const double* host, long long m, bool* bad)
 {
-    uint64_t bad = 0;
-    for (long long i = 0; i < m; i++) {
-        uint64_t u;
-        memcpy(&u, a + i, sizeof(u));
-        bad |= (uint64_t)((~u & 0x7ff0000000000000ull) == 0);
-    }
-    return bad == 0;
+    *bad = false;
+    if (m <= 0) return ATM_OK;
+    CU(cudaMemcpyAsync(dev, host, (size_t)m * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    CU(cudaMemsetAsync(c->d_chk, 0, sizeof(int), c->st));
+    CU(launch_check_finite(m, dev, c->d_chk, c->st));
+    c->n_launch += 1;
+    CU(cudaMemcpyAsync(c->h_chk, c->d_chk, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    CU(cudaStreamSynchronize(c->st));
+    *bad = *c->h_chk != 0;
+    return ATM_OK;
 }
 
 extern "C" atm_status atm_set_state(atm_ctx* c, const double* x, const double* v)
@@ -322,25 +329,22 @@ extern "C" atm_status atm_set_state(atm_ctx* c, const double* x, const double* v
     if (!x && c->n > 0) return ctx_fail(c, ATM_E_INVALID, "positions are required");
     CU(cudaSetDevice(c->device));
     const long long m = 3 * c->n;
-    size_t bytes = (size_t)m * sizeof(double);
-    // start the copies first; the host checks the same buffers meanwhile
-    if (bytes) {
-        CU(cudaMemcpyAsync(c->x, x, bytes, cudaMemcpyHostToDevice, c->st));
-        if (v)
-            CU(cudaMemcpyAsync(c->v, v, bytes, cudaMemcpyHostToDevice, c->st));
-        else
-            CU(cudaMemsetAsync(c->v, 0, bytes, c->st));
+    bool bx = false, bv = false;
+    atm_status s = copy_in_checked(c, c->x, x, m, &bx);
+    if (s != ATM_OK) return s;
+    if (v) {
+        s = copy_in_checked(c, c->v, v, m, &bv);
+        if (s != ATM_OK) return s;
+    } else if (m > 0) {
+        CU(cudaMemsetAsync(c->v, 0, (size_t)m * sizeof(double), c->st));
     }
-    if (!all_finite(x, m) || (v && !all_finite(v, m))) {
+    c->have_x = !(bx || bv);
+    invalidate(c);
+    if (bx || bv) {
         long long q = 0;
         while (q < m && std::isfinite(x[q]) && (!v || std::isfinite(v[q]))) q++;
-        c->have_x = false;
-        invalidate(c);
-        CU(cudaStreamSynchronize(c->st));  // the caller may reuse its buffers at once
         return ctx_fail(c, ATM_E_NONFINITE, "non-finite input at element %lld", q);
     }
-    c->have_x = true;
-    invalidate(c);
     return ATM_OK;
 }
 
@@ -931,10 +935,14 @@ extern "C" atm_status atm_set_forces(atm_ctx* c, const double* f, atm_traversal 
         return ctx_fail(c, ATM_E_INVALID, "set_forces needs an exact traversal, truncation, precision");
     if (!f && c->n > 0) return ctx_fail(c, ATM_E_INVALID, "forces are required");
     if (!c->have_x) return ctx_fail(c, ATM_E_STATE, "set the state before its forces");
-    const long long m = 3 * c->n;
-    if (!all_finite(f, m)) return ctx_fail(c, ATM_E_NONFINITE, "non-finite force");
     CU(cudaSetDevice(c->device));
-    if (m > 0) CU(cudaMemcpyAsync(c->f_in, f, (size_t)m * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    bool bad = false;
+    atm_status s = copy_in_checked(c, c->f_in, f, 3 * c->n, &bad);
+    if (s != ATM_OK) return s;
+    if (bad) {
+        c->f_in_valid = false;
+        return ctx_fail(c, ATM_E_NONFINITE, "non-finite force");
+    }
     c->f_in_valid = true;
     c->f_in_key[0] = trav;
     c->f_in_key[1] = trunc;

@@ -52,6 +52,8 @@ struct atm_ctx {
     atm3::ResultDev* h_res = nullptr;  // [R] pinned
     int* d_status = nullptr;
     int* h_status = nullptr;
+    int* d_chk = nullptr;  // finiteness flag of a state or force copied in
+    int* h_chk = nullptr;
     int* d_maxocc = nullptr;
     int* h_maxocc = nullptr;
     int* d_work = nullptr;
