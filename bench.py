@@ -663,11 +663,13 @@ def completeness_variant(atm3, device, stream, workload="liquid_n32k"):
 
 # ------------------------------------------------------------------ slab
 
-def slab_variant(atm3, device, stream, flush, steps=20, warmup=5, nbins=600, compare_steps=500):
+def slab_variant(atm3, device, stream, flush, steps=20, warmup=5, nbins=600, compare_steps=500,
+                 fit_equil=5000, fit_sample=5000, fit_bins=240):
     """Vapour-liquid slab: 30 x 30 x 120 box, a 30-sigma fcc liquid slab at
     rho 0.73 with vapour at rho 0.02 (random sequential insertion), T 0.85,
     3c08 + pair + FP32C; every step also adds the 600-bin histogram of z.  Then
-    the same start is run 500 steps in FP32C and in FP64 and the two density
+    Eq. tanh is fitted to the profile of an NVT run from the same start, and the
+    same start is run 500 steps in FP32C and in FP64 and the two density
     profiles are compared."""
     import torch
     cfg = synth.slab()
@@ -695,9 +697,26 @@ def slab_variant(atm3, device, stream, flush, steps=20, warmup=5, nbins=600, com
     z, rho = analysis.density_profile(counts[0], samples, L)
     mid = rho[nbins // 2 - 50: nbins // 2 + 50].mean()
     edge = np.concatenate([rho[:50], rho[-50:]]).mean()
+    # Eq. tanh fitted to an equilibrated profile: NVT (velocity rescaling to
+    # T 0.85 every 10 steps) for fit_equil steps from the lattice start, then
+    # fit_sample steps with the histogram (fit_bins bins) added every 10 steps
+    fit = {"equilibration_steps": fit_equil, "sample_steps": fit_sample, "bins": fit_bins,
+           "thermostat": "velocity rescaling to T 0.85 every 10 steps"}
+    with atm3.AtmSystem(cfg["box"], n, rc=RC, nu=NU, dt=0.002, device=device,
+                        stream=stream.cuda_stream) as b:
+        b.set_state(cfg["x"], cfg["v"])
+        b.set_options(graph=True)
+        for k in range((fit_equil + fit_sample) // 10):
+            b.step(10, "3c08", "pair", "fp32c", sync=False)
+            if k >= fit_equil // 10:
+                b.density_accumulate(axis=2, nbins=fit_bins)
+            b.thermostat([cfg["T"]])
+        c, smp = b.density_get(fit_bins)
     try:
-        fit = analysis.fit_interfaces(z, rho, L[2])
-        fit = {side: {k: round(v, 4) for k, v in fit[side].items()} for side in ("left", "right")}
+        zf, rf = analysis.density_profile(c[0], smp, L)
+        res = analysis.fit_interfaces(zf, rf, L[2])
+        for side in ("left", "right"):
+            fit[side] = {k: round(v, 4) for k, v in res[side].items()}
     except ImportError:
         fit = None
     # the same start run 500 steps in FP32C and in FP64 with rho(z) sampled
