@@ -37,7 +37,7 @@ struct Rep {
     float rcf, rc2f, rc6f, nuf, sig2f, eps4f, eps24f, eps48f, ushiftf;
     float wf[3];
     float p_lo, p_hi;          // FP64 prefilter band of a squared distance
-    float q_lo, q_hi, dmin;    // FP64 prefilter band of a sorted product
+    float q_lo, q_hi, dmin;    // FP64 prefilter band of the FP32 product of the squared sides
     double rw2;                // wide traversal: (2 min w)^2, partners and third sides below it
     float rw2f;
 };

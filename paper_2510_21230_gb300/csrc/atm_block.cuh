@@ -21,7 +21,7 @@
 //     and every lane of a round evaluates one triangle.
 // Product rule
 //  1. Dense FP32 squared distances (or on-the-fly when they do not fit).
-//  3. Every candidate p < q < r of the unit's tasks, enumerated r-major, is
+//  3. Every candidate p < q < r of the unit's tasks, enumerated q-major, is
 //     tested on the sorted product of its squared sides; interacting triplets
 //     are queued per warp and evaluated 32 at a time.
 // Both rules
@@ -298,6 +298,9 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
         if (f2 > rp.p_hi) return false;
         return disp(p, q, dx, dy, dz) < rc2;
     };
+    // product rule: D[dsel(x) + y] is the FP32 squared distance of x < y (the
+    // upper triangle packed row by row; row x starts at x M - x (x + 1) / 2)
+    auto dsel = [&](int x) -> int { return x * M - ((x * (x + 1)) >> 1) - x - 1; };
     // rank of y among the set bits of row x = edge number of (x, y) within row x
     auto rank = [&](int x, int y) -> int {
         int wy = y >> 5;
@@ -376,11 +379,11 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
             }
         }
     } else if (A.use_d) {
-        for (int t = tid; t < M * (M - 1) / 2; t += blockDim.x) {
-            int y = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)t)) * 0.5f);
-            while (y * (y - 1) / 2 > t) y--;
-            while ((y + 1) * y / 2 <= t) y++;
-            D[t] = disp32(t - y * (y - 1) / 2, y);
+        // row x of the upper triangle holds y = x+1 .. M-1 contiguously:
+        // D[dsel(x) + y]; one warp per row
+        for (int x = warp; x < M - 1; x += nwarps) {
+            const int dx = dsel(x);
+            for (int y = x + 1 + lane; y < M; y += 32) D[dx + y] = disp32(x, y);
         }
     }
     __syncthreads();
@@ -580,16 +583,15 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
         esum.add(uu);
         wsum.add(-(gpq * a + gpr * b + gqr * c));
         if (!use_acc) {
-            // runs of equal keys are contiguous in a batch: e(p,q) for the pair
-            // rule (edge-major order), e(p,r) for the product rule (r-major order)
-            int key = PAIR ? epq : epr;
+            // runs of equal e(p,q) are contiguous in a batch (q-major order)
+            int key = epq;
             if (!valid) key = -1 - lane;
-            R run = seg_sum<R>(PAIR ? gpq : gpr, key, lane);
+            R run = seg_sum<R>(gpq, key, lane);
             int prev = __shfl_up_sync(FULL, key, 1);
             bool head = lane == 0 || prev != key;
             if (valid) {
                 if (head) atomicAdd(G + key, run);
-                atomicAdd(G + (PAIR ? epr : epq), PAIR ? gpr : gpq);
+                atomicAdd(G + epr, gpr);
                 atomicAdd(G + eqr, gqr);
             }
         } else if (valid) {
@@ -606,6 +608,7 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
     };
     auto push = [&](bool keep, unsigned long long entry) {
         unsigned m = __ballot_sync(FULL, keep);
+        if (m == 0u) return;
         if (keep) queue[qn + __popc(m & lt_mask)] = entry;
         qn += __popc(m);
         nint += keep ? 1u : 0u;
@@ -709,59 +712,97 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
             if (!use_acc && e < Ework && gown != R(0)) atomicAdd(G + e, gown);
         }
     } else {
+        // the candidates p < q < r of each p run q-major (q, then r) and are cut
+        // into tasks of CH, numbered row by row; warps take tasks from the
+        // unit's counter (a warp's tasks only move forward, and so does its row
+        // cursor).  A task runs 32 candidates per round: every lane walks from
+        // the warp's cursor (qc, rc) to its own pair across the rows it
+        // crosses, so a round's lanes read consecutive words of the distance
+        // rows of p and q.
+        constexpr int CH = 2048;
+        const float t_lo = (float)rc6 * (1.0f - 0x1p-18f), t_hi = (float)rc6 * (1.0f + 0x1p-18f);
+        int pc = 0, kbase = 0;  // row cursor; tasks of the rows before it
         for (;;) {
-            int p = 0;
-            if (lane == 0) p = atomicAdd(&s_next, 1);
-            p = __shfl_sync(FULL, p, 0);
-            if (p >= Mfirst) break;
+            int k = 0;
+            if (lane == 0) k = atomicAdd(&s_next, 1);
+            k = __shfl_sync(FULL, k, 0);
+            for (; pc < Mfirst; pc++) {
+                const int Lc = M - 1 - pc;
+                // no later slot completes an anchored set: no tasks
+                const int nch = (TRAV == 2 && sslot[pc] == 7) ? 0 : (Lc * (Lc - 1) / 2 + CH - 1) / CH;
+                if (k < kbase + nch) break;
+                kbase += nch;
+            }
+            if (pc >= Mfirst) break;
+            const int p = pc;
             const int sp = sslot[p];
-            if (TRAV == 2 && sp == 7) continue;  // no later slot completes an anchored set
-            // every candidate p < q < r, r-major: t = kk (kk - 1) / 2 + jj, q = p+1+jj, r = p+1+kk
-            const int base = p + 1, L = M - base;
-            const int T = L * (L - 1) / 2;
-            for (int t0 = 0; t0 < T; t0 += 32) {
-                int kk0 = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)t0)) * 0.5f);
-                while (kk0 * (kk0 - 1) / 2 > t0) kk0--;
-                while ((kk0 + 1) * kk0 / 2 <= t0) kk0++;
-                const int t = t0 + lane;
+            const int dp = dsel(p);
+            // candidates t0 .. t1-1 of p; row i (q = p + 1 + i) starts at
+            // off(i) = i (L - 1) - i (i - 1) / 2
+            const int L = M - 1 - p;
+            const int t0 = (k - kbase) * CH, t1 = min(L * (L - 1) / 2, t0 + CH);
+            auto off = [&](int i) -> int { return i * (L - 1) - i * (i - 1) / 2; };
+            const float b2 = (float)(2 * L - 1);
+            int i = (int)((b2 - sqrtf(fmaxf(b2 * b2 - 8.0f * (float)t0, 0.0f))) * 0.5f);
+            i = max(i, 0);
+            while (i > 0 && off(i) > t0) i--;
+            while (off(i + 1) <= t0) i++;
+            int qc = p + 1 + i, rc = qc + 1 + (t0 - off(i)), dqc = dsel(qc);
+            for (int left = t1 - t0; left > 0; left -= 32) {
+                int q = qc, r = rc + lane, dq = dqc;
+                while (r >= M) {  // into the next row: it starts at r = q + 2
+                    if (q >= M - 2) {
+                        q = M;  // past the last pair
+                        break;
+                    }
+                    r += q + 2 - M;
+                    dq += M - q - 2;
+                    q++;
+                }
                 bool keep = false;
-                int q = 0, r = 0;
-                if (t < T) {
-                    int kk = kk0;
-                    while ((kk + 1) * kk / 2 <= t) kk++;
-                    q = base + (t - kk * (kk - 1) / 2);
-                    r = base + kk;
-                    if (TRAV != 2 || (sp & sslot[q] & sslot[r]) == 0) {
-                        float a32, b32, c32;
-                        if (A.use_d) {
-                            a32 = D[tri_index(p, q)];
-                            b32 = D[tri_index(p, r)];
-                            c32 = D[tri_index(q, r)];
+                if (lane < left && q <= M - 2 && (TRAV != 2 || (sp & sslot[q] & sslot[r]) == 0)) {
+                    float a32, b32, c32;
+                    if (A.use_d) {
+                        a32 = D[dp + q];
+                        b32 = D[dp + r];
+                        c32 = D[dq + r];
+                    } else {
+                        a32 = disp32(p, q);
+                        b32 = disp32(p, r);
+                        c32 = disp32(q, r);
+                    }
+                    // the product in this order is within 2^-22 (relative) of the
+                    // sorted product that decides: only products in the band
+                    // [t_lo, t_hi) around r_c^6 need the sorted form
+                    const float pr = (a32 * b32) * c32;
+                    if (!F64) {
+                        keep = pr < t_lo;
+                        if (!keep && pr < t_hi) keep = sorted_product<float>(a32, b32, c32) < (float)rc6;
+                    } else {
+                        float lo = fminf(a32, fminf(b32, c32));
+                        if (lo >= rp.dmin && pr < rp.q_lo) {
+                            keep = true;
+                        } else if (lo >= rp.dmin && pr > rp.q_hi) {
+                            keep = false;
                         } else {
-                            a32 = disp32(p, q);
-                            b32 = disp32(p, r);
-                            c32 = disp32(q, r);
-                        }
-                        float pr = sorted_product<float>(a32, b32, c32);
-                        if (!F64) {
-                            keep = pr < (float)rc6;
-                        } else {
-                            float lo = fminf(a32, fminf(b32, c32));
-                            if (lo >= rp.dmin && pr < rp.q_lo) {
-                                keep = true;
-                            } else if (lo >= rp.dmin && pr > rp.q_hi) {
-                                keep = false;
-                            } else {
-                                R dx, dy, dz;
-                                R a = disp(p, q, dx, dy, dz);
-                                R b = disp(p, r, dx, dy, dz);
-                                R c = disp(q, r, dx, dy, dz);
-                                keep = sorted_product<R>(a, b, c) < rc6;
-                            }
+                            R dx, dy, dz;
+                            R a = disp(p, q, dx, dy, dz);
+                            R b = disp(p, r, dx, dy, dz);
+                            R c = disp(q, r, dx, dy, dz);
+                            keep = sorted_product<R>(a, b, c) < rc6;
                         }
                     }
                 }
                 push(keep, pack(p, q, r, 0));
+                // the next cursor: one past lane 31's pair
+                qc = __shfl_sync(FULL, q, 31);
+                rc = __shfl_sync(FULL, r, 31) + 1;
+                dqc = __shfl_sync(FULL, dq, 31);
+                if (rc >= M && qc <= M - 2) {
+                    dqc += M - qc - 2;
+                    qc++;
+                    rc = qc + 1;
+                }
             }
         }
     }
