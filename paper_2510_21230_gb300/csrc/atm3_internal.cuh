@@ -241,7 +241,7 @@ __host__ __device__ inline BlockSmem block_smem_plan(int trunc, int mcap, int nw
 // scalars for 16 edges per staged molecule of the largest unit (the rho* =
 // 0.8 liquids have at most 14.4 (256k) and 15.9 (32k)), halved until they
 // fit (a unit with more edges falls back to per-molecule accumulators);
-// product rule: 8 warps,
+// product rule: 8 warps (FP32 3c18: 16 when one CTA fills an SM),
 // dense distances + dense pair scalars, else dense pair scalars only, else
 // per-molecule accumulators.  Returns false if nothing fits.
 struct AtmPlan {
@@ -308,8 +308,18 @@ inline bool atm_choose_plan_nw(int trav, int trunc, int prec, int mcap, int opti
 
 inline bool atm_choose_plan(int trav, int trunc, int prec, int mcap, int optin, AtmPlan& P)
 {
-    return atm_choose_plan_nw(trav, trunc, prec, mcap, optin,
-                              (trav == 0 || trav == 3 || (trunc == 0 && prec == 1)) ? 4 : 8, P);
+    if (!atm_choose_plan_nw(trav, trunc, prec, mcap, optin,
+                            (trav == 0 || trav == 3 || (trunc == 0 && prec == 1)) ? 4 : 8, P))
+        return false;
+    // FP32 3c18 product rule whose tables leave room for one CTA per SM: 16
+    // warps (same table mode) hide more of the scan's shared-memory latency
+    if (trunc == 1 && prec == 1 && trav == 1 && 2 * P.smem > (size_t)optin) {
+        AtmPlan Q;
+        if (atm_choose_plan_nw(trav, trunc, prec, mcap, optin, 16, Q) && Q.use_d == P.use_d &&
+            Q.acc_mode == P.acc_mode)
+            P = Q;
+    }
+    return true;
 }
 
 }  // namespace atm3

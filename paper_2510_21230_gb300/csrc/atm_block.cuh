@@ -126,8 +126,9 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
     __shared__ int s_cell0[S];
     __shared__ signed char s_off[S][3];
     __shared__ int s_next, s_edges;
-    __shared__ double s_red[2][8];
-    __shared__ unsigned long long s_redn[8];
+    constexpr int NWB = TRUNC == 1 && TRAV == 1 ? 16 : 8;  // most warps of a CTA
+    __shared__ double s_red[2][NWB];
+    __shared__ unsigned long long s_redn[NWB];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nwarps = blockDim.x >> 5;
@@ -503,7 +504,7 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
         // pair-scalar writes above before the triplet phase)
         unsigned long long cand2 = 0;
         if (warp == 0) cand2 = unit_pair_candidates_warp<S>(s_beg);
-        unit_reduce_store2<8>(e2sum.get(), w2sum.get(), (unsigned long long)n2, cand2, A.unit_ew2,
+        unit_reduce_store2<NWB>(e2sum.get(), w2sum.get(), (unsigned long long)n2, cand2, A.unit_ew2,
                               A.unit_cnt2, u, s_red, s_redn);
     }
     const bool use_acc = PAIR ? !edge_mode : (A.acc_mode == 1);
@@ -891,7 +892,7 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
 
     unsigned long long cand = 0;
     if (warp == 0) cand = unit_candidates_warp<TRAV, S>(s_beg);
-    unit_reduce_store<8>(esum.get(), wsum.get(), (unsigned long long)nint, 1.0, cand, A.unit_ew,
+    unit_reduce_store<NWB>(esum.get(), wsum.get(), (unsigned long long)nint, 1.0, cand, A.unit_ew,
                          A.unit_cnt, u, s_red, s_redn);
 }
 
@@ -899,9 +900,12 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
 // from a global counter until all units of the batch are done.
 // FP32: at most 56 registers, so that 9 CTAs of 4 warps fit an SM (with the
 // 16-edge-per-molecule pair-scalar table, 9 also fit its shared memory at the
-// rho* = 0.8 cell occupancy); FP64: 2 CTAs of 8 warps
+// rho* = 0.8 cell occupancy); FP64: 2 CTAs of 8 warps.  The 3c18 product
+// rule takes up to 16 warps (one CTA per SM when its tables fill shared
+// memory); the bound of 512 threads costs the other kernels registers.
 template <int TRAV, int TRUNC, typename R>
-__global__ void __launch_bounds__(256) __maxnreg__(sizeof(R) == 8 ? 128 : 56)
+__global__ void __launch_bounds__(TRUNC == 1 && TRAV == 1 ? 512 : 256)
+    __maxnreg__(sizeof(R) == 8 ? 128 : 56)
     atm_block_kernel(const AtmArgs<R> A)
 {
     if (A.work == nullptr) {
