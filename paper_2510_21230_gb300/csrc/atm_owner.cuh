@@ -207,19 +207,57 @@ __device__ __forceinline__ void atm_owner_unit(const AtmArgs<R>& A, const long l
             fzs.add(gij * dijz + gik * dikz);
         };
 
-        // pairs (jj < kk) of the partner list, t = kk (kk - 1) / 2 + jj
-        const int T = np * (np - 1) / 2;
-        for (int t0 = 0; t0 < T; t0 += 32) {
-            int t = t0 + lane;
+        // pairs (jj < kk) of the partner list, kk-major (row kk holds jj = 0 ..
+        // kk - 1), 32 per round: every lane walks from the warp's cursor
+        // (kc, jc) to its own pair.  FP32 decides the third side j-k from the
+        // partner vectors, d(j -> k) = d(i -> k) - d(i -> j): within 2.4e-4
+        // (relative) of the canonical square for |d| above the guard
+        // sqrt(dmin), so outside a band of 2^-10 around each threshold it
+        // decides as the canonical form does; in the band, or below the
+        // guard, the canonical displacement decides.
+        const float bl = 1.0f - 0x1p-10f, bh = 1.0f + 0x1p-10f;
+        int kc = 1, jc = 0;
+        while (kc < np) {
+            int kk = kc, jj = jc + lane;
+            while (jj >= kk) {
+                jj -= kk;
+                kk++;
+            }
             bool keep = false;
-            int jj = 0, kk = 0;
-            if (t < T) {
-                kk = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)t)) * 0.5f);
-                while (kk * (kk - 1) / 2 > t) kk--;
-                while ((kk + 1) * kk / 2 <= t) kk++;
-                jj = t - kk * (kk - 1) / 2;
+            if (kk < np) {
                 int j = pq[jj], k = pq[kk];
-                if (TRUNC == 0) {
+                if (!F64) {
+                    const float ex = (float)pdx[kk] - (float)pdx[jj];
+                    const float ey = (float)pdy[kk] - (float)pdy[jj];
+                    const float ez = (float)pdz[kk] - (float)pdz[jj];
+                    const float cq = ex * ex + ey * ey + ez * ez;
+                    const float a = (float)pa[jj], b = (float)pa[kk];
+                    int state;  // 0 out, 1 in, 2 undecided
+                    if (cq < rp.dmin) {
+                        state = 2;
+                    } else if (TRUNC == 0) {
+                        state = cq < (float)rc2 * bl ? 1 : (cq > (float)rc2 * bh ? 0 : 2);
+                    } else {
+                        const float pr = (a * b) * cq;
+                        state = pr < (float)rc6 * bl ? 1 : (pr > (float)rc6 * bh ? 0 : 2);
+                        if (WIDE && state != 0)
+                            state = cq > (float)rw2 * bh ? 0 : (cq < (float)rw2 * bl ? state : 2);
+                    }
+                    if (state == 2) {
+                        if (TRUNC == 0) {
+                            keep = close_pair(j, k);
+                        } else {
+                            int mx, my, mz;
+                            offs(j, k, mx, my, mz);
+                            R dx, dy, dz;
+                            R c = canon_disp<R>(px[j], py[j], pz[j], px[k], py[k], pz[k], mx, my,
+                                                mz, w0, w1, w2, dx, dy, dz);
+                            keep = (!WIDE || c < rw2) && sorted_product<R>(pa[jj], pa[kk], c) < rc6;
+                        }
+                    } else {
+                        keep = state == 1;
+                    }
+                } else if (TRUNC == 0) {
                     keep = close_pair(j, k);
                 } else if (WIDE) {
                     // third side below R_w, then the sorted product, in the working precision
@@ -232,29 +270,21 @@ __device__ __forceinline__ void atm_owner_unit(const AtmArgs<R>& A, const long l
                 } else {
                     int mx, my, mz;
                     offs(j, k, mx, my, mz);
-                    if (!F64) {
+                    float ex, ey, ez;
+                    float a32 = pa32[jj], b32 = pa32[kk];
+                    float c32 = canon_disp<float>(fx32[j], fy32[j], fz32[j], fx32[k], fy32[k],
+                                                  fz32[k], mx, my, mz, wf0, wf1, wf2, ex, ey, ez);
+                    float pr = sorted_product<float>(a32, b32, c32);
+                    float lo = fminf(a32, fminf(b32, c32));
+                    if (lo >= rp.dmin && pr < rp.q_lo) {
+                        keep = true;
+                    } else if (lo >= rp.dmin && pr > rp.q_hi) {
+                        keep = false;
+                    } else {
                         R dx, dy, dz;
                         R c = canon_disp<R>(px[j], py[j], pz[j], px[k], py[k], pz[k], mx, my, mz,
                                             w0, w1, w2, dx, dy, dz);
                         keep = sorted_product<R>(pa[jj], pa[kk], c) < rc6;
-                    } else {
-                        float ex, ey, ez;
-                        float a32 = pa32[jj], b32 = pa32[kk];
-                        float c32 = canon_disp<float>(fx32[j], fy32[j], fz32[j], fx32[k], fy32[k],
-                                                      fz32[k], mx, my, mz, wf0, wf1, wf2, ex, ey,
-                                                      ez);
-                        float pr = sorted_product<float>(a32, b32, c32);
-                        float lo = fminf(a32, fminf(b32, c32));
-                        if (lo >= rp.dmin && pr < rp.q_lo) {
-                            keep = true;
-                        } else if (lo >= rp.dmin && pr > rp.q_hi) {
-                            keep = false;
-                        } else {
-                            R dx, dy, dz;
-                            R c = canon_disp<R>(px[j], py[j], pz[j], px[k], py[k], pz[k], mx, my,
-                                                mz, w0, w1, w2, dx, dy, dz);
-                            keep = sorted_product<R>(pa[jj], pa[kk], c) < rc6;
-                        }
                     }
                 }
             }
@@ -269,6 +299,11 @@ __device__ __forceinline__ void atm_owner_unit(const AtmArgs<R>& A, const long l
                 if (lane < qn - 32) queue[lane] = queue[32 + lane];
                 qn -= 32;
                 __syncwarp();
+            }
+            jc += 32;  // the next cursor (uniform)
+            while (jc >= kc) {
+                jc -= kc;
+                kc++;
             }
         }
         if (lane < qn) evaluate(queue[lane]);
