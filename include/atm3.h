@@ -32,7 +32,7 @@
 extern "C" {
 #endif
 
-#define ATM3_ABI_VERSION 1
+#define ATM3_ABI_VERSION 2
 
 typedef enum {
     ATM_OK = 0,
@@ -209,14 +209,34 @@ atm_status atm_get_results(atm_ctx* ctx, atm_result* out);
  * Options reset any autotuned choice.  Errors: INVALID. */
 atm_status atm_set_options(atm_ctx* ctx, int persistent, int nwarps, int graph);
 
+/* Unit size classes of the block traversals (3C18, 3C08, 3C08A) for
+ * evaluations and steps without an autotuned choice.  nclass = 1: every unit
+ * in one launch sized for the largest unit (the default).  nclass = 2 or 3:
+ * every force evaluation first lists, on the device, the units of at most
+ * cuts[0] staged molecules, then (nclass = 3) those of at most cuts[1], then
+ * the rest, and launches the block kernel once per class with shared memory
+ * sized for the class bound (4 warps when it is at most 64): small units of
+ * a batch of uneven replicas then share an SM with more of their kind.
+ * Results are those of one launch (energies and counts per unit are the
+ * same; forces differ by the order of their FP64 atomic additions).  cuts
+ * (host, nclass - 1 values) must rise within 1 .. 2047.  Resets any
+ * autotuned choice.  Errors: INVALID. */
+atm_status atm_set_unit_classes(atm_ctx* ctx, int nclass, const int* cuts);
+
 typedef struct {
     int persistent;     /* chosen launch form */
     int nwarps;         /* chosen warps per CTA */
     double ms_per_eval; /* device time of one LJ + ATM evaluation with it */
+    int nclass;         /* unit size classes (1: all units in one launch) */
+    int cut[2];         /* staged-molecule bounds of the first classes */
 } atm_tuning;
 
 /* Autotuner: times `reps` force evaluations on the current cells for every
- * launch form (one CTA per unit or persistent; 4 or 8 warps for 3C18/3C08)
+ * launch form (one CTA per unit or persistent; 4 or 8 warps for 3C18/3C08;
+ * for 3C18/3C08/3C08A also unit size classes: {all}, {<= 64, rest},
+ * {<= 48, <= 96, rest}, {<= 64, <= 128, rest}, where every force evaluation
+ * sorts the units by their staged molecules on the device and launches each
+ * class with shared memory sized for its bound, 4 warps for bounds up to 64)
  * and keeps the fastest for this (trav, trunc, prec); later evaluations and
  * steps use it.  Cells must be built.  out may be NULL.
  * Errors: INVALID, STATE, CAPACITY, CUDA. */

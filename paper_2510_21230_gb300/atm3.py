@@ -23,6 +23,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "box smaller than three cells", 3: 
           4: "device wait timed out", 5: "non-finite input", 6: "call out of order",
           7: "capacity exceeded"}
 
+ABI_VERSION = 2  # ATM3_ABI_VERSION of include/atm3.h
 EXPORTED = ["atm_abi_version", "atm_create", "atm_batch_create", "atm_batch_size", "atm_destroy",
             "atm_last_error", "atm_set_state", "atm_set_state_dev", "atm_build_cells",
             "atm_get_cells", "atm_compute_forces", "atm_get_results", "atm_get_forces",
@@ -35,7 +36,8 @@ EXPORTED = ["atm_abi_version", "atm_create", "atm_batch_create", "atm_batch_size
             "atm_surrogate_add_rows", "atm_surrogate_dataset", "atm_surrogate_clear",
             "atm_surrogate_train", "atm_surrogate_options", "atm_surrogate_error",
             "atm_measure_fma_peak", "atm_rdf_accumulate", "atm_rdf_get", "atm_rdf_reset",
-            "atm_lj_tail", "atm_thermostat", "atm_measure_rsqrt_peak", "atm_set_forces"]
+            "atm_lj_tail", "atm_thermostat", "atm_measure_rsqrt_peak", "atm_set_forces",
+            "atm_set_unit_classes"]
 
 SUR_NDESC, SUR_NVEC, SUR_NPARAM = 32, 9, 6467
 
@@ -68,10 +70,13 @@ class Profile(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("persistent", ctypes.c_int), ("nwarps", ctypes.c_int),
-                ("ms_per_eval", ctypes.c_double)]
+                ("ms_per_eval", ctypes.c_double), ("nclass", ctypes.c_int),
+                ("cut", ctypes.c_int * 2)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "cut"}
+        d["cuts"] = [int(self.cut[i]) for i in range(max(0, self.nclass - 1))]
+        return d
 
 
 class AtmError(RuntimeError):
@@ -110,6 +115,7 @@ def load():
         "atm_get_state": [P, P, P],
         "atm_step": [P, i32, i32, i32, i32, ctypes.POINTER(Result)],
         "atm_set_options": [P, i32, i32, i32],
+        "atm_set_unit_classes": [P, i32, P],
         "atm_autotune": [P, i32, i32, i32, i32, ctypes.POINTER(Tuning)],
         "atm_density_accumulate": [P, i32, i32],
         "atm_density_get": [P, P, P],
@@ -148,6 +154,9 @@ def load():
         fn.argtypes = args
     L.atm_last_error.restype = ctypes.c_char_p
     L.atm_last_error.argtypes = [P]
+    if L.atm_abi_version() != ABI_VERSION:  # the structures above must match the library's
+        raise RuntimeError("libatm3.so has ABI version %d, this binding %d"
+                           % (L.atm_abi_version(), ABI_VERSION))
     _lib = L
     return L
 
@@ -327,6 +336,13 @@ class AtmSystem:
     def set_options(self, persistent=False, nwarps=0, graph=False):
         self._check(self._lib.atm_set_options(self._ctx, int(bool(persistent)), int(nwarps),
                                               int(bool(graph))))
+
+    def set_unit_classes(self, cuts=()):
+        """Unit size classes of the block traversals: cuts = () for one
+        launch, else 1 or 2 rising bounds (staged molecules)."""
+        cuts = [int(c) for c in cuts]
+        arr = (ctypes.c_int * max(1, len(cuts)))(*cuts) if cuts else None
+        self._check(self._lib.atm_set_unit_classes(self._ctx, len(cuts) + 1, arr))
 
     def autotune(self, trav="3c08", trunc="pair", prec="fp32c", reps=3):
         t = Tuning()

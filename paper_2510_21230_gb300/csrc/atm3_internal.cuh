@@ -156,6 +156,10 @@ struct AtmArgs {
     int lj;
     double* unit_ew2;
     unsigned long long* unit_cnt2;
+    // block kernels, unit size classes: the CTAs (or the persistent counter)
+    // take the units ulist[0 .. *ucount) instead of 0 .. ncell (nullptr: all)
+    const int* ulist;
+    const int* ucount;
 };
 
 // Shared-memory plan of the owner kernels (3c01, 3cw): staged positions,

@@ -897,7 +897,8 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
 }
 
 // One CTA per unit, or (A.work set) a persistent grid whose CTAs take units
-// from a global counter until all units of the batch are done.
+// from a global counter until all units of the batch are done; with a unit
+// list (size classes) the same over the listed units.
 // FP32: at most 56 registers, so that 9 CTAs of 4 warps fit an SM (with the
 // 16-edge-per-molecule pair-scalar table, 9 also fit its shared memory at the
 // rho* = 0.8 cell occupancy); FP64: 2 CTAs of 8 warps.  The 3c18 product
@@ -908,8 +909,11 @@ __global__ void __launch_bounds__(TRUNC == 1 && TRAV == 1 ? 512 : 256)
     __maxnreg__(sizeof(R) == 8 ? 128 : 56)
     atm_block_kernel(const AtmArgs<R> A)
 {
+    // units 0 .. ncell, or (size classes) the units ulist[0 .. *ucount)
+    const long long nu = A.ulist ? (long long)*A.ucount : A.b.ncell;
     if (A.work == nullptr) {
-        atm_block_unit<TRAV, TRUNC, R>(A, blockIdx.x);
+        if ((long long)blockIdx.x >= nu) return;
+        atm_block_unit<TRAV, TRUNC, R>(A, A.ulist ? A.ulist[blockIdx.x] : (long long)blockIdx.x);
         return;
     }
     __shared__ int s_u;
@@ -917,9 +921,9 @@ __global__ void __launch_bounds__(TRUNC == 1 && TRAV == 1 ? 512 : 256)
         __syncthreads();  // the previous unit is done with shared memory
         if (threadIdx.x == 0) s_u = atomicAdd(A.work, 1);
         __syncthreads();
-        const int u = s_u;
-        if (u >= A.b.ncell) break;
-        atm_block_unit<TRAV, TRUNC, R>(A, u);
+        const int k = s_u;
+        if (k >= nu) break;
+        atm_block_unit<TRAV, TRUNC, R>(A, A.ulist ? A.ulist[k] : (long long)k);
     }
 }
 

@@ -27,10 +27,17 @@ static bool lj_fused(int trav, int trunc, int prec)
     return (trav == ATM_3C08 || trav == ATM_3C08A) && trunc == ATM_TRUNC_PAIR && prec != ATM_SURROGATE;
 }
 
-// kernels of one step: two kicks, the cell build and the force kernels
-static int kernels_per_step(int trav, int trunc, int prec)
+// unit size classes the autotuner chooses among for the block traversals:
+// {classes, bound of the first, bound of the second}
+constexpr int N_SPLITS = 4;
+constexpr int SPLITS[N_SPLITS][3] = {{1, 0, 0}, {2, 64, 0}, {3, 48, 96}, {3, 64, 128}};
+
+// kernels of one step: two kicks, the cell build and the force kernels (with
+// ncls > 1 size classes: the class kernel and one ATM launch per class)
+static int kernels_per_step(int trav, int trunc, int prec, int ncls)
 {
-    const int forces = prec == ATM_SURROGATE ? SUR_LAUNCHES : (lj_fused(trav, trunc, prec) ? 1 : 2);
+    int forces = prec == ATM_SURROGATE ? SUR_LAUNCHES : (lj_fused(trav, trunc, prec) ? 1 : 2);
+    if (ncls > 1 && prec != ATM_SURROGATE) forces += ncls;
     return 2 + CELL_KERNELS + forces;
 }
 }  // namespace
@@ -107,7 +114,8 @@ static void free_all(atm_ctx* c)
                    c->xl32, c->cell_of, c->rank, c->count, c->start, c->perm, c->cell_sorted,
                    c->f_lj, c->f_atm, c->f_out, c->unit_ew, c->unit_cnt, c->mol_ew, c->mol_cnt,
                    c->ke, c->d_res, c->d_part, c->d_status, c->d_maxocc, c->d_work, c->d_dens,
-                   c->d_rdf, c->d_ttarget, c->unit_ew2, c->unit_cnt2, c->f_in, c->d_chk};
+                   c->d_rdf, c->d_ttarget, c->unit_ew2, c->unit_cnt2, c->f_in, c->d_chk,
+                   c->d_ulist, c->d_ucount};
     for (void* p : dev)
         if (p) cudaFree(p);
     if (c->h_res) cudaFreeHost(c->h_res);
@@ -223,7 +231,9 @@ extern "C" atm_status atm_batch_create(const atm_params* params, const int64_t* 
     ok = ok && alloc((void**)&c->d_part, (size_t)nrep * REDUCE_PARTS * sizeof(ResultDev));
     ok = ok && alloc((void**)&c->d_status, sizeof(int));
     ok = ok && alloc((void**)&c->d_maxocc, (1 + ATM_NTRAV) * sizeof(int));
-    ok = ok && alloc((void**)&c->d_work, sizeof(int));
+    ok = ok && alloc((void**)&c->d_work, 4 * sizeof(int));
+    ok = ok && alloc((void**)&c->d_ulist, 3 * NC * sizeof(int));
+    ok = ok && alloc((void**)&c->d_ucount, 4 * sizeof(int));
     ok = ok && alloc((void**)&c->d_dens, (size_t)nrep * DENS_MAX_BINS * sizeof(unsigned long long));
     ok = ok && alloc((void**)&c->d_rdf, (size_t)nrep * DENS_MAX_BINS * sizeof(unsigned long long));
     ok = ok && alloc((void**)&c->d_ttarget, nrep * sizeof(double));
@@ -433,19 +443,26 @@ extern "C" atm_status atm_get_cells(atm_ctx* c, int32_t* cell_of, int32_t* cell_
     return ATM_OK;
 }
 
-// launch options of one force evaluation: the tuned choice, else the context's options
+// launch options of one force evaluation: the tuned choice, else the context's
+// options; cls = {classes, first bound, second bound} (1 class: all units in
+// one launch)
 static void launch_choice(const atm_ctx* c, int trav, int trunc, int prec, int& persistent,
-                          int& nwarps)
+                          int& nwarps, int cls[3])
 {
     int t = c->tuned[prec][trav][trunc];
     if (t) {
         persistent = (t - 1) & 1;
         nwarps = ((t - 1) & 2) ? 8 : 4;
+        for (int k = 0; k < 3; k++) cls[k] = SPLITS[(t - 1) >> 2][k];
     } else {
         persistent = c->opt_persistent;
         nwarps = c->opt_nwarps;
+        for (int k = 0; k < 3; k++) cls[k] = c->opt_cls[k];
     }
-    if (trav == ATM_3C01 || trav == ATM_3CW) nwarps = 0;
+    if (trav == ATM_3C01 || trav == ATM_3CW) {
+        nwarps = 0;
+        cls[0] = 1;
+    }
 }
 
 // LJ + ATM force kernels for the current cells; mcap = staged-molecule capacity
@@ -484,7 +501,13 @@ atm_status atm3::ctx_enqueue_forces(atm_ctx* c, int trav, int trunc, int prec, i
     j.sms = c->sms;
     j.persistent = 0;
     j.nwarps = 0;
-    if (prec != ATM_SURROGATE) launch_choice(c, trav, trunc, prec, j.persistent, j.nwarps);
+    int cls[3] = {1, 0, 0};
+    if (prec != ATM_SURROGATE) launch_choice(c, trav, trunc, prec, j.persistent, j.nwarps, cls);
+    j.ncls = cls[0];
+    j.cuts[0] = cls[1];
+    j.cuts[1] = cls[2];
+    j.ulist = c->d_ulist;
+    j.ucount = c->d_ucount;
     j.st = c->st;
 
     cudaEvent_t ev;
@@ -509,6 +532,7 @@ atm_status atm3::ctx_enqueue_forces(atm_ctx* c, int trav, int trunc, int prec, i
                             "a traversal unit of %d molecules does not fit the kernels' shared memory",
                             j.mcap);
         CU(e);
+        if (atm_split_active(j)) c->n_launch += j.ncls;  // the class kernel and ncls - 1 more
     }
     ctx_prof_end(c, PK_ATM, ev);
     c->n_launch += 1;
@@ -675,9 +699,9 @@ static int graph_mcap(const atm_ctx* c, int trav)
 static atm_status run_graph_steps(atm_ctx* c, int nsteps, int trav, int trunc, int prec)
 {
     const int mcap = graph_mcap(c, trav);
-    int persistent = 0, nwarps = 0;
-    if (prec != ATM_SURROGATE) launch_choice(c, trav, trunc, prec, persistent, nwarps);
-    const int key[5] = {trav, trunc, prec, mcap, persistent + 2 * nwarps};
+    int persistent = 0, nwarps = 0, cls[3] = {1, 0, 0};
+    if (prec != ATM_SURROGATE) launch_choice(c, trav, trunc, prec, persistent, nwarps, cls);
+    const int key[8] = {trav, trunc, prec, mcap, persistent + 2 * nwarps, cls[0], cls[1], cls[2]};
     if (!c->graph || memcmp(key, c->graph_key, sizeof(key)) != 0) {
         drop_graph(c);
         cudaStream_t keep = c->st;
@@ -706,7 +730,7 @@ static atm_status run_graph_steps(atm_ctx* c, int nsteps, int trav, int trunc, i
     cudaEvent_t ev = ctx_prof_begin(c);
     for (int k = 0; k < nsteps; k++) CU(cudaGraphLaunch(c->graph, c->st));
     ctx_prof_end(c, PK_MD, ev);
-    c->n_launch += (long long)nsteps * kernels_per_step(trav, trunc, prec);
+    c->n_launch += (long long)nsteps * kernels_per_step(trav, trunc, prec, cls[0]);
     c->n_atm += nsteps;
     return ATM_OK;
 }
@@ -833,6 +857,22 @@ extern "C" atm_status atm_set_options(atm_ctx* c, int persistent, int nwarps, in
     return ATM_OK;
 }
 
+extern "C" atm_status atm_set_unit_classes(atm_ctx* c, int nclass, const int* cuts)
+{
+    if (!c) return ATM_E_INVALID;
+    if (nclass < 1 || nclass > 3 || (nclass > 1 && !cuts))
+        return ctx_fail(c, ATM_E_INVALID, "1 to 3 classes, with nclass - 1 bounds");
+    for (int k = 0; k + 1 < nclass; k++)
+        if (cuts[k] < 1 || cuts[k] > ATM_MCAP_LIMIT || (k > 0 && cuts[k] <= cuts[k - 1]))
+            return ctx_fail(c, ATM_E_INVALID, "bounds must rise within 1..%d", ATM_MCAP_LIMIT);
+    c->opt_cls[0] = nclass;
+    c->opt_cls[1] = nclass > 1 ? cuts[0] : 0;
+    c->opt_cls[2] = nclass > 2 ? cuts[1] : 0;
+    memset(c->tuned, 0, sizeof(c->tuned));
+    drop_graph(c);
+    return ATM_OK;
+}
+
 extern "C" atm_status atm_autotune(atm_ctx* c, atm_traversal trav, atm_truncation trunc,
                                    atm_precision prec, int reps, atm_tuning* out)
 {
@@ -853,10 +893,12 @@ extern "C" atm_status atm_autotune(atm_ctx* c, atm_traversal trav, atm_truncatio
     float best = 1e30f;
     int best_code = 1;
     atm_status s = ATM_OK;
-    const int nw_options = (trav == ATM_3C01 || trav == ATM_3CW) ? 1 : 2;
+    const bool owner = trav == ATM_3C01 || trav == ATM_3CW;
+    const int nw_options = owner ? 1 : 2, split_options = owner ? 1 : N_SPLITS;
+    for (int sp = 0; sp < split_options && s == ATM_OK; sp++)
     for (int nwi = 0; nwi < nw_options && s == ATM_OK; nwi++)
         for (int pers = 0; pers < 2 && s == ATM_OK; pers++) {
-            const int code = 1 + pers + 2 * nwi;
+            const int code = 1 + pers + 2 * nwi + 4 * sp;
             c->tuned[prec][trav][trunc] = code;
             s = ctx_enqueue_forces(c, trav, trunc, prec, c->unit_max[trav]);  // warm-up
             if (s != ATM_OK) break;
@@ -880,9 +922,13 @@ extern "C" atm_status atm_autotune(atm_ctx* c, atm_traversal trav, atm_truncatio
     drop_graph(c);
     if (s != ATM_OK) return s;
     if (out) {
+        const int sp = (best_code - 1) >> 2;
         out->persistent = (best_code - 1) & 1;
         out->nwarps = trav == ATM_3C01 ? 4 : (((best_code - 1) & 2) ? 8 : 4);
         out->ms_per_eval = best / reps;
+        out->nclass = SPLITS[sp][0];
+        out->cut[0] = SPLITS[sp][1];
+        out->cut[1] = SPLITS[sp][2];
     }
     return ATM_OK;
 }

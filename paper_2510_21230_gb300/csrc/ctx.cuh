@@ -56,7 +56,9 @@ struct atm_ctx {
     int* h_chk = nullptr;
     int* d_maxocc = nullptr;
     int* h_maxocc = nullptr;
-    int* d_work = nullptr;
+    int* d_work = nullptr;    // [4] persistent unit counters (one per unit size class)
+    int* d_ulist = nullptr;   // [3 * ncell] unit lists of the size classes
+    int* d_ucount = nullptr;  // [4] their lengths
     unsigned long long* d_dens = nullptr;  // [R * DENS_MAX_BINS]
     unsigned long long* d_rdf = nullptr;   // [R * DENS_MAX_BINS]
     double* d_ttarget = nullptr;           // [R] thermostat temperatures
@@ -81,11 +83,13 @@ struct atm_ctx {
     // launch options: persistent ATM grid, warps per block-kernel CTA (0 =
     // default), CUDA-graph steps; tuned choices per (prec, trav, trunc)
     int opt_persistent = 0, opt_nwarps = 0, opt_graph = 0;
-    int tuned[2][atm3::ATM_NTRAV][2] = {};  // 0 = not tuned, else 1 + persistent + 2 * (nwarps == 8)
+    int opt_cls[3] = {1, 0, 0};  // unit size classes: count, bounds of the first two
+    // 0 = not tuned, else 1 + persistent + 2 * (nwarps == 8) + 4 * size-class choice
+    int tuned[2][atm3::ATM_NTRAV][2] = {};
     // graph of one step, valid for (trav, trunc, prec, mcap, launch choice)
     cudaStream_t cap_st = nullptr;
     cudaGraphExec_t graph = nullptr;
-    int graph_key[5] = {-1, -1, -1, -1, -1};
+    int graph_key[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
     // profiling: event pairs around launch groups, summed per kind
     bool prof = false;
     struct EvRec {

@@ -87,9 +87,10 @@ cudaError_t enqueue_lj(const ForceJob& j)
     return launch_lj(j.prec, l64, l32, j.st);
 }
 
-cudaError_t enqueue_atm(const ForceJob& j, size_t* smem_set, bool* capacity)
+// one ATM launch over all units, or over the listed units (ulist, ucount)
+static cudaError_t launch_atm_one(const ForceJob& j, size_t* smem_set, bool* capacity,
+                                  const int* ulist, const int* ucount, int* work)
 {
-    *capacity = false;
     AtmPlan P;
     // the block kernel packs staged indices in 11 bits, the owner kernels in 16
     const int limit = (j.trav == 0 || j.trav == 3) ? 65535 : ATM_MCAP_LIMIT;
@@ -107,6 +108,68 @@ cudaError_t enqueue_atm(const ForceJob& j, size_t* smem_set, bool* capacity)
         if (e != cudaSuccess) return e;
         if (smem_set) *smem_set = P.smem;
     }
+    const int lj = j.lj && (j.trav == 2 || j.trav == 4) && j.trunc == 0;
+    int ctas = 0;
+    if (j.persistent && work) {
+        int per_sm = j.prec == 0 ? atm_occupancy_fp64(j.trav, j.trunc, P.nwarps, P.smem)
+                                 : atm_occupancy_fp32(j.trav, j.trunc, P.nwarps, P.smem);
+        ctas = std::max(1, per_sm) * std::max(1, j.sms);
+        e = cudaMemsetAsync(work, 0, sizeof(int), j.st);
+        if (e != cudaSuccess) return e;
+    }
+    if (j.prec == 0) {
+        AtmArgs<double> a{};
+        a.b = j.b; a.n = j.b.ntot; a.xl = j.xl; a.xl32 = j.xl32; a.cell_start = j.start;
+        a.fs = j.f_atm; a.unit_ew = j.unit_ew; a.unit_cnt = j.unit_cnt; a.status = j.status;
+        a.work = ctas > 0 ? work : nullptr;
+        a.mcap = j.mcap;
+        a.gcap = P.gcap;
+        a.use_d = P.use_d;
+        a.acc_mode = P.acc_mode;
+        a.pcap = P.pcap;
+        a.lj = lj;
+        a.unit_ew2 = j.unit_ew2;
+        a.unit_cnt2 = j.unit_cnt2;
+        a.ulist = ulist;
+        a.ucount = ucount;
+        return launch_atm_fp64(j.trav, j.trunc, a, P.nwarps, P.smem, ctas, j.st);
+    }
+    AtmArgs<float> a{};
+    a.b = j.b; a.n = j.b.ntot; a.xl = j.xl32; a.xl32 = j.xl32; a.cell_start = j.start;
+    a.fs = j.f_atm; a.unit_ew = j.unit_ew; a.unit_cnt = j.unit_cnt; a.status = j.status;
+    a.work = ctas > 0 ? work : nullptr;
+    a.mcap = j.mcap;
+    a.gcap = P.gcap;
+    a.use_d = P.use_d;
+    a.acc_mode = P.acc_mode;
+    a.pcap = P.pcap;
+    a.lj = lj;
+    a.unit_ew2 = j.unit_ew2;
+    a.unit_cnt2 = j.unit_cnt2;
+    a.ulist = ulist;
+    a.ucount = ucount;
+    return launch_atm_fp32(j.trav, j.trunc, a, P.nwarps, P.smem, ctas, j.st);
+}
+
+bool atm_split_active(const ForceJob& j)
+{
+    return j.ncls > 1 && (j.trav == 1 || j.trav == 2 || j.trav == 4) && j.ulist && j.ucount &&
+           j.b.ncell > 0;
+}
+
+cudaError_t enqueue_atm(const ForceJob& j, size_t* smem_set, bool* capacity)
+{
+    *capacity = false;
+    {
+        // every launch's plan must fit before anything is enqueued
+        AtmPlan P;
+        const int limit = (j.trav == 0 || j.trav == 3) ? 65535 : ATM_MCAP_LIMIT;
+        if (j.mcap > limit || !atm_choose_plan(j.trav, j.trunc, j.prec, j.mcap, j.optin, P)) {
+            *capacity = true;
+            return cudaErrorInvalidValue;
+        }
+    }
+    cudaError_t e;
     if (j.trav != 0 && j.trav != 3 && j.b.ntot > 0) {  // owner traversals write every F_i
         e = cudaMemsetAsync(j.f_atm, 0, 3 * (size_t)j.b.ntot * sizeof(double), j.st);
         if (e != cudaSuccess) return e;
@@ -116,42 +179,22 @@ cudaError_t enqueue_atm(const ForceJob& j, size_t* smem_set, bool* capacity)
         e = cudaMemsetAsync(j.f_lj, 0, 3 * (size_t)j.b.ntot * sizeof(double), j.st);
         if (e != cudaSuccess) return e;
     }
-    int ctas = 0;
-    if (j.persistent && j.work) {
-        int per_sm = j.prec == 0 ? atm_occupancy_fp64(j.trav, j.trunc, P.nwarps, P.smem)
-                                 : atm_occupancy_fp32(j.trav, j.trunc, P.nwarps, P.smem);
-        ctas = std::max(1, per_sm) * std::max(1, j.sms);
-        e = cudaMemsetAsync(j.work, 0, sizeof(int), j.st);
+    if (!atm_split_active(j)) return launch_atm_one(j, smem_set, capacity, nullptr, nullptr, j.work);
+    e = launch_unit_classes(j.b, j.start, j.trav, j.ncls, j.cuts[0], j.cuts[1], j.ulist, j.ucount,
+                            j.st);
+    if (e != cudaSuccess) return e;
+    for (int k = 0; k < j.ncls; k++) {
+        ForceJob jk = j;
+        if (k < j.ncls - 1) {
+            jk.mcap = std::min(j.cuts[k], j.mcap);
+            if (j.cuts[k] <= 64) jk.nwarps = 4;
+        }
+        if (jk.mcap < 1) jk.mcap = 1;
+        e = launch_atm_one(jk, smem_set, capacity, j.ulist + (size_t)k * j.b.ncell, j.ucount + k,
+                           j.work ? j.work + k : nullptr);
         if (e != cudaSuccess) return e;
     }
-    if (j.prec == 0) {
-        AtmArgs<double> a{};
-        a.b = j.b; a.n = j.b.ntot; a.xl = j.xl; a.xl32 = j.xl32; a.cell_start = j.start;
-        a.fs = j.f_atm; a.unit_ew = j.unit_ew; a.unit_cnt = j.unit_cnt; a.status = j.status;
-        a.work = ctas > 0 ? j.work : nullptr;
-        a.mcap = j.mcap;
-        a.gcap = P.gcap;
-        a.use_d = P.use_d;
-        a.acc_mode = P.acc_mode;
-        a.pcap = P.pcap;
-        a.lj = lj;
-        a.unit_ew2 = j.unit_ew2;
-        a.unit_cnt2 = j.unit_cnt2;
-        return launch_atm_fp64(j.trav, j.trunc, a, P.nwarps, P.smem, ctas, j.st);
-    }
-    AtmArgs<float> a{};
-    a.b = j.b; a.n = j.b.ntot; a.xl = j.xl32; a.xl32 = j.xl32; a.cell_start = j.start;
-    a.fs = j.f_atm; a.unit_ew = j.unit_ew; a.unit_cnt = j.unit_cnt; a.status = j.status;
-    a.work = ctas > 0 ? j.work : nullptr;
-    a.mcap = j.mcap;
-    a.gcap = P.gcap;
-    a.use_d = P.use_d;
-    a.acc_mode = P.acc_mode;
-    a.pcap = P.pcap;
-    a.lj = lj;
-    a.unit_ew2 = j.unit_ew2;
-    a.unit_cnt2 = j.unit_cnt2;
-    return launch_atm_fp32(j.trav, j.trunc, a, P.nwarps, P.smem, ctas, j.st);
+    return cudaSuccess;
 }
 
 }  // namespace atm3

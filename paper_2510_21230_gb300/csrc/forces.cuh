@@ -44,10 +44,20 @@ struct ForceJob {
     int lj = 0;
     double* unit_ew2 = nullptr;
     unsigned long long* unit_cnt2 = nullptr;
+    // block traversals: unit size classes (ncls 2 or 3; 1 = none).  Units of
+    // at most cuts[0] (then cuts[1]) staged molecules run in launches sized for
+    // that bound (4 warps when it is at most 64), the rest in one sized for
+    // mcap; ulist [ncls * ncell], ucount [ncls] and work [ncls] are scratch
+    int ncls = 1;
+    int cuts[2] = {0, 0};
+    int* ulist = nullptr;
+    int* ucount = nullptr;
 };
 
 cudaError_t enqueue_lj(const ForceJob& j);
 // *capacity is set when no kernel configuration fits the unit size
 cudaError_t enqueue_atm(const ForceJob& j, size_t* smem_set, bool* capacity);
+// the job runs its units in size classes (one more kernel, ncls ATM launches)
+bool atm_split_active(const ForceJob& j);
 
 }  // namespace atm3

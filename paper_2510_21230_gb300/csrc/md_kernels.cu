@@ -163,6 +163,47 @@ __global__ void k_unit_max(Batch B, const int* __restrict__ start, int wide, int
     }
 }
 
+// Unit size classes of the block traversals: unit u (its base cell) holds
+// the molecules of its 8 cells (3c08, corner-anchored 3c08) or 14 cells
+// (3c18); it goes to the first class whose bound holds them (cut0, then cut1
+// when there are three classes; the last class takes the rest).  Class k is
+// listed in ulist[k * ncell ..] and counted in counts[k] (zero at launch).
+__global__ void k_unit_classes(Batch B, const int* __restrict__ start, int trav, int ncls,
+                               int cut0, int cut1, int* __restrict__ ulist,
+                               int* __restrict__ counts)
+{
+    const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    int cls = -1;
+    if (c < B.ncell) {
+        const Rep& rp = B.rep[B.rep_of_cell[c]];
+        const int* st = start + rp.cell0;
+        int cx, cy, cz;
+        cell_coords(rp.g, c - rp.cell0, cx, cy, cz);
+        int m = 0;
+        for (int t = 0; t < 27; t++) {
+            int dx, dy, dz;
+            offset27(t, dx, dy, dz);
+            if (trav == 1 ? t >= 13 : (dx >= 0 && dy >= 0 && dz >= 0)) {
+                const long long nc = cell_at(rp.g, cx, cy, cz, dx, dy, dz);
+                m += st[nc + 1] - st[nc];
+            }
+        }
+        cls = m <= cut0 ? 0 : ((ncls > 2 && m <= cut1) ? 1 : ncls - 1);
+    }
+    // one append per class and warp
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    for (int k = 0; k < ncls; k++) {
+        const unsigned mk = __ballot_sync(FULL, cls == k);
+        if (mk == 0u) continue;
+        const int lead = __ffs(mk) - 1;
+        int base = 0;
+        if (lane == lead) base = atomicAdd(counts + k, __popc(mk));
+        base = __shfl_sync(FULL, base, lead);
+        if (cls == k) ulist[k * B.ncell + base + __popc(mk & ((1u << lane) - 1u))] = (int)c;
+    }
+}
+
 // K3a: scatter by arrival rank
 __global__ void k_scatter(long long n, const int* __restrict__ cell_of, const int* __restrict__ rank,
                           const int* __restrict__ start, int* __restrict__ perm)
@@ -611,6 +652,16 @@ cudaError_t launch_build_cells(const Batch& b, double* x, int* cell_of, int* ran
         k_cell_order<<<(unsigned)((b.ncell + 3) / 4), 128, 0, st>>>(b, x, start, perm, xl, xl32,
                                                                   cell_sorted);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unit_classes(const Batch& b, const int* start, int trav, int ncls, int cut0,
+                                int cut1, int* ulist, int* counts, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(counts, 0, ncls * sizeof(int), st);
+    if (e != cudaSuccess || b.ncell <= 0) return e;
+    k_unit_classes<<<nblk(b.ncell, MD_BLOCK), MD_BLOCK, 0, st>>>(b, start, trav, ncls, cut0, cut1,
+                                                                  ulist, counts);
     return cudaGetLastError();
 }
 

@@ -63,14 +63,20 @@ cudaError_t launch_check_finite(long long m, const double* a, int* status, cudaS
 cudaError_t launch_final_reduce(const ReduceArgs& r, cudaStream_t st);
 cudaError_t launch_gather_forces(long long n, const int* perm, const double* f_lj,
                                  const double* f_atm, int which, double* out, cudaStream_t st);
-// adds the histogram of coordinate `axis` (nbins equal bins over [0, L_axis))
-// of every replica's wrapped positions to counts[R * nbins]
 // adds the pair-distance histogram (nbins equal bins over [0, rmax), every
 // pair once, rmax at most the smallest cell edge) of every replica to
 // counts[R * nbins]
 cudaError_t launch_rdf(const Batch& b, const double* xl, const int* start, const int* cell_sorted,
                        double rmax, int nbins, unsigned long long* counts, cudaStream_t st);
+// adds the histogram of coordinate `axis` (nbins equal bins over [0, L_axis))
+// of every replica's wrapped positions to counts[R * nbins]
 cudaError_t launch_density(const Batch& b, const double* x, int axis, int nbins,
                            unsigned long long* counts, cudaStream_t st);
+// unit size classes of a block traversal (trav 1, 2 or 4) on built cells:
+// zeroes counts[ncls], then lists the units of class k (staged molecules
+// <= cut0, <= cut1 with three classes, the rest last) in ulist[k * ncell ..]
+// and counts them in counts[k]
+cudaError_t launch_unit_classes(const Batch& b, const int* start, int trav, int ncls, int cut0,
+                                int cut1, int* ulist, int* counts, cudaStream_t st);
 
 }  // namespace atm3

@@ -29,7 +29,7 @@ def test_library_builds_and_exports_every_declared_symbol():
     for name in sorted(declared):
         assert hasattr(lib, name), name
     assert set(atm3.EXPORTED) <= declared
-    assert atm3.load().atm_abi_version() == 1
+    assert atm3.load().atm_abi_version() == 2
 
 
 def test_invalid_arguments_are_rejected_without_a_gpu():

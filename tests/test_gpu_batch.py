@@ -182,3 +182,91 @@ def test_contexts_of_different_unit_sizes_interleave(atm3):
         for _ in range(2):
             a.step(3, "3c08", "pair", "fp32c")
             b.step(3, "3c08", "pair", "fp32c")
+
+
+def _unit_sizes(rep, trav):
+    """Staged molecules of every unit of one replica (8 cells of the 2x2x2
+    block for 3c08 / 3c08a, the base cell and its 13 forward neighbours for
+    3c18), from the cell counts."""
+    box = np.broadcast_to(np.asarray(rep["box"], dtype=np.float64), (3,))
+    nc = np.floor(box / 2.5).astype(int)
+    w = box / nc
+    ci = np.floor(np.mod(rep["x"].T, box) / w).astype(int) % nc
+    cnt = np.bincount((ci[:, 0] * nc[1] + ci[:, 1]) * nc[2] + ci[:, 2],
+                      minlength=int(np.prod(nc))).reshape(tuple(nc))
+    if trav == "3c18":
+        offs = [(0, 0, 0)] + [o for o in np.ndindex(3, 3, 3)
+                              if (o[0] - 1, o[1] - 1, o[2] - 1) > (0, 0, 0)]
+        offs = [(0, 0, 0)] + [(a - 1, b - 1, c - 1) for a, b, c in offs[1:]]
+    else:
+        offs = [(a, b, c) for a in (0, 1) for b in (0, 1) for c in (0, 1)]
+    return sum(np.roll(cnt, (-a, -b, -c), axis=(0, 1, 2)) for a, b, c in offs).ravel()
+
+
+@pytest.mark.parametrize("trav,trunc,prec", [("3c08", "pair", "fp32c"), ("3c08", "pair", "fp64"),
+                                             ("3c18", "pair", "fp32c"), ("3c08a", "pair", "fp32c"),
+                                             ("3c08", "product", "fp32c"),
+                                             ("3c18", "product", "fp64")])
+def test_unit_size_classes_equal_one_launch(atm3, ensemble, trav, trunc, prec):
+    """Units run in size classes (2 or 3 launches with their own shared-memory
+    plans) give the one-launch results: counts exactly, energies and forces to
+    rounding (FP64: the order of the additions; FP32C: also the warps and
+    pair-scalar tables of the class plans, within the parity tolerance).  The
+    bounds are chosen from the ensemble's unit sizes so that every class
+    holds units."""
+    ns = [r["n"] for r in ensemble]
+    sizes = np.concatenate([_unit_sizes(r, trav) for r in ensemble])
+    q = [int(np.percentile(sizes, p)) for p in (30, 70)]
+    assert sizes.min() <= q[0] < q[1] < sizes.max()
+    with atm3.AtmSystem([r["box"] for r in ensemble], ns, nu=NU) as b:
+        b.set_state(_concat(ensemble, "x"))
+        b.build_cells()
+        b.compute_forces(trav, trunc, prec)
+        ref = b.results()
+        fref = b.get_forces("atm")
+        for cuts in ((q[0],), (q[0], q[1]), (64,), (48, 96)):
+            b.set_unit_classes(cuts)
+            b.compute_forces(trav, trunc, prec)
+            got = b.results()
+            f = b.get_forces("atm")
+            tol = 1e-12 if prec == "fp64" else RTOL["fp32c"]
+            for a, c in zip(ref, got):
+                assert a["n_int3"] == c["n_int3"] and a["n_cand3"] == c["n_cand3"]
+                assert c["e3"] == pytest.approx(a["e3"], rel=tol, abs=1e-12)
+                assert c["w3"] == pytest.approx(a["w3"], rel=tol, abs=1e-12)
+            assert close(f, fref, 1e-10 if prec == "fp64" else RTOL["fp32c"])
+        b.set_unit_classes(())
+        b.compute_forces(trav, trunc, prec)
+        assert [r["n_int3"] for r in b.results()] == [r["n_int3"] for r in ref]
+
+
+def test_unit_size_classes_in_graph_steps(atm3, ensemble):
+    """Graph steps with three size classes follow the one-launch steps."""
+    ns = [r["n"] for r in ensemble]
+    boxes = [r["box"] for r in ensemble]
+    x, v = _concat(ensemble, "x"), _concat(ensemble, "v")
+    sizes = np.concatenate([_unit_sizes(r, "3c08") for r in ensemble])
+    cuts = (int(np.percentile(sizes, 30)), int(np.percentile(sizes, 70)))
+    out = []
+    for classes in ((), cuts):
+        with atm3.AtmSystem(boxes, ns, nu=NU, dt=0.002) as b:
+            b.set_state(x, v)
+            b.set_options(graph=True)
+            b.set_unit_classes(classes)
+            b.step(20, "3c08", "pair", "fp64")
+            out.append((b.results(), b.get_state()))
+    (ra, (xa, va)), (rb, (xb, vb)) = out
+    for a, c in zip(ra, rb):
+        assert a["n_int3"] == c["n_int3"]
+        assert c["e3"] == pytest.approx(a["e3"], rel=1e-9)
+    assert np.abs(xa - xb).max() < 1e-10 and np.abs(va - vb).max() < 1e-9
+
+
+def test_unit_size_class_arguments(atm3, ensemble):
+    ns = [r["n"] for r in ensemble]
+    with atm3.AtmSystem([r["box"] for r in ensemble], ns, nu=NU) as b:
+        for bad in ((0,), (64, 32), (64, 64), (10, 20, 30), (4096,)):
+            with pytest.raises(atm3.AtmError):
+                b.set_unit_classes(bad)
+        b.set_unit_classes((40,))
+        b.set_unit_classes(())
