@@ -60,15 +60,15 @@ FUSED_TRAV = ("3c08", "3c08a")
 # liquid_n256k is the N = 32,000 capture (2197 units) scaled to 19683 units.
 KERNEL_SOURCES = ["atm3_internal.cuh", "atm_common.cuh", "atm_block.cuh", "atm_owner.cuh",
                   "atm_fp32.cu", "atm_fp64.cu"]
-TRAFFIC = {("3c08", "pair", "fp32c", "liquid_n256k"): (11.56e6, "755339e4fb24ee31"),
-           ("3c08", "pair", "fp32c", "liquid_n32k"): (1.290e6, "755339e4fb24ee31")}
+TRAFFIC = {("3c08", "pair", "fp32c", "liquid_n256k"): (11.56e6, "3d76bb026207b270"),
+           ("3c08", "pair", "fp32c", "liquid_n32k"): (1.291e6, "3d76bb026207b270")}
 
 
 # Issued FP32 flops (fadd + fmul + 2 ffma thread instructions of the ATM
 # kernel, from the same ncu capture) over the useful flops of that launch,
 # with the source hash they belong to: what candidates and bookkeeping add
 # in floating point.
-ISSUED = {("3c08", "pair", "fp32c"): (1.233, "755339e4fb24ee31")}
+ISSUED = {("3c08", "pair", "fp32c"): (1.233, "3d76bb026207b270")}
 
 
 def kernel_hash():
@@ -526,8 +526,9 @@ def batch_variant(atm3, device, stream, flush, count=64, steps=10, warmup=5):
                         stream=stream.cuda_stream) as b:
         b.set_state(x, v)
         b.build_cells()
-        tuning = b.autotune("3c08", "pair", "fp32c", reps=3)
+        # options first: setting them resets an autotuned choice
         b.set_options(graph=True)
+        tuning = b.autotune("3c08", "pair", "fp32c", reps=3)
         b.step(warmup, "3c08", "pair", "fp32c")
         torch.cuda.synchronize()
         evs = []
