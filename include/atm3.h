@@ -215,7 +215,7 @@ atm_status atm_set_options(atm_ctx* ctx, int persistent, int nwarps, int graph);
  * every force evaluation first lists, on the device, the units of at most
  * cuts[0] staged molecules, then (nclass = 3) those of at most cuts[1], then
  * the rest, and launches the block kernel once per class with shared memory
- * sized for the class bound (4 warps when it is at most 64): small units of
+ * sized for the class bound (2 warps when it is at most 64): small units of
  * a batch of uneven replicas then share an SM with more of their kind.
  * Results are those of one launch (energies and counts per unit are the
  * same; forces differ by the order of their FP64 atomic additions).  cuts
@@ -236,7 +236,7 @@ typedef struct {
  * for 3C18/3C08/3C08A also unit size classes: {all}, {<= 64, rest},
  * {<= 48, <= 96, rest}, {<= 64, <= 128, rest}, where every force evaluation
  * sorts the units by their staged molecules on the device and launches each
- * class with shared memory sized for its bound, 4 warps for bounds up to 64)
+ * class with shared memory sized for its bound, 2 warps for bounds up to 64)
  * and keeps the fastest for this (trav, trunc, prec); later evaluations and
  * steps use it.  Cells must be built.  out may be NULL.
  * Errors: INVALID, STATE, CAPACITY, CUDA. */

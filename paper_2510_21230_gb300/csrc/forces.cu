@@ -98,7 +98,7 @@ static cudaError_t launch_atm_one(const ForceJob& j, size_t* smem_set, bool* cap
         *capacity = true;
         return cudaErrorInvalidValue;
     }
-    if ((j.nwarps == 4 || j.nwarps == 8) && j.trav != 0 && j.trav != 3) {
+    if ((j.nwarps == 2 || j.nwarps == 4 || j.nwarps == 8) && j.trav != 0 && j.trav != 3) {
         AtmPlan Q;
         if (atm_choose_plan_nw(j.trav, j.trunc, j.prec, j.mcap, j.optin, j.nwarps, Q)) P = Q;
     }
@@ -187,7 +187,10 @@ cudaError_t enqueue_atm(const ForceJob& j, size_t* smem_set, bool* capacity)
         ForceJob jk = j;
         if (k < j.ncls - 1) {
             jk.mcap = std::min(j.cuts[k], j.mcap);
-            if (j.cuts[k] <= 64) jk.nwarps = 4;
+            // small units: short phases between the CTA's barriers, so few
+            // warps (64-molecule bound: 2 warps measured best on a batch of
+            // 64 uneven replicas, against 1 and 4)
+            if (j.cuts[k] <= 64) jk.nwarps = 2;
         }
         if (jk.mcap < 1) jk.mcap = 1;
         e = launch_atm_one(jk, smem_set, capacity, j.ulist + (size_t)k * j.b.ncell, j.ucount + k,

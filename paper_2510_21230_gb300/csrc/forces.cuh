@@ -46,7 +46,7 @@ struct ForceJob {
     unsigned long long* unit_cnt2 = nullptr;
     // block traversals: unit size classes (ncls 2 or 3; 1 = none).  Units of
     // at most cuts[0] (then cuts[1]) staged molecules run in launches sized for
-    // that bound (4 warps when it is at most 64), the rest in one sized for
+    // that bound (2 warps when it is at most 64), the rest in one sized for
     // mcap; ulist [ncls * ncell], ucount [ncls] and work [ncls] are scratch
     int ncls = 1;
     int cuts[2] = {0, 0};
