@@ -319,14 +319,22 @@ static void invalidate(atm_ctx* c)
 // copies m doubles from host memory to dev and checks them for NaN / Inf on
 // the device (the copy's data, one pass); synchronises, so the caller may
 // reuse its buffer on return.  *bad: a non-finite element was found
-static atm_status copy_in_checked(atm_ctx* c, double* dev, const double* host, long long m, bool* bad)
+// copies host arrays (a, and b when given, m doubles each) to the device,
+// checks them for non-finite values there and waits once for the verdict
+static atm_status copy_in_checked(atm_ctx* c, double* dev_a, const double* host_a, double* dev_b,
+                                  const double* host_b, long long m, bool* bad)
 {
     *bad = false;
     if (m <= 0) return ATM_OK;
-    CU(cudaMemcpyAsync(dev, host, (size_t)m * sizeof(double), cudaMemcpyHostToDevice, c->st));
     CU(cudaMemsetAsync(c->d_chk, 0, sizeof(int), c->st));
-    CU(launch_check_finite(m, dev, c->d_chk, c->st));
+    CU(cudaMemcpyAsync(dev_a, host_a, (size_t)m * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    CU(launch_check_finite(m, dev_a, c->d_chk, c->st));
     c->n_launch += 1;
+    if (host_b) {
+        CU(cudaMemcpyAsync(dev_b, host_b, (size_t)m * sizeof(double), cudaMemcpyHostToDevice, c->st));
+        CU(launch_check_finite(m, dev_b, c->d_chk, c->st));
+        c->n_launch += 1;
+    }
     CU(cudaMemcpyAsync(c->h_chk, c->d_chk, sizeof(int), cudaMemcpyDeviceToHost, c->st));
     CU(cudaStreamSynchronize(c->st));
     *bad = *c->h_chk != 0;
@@ -339,18 +347,13 @@ extern "C" atm_status atm_set_state(atm_ctx* c, const double* x, const double* v
     if (!x && c->n > 0) return ctx_fail(c, ATM_E_INVALID, "positions are required");
     CU(cudaSetDevice(c->device));
     const long long m = 3 * c->n;
-    bool bx = false, bv = false;
-    atm_status s = copy_in_checked(c, c->x, x, m, &bx);
+    bool bad = false;
+    if (!v && m > 0) CU(cudaMemsetAsync(c->v, 0, (size_t)m * sizeof(double), c->st));
+    atm_status s = copy_in_checked(c, c->x, x, c->v, v, m, &bad);
     if (s != ATM_OK) return s;
-    if (v) {
-        s = copy_in_checked(c, c->v, v, m, &bv);
-        if (s != ATM_OK) return s;
-    } else if (m > 0) {
-        CU(cudaMemsetAsync(c->v, 0, (size_t)m * sizeof(double), c->st));
-    }
-    c->have_x = !(bx || bv);
+    c->have_x = !bad;
     invalidate(c);
-    if (bx || bv) {
+    if (bad) {
         long long q = 0;
         while (q < m && std::isfinite(x[q]) && (!v || std::isfinite(v[q]))) q++;
         return ctx_fail(c, ATM_E_NONFINITE, "non-finite input at element %lld", q);
@@ -983,7 +986,7 @@ extern "C" atm_status atm_set_forces(atm_ctx* c, const double* f, atm_traversal 
     if (!c->have_x) return ctx_fail(c, ATM_E_STATE, "set the state before its forces");
     CU(cudaSetDevice(c->device));
     bool bad = false;
-    atm_status s = copy_in_checked(c, c->f_in, f, 3 * c->n, &bad);
+    atm_status s = copy_in_checked(c, c->f_in, f, nullptr, nullptr, 3 * c->n, &bad);
     if (s != ATM_OK) return s;
     if (bad) {
         c->f_in_valid = false;
