@@ -257,6 +257,25 @@ def test_large_units_product_rule(atm3, trav, prec):
 
 @pytest.mark.parametrize("trav", ["3c18", "3c08", "3c08a"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_product_rule_at_the_256k_cell_edge(atm3, trav, prec):
+    """The cell edge of the 256,000-molecule liquid (2.53 sigma, about 13
+    molecules per cell; here 829 molecules, 4 cells per axis): the product
+    rule's dense distance and pair-scalar tables fit shared memory, 3c18's
+    units (up to 199 molecules) leave one CTA per SM and run 16 warps in FP32,
+    3c08's (up to 117) run 8 warps -- the plans the benchmark times, with the
+    candidate tasks spanning row ends and several rows."""
+    cfg = synth.homogeneous(829, 0.8, 1.0, seed=1003)
+    prm = oracle.params(cfg["box"], 2.5, NU)
+    ref = oracle.atm_cells(prm, cfg["x"], trav, "product", ORC_PREC[prec])
+    r, f, _, _ = run_gpu(atm3, cfg, trav, "product", prec)
+    assert r["n_cand3"] == ref["n_cand3"] and r["n_int3"] == ref["n_int3"]
+    assert r["e3"] == pytest.approx(ref["e3"], rel=RTOL[prec])
+    assert r["w3"] == pytest.approx(ref["w3"], rel=RTOL[prec])
+    assert_forces_close(f, ref["f"], RTOL[prec], "256k cell edge " + trav + prec)
+
+
+@pytest.mark.parametrize("trav", ["3c18", "3c08", "3c08a"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
 def test_dense_liquid_edge_table_overflow(atm3, trav, prec):
     """At rho* = 1.4 units have more pair-rule edges than the per-unit edge table
     holds and fall back to per-molecule accumulators; results are unchanged."""
