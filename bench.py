@@ -15,7 +15,6 @@ by rank); there is no data-path collective ("replicas only", weak scaling).
 """
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess

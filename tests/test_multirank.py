@@ -4,7 +4,6 @@ ranks.  Its host-side logic runs here as two gloo ranks on the CPU."""
 import os
 import socket
 
-import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
