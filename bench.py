@@ -90,7 +90,7 @@ def traffic_for(trav, trunc, prec, workload):
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--steps", type=int, default=300)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="liquid_n256k", choices=sorted(synth.CONFIGS))
@@ -190,6 +190,7 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.path = None
+        self.offset = 0
 
     def start(self):
         try:
@@ -198,10 +199,15 @@ class ClockSampler:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=self.fh, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+
+    def mark(self):
+        """Only samples written after this call count (the timed region starts)."""
+        if self.proc is not None:
+            self.offset = os.path.getsize(self.path)
 
     def stop(self):
         if self.proc is None:
@@ -214,6 +220,7 @@ class ClockSampler:
         self.fh.close()
         sm, smax, reasons = [], [], set()
         with open(self.path) as fh:
+            fh.seek(self.offset)
             for line in fh:
                 parts = [t.strip() for t in line.split(",")]
                 if len(parts) < 9:
@@ -275,6 +282,7 @@ def run_ours(args):
         if clocks:
             clocks.start()
             time.sleep(0.3)
+            clocks.mark()
         evs = []
         t_host = time.perf_counter()
         for _ in range(steps):
@@ -829,12 +837,18 @@ def run_reference(args):
     cells = oracle.build_cells(prm, cfg["x"])
     occ = np.diff(cells["cell_start"])
     ncell = len(occ)
-    # size one step's sample to about 4 s of CPU work
-    u = 16
-    t0 = time.perf_counter()
-    oracle.atm_cells(prm, cfg["x"], args.trav, args.trunc, "fp64", 0, u)
-    t = time.perf_counter() - t0
-    units = int(min(ncell, max(u, 4.0 / max(t / u, 1e-9))))
+    # size one step's sample to about 4 s of CPU work, less when there are
+    # many steps, so that the whole run stays near two minutes
+    per_step_s = min(4.0, 120.0 / max(1, args.steps))
+    # the cost of one unit from two sample sizes (a call also bins all
+    # molecules into cells, a fixed cost the difference cancels)
+    ts = []
+    for hi in (min(16, ncell), min(272, ncell)):
+        t0 = time.perf_counter()
+        oracle.atm_cells(prm, cfg["x"], args.trav, args.trunc, "fp64", 0, hi)
+        ts.append(time.perf_counter() - t0)
+    per_unit = max((ts[1] - ts[0]) / max(1, min(272, ncell) - min(16, ncell)), 1e-9)
+    units = int(min(ncell, max(16, per_step_s / per_unit)))
     for _ in range(args.warmup if args.warmup < 2 else 1):
         oracle.atm_cells(prm, cfg["x"], args.trav, args.trunc, "fp64", 0, min(units, 16))
     total, mol = 0.0, 0
