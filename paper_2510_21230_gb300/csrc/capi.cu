@@ -123,6 +123,9 @@ static void free_all(atm_ctx* c)
     if (c->h_chk) cudaFreeHost(c->h_chk);
     if (c->h_maxocc) cudaFreeHost(c->h_maxocc);
     if (c->cap_st) cudaStreamDestroy(c->cap_st);
+    if (c->side_st) cudaStreamDestroy(c->side_st);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     for (auto& r : c->ev_live) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -246,6 +249,9 @@ extern "C" atm_status atm_batch_create(const atm_params* params, const int64_t* 
     ok = ok && cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device) ==
                    cudaSuccess;
     ok = ok && cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking) == cudaSuccess;
+    ok = ok && cudaStreamCreateWithFlags(&c->side_st, cudaStreamNonBlocking) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) == cudaSuccess;
     if (ok) {
         std::vector<int> roc(NC), rom(N, 0);
         for (int r = 0; r < nrep; r++) {
@@ -512,6 +518,9 @@ atm_status atm3::ctx_enqueue_forces(atm_ctx* c, int trav, int trunc, int prec, i
     j.ulist = c->d_ulist;
     j.ucount = c->d_ucount;
     j.st = c->st;
+    j.side_st = c->side_st;
+    j.ev_fork = c->ev_fork;
+    j.ev_join = c->ev_join;
 
     cudaEvent_t ev;
     if (prec != ATM_SURROGATE && !fused) {

@@ -88,6 +88,10 @@ struct atm_ctx {
     int tuned[2][atm3::ATM_NTRAV][2] = {};
     // graph of one step, valid for (trav, trunc, prec, mcap, launch choice)
     cudaStream_t cap_st = nullptr;
+    // size classes: the small-unit class runs on side_st beside the rest
+    // (forked from and joined to the context's stream by the two events)
+    cudaStream_t side_st = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaGraphExec_t graph = nullptr;
     int graph_key[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
     // profiling: event pairs around launch groups, summed per kind

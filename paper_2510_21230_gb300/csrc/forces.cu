@@ -183,8 +183,17 @@ cudaError_t enqueue_atm(const ForceJob& j, size_t* smem_set, bool* capacity)
     e = launch_unit_classes(j.b, j.start, j.trav, j.ncls, j.cuts[0], j.cuts[1], j.ulist, j.ucount,
                             j.st);
     if (e != cudaSuccess) return e;
+    // the small-unit class on the side stream, beside the others: its CTAs
+    // fill the SMs the larger units' launch leaves idle in its tail
+    const bool side = j.side_st && j.ev_fork && j.ev_join;
+    if (side) {
+        e = cudaEventRecord(j.ev_fork, j.st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(j.side_st, j.ev_fork, 0);
+        if (e != cudaSuccess) return e;
+    }
     for (int k = 0; k < j.ncls; k++) {
         ForceJob jk = j;
+        if (side && k == 0) jk.st = j.side_st;
         if (k < j.ncls - 1) {
             jk.mcap = std::min(j.cuts[k], j.mcap);
             // small units: short phases between the CTA's barriers, so few
@@ -197,7 +206,11 @@ cudaError_t enqueue_atm(const ForceJob& j, size_t* smem_set, bool* capacity)
                            j.work ? j.work + k : nullptr);
         if (e != cudaSuccess) return e;
     }
-    return cudaSuccess;
+    if (side) {
+        e = cudaEventRecord(j.ev_join, j.side_st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(j.st, j.ev_join, 0);
+    }
+    return e;
 }
 
 }  // namespace atm3

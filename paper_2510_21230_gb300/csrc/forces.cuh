@@ -52,6 +52,10 @@ struct ForceJob {
     int cuts[2] = {0, 0};
     int* ulist = nullptr;
     int* ucount = nullptr;
+    // with a side stream the first class runs on it, forked from st after the
+    // class kernel and joined back before the evaluation ends
+    cudaStream_t side_st = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 cudaError_t enqueue_lj(const ForceJob& j);
