@@ -216,9 +216,12 @@ atm_status atm_set_options(atm_ctx* ctx, int persistent, int nwarps, int graph);
  * cuts[0] staged molecules, then (nclass = 3) those of at most cuts[1], then
  * the rest, and launches the block kernel once per class with shared memory
  * sized for the class bound (2 warps when it is at most 64): small units of
- * a batch of uneven replicas then share an SM with more of their kind.
- * Results are those of one launch (energies and counts per unit are the
- * same; forces differ by the order of their FP64 atomic additions).  cuts
+ * a batch of uneven replicas then share an SM with more of their kind.  The
+ * first class runs on a stream the context owns, forked from the context's
+ * stream after the sorting kernel and joined back before the evaluation
+ * ends, so later work on the context's stream sees its results.  Counts are
+ * those of one launch; energies and forces agree with it to rounding (the
+ * class plans' warps and tables change the order of the additions).  cuts
  * (host, nclass - 1 values) must rise within 1 .. 2047.  Resets any
  * autotuned choice.  Errors: INVALID. */
 atm_status atm_set_unit_classes(atm_ctx* ctx, int nclass, const int* cuts);
