@@ -94,9 +94,9 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="liquid_n256k", choices=sorted(synth.CONFIGS))
-    p.add_argument("--trav", default="3c08", choices=["3c01", "3c18", "3c08"])
+    p.add_argument("--trav", default="3c08", choices=["3c01", "3c18", "3c08", "3c08a", "3cw"])
     p.add_argument("--trunc", default="pair", choices=["pair", "product"])
-    p.add_argument("--prec", default="fp32c", choices=["fp64", "fp32c"])
+    p.add_argument("--prec", default="fp32c", choices=["fp64", "fp32c", "surrogate"])
     p.add_argument("--no-variants", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -107,6 +107,17 @@ def parse():
     p.add_argument("--sur-stride", type=int, default=10, help="MD steps between frames")
     p.add_argument("--sur-steps", type=int, default=20000, help="Adam steps")
     p.add_argument("--sur-batch", type=int, default=8192, help="rows per Adam step")
+    p.add_argument("--paper-table", action="store_true",
+                   help="also time the paper's own runtime workload (context only)")
+    p.add_argument("--kernel-case", action="store_true",
+                   help="only time repeated force evaluations of one combination (a small "
+                        "driver for profilers: cell build, LJ and the chosen ATM or surrogate "
+                        "kernel) and print their CUDA-event time")
+    p.add_argument("--n", type=int, default=0,
+                   help="--kernel-case: a liquid of N molecules at rho 0.8 instead of the "
+                        "workload (N = 104052 has the cell edge of the 256,000 liquid)")
+    p.add_argument("--reps", type=int, default=3, help="--kernel-case: evaluations per timing")
+    p.add_argument("--nwarps", type=int, default=0, help="--kernel-case: warps per CTA")
     return p.parse_args()
 
 
@@ -158,7 +169,7 @@ KICK_BYTES_PER_MOL = 2 * (24 + 24 + 24 + 24 + 8 + 4) + (24 + 24)
 
 def ncell_of(cfg):
     from paper_2510_21230_gb300 import atm3
-    return atm3.cell_count(cfg["box"], RC)
+    return int(np.prod(atm3.cell_grid(cfg["box"], RC)))
 
 
 def kernel_rooflines(prof, steps, n, ncell, atm_roof, pk):
@@ -253,7 +264,8 @@ def run_ours(args):
     torch.cuda.set_device(local)
     if ws > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    if rank == 0 or ws > 1:
+    # one build per node (ranks of a node share the build folder), then all load it
+    if local == 0:
         build.build()
     if ws > 1:
         dist.barrier()
@@ -318,19 +330,28 @@ def run_ours(args):
     pk = peaks()
     sm_max = pk.get("sm_max_mhz", 2070.0)
     per_clk = FP32_FLOPS_PER_CLK_SM if args.prec == "fp32c" else FP64_FLOPS_PER_CLK_SM
-    peak = SMS * per_clk * sm_max * 1e6 / 1e12
+    derived = SMS * per_clk * sm_max * 1e6 / 1e12
+    # the roof is the device's measured FMA throughput in the path's precision
+    # (independent FMA chains on every SM, same clocks, this run)
+    measured = atm3.measure_fma_peak(local, args.prec == "fp64")
+    peak = measured if measured and measured > 0 else derived
     achieved = flops / (atm_ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
                 "traffic": traffic_for(args.trav, args.trunc, args.prec, args.workload),
                 "kernel": ("atm_owner_kernel<%s,%s,%s>" if args.trav == "3c01" else "atm_block_kernel<%s,%s,%s>") % (args.trav, args.trunc, args.prec)
                           + (" (LJ of the c08 pairs inside)" if fused else ""),
-                "peak_source": "derived: %d SMs x %.2f flops/clk x %.0f MHz (%s pipe)"
-                               % (SMS, per_clk, sm_max, "FP32" if args.prec == "fp32c" else "FP64"),
+                "peak_source": ("measured: atm_measure_fma_peak, %s FMA chains on every SM"
+                                % ("FP32" if args.prec == "fp32c" else "FP64"))
+                               if peak == measured else "derived (measurement failed)",
+                "derived_peak_tflops": derived,
+                "derived_peak_source": "%d SMs x %.2f flops/clk x %.0f MHz (%s pipe)"
+                                       % (SMS, per_clk, sm_max,
+                                          "FP32" if args.prec == "fp32c" else "FP64, nominal"),
                 "flops_per_interacting_triplet": F3[args.trav],
                 "flops_per_interacting_pair": F2_FUSED if fused else None,
                 "ms_per_launch": atm_ms,
-                "measured_fma_peak_tflops": atm3.measure_fma_peak(local, args.prec == "fp64"),
+                "measured_fma_peak_tflops": measured,
                 "measured_rsqrt_peak_gops": atm3.measure_rsqrt_peak(local),
                 "rsqrt_per_s_needed_gops": main["res"]["n_int3"] / (atm_ms * 1e-3) / 1e9}
     tr = roofline["traffic"]
@@ -406,7 +427,7 @@ def run_ours(args):
     # the paper's own runtime workload (its node-level table): all six
     # traversal / truncation combinations, three-body force time only
     paper_table = None
-    if not args.no_variants and rank == 0:
+    if args.paper_table and rank == 0:
         paper_table = paper_table_variant(atm3, local, stream)
 
     # learned surrogate: trained on exact forces of smaller liquids, then
@@ -878,8 +899,55 @@ def run_reference(args):
     return line
 
 
+def kernel_case(args):
+    """Repeated force evaluations of one (traversal, truncation, precision) on
+    a workload, with their CUDA-event time and the ATM kernel's own time from
+    the library's launch profiler.  With --prec surrogate the model is random
+    (seeded) with the descriptor normalisation of the workload's descriptors."""
+    import torch
+
+    from paper_2510_21230_gb300 import atm3, build
+    build.build()
+    cfg = synth.homogeneous(args.n, 0.8, 1.0, seed=7000) if args.n > 0 else synth.config(args.workload)
+    name = "liquid_n%d" % args.n if args.n > 0 else args.workload
+    stream = torch.cuda.current_stream()
+    with atm3.AtmSystem(cfg["box"], cfg["n"], rc=RC, nu=NU, stream=stream.cuda_stream) as s:
+        s.set_state(cfg["x"], cfg["v"])
+        s.build_cells()
+        if args.prec == "surrogate":
+            D, _ = s.surrogate_descriptors()
+            sd = D.std(axis=0)
+            s.surrogate_set_model(synth.sur_params(7), D.mean(axis=0),
+                                  np.where(sd > 1e-12, sd, 1.0).astype(np.float32))
+        if args.nwarps:
+            s.set_options(nwarps=args.nwarps)
+        s.compute_forces(args.trav, args.trunc, args.prec)
+        torch.cuda.synchronize()
+        s.set_profiling(True)
+        times = []
+        for _ in range(3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.reps):
+                s.compute_forces(args.trav, args.trunc, args.prec, sync=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) / args.reps)
+        r = s.results()[0]
+        prof = s.get_profile()
+    atm = prof["ms_atm"] / max(1, prof["n_atm_launches"])
+    print(json.dumps({"kernel_case": name, "traversal": args.trav, "truncation": args.trunc,
+                      "precision": args.prec, "ms_per_evaluation": sorted(times)[1],
+                      "atm_ms_per_launch": atm, "n_int3": int(r["n_int3"]),
+                      "note": "median of 3 x %d evaluations, cell build excluded" % args.reps}))
+
+
 def main():
     args = parse()
+    if args.kernel_case:
+        kernel_case(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -32,7 +32,7 @@
 extern "C" {
 #endif
 
-#define ATM3_ABI_VERSION 2
+#define ATM3_ABI_VERSION 3
 
 typedef enum {
     ATM_OK = 0,
@@ -194,6 +194,15 @@ atm_status atm_step(atm_ctx* ctx, int nsteps, atm_traversal trav, atm_truncation
 atm_status atm_batch_create(const atm_params* params, const int64_t* n, int nrep, atm_ctx** out);
 /* Number of replicas and total molecules. */
 atm_status atm_batch_size(const atm_ctx* ctx, int* nrep, int64_t* ntot);
+/* Total cells of all replicas (the length of atm_get_cells' cell_start is
+ * this + 1).  Errors: INVALID (NULL). */
+atm_status atm_batch_cells(const atm_ctx* ctx, int64_t* ncell);
+
+/* The linked-cell grid of one system (paper section 3, the cell-edge rule
+ * above): ncell3[3] receives n_x, n_y, n_z.  Host arithmetic, no device.
+ * Errors: INVALID (NULL, non-positive or non-finite box or rc),
+ * BOX_TOO_SMALL (fewer than 3 cells along some axis). */
+atm_status atm_cell_grid(const atm_params* params, int32_t* ncell3);
 /* Scalars of the last evaluation for every replica: out[nrep] (synchronises).
  * (atm_compute_forces / atm_step return replica 0's.) */
 atm_status atm_get_results(atm_ctx* ctx, atm_result* out);
@@ -275,13 +284,20 @@ atm_status atm_density_reset(atm_ctx* ctx);
  *   f_dev   [3n] device output: total LJ + ATM force in the caller's order
  *   out     host scalars of the evaluation (ekin = 0), may be NULL
  *
- * Errors: INVALID (NULL pointer, bad enum, device index >= 64), BOX_TOO_SMALL,
- * CAPACITY (n > ATM_NOALLOC_MAX_N, more than ATM_NOALLOC_MAX_CELLS cells, or a
- * unit that does not fit shared memory), NONFINITE, CUDA.  There is no context,
- * so no message: the status code is the error.
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  The call synchronises params.cuda_stream.  All
+ * Accepted: traversals ATM_3C01, ATM_3C18, ATM_3C08 and ATM_3C08A with either
+ * truncation, precisions ATM_FP64 and ATM_FP32C.  ATM_3CW and ATM_SURROGATE
+ * return INVALID (the wide traversal's 5^3 unit sizes and the surrogate's
+ * model live in a context).
+ * Errors: INVALID (NULL pointer, unknown enum, ATM_3CW, ATM_SURROGATE, device
+ * index >= 64), BOX_TOO_SMALL, CAPACITY (n > ATM_NOALLOC_MAX_N, more than
+ * ATM_NOALLOC_MAX_CELLS cells, or a unit that does not fit shared memory),
+ * NONFINITE, CUDA.  There is no context, so no message: the status code is
+ * the error.
+ * The call makes params.device current while it runs and restores the
+ * caller's current device before it returns.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress, with that device
+ * current); make that first call before any stream capture.  The call
+ * synchronises params.cuda_stream.  All
  * calls share the one array and leave their data in it (what must start at
  * zero is cleared on every call); calls whose GPU work overlaps -- on two
  * streams, or from two host threads -- race on it and must be serialised by

@@ -23,7 +23,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "box smaller than three cells", 3: 
           4: "device wait timed out", 5: "non-finite input", 6: "call out of order",
           7: "capacity exceeded"}
 
-ABI_VERSION = 2  # ATM3_ABI_VERSION of include/atm3.h
+ABI_VERSION = 3  # ATM3_ABI_VERSION of include/atm3.h
 EXPORTED = ["atm_abi_version", "atm_create", "atm_batch_create", "atm_batch_size", "atm_destroy",
             "atm_last_error", "atm_set_state", "atm_set_state_dev", "atm_build_cells",
             "atm_get_cells", "atm_compute_forces", "atm_get_results", "atm_get_forces",
@@ -37,7 +37,7 @@ EXPORTED = ["atm_abi_version", "atm_create", "atm_batch_create", "atm_batch_size
             "atm_surrogate_train", "atm_surrogate_options", "atm_surrogate_error",
             "atm_measure_fma_peak", "atm_rdf_accumulate", "atm_rdf_get", "atm_rdf_reset",
             "atm_lj_tail", "atm_thermostat", "atm_measure_rsqrt_peak", "atm_set_forces",
-            "atm_set_unit_classes"]
+            "atm_set_unit_classes", "atm_batch_cells", "atm_cell_grid"]
 
 SUR_NDESC, SUR_NVEC, SUR_NPARAM = 32, 9, 6467
 
@@ -103,6 +103,8 @@ def load():
         "atm_create": [ctypes.POINTER(Params), i64, ctypes.POINTER(P)],
         "atm_batch_create": [ctypes.POINTER(Params), P, i32, ctypes.POINTER(P)],
         "atm_batch_size": [P, P, P],
+        "atm_batch_cells": [P, P],
+        "atm_cell_grid": [ctypes.POINTER(Params), P],
         "atm_destroy": [P],
         "atm_set_state": [P, P, P],
         "atm_set_state_dev": [P, P, P],
@@ -182,17 +184,15 @@ def make_params(box, rc=2.5, nu=0.073, lj_eps=1.0, lj_sigma=1.0, dt=0.002, lj_sh
     return p
 
 
-def cell_count(box, rc):
-    """Cells of one replica: n_d = largest k with L_d / k >= r_c."""
-    total = 1
-    for L in np.broadcast_to(np.asarray(box, dtype=np.float64), (3,)):
-        k = max(1, int(np.floor(L / rc)))
-        while L / (k + 1) >= rc:
-            k += 1
-        while k > 0 and L / k < rc:
-            k -= 1
-        total *= k
-    return total
+def cell_grid(box, rc=2.5):
+    """Linked-cell grid (n_x, n_y, n_z) of one system, as the library forms it
+    (``atm_cell_grid``)."""
+    L = load()
+    nc = np.zeros(3, dtype=np.int32)
+    st = L.atm_cell_grid(ctypes.byref(make_params(box, rc)), _host_ptr(nc))
+    if st != 0:
+        raise AtmError(st, "atm_cell_grid failed")
+    return nc
 
 
 class AtmSystem:
@@ -225,13 +225,15 @@ class AtmSystem:
         self.ns = ns
         self.n = int(sum(ns))
         self.box = np.array(boxes[0])
-        self.ncells = [cell_count(boxes[r], arr[r].rc) for r in range(R)]
         ctx = ctypes.c_void_p()
         nn = np.asarray(ns, dtype=np.int64)
         st = self._lib.atm_batch_create(arr, _host_ptr(nn), R, ctypes.byref(ctx))
         if st != 0:
             raise AtmError(st, "atm_batch_create failed")
         self._ctx = ctx
+        nc = ctypes.c_int64()
+        self._check(self._lib.atm_batch_cells(self._ctx, ctypes.byref(nc)))
+        self.ncell_total = int(nc.value)
 
     # -- helpers
     def _check(self, st):
@@ -296,7 +298,7 @@ class AtmSystem:
         """Cell arrays (for a batch in the global cell numbering; ncell is replica 0's grid)."""
         nc = np.zeros(3, dtype=np.int32)
         cell_of = np.zeros(self.n, dtype=np.int32)
-        start = np.zeros(sum(self.ncells) + 1, dtype=np.int32)
+        start = np.zeros(self.ncell_total + 1, dtype=np.int32)
         perm = np.zeros(self.n, dtype=np.int32)
         self._check(self._lib.atm_get_cells(self._ctx, _host_ptr(cell_of), _host_ptr(start),
                                             _host_ptr(perm), _host_ptr(nc)))

@@ -305,6 +305,23 @@ extern "C" atm_status atm_batch_size(const atm_ctx* c, int* nrep, int64_t* ntot)
     return ATM_OK;
 }
 
+extern "C" atm_status atm_batch_cells(const atm_ctx* c, int64_t* ncell)
+{
+    if (!c || !ncell) return ATM_E_INVALID;
+    *ncell = c->ncell;
+    return ATM_OK;
+}
+
+extern "C" atm_status atm_cell_grid(const atm_params* p, int32_t* ncell3)
+{
+    if (!p || !ncell3) return ATM_E_INVALID;
+    atm3::Rep r;
+    const atm_status st = atm3::make_rep(*p, 0, 0, 0, r);
+    if (st != ATM_OK) return st;
+    for (int d = 0; d < 3; d++) ncell3[d] = r.g.nc[d];
+    return ATM_OK;
+}
+
 extern "C" atm_status atm_destroy(atm_ctx* c)
 {
     if (!c) return ATM_OK;

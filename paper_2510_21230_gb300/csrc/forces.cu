@@ -191,7 +191,7 @@ cudaError_t enqueue_atm(const ForceJob& j, size_t* smem_set, bool* capacity)
         if (e == cudaSuccess) e = cudaStreamWaitEvent(j.side_st, j.ev_fork, 0);
         if (e != cudaSuccess) return e;
     }
-    for (int k = 0; k < j.ncls; k++) {
+    for (int k = 0; k < j.ncls && e == cudaSuccess; k++) {
         ForceJob jk = j;
         if (side && k == 0) jk.st = j.side_st;
         if (k < j.ncls - 1) {
@@ -204,11 +204,14 @@ cudaError_t enqueue_atm(const ForceJob& j, size_t* smem_set, bool* capacity)
         if (jk.mcap < 1) jk.mcap = 1;
         e = launch_atm_one(jk, smem_set, capacity, j.ulist + (size_t)k * j.b.ncell, j.ucount + k,
                            j.work ? j.work + k : nullptr);
-        if (e != cudaSuccess) return e;
     }
     if (side) {
-        e = cudaEventRecord(j.ev_join, j.side_st);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(j.st, j.ev_join, 0);
+        // once forked, the side stream is always joined back (a capture
+        // must not end with it unjoined, and later work on st must follow
+        // what was queued there); the first error is the one returned
+        cudaError_t ej = cudaEventRecord(j.ev_join, j.side_st);
+        if (ej == cudaSuccess) ej = cudaStreamWaitEvent(j.st, j.ev_join, 0);
+        if (e == cudaSuccess) e = ej;
     }
     return e;
 }

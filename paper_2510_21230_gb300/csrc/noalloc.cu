@@ -97,23 +97,55 @@ cudaError_t na_scratch(int device, unsigned char** out)
         if ((call) != cudaSuccess) return ATM_E_CUDA;    \
     } while (0)
 
+namespace {
+// makes params.device current for the call and gives the caller's current
+// device back on every return path
+struct DeviceScope {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceScope(int device)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) return;
+        ok = prev == device || cudaSetDevice(device) == cudaSuccess;
+    }
+    ~DeviceScope()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+}  // namespace
+
+static atm_status noalloc_run(const atm_params* p, int64_t n, const double* x_dev,
+                              atm_traversal trav, atm_truncation trunc, atm_precision prec,
+                              double* f_dev, atm_result* out);
+
 extern "C" atm_status atm_compute_forces_noalloc(const atm_params* p, int64_t n,
                                                  const double* x_dev, atm_traversal trav,
                                                  atm_truncation trunc, atm_precision prec,
                                                  double* f_dev, atm_result* out)
 {
     if (!p || n < 0 || (n > 0 && (!x_dev || !f_dev))) return ATM_E_INVALID;
-    if (trav < 0 || trav > 2 || trunc < 0 || trunc > 1 || prec < 0 || prec > 1)
+    // 3c01, 3c18, 3c08 and the corner-anchored 3c08; the wide traversal needs
+    // its 5^3 unit sizes, which this entry point does not form
+    if (trav < 0 || trav > 4 || trav == ATM_3CW || trunc < 0 || trunc > 1 || prec < 0 || prec > 1)
         return ATM_E_INVALID;
     if (p->device < 0 || p->device >= NA_MAX_DEVICES) return ATM_E_INVALID;
     if (n > NA_N) return ATM_E_CAPACITY;
+    DeviceScope dev(p->device);
+    if (!dev.ok) return ATM_E_CUDA;
+    return noalloc_run(p, n, x_dev, trav, trunc, prec, f_dev, out);
+}
+
+static atm_status noalloc_run(const atm_params* p, int64_t n, const double* x_dev,
+                              atm_traversal trav, atm_truncation trunc, atm_precision prec,
+                              double* f_dev, atm_result* out)
+{
     // the single system as a batch of one replica
     Rep rp;
     atm_status rs = make_rep(*p, n, 0, 0, rp);
     if (rs != ATM_OK) return rs;
     if (rp.g.ncell > NA_C) return ATM_E_CAPACITY;
 
-    NA_CU(cudaSetDevice(p->device));
     unsigned char* base = nullptr;
     NA_CU(na_scratch(p->device, &base));
     cudaStream_t st = (cudaStream_t)p->cuda_stream;

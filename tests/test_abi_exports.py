@@ -29,7 +29,7 @@ def test_library_builds_and_exports_every_declared_symbol():
     for name in sorted(declared):
         assert hasattr(lib, name), name
     assert set(atm3.EXPORTED) <= declared
-    assert atm3.load().atm_abi_version() == 2
+    assert atm3.load().atm_abi_version() == 3
 
 
 def test_invalid_arguments_are_rejected_without_a_gpu():
@@ -47,6 +47,21 @@ def test_invalid_arguments_are_rejected_without_a_gpu():
     assert lib.atm_create(ctypes.byref(p), 10, ctypes.byref(ctx)) == 1
     assert lib.atm_destroy(None) == 0
     assert lib.atm_compute_forces(None, 0, 0, 0, None) == 1
+
+
+@pytest.mark.parametrize("box,rc", [((10.77, 10.77, 10.77), 2.5), ((30.0, 30.0, 120.0), 2.5),
+                                    ((37.5, 37.5, 37.5), 2.5), ((7.5, 7.5, 7.5), 2.5),
+                                    ((9.0, 12.0, 40.0), 3.0)])
+def test_cell_grid_query_matches_the_oracle(box, rc):
+    """atm_cell_grid (host arithmetic) gives the oracle's cell grid: n_d the
+    largest k with L_d / k >= r_c (37.5 / 2.5 is not binary-exact; 7.5 / 2.5
+    lands on exactly 3 cells)."""
+    import oracle
+    nc = atm3.cell_grid(box, rc)
+    assert list(nc) == list(oracle.cell_grid(oracle.params(box, rc, 0.0))[0])
+    with pytest.raises(atm3.AtmError) as ei:
+        atm3.cell_grid((7.4, 10.0, 10.0), 2.5)
+    assert ei.value.status == 2
 
 
 @pytest.mark.parametrize("rc,rho,eps,sig", [(2.5, 0.8, 1.0, 1.0), (3.0, 0.65, 1.0, 1.0),

@@ -270,3 +270,59 @@ def test_unit_size_class_arguments(atm3, ensemble):
                 b.set_unit_classes(bad)
         b.set_unit_classes((40,))
         b.set_unit_classes(())
+
+
+@pytest.fixture(scope="module")
+def ensemble64():
+    """The batched-ensemble workload as benchmarked: 64 replicas, N
+    log-uniform in [500, 20000], rho U(0.1, 0.85), T U(0.7, 1.3)."""
+    return synth.replicas(count=64)
+
+
+def test_batch_of_64_replicas_as_benchmarked(atm3, ensemble64):
+    """The 64-replica batch in the benchmark's launch configuration (graph
+    steps, autotuned launch form with unit size classes on a side stream)
+    equals the same replicas as 64 separate contexts (counts bit-exact,
+    energies and forces within the FP32C tolerance), and three sampled
+    replicas equal the oracle."""
+    reps = ensemble64
+    ns = [r["n"] for r in reps]
+    x, v = _concat(reps, "x"), _concat(reps, "v")
+    with atm3.AtmSystem([r["box"] for r in reps], ns, nu=NU, dt=0.002) as b:
+        b.set_state(x, v)
+        b.build_cells()
+        b.set_options(graph=True)
+        b.autotune("3c08", "pair", "fp32c", reps=2)
+        b.step(3, "3c08", "pair", "fp32c")
+        xs, vs = b.get_state()
+        # forces of the stepped state, with the tuned launch form
+        b.set_state(xs, vs)
+        b.build_cells()
+        b.compute_forces("3c08", "pair", "fp32c")
+        res = b.results()
+        f = b.get_forces("total")
+        fa = b.get_forces("atm")
+    off = 0
+    for r, rep in enumerate(reps):
+        sl = slice(off, off + rep["n"])
+        with atm3.AtmSystem(rep["box"], rep["n"], nu=NU) as s:
+            s.set_state(np.ascontiguousarray(xs[:, sl]))
+            s.build_cells()
+            one = s.compute_forces("3c08", "pair", "fp32c")
+            f1 = s.get_forces("total")
+        for k in ("n_cand3", "n_int3", "n_cand2", "n_int2"):
+            assert res[r][k] == one[k], (r, k)
+        for k in ("e2", "e3", "w2", "w3"):
+            assert res[r][k] == pytest.approx(one[k], rel=RTOL["fp32c"], abs=1e-12), (r, k)
+        assert close(f[:, sl], f1, RTOL["fp32c"]), r
+        off += rep["n"]
+    # oracle parity on three replicas: the smallest, the largest and the densest
+    pick = {int(np.argmin(ns)), int(np.argmax(ns)), int(np.argmax([r["rho"] for r in reps]))}
+    starts = np.concatenate([[0], np.cumsum(ns)])
+    for r in sorted(pick):
+        sl = slice(starts[r], starts[r + 1])
+        ref = oracle.atm_cells(oracle.params(reps[r]["box"], 2.5, NU),
+                               np.ascontiguousarray(xs[:, sl]), "3c08", "pair", "fp32")
+        assert res[r]["n_int3"] == ref["n_int3"] and res[r]["n_cand3"] == ref["n_cand3"], r
+        assert res[r]["e3"] == pytest.approx(ref["e3"], rel=RTOL["fp32c"]), r
+        assert close(fa[:, sl], ref["f"], RTOL["fp32c"]), r

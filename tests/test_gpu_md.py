@@ -54,32 +54,102 @@ def _drift(e):
     return tot[-1] - tot[0], np.abs(tot - tot[0]).max()
 
 
-def test_nve_drift_32k_matches_oracle(atm3):
-    cfg = synth.homogeneous(32000, 0.8, 1.0, seed=2000)
-    nsteps, dt = 200, 0.002
-    n = cfg["n"]
+def _pressure(en, n, vol):
+    """Virial pressure rho T + (W2 + W3) / (3V), T = 2K / (3N - 3), per record."""
+    return n / vol * (2.0 * en[:, 2] / (3 * n - 3)) + en[:, 3] / (3.0 * vol)
+
+
+def _gpu_nve(atm3, cfg, trav, trunc, prec, nsteps, every, dt=0.002):
+    """Energies (E2, E3, K, W2 + W3) of the start and of every `every`-th step,
+    and the final state."""
+    en = []
+    with atm3.AtmSystem(cfg["box"], cfg["n"], nu=NU, dt=dt) as s:
+        s.set_state(cfg["x"], cfg["v"])
+        r = s.step(0, trav, trunc, prec)
+        en.append([r["e2"], r["e3"], r["ekin"], r["w2"] + r["w3"]])
+        for _ in range(nsteps // every):
+            r = s.step(every, trav, trunc, prec)
+            en.append([r["e2"], r["e3"], r["ekin"], r["w2"] + r["w3"]])
+        x, v = s.get_state()
+    return np.array(en), x, v
+
+
+@pytest.fixture(scope="module")
+def liquid_32k():
+    return synth.homogeneous(32000, 0.8, 1.0, seed=2000)
+
+
+@pytest.fixture(scope="module")
+def nve_ref_pair(liquid_32k):
+    """The oracle's 200-step FP64 run under the pair rule (every traversal sums
+    the same triplets under it, so one run serves all of them)."""
+    cfg = liquid_32k
     prm = oracle.params(cfg["box"], 2.5, NU)
-    ref = oracle.md_run(prm, cfg["x"], cfg["v"], nsteps, dt, "3c18", "pair", "fp64")
-    d_ref, m_ref = _drift(ref["energies"])
-    for trav, prec in [("3c08", "fp64"), ("3c08", "fp32c"), ("3c18", "fp32c")]:
-        en = []
-        with atm3.AtmSystem(cfg["box"], n, nu=NU, dt=dt) as s:
-            s.set_state(cfg["x"], cfg["v"])
-            r = s.step(0, trav, "pair", prec)
-            en.append([r["e2"], r["e3"], r["ekin"]])
-            for _ in range(20):
-                r = s.step(nsteps // 20, trav, "pair", prec)
-                en.append([r["e2"], r["e3"], r["ekin"]])
-        en = np.array(en)
-        d, m = _drift(en)
-        # same dynamics: the energy records agree with the oracle's every 10 steps
-        assert np.allclose(en[:, 1], ref["energies"][::10, 1], rtol=1e-3), (trav, prec)
-        assert np.allclose(en[:, 0] + en[:, 2], (ref["energies"][::10, 0] + ref["energies"][::10, 2]),
-                           rtol=1e-4), (trav, prec)
-        # drift per molecule as small as the oracle's (the truncated potentials
-        # make the total energy jump at every cutoff crossing on both sides)
-        assert abs(d - d_ref) / n < 1e-4, (trav, prec, d, d_ref)
-        assert m <= 1.2 * m_ref + 1e-3 * n, (trav, prec, m, m_ref)
+    return oracle.md_run(prm, cfg["x"], cfg["v"], 200, 0.002, "3c18", "pair", "fp64")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+@pytest.mark.parametrize("trav", ["3c01", "3c18", "3c08"])
+def test_nve_drift_32k_matches_oracle(atm3, liquid_32k, nve_ref_pair, trav, prec):
+    """N = 32,000, 200 steps of dt = 0.002 under the pair rule: the energy
+    records follow the oracle's every 10 steps, the drift matches the
+    oracle's, and the ensemble averages of U / N and P agree."""
+    cfg = liquid_32k
+    n = cfg["n"]
+    vol = float(np.prod(cfg["box"]))
+    ref = nve_ref_pair["energies"]
+    d_ref, m_ref = _drift(ref)
+    en, _, _ = _gpu_nve(atm3, cfg, trav, "pair", prec, 200, 10)
+    d, m = _drift(en)
+    # same dynamics: the energy records agree with the oracle's every 10 steps
+    assert np.allclose(en[:, 1], ref[::10, 1], rtol=1e-3), (trav, prec)
+    assert np.allclose(en[:, 0] + en[:, 2], ref[::10, 0] + ref[::10, 2], rtol=1e-4), (trav, prec)
+    # drift per molecule as small as the oracle's (the truncated potentials
+    # make the total energy jump at every cutoff crossing on both sides)
+    assert abs(d - d_ref) / n < 1e-4, (trav, prec, d, d_ref)
+    assert m <= 1.2 * m_ref + 1e-3 * n, (trav, prec, m, m_ref)
+    # ensemble averages over the run
+    u, u_ref = (en[:, 0] + en[:, 1]).mean() / n, (ref[::10, 0] + ref[::10, 1]).mean() / n
+    assert u == pytest.approx(u_ref, rel=1e-4), (trav, prec)
+    p, p_ref = _pressure(en, n, vol).mean(), _pressure(ref[::10], n, vol).mean()
+    assert p == pytest.approx(p_ref, abs=1e-3 * abs(p_ref) + 1e-4), (trav, prec)
+
+
+@pytest.mark.parametrize("trav", ["3c01", "3c18", "3c08"])
+def test_nve_product_rule_32k(atm3, liquid_32k, trav):
+    """N = 32,000, 200 steps of dt = 0.002 under the product rule, FP64 and
+    FP32C (each traversal sums its own triplet set, so each is checked on its
+    own; a 200-step oracle run of the product rule is minutes of CPU per
+    traversal): the first three steps follow the oracle's trajectory, the
+    oracle's evaluation of the FP64 run's final state equals what the run
+    reported there (counts exact), the FP32C run's drift and averages match
+    the FP64 run's, and the drift stays of the pair rule's size."""
+    cfg = liquid_32k
+    n = cfg["n"]
+    vol = float(np.prod(cfg["box"]))
+    prm = oracle.params(cfg["box"], 2.5, NU)
+    short = oracle.md_run(prm, cfg["x"], cfg["v"], 3, 0.002, trav, "product", "fp64")
+    en1, _, _ = _gpu_nve(atm3, cfg, trav, "product", "fp64", 3, 1)
+    assert np.allclose(en1, short["energies"], rtol=1e-8, atol=1e-9), trav
+    en64, x64, _ = _gpu_nve(atm3, cfg, trav, "product", "fp64", 200, 10)
+    ref_end = oracle.atm_cells(prm, x64, trav, "product", "fp64")
+    with atm3.AtmSystem(cfg["box"], n, nu=NU) as s:
+        s.set_state(x64)
+        s.build_cells()
+        r_end = s.compute_forces(trav, "product", "fp64")
+    assert r_end["e3"] == pytest.approx(en64[-1, 1], rel=1e-12), trav
+    assert r_end["n_int3"] == ref_end["n_int3"] and r_end["n_cand3"] == ref_end["n_cand3"], trav
+    assert r_end["e3"] == pytest.approx(ref_end["e3"], rel=1e-10), trav
+    en32, _, _ = _gpu_nve(atm3, cfg, trav, "product", "fp32c", 200, 10)
+    d64, m64 = _drift(en64)
+    d32, m32 = _drift(en32)
+    assert abs(d32 - d64) / n < 1e-4, (trav, d32, d64)
+    assert m32 <= 1.2 * m64 + 1e-3 * n, (trav, m32, m64)
+    assert m64 / n < 2e-3, (trav, m64 / n)
+    u64, u32 = [(e[:, 0] + e[:, 1]).mean() / n for e in (en64, en32)]
+    assert u32 == pytest.approx(u64, rel=1e-4), trav
+    p64, p32 = [_pressure(e, n, vol).mean() for e in (en64, en32)]
+    assert p32 == pytest.approx(p64, abs=1e-3 * abs(p64) + 1e-4), trav
 
 
 @pytest.mark.parametrize("trav,prec", [("3c08", "fp32c"), ("3c08", "fp64"), ("3c08a", "fp32c")])

@@ -198,6 +198,44 @@ def test_atm_parity_32k_pair(atm3, trav, prec):
     assert_forces_close(f, ref["f"], RTOL[prec], trav + prec)
 
 
+@pytest.fixture(scope="module")
+def liquid_32k():
+    return synth.homogeneous(32000, 0.8, 1.0, seed=2000)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+@pytest.mark.parametrize("trav", ["3c18", "3c08", "3c08a"])
+def test_atm_parity_32k_product(atm3, liquid_32k, trav, prec):
+    """Product rule on the N = 32,000 liquid (2197 units of 13 cells per axis):
+    the plans the benchmark times on the 256k liquid (dense distance and
+    pair-scalar tables, the task cursor crossing rows, 16 warps for 3c18 in
+    FP32) over many units, element by element against the oracle."""
+    cfg = liquid_32k
+    prm = oracle.params(cfg["box"], 2.5, NU)
+    ref = oracle.atm_cells(prm, cfg["x"], trav, "product", ORC_PREC[prec])
+    r, f, _, _ = run_gpu(atm3, cfg, trav, "product", prec)
+    assert r["n_cand3"] == ref["n_cand3"]
+    assert r["n_int3"] == ref["n_int3"]
+    assert r["e3"] == pytest.approx(ref["e3"], rel=RTOL[prec])
+    assert r["w3"] == pytest.approx(ref["w3"], rel=RTOL[prec])
+    assert_forces_close(f, ref["f"], RTOL[prec], "32k product " + trav + prec)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+@pytest.mark.parametrize("trunc", ["pair", "product"])
+def test_atm_parity_32k_3c01(atm3, liquid_32k, trunc, prec):
+    """3c01 (owner computes over 27 cells) on the N = 32,000 liquid."""
+    cfg = liquid_32k
+    prm = oracle.params(cfg["box"], 2.5, NU)
+    ref = oracle.atm_cells(prm, cfg["x"], "3c01", trunc, ORC_PREC[prec])
+    r, f, _, _ = run_gpu(atm3, cfg, "3c01", trunc, prec)
+    assert r["n_cand3"] == ref["n_cand3"]
+    assert r["n_int3"] == ref["n_int3"]
+    assert r["e3"] == pytest.approx(ref["e3"], rel=RTOL[prec])
+    assert r["w3"] == pytest.approx(ref["w3"], rel=RTOL[prec])
+    assert_forces_close(f, ref["f"], RTOL[prec], "32k 3c01 " + trunc + prec)
+
+
 # ------------------------------------------------------------------ full size, sampled
 
 def _units_touching(cells_nc, cell_ids, trav):
@@ -215,28 +253,38 @@ def _units_touching(cells_nc, cell_ids, trav):
     return np.array(sorted(out), dtype=np.int64)
 
 
+@pytest.fixture(scope="module")
+def liquid_256k():
+    return synth.homogeneous(256000, 0.8, 1.0, seed=5000)
+
+
+@pytest.mark.parametrize("trunc", ["pair", "product"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32c"])
-@pytest.mark.parametrize("trav", ["3c18", "3c08"])
-def test_full_size_256k_sampled(atm3, trav, prec):
+@pytest.mark.parametrize("trav", ["3c01", "3c18", "3c08"])
+def test_full_size_256k_sampled(atm3, liquid_256k, trav, trunc, prec):
     """N = 256,000 liquid in the benchmark's launch configuration: the forces
     of molecules in sampled cells are recomputed by the oracle from every unit
     that touches those cells; the totals are checked by invariants."""
-    cfg = synth.homogeneous(256000, 0.8, 1.0, seed=5000)
+    cfg = liquid_256k
     prm = oracle.params(cfg["box"], 2.5, NU)
-    r, f, _, cells = run_gpu(atm3, cfg, trav, "pair", prec)
+    r, f, _, cells = run_gpu(atm3, cfg, trav, trunc, prec)
     rng = np.random.default_rng(1)
     ncell = len(cells["cell_start"]) - 1
     sample = rng.choice(ncell, size=6, replace=False)
-    units = _units_touching(cells["ncell"], sample, trav)
-    ref = oracle.atm_cells_units(prm, cfg["x"], units, trav, "pair", ORC_PREC[prec])
+    # 3c01 writes F_i of its own base cell only
+    units = np.sort(sample).astype(np.int64) if trav == "3c01" else \
+        _units_touching(cells["ncell"], sample, trav)
+    ref = oracle.atm_cells_units(prm, cfg["x"], units, trav, trunc, ORC_PREC[prec])
     mol = np.concatenate([cells["perm"][cells["cell_start"][c]:cells["cell_start"][c + 1]]
                           for c in sample])
-    assert_forces_close(f[:, mol], ref["f"][:, mol], RTOL[prec], "sampled " + trav)
-    # invariants at full size: W3 = 9 E3, zero net force, counts positive
+    assert_forces_close(f[:, mol], ref["f"][:, mol], RTOL[prec], "sampled " + trav + trunc)
+    # invariants at full size: W3 = 9 E3, zero net force (Newton-3 traversals),
+    # counts of the order the liquid's density gives
     assert r["w3"] == pytest.approx(9 * r["e3"], rel=1e-9 if prec == "fp64" else 1e-5)
-    net = np.abs(f.sum(axis=1)).max()
-    assert net < (1e-9 if prec == "fp64" else 1e-3) * np.abs(f).max() * 10
-    assert r["n_int3"] > 0.5e7
+    if trav != "3c01":
+        net = np.abs(f.sum(axis=1)).max()
+        assert net < (1e-9 if prec == "fp64" else 1e-3) * np.abs(f).max() * 10
+    assert r["n_int3"] > (0.5e7 if trunc == "pair" else 2.5e8)
 
 
 # ------------------------------------------------------------------ capacity fallbacks

@@ -395,6 +395,126 @@ def test_fp32_decisions_close_to_fp64():
         assert abs(a["n_int3"] - b["n_int3"]) <= max(2, 1e-4 * a["n_int3"])
 
 
+# An independent float32 statement of the FP32 decision sequence: positions
+# wrapped into [0, L), cell c = min(n - 1, floor(x / w)), cell-local
+# coordinate x - c w in FP64 rounded once to float32; per pair
+# d = (l_q - l_p) + float32(dc) * float32(w) in float32 with dc the wrapped
+# cell offset, |d|^2 = (dx dx + dy dy) + dz dz in float32; r_c^2 and r_c^6
+# as float32 products of float32(r_c); pair rule: every side below r_c^2;
+# product rule: (lo * mid) * hi of the sorted sides below r_c^6.  numpy's
+# float32 operations round each result once and never contract.
+
+def _grid(L, rc):
+    n = []
+    for Ld in L:
+        k = 1
+        while Ld / (k + 1) >= rc:
+            k += 1
+        n.append(k)
+    return np.array(n)
+
+
+def _f32_decisions(x, box, rc, trunc, tri, variant=None):
+    """Decisions of the triangles tri[:, 0..2] (molecule indices)."""
+    L = np.asarray(box, dtype=np.float64)
+    n = _grid(L, rc)
+    w = L / n
+    c = np.minimum(n[:, None] - 1, np.floor(x / w[:, None])).astype(np.int64)
+    loc = np.clip(x - c * w[:, None], 0.0, w[:, None])
+    l32 = loc.astype(np.float32)
+    if variant == "local_from_rounded":  # planted: float32(x) - c float32(w)
+        l32 = x.astype(np.float32) - c.astype(np.float32) * w.astype(np.float32)[:, None]
+    wf = w.astype(np.float32)
+
+    def d2(p, q):
+        dc = (c[:, q] - c[:, p] + 1) % n[:, None] - 1  # wrapped offset of adjacent cells
+        d = (l32[:, q] - l32[:, p]) + dc.astype(np.float32) * wf[:, None]
+        if variant == "fp64":  # planted: the decision taken in FP64
+            d = (loc[:, q] - loc[:, p]) + dc * w[:, None]
+        if variant == "sum_order":  # planted: dx dx + (dy dy + dz dz)
+            return d[0] * d[0] + (d[1] * d[1] + d[2] * d[2])
+        return (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]
+
+    rcf = np.float32(rc)
+    rc2f = rcf * rcf
+    if variant == "rc2_from_fp64":  # planted: r_c^2 rounded from FP64
+        rc2f = np.float32(rc * rc)
+    rc6f = (rc2f * rc2f) * rc2f
+    a, b, cc = d2(tri[:, 0], tri[:, 1]), d2(tri[:, 0], tri[:, 2]), d2(tri[:, 1], tri[:, 2])
+    if variant == "fp64":
+        rc2f = rc * rc
+        rc6f = (rc2f * rc2f) * rc2f
+    if trunc == "pair":
+        return (a < rc2f) & (b < rc2f) & (cc < rc2f)
+    srt = np.sort(np.stack([a, b, cc]), axis=0)
+    if variant == "product_order":  # planted: (hi * mid) * lo
+        return (srt[2] * srt[1]) * srt[0] < rc6f
+    return (srt[0] * srt[1]) * srt[2] < rc6f
+
+
+def _near_cutoff_triangles(rc, trunc, seed, k=5, L_over_rc=14.5):
+    """k^3 isolated triangles (no molecule of another triangle within 1.4 r_c)
+    whose pair-rule sides, or whose product of sides, lie within a few float32
+    ulps of the cutoff; rotated at random, shifted by a random vector and
+    wrapped (some straddle cell faces and the periodic boundary)."""
+    rng = np.random.default_rng(seed)
+    L = L_over_rc * rc
+    sp = L / k
+    pts = []
+    for ix, iy, iz in itertools.product(range(k), repeat=3):
+        if trunc == "pair":
+            a, b, c = rc * (1.0 + rng.uniform(-1.5e-7, 1.5e-7, 3))
+        else:
+            f1, f2 = rng.uniform(0.99, 1.01, 2)
+            a, b, c = rc * f1, rc * f2, rc / (f1 * f2) * (1.0 + rng.uniform(-1.5e-7, 1.5e-7))
+        xx = (a * a + b * b - c * c) / (2 * a)
+        t = np.array([[0.0, 0.0, 0.0], [a, 0.0, 0.0], [xx, math.sqrt(b * b - xx * xx), 0.0]])
+        q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+        t = (t - t.mean(axis=0)) @ q.T
+        pts.append(t + (np.array([ix, iy, iz]) + 0.5) * sp + rng.uniform(-0.3, 0.3, 3))
+    x = np.concatenate(pts).T + rng.uniform(0.0, L, size=(3, 1))
+    x = x - np.floor(x / L) * L
+    x[x >= L] = 0.0
+    assert np.all((x >= 0.0) & (x < L))
+    tri = np.arange(3 * k ** 3).reshape(-1, 3)
+    return np.ascontiguousarray(x), np.array([L, L, L]), tri
+
+
+@pytest.mark.parametrize("rc", [2.5, 2.314])
+@pytest.mark.parametrize("trunc", ["pair", "product"])
+def test_fp32_decision_mode_equals_an_independent_float32_statement(rc, trunc):
+    """The oracle's FP32-decision mode (the triplet set the FP32C kernels are
+    compared with bit for bit) decides every near-cutoff triangle as the
+    float32 statement above does, for every traversal; and the fixture is
+    sharp enough that the FP64 decision and each planted variant of the
+    statement (another summation or product order, local coordinates from
+    rounded positions, r_c^2 rounded from FP64) decide some triangle
+    differently."""
+    for seed in range(5):
+        x, box, tri = _near_cutoff_triangles(rc, trunc, 7100 + seed)
+        keep = _f32_decisions(x, box, rc, trunc, tri)
+        assert 0 < keep.sum() < len(keep)
+        prm = oracle.params(box, rc, NU)
+        for trav, visits in (("3c01", 3), ("3c18", 1), ("3c08", 1)):
+            r = oracle.atm_cells(prm, x, trav, trunc, "fp32")
+            assert r["n_int3"] == visits * int(keep.sum()), (trav, seed)
+            hit = np.any(r["f"][:, tri[:, 0]] != 0.0, axis=0)
+            assert np.array_equal(hit, keep), (trav, seed)
+    # sensitivity over the five fixtures together
+    for variant in ("fp64", "sum_order", "local_from_rounded", "product_order",
+                    "rc2_from_fp64"):
+        if variant == "product_order" and trunc == "pair":
+            continue
+        if variant == "rc2_from_fp64" and np.float32(rc * rc) == np.float32(rc) * np.float32(rc):
+            continue
+        differs = False
+        for seed in range(5):
+            x, box, tri = _near_cutoff_triangles(rc, trunc, 7100 + seed)
+            differs |= not np.array_equal(_f32_decisions(x, box, rc, trunc, tri),
+                                          _f32_decisions(x, box, rc, trunc, tri, variant))
+        assert differs, variant
+
+
 def test_lj_cells_equal_brute_force():
     x, box = _small_fluid(n=200, rho=0.5, seed=24)
     prm = _prm(box)

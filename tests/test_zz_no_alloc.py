@@ -3,12 +3,14 @@
 Some callers cannot allocate device memory (an embedding application that owns
 the whole device budget, a plug-in given only raw device pointers); for them
 the library keeps its intermediate arrays in one fixed device array instead.
-This test calls that entry point through the C ABI twice in a row, on two
-different inputs, and checks each result against the context-based entry
-points (atm_compute_forces + atm_get_forces) with the tolerances of the other
-GPU parity tests: counts bit-exact, FP64 forces within 1e-10, FP32C within
-2e-5 relative per component (absolute floor of the same size times the RMS
-force).  The file is named to be collected last.
+This test calls that entry point through the C ABI several times in a row, on
+different inputs -- the last one smaller in molecules and cells than the one
+before it, so that anything a call fails to clear would show up as stale data
+-- and checks each result against the context-based entry points
+(atm_compute_forces + atm_get_forces) with the tolerances of the other GPU
+parity tests: counts bit-exact, FP64 forces within 1e-10, FP32C within 2e-5
+relative per component (absolute floor of the same size times the RMS force).
+The file is named to be collected last.
 """
 import numpy as np
 import pytest
@@ -27,14 +29,16 @@ def _close(got, ref, rtol):
 
 
 @pytest.mark.parametrize("trav,trunc,prec", [("3c08", "pair", "fp32c"), ("3c08", "product", "fp64"),
-                                             ("3c18", "pair", "fp64"), ("3c01", "pair", "fp64")])
+                                             ("3c18", "pair", "fp64"), ("3c01", "pair", "fp64"),
+                                             ("3c08a", "pair", "fp32c")])
 def test_noalloc_matches_context_entry_points_twice(trav, trunc, prec):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2510_21230_gb300 import atm3, build
     build.build()
-    for call, (n, seed) in enumerate([(1000, 1000), (1500, 1001)]):
+    # 4^3 cells, 4^3 cells with more molecules, then 3^3 cells with fewer
+    for call, (n, seed) in enumerate([(1000, 1000), (1500, 1001), (500, 1002)]):
         cfg = synth.homogeneous(n, 0.8, 1.0, seed=seed)
         with atm3.AtmSystem(cfg["box"], n) as s:
             s.set_state(cfg["x"])
@@ -67,3 +71,25 @@ def test_noalloc_rejects_sizes_beyond_its_array():
     with pytest.raises(atm3.AtmError) as ei:
         atm3.compute_forces_noalloc([60.0, 60.0, 60.0], x, f)
     assert ei.value.status == 7
+
+
+def test_noalloc_empty_system_and_unsupported_modes():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_21230_gb300 import atm3, build
+    build.build()
+    x = torch.zeros((3, 0), dtype=torch.float64, device="cuda")
+    f = torch.zeros((3, 0), dtype=torch.float64, device="cuda")
+    got = atm3.compute_forces_noalloc([9.0, 9.0, 9.0], x, f, "3c08", "pair", "fp64")
+    assert got["n_cand3"] == 0 and got["n_int3"] == 0 and got["n_int2"] == 0
+    assert got["e2"] == 0.0 and got["e3"] == 0.0
+    cfg = synth.homogeneous(1000, 0.8, 1.0, seed=1000)
+    x = torch.tensor(cfg["x"], dtype=torch.float64, device="cuda")
+    f = torch.zeros((3, 1000), dtype=torch.float64, device="cuda")
+    for trav, prec in (("3cw", "fp64"), ("3c08", "surrogate")):
+        with pytest.raises(atm3.AtmError) as ei:
+            atm3.compute_forces_noalloc(cfg["box"], x, f, trav, "pair", prec)
+        assert ei.value.status == 1
+    # the caller's current device is unchanged
+    assert torch.cuda.current_device() == 0
