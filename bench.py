@@ -118,6 +118,7 @@ def parse():
                         "workload (N = 104052 has the cell edge of the 256,000 liquid)")
     p.add_argument("--reps", type=int, default=3, help="--kernel-case: evaluations per timing")
     p.add_argument("--nwarps", type=int, default=0, help="--kernel-case: warps per CTA")
+    p.add_argument("--det", action="store_true", help="--kernel-case: deterministic mode")
     return p.parse_args()
 
 
@@ -921,6 +922,8 @@ def kernel_case(args):
                                   np.where(sd > 1e-12, sd, 1.0).astype(np.float32))
         if args.nwarps:
             s.set_options(nwarps=args.nwarps)
+        if args.det:
+            s.set_deterministic(True)
         s.compute_forces(args.trav, args.trunc, args.prec)
         torch.cuda.synchronize()
         s.set_profiling(True)
@@ -938,7 +941,8 @@ def kernel_case(args):
         prof = s.get_profile()
     atm = prof["ms_atm"] / max(1, prof["n_atm_launches"])
     print(json.dumps({"kernel_case": name, "traversal": args.trav, "truncation": args.trunc,
-                      "precision": args.prec, "ms_per_evaluation": sorted(times)[1],
+                      "precision": args.prec, "deterministic": bool(args.det),
+                      "ms_per_evaluation": sorted(times)[1],
                       "atm_ms_per_launch": atm, "n_int3": int(r["n_int3"]),
                       "note": "median of 3 x %d evaluations, cell build excluded" % args.reps}))
 

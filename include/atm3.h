@@ -42,7 +42,8 @@ typedef enum {
     ATM_E_TIMEOUT = 4,       /* a bounded device-side wait gave up */
     ATM_E_NONFINITE = 5,     /* a position or velocity is NaN or infinite */
     ATM_E_STATE = 6,         /* call out of order (e.g. forces before a state was set) */
-    ATM_E_CAPACITY = 7       /* a cell holds more molecules than the kernels stage (see atm_create) */
+    ATM_E_CAPACITY = 7,      /* a cell holds more molecules than the kernels stage (see atm_create) */
+    ATM_E_RANGE = 8          /* deterministic mode: a force term beyond its fixed-point range */
 } atm_status;
 
 /* Cell-triplet traversals (paper section 4, and one wide traversal).
@@ -83,8 +84,14 @@ typedef enum { ATM_TRUNC_PAIR = 0, ATM_TRUNC_PRODUCT = 1 } atm_truncation;
 /* Arithmetic of the force evaluation.
  *  FP64:  every decision and every force, energy and virial term in FP64.
  *  FP32C: decisions and per-triplet arithmetic in FP32 on FP32 cell-local
- *         coordinates; per-molecule force sums compensated (two-sum) in FP32 and
- *         combined in FP64; energy/virial reduced in FP64.
+ *         coordinates.  Force sums: 3C18 / 3C08 / 3C08A add each triplet's
+ *         three pair scalars to per-edge FP32 sums, then each molecule's share
+ *         of a unit is a plain FP32 sum over its edges, and the shares of
+ *         different units are added in FP64; 3C01 / 3CW keep compensated
+ *         (Kahan) FP32 per-lane sums of F_i, combined in FP64.  Energy and
+ *         virial: Kahan-compensated FP32 per lane, reduced in FP64.  (The
+ *         deterministic mode sums the block traversals' terms in fixed
+ *         point instead, see atm_set_deterministic.)
  *  SURROGATE: the ATM force comes from the learned per-molecule model below
  *         (atm_surrogate_*), not from triplets; LJ runs in FP32.  The model
  *         gives forces only: E3, W3 and the triplet counts are reported as 0.
@@ -217,6 +224,32 @@ atm_status atm_get_results(atm_ctx* ctx, atm_result* out);
  * which the run is restarted from its initial state without the graph.
  * Options reset any autotuned choice.  Errors: INVALID. */
 atm_status atm_set_options(atm_ctx* ctx, int persistent, int nwarps, int graph);
+
+/* Deterministic mode (on = 1; 0 = off, the default).  Repeated evaluations
+ * and steps of the same state with the same launch options give bit-identical
+ * forces, energies, virials and counts (without it, forces, energies and
+ * virials vary at the rounding level from run to run: warps take work from
+ * counters in the order they arrive and floating-point atomic additions
+ * round in the order they happen).  In this mode
+ *  - every warp takes its work in a fixed order (cell-triplet edge groups and
+ *    candidate tasks of the block traversals, base molecules of 3C01 / 3CW),
+ *    so each lane's energy and virial sums are the same every time;
+ *  - the block traversals (3C18, 3C08, 3C08A) sum their pair scalars, their
+ *    per-molecule fallback accumulators and the forces of different units as
+ *    signed 64-bit integers in units of 2^-32 (FP32C) or 2^-44 (FP64): each
+ *    term is rounded once to that grid and the sums do not depend on the
+ *    order of the additions, so the forces are also the same for every launch
+ *    form (one CTA per unit or persistent, warps per CTA, size classes);
+ *    energies and virials then depend on the launch form only through the
+ *    lanes' partial sums;
+ *  - a term of size 2^26 (FP32C) or 2^14 = 16,384 (FP64) or more, which a
+ *    liquid never reaches, makes the evaluation fail with ATM_E_RANGE.
+ * 3C01 and 3CW write each force once (owner computes) and the LJ kernel owns
+ * its molecules' sums, so they need no fixed point.  The surrogate is
+ * unaffected (its kernels already sum in a fixed order).  Resets any tuned
+ * choice and the current forces (the next step evaluates them).
+ * Errors: INVALID. */
+atm_status atm_set_deterministic(atm_ctx* ctx, int on);
 
 /* Unit size classes of the block traversals (3C18, 3C08, 3C08A) for
  * evaluations and steps without an autotuned choice.  nclass = 1: every unit

@@ -21,7 +21,7 @@ FORCES = {"total": 0, "lj": 1, "atm": 2}
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "box smaller than three cells", 3: "CUDA error",
           4: "device wait timed out", 5: "non-finite input", 6: "call out of order",
-          7: "capacity exceeded"}
+          7: "capacity exceeded", 8: "fixed-point range exceeded"}
 
 ABI_VERSION = 3  # ATM3_ABI_VERSION of include/atm3.h
 EXPORTED = ["atm_abi_version", "atm_create", "atm_batch_create", "atm_batch_size", "atm_destroy",
@@ -37,7 +37,7 @@ EXPORTED = ["atm_abi_version", "atm_create", "atm_batch_create", "atm_batch_size
             "atm_surrogate_train", "atm_surrogate_options", "atm_surrogate_error",
             "atm_measure_fma_peak", "atm_rdf_accumulate", "atm_rdf_get", "atm_rdf_reset",
             "atm_lj_tail", "atm_thermostat", "atm_measure_rsqrt_peak", "atm_set_forces",
-            "atm_set_unit_classes", "atm_batch_cells", "atm_cell_grid"]
+            "atm_set_unit_classes", "atm_batch_cells", "atm_cell_grid", "atm_set_deterministic"]
 
 SUR_NDESC, SUR_NVEC, SUR_NPARAM = 32, 9, 6467
 
@@ -118,6 +118,7 @@ def load():
         "atm_step": [P, i32, i32, i32, i32, ctypes.POINTER(Result)],
         "atm_set_options": [P, i32, i32, i32],
         "atm_set_unit_classes": [P, i32, P],
+        "atm_set_deterministic": [P, i32],
         "atm_autotune": [P, i32, i32, i32, i32, ctypes.POINTER(Tuning)],
         "atm_density_accumulate": [P, i32, i32],
         "atm_density_get": [P, P, P],
@@ -338,6 +339,11 @@ class AtmSystem:
     def set_options(self, persistent=False, nwarps=0, graph=False):
         self._check(self._lib.atm_set_options(self._ctx, int(bool(persistent)), int(nwarps),
                                               int(bool(graph))))
+
+    def set_deterministic(self, on=True):
+        """Deterministic mode (``atm_set_deterministic``): repeated runs give
+        bit-identical forces, energies, virials and counts."""
+        self._check(self._lib.atm_set_deterministic(self._ctx, 1 if on else 0))
 
     def set_unit_classes(self, cuts=()):
         """Unit size classes of the block traversals: cuts = () for one

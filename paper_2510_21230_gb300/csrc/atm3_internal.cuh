@@ -13,7 +13,21 @@ enum : int {
     ST_CAPACITY = 1,   // a unit stages more molecules than its shared memory holds
     ST_NONFINITE = 2,  // a non-finite position or velocity was seen
     ST_TIMEOUT = 4,    // a bounded device-side wait gave up
+    ST_RANGE = 8,      // deterministic mode: a term beyond the fixed-point range
 };
+
+// Deterministic mode: force terms are summed as signed 64-bit integers in
+// units of 2^-FIX_BITS (integer addition does not depend on the order of
+// the additions).  FP32C keeps 2^-32 (terms up to 2^30 in size), FP64 2^-44
+// (terms up to 2^18 = 262,144, below the resolution of a 1e-10 relative
+// force error for forces of order one).
+template <typename R>
+struct FixBits {
+    static constexpr int B = sizeof(R) == 8 ? 44 : 32;
+};
+// a term may not exceed 2^(FIX_LIMIT - B) in size, so that sums of up to
+// 2^(63 - FIX_LIMIT) = 32 such terms still fit
+constexpr int FIX_LIMIT = 58;
 
 // Linked-cell grid (section 3): n_d cells of edge w_d = L_d / n_d per axis.
 struct Grid {
@@ -160,6 +174,10 @@ struct AtmArgs {
     // take the units ulist[0 .. *ucount) instead of 0 .. ncell (nullptr: all)
     const int* ulist;
     const int* ucount;
+    // deterministic mode: warps take their work in a fixed order (owner
+    // kernels; the block kernels' deterministic instantiations also sum in
+    // fixed point and fs holds 64-bit fixed-point sums, see FixBits)
+    int det;
 };
 
 // Shared-memory plan of the owner kernels (3c01, 3cw): staged positions,
@@ -204,7 +222,7 @@ struct BlockSmem {
 
 template <typename R>
 __host__ __device__ inline BlockSmem block_smem_plan(int trunc, int mcap, int nwarps, int gcap,
-                                                     int use_d, int acc_mode)
+                                                     int use_d, int acc_mode, int det = 0)
 {
     BlockSmem p;
     size_t o = 0;
@@ -230,7 +248,9 @@ __host__ __device__ inline BlockSmem block_smem_plan(int trunc, int mcap, int nw
     p.off_ed = o;
     o = al(o + (pair && f64 ? sizeof(R) * 4 * (size_t)gcap : 0));
     p.off_el = o;     o = al(o + (pair ? sizeof(unsigned) * (size_t)gcap : 0));
-    const size_t gb = sizeof(R) * (pair ? (size_t)gcap : (acc_mode == 0 ? npair : 0));
+    // pair scalars: R, or 64-bit fixed point in the deterministic mode
+    const size_t gsz = det ? 8 : sizeof(R);
+    const size_t gb = gsz * (pair ? (size_t)gcap : (acc_mode == 0 ? npair : 0));
     p.off_G = o;      o = al(o + (pair ? (gb > accb ? gb : accb) : gb));
     p.off_D = o;      o = al(o + (!pair && use_d ? sizeof(float) * npair : 0));
     p.off_acc = pair ? p.off_G : o;  // pair rule: the fallback accumulators alias G
@@ -258,7 +278,7 @@ struct AtmPlan {
 constexpr int ATM_WIDE_PCAP = 1024;
 
 inline bool atm_choose_plan_nw(int trav, int trunc, int prec, int mcap, int optin, int nwarps,
-                               AtmPlan& P)
+                               AtmPlan& P, int det = 0)
 {
     // the kernels' static shared memory (slot tables, reductions; under 2 KB)
     // counts against the same per-block limit as the dynamic part
@@ -273,8 +293,8 @@ inline bool atm_choose_plan_nw(int trav, int trunc, int prec, int mcap, int opti
             return prec == 0 ? owner_smem_plan<double>(mcap, P.nwarps, P.pcap).total
                              : owner_smem_plan<float>(mcap, P.nwarps, P.pcap).total;
         return prec == 0
-                   ? block_smem_plan<double>(trunc, mcap, P.nwarps, P.gcap, P.use_d, P.acc_mode).total
-                   : block_smem_plan<float>(trunc, mcap, P.nwarps, P.gcap, P.use_d, P.acc_mode).total;
+                   ? block_smem_plan<double>(trunc, mcap, P.nwarps, P.gcap, P.use_d, P.acc_mode, det).total
+                   : block_smem_plan<float>(trunc, mcap, P.nwarps, P.gcap, P.use_d, P.acc_mode, det).total;
     };
     if (trav == 0 || trav == 3) {
         P.smem = bytes();
@@ -310,16 +330,17 @@ inline bool atm_choose_plan_nw(int trav, int trunc, int prec, int mcap, int opti
     return false;
 }
 
-inline bool atm_choose_plan(int trav, int trunc, int prec, int mcap, int optin, AtmPlan& P)
+inline bool atm_choose_plan(int trav, int trunc, int prec, int mcap, int optin, AtmPlan& P,
+                            int det = 0)
 {
     if (!atm_choose_plan_nw(trav, trunc, prec, mcap, optin,
-                            (trav == 0 || trav == 3 || (trunc == 0 && prec == 1)) ? 4 : 8, P))
+                            (trav == 0 || trav == 3 || (trunc == 0 && prec == 1)) ? 4 : 8, P, det))
         return false;
     // FP32 3c18 product rule whose tables leave room for one CTA per SM: 16
     // warps (same table mode) hide more of the scan's shared-memory latency
     if (trunc == 1 && prec == 1 && trav == 1 && 2 * P.smem > (size_t)optin) {
         AtmPlan Q;
-        if (atm_choose_plan_nw(trav, trunc, prec, mcap, optin, 16, Q) && Q.use_d == P.use_d &&
+        if (atm_choose_plan_nw(trav, trunc, prec, mcap, optin, 16, Q, det) && Q.use_d == P.use_d &&
             Q.acc_mode == P.acc_mode)
             P = Q;
     }
@@ -330,12 +351,23 @@ inline bool atm_choose_plan(int trav, int trunc, int prec, int mcap, int optin, 
 
 // kernel launchers (defined in atm_fp64.cu / atm_fp32.cu)
 namespace atm3 {
+// det != 0 selects the block kernels' deterministic instantiations (the
+// owner kernels read a.det themselves)
 cudaError_t launch_atm_fp64(int trav, int trunc, const AtmArgs<double>& a, int nwarps,
                             size_t smem, int ctas, cudaStream_t s);
 cudaError_t launch_atm_fp32(int trav, int trunc, const AtmArgs<float>& a, int nwarps,
                             size_t smem, int ctas, cudaStream_t s);
-cudaError_t atm_attr_fp64(int trav, int trunc, size_t smem);
-cudaError_t atm_attr_fp32(int trav, int trunc, size_t smem);
-int atm_occupancy_fp64(int trav, int trunc, int nwarps, size_t smem);
-int atm_occupancy_fp32(int trav, int trunc, int nwarps, size_t smem);
+cudaError_t atm_attr_fp64(int trav, int trunc, size_t smem, int det = 0);
+cudaError_t atm_attr_fp32(int trav, int trunc, size_t smem, int det = 0);
+int atm_occupancy_fp64(int trav, int trunc, int nwarps, size_t smem, int det = 0);
+int atm_occupancy_fp32(int trav, int trunc, int nwarps, size_t smem, int det = 0);
+// deterministic instantiations of the block kernels (atm_det64.cu / atm_det32.cu)
+cudaError_t launch_block_det64(int trav, int trunc, const AtmArgs<double>& a, int nwarps,
+                               size_t smem, int ctas, cudaStream_t s);
+cudaError_t launch_block_det32(int trav, int trunc, const AtmArgs<float>& a, int nwarps,
+                               size_t smem, int ctas, cudaStream_t s);
+cudaError_t attr_block_det64(int trav, int trunc, size_t smem);
+cudaError_t attr_block_det32(int trav, int trunc, size_t smem);
+int occupancy_block_det64(int trav, int trunc, int nwarps, size_t smem);
+int occupancy_block_det32(int trav, int trunc, int nwarps, size_t smem);
 }  // namespace atm3

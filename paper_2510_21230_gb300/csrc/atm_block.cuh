@@ -36,6 +36,8 @@
 // table does not fit, the unit falls back to per-molecule shared-memory force
 // accumulators (compensated atomics in FP32).
 #pragma once
+#include <type_traits>
+
 #include "atm_common.cuh"
 
 namespace atm3 {
@@ -114,7 +116,7 @@ __device__ __forceinline__ R seg_sum(R v, int key, int lane)
     return v;
 }
 
-template <int TRAV, int TRUNC, typename R>
+template <int TRAV, int TRUNC, typename R, bool DET>
 __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long long u)
 {
     constexpr int S = Trav<TRAV>::S;
@@ -133,7 +135,8 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nwarps = blockDim.x >> 5;
     const int mcap = A.mcap;
-    const BlockSmem plan = block_smem_plan<R>(TRUNC, mcap, nwarps, A.gcap, A.use_d, A.acc_mode);
+    const BlockSmem plan =
+        block_smem_plan<R>(TRUNC, mcap, nwarps, A.gcap, A.use_d, A.acc_mode, DET ? 1 : 0);
     // the replica this unit belongs to and the unit's index inside it
     const Rep& rp = A.b.rep[A.b.rep_of_cell[u]];
     const long long lu = u - rp.cell0;
@@ -162,7 +165,9 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
     unsigned* memb = reinterpret_cast<unsigned*>(smem + plan.off_memb);
     R* ED = reinterpret_cast<R*>(smem + plan.off_ed);                // FP64: edge vectors
     unsigned* el = reinterpret_cast<unsigned*>(smem + plan.off_el);  // edge list p | q << 16
-    R* G = reinterpret_cast<R*>(smem + plan.off_G);
+    // pair scalars: R, or (deterministic mode) 64-bit fixed point
+    using GT = std::conditional_t<DET, long long, R>;
+    GT* G = reinterpret_cast<GT*>(smem + plan.off_G);
     float* D = reinterpret_cast<float*>(smem + plan.off_D);
     unsigned char* acc = smem + plan.off_acc;
     unsigned long long* queue =
@@ -220,6 +225,46 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
         return -fw;
     };
 
+    // pair-scalar and per-molecule accumulation: floating-point atomics, or
+    // (deterministic mode) integer atomics on fixed-point terms, whose sums
+    // do not depend on the order of the additions
+    auto gadd = [&](int idx, R v) {
+        if constexpr (DET)
+            atomicAdd(reinterpret_cast<unsigned long long*>(G + idx), to_fix<R>((double)v, A.status));
+        else
+            atomicAdd(G + idx, v);
+    };
+    auto gset = [&](int idx, R v) {
+        if constexpr (DET)
+            G[idx] = (GT)to_fix<R>((double)v, A.status);
+        else
+            G[idx] = v;
+    };
+    auto gget = [&](int idx) -> R {
+        if constexpr (DET)
+            return from_fix<R>(G[idx]);
+        else
+            return G[idx];
+    };
+    auto acc_add = [&](int idx, R v) {
+        if constexpr (DET)
+            atomicAdd(reinterpret_cast<unsigned long long*>(acc) + idx, to_fix<R>((double)v, A.status));
+        else
+            Acc<R>::add(acc, mcap, idx, v);
+    };
+    auto acc_get = [&](int idx) -> double {
+        if constexpr (DET)
+            return (double)from_fix<R>(reinterpret_cast<const long long*>(acc)[idx]);
+        else
+            return Acc<R>::get(acc, mcap, idx);
+    };
+    auto acc_zero = [&](int idx) {
+        if constexpr (DET)
+            reinterpret_cast<long long*>(acc)[idx] = 0ll;
+        else
+            Acc<R>::zero(acc, mcap, idx);
+    };
+
     // ---- stage the unit: positions and exact shifts o * w
     for (int t = tid; t < M; t += blockDim.x) {
         int s = 0;
@@ -248,12 +293,12 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
     }
     const bool dense_g = !PAIR && A.acc_mode == 0;
     if (dense_g)
-        for (int t = tid; t < M * (M - 1) / 2; t += blockDim.x) G[t] = R(0);
+        for (int t = tid; t < M * (M - 1) / 2; t += blockDim.x) G[t] = GT(0);
     if (!PAIR && A.acc_mode == 1)
         for (int t = tid; t < M; t += blockDim.x) {
-            Acc<R>::zero(acc, mcap, t);
-            Acc<R>::zero(acc, mcap, mcap + t);
-            Acc<R>::zero(acc, mcap, 2 * mcap + t);
+            acc_zero(t);
+            acc_zero(mcap + t);
+            acc_zero(2 * mcap + t);
         }
     if (PAIR)
         for (int t = tid; t < M * W; t += blockDim.x) {
@@ -437,7 +482,7 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
                         const int q = (w << 5) + __ffs(word) - 1;
                         word &= word - 1u;
                         el[e] = (unsigned)p | ((unsigned)q << 16);
-                        G[e] = R(0);
+                        G[e] = GT(0);
                         e++;
                     }
                 }
@@ -456,9 +501,9 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
             }
         } else {
             for (int t = tid; t < M; t += blockDim.x) {
-                Acc<R>::zero(acc, mcap, t);
-                Acc<R>::zero(acc, mcap, mcap + t);
-                Acc<R>::zero(acc, mcap, 2 * mcap + t);
+                acc_zero(t);
+                acc_zero(mcap + t);
+                acc_zero(2 * mcap + t);
             }
             if (LJ) {
                 __syncthreads();
@@ -469,12 +514,12 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
                         if (((adj[p * W + w] >> lane) & 1u) && (sslot[p] & sslot[q]) == 0) {
                             R dx, dy, dz;
                             const R g = lj_pair(disp(p, q, dx, dy, dz));
-                            Acc<R>::add(acc, mcap, p, g * dx);
-                            Acc<R>::add(acc, mcap, mcap + p, g * dy);
-                            Acc<R>::add(acc, mcap, 2 * mcap + p, g * dz);
-                            Acc<R>::add(acc, mcap, q, -(g * dx));
-                            Acc<R>::add(acc, mcap, mcap + q, -(g * dy));
-                            Acc<R>::add(acc, mcap, 2 * mcap + q, -(g * dz));
+                            acc_add(p, g * dx);
+                            acc_add(mcap + p, g * dy);
+                            acc_add(2 * mcap + p, g * dz);
+                            acc_add(q, -(g * dx));
+                            acc_add(mcap + q, -(g * dy));
+                            acc_add(2 * mcap + q, -(g * dz));
                         }
                     }
             }
@@ -494,7 +539,7 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
                     R dx, dy, dz;
                     a = disp(p, q, dx, dy, dz);
                 }
-                G[e] = lj_pair(a);
+                gset(e, lj_pair(a));
             }
         }
     }
@@ -541,19 +586,19 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
         esum.add(uu);
         wsum.add(-(gpq * a + gpr * b + gqr * c));
         if (!use_acc) {
-            atomicAdd(G + epr, gpr);
-            atomicAdd(G + eqr, gqr);
+            gadd(epr, gpr);
+            gadd(eqr, gqr);
             return gpq;
         } else {
-            Acc<R>::add(acc, mcap, p, gpq * dpqx + gpr * dprx);
-            Acc<R>::add(acc, mcap, mcap + p, gpq * dpqy + gpr * dpry);
-            Acc<R>::add(acc, mcap, 2 * mcap + p, gpq * dpqz + gpr * dprz);
-            Acc<R>::add(acc, mcap, q, gqr * dqrx - gpq * dpqx);
-            Acc<R>::add(acc, mcap, mcap + q, gqr * dqry - gpq * dpqy);
-            Acc<R>::add(acc, mcap, 2 * mcap + q, gqr * dqrz - gpq * dpqz);
-            Acc<R>::add(acc, mcap, r, -(gpr * dprx + gqr * dqrx));
-            Acc<R>::add(acc, mcap, mcap + r, -(gpr * dpry + gqr * dqry));
-            Acc<R>::add(acc, mcap, 2 * mcap + r, -(gpr * dprz + gqr * dqrz));
+            acc_add(p, gpq * dpqx + gpr * dprx);
+            acc_add(mcap + p, gpq * dpqy + gpr * dpry);
+            acc_add(2 * mcap + p, gpq * dpqz + gpr * dprz);
+            acc_add(q, gqr * dqrx - gpq * dpqx);
+            acc_add(mcap + q, gqr * dqry - gpq * dpqy);
+            acc_add(2 * mcap + q, gqr * dqrz - gpq * dpqz);
+            acc_add(r, -(gpr * dprx + gqr * dqrx));
+            acc_add(mcap + r, -(gpr * dpry + gqr * dqry));
+            acc_add(2 * mcap + r, -(gpr * dprz + gqr * dqrz));
         }
         return R(0);
     };
@@ -583,7 +628,14 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
         }
         esum.add(uu);
         wsum.add(-(gpq * a + gpr * b + gqr * c));
-        if (!use_acc) {
+        if (DET && !use_acc) {
+            // every term on its own: integer sums, the same for any batching
+            if (valid) {
+                gadd(epq, gpq);
+                gadd(epr, gpr);
+                gadd(eqr, gqr);
+            }
+        } else if (!use_acc) {
             // runs of equal e(p,q) are contiguous in a batch (q-major order)
             int key = epq;
             if (!valid) key = -1 - lane;
@@ -591,20 +643,20 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
             int prev = __shfl_up_sync(FULL, key, 1);
             bool head = lane == 0 || prev != key;
             if (valid) {
-                if (head) atomicAdd(G + key, run);
-                atomicAdd(G + epr, gpr);
-                atomicAdd(G + eqr, gqr);
+                if (head) gadd(key, run);
+                gadd(epr, gpr);
+                gadd(eqr, gqr);
             }
         } else if (valid) {
-            Acc<R>::add(acc, mcap, p, gpq * dpqx + gpr * dprx);
-            Acc<R>::add(acc, mcap, mcap + p, gpq * dpqy + gpr * dpry);
-            Acc<R>::add(acc, mcap, 2 * mcap + p, gpq * dpqz + gpr * dprz);
-            Acc<R>::add(acc, mcap, q, gqr * dqrx - gpq * dpqx);
-            Acc<R>::add(acc, mcap, mcap + q, gqr * dqry - gpq * dpqy);
-            Acc<R>::add(acc, mcap, 2 * mcap + q, gqr * dqrz - gpq * dpqz);
-            Acc<R>::add(acc, mcap, r, -(gpr * dprx + gqr * dqrx));
-            Acc<R>::add(acc, mcap, mcap + r, -(gpr * dpry + gqr * dqry));
-            Acc<R>::add(acc, mcap, 2 * mcap + r, -(gpr * dprz + gqr * dqrz));
+            acc_add(p, gpq * dpqx + gpr * dprx);
+            acc_add(mcap + p, gpq * dpqy + gpr * dpry);
+            acc_add(2 * mcap + p, gpq * dpqz + gpr * dprz);
+            acc_add(q, gqr * dqrx - gpq * dpqx);
+            acc_add(mcap + q, gqr * dqry - gpq * dpqy);
+            acc_add(2 * mcap + q, gqr * dqrz - gpq * dpqz);
+            acc_add(r, -(gpr * dprx + gqr * dqrx));
+            acc_add(mcap + r, -(gpr * dpry + gqr * dqry));
+            acc_add(2 * mcap + r, -(gpr * dprz + gqr * dqrz));
         }
     };
     auto push = [&](bool keep, unsigned long long entry) {
@@ -648,10 +700,13 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
         // member); they are counted per lane, prefix-summed and expanded 32 per
         // round, so every lane of a round evaluates one triangle
         const int Ework = rowoff[Mfirst];  // edges whose first molecule can open a triangle
-        for (;;) {
-            int e0 = 0;
-            if (lane == 0) e0 = atomicAdd(&s_next, 32);
-            e0 = __shfl_sync(FULL, e0, 0);
+        for (int it = 0;; it++) {
+            // deterministic mode: warp w takes the groups w, w + nwarps, ...
+            int e0 = (it * nwarps + warp) * 32;
+            if (!DET) {
+                if (lane == 0) e0 = atomicAdd(&s_next, 32);
+                e0 = __shfl_sync(FULL, e0, 0);
+            }
             if (e0 >= Ework) break;
             const int e = e0 + lane;
             int p = 0, q = 0, v = 0, cnt = 0;
@@ -710,7 +765,7 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
                     if (mine) gown += got;
                 }
             }
-            if (!use_acc && e < Ework && gown != R(0)) atomicAdd(G + e, gown);
+            if (!use_acc && e < Ework && gown != R(0)) gadd(e, gown);
         }
     } else {
         // the candidates p < q < r of each p run q-major (q, then r) and are cut
@@ -723,10 +778,13 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
         constexpr int CH = 2048;
         const float t_lo = (float)rc6 * (1.0f - 0x1p-18f), t_hi = (float)rc6 * (1.0f + 0x1p-18f);
         int pc = 0, kbase = 0;  // row cursor; tasks of the rows before it
-        for (;;) {
-            int k = 0;
-            if (lane == 0) k = atomicAdd(&s_next, 1);
-            k = __shfl_sync(FULL, k, 0);
+        for (int it = 0;; it++) {
+            // deterministic mode: warp w takes the tasks w, w + nwarps, ...
+            int k = it * nwarps + warp;
+            if (!DET) {
+                if (lane == 0) k = atomicAdd(&s_next, 1);
+                k = __shfl_sync(FULL, k, 0);
+            }
             for (; pc < Mfirst; pc++) {
                 const int Lc = M - 1 - pc;
                 // no later slot completes an anchored set: no tasks
@@ -823,9 +881,9 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
     for (int m = tid; m < M; m += blockDim.x) {
         PlainSum fxs, fys, fzs;
         if (use_acc) {
-            fxs.add((R)Acc<R>::get(acc, mcap, m));
-            fys.add((R)Acc<R>::get(acc, mcap, mcap + m));
-            fzs.add((R)Acc<R>::get(acc, mcap, 2 * mcap + m));
+            fxs.add((R)acc_get(m));
+            fys.add((R)acc_get(mcap + m));
+            fzs.add((R)acc_get(2 * mcap + m));
         } else if (PAIR) {
             // edge vectors: FP64 from the table (d(lo -> hi), so the sign flips for
             // edges where m is the upper end), FP32 recomputed
@@ -836,7 +894,7 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
                     int y = (w << 5) + __ffs(up) - 1;
                     up &= up - 1u;
                     const int ee = e++;
-                    R g = G[ee];
+                    R g = gget(ee);
                     if (g != R(0)) {
                         R dx, dy, dz;
                         if (F64) {
@@ -854,7 +912,7 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
                     int x = (w << 5) + __ffs(dn) - 1;
                     dn &= dn - 1u;
                     const int ee = rowoff[x] + rank(x, m);
-                    R g = G[ee];
+                    R g = gget(ee);
                     if (g != R(0)) {
                         R dx, dy, dz;
                         if (F64) {
@@ -871,7 +929,7 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
         } else {
             for (int y = 0; y < M; y++) {
                 if (y == m) continue;
-                R g = G[y > m ? tri_index(m, y) : tri_index(y, m)];
+                R g = gget(y > m ? tri_index(m, y) : tri_index(y, m));
                 if (g != R(0)) {
                     R dx, dy, dz;
                     disp(m, y, dx, dy, dz);
@@ -881,13 +939,21 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
                 }
             }
         }
-        double f0 = use_acc ? Acc<R>::get(acc, mcap, m) : fxs.get();
-        double f1 = use_acc ? Acc<R>::get(acc, mcap, mcap + m) : fys.get();
-        double f2 = use_acc ? Acc<R>::get(acc, mcap, 2 * mcap + m) : fzs.get();
+        double f0 = use_acc ? acc_get(m) : fxs.get();
+        double f1 = use_acc ? acc_get(mcap + m) : fys.get();
+        double f2 = use_acc ? acc_get(2 * mcap + m) : fzs.get();
         int g = sidx[m];
-        if (f0 != 0.0) atomicAdd(A.fs + g, f0);
-        if (f1 != 0.0) atomicAdd(A.fs + n + g, f1);
-        if (f2 != 0.0) atomicAdd(A.fs + 2 * n + g, f2);
+        if constexpr (DET) {
+            // 64-bit fixed-point sums across units (converted after the launch)
+            unsigned long long* fsx = reinterpret_cast<unsigned long long*>(A.fs);
+            if (f0 != 0.0) atomicAdd(fsx + g, to_fix<R>(f0, A.status));
+            if (f1 != 0.0) atomicAdd(fsx + n + g, to_fix<R>(f1, A.status));
+            if (f2 != 0.0) atomicAdd(fsx + 2 * n + g, to_fix<R>(f2, A.status));
+        } else {
+            if (f0 != 0.0) atomicAdd(A.fs + g, f0);
+            if (f1 != 0.0) atomicAdd(A.fs + n + g, f1);
+            if (f2 != 0.0) atomicAdd(A.fs + 2 * n + g, f2);
+        }
     }
 
     unsigned long long cand = 0;
@@ -904,7 +970,7 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
 // rho* = 0.8 cell occupancy); FP64: 2 CTAs of 8 warps.  The 3c18 product
 // rule takes up to 16 warps (one CTA per SM when its tables fill shared
 // memory); the bound of 512 threads costs the other kernels registers.
-template <int TRAV, int TRUNC, typename R>
+template <int TRAV, int TRUNC, typename R, bool DET = false>
 __global__ void __launch_bounds__(TRUNC == 1 && TRAV == 1 ? 512 : 256)
     __maxnreg__(sizeof(R) == 8 ? 128 : 56)
     atm_block_kernel(const AtmArgs<R> A)
@@ -913,7 +979,7 @@ __global__ void __launch_bounds__(TRUNC == 1 && TRAV == 1 ? 512 : 256)
     const long long nu = A.ulist ? (long long)*A.ucount : A.b.ncell;
     if (A.work == nullptr) {
         if ((long long)blockIdx.x >= nu) return;
-        atm_block_unit<TRAV, TRUNC, R>(A, A.ulist ? A.ulist[blockIdx.x] : (long long)blockIdx.x);
+        atm_block_unit<TRAV, TRUNC, R, DET>(A, A.ulist ? A.ulist[blockIdx.x] : (long long)blockIdx.x);
         return;
     }
     __shared__ int s_u;
@@ -923,7 +989,7 @@ __global__ void __launch_bounds__(TRUNC == 1 && TRAV == 1 ? 512 : 256)
         __syncthreads();
         const int k = s_u;
         if (k >= nu) break;
-        atm_block_unit<TRAV, TRUNC, R>(A, A.ulist ? A.ulist[k] : (long long)k);
+        atm_block_unit<TRAV, TRUNC, R, DET>(A, A.ulist ? A.ulist[k] : (long long)k);
     }
 }
 

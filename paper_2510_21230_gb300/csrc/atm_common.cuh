@@ -108,6 +108,28 @@ __device__ __forceinline__ void atm_terms(R a, R b, R c, R nu, R& u, R& ua, R& u
     uc = nq5 * (R(0.375) * (R(2) * c * C - A * B) - K * (a * b));
 }
 
+// Deterministic mode: v as a term in units of 2^-B (B = FixBits<R>::B),
+// rounded to nearest; a term of size 2^(FIX_LIMIT - B) or more, or not
+// finite, sets ST_RANGE and counts as zero.  The scaling by a power of two
+// is exact, so a term is rounded once.
+template <typename R>
+__device__ __forceinline__ unsigned long long to_fix(double v, int* status)
+{
+    const double x = v * (double)(1ull << FixBits<R>::B);
+    if (!(fabs(x) < (double)(1ull << FIX_LIMIT))) {
+        atomicOr(status, ST_RANGE);
+        return 0ull;
+    }
+    return (unsigned long long)__double2ll_rn(x);
+}
+
+// a fixed-point sum back in working precision
+template <typename R>
+__device__ __forceinline__ R from_fix(long long v)
+{
+    return (R)((double)v * (1.0 / (double)(1ull << FixBits<R>::B)));
+}
+
 // running sum: plain for FP64, Kahan-compensated for FP32
 template <typename R>
 struct Sum;

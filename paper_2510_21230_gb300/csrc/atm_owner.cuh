@@ -147,10 +147,14 @@ __device__ __forceinline__ void atm_owner_unit(const AtmArgs<R>& A, const long l
     Sum<R> esum, wsum;
     unsigned int nint = 0;
 
-    for (;;) {
-        int i = 0;
-        if (lane == 0) i = atomicAdd(&s_next, 1);
-        i = __shfl_sync(FULL, i, 0);
+    for (int it = 0;; it++) {
+        // deterministic mode: warp w takes the molecules w, w + nwarps, ...
+        // (so every lane's energy and virial sums repeat); else the next free one
+        int i = it * nwarps + warp;
+        if (!A.det) {
+            if (lane == 0) i = atomicAdd(&s_next, 1);
+            i = __shfl_sync(FULL, i, 0);
+        }
         if (i >= Mfirst) break;
 
         // partner list of i: every other staged molecule (product) or those within r_c (pair)

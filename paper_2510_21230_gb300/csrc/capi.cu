@@ -146,6 +146,9 @@ static atm_status check_status(atm_ctx* c)
         return ctx_fail(c, ATM_E_CAPACITY, "a traversal unit holds more molecules than staged");
     if (s & ST_TIMEOUT)
         return ctx_fail(c, ATM_E_TIMEOUT, "a device-side wait for the tensor cores gave up");
+    if (s & ST_RANGE)
+        return ctx_fail(c, ATM_E_RANGE,
+                        "deterministic mode: a force term exceeds the fixed-point range");
     return ctx_fail(c, ATM_E_CUDA, "device status %d", s);
 }
 
@@ -538,6 +541,7 @@ atm_status atm3::ctx_enqueue_forces(atm_ctx* c, int trav, int trunc, int prec, i
     j.side_st = c->side_st;
     j.ev_fork = c->ev_fork;
     j.ev_join = c->ev_join;
+    j.det = c->det;
 
     cudaEvent_t ev;
     if (prec != ATM_SURROGATE && !fused) {
@@ -562,6 +566,8 @@ atm_status atm3::ctx_enqueue_forces(atm_ctx* c, int trav, int trunc, int prec, i
                             j.mcap);
         CU(e);
         if (atm_split_active(j)) c->n_launch += j.ncls;  // the class kernel and ncls - 1 more
+        if (j.det && (trav == ATM_3C18 || trav == ATM_3C08 || trav == ATM_3C08A) && c->n > 0)
+            c->n_launch += 1;  // the fixed-point force conversion
     }
     ctx_prof_end(c, PK_ATM, ev);
     c->n_launch += 1;
@@ -883,6 +889,17 @@ extern "C" atm_status atm_set_options(atm_ctx* c, int persistent, int nwarps, in
     c->opt_graph = graph;
     memset(c->tuned, 0, sizeof(c->tuned));
     drop_graph(c);
+    return ATM_OK;
+}
+
+extern "C" atm_status atm_set_deterministic(atm_ctx* c, int on)
+{
+    if (!c) return ATM_E_INVALID;
+    if (on < 0 || on > 1) return ctx_fail(c, ATM_E_INVALID, "on must be 0 or 1");
+    c->det = on;
+    memset(c->tuned, 0, sizeof(c->tuned));
+    drop_graph(c);
+    c->forces_valid = false;
     return ATM_OK;
 }
 

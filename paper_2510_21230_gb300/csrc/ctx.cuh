@@ -84,6 +84,7 @@ struct atm_ctx {
     // default), CUDA-graph steps; tuned choices per (prec, trav, trunc)
     int opt_persistent = 0, opt_nwarps = 0, opt_graph = 0;
     int opt_cls[3] = {1, 0, 0};  // unit size classes: count, bounds of the first two
+    int det = 0;                 // deterministic mode (atm_set_deterministic)
     // 0 = not tuned, else 1 + persistent + 2 * (nwarps == 8) + 4 * size-class choice
     int tuned[2][atm3::ATM_NTRAV][2] = {};
     // graph of one step, valid for (trav, trunc, prec, mcap, launch choice)

@@ -94,25 +94,28 @@ static cudaError_t launch_atm_one(const ForceJob& j, size_t* smem_set, bool* cap
     AtmPlan P;
     // the block kernel packs staged indices in 11 bits, the owner kernels in 16
     const int limit = (j.trav == 0 || j.trav == 3) ? 65535 : ATM_MCAP_LIMIT;
-    if (j.mcap > limit || !atm_choose_plan(j.trav, j.trunc, j.prec, j.mcap, j.optin, P)) {
+    if (j.mcap > limit || !atm_choose_plan(j.trav, j.trunc, j.prec, j.mcap, j.optin, P, j.det)) {
         *capacity = true;
         return cudaErrorInvalidValue;
     }
     if ((j.nwarps == 2 || j.nwarps == 4 || j.nwarps == 8) && j.trav != 0 && j.trav != 3) {
         AtmPlan Q;
-        if (atm_choose_plan_nw(j.trav, j.trunc, j.prec, j.mcap, j.optin, j.nwarps, Q)) P = Q;
+        if (atm_choose_plan_nw(j.trav, j.trunc, j.prec, j.mcap, j.optin, j.nwarps, Q, j.det)) P = Q;
     }
     cudaError_t e;
-    if (!smem_set || P.smem > *smem_set) {
-        e = j.prec == 0 ? atm_attr_fp64(j.trav, j.trunc, P.smem) : atm_attr_fp32(j.trav, j.trunc, P.smem);
+    // the deterministic instantiations are other kernels: their attribute is
+    // set on its own (smem_set tracks the floating-point ones)
+    if (j.det || !smem_set || P.smem > *smem_set) {
+        e = j.prec == 0 ? atm_attr_fp64(j.trav, j.trunc, P.smem, j.det)
+                        : atm_attr_fp32(j.trav, j.trunc, P.smem, j.det);
         if (e != cudaSuccess) return e;
-        if (smem_set) *smem_set = P.smem;
+        if (smem_set && !j.det) *smem_set = P.smem;
     }
     const int lj = j.lj && (j.trav == 2 || j.trav == 4) && j.trunc == 0;
     int ctas = 0;
     if (j.persistent && work) {
-        int per_sm = j.prec == 0 ? atm_occupancy_fp64(j.trav, j.trunc, P.nwarps, P.smem)
-                                 : atm_occupancy_fp32(j.trav, j.trunc, P.nwarps, P.smem);
+        int per_sm = j.prec == 0 ? atm_occupancy_fp64(j.trav, j.trunc, P.nwarps, P.smem, j.det)
+                                 : atm_occupancy_fp32(j.trav, j.trunc, P.nwarps, P.smem, j.det);
         ctas = std::max(1, per_sm) * std::max(1, j.sms);
         e = cudaMemsetAsync(work, 0, sizeof(int), j.st);
         if (e != cudaSuccess) return e;
@@ -132,6 +135,7 @@ static cudaError_t launch_atm_one(const ForceJob& j, size_t* smem_set, bool* cap
         a.unit_cnt2 = j.unit_cnt2;
         a.ulist = ulist;
         a.ucount = ucount;
+        a.det = j.det;
         return launch_atm_fp64(j.trav, j.trunc, a, P.nwarps, P.smem, ctas, j.st);
     }
     AtmArgs<float> a{};
@@ -148,6 +152,7 @@ static cudaError_t launch_atm_one(const ForceJob& j, size_t* smem_set, bool* cap
     a.unit_cnt2 = j.unit_cnt2;
     a.ulist = ulist;
     a.ucount = ucount;
+    a.det = j.det;
     return launch_atm_fp32(j.trav, j.trunc, a, P.nwarps, P.smem, ctas, j.st);
 }
 
@@ -157,14 +162,26 @@ bool atm_split_active(const ForceJob& j)
            j.b.ncell > 0;
 }
 
+static cudaError_t enqueue_atm_launches(const ForceJob& j, size_t* smem_set, bool* capacity);
+
 cudaError_t enqueue_atm(const ForceJob& j, size_t* smem_set, bool* capacity)
+{
+    cudaError_t e = enqueue_atm_launches(j, smem_set, capacity);
+    // deterministic block traversals left 64-bit fixed-point sums in f_atm
+    if (e == cudaSuccess && j.det && (j.trav == 1 || j.trav == 2 || j.trav == 4) && j.b.ntot > 0)
+        e = launch_fix_to_double(j.f_atm, 3 * j.b.ntot, j.prec == 0 ? FixBits<double>::B
+                                                                   : FixBits<float>::B, j.st);
+    return e;
+}
+
+static cudaError_t enqueue_atm_launches(const ForceJob& j, size_t* smem_set, bool* capacity)
 {
     *capacity = false;
     {
         // every launch's plan must fit before anything is enqueued
         AtmPlan P;
         const int limit = (j.trav == 0 || j.trav == 3) ? 65535 : ATM_MCAP_LIMIT;
-        if (j.mcap > limit || !atm_choose_plan(j.trav, j.trunc, j.prec, j.mcap, j.optin, P)) {
+        if (j.mcap > limit || !atm_choose_plan(j.trav, j.trunc, j.prec, j.mcap, j.optin, P, j.det)) {
             *capacity = true;
             return cudaErrorInvalidValue;
         }

@@ -56,6 +56,9 @@ struct ForceJob {
     // class kernel and joined back before the evaluation ends
     cudaStream_t side_st = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // deterministic mode: fixed work order; the block traversals sum their
+    // terms in 64-bit fixed point and f_atm is converted back after them
+    int det = 0;
 };
 
 cudaError_t enqueue_lj(const ForceJob& j);

@@ -631,6 +631,16 @@ __global__ void k_gather_forces(long long n, const int* __restrict__ perm,
     }
 }
 
+// the deterministic mode's force sums: 64-bit integers in units of 2^-bits,
+// read and rewritten in place as doubles (the value is rounded once)
+__global__ void k_fix_to_double(double* __restrict__ f, long long m, double scale)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const long long v = reinterpret_cast<const long long*>(f)[i];
+    f[i] = (double)v * scale;
+}
+
 // ---------------------------------------------------------------- launchers
 
 static inline unsigned nblk(long long m, int b) { return (unsigned)((m + b - 1) / b); }
@@ -744,6 +754,13 @@ cudaError_t launch_density(const Batch& b, const double* x, int axis, int nbins,
 {
     if (b.ntot <= 0) return cudaSuccess;
     k_density<<<nblk(b.ntot, MD_BLOCK), MD_BLOCK, 0, st>>>(b, x, axis, nbins, counts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fix_to_double(double* f, long long m, int bits, cudaStream_t st)
+{
+    if (m <= 0) return cudaSuccess;
+    k_fix_to_double<<<nblk(m, MD_BLOCK), MD_BLOCK, 0, st>>>(f, m, 1.0 / (double)(1ull << bits));
     return cudaGetLastError();
 }
 

@@ -78,5 +78,8 @@ cudaError_t launch_density(const Batch& b, const double* x, int axis, int nbins,
 // and counts them in counts[k]
 cudaError_t launch_unit_classes(const Batch& b, const int* start, int trav, int ncls, int cut0,
                                 int cut1, int* ulist, int* counts, cudaStream_t st);
+// in place: m signed 64-bit fixed-point sums in units of 2^-bits (the
+// deterministic mode's force accumulator) become doubles
+cudaError_t launch_fix_to_double(double* f, long long m, int bits, cudaStream_t st);
 
 }  // namespace atm3

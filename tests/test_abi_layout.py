@@ -29,7 +29,7 @@ ENUMS = {
     "PRECISIONS": {"fp64": "ATM_FP64", "fp32c": "ATM_FP32C", "surrogate": "ATM_SURROGATE"},
 }
 STATUS_NAMES = ["ATM_OK", "ATM_E_INVALID", "ATM_E_BOX_TOO_SMALL", "ATM_E_CUDA", "ATM_E_TIMEOUT",
-                "ATM_E_NONFINITE", "ATM_E_STATE", "ATM_E_CAPACITY"]
+                "ATM_E_NONFINITE", "ATM_E_STATE", "ATM_E_CAPACITY", "ATM_E_RANGE"]
 
 
 @pytest.fixture(scope="module")
