@@ -360,8 +360,12 @@ atm_status atm_compute_forces_noalloc(const atm_params* params, int64_t n, const
  * Parameters: ATM_SUR_NPARAM floats laid out W1[32][64], b1[64], W2[64][64],
  * b2[64], W3[64][3], b3[3] (row-major, input index first), plus mean[32] and
  * scale[32] (> 0).  Inference: inputs, weights and the two hidden layers in
- * bfloat16 on the tensor cores, FP32 sums.  Training: FP32 master weights,
- * FP32 gradients, Adam (beta1 0.9, beta2 0.999, eps 1e-8) on the loss
+ * bfloat16 on the tensor cores, FP32 sums.  Training: FP32 master weights;
+ * gradients by default on the tensor cores (the inference arithmetic forward,
+ * then the backward GEMMs with bfloat16 operands -- inputs, activations,
+ * weights, dL/dw and the pre-activation gradients -- and FP32 sums), or in
+ * FP32 on the CUDA cores (atm_surrogate_training_arithmetic); FP32
+ * gradients, Adam (beta1 0.9, beta2 0.999, eps 1e-8) on the loss
  *   L = sum_i |F_i - F_i^ref|^2 / (3 B sigma2)
  * over a minibatch of B rows, sigma2 = mean squared target force component of
  * the data set (L = 1 for the zero model).
@@ -400,8 +404,9 @@ atm_status atm_surrogate_descriptors(atm_ctx* ctx, float* desc, float* vec);
 atm_status atm_surrogate_mlp(atm_ctx* ctx, int64_t rows, const float* desc, const float* vec,
                              float* w, float* force);
 
-/* FP32 loss and gradient of the current master parameters on given rows (the
- * whole set is one batch).  loss may be NULL; grad has ATM_SUR_NPARAM floats. */
+/* Loss and gradient of the current master parameters on given rows (the whole
+ * set is one batch), in the arithmetic atm_surrogate_training_arithmetic
+ * selects.  loss may be NULL; grad has ATM_SUR_NPARAM floats. */
 atm_status atm_surrogate_loss_grad(atm_ctx* ctx, int64_t rows, const float* desc,
                                    const float* vec, const float* target, double sigma2,
                                    double* loss, float* grad);
@@ -423,6 +428,13 @@ atm_status atm_surrogate_clear(atm_ctx* ctx);
  * receives the minibatch loss of each step.  STATE without model or data. */
 atm_status atm_surrogate_train(atm_ctx* ctx, int64_t steps, int64_t batch, double lr,
                                uint64_t seed, double* loss);
+
+/* Arithmetic of the gradients of atm_surrogate_train and atm_surrogate_loss_grad:
+ * tensor_cores = 1 (the default): tcgen05 GEMMs with bfloat16 operands and
+ * FP32 accumulators, 128 samples per tile, the forward pass in the inference
+ * kernel's arithmetic; 0: FP32 on the CUDA cores (64 samples per block,
+ * FP32 activations).  Errors: INVALID. */
+atm_status atm_surrogate_training_arithmetic(atm_ctx* ctx, int tensor_cores);
 
 /* atm_step with ATM_SURROGATE: every `exact_every` steps (0 = never; default
  * 50) the step uses the exact FP32C traversal instead and the surrogate is

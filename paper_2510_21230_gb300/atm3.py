@@ -37,7 +37,8 @@ EXPORTED = ["atm_abi_version", "atm_create", "atm_batch_create", "atm_batch_size
             "atm_surrogate_train", "atm_surrogate_options", "atm_surrogate_error",
             "atm_measure_fma_peak", "atm_rdf_accumulate", "atm_rdf_get", "atm_rdf_reset",
             "atm_lj_tail", "atm_thermostat", "atm_measure_rsqrt_peak", "atm_set_forces",
-            "atm_set_unit_classes", "atm_batch_cells", "atm_cell_grid", "atm_set_deterministic"]
+            "atm_set_unit_classes", "atm_batch_cells", "atm_cell_grid", "atm_set_deterministic",
+            "atm_surrogate_training_arithmetic"]
 
 SUR_NDESC, SUR_NVEC, SUR_NPARAM = 32, 9, 6467
 
@@ -141,6 +142,7 @@ def load():
         "atm_surrogate_clear": [P],
         "atm_surrogate_train": [P, i64, i64, ctypes.c_double, ctypes.c_uint64, P],
         "atm_surrogate_options": [P, i32],
+        "atm_surrogate_training_arithmetic": [P, i32],
         "atm_surrogate_error": [P, P, P, P, i32],
         "atm_measure_fma_peak": [i32, i32, P],
         "atm_rdf_accumulate": [P, ctypes.c_double, i32],
@@ -483,6 +485,11 @@ class AtmSystem:
         self._check(self._lib.atm_surrogate_train(self._ctx, int(steps), int(batch), float(lr),
                                                 int(seed), _host_ptr(loss)))
         return loss
+
+    def surrogate_training_arithmetic(self, tensor_cores=True):
+        """Gradients on the tensor cores (bfloat16 operands, FP32 sums; the
+        default) or in FP32 on the CUDA cores."""
+        self._check(self._lib.atm_surrogate_training_arithmetic(self._ctx, 1 if tensor_cores else 0))
 
     def surrogate_options(self, exact_every=50):
         self._check(self._lib.atm_surrogate_options(self._ctx, int(exact_every)))

@@ -60,6 +60,9 @@ struct SurState {
     float* vb = nullptr;
     double* d_mon = nullptr;      // [2] sum |diff|^2, sum |exact|^2
     long long checks = 0;
+    // gradients on the tensor cores (bfloat16 operands, FP32 accumulators;
+    // the default) or in FP32 on the CUDA cores
+    int train_tc = 1;
 };
 
 }  // namespace atm3
@@ -439,7 +442,7 @@ atm_status grad_step(atm_ctx* c, SurState* S, const float* D, const float* V, co
                      const long long* idx, long long batch, double sigma2, int update, double lr,
                      double* loss_dev, float* grad_dev)
 {
-    const int nct = (int)((batch + SUR_TILE - 1) / SUR_TILE);
+    const int nct = S->train_tc ? sur_grad_tc_tiles(batch) : (int)((batch + SUR_TILE - 1) / SUR_TILE);
     if (nct > S->part_cap) {
         if (S->part) cudaFree(S->part);
         if (S->part_loss) cudaFree(S->part_loss);
@@ -462,7 +465,12 @@ atm_status grad_step(atm_ctx* c, SurState* S, const float* D, const float* V, co
     g.norm = (float)(1.0 / (3.0 * (double)batch * sigma2));
     g.part = S->part;
     g.part_loss = S->part_loss;
-    CU(launch_sur_grad(g, nct, c->st));
+    g.packed = S->packed;
+    g.status = c->d_status;
+    if (S->train_tc)
+        CU(launch_sur_grad_tc(g, c->sms, c->st));
+    else
+        CU(launch_sur_grad(g, nct, c->st));
     SurAdamArgs a{};
     a.part = S->part;
     a.part_loss = S->part_loss;
@@ -698,6 +706,16 @@ extern "C" atm_status atm_surrogate_options(atm_ctx* c, int exact_every)
     if (!S) return ctx_fail(c, ATM_E_CUDA, "out of host memory");
     S->exact_every = exact_every;
     S->count = 0;
+    return ATM_OK;
+}
+
+extern "C" atm_status atm_surrogate_training_arithmetic(atm_ctx* c, int tensor_cores)
+{
+    if (!c) return ATM_E_INVALID;
+    if (tensor_cores < 0 || tensor_cores > 1) return ctx_fail(c, ATM_E_INVALID, "0 or 1");
+    SurState* S = state(c);
+    if (!S) return ctx_fail(c, ATM_E_CUDA, "out of host memory");
+    S->train_tc = tensor_cores;
     return ATM_OK;
 }
 

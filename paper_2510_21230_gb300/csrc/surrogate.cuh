@@ -109,6 +109,10 @@ struct SurGradArgs {
     float norm;               // 1 / (3 batch sigma2)
     float* part;              // [nct][SUR_NP]
     double* part_loss;        // [nct]
+    // tensor-core training: the bfloat16 inference copy of the weights (the
+    // forward pass) and the device status word (ST_TIMEOUT)
+    const SurPacked* packed;
+    int* status;
 };
 
 constexpr int SUR_TILE = 64;      // samples per CTA of the training kernel
@@ -145,6 +149,10 @@ cudaError_t launch_sur_mlp_tc(long long n, const float* D, const __nv_bfloat16* 
                               const SurPacked* model, float* w, float* f, double* f_soa, int* status,
                               int sms, cudaStream_t st);
 cudaError_t launch_sur_grad(const SurGradArgs& a, int nct, cudaStream_t st);
+// the same gradient on the tensor cores (bfloat16 operands, FP32 accumulators):
+// one part per 128-sample tile, sur_grad_tc_tiles(batch) parts
+cudaError_t launch_sur_grad_tc(const SurGradArgs& a, int sms, cudaStream_t st);
+int sur_grad_tc_tiles(long long batch);
 cudaError_t launch_sur_adam(const SurAdamArgs& a, cudaStream_t st);
 // pack FP32 master parameters + normalisation into the inference layout
 cudaError_t launch_sur_pack(const float* P, const float* mean, const float* scale,

@@ -178,8 +178,39 @@ def test_batch_surrogate_equals_separate(atm3):
 
 # ------------------------------------------------------------------- training
 
+# parameter blocks of the flat parameter vector: W1, b1, W2, b2, W3, b3
+BLOCKS = [(0, 2048), (2048, 2112), (2112, 6208), (6208, 6272), (6272, 6464), (6464, 6467)]
+
+
 @pytest.mark.parametrize("rows", [64, 300, 2049])
-def test_loss_grad_matches_oracle(atm3, rows):
+def test_loss_grad_matches_oracle_fp32(atm3, rows):
+    """FP32 gradients on the CUDA cores against the FP64 oracle (1e-5)."""
+    P = synth.sur_params(21)
+    mean = np.linspace(-0.5, 0.5, 32).astype(np.float32)
+    scale = np.linspace(0.7, 1.5, 32).astype(np.float32)
+    D, V, T = synth.sur_rows(rows, 22, mean, scale)
+    s2 = 0.37
+    with atm3.AtmSystem(10.0, 1, rc=RC, nu=NU) as s:
+        s.surrogate_set_model(P, mean, scale)
+        s.surrogate_training_arithmetic(tensor_cores=False)
+        L, g = s.surrogate_loss_grad(D, V, T, s2)
+    Lo, go = oracle.sur_loss_grad(P.astype(np.float64), mean, scale, D, V, T, s2)
+    assert abs(L - Lo) <= 1e-5 * Lo
+    assert np.linalg.norm(g - go) <= 1e-5 * np.linalg.norm(go)
+    assert np.max(np.abs(g - go)) <= 1e-5 * np.abs(go).max()
+
+
+@pytest.mark.parametrize("rows", [64, 300, 2049, 8192])
+def test_loss_grad_tensor_cores_matches_oracle(atm3, rows):
+    """Gradients on the tensor cores (bfloat16 operands, FP32 sums; ragged last
+    tile for 300 and 2049 rows) against the FP64 oracle's backward pass.
+    bfloat16 keeps 8 significant bits (unit roundoff 2^-9 = 3.9e-3); every
+    gradient term is a product of two rounded operands whose own inputs were
+    rounded in the forward pass, a few times 2^-9 per term, and the sums over
+    the samples average the roundings, so each parameter block must agree to
+    1e-2 of its norm (elementwise to 3e-2 of the block's largest entry).  The
+    loss follows the same bfloat16 forward pass as the inference kernel, so it
+    is checked against the oracle's bfloat16 emulation of that pass (1e-3)."""
     P = synth.sur_params(21)
     mean = np.linspace(-0.5, 0.5, 32).astype(np.float32)
     scale = np.linspace(0.7, 1.5, 32).astype(np.float32)
@@ -188,10 +219,34 @@ def test_loss_grad_matches_oracle(atm3, rows):
     with atm3.AtmSystem(10.0, 1, rc=RC, nu=NU) as s:
         s.surrogate_set_model(P, mean, scale)
         L, g = s.surrogate_loss_grad(D, V, T, s2)
-    Lo, go = oracle.sur_loss_grad(P.astype(np.float64), mean, scale, D, V, T, s2)
-    assert abs(L - Lo) <= 1e-5 * Lo
-    assert np.linalg.norm(g - go) <= 1e-5 * np.linalg.norm(go)
-    assert np.max(np.abs(g - go)) <= 1e-5 * np.abs(go).max()
+    _, go = oracle.sur_loss_grad(P.astype(np.float64), mean, scale, D, V, T, s2)
+    _, Fb = oracle.sur_mlp(P.astype(np.float64), mean, scale, D, V, bf16_=True)
+    Lb = float(np.sum((Fb - T.astype(np.float64).reshape(-1, 3)) ** 2) / (3 * rows * s2))
+    assert abs(L - Lb) <= 1e-3 * Lb, (L, Lb)
+    for a, b in BLOCKS:
+        d = g[a:b] - go[a:b]
+        assert np.linalg.norm(d) <= 1e-2 * np.linalg.norm(go[a:b]), (a, b, np.linalg.norm(d) / np.linalg.norm(go[a:b]))
+        assert np.abs(d).max() <= 3e-2 * np.abs(go[a:b]).max(), (a, b)
+
+
+def test_tensor_core_and_fp32_training_agree(atm3):
+    """Fifty Adam steps from the same start with either gradient arithmetic
+    reach losses within 2 % of each other on teacher targets."""
+    mean = np.zeros(32, dtype=np.float32)
+    scale = np.ones(32, dtype=np.float32)
+    D, V, _ = synth.sur_rows(4096, 51, mean, scale)
+    teacher = synth.sur_params(52, wscale=0.2)
+    _, T = oracle.sur_mlp(teacher.astype(np.float64), mean, scale, D, V)
+    out = {}
+    for tc in (True, False):
+        with atm3.AtmSystem(10.0, 1, rc=RC, nu=NU) as s:
+            s.surrogate_set_model(synth.sur_params(53, wscale=0.05), mean, scale)
+            s.surrogate_training_arithmetic(tensor_cores=tc)
+            s.surrogate_add_rows(D, V, T.astype(np.float32))
+            out[tc] = s.surrogate_train(50, batch=1024, lr=2e-3, seed=3)
+    assert np.all(np.isfinite(out[True]))
+    assert out[True][-1] < 0.9 * out[True][0]
+    assert abs(out[True][-1] - out[False][-1]) <= 2e-2 * out[False][-1]
 
 
 def test_adam_step_matches_oracle(atm3):
@@ -202,6 +257,7 @@ def test_adam_step_matches_oracle(atm3):
     lr = 1e-3
     with atm3.AtmSystem(10.0, 1, rc=RC, nu=NU) as s:
         s.surrogate_set_model(P, mean, scale)
+        s.surrogate_training_arithmetic(tensor_cores=False)  # pins Adam on the exact gradient
         s.surrogate_add_rows(D, V, T)
         rows, s2 = s.surrogate_dataset()
         loss = s.surrogate_train(1, batch=0, lr=lr)
