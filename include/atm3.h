@@ -225,6 +225,24 @@ atm_status atm_get_results(atm_ctx* ctx, atm_result* out);
  * Options reset any autotuned choice.  Errors: INVALID. */
 atm_status atm_set_options(atm_ctx* ctx, int persistent, int nwarps, int graph);
 
+/* Domain decomposition (the paper's outlook: distributed memory).  The
+ * replica owns only the cell layers z_lo <= c_z < z_hi of its grid (0 <= z_lo
+ * < z_hi <= n_z; all layers by default): ATM units whose base cell (3C01,
+ * 3C18, 3CW) or anchor cell (3C08, 3C08A) lies in another layer, and the LJ
+ * pair terms of molecules in another layer, are skipped, so energies,
+ * virials and counts are those of the owned units and molecules.  A context
+ * that holds a domain's molecules plus one halo layer of the neighbouring
+ * domains' molecules below and above then gives: the complete force of each
+ * owned molecule under 3C01 and LJ (owner computes); under 3C18 / 3C08 /
+ * 3C08A the owned units' share, with the forces those units put on the halo
+ * layer above to be added to its owner's molecules (their units reach one
+ * layer up); the global sums are the sums over the domains.  The host side
+ * (partition, halo exchange, force return, sums) is
+ * paper_2510_21230_gb300/domain.py.  The surrogate evaluates whole replicas:
+ * it returns INVALID while layers are restricted.  Resets the current
+ * forces.  Errors: INVALID, CUDA. */
+atm_status atm_set_owned_layers(atm_ctx* ctx, int replica, int z_lo, int z_hi);
+
 /* Deterministic mode (on = 1; 0 = off, the default).  Repeated evaluations
  * and steps of the same state with the same launch options give bit-identical
  * forces, energies, virials and counts (without it, forces, energies and

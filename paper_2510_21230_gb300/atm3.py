@@ -38,7 +38,7 @@ EXPORTED = ["atm_abi_version", "atm_create", "atm_batch_create", "atm_batch_size
             "atm_measure_fma_peak", "atm_rdf_accumulate", "atm_rdf_get", "atm_rdf_reset",
             "atm_lj_tail", "atm_thermostat", "atm_measure_rsqrt_peak", "atm_set_forces",
             "atm_set_unit_classes", "atm_batch_cells", "atm_cell_grid", "atm_set_deterministic",
-            "atm_surrogate_training_arithmetic"]
+            "atm_surrogate_training_arithmetic", "atm_set_owned_layers"]
 
 SUR_NDESC, SUR_NVEC, SUR_NPARAM = 32, 9, 6467
 
@@ -120,6 +120,7 @@ def load():
         "atm_set_options": [P, i32, i32, i32],
         "atm_set_unit_classes": [P, i32, P],
         "atm_set_deterministic": [P, i32],
+        "atm_set_owned_layers": [P, i32, i32, i32],
         "atm_autotune": [P, i32, i32, i32, i32, ctypes.POINTER(Tuning)],
         "atm_density_accumulate": [P, i32, i32],
         "atm_density_get": [P, P, P],
@@ -341,6 +342,11 @@ class AtmSystem:
     def set_options(self, persistent=False, nwarps=0, graph=False):
         self._check(self._lib.atm_set_options(self._ctx, int(bool(persistent)), int(nwarps),
                                               int(bool(graph))))
+
+    def set_owned_layers(self, z_lo, z_hi, replica=0):
+        """Domain decomposition: the replica owns cell layers [z_lo, z_hi)
+        (``atm_set_owned_layers``)."""
+        self._check(self._lib.atm_set_owned_layers(self._ctx, int(replica), int(z_lo), int(z_hi)))
 
     def set_deterministic(self, on=True):
         """Deterministic mode (``atm_set_deterministic``): repeated runs give

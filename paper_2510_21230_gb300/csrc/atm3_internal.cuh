@@ -54,7 +54,18 @@ struct Rep {
     float q_lo, q_hi, dmin;    // FP64 prefilter band of the FP32 product of the squared sides
     double rw2;                // wide traversal: (2 min w)^2, partners and third sides below it
     float rw2f;
+    // domain decomposition: the cell layers z in [own_z0, own_z1) this context
+    // owns (all layers by default); ATM units based or anchored elsewhere and
+    // LJ for molecules elsewhere contribute nothing
+    int own_z0, own_z1;
 };
+
+// the unit (base or anchor cell, index inside its replica) lies in an owned layer
+__host__ __device__ __forceinline__ bool unit_owned(const Rep& rp, long long lu)
+{
+    const int cz = (int)(lu / ((long long)rp.g.nc[0] * rp.g.nc[1]));
+    return cz >= rp.own_z0 && cz < rp.own_z1;
+}
 
 struct Batch {
     const Rep* rep;          // [R]

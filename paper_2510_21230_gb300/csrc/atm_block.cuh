@@ -173,6 +173,22 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
     unsigned long long* queue =
         reinterpret_cast<unsigned long long*>(smem + plan.off_queue) + warp * 64;
 
+    if (!unit_owned(rp, lu)) {
+        // another domain's unit: no forces, zero sums
+        if (tid == 0) {
+            A.unit_ew[2 * u] = 0.0;
+            A.unit_ew[2 * u + 1] = 0.0;
+            A.unit_cnt[2 * u] = 0ull;
+            A.unit_cnt[2 * u + 1] = 0ull;
+            if (PAIR && (TRAV == 2 || TRAV == 4) && A.lj) {
+                A.unit_ew2[2 * u] = 0.0;
+                A.unit_ew2[2 * u + 1] = 0.0;
+                A.unit_cnt2[2 * u] = 0ull;
+                A.unit_cnt2[2 * u + 1] = 0ull;
+            }
+        }
+        return;
+    }
     if (warp == 0) unit_slots<TRAV, S>(rp.g, A.cell_start + rp.cell0, lu, s_beg, s_cell0, s_off);
     if (tid == 0) s_next = 0;
     __syncthreads();

@@ -316,7 +316,7 @@ __device__ __forceinline__ void unit_reduce_store2(double e, double w, unsigned 
         unit_ew2[2 * u] = et;
         unit_ew2[2 * u + 1] = wt;
         unit_cnt2[2 * u] = cand;
-        unit_cnt2[2 * u + 1] = 2 * nt;  // the reduction halves the pair visits of the owner kernel
+        unit_cnt2[2 * u + 1] = nt;
     }
 }
 

@@ -57,6 +57,22 @@ __device__ __forceinline__ void atm_owner_unit(const AtmArgs<R>& A, const long l
     float* pa32 = F64 ? reinterpret_cast<float*>(smem + plan.off_pa32) + warp * pcap : nullptr;
     unsigned* queue = reinterpret_cast<unsigned*>(smem + plan.off_queue) + warp * 64;
 
+    if (!unit_owned(rp, lu)) {
+        // another domain's base cell: its molecules get no owner force here
+        if (tid == 0) {
+            A.unit_ew[2 * u] = 0.0;
+            A.unit_ew[2 * u + 1] = 0.0;
+            A.unit_cnt[2 * u] = 0ull;
+            A.unit_cnt[2 * u + 1] = 0ull;
+        }
+        const long long n = A.n;
+        for (int g = A.cell_start[u] + tid; g < A.cell_start[u + 1]; g += blockDim.x) {
+            A.fs[g] = 0.0;
+            A.fs[n + g] = 0.0;
+            A.fs[2 * n + g] = 0.0;
+        }
+        return;
+    }
     if (warp == 0) unit_slots<TRAV, S>(rp.g, A.cell_start + rp.cell0, lu, s_beg, s_cell0, s_off);
     if (tid == 0) {
         s_next = 0;

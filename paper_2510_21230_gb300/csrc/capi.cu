@@ -499,6 +499,10 @@ atm_status atm3::ctx_enqueue_forces(atm_ctx* c, int trav, int trunc, int prec, i
                                     bool fuse_lj)
 {
     const bool fused = fuse_lj && lj_fused(trav, trunc, prec);
+    if (prec == ATM_SURROGATE)
+        for (const Rep& r : c->reps)
+            if (r.own_z0 != 0 || r.own_z1 != r.g.nc[2])
+                return ctx_fail(c, ATM_E_INVALID, "the surrogate evaluates whole replicas (owned layers set)");
     if (trav == ATM_3CW)
         for (const Rep& r : c->reps)
             if (r.g.nc[0] < 5 || r.g.nc[1] < 5 || r.g.nc[2] < 5)
@@ -889,6 +893,24 @@ extern "C" atm_status atm_set_options(atm_ctx* c, int persistent, int nwarps, in
     c->opt_graph = graph;
     memset(c->tuned, 0, sizeof(c->tuned));
     drop_graph(c);
+    return ATM_OK;
+}
+
+extern "C" atm_status atm_set_owned_layers(atm_ctx* c, int replica, int z_lo, int z_hi)
+{
+    if (!c) return ATM_E_INVALID;
+    if (replica < 0 || replica >= c->R) return ctx_fail(c, ATM_E_INVALID, "no replica %d", replica);
+    Rep& r = c->reps[replica];
+    if (z_lo < 0 || z_hi > r.g.nc[2] || z_lo >= z_hi)
+        return ctx_fail(c, ATM_E_INVALID, "owned layers must satisfy 0 <= z_lo < z_hi <= %d",
+                        r.g.nc[2]);
+    CU(cudaSetDevice(c->device));
+    r.own_z0 = z_lo;
+    r.own_z1 = z_hi;
+    CU(cudaMemcpyAsync(c->d_rep + replica, &r, sizeof(Rep), cudaMemcpyHostToDevice, c->st));
+    CU(cudaStreamSynchronize(c->st));
+    drop_graph(c);
+    c->forces_valid = false;
     return ATM_OK;
 }
 

@@ -68,6 +68,8 @@ atm_status make_rep(const atm_params& p, long long n, long long mol0, long long 
     const double wmin = std::min(r.g.w[0], std::min(r.g.w[1], r.g.w[2]));
     r.rw2 = (2.0 * wmin) * (2.0 * wmin);
     r.rw2f = (float)r.rw2;
+    r.own_z0 = 0;
+    r.own_z1 = r.g.nc[2];
     return ATM_OK;
 }
 

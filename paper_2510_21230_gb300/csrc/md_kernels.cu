@@ -286,10 +286,11 @@ struct LjArith<float> {
 
 // LJ (section 5) with owner-computes over the 27-cell neighbourhood: every
 // molecule sums its own pair forces (no atomics, deterministic); each pair is
-// seen from both ends, so the energy and virial take half per visit and the
-// interacting count is visits / 2.  The candidate count is that of the
-// half-shell traversal: later molecules of the own cell plus the 13 forward
-// cells.
+// seen from both ends, so the energy and virial take half per visit.  The
+// candidate and interacting counts are those of the half-shell traversal:
+// later molecules of the own cell plus the 13 forward cells, so every pair
+// is counted once, by one of its molecules (also when the two belong to
+// different domains).
 template <typename R>
 __global__ void __launch_bounds__(128) k_lj_owner(const LjArgs<R> A)
 {
@@ -302,6 +303,17 @@ __global__ void __launch_bounds__(128) k_lj_owner(const LjArgs<R> A)
     const int* st = A.cell_start + rp.cell0;
     int cx, cy, cz;
     cell_coords(rp.g, cg - rp.cell0, cx, cy, cz);
+    if (cz < rp.own_z0 || cz >= rp.own_z1) {
+        // another domain's molecule: no pair terms here
+        A.fs[s] = 0.0;
+        A.fs[n + s] = 0.0;
+        A.fs[2 * n + s] = 0.0;
+        A.mol_ew[2 * s] = 0.0;
+        A.mol_ew[2 * s + 1] = 0.0;
+        A.mol_cnt[2 * s] = 0u;
+        A.mol_cnt[2 * s + 1] = 0u;
+        return;
+    }
     const bool f64 = sizeof(R) == 8;
     const R w0 = (R)rp.g.w[0], w1 = (R)rp.g.w[1], w2 = (R)rp.g.w[2];
     const R rc2 = f64 ? (R)rp.rc2 : (R)rp.rc2f;
@@ -313,7 +325,7 @@ __global__ void __launch_bounds__(128) k_lj_owner(const LjArgs<R> A)
     R xs = A.xl[s], ys = A.xl[n + s], zs = A.xl[2 * n + s];
     R fx = 0, fy = 0, fz = 0;
     R esum = 0, wsum = 0;
-    unsigned visits = 0, cand = 0;
+    unsigned pairs = 0, cand = 0;
     for (int t = 0; t < 27; t++) {
         int dx, dy, dz;
         offset27(t, dx, dy, dz);
@@ -339,7 +351,7 @@ __global__ void __launch_bounds__(128) k_lj_owner(const LjArgs<R> A)
             R ddz = Q::add(Q::sub(A.xl[2 * n + q], zs), sz);
             R a = Q::add(Q::add(Q::mul(ddx, ddx), Q::mul(ddy, ddy)), Q::mul(ddz, ddz));
             if (!(a < rc2)) continue;
-            visits++;
+            if (t > 13 || (t == 13 && q > s)) pairs++;
             R ia = Q::rcp(a);  // correctly rounded: the same value as 1 / a
             R s2 = sig2 * ia;
             R s3 = s2 * s2 * s2;
@@ -358,7 +370,7 @@ __global__ void __launch_bounds__(128) k_lj_owner(const LjArgs<R> A)
     A.mol_ew[2 * s] = 0.5 * (double)esum;
     A.mol_ew[2 * s + 1] = 0.5 * (double)wsum;
     A.mol_cnt[2 * s] = cand;
-    A.mol_cnt[2 * s + 1] = visits;
+    A.mol_cnt[2 * s + 1] = pairs;
 }
 
 // ---------------------------------------------------------------- integrator
@@ -611,7 +623,7 @@ __global__ void __launch_bounds__(128) k_final_reduce(ReduceArgs R)
         t.n_cand3 = c3;
         t.n_int3 = i3;
         t.n_cand2 = c2;
-        t.n_int2 = i2 / 2;  // each pair was visited from both ends
+        t.n_int2 = i2;
         R.out[r] = t;
     }
 }

@@ -14,7 +14,7 @@ struct LjArgs {
     const int* cell_sorted;   // [n] global cell of each sorted slot
     double* fs;               // sorted-order LJ force, SoA [3n] (fully written)
     double* mol_ew;           // [2n] per sorted molecule: half of its pair energies, virials
-    unsigned* mol_cnt;        // [2n] per sorted molecule: half-shell candidates, visits
+    unsigned* mol_cnt;        // [2n] per sorted molecule: half-shell candidates, interacting pairs
 };
 
 // device-side copy of atm_result (same layout)

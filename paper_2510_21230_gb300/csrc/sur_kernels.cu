@@ -159,8 +159,10 @@ __global__ void __launch_bounds__(SUR_BLOCK, 5) k_sur_desc(const SurForceArgs A)
     };
     // LJ of one neighbour (the FP32 LJ kernel's expressions)
     float ljx = 0.f, ljy = 0.f, ljz = 0.f, lje = 0.f, ljw = 0.f;
-    unsigned lj_cand = 0u, lj_visits = 0u;
-    auto lj_add = [&](float ex, float ey, float ez, float a) {
+    unsigned lj_cand = 0u, lj_pairs = 0u;
+    // fwd: the neighbour is in the forward half shell (a later molecule of the
+    // own cell, or a forward cell), so the pair is counted once, here
+    auto lj_add = [&](float ex, float ey, float ez, float a, bool fwd) {
         const float ia = __frcp_rn(a);  // correctly rounded: the same value as 1 / a
         const float s2 = rp.sig2f * ia;
         const float s3 = s2 * s2 * s2;
@@ -171,7 +173,7 @@ __global__ void __launch_bounds__(SUR_BLOCK, 5) k_sur_desc(const SurForceArgs A)
         ljz -= fw * ez;
         lje += rp.eps4f * (s6 - s3) - rp.ushiftf;
         ljw += fw * a;
-        lj_visits++;
+        lj_pairs += fwd ? 1u : 0u;
     };
     int K = 0, kself = 0;
     unsigned word = 0u;
@@ -216,10 +218,11 @@ __global__ void __launch_bounds__(SUR_BLOCK, 5) k_sur_desc(const SurForceArgs A)
             int dx, dy, dz;
             offset27(t, dx, dy, dz);
             float ex, ey, ez;
-            const float r2 = dist2(x4[k + s_qoff[t * SUR_BLOCK + tid]], (float)dx * rp.wf[0],
-                                   (float)dy * rp.wf[1], (float)dz * rp.wf[2], ex, ey, ez);
+            const int q = k + s_qoff[t * SUR_BLOCK + tid];
+            const float r2 = dist2(x4[q], (float)dx * rp.wf[0], (float)dy * rp.wf[1],
+                                   (float)dz * rp.wf[2], ex, ey, ez);
             sur_add(acc, kc, ex, ey, ez, r2);
-            if (LJ) lj_add(ex, ey, ez, r2);
+            if (LJ) lj_add(ex, ey, ez, r2, t > 13 || (t == 13 && q > s));
         }
     } else {
         // crowded neighbourhood: test and accumulate in one pass
@@ -235,7 +238,7 @@ __global__ void __launch_bounds__(SUR_BLOCK, 5) k_sur_desc(const SurForceArgs A)
                 const float r2 = dist2(x4[q], sx, sy, sz, ex, ey, ez);
                 if (r2 < kc.rc2) {
                     sur_add(acc, kc, ex, ey, ez, r2);
-                    if (LJ) lj_add(ex, ey, ez, r2);
+                    if (LJ) lj_add(ex, ey, ez, r2, t > 13 || (t == 13 && q > s));
                 }
             }
         }
@@ -247,7 +250,7 @@ __global__ void __launch_bounds__(SUR_BLOCK, 5) k_sur_desc(const SurForceArgs A)
         A.mol_ew[2 * s] = 0.5 * (double)lje;
         A.mol_ew[2 * s + 1] = 0.5 * (double)ljw;
         A.mol_cnt[2 * s] = lj_cand;
-        A.mol_cnt[2 * s + 1] = lj_visits;
+        A.mol_cnt[2 * s + 1] = lj_pairs;
     }
     // the invariants, streamed out eight at a time: raw FP32 (mode 1) or
     // normalised bfloat16 in 16-byte stores (mode 0)
