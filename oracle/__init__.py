@@ -268,7 +268,7 @@ def num_threads():
 
 # ---------------------------------------------------------------- surrogate
 
-SUR_ND, SUR_NH, SUR_NO, SUR_NV = 32, 64, 3, 9
+SUR_ND, SUR_NH, SUR_NO, SUR_NV = 32, 64, 16, 48
 SUR_NP = SUR_ND * SUR_NH + SUR_NH + SUR_NH * SUR_NH + SUR_NH + SUR_NH * SUR_NO + SUR_NO
 
 
@@ -286,7 +286,7 @@ def sur_fcut(r, rc):
 
 
 def sur_descriptors(prm, x, rows=None):
-    """Descriptors ``[nrows, 32]`` and vectors ``[nrows, 9]`` (v_0, v_1, v_2) of
+    """Descriptors ``[nrows, 32]`` and vectors ``[nrows, 48]`` (v_0 .. v_15) of
     the molecules ``rows`` (default all), brute force over all molecules."""
     x = _soa(x)
     n = x.shape[1]

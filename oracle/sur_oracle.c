@@ -19,9 +19,12 @@
  *   descriptors D = [G_0..G_15,
  *                    p_a . p_b for (a, b) = 00 01 02 03 11 12 13 22 23 33,
  *                    tr(T_a T_b) for (a, b) = 00 01 02 11 12 22];
- *   equivariant vectors v_m = p_m (m < 3);
+ *   equivariant vectors (16): v_m = p_m (m < 4) and v_{4 + 4a + b} = T_a p_b
+ *                     (a < 3, b < 4), the quadrupole channels applied to the
+ *                     vector channels (they carry the angular correlation of
+ *                     two neighbours that a triplet force depends on);
  *   MLP: xn = (D - mean) / scale, h1 = silu(xn W1 + b1), h2 = silu(h1 W2 + b2),
- *        w = h2 W3 + b3, silu(z) = z / (1 + exp(-z));
+ *        w = h2 W3 + b3 (16 outputs), silu(z) = z / (1 + exp(-z));
  *   force F_i = sum_m w_m v_m.
  *
  * Everything is FP64 and written for reading, not speed.
@@ -115,8 +118,16 @@ int orc_sur_descriptors(const double* prm, const double* x, int64_t n, const int
                 for (int t = 0; t < 3; t++) tr += T[TA[e]][s][t] * T[TB[e]][t][s];
             Dq[26 + e] = tr;
         }
-        for (int m = 0; m < 3; m++)
-            for (int k = 0; k < 3; k++) V[q * SUR_NV + 3 * m + k] = p[m][k];
+        double* Vq = V + q * SUR_NV;
+        for (int m = 0; m < 4; m++)
+            for (int k = 0; k < 3; k++) Vq[3 * m + k] = p[m][k];
+        for (int a = 0; a < 3; a++)
+            for (int b = 0; b < 4; b++)
+                for (int k = 0; k < 3; k++) {
+                    double tp = 0.0;
+                    for (int t = 0; t < 3; t++) tp += T[a][k][t] * p[b][t];
+                    Vq[3 * (4 + 4 * a + b) + k] = tp;
+                }
     }
     return 0;
 }
@@ -184,7 +195,7 @@ void orc_sur_mlp(const double* P, const double* mean, const double* scale, int64
 {
     double xn[SUR_ND], z1[SUR_NH], h1[SUR_NH], z2[SUR_NH], h2[SUR_NH];
     for (int64_t i = 0; i < n; i++) {
-        double* wi = w + 3 * i;
+        double* wi = w + SUR_NO * i;
         forward_row(P, mean, scale, D + i * SUR_ND, bf16, xn, z1, h1, z2, h2, wi);
         for (int c = 0; c < 3; c++) {
             double f = 0.0;

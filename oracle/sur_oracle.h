@@ -5,12 +5,14 @@
  * The surrogate is not part of the paper; it replaces the ATM triplet sum of
  * Section 2 (Eq. atm / Eq. forcepairs) by a per-molecule model:
  *   descriptors D_i (32 rotation invariants of the neighbourhood r < r_c),
- *   three equivariant vectors v_m(i) = sum_j phi_m(r_ij) rhat_ij,
- *   an MLP 32 -> 64 -> 64 -> 3 (SiLU) giving weights w_m(i),
+ *   16 equivariant vectors v_m(i): the four vector channels
+ *   p_a = sum_j phi_a(r_ij) rhat_ij and the twelve products T_a p_b of the
+ *   three quadrupole channels with them,
+ *   an MLP 32 -> 64 -> 64 -> 16 (SiLU) giving weights w_m(i),
  *   F_i = sum_m w_m(i) v_m(i).
  *
  * Parameter vector layout (SUR_NP doubles), all matrices row-major with the
- * input index first:  W1[32][64], b1[64], W2[64][64], b2[64], W3[64][3], b3[3].
+ * input index first:  W1[32][64], b1[64], W2[64][64], b2[64], W3[64][16], b3[16].
  */
 #ifndef SUR_ORACLE_H
 #define SUR_ORACLE_H
@@ -19,8 +21,8 @@
 
 #define SUR_ND 32
 #define SUR_NH 64
-#define SUR_NO 3
-#define SUR_NV 9
+#define SUR_NO 16
+#define SUR_NV 48
 #define SUR_NP (SUR_ND * SUR_NH + SUR_NH + SUR_NH * SUR_NH + SUR_NH + SUR_NH * SUR_NO + SUR_NO)
 
 #ifdef __cplusplus
@@ -34,7 +36,7 @@ void orc_sur_basis(double rc, double* mu_g, double* eta_g, double* mu_v, double*
 /* smooth cutoff 0.5 (cos(pi r / rc) + 1) for r < rc, else 0 */
 double orc_sur_fcut(double r, double rc);
 
-/* descriptors D[nrows][32] and vectors V[nrows][9] of the molecules rows[],
+/* descriptors D[nrows][32] and vectors V[nrows][48] of the molecules rows[],
  * by brute force over all other molecules (minimum image); prm as the ATM
  * oracle: [Lx, Ly, Lz, rc, ...]; x SoA [3][n].  Returns 0, or -1 if rc <= 0.8
  * or a box side is below 2 rc. */
@@ -45,7 +47,7 @@ int orc_sur_descriptors(const double* prm, const double* x, int64_t n, const int
 double orc_bf16(double x);
 
 /* MLP forward for n rows: normalised input xn = (D - mean) / scale, outputs
- * w[n][3] and F[n][3] = sum_m w_m v_m.  bf16 != 0 rounds xn, the three weight
+ * w[n][16] and F[n][3] = sum_m w_m v_m.  bf16 != 0 rounds xn, the three weight
  * matrices and the two hidden activations to bfloat16 (biases and sums stay
  * FP64). */
 void orc_sur_mlp(const double* P, const double* mean, const double* scale, int64_t n,

@@ -3,8 +3,10 @@ forms, symmetries, library routines and finite differences -- no GPU.
 
 The surrogate is defined in the oracle's header comment: 16 radial Gaussian
 channels and 16 angular invariants of the neighbourhood r < r_c with a cosine
-cutoff, three equivariant vectors v_m = sum_j phi_m(r) rhat, an MLP
-32 -> 64 -> 64 -> 3 (SiLU) and F_i = sum_m w_m v_m.
+cutoff, 16 equivariant vectors (the four vector channels
+p_a = sum_j phi_a(r) rhat and the products T_a p_b of the three quadrupole
+channels with them), an MLP 32 -> 64 -> 64 -> 16 (SiLU) and
+F_i = sum_m w_m v_m.
 """
 import math
 
@@ -76,8 +78,42 @@ def test_single_neighbour_closed_form():
         tpairs = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
         assert np.allclose(D[row, 26:], [2.0 / 3.0 * ph[a] * ph[b] for a, b in tpairs],
                            rtol=1e-13)
-        for m in range(3):
+        for m in range(4):
             assert np.allclose(V[row, 3 * m:3 * m + 3], sgn * ph[m] * u, rtol=1e-13, atol=1e-16)
+        # (uu^T - I/3) u = 2/3 u: T_a p_b = 2/3 phi_a phi_b u
+        for a in range(3):
+            for b in range(4):
+                m = 4 + 4 * a + b
+                assert np.allclose(V[row, 3 * m:3 * m + 3], sgn * 2.0 / 3.0 * ph[a] * ph[b] * u,
+                                   rtol=1e-13, atol=1e-16)
+
+
+def test_two_orthogonal_neighbours_quadrupole_products():
+    # neighbours at r1 along u1 and r2 along u2 (u1 . u2 = 0): with
+    # P_k = uk uk^T - I/3, P_1 u1 = 2/3 u1 and P_1 u2 = -u2/3, so
+    # T_a p_b = phi_a(r1) (2/3 phi_b(r1) u1 - 1/3 phi_b(r2) u2)
+    #         + phi_a(r2) (2/3 phi_b(r2) u2 - 1/3 phi_b(r1) u1)
+    L = 12.0
+    r1, r2 = 1.05, 1.9
+    u1 = np.array([2.0, 1.0, 2.0]) / 3.0
+    u2 = np.array([1.0, 2.0, -2.0]) / 3.0
+    assert abs(u1 @ u2) < 1e-15
+    x = np.zeros((3, 3))
+    x[:, 0] = [5.0, 5.0, 5.0]
+    x[:, 1] = x[:, 0] + r1 * u1
+    x[:, 2] = x[:, 0] + r2 * u2
+    _, V = oracle.sur_descriptors(_prm(L), x, rows=[0])
+    _, _, mu_v, eta_v = oracle.sur_basis(RC)
+    f1 = [_phi(r1, m, eta_v) for m in mu_v]
+    f2 = [_phi(r2, m, eta_v) for m in mu_v]
+    for b in range(4):
+        assert np.allclose(V[0, 3 * b:3 * b + 3], f1[b] * u1 + f2[b] * u2, rtol=1e-13)
+    for a in range(3):
+        for b in range(4):
+            m = 4 + 4 * a + b
+            expect = (f1[a] * (2.0 / 3.0 * f1[b] * u1 - f2[b] / 3.0 * u2)
+                      + f2[a] * (2.0 / 3.0 * f2[b] * u2 - f1[b] / 3.0 * u1))
+            assert np.allclose(V[0, 3 * m:3 * m + 3], expect, rtol=1e-12, atol=1e-16), (a, b)
 
 
 def test_beyond_cutoff_and_periodic_image():
@@ -144,7 +180,7 @@ def test_rotation_invariance_and_equivariance():
     xr = (q @ (x - c[:, None])) + c[:, None]
     D1, V1 = oracle.sur_descriptors(_prm(L), xr, rows=[0])
     assert np.allclose(D1, D0, rtol=1e-11, atol=1e-13)
-    for m in range(3):
+    for m in range(16):
         assert np.allclose(V1[0, 3 * m:3 * m + 3], q @ V0[0, 3 * m:3 * m + 3], atol=1e-12)
 
 
@@ -191,26 +227,27 @@ def _torch_mlp(P, mean, sd, D, V, bf16=False):
     b1 = P[2048:2112]
     W2 = P[2112:6208].reshape(64, 64)
     b2 = P[6208:6272]
-    W3 = P[6272:6464].reshape(64, 3)
-    b3 = P[6464:6467]
+    W3 = P[6272:7296].reshape(64, 16)
+    b3 = P[7296:7312]
     q = (lambda t: t.to(torch.bfloat16).to(torch.float64)) if bf16 else (lambda t: t)
     xn = q((torch.from_numpy(D) - torch.from_numpy(mean)) / torch.from_numpy(sd))
     h1 = q(torch.nn.functional.silu(xn @ q(W1) + b1))
     h2 = q(torch.nn.functional.silu(h1 @ q(W2) + b2))
     w = h2 @ q(W3) + b3
-    F = torch.einsum("nm,nmc->nc", w, torch.from_numpy(V).reshape(-1, 3, 3))
+    F = torch.einsum("nm,nmc->nc", w, torch.from_numpy(V).reshape(-1, 16, 3))
     return w.numpy(), F.numpy()
 
 
 def test_mlp_zero_weights_gives_bias_combination():
     rng = np.random.default_rng(4)
     P = np.zeros(oracle.SUR_NP)
-    P[6464:6467] = [0.5, -1.5, 2.0]
+    b3 = np.linspace(-1.5, 2.0, 16)
+    P[7296:7312] = b3
     D = rng.normal(size=(5, 32))
-    V = rng.normal(size=(5, 9))
+    V = rng.normal(size=(5, 48))
     w, F = oracle.sur_mlp(P, np.zeros(32), np.ones(32), D, V)
-    assert np.allclose(w, [[0.5, -1.5, 2.0]] * 5, atol=0)
-    expect = 0.5 * V[:, 0:3] - 1.5 * V[:, 3:6] + 2.0 * V[:, 6:9]
+    assert np.allclose(w, [b3] * 5, atol=0)
+    expect = sum(b3[m] * V[:, 3 * m:3 * m + 3] for m in range(16))
     assert np.allclose(F, expect, rtol=1e-15, atol=1e-15)
 
 
@@ -221,23 +258,23 @@ def test_mlp_single_path_closed_form():
     P = np.zeros(oracle.SUR_NP)
     P[0 * 64 + 0] = 1.0                 # W1[0][0]
     P[2112 + 0 * 64 + 0] = 1.0 / s1     # W2[0][0]
-    P[6272 + 0 * 3 + 0] = 2.0           # W3[0][0]
-    P[6272 + 0 * 3 + 2] = -3.0          # W3[0][2]
-    P[6464 + 1] = 0.25                  # b3[1]
+    P[6272 + 0 * 16 + 0] = 2.0          # W3[0][0]
+    P[6272 + 0 * 16 + 2] = -3.0         # W3[0][2]
+    P[7296 + 1] = 0.25                  # b3[1]
     mean = np.full(32, 0.5)
     sd = np.full(32, 2.0)
     D = np.full((1, 32), 0.5)
     D[0, 0] = 2.5                       # xn_0 = (2.5 - 0.5) / 2 = 1
-    V = np.arange(9, dtype=np.float64).reshape(1, 9)
+    V = np.arange(48, dtype=np.float64).reshape(1, 48)
     w, F = oracle.sur_mlp(P, mean, sd, D, V)
-    assert np.allclose(w[0], [2.0 * s1, 0.25, -3.0 * s1], rtol=1e-15, atol=1e-16)
+    assert np.allclose(w[0], [2.0 * s1, 0.25, -3.0 * s1] + [0.0] * 13, rtol=1e-15, atol=1e-16)
 
 
 def test_mlp_matches_torch_layers():
     rng = np.random.default_rng(5)
     P, mean, sd = _random_model(rng)
     D = rng.normal(size=(64, 32)) * sd + mean
-    V = rng.normal(size=(64, 9))
+    V = rng.normal(size=(64, 48))
     w, F = oracle.sur_mlp(P, mean, sd, D, V)
     wt, Ft = _torch_mlp(P, mean, sd, D, V)
     assert np.allclose(w, wt, rtol=1e-12, atol=1e-12)
@@ -248,7 +285,7 @@ def test_mlp_bf16_matches_torch_rounding():
     rng = np.random.default_rng(6)
     P, mean, sd = _random_model(rng)
     D = rng.normal(size=(256, 32)) * sd + mean
-    V = rng.normal(size=(256, 9))
+    V = rng.normal(size=(256, 48))
     w, F = oracle.sur_mlp(P, mean, sd, D, V, bf16_=True)
     wt, Ft = _torch_mlp(P, mean, sd, D, V, bf16=True)
     # torch rounds float64 -> bfloat16 directly as the oracle does; rows agree
@@ -266,9 +303,9 @@ def test_mlp_equivariance():
     rng = np.random.default_rng(7)
     P, mean, sd = _random_model(rng)
     D = rng.normal(size=(16, 32))
-    V = rng.normal(size=(16, 9))
+    V = rng.normal(size=(16, 48))
     q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
-    Vr = np.einsum("ij,nmj->nmi", q, V.reshape(16, 3, 3)).reshape(16, 9)
+    Vr = np.einsum("ij,nmj->nmi", q, V.reshape(16, 16, 3)).reshape(16, 48)
     _, F = oracle.sur_mlp(P, mean, sd, D, V)
     _, Fr = oracle.sur_mlp(P, mean, sd, D, Vr)
     assert np.allclose(Fr, F @ q.T, atol=1e-12)
@@ -279,7 +316,7 @@ def test_mlp_equivariance():
 def _problem(rng, n=24):
     P, mean, sd = _random_model(rng)
     D = rng.normal(size=(n, 32)) * sd + mean
-    V = rng.normal(size=(n, 9))
+    V = rng.normal(size=(n, 48))
     Fref = rng.normal(size=(n, 3))
     return P, mean, sd, D, V, Fref
 
@@ -303,7 +340,7 @@ def test_gradient_matches_finite_differences():
     L, g = oracle.sur_loss_grad(P, mean, sd, D, V, Fref, 1.3)
     idx = np.concatenate([rng.choice(2048, 12, replace=False), 2048 + np.arange(4),
                           2112 + rng.choice(4096, 12, replace=False), 6208 + np.arange(4),
-                          6272 + rng.choice(192, 8, replace=False), [6464, 6465, 6466]])
+                          6272 + rng.choice(1024, 8, replace=False), [7296, 7301, 7311]])
     h = 1e-5
     # truncation error O(h^2), rounding error about eps L / h
     round_tol = 8 * np.finfo(float).eps * L / h
@@ -325,12 +362,12 @@ def test_gradient_matches_torch_autograd():
     Pt = torch.from_numpy(P.copy()).requires_grad_(True)
     W1 = Pt[0:2048].reshape(32, 64)
     W2 = Pt[2112:6208].reshape(64, 64)
-    W3 = Pt[6272:6464].reshape(64, 3)
+    W3 = Pt[6272:7296].reshape(64, 16)
     xn = (torch.from_numpy(D) - torch.from_numpy(mean)) / torch.from_numpy(sd)
     h1 = torch.nn.functional.silu(xn @ W1 + Pt[2048:2112])
     h2 = torch.nn.functional.silu(h1 @ W2 + Pt[6208:6272])
-    w = h2 @ W3 + Pt[6464:6467]
-    F = torch.einsum("nm,nmc->nc", w, torch.from_numpy(V).reshape(-1, 3, 3))
+    w = h2 @ W3 + Pt[7296:7312]
+    F = torch.einsum("nm,nmc->nc", w, torch.from_numpy(V).reshape(-1, 16, 3))
     Lt = ((F - torch.from_numpy(Fref)) ** 2).sum() / (3 * len(D) * 0.9)
     Lt.backward()
     assert abs(Lt.item() - L) < 1e-12 * L
