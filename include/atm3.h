@@ -370,13 +370,15 @@ atm_status atm_compute_forces_noalloc(const atm_params* params, int64_t n, const
  *               d_g = (r_c - 0.8) / 15, eta_g = 1 / (2 d_g^2);
  *   phi_a     = exp(-eta_v (r - nu_a)^2) f_c, nu_a = 0.8 + (a + 1/2) d_v,
  *               d_v = (r_c - 0.8) / 4, eta_v = 1 / (2 d_v^2), a = 0..3;
- *   p_a       = sum_j phi_a rhat, T_a = sum_j phi_a (rhat rhat^T - I/3);
+ *   p_a       = sum_j phi_a rhat, T_a = sum_j phi_a (rhat rhat^T - I/3) (a < 3);
  *   D[16..25] = p_a . p_b for ab = 00 01 02 03 11 12 13 22 23 33;
  *   D[26..31] = tr(T_a T_b) for ab = 00 01 02 11 12 22;
- *   w = W3^T silu(W2^T silu(W1^T xn + b1) + b2) + b3, xn = (D - mean) / scale;
- *   F_i = w_0 p_0 + w_1 p_1 + w_2 p_2.
+ *   vectors   v_m = p_m (m < 4), v_{4 + 4a + b} = T_a p_b (a < 3, b < 4);
+ *   w = W3^T silu(W2^T silu(W1^T xn + b1) + b2) + b3 (16 outputs),
+ *   xn = (D - mean) / scale;
+ *   F_i = sum_m w_m v_m.
  * Parameters: ATM_SUR_NPARAM floats laid out W1[32][64], b1[64], W2[64][64],
- * b2[64], W3[64][3], b3[3] (row-major, input index first), plus mean[32] and
+ * b2[64], W3[64][16], b3[16] (row-major, input index first), plus mean[32] and
  * scale[32] (> 0).  Inference: inputs, weights and the two hidden layers in
  * bfloat16 on the tensor cores, FP32 sums.  Training: FP32 master weights;
  * gradients by default on the tensor cores (the inference arithmetic forward,
@@ -387,12 +389,13 @@ atm_status atm_compute_forces_noalloc(const atm_params* params, int64_t n, const
  *   L = sum_i |F_i - F_i^ref|^2 / (3 B sigma2)
  * over a minibatch of B rows, sigma2 = mean squared target force component of
  * the data set (L = 1 for the zero model).
- * Descriptor / vector rows are float [rows][32] and [rows][9] (p_0, p_1, p_2),
+ * Descriptor / vector rows are float [rows][32] and [rows][48] (v_0 .. v_15),
  * targets float [rows][3]; all host arrays, caller-owned.
  * ------------------------------------------------------------------------ */
 #define ATM_SUR_NDESC 32
-#define ATM_SUR_NVEC 9
-#define ATM_SUR_NPARAM 6467
+#define ATM_SUR_NVEC 48
+#define ATM_SUR_NOUT 16
+#define ATM_SUR_NPARAM 7312
 
 /* Set / get the model.  set_model copies (and validates: finite, scale > 0)
  * the parameters and resets the Adam state.  get_model accepts NULL for any
@@ -417,7 +420,7 @@ atm_status atm_surrogate_load(atm_ctx* ctx, const char* path);
  * order), computed by the same kernel as the inference.  STATE without cells. */
 atm_status atm_surrogate_descriptors(atm_ctx* ctx, float* desc, float* vec);
 
-/* Inference on given rows (no neighbour search): w[rows][3] and
+/* Inference on given rows (no neighbour search): w[rows][16] and
  * force[rows][3] = sum_m w_m vec_m.  STATE without a model. */
 atm_status atm_surrogate_mlp(atm_ctx* ctx, int64_t rows, const float* desc, const float* vec,
                              float* w, float* force);

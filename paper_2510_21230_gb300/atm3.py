@@ -40,7 +40,7 @@ EXPORTED = ["atm_abi_version", "atm_create", "atm_batch_create", "atm_batch_size
             "atm_set_unit_classes", "atm_batch_cells", "atm_cell_grid", "atm_set_deterministic",
             "atm_surrogate_training_arithmetic", "atm_set_owned_layers"]
 
-SUR_NDESC, SUR_NVEC, SUR_NPARAM = 32, 9, 6467
+SUR_NDESC, SUR_NVEC, SUR_NOUT, SUR_NPARAM = 32, 48, 16, 7312
 
 
 class Params(ctypes.Structure):
@@ -436,7 +436,7 @@ class AtmSystem:
         self._check(self._lib.atm_surrogate_load(self._ctx, os.fsencode(path)))
 
     def surrogate_descriptors(self):
-        """Descriptors ``[n, 32]`` and vectors ``[n, 9]`` (float32, original order)."""
+        """Descriptors ``[n, 32]`` and vectors ``[n, 48]`` (float32, original order)."""
         D = np.zeros((self.n, SUR_NDESC), dtype=np.float32)
         V = np.zeros((self.n, SUR_NVEC), dtype=np.float32)
         self._check(self._lib.atm_surrogate_descriptors(self._ctx, _host_ptr(D), _host_ptr(V)))
@@ -447,7 +447,7 @@ class AtmSystem:
         D = np.ascontiguousarray(D, dtype=np.float32).reshape(-1, SUR_NDESC)
         V = np.ascontiguousarray(V, dtype=np.float32).reshape(-1, SUR_NVEC)
         n = D.shape[0]
-        w = np.zeros((n, 3), dtype=np.float32)
+        w = np.zeros((n, SUR_NOUT), dtype=np.float32)
         F = np.zeros((n, 3), dtype=np.float32)
         self._check(self._lib.atm_surrogate_mlp(self._ctx, n, _host_ptr(D), _host_ptr(V),
                                               _host_ptr(w), _host_ptr(F)))

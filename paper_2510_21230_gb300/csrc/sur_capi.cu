@@ -416,9 +416,10 @@ extern "C" atm_status atm_surrogate_mlp(atm_ctx* c, int64_t rows, const float* d
     if (rows == 0) return ATM_OK;
     CU(cudaSetDevice(c->device));
     const size_t n = (size_t)rows;
-    const size_t bd = al256(n * SUR_ND * 4), bv = al256(n * SUR_NV * 4), bw = al256(n * 3 * 4);
+    const size_t bd = al256(n * SUR_ND * 4), bv = al256(n * SUR_NV * 4),
+                 bw = al256(n * SUR_NO * 4), bf = al256(n * 3 * 4);
     void* buf = nullptr;
-    atm_status s = stage(c, S, bd + bv + 2 * bw, &buf);
+    atm_status s = stage(c, S, bd + bv + bw + bf, &buf);
     if (s != ATM_OK) return s;
     char* b = static_cast<char*>(buf);
     float* dD = reinterpret_cast<float*>(b);
@@ -429,7 +430,7 @@ extern "C" atm_status atm_surrogate_mlp(atm_ctx* c, int64_t rows, const float* d
     CU(cudaMemcpyAsync(dV, vec, n * SUR_NV * 4, cudaMemcpyHostToDevice, c->st));
     CU(launch_sur_mlp_rows(rows, dD, dV, S->packed, dW, dF, c->d_status, c->sms, c->st));
     c->n_launch += 1;
-    CU(cudaMemcpyAsync(w, dW, n * 3 * 4, cudaMemcpyDeviceToHost, c->st));
+    CU(cudaMemcpyAsync(w, dW, n * SUR_NO * 4, cudaMemcpyDeviceToHost, c->st));
     CU(cudaMemcpyAsync(force, dF, n * 3 * 4, cudaMemcpyDeviceToHost, c->st));
     return ctx_sync_and_check(c);
 }

@@ -296,13 +296,30 @@ __global__ void __launch_bounds__(SUR_BLOCK, 5) k_sur_desc(const SurForceArgs A)
             put(e++, acc.T[m][0] * acc.T[b][0] + acc.T[m][1] * acc.T[b][1] + acc.T[m][2] * acc.T[b][2] +
                          2.0f * (acc.T[m][3] * acc.T[b][3] + acc.T[m][4] * acc.T[b][4] +
                                  acc.T[m][5] * acc.T[b][5]));
-    float* v = collect ? A.v_out + row * SUR_NV : A.vb + s * SUR_NV;
+    // the 16 equivariant vectors: p_0..p_3, then T_a p_b (a < 3, b < 4) with
+    // T stored as (xx, yy, zz, xy, xz, yz); twelve 16-byte stores of a row
+    float vv[SUR_NV];
 #pragma unroll
-    for (int m = 0; m < 3; m++) {
-        v[3 * m] = acc.p[m][0];
-        v[3 * m + 1] = acc.p[m][1];
-        v[3 * m + 2] = acc.p[m][2];
+    for (int m = 0; m < 4; m++) {
+        vv[3 * m] = acc.p[m][0];
+        vv[3 * m + 1] = acc.p[m][1];
+        vv[3 * m + 2] = acc.p[m][2];
     }
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = 0; b < 4; b++) {
+            const float* T = acc.T[a];
+            const float* p = acc.p[b];
+            const int m = 4 + 4 * a + b;
+            vv[3 * m] = T[0] * p[0] + T[3] * p[1] + T[4] * p[2];
+            vv[3 * m + 1] = T[3] * p[0] + T[1] * p[1] + T[5] * p[2];
+            vv[3 * m + 2] = T[4] * p[0] + T[5] * p[1] + T[2] * p[2];
+        }
+    float4* v4 = reinterpret_cast<float4*>(collect ? A.v_out + row * SUR_NV : A.vb + s * SUR_NV);
+#pragma unroll
+    for (int q = 0; q < SUR_NV / 4; q++)
+        v4[q] = make_float4(vv[4 * q], vv[4 * q + 1], vv[4 * q + 2], vv[4 * q + 3]);
     if (collect) {
         float* t = A.t_out + row * 3;
         t[0] = (float)A.f_atm[s];
@@ -315,7 +332,7 @@ __global__ void __launch_bounds__(SUR_BLOCK, 5) k_sur_desc(const SurForceArgs A)
 
 constexpr int GH = 65;                 // row stride of the 64-wide FP32 tiles
 constexpr int GX = 33;                 // row stride of the input tile
-constexpr int SUR_NP_PAD = 6468;
+constexpr int SUR_NP_PAD = (SUR_NP + 3) & ~3;
 
 struct GradSmem {
     static constexpr int P = 0;
@@ -327,8 +344,8 @@ struct GradSmem {
     static constexpr int S2 = H2 + SUR_TILE * GH;       // silu'(z2), then dL/dz2
     static constexpr int V = S2 + SUR_TILE * GH;
     static constexpr int T = V + SUR_TILE * SUR_NV;
-    static constexpr int W = T + SUR_TILE * 3;          // outputs w, then dL/dw
-    static constexpr int END = W + SUR_TILE * 4;
+    static constexpr int W = T + SUR_TILE * 3;          // outputs w, then dL/dw [i][SUR_NO]
+    static constexpr int END = W + SUR_TILE * SUR_NO;
 };
 constexpr size_t SUR_GRAD_SMEM = GradSmem::END * sizeof(float) + SUR_TILE * sizeof(double);
 
@@ -438,30 +455,31 @@ __global__ void __launch_bounds__(SUR_GRAD_THREADS) k_sur_grad(const SurGradArgs
     }
     __syncthreads();
     // outputs w = H2 W3 + b3
-    if (tid < SUR_TILE * SUR_NO) {
-        const int i = tid / SUR_NO, m = tid % SUR_NO;
+    for (int e = tid; e < SUR_TILE * SUR_NO; e += SUR_GRAD_THREADS) {
+        const int i = e / SUR_NO, m = e % SUR_NO;
         float acc = P[SUR_OFF_B3 + m];
         for (int k = 0; k < SUR_NH; k++) acc = fmaf(H2[i * GH + k], P[SUR_OFF_W3 + k * SUR_NO + m], acc);
-        Wt[i * 4 + m] = acc;
+        Wt[i * SUR_NO + m] = acc;
     }
     __syncthreads();
     // residuals, loss and dL/dw (padding rows have V = T = 0: no contribution)
     if (tid < SUR_TILE) {
         const int i = tid;
         const float* v = Vs + i * SUR_NV;
-        const float w0 = Wt[i * 4], w1 = Wt[i * 4 + 1], w2 = Wt[i * 4 + 2];
+        const float* wi = Wt + i * SUR_NO;
         float r[3];
         double l = 0.0;
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-            r[c] = (w0 * v[c] + w1 * v[3 + c] + w2 * v[6 + c]) - Ts[i * 3 + c];
+            float fc = 0.0f;
+            for (int m = 0; m < SUR_NO; m++) fc = fmaf(wi[m], v[3 * m + c], fc);
+            r[c] = fc - Ts[i * 3 + c];
             l += (double)r[c] * (double)r[c];
         }
         Ls[i] = l * (double)A.norm;
         const float two_norm = 2.0f * A.norm;
-#pragma unroll
-        for (int m = 0; m < 3; m++)
-            Wt[i * 4 + m] = two_norm * (r[0] * v[3 * m] + r[1] * v[3 * m + 1] + r[2] * v[3 * m + 2]);
+        for (int m = 0; m < SUR_NO; m++)
+            Wt[i * SUR_NO + m] = two_norm * (r[0] * v[3 * m] + r[1] * v[3 * m + 1] + r[2] * v[3 * m + 2]);
     }
     __syncthreads();
     float* G = A.part + (long long)blockIdx.x * SUR_NP;
@@ -471,24 +489,26 @@ __global__ void __launch_bounds__(SUR_GRAD_THREADS) k_sur_grad(const SurGradArgs
         A.part_loss[blockIdx.x] = l;
     }
     // output layer gradient; dL/dz2 = silu'(z2) * (W3 dL/dw)
-    if (tid < SUR_NH * SUR_NO) {
-        const int k = tid / SUR_NO, m = tid % SUR_NO;
-        float acc = 0.0f;
-        for (int i = 0; i < SUR_TILE; i++) acc = fmaf(H2[i * GH + k], Wt[i * 4 + m], acc);
-        G[SUR_OFF_W3 + k * SUR_NO + m] = acc;
-    } else if (tid < SUR_NH * SUR_NO + SUR_NO) {
-        const int m = tid - SUR_NH * SUR_NO;
-        float acc = 0.0f;
-        for (int i = 0; i < SUR_TILE; i++) acc += Wt[i * 4 + m];
-        G[SUR_OFF_B3 + m] = acc;
+    for (int e = tid; e < SUR_NH * SUR_NO + SUR_NO; e += SUR_GRAD_THREADS) {
+        if (e < SUR_NH * SUR_NO) {
+            const int k = e / SUR_NO, m = e % SUR_NO;
+            float acc = 0.0f;
+            for (int i = 0; i < SUR_TILE; i++) acc = fmaf(H2[i * GH + k], Wt[i * SUR_NO + m], acc);
+            G[SUR_OFF_W3 + k * SUR_NO + m] = acc;
+        } else {
+            const int m = e - SUR_NH * SUR_NO;
+            float acc = 0.0f;
+            for (int i = 0; i < SUR_TILE; i++) acc += Wt[i * SUR_NO + m];
+            G[SUR_OFF_B3 + m] = acc;
+        }
     }
 #pragma unroll
     for (int r = 0; r < 4; r++)
 #pragma unroll
         for (int c = 0; c < 4; c++) {
             const int i = rg + r, k = cg + 16 * c;
-            const float dh = P[SUR_OFF_W3 + k * 3] * Wt[i * 4] + P[SUR_OFF_W3 + k * 3 + 1] * Wt[i * 4 + 1] +
-                             P[SUR_OFF_W3 + k * 3 + 2] * Wt[i * 4 + 2];
+            float dh = 0.0f;
+            for (int m = 0; m < SUR_NO; m++) dh = fmaf(P[SUR_OFF_W3 + k * SUR_NO + m], Wt[i * SUR_NO + m], dh);
             S2[i * GH + k] *= dh;
         }
     __syncthreads();

@@ -3,9 +3,10 @@
 // shared memory and FP32 accumulators in tensor memory (TMEM).
 //
 // A persistent CTA of 128 threads takes 128-row tiles.  The input tile (stored
-// by the descriptor kernel already in the operand layout) and its vectors
-// arrive by bulk asynchronous copies (cp.async.bulk on the TMA engine) issued
-// one tile ahead, completing on an mbarrier.  Thread t owns row t: after each
+// by the descriptor kernel already in the operand layout) arrives by a bulk
+// asynchronous copy (cp.async.bulk on the TMA engine) issued one tile ahead,
+// completing on an mbarrier; each thread reads its row's 16 vectors from
+// global memory (L2, where the descriptor kernel left them) in the epilogue.  Thread t owns row t: after each
 // layer it reads
 // the row's accumulators back from TMEM lane t (tcgen05.ld 32x32b), applies
 // bias + SiLU and writes the next layer's operand row -- no shuffles, no
@@ -38,10 +39,9 @@ static_assert(TC_M == SUR_TILE_M && TC_LBO == 128, "the tile layout is the opera
 struct TcSmem {
     alignas(128) unsigned char w1[64 * 32 * 2];   // W1^T  N 64 x K 32
     alignas(128) unsigned char w2[64 * 64 * 2];   // W2^T  N 64 x K 64
-    alignas(128) unsigned char w3[16 * 64 * 2];   // W3^T  N 16 (rows 3..15 zero) x K 64
+    alignas(128) unsigned char w3[16 * 64 * 2];   // W3^T  N 16 x K 64
     alignas(128) unsigned char x[TC_M * 32 * 2];  // input tile   M 128 x K 32
     alignas(128) unsigned char h[TC_M * 64 * 2];  // hidden tile  M 128 x K 64
-    alignas(16) float v[TC_M * SUR_NV];           // vectors of the tile's rows
     float b1[64], b2[64], b3[16];
     alignas(8) unsigned long long mbar;           // MMA completion
     alignas(8) unsigned long long xbar;           // bulk-copy completion
@@ -49,7 +49,6 @@ struct TcSmem {
 };
 
 constexpr uint32_t TC_X_BYTES = TC_M * 32 * 2;
-constexpr uint32_t TC_V_BYTES = TC_M * SUR_NV * 4;
 
 template <bool BF16_IN>
 __global__ void __launch_bounds__(TC_M) k_sur_mlp_tc(long long n, const float* __restrict__ Din,
@@ -73,13 +72,13 @@ __global__ void __launch_bounds__(TC_M) k_sur_mlp_tc(long long n, const float* _
     for (int e = tid; e < 16 * 8; e += TC_M) {
         const int r = e >> 3, j = e & 7;
         const uint4 z = make_uint4(0u, 0u, 0u, 0u);
-        put_chunk(S.w3, r, j, 8, r < 8 ? *reinterpret_cast<const uint4*>(model->w3t + r * SUR_HS + 8 * j) : z);
+        put_chunk(S.w3, r, j, 8, r < SUR_NO ? *reinterpret_cast<const uint4*>(model->w3t + r * SUR_HS + 8 * j) : z);
     }
     if (tid < 64) {
         S.b1[tid] = model->b1[tid];
         S.b2[tid] = model->b2[tid];
     }
-    if (tid < 16) S.b3[tid] = tid < 8 ? model->b3[tid] : 0.0f;
+    if (tid < 16) S.b3[tid] = tid < SUR_NO ? model->b3[tid] : 0.0f;
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.mbar)) : "memory");
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.xbar)) : "memory");
@@ -113,15 +112,13 @@ __global__ void __launch_bounds__(TC_M) k_sur_mlp_tc(long long n, const float* _
         wait_bar(&S.mbar, phase);
         tc_fence_after();
     };
-    // the next tile's inputs: one bulk copy each for the X tile and its vectors
+    // the next tile's inputs: one bulk copy of the X tile
     auto prefetch = [&](long long tile) {
         if (tid == 0) {
-            fence_async_smem();  // earlier generic reads of S.v before the async writes
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&S.xbar)),
-                         "r"(TC_X_BYTES + TC_V_BYTES)
+                         "r"(TC_X_BYTES)
                          : "memory");
             bulk_g2s(S.x, Xin + tile * (TC_M * SUR_ND), TC_X_BYTES, &S.xbar);
-            bulk_g2s(S.v, Vin + tile * (TC_M * SUR_NV), TC_V_BYTES, &S.xbar);
         }
     };
     // bias + SiLU of 64 accumulator columns at TMEM column c0, written as row
@@ -148,12 +145,9 @@ __global__ void __launch_bounds__(TC_M) k_sur_mlp_tc(long long n, const float* _
     for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         const long long s = tile * TC_M + tid;
         const bool active = s < n;
-        float v9[SUR_NV];
         if (BF16_IN) {
             wait_bar(&S.xbar, xphase);
             if (!ok) break;
-#pragma unroll
-            for (int k = 0; k < SUR_NV; k++) v9[k] = S.v[tid * SUR_NV + k];
         } else {
 #pragma unroll
             for (int j = 0; j < 4; j++) {
@@ -167,8 +161,6 @@ __global__ void __launch_bounds__(TC_M) k_sur_mlp_tc(long long n, const float* _
                 }
                 put_chunk(S.x, tid, j, 4, make_uint4(p[0], p[1], p[2], p[3]));
             }
-#pragma unroll
-            for (int k = 0; k < SUR_NV; k++) v9[k] = active ? Vin[s * SUR_NV + k] : 0.0f;
             fence_async_smem();
             __syncthreads();
         }
@@ -184,7 +176,7 @@ __global__ void __launch_bounds__(TC_M) k_sur_mlp_tc(long long n, const float* _
         }
         wait_mma();
         if (!ok) break;
-        // the X tile and the vectors are consumed: fetch the next tile's meanwhile
+        // the X tile is consumed: fetch the next tile's meanwhile
         if (BF16_IN && tile + gridDim.x < ntiles) prefetch(tile + gridDim.x);
         hidden(0u, S.b1);
 
@@ -215,17 +207,22 @@ __global__ void __launch_bounds__(TC_M) k_sur_mlp_tc(long long n, const float* _
         float o[16];
         tmem_ld16(tmem + lane_base, o);
         if (active) {
-            const float w0 = o[0] + S.b3[0], w1 = o[1] + S.b3[1], w2 = o[2] + S.b3[2];
-            if (w) {
-                w[s * 3] = w0;
-                w[s * 3 + 1] = w1;
-                w[s * 3 + 2] = w2;
+            float wm[SUR_NO];
+#pragma unroll
+            for (int m = 0; m < SUR_NO; m++) {
+                wm[m] = o[m] + S.b3[m];
+                if (w) w[s * SUR_NO + m] = wm[m];
             }
+            const float* vrow = Vin + s * SUR_NV;
+            float fc[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+            for (int m = 0; m < SUR_NO; m++)
+#pragma unroll
+                for (int c = 0; c < 3; c++) fc[c] = fmaf(wm[m], vrow[3 * m + c], fc[c]);
 #pragma unroll
             for (int c = 0; c < 3; c++) {
-                const float fc = w0 * v9[c] + w1 * v9[3 + c] + w2 * v9[6 + c];
-                if (f) f[s * 3 + c] = fc;
-                if (f_soa) f_soa[c * n + s] = (double)fc;
+                if (f) f[s * 3 + c] = fc[c];
+                if (f_soa) f_soa[c * n + s] = (double)fc[c];
             }
         }
         tc_fence_before();

@@ -47,18 +47,18 @@ constexpr uint32_t SBO_K32 = 4 * 128, SBO_K64 = 8 * 128, SBO_K128 = 16 * 128;
 struct TrSmem {
     alignas(128) unsigned char w1t[64 * 32 * 2];    // B, layer 1: N 64 x K 32 (W1^T)
     alignas(128) unsigned char w2t[64 * 64 * 2];    // B, layer 2: N 64 x K 64 (W2^T)
-    alignas(128) unsigned char w3t[16 * 64 * 2];    // B, layer 3: N 16 x K 64 (W3^T, rows 3.. zero)
+    alignas(128) unsigned char w3t[16 * 64 * 2];    // B, layer 3: N 16 x K 64 (W3^T)
     alignas(128) unsigned char w2[64 * 64 * 2];     // B of dH1 = dZ2 W2^T: N 64 (k) x K 64 (j)
     alignas(128) unsigned char x[TR_M * 32 * 2];    // A, layer 1: M 128 x K 32
     alignas(128) unsigned char h[TR_M * 64 * 2];    // A: H1 (layer 2), H2 (layer 3), dZ2 (dH1)
     alignas(128) unsigned char xt[128 * TR_M * 2];  // A of dW1: rows q < 32 X^T, row 32 ones
     alignas(128) unsigned char h1t[128 * TR_M * 2]; // A of dW2: rows k < 64 H1^T, row 64 ones
     alignas(128) unsigned char h2t[128 * TR_M * 2]; // A of dW3: rows k < 64 H2^T, row 64 ones
-    alignas(128) unsigned char dyt[16 * TR_M * 2];  // B of dW3: N 16 (rows m < 3: dL/dw_m) x K samples
+    alignas(128) unsigned char dyt[16 * TR_M * 2];  // B of dW3: N 16 (dL/dw_m) x K samples
     alignas(128) unsigned char dz2t[64 * TR_M * 2]; // B of dW2: N 64 x K samples
     alignas(128) unsigned char dz1t[64 * TR_M * 2]; // B of dW1: N 64 x K samples
     float w3[SUR_NH * SUR_NO];                      // FP32 master W3
-    float b1[64], b2[64], b3[4];
+    float b1[64], b2[64], b3[SUR_NO];
     double lsum[TR_M / 32];
     alignas(8) unsigned long long mbar;
     uint32_t tmem_base;
@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(TR_M) k_sur_grad_tc(const SurGradArgs A)
     for (int e = tid; e < 16 * 8; e += TR_M) {
         const int r = e >> 3, j = e & 7;
         const uint4 z = make_uint4(0u, 0u, 0u, 0u);
-        put_chunk(S.w3t, r, j, 8, r < 8 ? *reinterpret_cast<const uint4*>(model->w3t + r * SUR_HS + 8 * j) : z);
+        put_chunk(S.w3t, r, j, 8, r < SUR_NO ? *reinterpret_cast<const uint4*>(model->w3t + r * SUR_HS + 8 * j) : z);
     }
     // W2 itself (row k holds W2[k][j], j contiguous) for dH1 = dZ2 W2^T
     for (int e = tid; e < SUR_NH * SUR_NH; e += TR_M)
@@ -109,9 +109,9 @@ __global__ void __launch_bounds__(TR_M) k_sur_grad_tc(const SurGradArgs A)
         S.b1[tid] = model->b1[tid];
         S.b2[tid] = model->b2[tid];
     }
-    if (tid < 4) S.b3[tid] = tid < 3 ? model->b3[tid] : 0.0f;
+    if (tid < SUR_NO) S.b3[tid] = model->b3[tid];
     {
-        // zero rows of the padded left operands (and of dY's rows 3..15)
+        // zero rows of the padded left operands
         const uint4 z = make_uint4(0u, 0u, 0u, 0u);
         for (int e = tid; e < (int)(sizeof(S.xt) / 16); e += TR_M) {
             reinterpret_cast<uint4*>(S.xt)[e] = z;
@@ -187,11 +187,10 @@ __global__ void __launch_bounds__(TR_M) k_sur_grad_tc(const SurGradArgs A)
 #pragma unroll
             for (int q = 0; q < SUR_ND; q++) put_bf(S.xt, q, tid, 16, xv[q]);
         }
-        float v9[SUR_NV], tg[3];
-#pragma unroll
-        for (int k = 0; k < SUR_NV; k++) v9[k] = active ? A.V[smp * SUR_NV + k] : 0.0f;
+        float tg[3];
 #pragma unroll
         for (int c = 0; c < 3; c++) tg[c] = active ? A.T[smp * 3 + c] : 0.0f;
+        const float* vrow = A.V + smp * SUR_NV;  // the sample's 16 vectors (read when active)
         publish();
 
         // ---- layer 1: TMEM [0, 64) = X W1
@@ -263,22 +262,27 @@ __global__ void __launch_bounds__(TR_M) k_sur_grad_tc(const SurGradArgs A)
         wait_mma();
         if (!ok) break;
         double loss = 0.0;
-        float dy[3];
+        float dy[SUR_NO];
         {
             float o[16];
             tmem_ld16(lane + 128, o);
-            const float w0 = o[0] + S.b3[0], w1 = o[1] + S.b3[1], w2 = o[2] + S.b3[2];
             float r[3];
 #pragma unroll
             for (int c = 0; c < 3; c++) {
-                r[c] = (w0 * v9[c] + w1 * v9[3 + c] + w2 * v9[6 + c]) - tg[c];
+                float fc = 0.0f;
+                if (active)
+#pragma unroll
+                    for (int m = 0; m < SUR_NO; m++) fc = fmaf(o[m] + S.b3[m], vrow[3 * m + c], fc);
+                r[c] = fc - tg[c];
                 loss += (double)r[c] * (double)r[c];
             }
             loss *= (double)A.norm;
             const float two_norm = 2.0f * A.norm;
 #pragma unroll
-            for (int m = 0; m < 3; m++) {
-                dy[m] = two_norm * (r[0] * v9[3 * m] + r[1] * v9[3 * m + 1] + r[2] * v9[3 * m + 2]);
+            for (int m = 0; m < SUR_NO; m++) {
+                dy[m] = active ? two_norm * (r[0] * vrow[3 * m] + r[1] * vrow[3 * m + 1] +
+                                             r[2] * vrow[3 * m + 2])
+                               : 0.0f;
                 put_bf(S.dyt, m, tid, 16, dy[m]);
             }
         }
@@ -291,7 +295,9 @@ __global__ void __launch_bounds__(TR_M) k_sur_grad_tc(const SurGradArgs A)
 #pragma unroll
             for (int i = 0; i < 16; i++) {
                 const int k = 16 * q + i;
-                const float dh = dy[0] * S.w3[3 * k] + dy[1] * S.w3[3 * k + 1] + dy[2] * S.w3[3 * k + 2];
+                float dh = 0.0f;
+#pragma unroll
+                for (int m = 0; m < SUR_NO; m++) dh = fmaf(dy[m], S.w3[SUR_NO * k + m], dh);
                 dz[i] = dh * s2[i];
                 put_bf(S.dz2t, k, tid, 16, dz[i]);
             }

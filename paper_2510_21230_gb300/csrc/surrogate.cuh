@@ -26,15 +26,15 @@ namespace atm3 {
 
 constexpr int SUR_ND = 32;   // descriptors
 constexpr int SUR_NH = 64;   // hidden width
-constexpr int SUR_NO = 3;    // outputs (weights of the three vectors)
-constexpr int SUR_NV = 9;    // three 3-vectors
+constexpr int SUR_NO = 16;   // outputs (weights of the 16 vectors)
+constexpr int SUR_NV = 48;   // 16 3-vectors: p_0..p_3, then T_a p_b (a < 3, b < 4)
 constexpr int SUR_OFF_W1 = 0;
 constexpr int SUR_OFF_B1 = SUR_OFF_W1 + SUR_ND * SUR_NH;
 constexpr int SUR_OFF_W2 = SUR_OFF_B1 + SUR_NH;
 constexpr int SUR_OFF_B2 = SUR_OFF_W2 + SUR_NH * SUR_NH;
 constexpr int SUR_OFF_W3 = SUR_OFF_B2 + SUR_NH;
 constexpr int SUR_OFF_B3 = SUR_OFF_W3 + SUR_NH * SUR_NO;
-constexpr int SUR_NP = SUR_OFF_B3 + SUR_NO;  // 6467
+constexpr int SUR_NP = SUR_OFF_B3 + SUR_NO;  // 7312
 
 // row strides (bf16 elements) of the packed weight rows: 16-byte multiples,
 // so the tensor-core kernel stages them in 16-byte chunks
@@ -42,13 +42,13 @@ constexpr int SUR_XS = 40;   // K = 32 rows
 constexpr int SUR_HS = 72;   // K = 64 rows
 
 // Inference weights in bfloat16, n-major with k contiguous (row n holds the
-// weights into output n), padded rows; W3 padded to 8 outputs (rows 3..7
-// zero); FP32 biases and the descriptor normalisation.
+// weights into output n), padded rows; FP32 biases and the descriptor
+// normalisation.
 struct SurPacked {
     __nv_bfloat16 w1t[SUR_NH * SUR_XS];
     __nv_bfloat16 w2t[SUR_NH * SUR_HS];
-    __nv_bfloat16 w3t[8 * SUR_HS];
-    float b1[SUR_NH], b2[SUR_NH], b3[8];
+    __nv_bfloat16 w3t[SUR_NO * SUR_HS];
+    float b1[SUR_NH], b2[SUR_NH], b3[SUR_NO];
     float mean[SUR_ND], scale[SUR_ND];
 };
 static_assert(sizeof(SurPacked) % 16 == 0, "SurPacked is copied in 16-byte pieces");

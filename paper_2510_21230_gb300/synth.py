@@ -177,7 +177,7 @@ def config(name):
 
 # ------------------------------------------------- surrogate test inputs
 
-SUR_NDESC, SUR_NVEC, SUR_NPARAM = 32, 9, 6467
+SUR_NDESC, SUR_NVEC, SUR_NOUT, SUR_NPARAM = 32, 48, 16, 7312
 
 
 def sur_params(seed, wscale=0.3):

@@ -179,7 +179,7 @@ def test_batch_surrogate_equals_separate(atm3):
 # ------------------------------------------------------------------- training
 
 # parameter blocks of the flat parameter vector: W1, b1, W2, b2, W3, b3
-BLOCKS = [(0, 2048), (2048, 2112), (2112, 6208), (6208, 6272), (6272, 6464), (6464, 6467)]
+BLOCKS = [(0, 2048), (2048, 2112), (2112, 6208), (6208, 6272), (6272, 7296), (7296, 7312)]
 
 
 @pytest.mark.parametrize("rows", [64, 300, 2049])
