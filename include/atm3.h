@@ -220,7 +220,9 @@ atm_status atm_get_results(atm_ctx* ctx, atm_result* out);
  * default).  graph = 1: atm_step captures one step in a CUDA graph (on a
  * stream of its own) and replays it, with no host synchronisation between
  * steps; the graph sizes the kernels for the current largest unit plus
- * headroom, and a step that outgrows it is detected on the device, after
+ * headroom (at most a quarter of it, the largest amount that keeps the
+ * resident CTAs per SM of the current size, else 4 molecules), and a step
+ * that outgrows it is detected on the device, after
  * which the run is restarted from its initial state without the graph.
  * Options reset any autotuned choice.  Errors: INVALID. */
 atm_status atm_set_options(atm_ctx* ctx, int persistent, int nwarps, int graph);

@@ -724,22 +724,45 @@ static atm_status enqueue_step(atm_ctx* c, int trav, int trunc, int prec, int mc
     return ATM_OK;
 }
 
-// staged-molecule capacity of a graph: the current largest unit plus headroom
-// for molecules moving between cells during the steps the graph replays
-static int graph_mcap(const atm_ctx* c, int trav)
+// resident CTAs per SM of the ATM launch sized for mcap staged molecules
+static int atm_ctas_per_sm(const atm_ctx* c, int trav, int trunc, int prec, int nwarps, int mcap)
 {
-    int m = c->unit_max[trav];
+    AtmPlan P;
+    if (!atm_choose_plan(trav, trunc, prec, mcap, c->smem_optin, P, c->det)) return 0;
+    if ((nwarps == 2 || nwarps == 4 || nwarps == 8) && trav != ATM_3C01 && trav != ATM_3CW) {
+        AtmPlan Q;
+        if (atm_choose_plan_nw(trav, trunc, prec, mcap, c->smem_optin, nwarps, Q, c->det)) P = Q;
+    }
+    return prec == ATM_FP64 ? atm_occupancy_fp64(trav, trunc, P.nwarps, P.smem, c->det)
+                            : atm_occupancy_fp32(trav, trunc, P.nwarps, P.smem, c->det);
+}
+
+// staged-molecule capacity of a graph: the current largest unit plus headroom
+// for molecules moving between cells during the steps the graph replays.  The
+// headroom is at most a quarter of the unit (at least 8), and the largest
+// capacity in that range that keeps the resident CTAs per SM of the current
+// unit size is taken (a bigger unit costs shared memory per CTA); with none,
+// 4 molecules.  A unit that outgrows the capacity during the replayed steps
+// is detected on the device and the run restarts without the graph.
+static int graph_mcap(const atm_ctx* c, int trav, int trunc, int prec, int nwarps)
+{
+    const int m = c->unit_max[trav];
     const int limit = (trav == ATM_3C01 || trav == ATM_3CW) ? 65535 : ATM_MCAP_LIMIT;
-    return std::min(limit, m + std::max(8, m / 4));
+    const int hi = std::min(limit, m + std::max(8, m / 4));
+    if (prec == ATM_SURROGATE || m < 1) return hi;
+    const int occ = atm_ctas_per_sm(c, trav, trunc, prec, nwarps, m);
+    for (int cap = hi; cap > m + 4; cap--)
+        if (atm_ctas_per_sm(c, trav, trunc, prec, nwarps, cap) >= occ) return cap;
+    return std::min(limit, m + 4);
 }
 
 // run nsteps with a CUDA graph of one step (no host synchronisation between
 // steps); a capacity overflow surfaces in the status word
 static atm_status run_graph_steps(atm_ctx* c, int nsteps, int trav, int trunc, int prec)
 {
-    const int mcap = graph_mcap(c, trav);
     int persistent = 0, nwarps = 0, cls[3] = {1, 0, 0};
     if (prec != ATM_SURROGATE) launch_choice(c, trav, trunc, prec, persistent, nwarps, cls);
+    const int mcap = graph_mcap(c, trav, trunc, prec, nwarps);
     const int key[8] = {trav, trunc, prec, mcap, persistent + 2 * nwarps, cls[0], cls[1], cls[2]};
     if (!c->graph || memcmp(key, c->graph_key, sizeof(key)) != 0) {
         drop_graph(c);
