@@ -431,6 +431,6 @@ def test_trained_surrogate_gains_over_the_method_without_it(atm3):
         return np.sqrt(np.mean((f - f_exact) ** 2)) / np.sqrt(np.mean(f_exact ** 2))
 
     e_tr, e_un = err(f_trained), err(f_untrained)
-    assert e_tr < 0.6, e_tr                 # without the surrogate (no ATM force): error 1.0
+    assert e_tr < 0.25, e_tr                # without the surrogate (no ATM force): error 1.0; measured 0.158
     assert e_tr < 0.7 * e_un, (e_tr, e_un)  # training is what brings it there
     assert t_sur < t_exact, (t_sur, t_exact)
