@@ -141,9 +141,12 @@ static atm_status check_status(atm_ctx* c)
     if (s == 0) return ATM_OK;
     *c->h_status = 0;
     cudaMemsetAsync(c->d_status, 0, sizeof(int), c->st);
-    if (s & ST_NONFINITE) return ctx_fail(c, ATM_E_NONFINITE, "non-finite position or velocity");
+    // capacity first: a unit skipped for capacity during graph steps leaves its
+    // molecules without forces, and what follows (overlaps, non-finite
+    // positions) is its consequence; graph steps restart on ATM_E_CAPACITY
     if (s & ST_CAPACITY)
         return ctx_fail(c, ATM_E_CAPACITY, "a traversal unit holds more molecules than staged");
+    if (s & ST_NONFINITE) return ctx_fail(c, ATM_E_NONFINITE, "non-finite position or velocity");
     if (s & ST_TIMEOUT)
         return ctx_fail(c, ATM_E_TIMEOUT, "a device-side wait for the tensor cores gave up");
     if (s & ST_RANGE)

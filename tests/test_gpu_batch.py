@@ -129,6 +129,36 @@ def test_graph_steps_equal_plain_steps(atm3, ensemble):
     assert np.abs(xa - xb).max() < 1e-10 and np.abs(va - vb).max() < 1e-9
 
 
+@pytest.mark.parametrize("prec", ["fp32c", "fp64"])
+def test_graph_steps_restart_when_a_unit_outgrows_the_capacity(atm3, prec):
+    """A graph sizes its kernels for the largest unit at capture plus at most a
+    quarter of it (at least 8) of headroom.  Under a compressing velocity
+    field v = -k (x - centre) the central units of a dilute liquid fill up
+    during the replayed steps beyond that capacity: the run must detect it,
+    restart from its snapshot without the graph, and end where plain steps
+    end.  In deterministic mode the forces do not depend on the launch form,
+    so positions and velocities must agree bit for bit."""
+    cfg = synth.homogeneous(2000, 0.25, 1.0, seed=1300)  # 20-sigma box, 8 cells per axis
+    box = cfg["box"]
+    x = np.ascontiguousarray(cfg["x"])
+    v = np.ascontiguousarray(cfg["v"] - 4.0 * (np.mod(x, box[:, None]) - 0.5 * box[:, None]))
+    m0 = int(_unit_sizes(dict(box=box, x=x), "3c08").max())
+    final = []
+    for graph in (False, True):
+        with atm3.AtmSystem(box, cfg["n"], nu=NU, dt=0.002) as s:
+            s.set_deterministic(True)
+            s.set_options(graph=graph)
+            s.set_state(x, v)
+            res = s.step(40, "3c08", "pair", prec)
+            xs, vs = s.get_state()
+            final.append((res, xs, vs))
+    m1 = int(_unit_sizes(dict(box=box, x=final[0][1]), "3c08").max())
+    assert m1 > m0 + max(8, m0 // 4), (m0, m1)  # the graph's capacity was exceeded
+    (ra, xa, va), (rb, xb, vb) = final
+    assert ra["n_int3"] == rb["n_int3"] and ra["n_int2"] == rb["n_int2"]
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+
+
 def test_autotune_keeps_results(atm3, ensemble):
     ns = [r["n"] for r in ensemble]
     with atm3.AtmSystem([r["box"] for r in ensemble], ns, nu=NU) as b:
