@@ -84,7 +84,10 @@ typedef enum { ATM_TRUNC_PAIR = 0, ATM_TRUNC_PRODUCT = 1 } atm_truncation;
 /* Arithmetic of the force evaluation.
  *  FP64:  every decision and every force, energy and virial term in FP64.
  *  FP32C: decisions and per-triplet arithmetic in FP32 on FP32 cell-local
- *         coordinates.  Force sums: 3C18 / 3C08 / 3C08A add each triplet's
+ *         coordinates (every pair decision on the canonical displacement
+ *         (xl_q - xl_p) + (o_q - o_p) w; the pair-rule block traversals then
+ *         evaluate triplets and forces on the FP32-rounded unit-frame
+ *         positions xl + o w).  Force sums: 3C18 / 3C08 / 3C08A add each triplet's
  *         three pair scalars to per-edge FP32 sums, then each molecule's share
  *         of a unit is a plain FP32 sum over its edges, and the shares of
  *         different units are added in FP64; 3C01 / 3CW keep compensated

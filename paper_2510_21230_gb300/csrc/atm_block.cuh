@@ -7,7 +7,10 @@
 // are staged in shared memory in slot order, so a triplet p < q < r of staged
 // indices lists its cells in the order the traversal's tasks do.  Each staged
 // molecule carries its exact base-frame shift o*w, so the canonical
-// displacement (xl_q - xl_p) + (o_q - o_p) w needs no slot lookups.
+// displacement (xl_q - xl_p) + (o_q - o_p) w needs no slot lookups.  FP32
+// pair rule: once the pairs are decided, the shift rows are replaced by the
+// rounded unit-frame positions xl + o w, so the triplet evaluation and the
+// gather take one difference per component (the decisions stay canonical).
 //
 // Pair rule
 //  1. Upper-triangular bitmask adjacency adj[p] = {q > p : |d(p,q)| < r_c}
@@ -155,7 +158,7 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
     float* sy32 = sx32 + mcap;
     float* sz32 = sy32 + mcap;
     float4* P4 = reinterpret_cast<float4*>(smem + plan.off_pos);
-    float4* S4 = reinterpret_cast<float4*>(smem + plan.off_sh);
+    float4* S4 = reinterpret_cast<float4*>(smem + plan.off_sh);  // FP32 pair rule: the shifted rows after the decisions
     int* sidx = reinterpret_cast<int*>(smem + plan.off_idx);
     unsigned char* sslot = smem + plan.off_slot;
     unsigned* adj = reinterpret_cast<unsigned*>(smem + plan.off_adj);
@@ -246,13 +249,13 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
     // do not depend on the order of the additions
     auto gadd = [&](int idx, R v) {
         if constexpr (DET)
-            atomicAdd(reinterpret_cast<unsigned long long*>(G + idx), to_fix<R>((double)v, A.status));
+            atomicAdd(reinterpret_cast<unsigned long long*>(G + idx), to_fix_w<R>(v, A.status));
         else
             atomicAdd(G + idx, v);
     };
     auto gset = [&](int idx, R v) {
         if constexpr (DET)
-            G[idx] = (GT)to_fix<R>((double)v, A.status);
+            G[idx] = (GT)to_fix_w<R>(v, A.status);
         else
             G[idx] = v;
     };
@@ -264,7 +267,7 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
     };
     auto acc_add = [&](int idx, R v) {
         if constexpr (DET)
-            atomicAdd(reinterpret_cast<unsigned long long*>(acc) + idx, to_fix<R>((double)v, A.status));
+            atomicAdd(reinterpret_cast<unsigned long long*>(acc) + idx, to_fix_w<R>(v, A.status));
         else
             Acc<R>::add(acc, mcap, idx, v);
     };
@@ -569,6 +572,18 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
                               A.unit_cnt2, u, s_red, s_redn);
     }
     const bool use_acc = PAIR ? !edge_mode : (A.acc_mode == 1);
+    if constexpr (PAIR && !F64) {
+        // decisions and LJ are done with the canonical displacement; the
+        // triplet phase and the gather take the FP32 shifted rows xl + o w
+        // (one rounding per coordinate), so a displacement is one difference
+        // per component and the third side of a triangle costs no load
+        __syncthreads();
+        for (int t = tid; t < M; t += blockDim.x) {
+            const float4 a = P4[t], sh = S4[t];
+            S4[t] = make_float4(a.x + sh.x, a.y + sh.y, a.z + sh.z, 0.0f);
+        }
+        __syncthreads();
+    }
 
     // ---- 3 + 4. triangles, evaluation, pair scalars
     Sum<R> esum, wsum;
@@ -590,6 +605,14 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
             dpqx = ED[4 * epq]; dpqy = ED[4 * epq + 1]; dpqz = ED[4 * epq + 2]; a = ED[4 * epq + 3];
             dprx = ED[4 * epr]; dpry = ED[4 * epr + 1]; dprz = ED[4 * epr + 2]; b = ED[4 * epr + 3];
             dqrx = ED[4 * eqr]; dqry = ED[4 * eqr + 1]; dqrz = ED[4 * eqr + 2]; c = ED[4 * eqr + 3];
+        } else if constexpr (!F64) {
+            const float4 P = S4[p], Qv = S4[q], Rv = S4[r];  // shifted rows
+            dpqx = Qv.x - P.x; dpqy = Qv.y - P.y; dpqz = Qv.z - P.z;
+            dprx = Rv.x - P.x; dpry = Rv.y - P.y; dprz = Rv.z - P.z;
+            dqrx = Rv.x - Qv.x; dqry = Rv.y - Qv.y; dqrz = Rv.z - Qv.z;
+            a = dpqx * dpqx + dpqy * dpqy + dpqz * dpqz;
+            b = dprx * dprx + dpry * dpry + dprz * dprz;
+            c = dqrx * dqrx + dqry * dqry + dqrz * dqrz;
         } else {
             a = disp(p, q, dpqx, dpqy, dpqz);
             b = disp(p, r, dprx, dpry, dprz);
@@ -902,8 +925,9 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
             fzs.add((R)acc_get(2 * mcap + m));
         } else if (PAIR) {
             // edge vectors: FP64 from the table (d(lo -> hi), so the sign flips for
-            // edges where m is the upper end), FP32 recomputed
+            // edges where m is the upper end), FP32 from the shifted rows
             int e = rowoff[m];
+            const float4 Pm = F64 ? make_float4(0.f, 0.f, 0.f, 0.f) : S4[m];
             for (int w = 0; w < Wm; w++) {
                 unsigned up = adj[m * W + w];
                 while (up) {
@@ -916,7 +940,8 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
                         if (F64) {
                             dx = ED[4 * ee]; dy = ED[4 * ee + 1]; dz = ED[4 * ee + 2];
                         } else {
-                            disp(m, y, dx, dy, dz);
+                            const float4 Y = S4[y];
+                            dx = Y.x - Pm.x; dy = Y.y - Pm.y; dz = Y.z - Pm.z;
                         }
                         fxs.add(g * dx);
                         fys.add(g * dy);
@@ -934,7 +959,8 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
                         if (F64) {
                             dx = -ED[4 * ee]; dy = -ED[4 * ee + 1]; dz = -ED[4 * ee + 2];
                         } else {
-                            disp(m, x, dx, dy, dz);
+                            const float4 X = S4[x];
+                            dx = X.x - Pm.x; dy = X.y - Pm.y; dz = X.z - Pm.z;
                         }
                         fxs.add(g * dx);
                         fys.add(g * dy);

@@ -123,11 +123,33 @@ __device__ __forceinline__ unsigned long long to_fix(double v, int* status)
     return (unsigned long long)__double2ll_rn(x);
 }
 
-// a fixed-point sum back in working precision
+// to_fix of a term in working precision: the FP32 path stays in FP32 (the
+// scaling by 2^32 is exact there too, so the integer is the same) and keeps
+// the hot loops off the slow FP64 pipe
+template <typename R>
+__device__ __forceinline__ unsigned long long to_fix_w(R v, int* status)
+{
+    if constexpr (sizeof(R) == 8) {
+        return to_fix<R>(v, status);
+    } else {
+        const float x = v * (float)(1ull << FixBits<R>::B);
+        if (!(fabsf(x) < (float)(1ull << FIX_LIMIT))) {
+            atomicOr(status, ST_RANGE);
+            return 0ull;
+        }
+        return (unsigned long long)__float2ll_rn(x);
+    }
+}
+
+// a fixed-point sum back in working precision (FP32: the integer rounded to
+// FP32 once, then scaled exactly)
 template <typename R>
 __device__ __forceinline__ R from_fix(long long v)
 {
-    return (R)((double)v * (1.0 / (double)(1ull << FixBits<R>::B)));
+    if constexpr (sizeof(R) == 8)
+        return (R)((double)v * (1.0 / (double)(1ull << FixBits<R>::B)));
+    else
+        return (float)v * (1.0f / (float)(1ull << FixBits<R>::B));
 }
 
 // running sum: plain for FP64, Kahan-compensated for FP32
