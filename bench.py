@@ -494,20 +494,30 @@ def run_ours(args):
         sysm.step(0, args.trav, args.trunc, args.prec)   # the force of the start state
         sysm.get_forces("total", out=fh.numpy())
         k = max(3, min(args.steps, 10))
+        xs, vs, fs = xh.numpy(), vh.numpy(), fh.numpy()
         for it in range(k + 2):
             if it == 2:
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
-            sysm.set_state(xh.numpy(), vh.numpy())
-            sysm.set_forces(fh.numpy(), args.trav, args.trunc, args.prec)
-            sysm.step(1, args.trav, args.trunc, args.prec)
-            sysm.get_state(xh.numpy(), vh.numpy())  # into the pinned buffers
-            sysm.get_forces("total", out=fh.numpy())
+            # state and force in, one step, state and force out (atm_step_host)
+            sysm.step_host(xs, vs, fs, 1, args.trav, args.trunc, args.prec)
         dt = time.perf_counter() - t0
         e2e = {"value": n * k / dt, "unit": UNIT, "h2d_bytes_per_step": 3 * 3 * n * 8,
                "d2h_bytes_per_step": 3 * 3 * n * 8 + 72,
-               "note": "host state (x, v) and its force in, one velocity-Verlet step (one "
-                       "force evaluation), state and force out"}
+               "note": "atm_step_host from pinned host buffers: state (x, v) and its force in, "
+                       "one velocity-Verlet step (one force evaluation), state, force and "
+                       "scalars out"}
+        # the same round trip through the separate calls (each synchronises)
+        for it in range(k + 2):
+            if it == 2:
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+            sysm.set_state(xs, vs)
+            sysm.set_forces(fs, args.trav, args.trunc, args.prec)
+            sysm.step(1, args.trav, args.trunc, args.prec)
+            sysm.get_state(xs, vs)
+            sysm.get_forces("total", out=fs)
+        e2e["separate_calls_value"] = n * k / (time.perf_counter() - t1)
 
     line = None
     if rank == 0:

@@ -190,6 +190,24 @@ atm_status atm_get_state(atm_ctx* ctx, double* x, double* v);
 atm_status atm_step(atm_ctx* ctx, int nsteps, atm_traversal trav, atm_truncation trunc,
                     atm_precision prec, atm_result* last);
 
+/* A round trip through host memory for callers that keep the state on the
+ * host: x[3n] and v[3n] (host, original order) become the state and f[3n]
+ * (host, or NULL) its total force as computed with (trav, trunc, prec), as
+ * atm_set_forces takes it (NULL: the first step evaluates it; with
+ * ATM_SURROGATE f must be NULL); then nsteps steps as atm_step; then the new
+ * (wrapped) positions and velocities are written back into x and v, the total
+ * force of the new state into f (when given), and the scalars into *last (when
+ * non-NULL).  The result equals atm_set_state, atm_set_forces, atm_step,
+ * atm_get_state and atm_get_forces(..., 0) in sequence, but the stream is
+ * synchronised only by the steps' cell builds and once at the end (those calls
+ * synchronise one by one).  The inputs are checked for NaN / Inf on the
+ * device: a non-finite input returns NONFINITE, after which the contents of x,
+ * v and f are unspecified and the context has no state.  Host memory that is
+ * page-locked (cudaHostAlloc / cudaHostRegister) is copied fastest.
+ * Errors: as atm_step, NONFINITE. */
+atm_status atm_step_host(atm_ctx* ctx, int nsteps, atm_traversal trav, atm_truncation trunc,
+                         atm_precision prec, double* x, double* v, double* f, atm_result* last);
+
 /* ---- Batches of independent replicas ------------------------------------
  * A context may hold nrep independent periodic systems ("replicas", e.g. an
  * ensemble of uneven N, density and temperature).  Every kernel of a force

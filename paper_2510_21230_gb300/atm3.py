@@ -27,7 +27,8 @@ ABI_VERSION = 3  # ATM3_ABI_VERSION of include/atm3.h
 EXPORTED = ["atm_abi_version", "atm_create", "atm_batch_create", "atm_batch_size", "atm_destroy",
             "atm_last_error", "atm_set_state", "atm_set_state_dev", "atm_build_cells",
             "atm_get_cells", "atm_compute_forces", "atm_get_results", "atm_get_forces",
-            "atm_get_forces_dev", "atm_get_state", "atm_step", "atm_set_options", "atm_autotune",
+            "atm_get_forces_dev", "atm_get_state", "atm_step", "atm_step_host", "atm_set_options",
+            "atm_autotune",
             "atm_density_accumulate", "atm_density_get", "atm_density_reset",
             "atm_set_profiling", "atm_get_profile", "atm_compute_forces_noalloc",
             "atm_surrogate_set_model", "atm_surrogate_get_model", "atm_surrogate_init",
@@ -117,6 +118,7 @@ def load():
         "atm_get_forces_dev": [P, P, i32],
         "atm_get_state": [P, P, P],
         "atm_step": [P, i32, i32, i32, i32, ctypes.POINTER(Result)],
+        "atm_step_host": [P, i32, i32, i32, i32, P, P, P, ctypes.POINTER(Result)],
         "atm_set_options": [P, i32, i32, i32],
         "atm_set_unit_classes": [P, i32, P],
         "atm_set_deterministic": [P, i32],
@@ -287,6 +289,19 @@ class AtmSystem:
         assert f.shape == (3, self.n)
         self._check(self._lib.atm_set_forces(self._ctx, _host_ptr(f), TRAVERSALS[trav],
                                              TRUNCATIONS[trunc], PRECISIONS[prec]))
+
+    def step_host(self, x, v, f=None, nsteps=1, trav="3c08", trunc="pair", prec="fp32c"):
+        """One host round trip (atm_step_host): x, v (and f, when given) are the
+        state and its total force; they are overwritten in place with the state
+        and total force after nsteps steps.  Returns the scalars."""
+        for a in (x, v) + ((f,) if f is not None else ()):
+            assert a.shape == (3, self.n) and a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+        r = Result()
+        self._check(self._lib.atm_step_host(self._ctx, int(nsteps), TRAVERSALS[trav],
+                                            TRUNCATIONS[trunc], PRECISIONS[prec], _host_ptr(x),
+                                            _host_ptr(v), _host_ptr(f) if f is not None else None,
+                                            ctypes.byref(r)))
+        return r.as_dict()
 
     def get_state(self, x=None, v=None):
         x = np.zeros((3, self.n)) if x is None else x

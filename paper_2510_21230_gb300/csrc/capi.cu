@@ -908,6 +908,71 @@ extern "C" atm_status atm_step(atm_ctx* c, int nsteps, atm_traversal trav, atm_t
     return ATM_OK;
 }
 
+extern "C" atm_status atm_step_host(atm_ctx* c, int nsteps, atm_traversal trav,
+                                    atm_truncation trunc, atm_precision prec, double* x,
+                                    double* v, double* f, atm_result* last)
+{
+    if (!c) return ATM_E_INVALID;
+    if (nsteps < 0 || !valid_enums(trav, trunc, prec))
+        return ctx_fail(c, ATM_E_INVALID, "bad step arguments");
+    if ((!x || !v) && c->n > 0) return ctx_fail(c, ATM_E_INVALID, "positions and velocities are required");
+    if (f && prec == ATM_SURROGATE)
+        return ctx_fail(c, ATM_E_INVALID, "given forces need an exact traversal, truncation, precision");
+    CU(cudaSetDevice(c->device));
+    const long long m = 3 * c->n;
+    const size_t bytes = (size_t)m * sizeof(double);
+    // inputs: copies and device-side finite checks; the verdict travels back
+    // with the first synchronisation of the step (its cell build) or the last
+    *c->h_chk = 0;
+    if (m > 0) {
+        CU(cudaMemsetAsync(c->d_chk, 0, sizeof(int), c->st));
+        CU(cudaMemcpyAsync(c->x, x, bytes, cudaMemcpyHostToDevice, c->st));
+        CU(launch_check_finite(m, c->x, c->d_chk, c->st));
+        CU(cudaMemcpyAsync(c->v, v, bytes, cudaMemcpyHostToDevice, c->st));
+        CU(launch_check_finite(m, c->v, c->d_chk, c->st));
+        c->n_launch += 2;
+        if (f) {
+            CU(cudaMemcpyAsync(c->f_in, f, bytes, cudaMemcpyHostToDevice, c->st));
+            CU(launch_check_finite(m, c->f_in, c->d_chk, c->st));
+            c->n_launch += 1;
+        }
+        CU(cudaMemcpyAsync(c->h_chk, c->d_chk, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    }
+    c->have_x = true;
+    invalidate(c);
+    if (f) {
+        c->f_in_valid = true;
+        c->f_in_key[0] = trav;
+        c->f_in_key[1] = trunc;
+        c->f_in_key[2] = prec;
+    }
+    auto bad_input = [&]() -> atm_status {
+        c->have_x = false;
+        invalidate(c);
+        return ctx_fail(c, ATM_E_NONFINITE, "non-finite position, velocity or force given");
+    };
+    atm_status s = atm_step(c, nsteps, trav, trunc, prec, nullptr);
+    if (s != ATM_OK) {
+        cudaStreamSynchronize(c->st);
+        return *c->h_chk ? bad_input() : s;
+    }
+    // outputs: state, total force and scalars, then one synchronisation
+    if (m > 0) {
+        CU(cudaMemcpyAsync(x, c->x, bytes, cudaMemcpyDeviceToHost, c->st));
+        CU(cudaMemcpyAsync(v, c->v, bytes, cudaMemcpyDeviceToHost, c->st));
+        if (f) {
+            CU(launch_gather_forces(c->n, c->perm, c->f_lj, c->f_atm, 0, c->f_out, c->st));
+            c->n_launch += 1;
+            CU(cudaMemcpyAsync(f, c->f_out, bytes, cudaMemcpyDeviceToHost, c->st));
+        }
+    }
+    s = ctx_sync_and_check(c);
+    if (*c->h_chk) return bad_input();
+    if (s != ATM_OK) return s;
+    if (last) copy_result(c->h_res[0], last);
+    return ATM_OK;
+}
+
 extern "C" atm_status atm_set_options(atm_ctx* c, int persistent, int nwarps, int graph)
 {
     if (!c) return ATM_E_INVALID;

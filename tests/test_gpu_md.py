@@ -276,3 +276,64 @@ def test_forces_are_forgotten_with_a_new_state(atm3):
     # zero forces in the first half kick would change the kinetic energy by far more
     assert r1["e3"] == pytest.approx(r2["e3"], rel=1e-6)
     assert r1["ekin"] == pytest.approx(r2["ekin"], rel=1e-9)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_step_host_equals_the_separate_calls(atm3, prec):
+    """atm_step_host (state and force in from host memory, steps, state and
+    force out, one synchronisation at the end) gives what the separate calls
+    give: bit for bit in deterministic mode, where the force sums do not
+    depend on the order of the atomic additions.  Also without given forces,
+    and with two steps per round trip."""
+    cfg = synth.homogeneous(2000, 0.8, 1.0, seed=1302)
+    runs = []
+    for api in ("separate", "host"):
+        with atm3.AtmSystem(cfg["box"], cfg["n"], nu=NU, dt=0.002) as s:
+            s.set_deterministic(True)
+            s.set_state(cfg["x"], cfg["v"])
+            s.step(0, "3c08", "pair", prec)
+            x, v = s.get_state()
+            f = s.get_forces("total")
+            res = []
+            for nsteps in (1, 1, 2):
+                if api == "separate":
+                    s.set_state(x, v)
+                    s.set_forces(f, "3c08", "pair", prec)
+                    res.append(s.step(nsteps, "3c08", "pair", prec))
+                    x, v = s.get_state()
+                    f = s.get_forces("total")
+                else:
+                    res.append(s.step_host(x, v, f, nsteps, "3c08", "pair", prec))
+            if api == "separate":
+                s.set_state(x, v)
+                res.append(s.step(1, "3c08", "pair", prec))
+                x, v = s.get_state()
+            else:
+                res.append(s.step_host(x, v, None, 1, "3c08", "pair", prec))
+            runs.append((x.copy(), v.copy(), f.copy(), res))
+    (xa, va, fa, ra), (xb, vb, fb, rb) = runs
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb) and np.array_equal(fa, fb)
+    for a, b in zip(ra, rb):
+        for k in ("n_int3", "n_int2", "n_cand3"):
+            assert a[k] == b[k], k
+        for k in ("e2", "e3", "ekin", "w3"):
+            assert b[k] == pytest.approx(a[k], rel=1e-12), k
+
+
+def test_step_host_rejects_non_finite_input(atm3):
+    cfg = synth.homogeneous(1000, 0.8, 1.0, seed=1303)
+    with atm3.AtmSystem(cfg["box"], cfg["n"], nu=NU) as s:
+        for which in ("x", "v", "f"):
+            x, v = cfg["x"].copy(), cfg["v"].copy()
+            f = np.zeros((3, cfg["n"]))
+            {"x": x, "v": v, "f": f}[which][1, 7] = np.nan
+            with pytest.raises(atm3.AtmError, match="NONFINITE|non-finite"):
+                s.step_host(x, v, f, 1, "3c08", "pair", "fp32c")
+            with pytest.raises(atm3.AtmError):
+                s.step(1, "3c08", "pair", "fp32c")         # no state after the rejection
+        with pytest.raises(atm3.AtmError):                  # given forces need an exact mode
+            s.step_host(cfg["x"].copy(), cfg["v"].copy(), np.zeros((3, cfg["n"])), 1,
+                        "3c08", "pair", "surrogate")
+        x, v = cfg["x"].copy(), cfg["v"].copy()
+        r = s.step_host(x, v, None, 0, "3c08", "pair", "fp32c")   # zero steps: forces of the state
+        assert r["n_int3"] > 0
