@@ -292,6 +292,23 @@ atm_status atm_set_owned_layers(atm_ctx* ctx, int replica, int z_lo, int z_hi);
  * Errors: INVALID. */
 atm_status atm_set_deterministic(atm_ctx* ctx, int on);
 
+/* Pair bitmaps for the FP32C pair rule of the block traversals (on = 1, the
+ * default; 0 = off).  With them on, each force evaluation first decides every
+ * pair of molecules in neighbouring cells once, in one kernel and its
+ * transposition: 27 words per molecule (4 bytes each, held by the context),
+ * bit j of word k set when the molecule and the j-th molecule of the
+ * neighbour cell at offset k are closer
+ * than r_c by the same FP32 arithmetic the units use (the canonical
+ * displacement (xl_q - xl_p) + (o_q - o_p) w), and the 3C18 / 3C08 / 3C08A
+ * units assemble their adjacency from those words instead of deciding each
+ * pair of their 14 or 8 cells again.  The decisions, so the triplets and the
+ * counts, are the same either way.  Used when every cell holds at most 32
+ * molecules (the cell build's largest occupancy; graph steps whose cells fill
+ * beyond that restart without the graph) and, for 3C18, when the cells are
+ * wide enough in FP32 that cells two apart hold no pair within r_c.  Drops
+ * any tuned choice and graph.  Errors: INVALID. */
+atm_status atm_set_pair_masks(atm_ctx* ctx, int on);
+
 /* Unit size classes of the block traversals (3C18, 3C08, 3C08A) for
  * evaluations and steps without an autotuned choice.  nclass = 1: every unit
  * in one launch sized for the largest unit (the default).  nclass = 2 or 3:

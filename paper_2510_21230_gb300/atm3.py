@@ -39,6 +39,7 @@ EXPORTED = ["atm_abi_version", "atm_create", "atm_batch_create", "atm_batch_size
             "atm_measure_fma_peak", "atm_rdf_accumulate", "atm_rdf_get", "atm_rdf_reset",
             "atm_lj_tail", "atm_thermostat", "atm_measure_rsqrt_peak", "atm_set_forces",
             "atm_set_unit_classes", "atm_batch_cells", "atm_cell_grid", "atm_set_deterministic",
+            "atm_set_pair_masks",
             "atm_surrogate_training_arithmetic", "atm_set_owned_layers"]
 
 SUR_NDESC, SUR_NVEC, SUR_NOUT, SUR_NPARAM = 32, 48, 16, 7312
@@ -122,6 +123,7 @@ def load():
         "atm_set_options": [P, i32, i32, i32],
         "atm_set_unit_classes": [P, i32, P],
         "atm_set_deterministic": [P, i32],
+        "atm_set_pair_masks": [P, i32],
         "atm_set_owned_layers": [P, i32, i32, i32],
         "atm_autotune": [P, i32, i32, i32, i32, ctypes.POINTER(Tuning)],
         "atm_density_accumulate": [P, i32, i32],
@@ -362,6 +364,11 @@ class AtmSystem:
         """Domain decomposition: the replica owns cell layers [z_lo, z_hi)
         (``atm_set_owned_layers``)."""
         self._check(self._lib.atm_set_owned_layers(self._ctx, int(replica), int(z_lo), int(z_hi)))
+
+    def set_pair_masks(self, on=True):
+        """FP32C pair rule of the block traversals: pairs decided once per
+        evaluation into per-molecule bitmaps (on, the default) or by each unit."""
+        self._check(self._lib.atm_set_pair_masks(self._ctx, int(bool(on))))
 
     def set_deterministic(self, on=True):
         """Deterministic mode (``atm_set_deterministic``): repeated runs give

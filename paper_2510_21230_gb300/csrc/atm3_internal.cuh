@@ -189,7 +189,17 @@ struct AtmArgs {
     // kernels; the block kernels' deterministic instantiations also sum in
     // fixed point and fs holds 64-bit fixed-point sums, see FixBits)
     int det;
+    // FP32 pair rule of the block traversals: the evaluation's pair bitmaps
+    // (k_pair_masks, [PM_WORDS n] words, nullptr: the units decide their
+    // pairs themselves); the units assemble their adjacency from them
+    const unsigned* pmask;
 };
+
+// pair bitmaps: word k - 13 of molecule s (sorted) covers the molecules of
+// the cell at offset27(k), k = 13 (its own cell, the later molecules) .. 26
+// (the 13 forward cells); a cell holds at most PM_CELL_MAX molecules
+constexpr int PM_WORDS = 14;
+constexpr int PM_CELL_MAX = 32;
 
 // Shared-memory plan of the owner kernels (3c01, 3cw): staged positions,
 // per-warp partner lists of capacity pcap (index, displacement, squared

@@ -407,7 +407,79 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
         // broadcast load).  FP64: one warp per row, one ballot per 32 pairs
         // (the rare FP64 recomputations of the prefilter band stay spread
         // over the lanes).
-        if (!F64) {
+        if (!F64 && A.pmask) {
+            // from the evaluation's pair bitmaps (k_pair_masks): word k - 13 of
+            // a molecule covers the molecules of the cell at offset27(k), k =
+            // 13 (its own cell, the later molecules) .. 26 (the forward
+            // cells), in cell order, which is the staging order.  Slot s2
+            // lies at offset o(s2) - o(sp) from p's slot, and a later slot is
+            // a forward cell in both unit kinds (3c08: s = ox + 2 oy + 4 oz;
+            // 3c18: forward neighbours in lexicographic order), so row p of
+            // adj comes from p's own words.  Cells two apart (a 3c18 unit's
+            // outer slots) hold no pair within r_c: the host hands over
+            // bitmaps only when fl(w^2) >= the FP32 r_c^2 on every axis.
+            for (int p = tid; p < M; p += blockDim.x) {
+                const int sp = sslot[p];
+                const long long gp = sidx[p];
+                unsigned* rowa = adj + p * W;
+                unsigned wd[S];  // the row's words first: independent loads in flight
+#pragma unroll
+                for (int s2 = 0; s2 < S; s2++) {
+                    const int ox = s_off[s2][0] - s_off[sp][0];
+                    const int oy = s_off[s2][1] - s_off[sp][1];
+                    const int oz = s_off[s2][2] - s_off[sp][2];
+                    const bool use = s2 >= sp && ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 &&
+                                     oz >= -1 && oz <= 1;
+                    const int k = (oz + 1) * 9 + (oy + 1) * 3 + (ox + 1);
+                    wd[s2] = use ? __ldg(A.pmask + (long long)(k - 13) * n + gp) : 0u;
+                }
+#pragma unroll
+                for (int s2 = 0; s2 < S; s2++) {
+                    const int b = s_beg[s2], nb = s_beg[s2 + 1] - b;
+                    // bits beyond the slot's molecules cannot be set by an
+                    // evaluation with every cell within 32; a graph replay
+                    // whose cells outgrew that (flagged, and discarded) must
+                    // not place them outside the slot either
+                    const unsigned word = wd[s2] & (nb >= 32 ? ~0u : (1u << nb) - 1u);
+                    if (!word) continue;
+                    const int w0 = b >> 5, sh = b & 31;
+                    rowa[w0] |= word << sh;
+                    if (sh && (word >> (32 - sh))) rowa[w0 + 1] |= word >> (32 - sh);
+                }
+            }
+            __syncthreads();
+            // adjT by transposing 32 x 32 blocks of adj (row block rb, column
+            // word cb >= rb): lane i holds row rb * 32 + i's word cb, and the
+            // ballot of bit j is column cb * 32 + j's word rb
+            const int nblk = Wm * (Wm + 1) / 2;
+            for (int it = warp; it < nblk; it += nwarps) {
+                int rb = 0, cb = it;
+                while (cb >= Wm - rb) {
+                    cb -= Wm - rb;
+                    rb++;
+                }
+                cb += rb;
+                const int p = (rb << 5) + lane;
+                const unsigned a = p < M ? adj[p * W + cb] : 0u;
+                const int jn = min(32, M - (cb << 5));
+                unsigned col = 0u;
+                for (int jj = 0; jj < jn; jj++) {
+                    const unsigned bb = __ballot_sync(FULL, (a >> jj) & 1u);
+                    if (lane == jj) col = bb;
+                }
+                if (lane < jn) adjT[((cb << 5) + lane) * W + rb] = col;
+            }
+            __syncthreads();
+            // per-word prefix popcounts and the row's edge count
+            for (int p = tid; p < M; p += blockDim.x) {
+                int run = 0;
+                for (int w = p >> 5; w < Wm; w++) {
+                    rowpre[p * W + w] = (unsigned short)run;
+                    run += __popc(adj[p * W + w]);
+                }
+                rowoff[p + 1] = run;
+            }
+        } else if (!F64) {
             for (int p = tid; p < M; p += blockDim.x) {
                 int run = 0;
                 const unsigned pbit = 1u << (p & 31);

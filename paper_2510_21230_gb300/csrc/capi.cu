@@ -115,7 +115,7 @@ static void free_all(atm_ctx* c)
                    c->f_lj, c->f_atm, c->f_out, c->unit_ew, c->unit_cnt, c->mol_ew, c->mol_cnt,
                    c->ke, c->d_res, c->d_part, c->d_status, c->d_maxocc, c->d_work, c->d_dens,
                    c->d_rdf, c->d_ttarget, c->unit_ew2, c->unit_cnt2, c->f_in, c->d_chk,
-                   c->d_ulist, c->d_ucount};
+                   c->d_ulist, c->d_ucount, c->pmask};
     for (void* p : dev)
         if (p) cudaFree(p);
     if (c->h_res) cudaFreeHost(c->h_res);
@@ -204,6 +204,16 @@ extern "C" atm_status atm_batch_create(const atm_params* params, const int64_t* 
     }
     c->n = ntot;
     c->ncell = ncell;
+    // a pair two cells apart is at least a cell edge w apart along that axis,
+    // and its FP32 squared distance at least fl(wf * wf): no pair within r_c
+    // when that is not below the FP32 r_c^2 (the 3c18 units' outer slots)
+    c->pm_3c18 = true;
+    for (const atm3::Rep& r : c->reps)
+        for (int d = 0; d < 3; d++) {
+            volatile float wf = r.wf[d];
+            volatile float w2 = wf * wf;
+            if (!(w2 >= r.rc2f)) c->pm_3c18 = false;
+        }
     auto alloc = [&](void** ptr, size_t bytes) -> bool {
         return cudaMalloc(ptr, bytes > 0 ? bytes : 16) == cudaSuccess;
     };
@@ -246,6 +256,7 @@ extern "C" atm_status atm_batch_create(const atm_params* params, const int64_t* 
     ok = ok && alloc((void**)&c->d_dens, (size_t)nrep * DENS_MAX_BINS * sizeof(unsigned long long));
     ok = ok && alloc((void**)&c->d_rdf, (size_t)nrep * DENS_MAX_BINS * sizeof(unsigned long long));
     ok = ok && alloc((void**)&c->d_ttarget, nrep * sizeof(double));
+    ok = ok && alloc((void**)&c->pmask, atm3::PM_WORDS * N * sizeof(unsigned));
     ok = ok && cudaMallocHost((void**)&c->h_res, nrep * sizeof(ResultDev)) == cudaSuccess;
     ok = ok && cudaMallocHost((void**)&c->h_status, sizeof(int)) == cudaSuccess;
     ok = ok && cudaMallocHost((void**)&c->h_chk, sizeof(int)) == cudaSuccess;
@@ -498,6 +509,14 @@ static void launch_choice(const atm_ctx* c, int trav, int trunc, int prec, int& 
 }
 
 // LJ + ATM force kernels for the current cells; mcap = staged-molecule capacity
+// FP32 pair rule of a block traversal, bitmaps enabled, every cell within 32
+static bool use_pair_masks(const atm_ctx* c, int trav, int trunc, int prec)
+{
+    return c->opt_pmask && c->pmask && prec == ATM_FP32C && trunc == ATM_TRUNC_PAIR &&
+           (trav == ATM_3C08 || trav == ATM_3C08A || (trav == ATM_3C18 && c->pm_3c18)) &&
+           c->maxocc <= atm3::PM_CELL_MAX;
+}
+
 atm_status atm3::ctx_enqueue_forces(atm_ctx* c, int trav, int trunc, int prec, int mcap,
                                     bool fuse_lj)
 {
@@ -549,6 +568,7 @@ atm_status atm3::ctx_enqueue_forces(atm_ctx* c, int trav, int trunc, int prec, i
     j.ev_fork = c->ev_fork;
     j.ev_join = c->ev_join;
     j.det = c->det;
+    j.pmask = use_pair_masks(c, trav, trunc, prec) ? c->pmask : nullptr;
 
     cudaEvent_t ev;
     if (prec != ATM_SURROGATE && !fused) {
@@ -573,6 +593,7 @@ atm_status atm3::ctx_enqueue_forces(atm_ctx* c, int trav, int trunc, int prec, i
                             j.mcap);
         CU(e);
         if (atm_split_active(j)) c->n_launch += j.ncls;  // the class kernel and ncls - 1 more
+        if (atm_uses_pair_masks(j)) c->n_launch += 1;      // the pair bitmaps
         if (j.det && (trav == ATM_3C18 || trav == ATM_3C08 || trav == ATM_3C08A) && c->n > 0)
             c->n_launch += 1;  // the fixed-point force conversion
     }
@@ -766,7 +787,9 @@ static atm_status run_graph_steps(atm_ctx* c, int nsteps, int trav, int trunc, i
     int persistent = 0, nwarps = 0, cls[3] = {1, 0, 0};
     if (prec != ATM_SURROGATE) launch_choice(c, trav, trunc, prec, persistent, nwarps, cls);
     const int mcap = graph_mcap(c, trav, trunc, prec, nwarps);
-    const int key[8] = {trav, trunc, prec, mcap, persistent + 2 * nwarps, cls[0], cls[1], cls[2]};
+    const int key[8] = {trav, trunc, prec, mcap,
+                        persistent + 2 * nwarps + 64 * (use_pair_masks(c, trav, trunc, prec) ? 1 : 0),
+                        cls[0], cls[1], cls[2]};
     if (!c->graph || memcmp(key, c->graph_key, sizeof(key)) != 0) {
         drop_graph(c);
         cudaStream_t keep = c->st;
@@ -970,6 +993,16 @@ extern "C" atm_status atm_step_host(atm_ctx* c, int nsteps, atm_traversal trav,
     if (*c->h_chk) return bad_input();
     if (s != ATM_OK) return s;
     if (last) copy_result(c->h_res[0], last);
+    return ATM_OK;
+}
+
+extern "C" atm_status atm_set_pair_masks(atm_ctx* c, int on)
+{
+    if (!c) return ATM_E_INVALID;
+    if (on < 0 || on > 1) return ctx_fail(c, ATM_E_INVALID, "on is 0 or 1");
+    c->opt_pmask = on;
+    memset(c->tuned, 0, sizeof(c->tuned));
+    drop_graph(c);
     return ATM_OK;
 }
 

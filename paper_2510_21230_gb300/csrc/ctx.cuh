@@ -85,6 +85,13 @@ struct atm_ctx {
     int opt_persistent = 0, opt_nwarps = 0, opt_graph = 0;
     int opt_cls[3] = {1, 0, 0};  // unit size classes: count, bounds of the first two
     int det = 0;                 // deterministic mode (atm_set_deterministic)
+    // FP32 pair-rule decisions of the block traversals from per-molecule pair
+    // bitmaps ([27 n] words) when every cell holds at most 32 molecules
+    // (atm_set_pair_masks; on by default); pm_3c18: every replica's cells are
+    // wide enough in FP32 that cells two apart hold no pair within r_c
+    unsigned* pmask = nullptr;
+    int opt_pmask = 1;
+    bool pm_3c18 = false;
     // 0 = not tuned, else 1 + persistent + 2 * (nwarps == 8) + 4 * size-class choice
     int tuned[2][atm3::ATM_NTRAV][2] = {};
     // graph of one step, valid for (trav, trunc, prec, mcap, launch choice)

@@ -155,7 +155,14 @@ static cudaError_t launch_atm_one(const ForceJob& j, size_t* smem_set, bool* cap
     a.ulist = ulist;
     a.ucount = ucount;
     a.det = j.det;
+    a.pmask = atm_uses_pair_masks(j) ? j.pmask : nullptr;
     return launch_atm_fp32(j.trav, j.trunc, a, P.nwarps, P.smem, ctas, j.st);
+}
+
+bool atm_uses_pair_masks(const ForceJob& j)
+{
+    return j.pmask && j.prec == 1 && j.trunc == 0 && (j.trav == 1 || j.trav == 2 || j.trav == 4) &&
+           j.b.ntot > 0;
 }
 
 bool atm_split_active(const ForceJob& j)
@@ -196,6 +203,10 @@ static cudaError_t enqueue_atm_launches(const ForceJob& j, size_t* smem_set, boo
     const int lj = j.lj && (j.trav == 2 || j.trav == 4) && j.trunc == 0;
     if (lj && j.b.ntot > 0) {  // the units write LJ + ATM into f_atm
         e = cudaMemsetAsync(j.f_lj, 0, 3 * (size_t)j.b.ntot * sizeof(double), j.st);
+        if (e != cudaSuccess) return e;
+    }
+    if (atm_uses_pair_masks(j)) {
+        e = launch_pair_masks(j.b, j.start, j.xl32, j.cell_sorted, j.pmask, j.status, j.st);
         if (e != cudaSuccess) return e;
     }
     if (!atm_split_active(j)) return launch_atm_one(j, smem_set, capacity, nullptr, nullptr, j.work);

@@ -59,6 +59,12 @@ struct ForceJob {
     // deterministic mode: fixed work order; the block traversals sum their
     // terms in 64-bit fixed point and f_atm is converted back after them
     int det = 0;
+    // FP32 pair rule of the block traversals: [PM_WORDS n] words for the pair
+    // bitmaps, computed by one kernel ahead of the units, which assemble
+    // their adjacency from them (nullptr: the units decide their own pairs).
+    // The caller passes it only when every cell holds at most PM_CELL_MAX
+    // molecules (a fuller cell found on the device sets ST_CAPACITY)
+    unsigned* pmask = nullptr;
 };
 
 cudaError_t enqueue_lj(const ForceJob& j);
@@ -66,5 +72,7 @@ cudaError_t enqueue_lj(const ForceJob& j);
 cudaError_t enqueue_atm(const ForceJob& j, size_t* smem_set, bool* capacity);
 // the job runs its units in size classes (one more kernel, ncls ATM launches)
 bool atm_split_active(const ForceJob& j);
+// the job's units take their pairs from bitmaps (one more kernel ahead of them)
+bool atm_uses_pair_masks(const ForceJob& j);
 
 }  // namespace atm3

@@ -61,6 +61,15 @@ cudaError_t launch_rescale(const Batch& b, double* v, double* ke, const ResultDe
                            const double* t_target, cudaStream_t st);
 cudaError_t launch_check_finite(long long m, const double* a, int* status, cudaStream_t st);
 cudaError_t launch_final_reduce(const ReduceArgs& r, cudaStream_t st);
+// pair bitmaps of the FP32 pair-rule decisions: pm[(k - 13) n + s] bit j is
+// set when molecule s (cell-sorted) and the j-th molecule of the cell at
+// offset27(k) from its cell, k = 13 (the cell itself; molecules after s only)
+// .. 26 (the forward cells), are closer than r_c by the canonical FP32
+// displacement (xl_t - xl_s) + delta w, the value the block kernels' own
+// decisions compute; grid n x PM_WORDS.  A neighbour cell of more than
+// PM_CELL_MAX molecules sets ST_CAPACITY in status (its words stay 0).
+cudaError_t launch_pair_masks(const Batch& b, const int* start, const float* xl32,
+                              const int* cell_sorted, unsigned* pm, int* status, cudaStream_t st);
 cudaError_t launch_gather_forces(long long n, const int* perm, const double* f_lj,
                                  const double* f_atm, int which, double* out, cudaStream_t st);
 // adds the pair-distance histogram (nbins equal bins over [0, rmax), every
