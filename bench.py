@@ -61,7 +61,7 @@ FUSED_TRAV = ("3c08", "3c08a")
 # reports null until it is captured again.  liquid_n256k is the N = 32,000
 # capture (2197 units) scaled to 19683 units.
 KERNEL_SOURCES = ["atm3_internal.cuh", "atm_common.cuh", "atm_block.cuh", "atm_owner.cuh",
-                  "atm_fp32.cu", "atm_fp64.cu", "atm_launch.cuh", "md_kernels.cu"]
+                  "atm_fp32.cu", "atm_fp64.cu", "atm_launch.cuh", "pair_masks.cu"]
 TRAFFIC = {("3c08", "pair", "fp32c", "liquid_n256k"): (32.43e6, "40470b7545927bec"),
            ("3c08", "pair", "fp32c", "liquid_n32k"): (3.620e6, "40470b7545927bec")}
 

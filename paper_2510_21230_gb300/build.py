@@ -18,7 +18,7 @@ LIB = os.path.join(HERE, "libatm3.so")
 
 SOURCES = ["capi.cu", "forces.cu", "md_kernels.cu", "atm_fp64.cu", "atm_fp32.cu", "atm_det64.cu",
            "atm_det32.cu", "noalloc.cu",
-           "sur_kernels.cu", "sur_capi.cu", "sur_tc.cu", "sur_train_tc.cu", "peak.cu"]
+           "sur_kernels.cu", "sur_capi.cu", "sur_tc.cu", "sur_train_tc.cu", "peak.cu", "pair_masks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                      "-I" + INCLUDE, "-I" + CSRC]

@@ -69,97 +69,57 @@ __global__ void k_wrap_bin(Batch B, double* __restrict__ x, int* __restrict__ ce
     rank[i] = atomicAdd(count + id, 1);
 }
 
-// Pair bitmaps (see launch_pair_masks): one thread per (molecule, offset);
-// the threads of a warp share a cell and an offset, so the neighbour rows
-// they read are broadcast loads, and each offset's words are written by
-// consecutive threads.  The arithmetic is the block kernels' decision term by
-// term: (xl_t - xl_s) + delta w per component, delta w exact for
-// |delta| <= 1, squares summed x, y, z, compared with the FP32 r_c^2.
-__global__ void __launch_bounds__(128) k_pair_masks(Batch B, const int* __restrict__ start,
-                                                    const float* __restrict__ xl32,
-                                                    const int* __restrict__ cell_sorted,
-                                                    unsigned* __restrict__ pm,
-                                                    int* __restrict__ status)
-{
-    const long long n = B.ntot;
-    const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const int k = 13 + (int)blockIdx.y;  // the cell itself, then the 13 forward cells
-    if (s >= n) return;
-    const int c = cell_sorted[s];
-    const Rep& rp = B.rep[B.rep_of_cell[c]];
-    const int nx = rp.g.nc[0], ny = rp.g.nc[1], nz = rp.g.nc[2];
-    const int id = (int)(c - rp.cell0);  // below 2^30
-    const int cx = id % nx, cyz = id / nx, cy = cyz % ny, cz = cyz / ny;
-    int dx, dy, dz;
-    offset27(k, dx, dy, dz);
-    int x = cx + dx, y = cy + dy, z = cz + dz;
-    x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
-    y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
-    z = z < 0 ? z + nz : (z >= nz ? z - nz : z);
-    const long long c2 = rp.cell0 + ((long long)z * ny + y) * nx + x;
-    const int t0 = start[c2], t1 = start[c2 + 1];
-    unsigned word = 0u;
-    if (t1 - t0 > PM_CELL_MAX) {
-        atomicOr(status, ST_CAPACITY);
-    } else {
-        const float xs = xl32[s], ys = xl32[n + s], zs = xl32[2 * n + s];
-        const float sx = __fmul_rn((float)dx, rp.wf[0]);
-        const float sy = __fmul_rn((float)dy, rp.wf[1]);
-        const float sz = __fmul_rn((float)dz, rp.wf[2]);
-        const float rc2 = rp.rc2f;
-        // own cell: the later molecules only
-#pragma unroll 4
-        for (int t = k == 13 ? (int)s + 1 : t0; t < t1; t++) {
-            const float ex = __fadd_rn(__fsub_rn(xl32[t], xs), sx);
-            const float ey = __fadd_rn(__fsub_rn(xl32[n + t], ys), sy);
-            const float ez = __fadd_rn(__fsub_rn(xl32[2 * n + t], zs), sz);
-            const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)), __fmul_rn(ez, ez));
-            if (d2 < rc2) word |= 1u << (t - t0);
-        }
-    }
-    pm[(long long)(k - 13) * n + s] = word;
-}
-
-// K2: exclusive scan of the cell counts (one CTA of 1024 threads, each owns a
-// contiguous chunk) and the largest occupancy
+// K2: exclusive scan of the cell counts (one CTA of 1024 threads, each warp
+// owns a contiguous segment) and the largest occupancy
 __global__ void __launch_bounds__(1024) k_scan(long long ncell, const int* __restrict__ count,
                                                int* __restrict__ start, int* __restrict__ maxocc)
 {
-    __shared__ int s_part[1024];
+    // warp w owns the contiguous segment [w seg, (w + 1) seg) of the cells and
+    // reads it 32 consecutive counts at a time (coalesced): its total and
+    // largest count first, then, after a scan of the 32 totals, the exclusive
+    // prefix of every cell with a shuffle scan per 32 and a running carry
+    __shared__ int s_tot[32];
     __shared__ int s_max[32];
-    const int tid = threadIdx.x;
-    long long chunk = (ncell + 1023) / 1024;
-    long long lo = tid * chunk, hi = lo + chunk < ncell ? lo + chunk : ncell;
-    int sum = 0, mx = 0;
-    for (long long c = lo; c < hi; c++) {
-        int v = count[c];
-        sum += v;
-        mx = v > mx ? v : mx;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long seg = ((ncell + 31) / 32 + 31) / 32 * 32;
+    const long long lo = warp * seg, hi = lo + seg < ncell ? lo + seg : ncell;
+    int tot = 0, mx = 0;
+    for (long long c0 = lo; c0 < hi; c0 += 32) {
+        const long long c = c0 + lane;
+        const int v = c < hi ? count[c] : 0;
+        tot += __reduce_add_sync(FULL, v);
+        mx = max(mx, (int)__reduce_max_sync(FULL, (unsigned)v));
     }
-    s_part[tid] = sum;
-    for (int o = 16; o > 0; o >>= 1) {
-        int v = __shfl_down_sync(0xffffffffu, mx, o);
-        mx = v > mx ? v : mx;
+    if (lane == 0) {
+        s_tot[warp] = tot;
+        s_max[warp] = mx;
     }
-    if ((tid & 31) == 0) s_max[tid >> 5] = mx;
     __syncthreads();
-    // Hillis-Steele inclusive scan over the 1024 partial sums
-    for (int o = 1; o < 1024; o <<= 1) {
-        int v = tid >= o ? s_part[tid - o] : 0;
-        __syncthreads();
-        s_part[tid] += v;
-        __syncthreads();
+    if (warp == 0) {
+        const int t = s_tot[lane];
+        int incl = t;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += u;
+        }
+        s_tot[lane] = incl - t;  // exclusive: the cells before warp lane's segment
+        const int m = (int)__reduce_max_sync(FULL, (unsigned)s_max[lane]);
+        if (lane == 0) *maxocc = m;
+        if (lane == 31) start[ncell] = incl;
     }
-    int run = tid > 0 ? s_part[tid - 1] : 0;
-    for (long long c = lo; c < hi; c++) {
-        start[c] = run;
-        run += count[c];
-    }
-    if (tid == 1023) start[ncell] = s_part[1023];
-    if (tid == 0) {
-        int m = 0;
-        for (int q = 0; q < 32; q++) m = s_max[q] > m ? s_max[q] : m;
-        *maxocc = m;
+    __syncthreads();
+    int carry = s_tot[warp];
+    for (long long c0 = lo; c0 < hi; c0 += 32) {
+        const long long c = c0 + lane;
+        const int v = c < hi ? count[c] : 0;
+        int incl = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += u;
+        }
+        if (c < hi) start[c] = carry + incl - v;
+        carry += __shfl_sync(FULL, incl, 31);
     }
 }
 
@@ -725,15 +685,6 @@ cudaError_t launch_build_cells(const Batch& b, double* x, int* cell_of, int* ran
         k_cell_order<<<(unsigned)((b.ncell + 3) / 4), 128, 0, st>>>(b, x, start, perm, xl, xl32,
                                                                   cell_sorted);
     }
-    return cudaGetLastError();
-}
-
-cudaError_t launch_pair_masks(const Batch& b, const int* start, const float* xl32,
-                              const int* cell_sorted, unsigned* pm, int* status, cudaStream_t st)
-{
-    if (b.ntot <= 0) return cudaSuccess;
-    const dim3 grid((unsigned)((b.ntot + 127) / 128), PM_WORDS);
-    k_pair_masks<<<grid, 128, 0, st>>>(b, start, xl32, cell_sorted, pm, status);
     return cudaGetLastError();
 }
 

@@ -86,6 +86,24 @@ def test_cells_bit_exact(atm3, maker):
     assert np.array_equal(xw, ref["xw"])
 
 
+def test_cells_bit_exact_many_cells(atm3):
+    """A dilute gas over 68^3 = 314,432 cells: the scan of the cell counts runs
+    over segments of many 32-cell chunks per warp; cell arrays bit-exact
+    against the oracle's cell build."""
+    rng = np.random.default_rng(78)
+    n, box = 100000, 171.0
+    x = rng.uniform(0.0, box, size=(3, n))
+    prm = oracle.params(np.array([box, box, box]), 2.5, 0.073)
+    ref = oracle.build_cells(prm, x)
+    with atm3.AtmSystem(np.array([box, box, box]), n) as s:
+        s.set_state(x)
+        s.build_cells()
+        c = s.get_cells()
+    assert int(np.prod(c["ncell"])) == 68 ** 3
+    assert np.array_equal(c["cell_start"], ref["cell_start"])
+    assert np.array_equal(c["perm"], ref["perm"])
+
+
 # ------------------------------------------------------------------ forces, small liquid
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32c"])
