@@ -181,11 +181,12 @@ def ncell_of(cfg):
 
 def kernel_rooflines(prof, steps, n, ncell, atm_roof, pk):
     """Achieved fraction of the bounding roofline for each phase of a step:
-    the ATM kernel against the FP32 pipe (from `roofline`), the cell build and
-    the kicks against the measured HBM bandwidth (algorithmic bytes)."""
+    the ATM kernel against the FP32 pipe (from `roofline`, the timed steps),
+    the cell build and the kicks (from prof, the split pass) against the
+    measured HBM bandwidth (algorithmic bytes)."""
     hbm = pk.get("hbm_gbs")
     out = {"atm_triplets": {"bound": "alu", "frac": atm_roof["frac"],
-                            "ms_per_step": prof["ms_atm"] / max(1, prof["n_atm_launches"])}}
+                            "ms_per_step": atm_roof["ms_per_launch"]}}
     per_step = max(1, steps)
     for name, key, nbytes in (("cell_build", "ms_cells", CELL_BYTES_PER_MOL * n + CELL_BYTES_PER_CELL * ncell),
                               ("kicks_and_reductions", "ms_md", KICK_BYTES_PER_MOL * n)):
@@ -291,10 +292,13 @@ def run_ours(args):
         tuning = sysm.autotune(args.trav, args.trunc, args.prec, reps=3)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
-    def timed(trav, trunc, prec, steps, warmup, clocks=None):
+    def timed(trav, trunc, prec, steps, warmup, clocks=None, forces_only=True):
+        # the timed steps record timestamps around the force evaluations only
+        # (the roofline's kernel time); the other phases' split comes from an
+        # untimed pass with every launch group bracketed
         sysm.step(warmup, trav, trunc, prec)
         torch.cuda.synchronize()
-        sysm.set_profiling(True)
+        sysm.set_profiling(True, forces_only=forces_only)
         if ws > 1:
             dist.barrier()
         torch.cuda.synchronize()
@@ -326,6 +330,8 @@ def run_ours(args):
     main = timed(args.trav, args.trunc, args.prec, args.steps, args.warmup, clocks)
     ms_step = main["ms"] / args.steps
     value = n * ws * args.steps / (main["ms"] * 1e-3)
+    split_steps = max(3, min(args.steps, 50))
+    split = timed(args.trav, args.trunc, args.prec, split_steps, 1, None, forces_only=False)
 
     # roofline of the dominant kernel (ATM triplets): useful flops per launch / launch time
     prof = main["prof"]
@@ -550,8 +556,10 @@ def run_ours(args):
             "gpu_launches_per_step": launches_per_step,
             "clocks": main["clocks"],
             "force_error": force_err,
-            "profile_ms": {k: prof[k] for k in ("ms_cells", "ms_lj", "ms_atm", "ms_md")},
-            "kernels": kernel_rooflines(prof, args.steps, n, ncell_of(cfg), roofline, pk),
+            "profile_ms": dict({k: split["prof"][k] for k in ("ms_cells", "ms_lj", "ms_atm", "ms_md")},
+                               steps=split_steps,
+                               note="every launch group timed, an untimed pass after the timed steps"),
+            "kernels": kernel_rooflines(split["prof"], split_steps, n, ncell_of(cfg), roofline, pk),
             "counts": {k: int(main["res"][k]) for k in ("n_cand3", "n_int3", "n_cand2", "n_int2")},
             "variants": variants,
             "surrogate": surrogate,

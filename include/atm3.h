@@ -565,7 +565,10 @@ typedef struct {
     int64_t n_launches, n_atm_launches;
 } atm_profile;
 
-/* on != 0: start recording (and reset the sums and counters); 0: stop. */
+/* on = 1: start recording every launch group (and reset the sums and
+ * counters); on = 2: the same for the force evaluations only (ms_atm; the
+ * other sums stay 0), which puts fewer timestamps between a step's kernels;
+ * 0: stop. */
 atm_status atm_set_profiling(atm_ctx* ctx, int on);
 /* Synchronises the stream and returns the sums. */
 atm_status atm_get_profile(atm_ctx* ctx, atm_profile* out);

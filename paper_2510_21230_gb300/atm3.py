@@ -421,8 +421,10 @@ class AtmSystem:
         self._check(self._lib.atm_density_reset(self._ctx))
 
     # -- profiling (device time of the library's kernels, launch counts)
-    def set_profiling(self, on=True):
-        self._check(self._lib.atm_set_profiling(self._ctx, 1 if on else 0))
+    def set_profiling(self, on=True, forces_only=False):
+        """Device-time profile of the library's launch groups; forces_only
+        times the force evaluations alone (fewer timestamps in a step)."""
+        self._check(self._lib.atm_set_profiling(self._ctx, (2 if forces_only else 1) if on else 0))
 
     def get_profile(self):
         p = Profile()

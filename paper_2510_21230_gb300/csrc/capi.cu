@@ -45,9 +45,11 @@ static int kernels_per_step(int trav, int trunc, int prec, int ncls)
 
 enum { PK_CELLS = 0, PK_LJ = 1, PK_ATM = 2, PK_MD = 3 };
 
-cudaEvent_t atm3::ctx_prof_begin(atm_ctx* c)
+cudaEvent_t atm3::ctx_prof_begin(atm_ctx* c, int kind)
 {
-    if (!c->prof) return nullptr;
+    // level 2 times the force evaluations only: fewer timestamps between the
+    // step's other kernels
+    if (!c->prof || (c->prof == 2 && kind != PK_ATM)) return nullptr;
     cudaEvent_t e = nullptr;
     if (!c->ev_pool.empty()) {
         e = c->ev_pool.back();
@@ -159,7 +161,10 @@ atm_status atm3::ctx_sync_and_check(atm_ctx* c)
 {
     CU(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->st));
     CU(cudaStreamSynchronize(c->st));
-    prof_drain(c);
+    // the profiling events are folded in by atm_get_profile, or here once
+    // many are pending: a step's own synchronisation (the cell build's) is on
+    // its critical path, and querying events there would lengthen it
+    if (c->ev_live.size() >= 4096) prof_drain(c);
     return check_status(c);
 }
 
@@ -425,7 +430,7 @@ extern "C" atm_status atm_set_state_dev(atm_ctx* c, const double* x_dev, const d
 // cell build kernels only (no host synchronisation; capturable)
 static atm_status launch_cells(atm_ctx* c)
 {
-    cudaEvent_t ev = ctx_prof_begin(c);
+    cudaEvent_t ev = ctx_prof_begin(c, PK_CELLS);
     CU(launch_build_cells(c->b, c->x, c->cell_of, c->rank, c->count, c->start, c->perm, c->xl,
                           c->xl32, c->cell_sorted, c->d_maxocc, c->d_status, c->wide_cells,
                           c->st));
@@ -573,13 +578,13 @@ atm_status atm3::ctx_enqueue_forces(atm_ctx* c, int trav, int trunc, int prec, i
     cudaEvent_t ev;
     if (prec != ATM_SURROGATE && !fused) {
         // (the surrogate's descriptor pass computes LJ from the same neighbours)
-        ev = ctx_prof_begin(c);
+        ev = ctx_prof_begin(c, PK_LJ);
         CU(enqueue_lj(j));
         ctx_prof_end(c, PK_LJ, ev);
         c->n_launch += 1;
     }
 
-    ev = ctx_prof_begin(c);
+    ev = ctx_prof_begin(c, PK_ATM);
     if (prec == ATM_SURROGATE) {
         atm_status s = sur_enqueue_atm(c);
         if (s != ATM_OK) return s;
@@ -621,7 +626,7 @@ static atm_status enqueue_reduce(atm_ctx* c)
     r.ke = c->ke;
     r.part = c->d_part;
     r.out = c->d_res;
-    cudaEvent_t ev = ctx_prof_begin(c);
+    cudaEvent_t ev = ctx_prof_begin(c, PK_MD);
     CU(launch_final_reduce(r, c->st));
     ctx_prof_end(c, PK_MD, ev);
     c->n_launch += 2;
@@ -660,7 +665,7 @@ extern "C" atm_status atm_compute_forces(atm_ctx* c, atm_traversal trav, atm_tru
     }
     atm_status s = ctx_enqueue_forces(c, trav, trunc, prec, c->unit_max[trav]);
     if (s != ATM_OK) return s;
-    cudaEvent_t ev = ctx_prof_begin(c);
+    cudaEvent_t ev = ctx_prof_begin(c, PK_MD);
     CU(launch_kinetic(c->n, c->v, c->ke, c->st));
     ctx_prof_end(c, PK_MD, ev);
     c->n_launch += 1;
@@ -733,7 +738,7 @@ extern "C" atm_status atm_get_state(atm_ctx* c, double* x, double* v)
 // forces (capacity mcap), kick
 static atm_status enqueue_step(atm_ctx* c, int trav, int trunc, int prec, int mcap)
 {
-    cudaEvent_t ev = ctx_prof_begin(c);
+    cudaEvent_t ev = ctx_prof_begin(c, PK_MD);
     CU(launch_kick(c->b, c->perm, c->f_lj, c->f_atm, c->x, c->v, 1, c->ke, c->st));
     ctx_prof_end(c, PK_MD, ev);
     c->n_launch += 1;
@@ -741,7 +746,7 @@ static atm_status enqueue_step(atm_ctx* c, int trav, int trunc, int prec, int mc
     if (s != ATM_OK) return s;
     s = ctx_enqueue_forces(c, trav, trunc, prec, mcap, true);
     if (s != ATM_OK) return s;
-    ev = ctx_prof_begin(c);
+    ev = ctx_prof_begin(c, PK_MD);
     CU(launch_kick(c->b, c->perm, c->f_lj, c->f_atm, c->x, c->v, 0, c->ke, c->st));
     ctx_prof_end(c, PK_MD, ev);
     c->n_launch += 1;
@@ -793,9 +798,9 @@ static atm_status run_graph_steps(atm_ctx* c, int nsteps, int trav, int trunc, i
     if (!c->graph || memcmp(key, c->graph_key, sizeof(key)) != 0) {
         drop_graph(c);
         cudaStream_t keep = c->st;
-        const bool keep_prof = c->prof;
+        const int keep_prof = c->prof;
         const long long nl = c->n_launch, na = c->n_atm;
-        c->prof = false;
+        c->prof = 0;
         c->st = c->cap_st;
         cudaGraph_t g = nullptr;
         CU(cudaStreamBeginCapture(c->cap_st, cudaStreamCaptureModeThreadLocal));
@@ -815,7 +820,7 @@ static atm_status run_graph_steps(atm_ctx* c, int nsteps, int trav, int trunc, i
         CU(e);
         memcpy(c->graph_key, key, sizeof(key));
     }
-    cudaEvent_t ev = ctx_prof_begin(c);
+    cudaEvent_t ev = ctx_prof_begin(c, PK_MD);
     for (int k = 0; k < nsteps; k++) CU(cudaGraphLaunch(c->graph, c->st));
     ctx_prof_end(c, PK_MD, ev);
     c->n_launch += (long long)nsteps * kernels_per_step(trav, trunc, prec, cls[0]);
@@ -894,7 +899,7 @@ extern "C" atm_status atm_step(atm_ctx* c, int nsteps, atm_traversal trav, atm_t
     }
     if (!done) {
         for (int k = 0; k < nsteps; k++) {
-            cudaEvent_t ev = ctx_prof_begin(c);
+            cudaEvent_t ev = ctx_prof_begin(c, PK_MD);
             CU(launch_kick(c->b, c->perm, c->f_lj, c->f_atm, c->x, c->v, 1, c->ke, c->st));
             ctx_prof_end(c, PK_MD, ev);
             c->n_launch += 1;
@@ -911,7 +916,7 @@ extern "C" atm_status atm_step(atm_ctx* c, int nsteps, atm_traversal trav, atm_t
                 if (s != ATM_OK) return s;
             }
             if (prec == ATM_SURROGATE) sur_count_step(c);
-            ev = ctx_prof_begin(c);
+            ev = ctx_prof_begin(c, PK_MD);
             CU(launch_kick(c->b, c->perm, c->f_lj, c->f_atm, c->x, c->v, 0, c->ke, c->st));
             ctx_prof_end(c, PK_MD, ev);
             c->n_launch += 1;
@@ -1080,8 +1085,8 @@ extern "C" atm_status atm_autotune(atm_ctx* c, atm_traversal trav, atm_truncatio
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
-    const bool keep_prof = c->prof;
-    c->prof = false;
+    const int keep_prof = c->prof;
+    c->prof = 0;
     float best = 1e30f;
     int best_code = 1;
     atm_status s = ATM_OK;
@@ -1271,7 +1276,7 @@ extern "C" atm_status atm_set_profiling(atm_ctx* c, int on)
     CU(cudaSetDevice(c->device));
     CU(cudaStreamSynchronize(c->st));
     prof_drain(c);
-    c->prof = on != 0;
+    c->prof = on == 2 ? 2 : (on != 0 ? 1 : 0);
     for (double& v : c->prof_ms) v = 0.0;
     c->n_launch = 0;
     c->n_atm = 0;

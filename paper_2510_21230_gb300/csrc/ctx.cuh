@@ -103,7 +103,7 @@ struct atm_ctx {
     cudaGraphExec_t graph = nullptr;
     int graph_key[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
     // profiling: event pairs around launch groups, summed per kind
-    bool prof = false;
+    int prof = 0;  // profiling: 0 off, 1 every launch group, 2 force evaluations only
     struct EvRec {
         cudaEvent_t a, b;
         int kind;
@@ -132,7 +132,7 @@ atm_status ctx_want_wide(atm_ctx* c, int trav);
 atm_status ctx_enqueue_forces(atm_ctx* c, int trav, int trunc, int prec, int mcap,
                               bool fuse_lj = false);
 // profiling of a launch group (kind: 0 cells, 1 LJ, 2 ATM, 3 MD)
-cudaEvent_t ctx_prof_begin(atm_ctx* c);
+cudaEvent_t ctx_prof_begin(atm_ctx* c, int kind);
 void ctx_prof_end(atm_ctx* c, int kind, cudaEvent_t a);
 
 // surrogate hooks (sur_capi.cu)
