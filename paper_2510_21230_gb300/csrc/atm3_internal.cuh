@@ -173,11 +173,13 @@ struct AtmArgs {
     int use_d;                // block kernel, product rule: dense FP32 distance table in smem
     int acc_mode;             // block kernel, product rule: 0 dense pair scalars, 1 per-molecule atomics
     int pcap;                 // owner kernels: partner-list capacity per warp
-    // 3c08 pair rule in a velocity-Verlet step: the unit also evaluates the LJ
-    // forces of its c08 cell pairs (pairs whose two cells have their bounding
-    // box anchored at the unit) and adds them to the same pair scalars, so
-    // fs receives LJ + ATM; per-unit E2, W2 and counts go to unit_ew2 /
-    // unit_cnt2 ([2 * ncell] each: E2, W2; half-shell candidates, 2 x pairs)
+    // pair rule of a block traversal in a velocity-Verlet step: the unit also
+    // evaluates the LJ forces of its own pairs (3c08 and the corner-anchored
+    // 3c08: pairs whose two cells have their bounding box anchored at the
+    // unit; 3c18: pairs with a molecule in the base cell) and adds them to the
+    // same pair scalars, so fs receives LJ + ATM; per-unit E2, W2 and counts
+    // go to unit_ew2 / unit_cnt2 ([2 * ncell] each: E2, W2; half-shell
+    // candidates, pairs)
     int lj;
     double* unit_ew2;
     unsigned long long* unit_cnt2;

@@ -183,7 +183,7 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
             A.unit_ew[2 * u + 1] = 0.0;
             A.unit_cnt[2 * u] = 0ull;
             A.unit_cnt[2 * u + 1] = 0ull;
-            if (PAIR && (TRAV == 2 || TRAV == 4) && A.lj) {
+            if (PAIR && (TRAV == 1 || TRAV == 2 || TRAV == 4) && A.lj) {
                 A.unit_ew2[2 * u] = 0.0;
                 A.unit_ew2[2 * u + 1] = 0.0;
                 A.unit_cnt2[2 * u] = 0ull;
@@ -204,7 +204,7 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
             A.unit_ew[2 * u + 1] = 0.0;
             A.unit_cnt[2 * u] = 0ull;
             A.unit_cnt[2 * u + 1] = 0ull;
-            if (PAIR && (TRAV == 2 || TRAV == 4) && A.lj) {
+            if (PAIR && (TRAV == 1 || TRAV == 2 || TRAV == 4) && A.lj) {
                 A.unit_ew2[2 * u] = 0.0;
                 A.unit_ew2[2 * u + 1] = 0.0;
                 A.unit_cnt2[2 * u] = 0ull;
@@ -221,9 +221,16 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
     const R rc6 = F64 ? (R)rp.rc6 : (R)rp.rc6f;
     const R nu = F64 ? (R)rp.nu : (R)rp.nuf;
     const unsigned lt_mask = (1u << lane) - 1u;
-    // LJ of the unit's c08 cell pairs (3c08 pair rule in a step): the LJ
-    // kernel's arithmetic on the same canonical displacement
-    const bool LJ = PAIR && (TRAV == 2 || TRAV == 4) && A.lj != 0;
+    // LJ of the unit's own cell pairs (pair rule in a step): 3c08 and the
+    // corner-anchored 3c08 the c08 cell pairs (the pair's cells anchored at
+    // the unit), 3c18 the pairs with a molecule in the base cell (the
+    // half-shell of the base cell); the LJ kernel's arithmetic on the same
+    // canonical displacement
+    const bool LJ = PAIR && (TRAV == 1 || TRAV == 2 || TRAV == 4) && A.lj != 0;
+    // p < q in staging order, so a pair with a base-cell molecule has it at p
+    auto lj_own = [&](int p, int q) -> bool {
+        return TRAV == 1 ? sslot[p] == 0 : (sslot[p] & sslot[q]) == 0;
+    };
     const R sig2 = F64 ? (R)rp.sig2 : (R)rp.sig2f;
     const R eps4 = F64 ? (R)rp.eps4 : (R)rp.eps4f;
     const R eps24 = F64 ? (R)rp.eps24 : (R)rp.eps24f;
@@ -602,7 +609,7 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
                 for (int p = warp; p < M; p += nwarps)
                     for (int w = p >> 5; w < Wm; w++) {
                         const int q = (w << 5) + lane;
-                        if (((adj[p * W + w] >> lane) & 1u) && (sslot[p] & sslot[q]) == 0) {
+                        if (((adj[p * W + w] >> lane) & 1u) && lj_own(p, q)) {
                             R dx, dy, dz;
                             const R g = lj_pair(disp(p, q, dx, dy, dz));
                             acc_add(p, g * dx);
@@ -622,7 +629,7 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
         for (int e = tid; e < s_edges; e += blockDim.x) {
             const unsigned x = el[e];
             const int p = (int)(x & 0xffffu), q = (int)(x >> 16);
-            if ((sslot[p] & sslot[q]) == 0) {
+            if (lj_own(p, q)) {
                 R a;
                 if (F64) {
                     a = ED[4 * e + 3];
@@ -639,7 +646,7 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
         // through the triplet phase; the reduction's barriers also order the
         // pair-scalar writes above before the triplet phase)
         unsigned long long cand2 = 0;
-        if (warp == 0) cand2 = unit_pair_candidates_warp<S>(s_beg);
+        if (warp == 0) cand2 = unit_pair_candidates_warp<TRAV, S>(s_beg);
         unit_reduce_store2<NWB>(e2sum.get(), w2sum.get(), (unsigned long long)n2, cand2, A.unit_ew2,
                               A.unit_cnt2, u, s_red, s_redn);
     }

@@ -249,11 +249,13 @@ __device__ inline unsigned long long unit_candidates_warp(const int* beg)
     return cand;
 }
 
-// Candidate pairs of the c08 2-body traversal in one 2x2x2 block: the
-// anchor cell's own pairs and the pairs of every two slots whose bounding
-// box starts at the anchor (13 slot pairs); summed over all blocks this is
-// the half-shell count.  Lane 0 of the calling warp gets the total.
-template <int S>
+// Candidate pairs of a unit's own 2-body share: 3c08 / corner-anchored 3c08,
+// the c08 traversal in one 2x2x2 block -- the anchor cell's own pairs and the
+// pairs of every two slots whose bounding box starts at the anchor (13 slot
+// pairs); 3c18, the base cell's half-shell -- its own pairs and its pairs
+// with the 13 forward cells.  Summed over all units either is the half-shell
+// count.  Lane 0 of the calling warp gets the total.
+template <int TRAV, int S>
 __device__ inline unsigned long long unit_pair_candidates_warp(const int* beg)
 {
     const int lane = threadIdx.x & 31;
@@ -262,7 +264,8 @@ __device__ inline unsigned long long unit_pair_candidates_warp(const int* beg)
         const unsigned long long Ns = (unsigned long long)(beg[lane + 1] - beg[lane]);
         if (lane == 0) c = Ns < 2 ? 0ull : Ns * (Ns - 1) / 2;
         for (int t = lane + 1; t < S; t++)
-            if ((lane & t) == 0) c += Ns * (unsigned long long)(beg[t + 1] - beg[t]);
+            if (TRAV == 1 ? lane == 0 : (lane & t) == 0)
+                c += Ns * (unsigned long long)(beg[t + 1] - beg[t]);
     }
     for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
     return c;

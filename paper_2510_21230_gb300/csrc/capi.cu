@@ -21,10 +21,11 @@ namespace {
 constexpr int DENS_MAX_BINS = 4096;
 constexpr int CELL_KERNELS = 5;  // wrap/bin, scan, unit sizes, scatter, per-cell order
 
-// steps under the 3c08 (or corner-anchored 3c08) pair rule evaluate LJ inside the ATM units
+// steps under the 3c08, corner-anchored 3c08 or 3c18 pair rule evaluate LJ inside the ATM units
 static bool lj_fused(int trav, int trunc, int prec)
 {
-    return (trav == ATM_3C08 || trav == ATM_3C08A) && trunc == ATM_TRUNC_PAIR && prec != ATM_SURROGATE;
+    return (trav == ATM_3C08 || trav == ATM_3C08A || trav == ATM_3C18) && trunc == ATM_TRUNC_PAIR &&
+           prec != ATM_SURROGATE;
 }
 
 // unit size classes the autotuner chooses among for the block traversals:

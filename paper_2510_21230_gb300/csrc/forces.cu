@@ -113,7 +113,7 @@ static cudaError_t launch_atm_one(const ForceJob& j, size_t* smem_set, bool* cap
         if (e != cudaSuccess) return e;
         if (smem_set && !j.det) *smem_set = P.smem;
     }
-    const int lj = j.lj && (j.trav == 2 || j.trav == 4) && j.trunc == 0;
+    const int lj = j.lj && (j.trav == 1 || j.trav == 2 || j.trav == 4) && j.trunc == 0;
     int ctas = 0;
     if (j.persistent && work) {
         int per_sm = j.prec == 0 ? atm_occupancy_fp64(j.trav, j.trunc, P.nwarps, P.smem, j.det)
@@ -200,7 +200,7 @@ static cudaError_t enqueue_atm_launches(const ForceJob& j, size_t* smem_set, boo
         e = cudaMemsetAsync(j.f_atm, 0, 3 * (size_t)j.b.ntot * sizeof(double), j.st);
         if (e != cudaSuccess) return e;
     }
-    const int lj = j.lj && (j.trav == 2 || j.trav == 4) && j.trunc == 0;
+    const int lj = j.lj && (j.trav == 1 || j.trav == 2 || j.trav == 4) && j.trunc == 0;
     if (lj && j.b.ntot > 0) {  // the units write LJ + ATM into f_atm
         e = cudaMemsetAsync(j.f_lj, 0, 3 * (size_t)j.b.ntot * sizeof(double), j.st);
         if (e != cudaSuccess) return e;

@@ -38,8 +38,8 @@ struct ForceJob {
     int persistent;          // 1: persistent grid over a unit counter
     int nwarps;              // 0: the plan's default, else 4 or 8
     cudaStream_t st;
-    // 3c08 / corner-anchored 3c08, pair rule: LJ evaluated inside the ATM
-    // units (f_atm receives LJ + ATM, f_lj is zeroed; E2, W2 and the pair
+    // 3c08 / corner-anchored 3c08 / 3c18, pair rule: LJ evaluated inside the
+    // ATM units (f_atm receives LJ + ATM, f_lj is zeroed; E2, W2 and the pair
     // counts go to unit_ew2 / unit_cnt2 instead of mol_ew / mol_cnt)
     int lj = 0;
     double* unit_ew2 = nullptr;

@@ -177,12 +177,14 @@ def test_nve_product_rule_drift_matches_oracle(atm3):
         assert p == pytest.approx(p_ref, abs=1e-3 * abs(p_ref) + 1e-4), prec
 
 
-@pytest.mark.parametrize("trav,prec", [("3c08", "fp32c"), ("3c08", "fp64"), ("3c08a", "fp32c")])
+@pytest.mark.parametrize("trav,prec", [("3c08", "fp32c"), ("3c08", "fp64"), ("3c08a", "fp32c"),
+                                       ("3c18", "fp32c"), ("3c18", "fp64")])
 def test_step_with_lj_inside_the_units_equals_separate_kernels(atm3, trav, prec):
-    """A step under the 3c08 pair rule evaluates LJ inside the ATM units (the
-    c08 cell pairs of each block): same counts, energies and total force as
-    the separate LJ and ATM kernels on the same state; asking for the LJ or
-    ATM part afterwards re-evaluates them apart."""
+    """A step under the 3c08 or 3c18 pair rule evaluates LJ inside the ATM
+    units (the c08 cell pairs of each block; the base cell's half-shell pairs
+    of each 3c18 unit): same counts, energies and total force as the separate
+    LJ and ATM kernels on the same state; asking for the LJ or ATM part
+    afterwards re-evaluates them apart."""
     rtol = 1e-10 if prec == "fp64" else 2e-5
     cfg = synth.homogeneous(4000, 0.8, 1.0, seed=1100)
     with atm3.AtmSystem(cfg["box"], cfg["n"], nu=NU, dt=0.002) as s:
