@@ -71,12 +71,16 @@ cudaError_t atm_attr_t(int trav, int trunc, size_t smem)
 }
 
 // resident CTAs per SM of the kernel at this block size and shared memory
+// (the kernel's dynamic shared-memory limit is raised to smem first: below
+// it the query answers 0, and the answer would depend on which launches came
+// before)
 template <typename R, bool DET>
 int atm_occupancy_t(int trav, int trunc, int nwarps, size_t smem)
 {
     const AtmKernel<R> k = atm_kernel<R, DET>(trav, trunc);
     int nb = 0;
-    if (k) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, 32 * nwarps, smem);
+    if (k && atm_attr_t<R, DET>(trav, trunc, smem) == cudaSuccess)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, 32 * nwarps, smem);
     return nb;
 }
 

@@ -495,7 +495,9 @@ extern "C" atm_status atm_get_cells(atm_ctx* c, int32_t* cell_of, int32_t* cell_
 // launch options of one force evaluation: the tuned choice, else the context's
 // options; cls = {classes, first bound, second bound} (1 class: all units in
 // one launch)
-static void launch_choice(const atm_ctx* c, int trav, int trunc, int prec, int& persistent,
+static int atm_ctas_per_sm(const atm_ctx* c, int trav, int trunc, int prec, int nwarps, int mcap);
+
+static void launch_choice(atm_ctx* c, int trav, int trunc, int prec, int mcap, int& persistent,
                           int& nwarps, int cls[3])
 {
     int t = c->tuned[prec][trav][trunc];
@@ -507,6 +509,24 @@ static void launch_choice(const atm_ctx* c, int trav, int trunc, int prec, int& 
         persistent = c->opt_persistent;
         nwarps = c->opt_nwarps;
         for (int k = 0; k < 3; k++) cls[k] = c->opt_cls[k];
+        if (nwarps == 0 && prec == ATM_FP32C && trunc == ATM_TRUNC_PAIR && !c->det &&
+            (trav == ATM_3C18 || trav == ATM_3C08 || trav == ATM_3C08A) && mcap > 0) {
+            // without a tuned choice: 4 or 8 warps, whichever keeps more warps
+            // resident per SM for this unit size (4 on a tie).  Measured
+            // (256k / 32k liquids): 3c08 1.20 / 0.27 ms at 4 and 1.50 / 0.23 ms
+            // at 8 warps, 3c18 1.98 / 0.85 at 4 and 1.70 / 0.55 at 8.  (Not
+            // the deterministic mode: its 8-byte scalars change the balance,
+            // and 8 warps measured slower there, 1.87 against 1.70 ms.)
+            int* e = c->nw_auto[trav][trunc];
+            const int band = mcap / 8 + 1;
+            if (e[0] != band) {
+                const int w4 = 4 * atm_ctas_per_sm(c, trav, trunc, prec, 4, mcap);
+                const int w8 = 8 * atm_ctas_per_sm(c, trav, trunc, prec, 8, mcap);
+                e[0] = band;
+                e[1] = w8 > w4 ? 8 : 4;
+            }
+            nwarps = e[1];
+        }
     }
     if (trav == ATM_3C01 || trav == ATM_3CW) {
         nwarps = 0;
@@ -563,7 +583,10 @@ atm_status atm3::ctx_enqueue_forces(atm_ctx* c, int trav, int trunc, int prec, i
     j.persistent = 0;
     j.nwarps = 0;
     int cls[3] = {1, 0, 0};
-    if (prec != ATM_SURROGATE) launch_choice(c, trav, trunc, prec, j.persistent, j.nwarps, cls);
+    // (the warps follow the current unit size, also when a graph sizes the
+    // launch for more)
+    if (prec != ATM_SURROGATE)
+        launch_choice(c, trav, trunc, prec, c->unit_max[trav], j.persistent, j.nwarps, cls);
     j.ncls = cls[0];
     j.cuts[0] = cls[1];
     j.cuts[1] = cls[2];
@@ -791,7 +814,8 @@ static int graph_mcap(const atm_ctx* c, int trav, int trunc, int prec, int nwarp
 static atm_status run_graph_steps(atm_ctx* c, int nsteps, int trav, int trunc, int prec)
 {
     int persistent = 0, nwarps = 0, cls[3] = {1, 0, 0};
-    if (prec != ATM_SURROGATE) launch_choice(c, trav, trunc, prec, persistent, nwarps, cls);
+    if (prec != ATM_SURROGATE)
+        launch_choice(c, trav, trunc, prec, c->unit_max[trav], persistent, nwarps, cls);
     const int mcap = graph_mcap(c, trav, trunc, prec, nwarps);
     const int key[8] = {trav, trunc, prec, mcap,
                         persistent + 2 * nwarps + 64 * (use_pair_masks(c, trav, trunc, prec) ? 1 : 0),
@@ -1008,6 +1032,7 @@ extern "C" atm_status atm_set_pair_masks(atm_ctx* c, int on)
     if (on < 0 || on > 1) return ctx_fail(c, ATM_E_INVALID, "on is 0 or 1");
     c->opt_pmask = on;
     memset(c->tuned, 0, sizeof(c->tuned));
+    memset(c->nw_auto, 0, sizeof(c->nw_auto));
     drop_graph(c);
     return ATM_OK;
 }
@@ -1022,6 +1047,7 @@ extern "C" atm_status atm_set_options(atm_ctx* c, int persistent, int nwarps, in
     c->opt_nwarps = nwarps;
     c->opt_graph = graph;
     memset(c->tuned, 0, sizeof(c->tuned));
+    memset(c->nw_auto, 0, sizeof(c->nw_auto));
     drop_graph(c);
     return ATM_OK;
 }
@@ -1050,6 +1076,7 @@ extern "C" atm_status atm_set_deterministic(atm_ctx* c, int on)
     if (on < 0 || on > 1) return ctx_fail(c, ATM_E_INVALID, "on must be 0 or 1");
     c->det = on;
     memset(c->tuned, 0, sizeof(c->tuned));
+    memset(c->nw_auto, 0, sizeof(c->nw_auto));
     drop_graph(c);
     c->forces_valid = false;
     return ATM_OK;
@@ -1067,6 +1094,7 @@ extern "C" atm_status atm_set_unit_classes(atm_ctx* c, int nclass, const int* cu
     c->opt_cls[1] = nclass > 1 ? cuts[0] : 0;
     c->opt_cls[2] = nclass > 2 ? cuts[1] : 0;
     memset(c->tuned, 0, sizeof(c->tuned));
+    memset(c->nw_auto, 0, sizeof(c->nw_auto));
     drop_graph(c);
     return ATM_OK;
 }

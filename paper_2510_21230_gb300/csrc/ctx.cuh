@@ -94,6 +94,9 @@ struct atm_ctx {
     bool pm_3c18 = false;
     // 0 = not tuned, else 1 + persistent + 2 * (nwarps == 8) + 4 * size-class choice
     int tuned[2][atm3::ATM_NTRAV][2] = {};
+    // untuned FP32 pair rule of the block traversals: warps per CTA chosen by
+    // resident warps per SM, cached for a band of unit sizes (mcap / 8)
+    int nw_auto[atm3::ATM_NTRAV][2][2] = {};  // [trav][trunc] = {mcap band + 1, warps}
     // graph of one step, valid for (trav, trunc, prec, mcap, launch choice)
     cudaStream_t cap_st = nullptr;
     // size classes: the small-unit class runs on side_st beside the rest
