@@ -651,11 +651,15 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
                               A.unit_cnt2, u, s_red, s_redn);
     }
     const bool use_acc = PAIR ? !edge_mode : (A.acc_mode == 1);
-    if constexpr (PAIR && !F64) {
-        // decisions and LJ are done with the canonical displacement; the
-        // triplet phase and the gather take the FP32 shifted rows xl + o w
-        // (one rounding per coordinate), so a displacement is one difference
-        // per component and the third side of a triangle costs no load
+    // FP32: once every decision is taken with the canonical displacement (the
+    // pair rule's adjacency and LJ; the product rule's dense distance table),
+    // the triplet phase and the gather take the FP32 shifted rows xl + o w
+    // (one rounding per coordinate), so a displacement is one difference per
+    // component and the third side of a triangle costs no load.  (The product
+    // rule without the table decides from the rows and keeps them.)
+    bool shifted = false;
+    if constexpr (!F64) shifted = PAIR || A.use_d;
+    if (shifted) {
         __syncthreads();
         for (int t = tid; t < M; t += blockDim.x) {
             const float4 a = P4[t], sh = S4[t];
@@ -728,9 +732,25 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
         R dpqx, dpqy, dpqz, dprx, dpry, dprz, dqrx, dqry, dqrz, a, b, c;
         int epq = 0, epr = 0, eqr = 0;
         {
-            a = disp(p, q, dpqx, dpqy, dpqz);
-            b = disp(p, r, dprx, dpry, dprz);
-            c = disp(q, r, dqrx, dqry, dqrz);
+            if constexpr (!F64) {
+                if (shifted) {
+                    const float4 P = S4[p], Qv = S4[q], Rv = S4[r];  // shifted rows
+                    dpqx = Qv.x - P.x; dpqy = Qv.y - P.y; dpqz = Qv.z - P.z;
+                    dprx = Rv.x - P.x; dpry = Rv.y - P.y; dprz = Rv.z - P.z;
+                    dqrx = Rv.x - Qv.x; dqry = Rv.y - Qv.y; dqrz = Rv.z - Qv.z;
+                    a = dpqx * dpqx + dpqy * dpqy + dpqz * dpqz;
+                    b = dprx * dprx + dpry * dpry + dprz * dprz;
+                    c = dqrx * dqrx + dqry * dqry + dqrz * dqrz;
+                } else {
+                    a = disp(p, q, dpqx, dpqy, dpqz);
+                    b = disp(p, r, dprx, dpry, dprz);
+                    c = disp(q, r, dqrx, dqry, dqrz);
+                }
+            } else {
+                a = disp(p, q, dpqx, dpqy, dpqz);
+                b = disp(p, r, dprx, dpry, dprz);
+                c = disp(q, r, dqrx, dqry, dqrz);
+            }
             if (!PAIR) {
                 epq = tri_index(p, q);
                 epr = tri_index(p, r);
@@ -1053,7 +1073,12 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
                 R g = gget(y > m ? tri_index(m, y) : tri_index(y, m));
                 if (g != R(0)) {
                     R dx, dy, dz;
-                    disp(m, y, dx, dy, dz);
+                    if (shifted) {
+                        const float4 Pm4 = S4[m], Y = S4[y];
+                        dx = Y.x - Pm4.x; dy = Y.y - Pm4.y; dz = Y.z - Pm4.z;
+                    } else {
+                        disp(m, y, dx, dy, dz);
+                    }
                     fxs.add(g * dx);
                     fys.add(g * dy);
                     fzs.add(g * dz);
