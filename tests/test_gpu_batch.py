@@ -356,3 +356,25 @@ def test_batch_of_64_replicas_as_benchmarked(atm3, ensemble64):
         assert res[r]["n_int3"] == ref["n_int3"] and res[r]["n_cand3"] == ref["n_cand3"], r
         assert res[r]["e3"] == pytest.approx(ref["e3"], rel=RTOL["fp32c"]), r
         assert close(fa[:, sl], ref["f"], RTOL["fp32c"]), r
+
+
+def test_profiling_levels(atm3):
+    """atm_set_profiling: level 1 times every launch group of a step, level 2
+    the force evaluations only; both count the library's launches; the profile
+    is folded in when it is read."""
+    cfg = synth.homogeneous(4000, 0.8, 1.0, seed=1400)
+    with atm3.AtmSystem(cfg["box"], cfg["n"], nu=NU, dt=0.002) as s:
+        s.set_state(cfg["x"], cfg["v"])
+        s.step(1, "3c08", "pair", "fp32c")
+        out = {}
+        for level in (1, 2):
+            s.set_profiling(True, forces_only=(level == 2))
+            for _ in range(3):
+                s.step(1, "3c08", "pair", "fp32c", sync=False)
+            out[level] = s.get_profile()
+        s.set_profiling(False)
+    full, forces = out[1], out[2]
+    assert full["ms_atm"] > 0 and full["ms_cells"] > 0 and full["ms_md"] > 0
+    assert forces["ms_atm"] > 0 and forces["ms_cells"] == 0 and forces["ms_md"] == 0
+    assert full["n_atm_launches"] == forces["n_atm_launches"] == 3
+    assert full["n_launches"] == forces["n_launches"] > 0
