@@ -265,11 +265,12 @@ __host__ __device__ inline BlockSmem block_smem_plan(int trunc, int mcap, int nw
     p.off_rowpre = o; o = al(o + (pair ? sizeof(unsigned short) * M * p.W : 0));
     p.off_rowoff = o; o = al(o + (pair ? sizeof(int) * (M + 1) : 0));
     p.off_memb = o;   o = al(o + (pair ? sizeof(unsigned) * 8 * p.W : 0));
-    // pair rule: FP64 keeps the edge vectors (dx, dy, dz, r^2) of the unit's
-    // edges (FP64 arithmetic is the scarce resource); FP32 recomputes them
-    // (shared memory is).  Both keep the edge list (p | q << 16).
+    // pair rule: FP64 with use_d keeps the edge vectors (dx, dy, dz, r^2) of
+    // the unit's edges (FP64 work once per edge instead of once per triangle
+    // side); otherwise the triplets take the shifted rows.  Both keep the
+    // edge list (p | q << 16).
     p.off_ed = o;
-    o = al(o + (pair && f64 ? sizeof(R) * 4 * (size_t)gcap : 0));
+    o = al(o + (pair && f64 && use_d ? sizeof(R) * 4 * (size_t)gcap : 0));
     p.off_el = o;     o = al(o + (pair ? sizeof(unsigned) * (size_t)gcap : 0));
     // pair scalars: R, or 64-bit fixed point in the deterministic mode
     const size_t gsz = det ? 8 : sizeof(R);
@@ -334,14 +335,42 @@ inline bool atm_choose_plan_nw(int trav, int trunc, int prec, int mcap, int opti
     }
     const long long npair = (long long)mcap * (mcap - 1) / 2;
     if (trunc == 0) {
-        long long g = npair < 16ll * mcap ? npair : 16ll * mcap;
-        for (;;) {
-            P.gcap = (int)g;
-            P.smem = bytes();
-            if (P.smem <= (size_t)optin || g == 0) break;
-            g /= 2;
+        auto fit = [&](int use_d) -> bool {
+            P.use_d = use_d;
+            long long g = npair < 16ll * mcap ? npair : 16ll * mcap;
+            for (;;) {
+                P.gcap = (int)g;
+                P.smem = bytes();
+                if (P.smem <= (size_t)optin || g == 0) break;
+                g /= 2;
+            }
+            return P.smem <= (size_t)optin;
+        };
+        // (the deterministic mode keeps one arithmetic for every launch form:
+        // the shifted rows)
+        if (prec != 0 || det) return fit(0);
+        // FP64: the edge-vector table when it costs no resident CTA.  CTAs per
+        // SM from shared memory (228 KB per SM, 1 KB reserved per CTA) and from
+        // registers (the FP64 block kernels' cap of 128 per thread).  Measured
+        // (liquids, 3c08 / 3c18 pair FP64): the 256k 3c08 units (2 CTAs either
+        // way) 10.23 ms with the table, 11.97 without; the 256k 3c18 units
+        // (1 CTA with it, 2 without) 16.33 and 13.27; the 32k 3c08 units 1.79
+        // and 1.68.
+        const bool okn = fit(0);
+        const AtmPlan Pn = P;
+        const bool oke = fit(1);
+        const AtmPlan Pe = P;
+        if (!oke || !okn) {
+            P = oke ? Pe : Pn;
+            return oke || okn;
         }
-        return P.smem <= (size_t)optin;
+        const int regs = 65536 / (128 * 32 * P.nwarps);
+        auto ctas = [&](size_t smem) {
+            const int c = (int)(233472 / (smem + 1024));
+            return c < regs ? c : regs;
+        };
+        P = ctas(Pe.smem) >= ctas(Pn.smem) ? Pe : Pn;
+        return true;
     }
     const int modes[3][2] = {{1, 0}, {0, 0}, {0, 1}};
     for (const auto& m : modes) {

@@ -585,7 +585,7 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
                     }
                 }
             }
-            if (F64) {
+            if (F64 && A.use_d) {
                 __syncthreads();
                 for (int e = tid; e < s_edges; e += blockDim.x) {
                     const unsigned x = el[e];
@@ -631,7 +631,7 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
             const int p = (int)(x & 0xffffu), q = (int)(x >> 16);
             if (lj_own(p, q)) {
                 R a;
-                if (F64) {
+                if (F64 && A.use_d) {
                     a = ED[4 * e + 3];
                 } else {
                     R dx, dy, dz;
@@ -659,11 +659,18 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
     // rule without the table decides from the rows and keeps them.)
     bool shifted = false;
     if constexpr (!F64) shifted = PAIR || A.use_d;
+    else shifted = PAIR && !A.use_d;  // FP64 pair rule without the edge-vector table
     if (shifted) {
         __syncthreads();
         for (int t = tid; t < M; t += blockDim.x) {
-            const float4 a = P4[t], sh = S4[t];
-            S4[t] = make_float4(a.x + sh.x, a.y + sh.y, a.z + sh.z, 0.0f);
+            if constexpr (!F64) {
+                const float4 a = P4[t], sh = S4[t];
+                S4[t] = make_float4(a.x + sh.x, a.y + sh.y, a.z + sh.z, 0.0f);
+            } else {
+                px[t] += shx[t];
+                py[t] += shy[t];
+                pz[t] += shz[t];
+            }
         }
         __syncthreads();
     }
@@ -684,7 +691,16 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
             epr = rowoff[p] + rank(p, r);
             eqr = rowoff[q] + rank(q, r);
         }
-        if (F64 && !use_acc) {
+        if (F64 && shifted) {
+            const R Px = px[p], Py = py[p], Pz = pz[p], Qx = px[q], Qy = py[q], Qz = pz[q];
+            const R Rx = px[r], Ry = py[r], Rz = pz[r];
+            dpqx = Qx - Px; dpqy = Qy - Py; dpqz = Qz - Pz;
+            dprx = Rx - Px; dpry = Ry - Py; dprz = Rz - Pz;
+            dqrx = Rx - Qx; dqry = Ry - Qy; dqrz = Rz - Qz;
+            a = dpqx * dpqx + dpqy * dpqy + dpqz * dpqz;
+            b = dprx * dprx + dpry * dpry + dprz * dprz;
+            c = dqrx * dqrx + dqry * dqry + dqrz * dqrz;
+        } else if (F64 && !use_acc) {
             dpqx = ED[4 * epq]; dpqy = ED[4 * epq + 1]; dpqz = ED[4 * epq + 2]; a = ED[4 * epq + 3];
             dprx = ED[4 * epr]; dpry = ED[4 * epr + 1]; dprz = ED[4 * epr + 2]; b = ED[4 * epr + 3];
             dqrx = ED[4 * eqr]; dqry = ED[4 * eqr + 1]; dqrz = ED[4 * eqr + 2]; c = ED[4 * eqr + 3];
@@ -1036,7 +1052,9 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
                     R g = gget(ee);
                     if (g != R(0)) {
                         R dx, dy, dz;
-                        if (F64) {
+                        if (F64 && shifted) {
+                            dx = px[y] - px[m]; dy = py[y] - py[m]; dz = pz[y] - pz[m];
+                        } else if (F64) {
                             dx = ED[4 * ee]; dy = ED[4 * ee + 1]; dz = ED[4 * ee + 2];
                         } else {
                             const float4 Y = S4[y];
@@ -1055,7 +1073,9 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
                     R g = gget(ee);
                     if (g != R(0)) {
                         R dx, dy, dz;
-                        if (F64) {
+                        if (F64 && shifted) {
+                            dx = px[x] - px[m]; dy = py[x] - py[m]; dz = pz[x] - pz[m];
+                        } else if (F64) {
                             dx = -ED[4 * ee]; dy = -ED[4 * ee + 1]; dz = -ED[4 * ee + 2];
                         } else {
                             const float4 X = S4[x];
