@@ -19,9 +19,10 @@
 //     popcounts) and listed as (p, q); FP64 also tabulates their vectors.
 //  3. A warp takes 32 edges (p, q) at a time.  The triangles of an edge are
 //     the set bits r > q of adj[p] & adj[q] & (slots allowed as third member):
-//     counted per lane, prefix-summed over the warp and expanded 32 per round,
-//     so every pair test is shared by all the triplets that contain the pair
-//     and every lane of a round evaluates one triangle.
+//     counted per lane (per word, packed in bytes), prefix-summed over the
+//     warp and expanded 32 per round, so every pair test is shared by all the
+//     triplets that contain the pair and every lane of a round evaluates one
+//     triangle.
 // Product rule
 //  1. Dense FP32 squared distances (or on-the-fly when they do not fit).
 //  3. Every candidate p < q < r of the unit's tasks, enumerated q-major, is
@@ -456,8 +457,8 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
             }
             __syncthreads();
             // adjT by transposing 32 x 32 blocks of adj (row block rb, column
-            // word cb >= rb): lane i holds row rb * 32 + i's word cb, and the
-            // ballot of bit j is column cb * 32 + j's word rb
+            // word cb >= rb): lane i holds row rb * 32 + i's word cb and ends
+            // with column cb * 32 + i's word rb
             const int nblk = Wm * (Wm + 1) / 2;
             for (int it = warp; it < nblk; it += nwarps) {
                 int rb = 0, cb = it;
@@ -467,12 +468,16 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
                 }
                 cb += rb;
                 const int p = (rb << 5) + lane;
-                const unsigned a = p < M ? adj[p * W + cb] : 0u;
+                unsigned col = p < M ? adj[p * W + cb] : 0u;
                 const int jn = min(32, M - (cb << 5));
-                unsigned col = 0u;
-                for (int jj = 0; jj < jn; jj++) {
-                    const unsigned bb = __ballot_sync(FULL, (a >> jj) & 1u);
-                    if (lane == jj) col = bb;
+                // recursive block transpose: at size sz = 16, 8, .., 1 lanes i and
+                // i ^ sz swap the off-diagonal sz x sz sub-blocks of their
+                // 2sz x 2sz block (msk: the bits of the left sub-block columns)
+                unsigned msk = 0x0000ffffu;
+#pragma unroll
+                for (int sz = 16; sz >= 1; sz >>= 1, msk ^= msk << sz) {
+                    const unsigned o = __shfl_xor_sync(FULL, col, sz);
+                    col = (lane & sz) ? (col & ~msk) | ((o >> sz) & msk) : (col & msk) | ((o << sz) & ~msk);
                 }
                 if (lane < jn) adjT[((cb << 5) + lane) * W + rb] = col;
             }
@@ -684,13 +689,8 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
     // lanes call; invalid lanes carry a valid stand-in and discard the result).
     // Adds the (p, r) and (q, r) pair scalars and returns the (p, q) one (0 for
     // invalid lanes and in accumulator mode), which the edge's owner lane sums.
-    auto eval_tri = [&](int p, int q, int r, int epq, bool valid) -> R {
+    auto eval_tri = [&](int p, int q, int r, int epq, int epr, int eqr, bool valid) -> R {
         R dpqx, dpqy, dpqz, dprx, dpry, dprz, dqrx, dqry, dqrz, a, b, c;
-        int epr = 0, eqr = 0;
-        if (!use_acc) {
-            epr = rowoff[p] + rank(p, r);
-            eqr = rowoff[q] + rank(q, r);
-        }
         if (F64 && shifted) {
             const R Px = px[p], Py = py[p], Pz = pz[p], Qx = px[q], Qy = py[q], Qz = pz[q];
             const R Rx = px[r], Ry = py[r], Rz = pz[r];
@@ -864,12 +864,25 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
             if (e0 >= Ework) break;
             const int e = e0 + lane;
             int p = 0, q = 0, v = 0, cnt = 0;
+            unsigned long long cw = 0ull;  // third members per word, byte j = word (q >> 5) + j
             if (e < Ework) {
                 edge_ends(e, p, q);
                 v = sslot[p] & sslot[q];
-                if (!(TRAV == 2 && sslot[p] == 7))  // no later slot completes an anchored set
-                    for (int w = q >> 5; w < Wm; w++) cnt += __popc(kword(p, q, v, w));
+                if (!(TRAV == 2 && sslot[p] == 7)) {  // no later slot completes an anchored set
+                    const int wq = q >> 5;
+                    for (int w = wq; w < Wm; w++) {
+                        const unsigned c = __popc(kword(p, q, v, w));
+                        cnt += (int)c;
+                        if (Wm <= 8) cw |= (unsigned long long)c << ((w - wq) << 3);
+                    }
+                }
             }
+            // inclusive byte sums of the per-word counts (no carry between
+            // bytes while every count of the group is below 128)
+            const bool packed = Wm <= 8 && __all_sync(FULL, cnt < 128);
+            const unsigned c0 = (unsigned)cw * 0x01010101u;
+            const unsigned c1 = Wm > 4 ? (unsigned)(cw >> 32) * 0x01010101u + (c0 >> 24) * 0x01010101u
+                                       : 0x7f7f7f7fu;
             int incl = cnt;
             for (int o = 1; o < 32; o <<= 1) {
                 int t = __shfl_up_sync(FULL, incl, o);
@@ -877,6 +890,8 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
             }
             const int total = __shfl_sync(FULL, incl, 31);
             const int excl = incl - cnt;
+            // the edge's ends and slot mask in one word (staged indices < 2048)
+            const unsigned pqv = (unsigned)p | ((unsigned)q << 11) | ((unsigned)v << 22);
             R gown = R(0);  // (p, q) scalar of this lane's edge, summed over its triangles
             for (int t0 = 0; t0 < total; t0 += 32) {
                 const bool valid = t0 + lane < total;
@@ -887,32 +902,57 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
                     int ec = __shfl_sync(FULL, excl, l + s);
                     if (ec <= t) l += s;
                 }
-                const int pl = __shfl_sync(FULL, p, l);
-                const int ql = __shfl_sync(FULL, q, l);
-                const int vl = __shfl_sync(FULL, v, l);
+                const unsigned pk = __shfl_sync(FULL, pqv, l);
+                const int pl = (int)(pk & 0x7ffu), ql = (int)((pk >> 11) & 0x7ffu), vl = (int)(pk >> 22);
                 int nth = t - __shfl_sync(FULL, excl, l);
-                // the word holding the nth third member, then its bit: the bit
-                // search runs once per lane, outside the (divergent) word loop
+                // the word holding the nth third member: from the owner's
+                // packed counts (the number of words whose inclusive count is
+                // <= nth), else by a scan; then its bit
                 int wsel = ql >> 5;
-                unsigned Ksel = 0u;
-                for (int w = ql >> 5; w < Wm; w++) {
-                    const unsigned K = kword(pl, ql, vl, w);
-                    const int c = __popc(K);
-                    if (nth < c) {
-                        wsel = w;
-                        Ksel = K;
-                        break;
+                if (packed) {
+                    const unsigned k0 = __shfl_sync(FULL, c0, l);
+                    const unsigned k1 = Wm > 4 ? __shfl_sync(FULL, c1, l) : 0x7f7f7f7fu;
+                    const unsigned n4 = ((unsigned)nth * 0x01010101u) | 0x80808080u;
+                    const int js = __popc((n4 - k0) & 0x80808080u) + __popc((n4 - k1) & 0x80808080u);
+                    if (js > 0) nth -= (int)(((js <= 4 ? k0 : k1) >> (((js - 1) & 3) << 3)) & 0xffu);
+                    wsel += js;
+                } else {
+                    for (int w = ql >> 5; w < Wm; w++) {
+                        const int c = __popc(kword(pl, ql, vl, w));
+                        if (nth < c) {
+                            wsel = w;
+                            break;
+                        }
+                        nth -= c;
                     }
-                    nth -= c;
                 }
+                const unsigned Ap = adj[pl * W + wsel], Aq = adj[ql * W + wsel];
+                const unsigned Ksel = Ap & Aq & (TRAV == 2 ? memb[vl * W + wsel] : FULL);
                 // invalid lanes repeat a valid triangle, so Ksel has a set bit here
                 const int r = (wsel << 5) + nth_bit(Ksel, nth);
+                int epr = 0, eqr = 0;
+                if (!use_acc) {
+                    const unsigned below = (1u << (r & 31)) - 1u;
+                    epr = rowoff[pl] + rowpre[pl * W + wsel] + __popc(Ap & below);
+                    eqr = rowoff[ql] + rowpre[ql * W + wsel] + __popc(Aq & below);
+                }
                 nint += valid ? 1u : 0u;
-                const R gpq = eval_tri(pl, ql, r, e0 + l, valid);
+                const R gpq = eval_tri(pl, ql, r, e0 + l, epr, eqr, valid);
                 if (!use_acc) {
                     // a round holds each edge's triangles as one run of lanes:
                     // the run's sum goes to the edge's owner lane
-                    const R run = seg_sum<R>(gpq, valid ? l : -1 - lane, lane);
+                    // (runs start at lane 0 and where the owner changes; the
+                    // invalid lanes' zeros may join the last run)
+                    const int lprev = __shfl_up_sync(FULL, l, 1);
+                    const unsigned heads = __ballot_sync(FULL, lane == 0 || lprev != l);
+                    const unsigned above = heads & ~((2u << lane) - 1u);
+                    const int rend = above ? __ffs(above) - 1 : 32;
+                    R run = gpq;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const R tt = __shfl_down_sync(FULL, run, o);
+                        if (lane + o < rend) run += tt;
+                    }
                     const bool mine = cnt > 0 && excl < t0 + 32 && excl + cnt > t0;
                     const int head = (excl > t0 ? excl : t0) - t0;
                     const R got = __shfl_sync(FULL, run, mine ? head : 0);
@@ -1038,11 +1078,61 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
             fxs.add((R)acc_get(m));
             fys.add((R)acc_get(mcap + m));
             fzs.add((R)acc_get(2 * mcap + m));
-        } else if (PAIR) {
-            // edge vectors: FP64 from the table (d(lo -> hi), so the sign flips for
-            // edges where m is the upper end), FP32 from the shifted rows
+        } else if (PAIR && !F64) {
+            // FP32 edge vectors from the shifted rows; two pairs per iteration
+            // (their loads in flight together), added in pair order
             int e = rowoff[m];
-            const float4 Pm = F64 ? make_float4(0.f, 0.f, 0.f, 0.f) : S4[m];
+            const float4 Pm = S4[m];
+            for (int w = 0; w < Wm; w++) {
+                unsigned up = adj[m * W + w];
+                while (up) {
+                    const int y0 = (w << 5) + __ffs(up) - 1;
+                    up &= up - 1u;
+                    const bool two = up != 0u;
+                    const int y1 = two ? (w << 5) + __ffs(up) - 1 : y0;
+                    up &= up - 1u;
+                    const int ee0 = e;
+                    e += two ? 2 : 1;
+                    const R g0 = gget(ee0);
+                    const R g1 = two ? gget(ee0 + 1) : R(0);
+                    const float4 Y0 = S4[y0], Y1 = S4[y1];
+                    if (g0 != R(0)) {
+                        fxs.add(g0 * (Y0.x - Pm.x));
+                        fys.add(g0 * (Y0.y - Pm.y));
+                        fzs.add(g0 * (Y0.z - Pm.z));
+                    }
+                    if (g1 != R(0)) {
+                        fxs.add(g1 * (Y1.x - Pm.x));
+                        fys.add(g1 * (Y1.y - Pm.y));
+                        fzs.add(g1 * (Y1.z - Pm.z));
+                    }
+                }
+                unsigned dn = adjT[m * W + w];
+                while (dn) {
+                    const int x0 = (w << 5) + __ffs(dn) - 1;
+                    dn &= dn - 1u;
+                    const bool two = dn != 0u;
+                    const int x1 = two ? (w << 5) + __ffs(dn) - 1 : x0;
+                    dn &= dn - 1u;
+                    const R g0 = gget(rowoff[x0] + rank(x0, m));
+                    const R g1 = two ? gget(rowoff[x1] + rank(x1, m)) : R(0);
+                    const float4 X0 = S4[x0], X1 = S4[x1];
+                    if (g0 != R(0)) {
+                        fxs.add(g0 * (X0.x - Pm.x));
+                        fys.add(g0 * (X0.y - Pm.y));
+                        fzs.add(g0 * (X0.z - Pm.z));
+                    }
+                    if (g1 != R(0)) {
+                        fxs.add(g1 * (X1.x - Pm.x));
+                        fys.add(g1 * (X1.y - Pm.y));
+                        fzs.add(g1 * (X1.z - Pm.z));
+                    }
+                }
+            }
+        } else if (PAIR) {
+            // FP64 edge vectors: from the shifted rows, or from the table
+            // (d(lo -> hi), so the sign flips for edges where m is the upper end)
+            int e = rowoff[m];
             for (int w = 0; w < Wm; w++) {
                 unsigned up = adj[m * W + w];
                 while (up) {
@@ -1052,13 +1142,10 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
                     R g = gget(ee);
                     if (g != R(0)) {
                         R dx, dy, dz;
-                        if (F64 && shifted) {
+                        if (shifted) {
                             dx = px[y] - px[m]; dy = py[y] - py[m]; dz = pz[y] - pz[m];
-                        } else if (F64) {
-                            dx = ED[4 * ee]; dy = ED[4 * ee + 1]; dz = ED[4 * ee + 2];
                         } else {
-                            const float4 Y = S4[y];
-                            dx = Y.x - Pm.x; dy = Y.y - Pm.y; dz = Y.z - Pm.z;
+                            dx = ED[4 * ee]; dy = ED[4 * ee + 1]; dz = ED[4 * ee + 2];
                         }
                         fxs.add(g * dx);
                         fys.add(g * dy);
@@ -1073,13 +1160,10 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
                     R g = gget(ee);
                     if (g != R(0)) {
                         R dx, dy, dz;
-                        if (F64 && shifted) {
+                        if (shifted) {
                             dx = px[x] - px[m]; dy = py[x] - py[m]; dz = pz[x] - pz[m];
-                        } else if (F64) {
-                            dx = -ED[4 * ee]; dy = -ED[4 * ee + 1]; dz = -ED[4 * ee + 2];
                         } else {
-                            const float4 X = S4[x];
-                            dx = X.x - Pm.x; dy = X.y - Pm.y; dz = X.z - Pm.z;
+                            dx = -ED[4 * ee]; dy = -ED[4 * ee + 1]; dz = -ED[4 * ee + 2];
                         }
                         fxs.add(g * dx);
                         fys.add(g * dy);
