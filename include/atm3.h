@@ -200,7 +200,9 @@ atm_status atm_step(atm_ctx* ctx, int nsteps, atm_traversal trav, atm_truncation
  * non-NULL).  The result equals atm_set_state, atm_set_forces, atm_step,
  * atm_get_state and atm_get_forces(..., 0) in sequence, but the stream is
  * synchronised only by the steps' cell builds and once at the end (those calls
- * synchronise one by one).  The inputs are checked for NaN / Inf on the
+ * synchronise one by one), and the input checks and the copy of the last
+ * step's positions run beside the other copies and the force evaluation on
+ * a second stream of the context.  The inputs are checked for NaN / Inf on the
  * device: a non-finite input returns NONFINITE, after which the contents of x,
  * v and f are unspecified and the context has no state.  Host memory that is
  * page-locked (cudaHostAlloc / cudaHostRegister) is copied fastest.
@@ -334,8 +336,10 @@ typedef struct {
     int cut[2];         /* staged-molecule bounds of the first classes */
 } atm_tuning;
 
-/* Autotuner: times `reps` force evaluations on the current cells for every
- * launch form (one CTA per unit or persistent; 4 or 8 warps for 3C18/3C08;
+/* Autotuner: times `reps` force evaluations on the current cells, in the form
+ * steps take them (LJ inside the ATM units for the 3C18/3C08/3C08A pair
+ * rule), for every launch form (one CTA per unit or persistent; 4 or 8 warps
+ * for 3C18/3C08;
  * for 3C18/3C08/3C08A also unit size classes: {all}, {<= 64, rest},
  * {<= 48, <= 96, rest}, {<= 64, <= 128, rest}, where every force evaluation
  * sorts the units by their staged molecules on the device and launches each

@@ -129,6 +129,9 @@ static void free_all(atm_ctx* c)
     if (c->side_st) cudaStreamDestroy(c->side_st);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->io_st) cudaStreamDestroy(c->io_st);
+    if (c->ev_io) cudaEventDestroy(c->ev_io);
+    if (c->ev_io_done) cudaEventDestroy(c->ev_io_done);
     for (auto& r : c->ev_live) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -275,6 +278,9 @@ extern "C" atm_status atm_batch_create(const atm_params* params, const int64_t* 
     ok = ok && cudaStreamCreateWithFlags(&c->side_st, cudaStreamNonBlocking) == cudaSuccess;
     ok = ok && cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess;
     ok = ok && cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaStreamCreateWithFlags(&c->io_st, cudaStreamNonBlocking) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&c->ev_io, cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&c->ev_io_done, cudaEventDisableTiming) == cudaSuccess;
     if (ok) {
         std::vector<int> roc(NC), rom(N, 0);
         for (int r = 0; r < nrep; r++) {
@@ -758,6 +764,19 @@ extern "C" atm_status atm_get_state(atm_ctx* c, double* x, double* v)
     return ATM_OK;
 }
 
+// atm_step_host: once the last step's cell build has wrapped the positions
+// (enqueue_cells has just synchronised with it, and nothing later in the step
+// writes them) they are copied to the caller beside the force evaluation
+static atm_status early_x_out(atm_ctx* c)
+{
+    if (!c->x_host_out || c->n == 0) return ATM_OK;
+    CU(cudaMemcpyAsync(c->x_host_out, c->x, 3 * (size_t)c->n * sizeof(double),
+                       cudaMemcpyDeviceToHost, c->io_st));
+    c->x_host_out = nullptr;
+    c->x_out_issued = true;
+    return ATM_OK;
+}
+
 // one velocity-Verlet step without host synchronisation: kick + drift, cells,
 // forces (capacity mcap), kick
 static atm_status enqueue_step(atm_ctx* c, int trav, int trunc, int prec, int mcap)
@@ -876,6 +895,10 @@ extern "C" atm_status atm_step(atm_ctx* c, int nsteps, atm_traversal trav, atm_t
         c->f_in_valid = false;
         s = enqueue_cells(c);
         if (s != ATM_OK) return s;
+        if (nsteps == 1) {
+            s = early_x_out(c);
+            if (s != ATM_OK) return s;
+        }
         s = ctx_enqueue_forces(c, trav, trunc, prec, c->unit_max[trav], true);
         if (s != ATM_OK) return s;
         CU(launch_kick(c->b, c->perm, c->f_lj, c->f_atm, c->x, c->v, 0, c->ke, c->st));
@@ -930,6 +953,10 @@ extern "C" atm_status atm_step(atm_ctx* c, int nsteps, atm_traversal trav, atm_t
             c->n_launch += 1;
             s = enqueue_cells(c);
             if (s != ATM_OK) return s;
+            if (k == nsteps - 1) {
+                s = early_x_out(c);
+                if (s != ATM_OK) return s;
+            }
             // every exact_every-th surrogate step uses the exact FP32C traversal
             // and compares the surrogate with it
             const bool exact = sur_mixed && sur_exact_due(c);
@@ -976,19 +1003,28 @@ extern "C" atm_status atm_step_host(atm_ctx* c, int nsteps, atm_traversal trav,
     const size_t bytes = (size_t)m * sizeof(double);
     // inputs: copies and device-side finite checks; the verdict travels back
     // with the first synchronisation of the step (its cell build) or the last
+    // (each check runs on io_st while the next copy runs on the stream)
     *c->h_chk = 0;
     if (m > 0) {
+        auto check_on_io = [&](const double* a) -> cudaError_t {
+            cudaError_t e = cudaEventRecord(c->ev_io, c->st);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(c->io_st, c->ev_io, 0);
+            if (e == cudaSuccess) e = launch_check_finite(m, a, c->d_chk, c->io_st);
+            return e;
+        };
         CU(cudaMemsetAsync(c->d_chk, 0, sizeof(int), c->st));
         CU(cudaMemcpyAsync(c->x, x, bytes, cudaMemcpyHostToDevice, c->st));
-        CU(launch_check_finite(m, c->x, c->d_chk, c->st));
+        CU(check_on_io(c->x));
         CU(cudaMemcpyAsync(c->v, v, bytes, cudaMemcpyHostToDevice, c->st));
-        CU(launch_check_finite(m, c->v, c->d_chk, c->st));
+        CU(check_on_io(c->v));
         c->n_launch += 2;
         if (f) {
             CU(cudaMemcpyAsync(c->f_in, f, bytes, cudaMemcpyHostToDevice, c->st));
-            CU(launch_check_finite(m, c->f_in, c->d_chk, c->st));
+            CU(check_on_io(c->f_in));
             c->n_launch += 1;
         }
+        CU(cudaEventRecord(c->ev_io_done, c->io_st));
+        CU(cudaStreamWaitEvent(c->st, c->ev_io_done, 0));
         CU(cudaMemcpyAsync(c->h_chk, c->d_chk, sizeof(int), cudaMemcpyDeviceToHost, c->st));
     }
     c->have_x = true;
@@ -1004,14 +1040,26 @@ extern "C" atm_status atm_step_host(atm_ctx* c, int nsteps, atm_traversal trav,
         invalidate(c);
         return ctx_fail(c, ATM_E_NONFINITE, "non-finite position, velocity or force given");
     };
+    // the last step copies its positions to x as soon as its cells are built
+    c->x_host_out = m > 0 ? x : nullptr;
+    c->x_out_issued = false;
     atm_status s = atm_step(c, nsteps, trav, trunc, prec, nullptr);
+    const bool x_early = c->x_out_issued;
+    c->x_host_out = nullptr;
+    c->x_out_issued = false;
     if (s != ATM_OK) {
         cudaStreamSynchronize(c->st);
+        cudaStreamSynchronize(c->io_st);
         return *c->h_chk ? bad_input() : s;
     }
     // outputs: state, total force and scalars, then one synchronisation
     if (m > 0) {
-        CU(cudaMemcpyAsync(x, c->x, bytes, cudaMemcpyDeviceToHost, c->st));
+        if (x_early) {
+            CU(cudaEventRecord(c->ev_io_done, c->io_st));
+            CU(cudaStreamWaitEvent(c->st, c->ev_io_done, 0));
+        } else {
+            CU(cudaMemcpyAsync(x, c->x, bytes, cudaMemcpyDeviceToHost, c->st));
+        }
         CU(cudaMemcpyAsync(v, c->v, bytes, cudaMemcpyDeviceToHost, c->st));
         if (f) {
             CU(launch_gather_forces(c->n, c->perm, c->f_lj, c->f_atm, 0, c->f_out, c->st));
@@ -1121,16 +1169,18 @@ extern "C" atm_status atm_autotune(atm_ctx* c, atm_traversal trav, atm_truncatio
     atm_status s = ATM_OK;
     const bool owner = trav == ATM_3C01 || trav == ATM_3CW;
     const int nw_options = owner ? 1 : 2, split_options = owner ? 1 : N_SPLITS;
+    // the evaluation as steps take it (LJ inside the units where steps fuse it)
+    const bool fuse = lj_fused(trav, trunc, prec);
     for (int sp = 0; sp < split_options && s == ATM_OK; sp++)
     for (int nwi = 0; nwi < nw_options && s == ATM_OK; nwi++)
         for (int pers = 0; pers < 2 && s == ATM_OK; pers++) {
             const int code = 1 + pers + 2 * nwi + 4 * sp;
             c->tuned[prec][trav][trunc] = code;
-            s = ctx_enqueue_forces(c, trav, trunc, prec, c->unit_max[trav]);  // warm-up
+            s = ctx_enqueue_forces(c, trav, trunc, prec, c->unit_max[trav], fuse);  // warm-up
             if (s != ATM_OK) break;
             cudaEventRecord(e0, c->st);
             for (int k = 0; k < reps && s == ATM_OK; k++)
-                s = ctx_enqueue_forces(c, trav, trunc, prec, c->unit_max[trav]);
+                s = ctx_enqueue_forces(c, trav, trunc, prec, c->unit_max[trav], fuse);
             cudaEventRecord(e1, c->st);
             if (s != ATM_OK) break;
             s = ctx_sync_and_check(c);

@@ -103,6 +103,12 @@ struct atm_ctx {
     // (forked from and joined to the context's stream by the two events)
     cudaStream_t side_st = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // host round trips (atm_step_host): the input checks and the copy of the
+    // last step's positions run on io_st beside the context's stream
+    cudaStream_t io_st = nullptr;
+    cudaEvent_t ev_io = nullptr, ev_io_done = nullptr;
+    double* x_host_out = nullptr;  // where the last step copies its positions early
+    bool x_out_issued = false;     // that copy is in flight on io_st
     cudaGraphExec_t graph = nullptr;
     int graph_key[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
     // profiling: event pairs around launch groups, summed per kind

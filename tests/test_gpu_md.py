@@ -280,18 +280,20 @@ def test_forces_are_forgotten_with_a_new_state(atm3):
     assert r1["ekin"] == pytest.approx(r2["ekin"], rel=1e-9)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
-def test_step_host_equals_the_separate_calls(atm3, prec):
+@pytest.mark.parametrize("prec,graph", [("fp64", False), ("fp32c", False), ("fp32c", True)])
+def test_step_host_equals_the_separate_calls(atm3, prec, graph):
     """atm_step_host (state and force in from host memory, steps, state and
-    force out, one synchronisation at the end) gives what the separate calls
+    force out, one synchronisation at the end; the last step's positions
+    copied out beside its force evaluation) gives what the separate calls
     give: bit for bit in deterministic mode, where the force sums do not
     depend on the order of the atomic additions.  Also without given forces,
-    and with two steps per round trip."""
+    with two steps per round trip, and with graph steps."""
     cfg = synth.homogeneous(2000, 0.8, 1.0, seed=1302)
     runs = []
     for api in ("separate", "host"):
         with atm3.AtmSystem(cfg["box"], cfg["n"], nu=NU, dt=0.002) as s:
             s.set_deterministic(True)
+            s.set_options(graph=graph)
             s.set_state(cfg["x"], cfg["v"])
             s.step(0, "3c08", "pair", prec)
             x, v = s.get_state()
