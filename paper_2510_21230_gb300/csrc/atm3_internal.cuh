@@ -195,6 +195,11 @@ struct AtmArgs {
     // (k_pair_masks, [PM_WORDS n] words, nullptr: the units decide their
     // pairs themselves); the units assemble their adjacency from them
     const unsigned* pmask;
+    // pair rule of the block traversals: each unit raises *emax to the edge
+    // table it needed, in 1/16 edges per staged molecule of this launch
+    // (ceil(16 edges / mcap)), so later launches can size the table from it
+    // (nullptr: not recorded)
+    int* emax;
 };
 
 // pair bitmaps: word k - 13 of molecule s (sorted) covers the molecules of
@@ -258,7 +263,7 @@ __host__ __device__ inline BlockSmem block_smem_plan(int trunc, int mcap, int nw
     p.off_sh = o;     o = al(o + (f64 ? sizeof(R) * 3 * M : 16 * M));
     p.off_pos32 = o;  o = al(o + (f64 ? sizeof(float) * 3 * M : 0));
     p.off_sh32 = o;   o = al(o + (f64 ? sizeof(float) * 3 * M : 0));
-    p.off_idx = o;    o = al(o + sizeof(int) * M);
+    p.off_idx = o;    o = al(o + (f64 ? sizeof(int) * M : 0));  // FP32: in the position rows' w
     p.off_slot = o;   o = al(o + M);
     p.off_adj = o;    o = al(o + (pair ? sizeof(unsigned) * M * p.W : 0));
     p.off_adjT = o;   o = al(o + (pair ? sizeof(unsigned) * M * p.W : 0));
@@ -286,9 +291,11 @@ __host__ __device__ inline BlockSmem block_smem_plan(int trunc, int mcap, int nw
 
 // Launch configuration of the ATM kernels for units of at most mcap molecules.
 // 3c01: 4 warps.  3c18/3c08 pair rule: 4 warps (FP32) or 8 (FP64) and pair
-// scalars for 16 edges per staged molecule of the largest unit (the rho* =
-// 0.8 liquids have at most 14.4 (256k) and 15.9 (32k)), halved until they
-// fit (a unit with more edges falls back to per-molecule accumulators);
+// scalars for gpm16 / 16 edges per staged molecule of the largest unit
+// (gpm16 = 256 before any measurement: the rho* = 0.8 liquids have at most
+// 14.4 (256k, fcc start) and 15.9 (32k); a context then sizes the table from
+// the needs its units recorded), halved until they fit (a unit with more
+// edges falls back to per-molecule accumulators);
 // product rule: 8 warps (FP32 3c18: 16 when one CTA fills an SM),
 // dense distances + dense pair scalars, else dense pair scalars only, else
 // per-molecule accumulators.  Returns false if nothing fits.
@@ -302,7 +309,7 @@ struct AtmPlan {
 constexpr int ATM_WIDE_PCAP = 1024;
 
 inline bool atm_choose_plan_nw(int trav, int trunc, int prec, int mcap, int optin, int nwarps,
-                               AtmPlan& P, int det = 0)
+                               AtmPlan& P, int det = 0, int gpm16 = 256)
 {
     // the kernels' static shared memory (slot tables, reductions; under 2 KB)
     // counts against the same per-block limit as the dynamic part
@@ -337,7 +344,8 @@ inline bool atm_choose_plan_nw(int trav, int trunc, int prec, int mcap, int opti
     if (trunc == 0) {
         auto fit = [&](int use_d) -> bool {
             P.use_d = use_d;
-            long long g = npair < 16ll * mcap ? npair : 16ll * mcap;
+            const long long cap = ((long long)gpm16 * mcap + 15) / 16;
+            long long g = npair < cap ? npair : cap;
             for (;;) {
                 P.gcap = (int)g;
                 P.smem = bytes();
@@ -383,16 +391,17 @@ inline bool atm_choose_plan_nw(int trav, int trunc, int prec, int mcap, int opti
 }
 
 inline bool atm_choose_plan(int trav, int trunc, int prec, int mcap, int optin, AtmPlan& P,
-                            int det = 0)
+                            int det = 0, int gpm16 = 256)
 {
     if (!atm_choose_plan_nw(trav, trunc, prec, mcap, optin,
-                            (trav == 0 || trav == 3 || (trunc == 0 && prec == 1)) ? 4 : 8, P, det))
+                            (trav == 0 || trav == 3 || (trunc == 0 && prec == 1)) ? 4 : 8, P, det,
+                            gpm16))
         return false;
     // FP32 3c18 product rule whose tables leave room for one CTA per SM: 16
     // warps (same table mode) hide more of the scan's shared-memory latency
     if (trunc == 1 && prec == 1 && trav == 1 && 2 * P.smem > (size_t)optin) {
         AtmPlan Q;
-        if (atm_choose_plan_nw(trav, trunc, prec, mcap, optin, 16, Q, det) && Q.use_d == P.use_d &&
+        if (atm_choose_plan_nw(trav, trunc, prec, mcap, optin, 16, Q, det, gpm16) && Q.use_d == P.use_d &&
             Q.acc_mode == P.acc_mode)
             P = Q;
     }

@@ -160,7 +160,7 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
     float* sz32 = sy32 + mcap;
     float4* P4 = reinterpret_cast<float4*>(smem + plan.off_pos);
     float4* S4 = reinterpret_cast<float4*>(smem + plan.off_sh);  // FP32 pair rule: the shifted rows after the decisions
-    int* sidx = reinterpret_cast<int*>(smem + plan.off_idx);
+    int* sidx = reinterpret_cast<int*>(smem + plan.off_idx);  // FP64; FP32: P4[t].w
     unsigned char* sslot = smem + plan.off_slot;
     unsigned* adj = reinterpret_cast<unsigned*>(smem + plan.off_adj);
     unsigned* adjT = reinterpret_cast<unsigned*>(smem + plan.off_adjT);
@@ -298,7 +298,9 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
         while (s_beg[s + 1] <= t) s++;
         int g = s_cell0[s] + (t - s_beg[s]);
         if (!F64) {
-            P4[t] = make_float4((float)A.xl[g], (float)A.xl[n + g], (float)A.xl[2 * n + g], 0.0f);
+            // (w: the molecule's sorted index)
+            P4[t] = make_float4((float)A.xl[g], (float)A.xl[n + g], (float)A.xl[2 * n + g],
+                                __int_as_float(g));
             S4[t] = make_float4((float)s_off[s][0] * wf0, (float)s_off[s][1] * wf1,
                                 (float)s_off[s][2] * wf2, 0.0f);
         } else {
@@ -315,7 +317,7 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
             sy32[t] = (float)s_off[s][1] * wf1;
             sz32[t] = (float)s_off[s][2] * wf2;
         }
-        sidx[t] = g;
+        if (F64) sidx[t] = g;
         sslot[t] = (unsigned char)s;
     }
     const bool dense_g = !PAIR && A.acc_mode == 0;
@@ -428,7 +430,7 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
             // bitmaps only when fl(w^2) >= the FP32 r_c^2 on every axis.
             for (int p = tid; p < M; p += blockDim.x) {
                 const int sp = sslot[p];
-                const long long gp = sidx[p];
+                const long long gp = __float_as_int(P4[p].w);
                 unsigned* rowa = adj + p * W;
                 unsigned wd[S];  // the row's words first: independent loads in flight
 #pragma unroll
@@ -573,6 +575,7 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
         }
         __syncthreads();
         edge_mode = s_edges <= A.gcap;
+        if (tid == 0 && A.emax) atomicMax(A.emax, (16 * s_edges + mcap - 1) / mcap);
         if (edge_mode) {
             // edge list (p, q) in edge order, one thread per row; FP64 then
             // tabulates d(p -> q) and |d|^2 one thread per edge (every lane
@@ -1222,7 +1225,7 @@ __device__ __forceinline__ void atm_block_unit(const AtmArgs<R>& A, const long l
         double f0 = use_acc ? acc_get(m) : fxs.get();
         double f1 = use_acc ? acc_get(mcap + m) : fys.get();
         double f2 = use_acc ? acc_get(2 * mcap + m) : fzs.get();
-        int g = sidx[m];
+        const int g = F64 ? sidx[m] : __float_as_int(P4[m].w);
         if constexpr (DET) {
             // 64-bit fixed-point sums across units (converted after the launch)
             unsigned long long* fsx = reinterpret_cast<unsigned long long*>(A.fs);

@@ -258,7 +258,9 @@ extern "C" atm_status atm_batch_create(const atm_params* params, const int64_t* 
     ok = ok && alloc((void**)&c->d_res, nrep * sizeof(ResultDev));
     ok = ok && alloc((void**)&c->d_part, (size_t)nrep * REDUCE_PARTS * sizeof(ResultDev));
     ok = ok && alloc((void**)&c->d_status, sizeof(int));
-    ok = ok && alloc((void**)&c->d_maxocc, (1 + ATM_NTRAV) * sizeof(int));
+    // largest cell, largest unit per traversal, edge-table need per traversal
+    ok = ok && alloc((void**)&c->d_maxocc, (1 + 2 * ATM_NTRAV) * sizeof(int));
+    ok = ok && cudaMemset(c->d_maxocc, 0, (1 + 2 * ATM_NTRAV) * sizeof(int)) == cudaSuccess;
     ok = ok && alloc((void**)&c->d_work, 4 * sizeof(int));
     ok = ok && alloc((void**)&c->d_ulist, 3 * NC * sizeof(int));
     ok = ok && alloc((void**)&c->d_ucount, 4 * sizeof(int));
@@ -269,7 +271,7 @@ extern "C" atm_status atm_batch_create(const atm_params* params, const int64_t* 
     ok = ok && cudaMallocHost((void**)&c->h_res, nrep * sizeof(ResultDev)) == cudaSuccess;
     ok = ok && cudaMallocHost((void**)&c->h_status, sizeof(int)) == cudaSuccess;
     ok = ok && cudaMallocHost((void**)&c->h_chk, sizeof(int)) == cudaSuccess;
-    ok = ok && cudaMallocHost((void**)&c->h_maxocc, (1 + ATM_NTRAV) * sizeof(int)) == cudaSuccess;
+    ok = ok && cudaMallocHost((void**)&c->h_maxocc, (1 + 2 * ATM_NTRAV) * sizeof(int)) == cudaSuccess;
     ok = ok && cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin,
                                       c->device) == cudaSuccess;
     ok = ok && cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device) ==
@@ -447,15 +449,33 @@ static atm_status launch_cells(atm_ctx* c)
 }
 
 // cell build + read back of the occupancy maxima that size the force kernels
+// the unit sizes of the last cell build and the edge-table needs recorded by
+// the units so far (h_maxocc, after a synchronisation): each traversal's
+// table capacity becomes its need plus a quarter edge per staged molecule
+// (the needs only grow, so a system that changes slowly keeps its capacity)
+static void take_unit_sizes(atm_ctx* c)
+{
+    c->maxocc = c->h_maxocc[0];
+    for (int t = 0; t < ATM_NTRAV; t++) {
+        c->unit_max[t] = c->h_maxocc[1 + t];
+        const int need = c->h_maxocc[1 + ATM_NTRAV + t];
+        const int g = need > 0 ? std::min(256, need + 4) : c->gpm16[t];
+        if (g != c->gpm16[t]) {
+            c->gpm16[t] = g;
+            memset(c->nw_auto[t], 0, sizeof(c->nw_auto[t]));  // keyed by unit size only
+        }
+    }
+}
+
 static atm_status enqueue_cells(atm_ctx* c)
 {
     atm_status s = launch_cells(c);
     if (s != ATM_OK) return s;
-    CU(cudaMemcpyAsync(c->h_maxocc, c->d_maxocc, (1 + ATM_NTRAV) * sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    CU(cudaMemcpyAsync(c->h_maxocc, c->d_maxocc, (1 + 2 * ATM_NTRAV) * sizeof(int),
+                       cudaMemcpyDeviceToHost, c->st));
     s = ctx_sync_and_check(c);
     if (s != ATM_OK) return s;
-    c->maxocc = c->h_maxocc[0];
-    for (int t = 0; t < ATM_NTRAV; t++) c->unit_max[t] = c->h_maxocc[1 + t];
+    take_unit_sizes(c);
     c->cells_built = true;
     c->forces_valid = false;
     return ATM_OK;
@@ -542,6 +562,21 @@ static void launch_choice(atm_ctx* c, int trav, int trunc, int prec, int mcap, i
 
 // LJ + ATM force kernels for the current cells; mcap = staged-molecule capacity
 // FP32 pair rule of a block traversal, bitmaps enabled, every cell within 32
+// pair rule of a block traversal outside the deterministic mode (whose
+// results must not depend on the context's history): the units record their
+// edge-table need and the table is sized from it
+static bool measured_edges(const atm_ctx* c, int trav, int trunc)
+{
+    return trunc == ATM_TRUNC_PAIR && !c->det &&
+           (trav == ATM_3C18 || trav == ATM_3C08 || trav == ATM_3C08A);
+}
+
+// edge-table capacity of a launch, 1/16 edges per staged molecule
+static int edge_capacity(const atm_ctx* c, int trav, int trunc)
+{
+    return measured_edges(c, trav, trunc) ? c->gpm16[trav] : 256;
+}
+
 static bool use_pair_masks(const atm_ctx* c, int trav, int trunc, int prec)
 {
     return c->opt_pmask && c->pmask && prec == ATM_FP32C && trunc == ATM_TRUNC_PAIR &&
@@ -604,6 +639,8 @@ atm_status atm3::ctx_enqueue_forces(atm_ctx* c, int trav, int trunc, int prec, i
     j.ev_join = c->ev_join;
     j.det = c->det;
     j.pmask = use_pair_masks(c, trav, trunc, prec) ? c->pmask : nullptr;
+    j.gpm16 = edge_capacity(c, trav, trunc);
+    j.emax = measured_edges(c, trav, trunc) ? c->d_maxocc + 1 + ATM_NTRAV + trav : nullptr;
 
     cudaEvent_t ev;
     if (prec != ATM_SURROGATE && !fused) {
@@ -800,10 +837,11 @@ static atm_status enqueue_step(atm_ctx* c, int trav, int trunc, int prec, int mc
 static int atm_ctas_per_sm(const atm_ctx* c, int trav, int trunc, int prec, int nwarps, int mcap)
 {
     AtmPlan P;
-    if (!atm_choose_plan(trav, trunc, prec, mcap, c->smem_optin, P, c->det)) return 0;
+    const int g = edge_capacity(c, trav, trunc);
+    if (!atm_choose_plan(trav, trunc, prec, mcap, c->smem_optin, P, c->det, g)) return 0;
     if ((nwarps == 2 || nwarps == 4 || nwarps == 8) && trav != ATM_3C01 && trav != ATM_3CW) {
         AtmPlan Q;
-        if (atm_choose_plan_nw(trav, trunc, prec, mcap, c->smem_optin, nwarps, Q, c->det)) P = Q;
+        if (atm_choose_plan_nw(trav, trunc, prec, mcap, c->smem_optin, nwarps, Q, c->det, g)) P = Q;
     }
     return prec == ATM_FP64 ? atm_occupancy_fp64(trav, trunc, P.nwarps, P.smem, c->det)
                             : atm_occupancy_fp32(trav, trunc, P.nwarps, P.smem, c->det);
@@ -836,9 +874,9 @@ static atm_status run_graph_steps(atm_ctx* c, int nsteps, int trav, int trunc, i
     if (prec != ATM_SURROGATE)
         launch_choice(c, trav, trunc, prec, c->unit_max[trav], persistent, nwarps, cls);
     const int mcap = graph_mcap(c, trav, trunc, prec, nwarps);
-    const int key[8] = {trav, trunc, prec, mcap,
+    const int key[9] = {trav, trunc, prec, mcap,
                         persistent + 2 * nwarps + 64 * (use_pair_masks(c, trav, trunc, prec) ? 1 : 0),
-                        cls[0], cls[1], cls[2]};
+                        cls[0], cls[1], cls[2], edge_capacity(c, trav, trunc)};
     if (!c->graph || memcmp(key, c->graph_key, sizeof(key)) != 0) {
         drop_graph(c);
         cudaStream_t keep = c->st;
@@ -923,12 +961,12 @@ extern "C" atm_status atm_step(atm_ctx* c, int nsteps, atm_traversal trav, atm_t
         }
         s = run_graph_steps(c, nsteps, trav, trunc, prec);
         if (s != ATM_OK) return s;
-        CU(cudaMemcpyAsync(c->h_maxocc, c->d_maxocc, (1 + ATM_NTRAV) * sizeof(int), cudaMemcpyDeviceToHost, c->st));
+        CU(cudaMemcpyAsync(c->h_maxocc, c->d_maxocc, (1 + 2 * ATM_NTRAV) * sizeof(int),
+                           cudaMemcpyDeviceToHost, c->st));
         s = ctx_sync_and_check(c);
         if (s == ATM_OK) {
             done = true;
-            c->maxocc = c->h_maxocc[0];
-            for (int t = 0; t < ATM_NTRAV; t++) c->unit_max[t] = c->h_maxocc[1 + t];
+            take_unit_sizes(c);
         } else if (s == ATM_E_CAPACITY) {
             // a unit outgrew the graph's capacity: restart from the snapshot
             // and step with per-step sizing

@@ -69,6 +69,11 @@ struct atm_ctx {
     long long dens_samples = 0;
     int maxocc = 0;
     int unit_max[atm3::ATM_NTRAV] = {};  // largest unit (staged molecules) of 3c01, 3c18, 3c08, 3cw
+    // pair rule of the block traversals outside the deterministic mode: the
+    // edge table's capacity in 1/16 edges per staged molecule, from the
+    // largest need the units of this context recorded (d_maxocc[1 + NTRAV +
+    // trav], read with the unit sizes) plus a margin; 256 before any
+    int gpm16[atm3::ATM_NTRAV] = {256, 256, 256, 256, 256};
     bool have_x = false, cells_built = false, forces_valid = false;
     int f_trav = -1, f_trunc = -1, f_prec = -1;
     bool f_fused = false;  // the current forces came from units that also did LJ
@@ -110,7 +115,7 @@ struct atm_ctx {
     double* x_host_out = nullptr;  // where the last step copies its positions early
     bool x_out_issued = false;     // that copy is in flight on io_st
     cudaGraphExec_t graph = nullptr;
-    int graph_key[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
+    int graph_key[9] = {-1, -1, -1, -1, -1, -1, -1, -1, -1};
     // profiling: event pairs around launch groups, summed per kind
     int prof = 0;  // profiling: 0 off, 1 every launch group, 2 force evaluations only
     struct EvRec {

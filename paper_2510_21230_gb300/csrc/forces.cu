@@ -96,13 +96,13 @@ static cudaError_t launch_atm_one(const ForceJob& j, size_t* smem_set, bool* cap
     AtmPlan P;
     // the block kernel packs staged indices in 11 bits, the owner kernels in 16
     const int limit = (j.trav == 0 || j.trav == 3) ? 65535 : ATM_MCAP_LIMIT;
-    if (j.mcap > limit || !atm_choose_plan(j.trav, j.trunc, j.prec, j.mcap, j.optin, P, j.det)) {
+    if (j.mcap > limit || !atm_choose_plan(j.trav, j.trunc, j.prec, j.mcap, j.optin, P, j.det, j.gpm16)) {
         *capacity = true;
         return cudaErrorInvalidValue;
     }
     if ((j.nwarps == 2 || j.nwarps == 4 || j.nwarps == 8) && j.trav != 0 && j.trav != 3) {
         AtmPlan Q;
-        if (atm_choose_plan_nw(j.trav, j.trunc, j.prec, j.mcap, j.optin, j.nwarps, Q, j.det)) P = Q;
+        if (atm_choose_plan_nw(j.trav, j.trunc, j.prec, j.mcap, j.optin, j.nwarps, Q, j.det, j.gpm16)) P = Q;
     }
     cudaError_t e;
     // the deterministic instantiations are other kernels: their attribute is
@@ -138,6 +138,7 @@ static cudaError_t launch_atm_one(const ForceJob& j, size_t* smem_set, bool* cap
         a.ulist = ulist;
         a.ucount = ucount;
         a.det = j.det;
+        a.emax = j.emax;
         return launch_atm_fp64(j.trav, j.trunc, a, P.nwarps, P.smem, ctas, j.st);
     }
     AtmArgs<float> a{};
@@ -156,6 +157,7 @@ static cudaError_t launch_atm_one(const ForceJob& j, size_t* smem_set, bool* cap
     a.ucount = ucount;
     a.det = j.det;
     a.pmask = atm_uses_pair_masks(j) ? j.pmask : nullptr;
+    a.emax = j.emax;
     return launch_atm_fp32(j.trav, j.trunc, a, P.nwarps, P.smem, ctas, j.st);
 }
 
@@ -190,7 +192,7 @@ static cudaError_t enqueue_atm_launches(const ForceJob& j, size_t* smem_set, boo
         // every launch's plan must fit before anything is enqueued
         AtmPlan P;
         const int limit = (j.trav == 0 || j.trav == 3) ? 65535 : ATM_MCAP_LIMIT;
-        if (j.mcap > limit || !atm_choose_plan(j.trav, j.trunc, j.prec, j.mcap, j.optin, P, j.det)) {
+        if (j.mcap > limit || !atm_choose_plan(j.trav, j.trunc, j.prec, j.mcap, j.optin, P, j.det, j.gpm16)) {
             *capacity = true;
             return cudaErrorInvalidValue;
         }

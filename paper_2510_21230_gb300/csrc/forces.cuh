@@ -65,6 +65,11 @@ struct ForceJob {
     // The caller passes it only when every cell holds at most PM_CELL_MAX
     // molecules (a fuller cell found on the device sets ST_CAPACITY)
     unsigned* pmask = nullptr;
+    // pair rule of the block traversals: edge-table capacity in 1/16 edges per
+    // staged molecule (256: 16), and where the units record their need
+    // (nullptr: not recorded)
+    int gpm16 = 256;
+    int* emax = nullptr;
 };
 
 cudaError_t enqueue_lj(const ForceJob& j);

@@ -354,6 +354,38 @@ def test_dense_liquid_edge_table_overflow(atm3, trav, prec):
     assert_forces_close(f, ref["f"], RTOL[prec], "dense " + trav + prec)
 
 
+@pytest.mark.parametrize("trav", ["3c18", "3c08", "3c08a"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_edge_table_follows_the_recorded_need(atm3, trav, prec):
+    """Outside the deterministic mode the pair rule's edge table is sized from
+    the needs the units recorded in earlier evaluations of the context.  A
+    liquid at rho* 0.5 sets a small capacity; the same context then evaluates
+    a state whose molecules are packed into one corner region at rho* 0.8:
+    its first evaluation overflows the small table (those units fall back to
+    per-molecule accumulators), the second sizes the table from the new need.
+    Both equal the oracle, with the same counts."""
+    cfg = synth.homogeneous(2000, 0.5, 1.0, seed=1004)
+    box = np.broadcast_to(np.asarray(cfg["box"], dtype=np.float64), (3,))
+    packed = np.ascontiguousarray(np.mod(cfg["x"], box[:, None]) * (0.5 / 0.8) ** (1.0 / 3.0))
+    prm = oracle.params(cfg["box"], 2.5, NU)
+    ref = oracle.atm_cells(prm, packed, trav, "pair", ORC_PREC[prec])
+    got = []
+    with atm3.AtmSystem(cfg["box"], cfg["n"], nu=NU) as s:
+        s.set_state(cfg["x"])
+        s.build_cells()
+        for _ in range(2):
+            s.compute_forces(trav, "pair", prec)
+        s.set_state(packed)
+        s.build_cells()
+        for _ in range(2):
+            r = s.compute_forces(trav, "pair", prec)
+            got.append((r, s.get_forces("atm")))
+    for r, f in got:
+        assert r["n_cand3"] == ref["n_cand3"] and r["n_int3"] == ref["n_int3"]
+        assert r["e3"] == pytest.approx(ref["e3"], rel=RTOL[prec])
+        assert_forces_close(f, ref["f"], RTOL[prec], "recorded need " + trav + prec)
+
+
 # ------------------------------------------------------------------ wide traversal
 
 def _wide_liquid():
