@@ -448,7 +448,6 @@ static atm_status launch_cells(atm_ctx* c)
     return ATM_OK;
 }
 
-// cell build + read back of the occupancy maxima that size the force kernels
 // the unit sizes of the last cell build and the edge-table needs recorded by
 // the units so far (h_maxocc, after a synchronisation): each traversal's
 // table capacity becomes its need plus a quarter edge per staged molecule
@@ -467,6 +466,7 @@ static void take_unit_sizes(atm_ctx* c)
     }
 }
 
+// cell build + read back of the occupancy maxima that size the force kernels
 static atm_status enqueue_cells(atm_ctx* c)
 {
     atm_status s = launch_cells(c);
@@ -560,8 +560,6 @@ static void launch_choice(atm_ctx* c, int trav, int trunc, int prec, int mcap, i
     }
 }
 
-// LJ + ATM force kernels for the current cells; mcap = staged-molecule capacity
-// FP32 pair rule of a block traversal, bitmaps enabled, every cell within 32
 // pair rule of a block traversal outside the deterministic mode (whose
 // results must not depend on the context's history): the units record their
 // edge-table need and the table is sized from it
@@ -577,6 +575,7 @@ static int edge_capacity(const atm_ctx* c, int trav, int trunc)
     return measured_edges(c, trav, trunc) ? c->gpm16[trav] : 256;
 }
 
+// FP32 pair rule of a block traversal, bitmaps enabled, every cell within 32
 static bool use_pair_masks(const atm_ctx* c, int trav, int trunc, int prec)
 {
     return c->opt_pmask && c->pmask && prec == ATM_FP32C && trunc == ATM_TRUNC_PAIR &&
@@ -584,6 +583,7 @@ static bool use_pair_masks(const atm_ctx* c, int trav, int trunc, int prec)
            c->maxocc <= atm3::PM_CELL_MAX;
 }
 
+// LJ + ATM force kernels for the current cells; mcap = staged-molecule capacity
 atm_status atm3::ctx_enqueue_forces(atm_ctx* c, int trav, int trunc, int prec, int mcap,
                                     bool fuse_lj)
 {
