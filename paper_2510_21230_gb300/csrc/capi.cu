@@ -374,7 +374,7 @@ static void invalidate(atm_ctx* c)
 // the device (the copy's data, one pass); synchronises, so the caller may
 // reuse its buffer on return.  *bad: a non-finite element was found
 // copies host arrays (a, and b when given, m doubles each) to the device,
-// checks them for non-finite values there and waits once for the verdict
+// checks them for non-finite values there and waits once for their result
 static atm_status copy_in_checked(atm_ctx* c, double* dev_a, const double* host_a, double* dev_b,
                                   const double* host_b, long long m, bool* bad)
 {
@@ -1039,7 +1039,7 @@ extern "C" atm_status atm_step_host(atm_ctx* c, int nsteps, atm_traversal trav,
     CU(cudaSetDevice(c->device));
     const long long m = 3 * c->n;
     const size_t bytes = (size_t)m * sizeof(double);
-    // inputs: copies and device-side finite checks; the verdict travels back
+    // inputs: copies and device-side finite checks; the checks' result travels back
     // with the first synchronisation of the step (its cell build) or the last
     // (each check runs on io_st while the next copy runs on the stream)
     *c->h_chk = 0;
