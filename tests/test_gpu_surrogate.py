@@ -69,8 +69,11 @@ def test_descriptors_match_oracle(atm3, liquid, liquid_desc):
     assert np.all(np.abs(V - Vo) <= 1e-4 * _colscale(Vo))
 
 
-def test_descriptors_sampled_rows_n32k(atm3):
-    cfg = synth.config("liquid_n32k")
+@pytest.mark.parametrize("workload", ["liquid_n32k", "liquid_n256k"])
+def test_descriptors_sampled_rows(atm3, workload):
+    """400 sampled rows of the 32,000- and the 256,000-molecule liquids (the
+    size the benchmark's surrogate runs) against the oracle's descriptors."""
+    cfg = synth.config(workload)
     prm = oracle.params(cfg["box"], RC, NU)
     rows = np.random.default_rng(5).choice(cfg["n"], 400, replace=False)
     Do, Vo = oracle.sur_descriptors(prm, cfg["x"], rows)
