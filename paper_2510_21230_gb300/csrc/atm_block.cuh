@@ -19,10 +19,10 @@
 //     popcounts) and listed as (p, q); FP64 also tabulates their vectors.
 //  3. A warp takes 32 edges (p, q) at a time.  The triangles of an edge are
 //     the set bits r > q of adj[p] & adj[q] & (slots allowed as third member):
-//     counted per lane (per word, packed in bytes), prefix-summed over the
-//     warp and expanded 32 per round, so every pair test is shared by all the
-//     triplets that contain the pair and every lane of a round evaluates one
-//     triangle.
+//     counted per lane (3c18: per word, packed in bytes), prefix-summed over
+//     the warp and expanded 32 per round, so every pair test is shared by all
+//     the triplets that contain the pair and every lane of a round evaluates
+//     one triangle.
 // Product rule
 //  1. Dense FP32 squared distances (or on-the-fly when they do not fit).
 //  3. Every candidate p < q < r of the unit's tasks, enumerated q-major, is
