@@ -47,10 +47,10 @@ FP64_FLOPS_PER_CLK_SM = 1.25e12 / (SMS * 2.07e9)
 F3 = {"3c01": 109.0, "3c18": 127.0, "3c08": 127.0, "3c08a": 127.0}
 
 # Useful flops per interacting LJ pair when a step evaluates LJ inside the
-# 3c08 units (3c08 / 3c08a, pair rule): displacement and square 14, the LJ
-# scalar 9, energy and virial 4 (the force vector is the ATM gather's).
+# block units (3c08 / 3c18 / 3c08a, pair rule): displacement and square 14,
+# the LJ scalar 9, energy and virial 4 (the force vector is the ATM gather's).
 F2_FUSED = 27.0
-FUSED_TRAV = ("3c08", "3c08a")
+FUSED_TRAV = ("3c08", "3c18", "3c08a")
 
 # DRAM traffic per ATM evaluation (dram__bytes_read.sum + dram__bytes_write.sum
 # of its kernels -- the FP32C pair rule's pair-bitmap kernel and the block
@@ -404,6 +404,7 @@ def run_ours(args):
 
     # variants (same state, fewer steps)
     variants = []
+    vpeak = {args.prec: measured}  # measured FMA peaks per precision
     if not args.no_variants and rank == 0:
         for tv, tr, pr, det in [("3c08", "pair", "fp64", False), ("3c18", "pair", "fp32c", False),
                                 ("3c08", "product", "fp32c", False), ("3c18", "pair", "fp64", False),
@@ -417,11 +418,24 @@ def run_ours(args):
             if det:
                 sysm.set_deterministic(False)
             am = r["prof"]["ms_atm"] / max(1, r["prof"]["n_atm_launches"])
+            # useful flops over the ATM evaluation's time, against the measured
+            # FMA peak of the variant's precision
+            vflops = F3[tv] * r["res"]["n_int3"]
+            if tv in FUSED_TRAV and tr == "pair":
+                vflops += F2_FUSED * r["res"]["n_int2"]
+            if pr not in vpeak:
+                vpeak[pr] = atm3.measure_fma_peak(local, pr == "fp64")
+            vach = vflops / (am * 1e-3) / 1e12
             variants.append({"traversal": tv, "truncation": tr, "precision": pr,
                              "deterministic": det,
                              "value": n * k / (r["ms"] * 1e-3), "ms_per_step": r["ms"] / k,
                              "atm_ms_per_launch": am, "mups_3body": n / (am * 1e-3),
-                             "n_int3": r["res"]["n_int3"]})
+                             "n_int3": r["res"]["n_int3"],
+                             "roofline": {"bound": "alu", "achieved": vach, "peak": vpeak[pr],
+                                          "unit": "TFLOP/s",
+                                          "frac": vach / vpeak[pr] if vpeak[pr] else None,
+                                          "peak_source": "measured: atm_measure_fma_peak, %s FMA "
+                                          "chains on every SM" % ("FP64" if pr == "fp64" else "FP32")}})
             if det and tuning is not None:
                 # the mode switch reset the tuned launch form: tune again
                 sysm.build_cells()
